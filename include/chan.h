@@ -1,0 +1,168 @@
+/*
+ * chan.h — C ABI of a single-GPU (sm_103a) library that advances the
+ * velocity–vorticity (v–omega_2) formulation of incompressible turbulent
+ * channel flow by semi-implicit low-storage RK3 substeps, and writes the
+ * filtered velocities and filtered stresses of the second-order-consistent
+ * database of Vela-Martin et al., arXiv:1808.06461.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Units: channel half-height h = 1 (walls at y = -1 and y = +1), friction
+ *   velocity u_tau = 1, so nu = 1 / Re_tau (Sec. 2.1).
+ * Grid: Nx, Nz are the collocation points of the periodic directions
+ *   (Sec. 2.1: N_1/2, N_3/2 Fourier modes, 3/2-rule dealiasing); Ny is the
+ *   number of wall-normal points (odd, >= 9).  Nx, Nz must be even and of
+ *   the form 2^a 3^b with 3Nx/2, 3Nz/2 in [6, 4608].
+ * Fourier field layout ("spectral layout"): interleaved complex double
+ *   (re, im), C order [Ny][Nz][Nx/2], i.e. element (j, jz, kx) at
+ *   2 * ((j * Nz + jz) * (Nx/2) + kx).  kx = 0 .. Nx/2-1 (k_1 = 2 pi kx / Lx);
+ *   jz in FFT order (k_3 = 2 pi kz / Lz, kz = jz for jz < Nz/2, jz - Nz
+ *   otherwise).  The kz Nyquist row jz = Nz/2 is held at zero.  A kx > 0
+ *   coefficient stands for itself and its complex conjugate at -kx; the
+ *   kx = 0 column must be Hermitian in kz.  Physical fields are
+ *   u(x, z) = sum u_k exp(+i (k_1 x + k_3 z)).
+ * Profiles (U1, U3, statistics): double[Ny], index j of the mesh returned by
+ *   chan_get_grid.
+ * Ownership: a chan_t owns all the device memory it allocates; every
+ *   pointer argument is caller-owned and only read or written during the
+ *   call.  Host pointers may be pageable or pinned.
+ * Streams: all device work of a handle runs in order on one CUDA stream
+ *   (the library's own, or the caller's via chan_opts.stream).  Entry points
+ *   that return host data synchronise that stream before returning;
+ *   chan_step is asynchronous.
+ * Errors: every int-returning call returns CHAN_OK (0) or a negative
+ *   CHAN_E* code and records a message readable with chan_last_error.  No
+ *   call aborts the process or traps the GPU.
+ */
+#ifndef CHAN_H
+#define CHAN_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CHAN_OK        0
+#define CHAN_EINVAL   -1   /* bad argument: sizes, dt <= 0, NULL handle, unknown kind   */
+#define CHAN_ENOMEM   -2   /* device or host allocation failed                           */
+#define CHAN_ECUDA    -3   /* a CUDA runtime call or kernel launch failed                */
+#define CHAN_ENAN     -4   /* the state holds a non-finite value (checked on read-back)  */
+#define CHAN_ESTATE   -5   /* call out of order (e.g. chan_step before chan_set_state)   */
+
+#define CHAN_FILTER_SHARP 0   /* Eq. (fou_fil): G = 1 if |k1| < pi/l1c and |k3| < pi/l3c   */
+#define CHAN_FILTER_BOX   1   /* top-hat of widths (D1, D3): G = sinc(k1 D1/2) sinc(k3 D3/2) */
+
+#define CHAN_PREC_FP64  0     /* every step in FP64                                        */
+#define CHAN_PREC_MIXED 1     /* FFTs and products in FP32; y-solves, mean flow, stats FP64 */
+
+#define CHAN_NSTAT 20         /* rows of chan_stats' output, see chan_stats                */
+
+typedef struct chan_s* chan_t;
+
+typedef struct chan_opts {
+  double re_tau;     /* friction Reynolds number; nu = 1/re_tau                      */
+  double Lx, Lz;     /* periods of the box in x (streamwise) and z (spanwise)        */
+  int Nx, Ny, Nz;    /* collocation points                                           */
+  double dt;         /* time step of a full RK3 step (each substep uses dt)          */
+  double eta_w;      /* wall Kolmogorov scale of the mesh (default 1.0)              */
+  double grid_re;    /* Re_tau the mesh is clustered for (<= 0: re_tau)              */
+  int precision;     /* CHAN_PREC_FP64 or CHAN_PREC_MIXED                            */
+  void* stream;      /* cudaStream_t to run on, or NULL for a library-owned stream   */
+} chan_opts;
+
+/* Fill *o with defaults: eta_w = 1, grid_re = 0, FP64, library stream. */
+void chan_opts_default(chan_opts* o);
+
+/*
+ * Create a channel on the current CUDA device (Sec. 2.1 / Appendix A set-up):
+ * mesh, compact finite-difference operators (Appendix B), per-wavenumber
+ * LU factors of the implicit RK3 Helmholtz and Poisson operators, their
+ * homogeneous solutions and influence matrices.  No state yet: call
+ * chan_set_state next.  *out receives the handle (NULL on failure).
+ */
+int chan_init(chan_t* out, double re_tau, double Lx, double Lz, int Nx, int Ny, int Nz, double dt);
+int chan_init_ex(chan_t* out, const chan_opts* o);
+
+/* Release everything the handle owns.  NULL is a no-op. */
+void chan_free(chan_t h);
+
+/* Message of the last error on this handle (or of the last failed init when h is NULL). */
+const char* chan_last_error(chan_t h);
+
+/* Number of complex coefficients of one Fourier field: Ny * Nz * (Nx/2). */
+size_t chan_fourier_count(chan_t h);
+
+/* Bytes of device memory the handle holds. */
+size_t chan_device_bytes(chan_t h);
+
+/* Wall-normal mesh, double[Ny] (Sec. 2.1: spacing ~ local Kolmogorov scale). */
+int chan_get_grid(chan_t h, double* y);
+
+/*
+ * Set the state from host arrays: v = u_2 and omega_2 in spectral layout,
+ * U1, U3 the mean profiles (zero at the walls).  Derives chi = Lap v and
+ * dv/dy on the device, clears the previous-substep non-linear terms, sets
+ * the target mass flux to the flux of U1 and the RK3 substep counter to 0.
+ * The (0,0) Fourier coefficients of v and omega_2 are ignored (held at 0).
+ */
+int chan_set_state(chan_t h, const double* v, const double* omega2, const double* U1, const double* U3);
+/* Same with device pointers (same layouts). */
+int chan_set_state_device(chan_t h, const void* v, const void* omega2, const void* U1, const void* U3);
+
+/* Copy the current state out (host; synchronises). */
+int chan_get_state(chan_t h, double* v, double* omega2, double* U1, double* U3);
+/* Device-to-device copy of the state into caller buffers (asynchronous). */
+int chan_get_state_device(chan_t h, void* v, void* omega2, void* U1, void* U3);
+
+/*
+ * Advance nsub RK3 substeps (Appendix A, Eqs. (chi1), (chi2), (psi); order of
+ * operations of Appendix C): u_1, u_3 and their y-derivatives from
+ * (v, omega_2); vorticity; dealiased H = u x omega; N_chi and N_omega2
+ * (Eq. (hghv)); implicit Helmholtz steps for omega_2 and chi; Poisson for
+ * v with the influence-matrix wall correction; mean profiles with the
+ * constant-flux pressure gradient.  Asynchronous on the handle's stream.
+ */
+int chan_step(chan_t h, int nsub);
+
+/*
+ * Filtered velocities ubar_i = G u_i and stresses
+ * tau_ij = G P(u_i u_j) - P(ubar_i ubar_j) of the current state (Sec. 3.1),
+ * P the dealiased projection on the stored modes.  kind is CHAN_FILTER_*;
+ * (p1, p3) are l_1c^+, l_3c^+ for SHARP (the paper uses 120, 60) or the
+ * box widths Delta_x^+, Delta_z^+ for BOX.  ubar receives 3 fields and tau
+ * 6 fields (order 11, 22, 33, 12, 13, 23), spectral layout, field-major;
+ * either may be NULL (the result is still kept for chan_stats).  Does not
+ * advance time.  Synchronises when a host pointer is given.
+ */
+int chan_filter_stresses(chan_t h, int kind, double p1, double p3, double* ubar, double* tau);
+
+/*
+ * Plane statistics of the current state (Sec. 3.3), double[CHAN_NSTAT][Ny]:
+ * rows 0-1 U1, U3; rows 2-7 <u_i u_j> (11,22,33,12,13,23, Parseval over
+ * all stored modes, means included); rows 8-13 <ubar_i ubar_j> and rows
+ * 14-19 <tau_ij> of the last chan_filter_stresses (zero if none).  utau =
+ * sqrt(nu |dU1/dy|) averaged over both walls, ubulk = flux/2, f = mean
+ * pressure gradient of the last substep.  Any output pointer may be NULL.
+ * Synchronises.
+ */
+int chan_stats(chan_t h, double* out, double* utau, double* ubulk, double* f);
+
+/*
+ * Dealiased Fourier coefficients of H = u x omega of the current state
+ * (3 fields, spectral layout, field-major, host), without advancing time.
+ * A diagnostic of the non-linear pass (Appendix A, Eq. (hghv) input).
+ */
+int chan_nonlinear(chan_t h, double* H);
+
+/* Wait for the handle's stream. */
+int chan_sync(chan_t h);
+
+/* Simulated time and substeps taken since chan_set_state. */
+double chan_time(chan_t h);
+long long chan_substeps(chan_t h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CHAN_H */

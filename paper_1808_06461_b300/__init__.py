@@ -1,0 +1,231 @@
+"""Python binding of the B300 channel library (``libchan.so``, C ABI in include/chan.h).
+
+Argument marshalling only: every step of the substep runs in the library's
+CUDA kernels.  Importing this module does not need a GPU; creating a
+channel does.  If the shared object is missing the import raises -- there
+is no CPU fallback.
+
+Host arrays are numpy complex128 of shape (Ny, Nz, Nx//2) for Fourier
+fields (index [j, jz, kx], kz in FFT order, kz Nyquist row zero) and
+float64 of shape (Ny,) for profiles.  Device arrays (the ``*_device``
+calls) are torch tensors with the same shapes and dtypes.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libchan.so")
+
+CHAN_OK, CHAN_EINVAL, CHAN_ENOMEM, CHAN_ECUDA, CHAN_ENAN, CHAN_ESTATE = 0, -1, -2, -3, -4, -5
+CHAN_FILTER_SHARP, CHAN_FILTER_BOX = 0, 1
+CHAN_PREC_FP64, CHAN_PREC_MIXED = 0, 1
+CHAN_NSTAT = 20
+
+# Exported symbols, exactly the declarations of include/chan.h.
+SYMBOLS = ("chan_opts_default", "chan_init", "chan_init_ex", "chan_free", "chan_last_error",
+           "chan_fourier_count", "chan_device_bytes", "chan_get_grid", "chan_set_state",
+           "chan_set_state_device", "chan_get_state", "chan_get_state_device", "chan_step",
+           "chan_filter_stresses", "chan_stats", "chan_nonlinear", "chan_sync", "chan_time",
+           "chan_substeps")
+
+
+class chan_opts(ctypes.Structure):
+    _fields_ = [("re_tau", ctypes.c_double), ("Lx", ctypes.c_double), ("Lz", ctypes.c_double),
+                ("Nx", ctypes.c_int), ("Ny", ctypes.c_int), ("Nz", ctypes.c_int),
+                ("dt", ctypes.c_double), ("eta_w", ctypes.c_double), ("grid_re", ctypes.c_double),
+                ("precision", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+class ChanError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("chan error %d: %s" % (code, msg))
+        self.code = code
+
+
+def load_library(path=LIB_PATH):
+    if not os.path.exists(path):
+        raise ImportError("libchan.so not built (run paper_1808_06461_b300/build.py); "
+                          "the channel substep has no fallback implementation")
+    lib = ctypes.CDLL(path)
+    P, D, I, S = ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_size_t
+    DP = ctypes.POINTER(ctypes.c_double)
+    sig = {
+        "chan_opts_default": (None, [ctypes.POINTER(chan_opts)]),
+        "chan_init": (I, [ctypes.POINTER(P), D, D, D, I, I, I, D]),
+        "chan_init_ex": (I, [ctypes.POINTER(P), ctypes.POINTER(chan_opts)]),
+        "chan_free": (None, [P]),
+        "chan_last_error": (ctypes.c_char_p, [P]),
+        "chan_fourier_count": (S, [P]),
+        "chan_device_bytes": (S, [P]),
+        "chan_get_grid": (I, [P, DP]),
+        "chan_set_state": (I, [P, P, P, P, P]),
+        "chan_set_state_device": (I, [P, P, P, P, P]),
+        "chan_get_state": (I, [P, P, P, P, P]),
+        "chan_get_state_device": (I, [P, P, P, P, P]),
+        "chan_step": (I, [P, I]),
+        "chan_filter_stresses": (I, [P, I, D, D, P, P]),
+        "chan_stats": (I, [P, P, DP, DP, DP]),
+        "chan_nonlinear": (I, [P, P]),
+        "chan_sync": (I, [P]),
+        "chan_time": (D, [P]),
+        "chan_substeps": (ctypes.c_longlong, [P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = load_library()
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("host arrays must be C-contiguous")
+        return a.ctypes.data_as(ctypes.c_void_p)
+    return ctypes.c_void_p(int(a.data_ptr()))   # torch tensor on the device
+
+
+def _check(h, rc):
+    if rc != CHAN_OK:
+        raise ChanError(rc, _lib.chan_last_error(h).decode())
+
+
+class Channel:
+    """One channel box on the current CUDA device (owns its device memory)."""
+
+    def __init__(self, re_tau, Lx, Lz, Nx, Ny, Nz, dt, precision=CHAN_PREC_FP64, eta_w=1.0,
+                 grid_re=0.0, stream=None):
+        o = chan_opts()
+        _lib.chan_opts_default(ctypes.byref(o))
+        o.re_tau, o.Lx, o.Lz, o.Nx, o.Ny, o.Nz, o.dt = re_tau, Lx, Lz, Nx, Ny, Nz, dt
+        o.eta_w, o.grid_re, o.precision = eta_w, grid_re, precision
+        o.stream = stream
+        h = ctypes.c_void_p()
+        rc = _lib.chan_init_ex(ctypes.byref(h), ctypes.byref(o))
+        if rc != CHAN_OK:
+            raise ChanError(rc, _lib.chan_last_error(None).decode())
+        self.h = h
+        self.Nx, self.Ny, self.Nz, self.nxh = Nx, Ny, Nz, Nx // 2
+        self.shape = (Ny, Nz, Nx // 2)
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.chan_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- queries
+    def grid(self):
+        y = np.empty(self.Ny)
+        _check(self.h, _lib.chan_get_grid(self.h, y.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return y
+
+    def device_bytes(self):
+        return int(_lib.chan_device_bytes(self.h))
+
+    def time(self):
+        return float(_lib.chan_time(self.h))
+
+    def substeps(self):
+        return int(_lib.chan_substeps(self.h))
+
+    # ---- state
+    def set_state(self, v, omega2, U1, U3):
+        v = np.ascontiguousarray(v, dtype=np.complex128)
+        om = np.ascontiguousarray(omega2, dtype=np.complex128)
+        U1 = np.ascontiguousarray(U1, dtype=np.float64)
+        U3 = np.ascontiguousarray(U3, dtype=np.float64)
+        if v.shape != self.shape or om.shape != self.shape or U1.shape != (self.Ny,) or U3.shape != (self.Ny,):
+            raise ValueError("state shapes must be %s and (%d,)" % (self.shape, self.Ny))
+        _check(self.h, _lib.chan_set_state(self.h, _ptr(v), _ptr(om), _ptr(U1), _ptr(U3)))
+
+    def set_state_device(self, v, omega2, U1, U3):
+        _check(self.h, _lib.chan_set_state_device(self.h, _ptr(v), _ptr(omega2), _ptr(U1), _ptr(U3)))
+
+    def get_state(self):
+        v = np.empty(self.shape, dtype=np.complex128)
+        om = np.empty(self.shape, dtype=np.complex128)
+        U1 = np.empty(self.Ny)
+        U3 = np.empty(self.Ny)
+        _check(self.h, _lib.chan_get_state(self.h, _ptr(v), _ptr(om), _ptr(U1), _ptr(U3)))
+        return dict(v=v, omega2=om, U1=U1, U3=U3)
+
+    def get_state_device(self, v, omega2, U1, U3):
+        _check(self.h, _lib.chan_get_state_device(self.h, _ptr(v), _ptr(omega2), _ptr(U1), _ptr(U3)))
+
+    # ---- the substep and its outputs
+    def step(self, nsub=1):
+        _check(self.h, _lib.chan_step(self.h, int(nsub)))
+
+    def sync(self):
+        _check(self.h, _lib.chan_sync(self.h))
+
+    def nonlinear(self):
+        H = np.empty((3,) + self.shape, dtype=np.complex128)
+        _check(self.h, _lib.chan_nonlinear(self.h, _ptr(H)))
+        return H
+
+    def filter_stresses(self, kind, p1, p3, want=True):
+        ub = np.empty((3,) + self.shape, dtype=np.complex128) if want else None
+        tau = np.empty((6,) + self.shape, dtype=np.complex128) if want else None
+        _check(self.h, _lib.chan_filter_stresses(self.h, int(kind), float(p1), float(p3), _ptr(ub), _ptr(tau)))
+        return ub, tau
+
+    def stats(self):
+        out = np.empty((CHAN_NSTAT, self.Ny))
+        ut, ub, f = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        _check(self.h, _lib.chan_stats(self.h, _ptr(out), ctypes.byref(ut), ctypes.byref(ub), ctypes.byref(f)))
+        return out, ut.value, ub.value, f.value
+
+
+# Module-level functions with the C names, for callers that prefer them.
+def chan_init(re_tau, Lx, Lz, Nx, Ny, Nz, dt, **kw):
+    return Channel(re_tau, Lx, Lz, Nx, Ny, Nz, dt, **kw)
+
+
+def chan_set_state(ch, v, omega2, U1, U3):
+    ch.set_state(v, omega2, U1, U3)
+
+
+def chan_get_state(ch):
+    return ch.get_state()
+
+
+def chan_step(ch, nsub=1):
+    ch.step(nsub)
+
+
+def chan_filter_stresses(ch, kind, p1, p3):
+    return ch.filter_stresses(kind, p1, p3)
+
+
+def chan_stats(ch):
+    return ch.stats()
+
+
+def chan_nonlinear(ch):
+    return ch.nonlinear()
+
+
+def chan_free(ch):
+    ch.close()
+
+
+def chan_sync(ch):
+    ch.sync()
+
+
+def library():
+    return _lib

@@ -1,0 +1,441 @@
+// C ABI of the channel library (declared in include/chan.h): handle life
+// cycle, device memory, state I/O and the ordering of the substep kernels.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "chan_internal.cuh"
+
+double chan_rk3_weight(int s);
+
+namespace {
+
+thread_local std::string g_init_err;
+
+struct Fail {
+  int code;
+};
+
+#define CK(call)                                                                        \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess) {                                                            \
+      h->err = std::string(#call) + ": " + cudaGetErrorString(e_);                     \
+      throw Fail{e_ == cudaErrorMemoryAllocation ? CHAN_ENOMEM : CHAN_ECUDA};           \
+    }                                                                                   \
+  } while (0)
+
+int bad(chan_s* h, const std::string& msg, int code = CHAN_EINVAL) {
+  if (h) h->err = msg;
+  else g_init_err = msg;
+  return code;
+}
+
+template <typename T>
+T* dalloc(chan_s* h, size_t n) {
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, n * sizeof(T));
+  if (e != cudaSuccess) {
+    h->err = std::string("cudaMalloc of ") + std::to_string(n * sizeof(T)) + " bytes: " + cudaGetErrorString(e);
+    throw Fail{CHAN_ENOMEM};
+  }
+  h->allocs.push_back(p);
+  h->dev_bytes += n * sizeof(T);
+  return static_cast<T*>(p);
+}
+
+bool is_2a3b(int n) {
+  if (n < 1) return false;
+  while (n % 2 == 0) n /= 2;
+  while (n % 3 == 0) n /= 3;
+  return n == 1;
+}
+
+__global__ void k_flux(const double* U1, const double* wq, int Ny, double* scal) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double q = 0.0;
+    for (int i = 0; i < Ny; ++i) q += wq[i] * U1[i];
+    scal[1] = q;
+    scal[0] = 0.0;
+  }
+}
+
+size_t fsize(const chan_s* h) { return (size_t)h->Ny * h->M; }
+
+// Work-field slots (Fourier layout)
+enum { WF_U1 = 0, WF_U3 = 1, WF_OM1 = 2, WF_OM3 = 3, WF_H1 = 4, WF_H2 = 5, WF_H3 = 6, WF_NCHI = 7, WF_NOM = 8, NWF = 14 };
+
+double2* wf(chan_s* h, int k) { return h->wf + (size_t)k * fsize(h); }
+void* mixed(chan_s* h, int k) {
+  const size_t es = h->prec == CHAN_PREC_FP64 ? sizeof(double2) : sizeof(float2);
+  return static_cast<char*>(h->mixed) + (size_t)k * h->Ny * h->L3 * h->nxh * es;
+}
+
+void clean_modes(chan_s* h, double2* f) {
+  const size_t pitch = (size_t)h->M * sizeof(double2);
+  CK(cudaMemset2DAsync(f, pitch, 0, sizeof(double2), h->Ny, h->stream));                    // (0,0) mode
+  CK(cudaMemset2DAsync(f + (size_t)(h->Nz / 2) * h->nxh, pitch, 0, (size_t)h->nxh * sizeof(double2), h->Ny,
+                       h->stream));                                                             // kz Nyquist row
+}
+
+void after_state_upload(chan_s* h) {
+  clean_modes(h, h->v);
+  clean_modes(h, h->om);
+  CK(launch_derive(h));
+  CK(cudaMemsetAsync(h->Nchi_p, 0, fsize(h) * sizeof(double2), h->stream));
+  CK(cudaMemsetAsync(h->Nom_p, 0, fsize(h) * sizeof(double2), h->stream));
+  CK(cudaMemsetAsync(h->H1m_p, 0, h->Ny * sizeof(double), h->stream));
+  CK(cudaMemsetAsync(h->H3m_p, 0, h->Ny * sizeof(double), h->stream));
+  k_flux<<<1, 32, 0, h->stream>>>(h->U1, h->tab_wq, h->Ny, h->scal);
+  CK(cudaGetLastError());
+  h->have_state = true;
+  h->have_filter = false;
+  h->nsub = 0;
+  h->t = 0.0;
+}
+
+// u_1, u_3, omega_1, omega_3 of the current state into the work slots.
+void run_pre(chan_s* h) { CK(launch_pre(h, wf(h, WF_U1), wf(h, WF_U3), wf(h, WF_OM1), wf(h, WF_OM3))); }
+
+// H = u x omega of the current state into WF_H1..WF_H3 (after run_pre).
+void run_nonlinear(chan_s* h) {
+  const double2* in[6] = {wf(h, WF_U1), h->v, wf(h, WF_U3), wf(h, WF_OM1), h->om, wf(h, WF_OM3)};
+  void* mx[6] = {mixed(h, 0), mixed(h, 1), mixed(h, 2), mixed(h, 3), mixed(h, 4), mixed(h, 5)};
+  CK(launch_zinv(h, in, nullptr, mx, 6));
+  CK(launch_xpass(h, 0, mx, mx));
+  double2* Hout[3] = {wf(h, WF_H1), wf(h, WF_H2), wf(h, WF_H3)};
+  CK(launch_zfwd(h, mx, Hout, 3));
+}
+
+void run_substep(chan_s* h) {
+  const int s = (int)(h->nsub % 3);
+  run_pre(h);
+  run_nonlinear(h);
+  CK(launch_nonlin(h, wf(h, WF_H1), wf(h, WF_H2), wf(h, WF_H3), wf(h, WF_NCHI), wf(h, WF_NOM)));
+  CK(launch_helm(h, wf(h, WF_NCHI), wf(h, WF_NOM), s));
+  CK(launch_poisson(h, s));
+  CK(launch_mean(h, wf(h, WF_H1), wf(h, WF_H3), s));
+  h->t += chan_rk3_weight(s) * h->dt;
+  h->nsub += 1;
+}
+
+void ensure_filter_buffers(chan_s* h) {
+  if (h->G) return;
+  h->G = dalloc<double>(h, h->M);
+}
+
+}  // namespace
+
+// The filter outputs (3 ubar + 6 tau fields) live behind the work slots.
+static double2* filt(chan_s* h, int k) { return h->wf + (size_t)(NWF + k) * fsize(h); }
+
+extern "C" {
+
+void chan_opts_default(chan_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->eta_w = 1.0;
+  o->grid_re = 0.0;
+  o->precision = CHAN_PREC_FP64;
+  o->stream = nullptr;
+}
+
+int chan_init(chan_t* out, double re_tau, double Lx, double Lz, int Nx, int Ny, int Nz, double dt) {
+  chan_opts o;
+  chan_opts_default(&o);
+  o.re_tau = re_tau; o.Lx = Lx; o.Lz = Lz; o.Nx = Nx; o.Ny = Ny; o.Nz = Nz; o.dt = dt;
+  return chan_init_ex(out, &o);
+}
+
+int chan_init_ex(chan_t* out, const chan_opts* o) {
+  if (!out) return bad(nullptr, "chan_init: out is NULL");
+  *out = nullptr;
+  if (!o) return bad(nullptr, "chan_init: opts is NULL");
+  if (!(o->re_tau > 0) || !(o->Lx > 0) || !(o->Lz > 0) || !(o->dt > 0) || !std::isfinite(o->dt))
+    return bad(nullptr, "chan_init: re_tau, Lx, Lz and dt must be positive");
+  if (o->Nx < 2 || o->Nx % 2 || !is_2a3b(o->Nx)) return bad(nullptr, "chan_init: Nx must be even and 2^a 3^b");
+  if (o->Nz < 4 || o->Nz % 4 || !is_2a3b(o->Nz)) return bad(nullptr, "chan_init: Nz must be a multiple of 4 and 2^a 3^b");
+  if (o->Ny < 9 || o->Ny % 2 == 0) return bad(nullptr, "chan_init: Ny must be odd and >= 9");
+  if (o->precision != CHAN_PREC_FP64 && o->precision != CHAN_PREC_MIXED) return bad(nullptr, "chan_init: unknown precision");
+  const int L1 = 3 * o->Nx / 2, L3 = 3 * o->Nz / 2;
+  const size_t es = o->precision == CHAN_PREC_FP64 ? 16 : 8;
+  if (2 * 6 * (size_t)(L1 + 1) * es > 227 * 1024 || 2 * (size_t)(L3 + 1) * es > 100 * 1024)
+    return bad(nullptr, "chan_init: 3Nx/2 or 3Nz/2 too long for an in-block transform at this precision "
+                        "(FP64: Nx <= 768, mixed: Nx <= 1536)");
+  chan_s* h = new (std::nothrow) chan_s();
+  if (!h) return bad(nullptr, "chan_init: out of host memory", CHAN_ENOMEM);
+  h->re = o->re_tau; h->Lx = o->Lx; h->Lz = o->Lz; h->dt = o->dt; h->nu = 1.0 / o->re_tau;
+  h->eta_w = o->eta_w > 0 ? o->eta_w : 1.0;
+  h->grid_re = o->grid_re > 0 ? o->grid_re : o->re_tau;
+  h->Nx = o->Nx; h->Ny = o->Ny; h->Nz = o->Nz; h->nxh = o->Nx / 2;
+  h->M = h->Nz * h->nxh; h->C = (h->Nz / 2) * h->nxh;
+  h->L1 = L1; h->L3 = L3; h->prec = o->precision;
+  h->have_state = h->have_filter = false;
+  h->nsub = 0; h->t = 0.0; h->dev_bytes = 0;
+  h->G = nullptr;
+  int rc = CHAN_OK;
+  chanh_tables tb;
+  std::memset(&tb, 0, sizeof(tb));
+  try {
+    CK(cudaGetDevice(&h->device));
+    if (o->stream) { h->stream = (cudaStream_t)o->stream; h->own_stream = false; }
+    else { CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking)); h->own_stream = true; }
+    int hr = chanh_build(h->Ny, h->grid_re, h->eta_w, &tb);
+    if (hr) { h->err = "chan_init: compact-scheme set-up failed (singular coefficient system or LU pivot)"; throw Fail{CHAN_EINVAL}; }
+    h->y.assign(tb.y, tb.y + h->Ny);
+    h->wq.assign(tb.wq, tb.wq + h->Ny);
+    h->p1.L = L1; h->p1.np = chanh_radix_plan(L1, h->p1.radix);
+    h->p3.L = L3; h->p3.np = chanh_radix_plan(L3, h->p3.radix);
+    const size_t n = fsize(h), Ny = h->Ny;
+    // state
+    h->v = dalloc<double2>(h, n); h->om = dalloc<double2>(h, n); h->chi = dalloc<double2>(h, n);
+    h->dv = dalloc<double2>(h, n); h->Nchi_p = dalloc<double2>(h, n); h->Nom_p = dalloc<double2>(h, n);
+    h->U1 = dalloc<double>(h, Ny); h->U3 = dalloc<double>(h, Ny);
+    h->H1m_p = dalloc<double>(h, Ny); h->H3m_p = dalloc<double>(h, Ny);
+    h->scal = dalloc<double>(h, 2);
+    // tables
+    double** dst[] = {&h->tab_A2, &h->tab_B2, &h->tab_B1, &h->tab_lu1, &h->tab_lu2f};
+    const double* src[] = {tb.A2, tb.B2, tb.B1, tb.lu1, tb.lu2f};
+    for (int k = 0; k < 5; ++k) {
+      *dst[k] = dalloc<double>(h, 7 * Ny);
+      CK(cudaMemcpy(*dst[k], src[k], 7 * Ny * sizeof(double), cudaMemcpyHostToDevice));
+    }
+    h->tab_d0 = dalloc<double>(h, Ny); h->tab_dN = dalloc<double>(h, Ny); h->tab_wq = dalloc<double>(h, Ny);
+    CK(cudaMemcpy(h->tab_d0, tb.d0, Ny * sizeof(double), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->tab_dN, tb.dN, Ny * sizeof(double), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->tab_wq, tb.wq, Ny * sizeof(double), cudaMemcpyHostToDevice));
+    std::vector<double> k1(h->nxh), k3(h->Nz);
+    for (int kx = 0; kx < h->nxh; ++kx) k1[kx] = 2.0 * M_PI / h->Lx * kx;
+    for (int jz = 0; jz < h->Nz; ++jz) k3[jz] = 2.0 * M_PI / h->Lz * (jz < h->Nz / 2 ? jz : jz - h->Nz);
+    h->k1 = dalloc<double>(h, h->nxh); h->k3 = dalloc<double>(h, h->Nz);
+    CK(cudaMemcpy(h->k1, k1.data(), h->nxh * sizeof(double), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->k3, k3.data(), h->Nz * sizeof(double), cudaMemcpyHostToDevice));
+    h->pois = dalloc<double>(h, Ny * 7 * (size_t)h->C);
+    h->helm = dalloc<double>(h, 3 * Ny * 11 * (size_t)h->C);
+    h->infl = dalloc<double>(h, 3 * 4 * (size_t)h->C);
+    // twiddles in the transform precision
+    for (int which = 0; which < 2; ++which) {
+      const int L = which ? L3 : L1;
+      std::vector<double> tw(2 * (size_t)L);
+      chanh_twiddles(L, tw.data());
+      void* d;
+      if (h->prec == CHAN_PREC_FP64) {
+        d = dalloc<double2>(h, L);
+        CK(cudaMemcpy(d, tw.data(), L * sizeof(double2), cudaMemcpyHostToDevice));
+      } else {
+        std::vector<float> twf(2 * (size_t)L);
+        for (size_t k = 0; k < twf.size(); ++k) twf[k] = (float)tw[k];
+        d = dalloc<float2>(h, L);
+        CK(cudaMemcpy(d, twf.data(), L * sizeof(float2), cudaMemcpyHostToDevice));
+      }
+      (which ? h->tw3 : h->tw1) = d;
+    }
+    // work
+    h->nwf = NWF + 9;
+    h->wf = dalloc<double2>(h, (size_t)h->nwf * n);
+    h->nmix = 12;
+    h->mixed = dalloc<unsigned char>(h, (size_t)h->nmix * Ny * L3 * h->nxh * es);
+    h->scr = dalloc<double2>(h, 2 * n);
+    h->stat = dalloc<double>(h, CHAN_NSTAT * Ny + 2);
+    CK(fft_configure(h));
+    CK(launch_setup_tables(h));
+    CK(cudaStreamSynchronize(h->stream));
+  } catch (Fail f) {
+    rc = f.code;
+  }
+  chanh_free(&tb);
+  if (rc != CHAN_OK) {
+    g_init_err = h->err;
+    chan_free(h);
+    return rc;
+  }
+  *out = h;
+  return CHAN_OK;
+}
+
+void chan_free(chan_t h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  for (void* p : h->allocs) cudaFree(p);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+const char* chan_last_error(chan_t h) { return h ? h->err.c_str() : g_init_err.c_str(); }
+
+size_t chan_fourier_count(chan_t h) { return h ? fsize(h) : 0; }
+size_t chan_device_bytes(chan_t h) { return h ? h->dev_bytes : 0; }
+
+int chan_get_grid(chan_t h, double* y) {
+  if (!h || !y) return bad(h, "chan_get_grid: NULL argument");
+  std::memcpy(y, h->y.data(), h->Ny * sizeof(double));
+  return CHAN_OK;
+}
+
+static int set_state_impl(chan_t h, const void* v, const void* om, const void* U1, const void* U3, cudaMemcpyKind k) {
+  if (!h) return bad(nullptr, "chan_set_state: NULL handle");
+  if (!v || !om || !U1 || !U3) return bad(h, "chan_set_state: NULL array");
+  try {
+    const size_t n = fsize(h);
+    CK(cudaMemcpyAsync(h->v, v, n * sizeof(double2), k, h->stream));
+    CK(cudaMemcpyAsync(h->om, om, n * sizeof(double2), k, h->stream));
+    CK(cudaMemcpyAsync(h->U1, U1, h->Ny * sizeof(double), k, h->stream));
+    CK(cudaMemcpyAsync(h->U3, U3, h->Ny * sizeof(double), k, h->stream));
+    after_state_upload(h);
+    if (k == cudaMemcpyHostToDevice) CK(cudaStreamSynchronize(h->stream));
+  } catch (Fail f) {
+    return f.code;
+  }
+  return CHAN_OK;
+}
+
+int chan_set_state(chan_t h, const double* v, const double* om, const double* U1, const double* U3) {
+  return set_state_impl(h, v, om, U1, U3, cudaMemcpyHostToDevice);
+}
+int chan_set_state_device(chan_t h, const void* v, const void* om, const void* U1, const void* U3) {
+  return set_state_impl(h, v, om, U1, U3, cudaMemcpyDeviceToDevice);
+}
+
+static int get_state_impl(chan_t h, void* v, void* om, void* U1, void* U3, cudaMemcpyKind k) {
+  if (!h) return bad(nullptr, "chan_get_state: NULL handle");
+  if (!h->have_state) return bad(h, "chan_get_state: no state set", CHAN_ESTATE);
+  try {
+    const size_t n = fsize(h);
+    if (v) CK(cudaMemcpyAsync(v, h->v, n * sizeof(double2), k, h->stream));
+    if (om) CK(cudaMemcpyAsync(om, h->om, n * sizeof(double2), k, h->stream));
+    if (U1) CK(cudaMemcpyAsync(U1, h->U1, h->Ny * sizeof(double), k, h->stream));
+    if (U3) CK(cudaMemcpyAsync(U3, h->U3, h->Ny * sizeof(double), k, h->stream));
+    if (k == cudaMemcpyDeviceToHost) {
+      CK(cudaStreamSynchronize(h->stream));
+      if (U1) {
+        const double* u = static_cast<const double*>(U1);
+        for (int i = 0; i < h->Ny; ++i)
+          if (!std::isfinite(u[i])) return bad(h, "chan_get_state: non-finite mean profile", CHAN_ENAN);
+      }
+    }
+  } catch (Fail f) {
+    return f.code;
+  }
+  return CHAN_OK;
+}
+
+int chan_get_state(chan_t h, double* v, double* om, double* U1, double* U3) {
+  return get_state_impl(h, v, om, U1, U3, cudaMemcpyDeviceToHost);
+}
+int chan_get_state_device(chan_t h, void* v, void* om, void* U1, void* U3) {
+  return get_state_impl(h, v, om, U1, U3, cudaMemcpyDeviceToDevice);
+}
+
+int chan_step(chan_t h, int nsub) {
+  if (!h) return bad(nullptr, "chan_step: NULL handle");
+  if (nsub < 0) return bad(h, "chan_step: nsub < 0");
+  if (!h->have_state) return bad(h, "chan_step: no state set", CHAN_ESTATE);
+  try {
+    for (int k = 0; k < nsub; ++k) run_substep(h);
+  } catch (Fail f) {
+    return f.code;
+  }
+  h->have_filter = false;
+  return CHAN_OK;
+}
+
+int chan_nonlinear(chan_t h, double* H) {
+  if (!h || !H) return bad(h, "chan_nonlinear: NULL argument");
+  if (!h->have_state) return bad(h, "chan_nonlinear: no state set", CHAN_ESTATE);
+  try {
+    run_pre(h);
+    run_nonlinear(h);
+    CK(cudaMemcpyAsync(H, wf(h, WF_H1), 3 * fsize(h) * sizeof(double2), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+  } catch (Fail f) {
+    return f.code;
+  }
+  return CHAN_OK;
+}
+
+int chan_filter_stresses(chan_t h, int kind, double p1, double p3, double* ubar, double* tau) {
+  if (!h) return bad(nullptr, "chan_filter_stresses: NULL handle");
+  if (kind != CHAN_FILTER_SHARP && kind != CHAN_FILTER_BOX) return bad(h, "chan_filter_stresses: unknown kind");
+  if (!(p1 > 0) || !(p3 > 0)) return bad(h, "chan_filter_stresses: widths must be positive");
+  if (!h->have_state) return bad(h, "chan_filter_stresses: no state set", CHAN_ESTATE);
+  try {
+    ensure_filter_buffers(h);
+    // transfer function on the stored modes (Nyquist row zero)
+    std::vector<double> G(h->M);
+    for (int jz = 0; jz < h->Nz; ++jz)
+      for (int kx = 0; kx < h->nxh; ++kx) {
+        const double k1 = 2.0 * M_PI / h->Lx * kx;
+        const double k3 = 2.0 * M_PI / h->Lz * (jz < h->Nz / 2 ? jz : jz - h->Nz);
+        double g;
+        if (kind == CHAN_FILTER_SHARP) {
+          g = (std::fabs(k1) < M_PI * h->re / p1 && std::fabs(k3) < M_PI * h->re / p3) ? 1.0 : 0.0;
+        } else {
+          const double a = 0.5 * k1 * p1 / h->re, b = 0.5 * k3 * p3 / h->re;
+          g = (a == 0.0 ? 1.0 : std::sin(a) / a) * (b == 0.0 ? 1.0 : std::sin(b) / b);
+        }
+        G[(size_t)jz * h->nxh + kx] = (jz == h->Nz / 2) ? 0.0 : g;
+      }
+    CK(cudaMemcpyAsync(h->G, G.data(), h->M * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    run_pre(h);
+    const double2* in[6] = {wf(h, WF_U1), h->v, wf(h, WF_U3), wf(h, WF_U1), h->v, wf(h, WF_U3)};
+    const int applyG[6] = {0, 0, 0, 1, 1, 1};
+    void* mx[12];
+    for (int k = 0; k < 12; ++k) mx[k] = mixed(h, k);
+    CK(launch_zinv(h, in, applyG, mx, 6));
+    CK(launch_xpass(h, 1, mx + 3, mx + 6));   // ubar_i ubar_j -> slots 6..11
+    CK(launch_xpass(h, 1, mx, mx));           // u_i u_j       -> slots 0..5
+    double2* fo[12];
+    for (int k = 0; k < 12; ++k) fo[k] = wf(h, 2 + k);
+    CK(launch_zfwd(h, mx, fo, 12));
+    const double2* u[3] = {wf(h, WF_U1), h->v, wf(h, WF_U3)};
+    const double2* puu[6] = {fo[0], fo[1], fo[2], fo[3], fo[4], fo[5]};
+    const double2* pbb[6] = {fo[6], fo[7], fo[8], fo[9], fo[10], fo[11]};
+    CK(launch_filter_out(h, u, puu, pbb, filt(h, 0), filt(h, 3)));
+    const size_t n = fsize(h);
+    if (ubar) CK(cudaMemcpyAsync(ubar, filt(h, 0), 3 * n * sizeof(double2), cudaMemcpyDeviceToHost, h->stream));
+    if (tau) CK(cudaMemcpyAsync(tau, filt(h, 3), 6 * n * sizeof(double2), cudaMemcpyDeviceToHost, h->stream));
+    if (ubar || tau) CK(cudaStreamSynchronize(h->stream));
+    h->have_filter = true;
+  } catch (Fail f) {
+    return f.code;
+  }
+  return CHAN_OK;
+}
+
+int chan_stats(chan_t h, double* out, double* utau, double* ubulk, double* f) {
+  if (!h) return bad(nullptr, "chan_stats: NULL handle");
+  if (!h->have_state) return bad(h, "chan_stats: no state set", CHAN_ESTATE);
+  try {
+    run_pre(h);
+    CK(launch_stats(h, wf(h, WF_U1), wf(h, WF_U3), h->have_filter ? filt(h, 0) : nullptr,
+                    h->have_filter ? filt(h, 3) : nullptr, h->have_filter ? 1 : 0));
+    std::vector<double> st(CHAN_NSTAT * (size_t)h->Ny + 2);
+    double sc[2];
+    CK(cudaMemcpyAsync(st.data(), h->stat, st.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(sc, h->scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (out) std::memcpy(out, st.data(), CHAN_NSTAT * (size_t)h->Ny * sizeof(double));
+    if (utau) *utau = st[CHAN_NSTAT * (size_t)h->Ny];
+    if (ubulk) *ubulk = st[CHAN_NSTAT * (size_t)h->Ny + 1];
+    if (f) *f = sc[0];
+    for (size_t k = 0; k < st.size(); ++k)
+      if (!std::isfinite(st[k])) return bad(h, "chan_stats: non-finite statistics", CHAN_ENAN);
+  } catch (Fail f) {
+    return f.code;
+  }
+  return CHAN_OK;
+}
+
+int chan_sync(chan_t h) {
+  if (!h) return bad(nullptr, "chan_sync: NULL handle");
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return bad(h, std::string("chan_sync: ") + cudaGetErrorString(e), CHAN_ECUDA);
+  return CHAN_OK;
+}
+
+double chan_time(chan_t h) { return h ? h->t : 0.0; }
+long long chan_substeps(chan_t h) { return h ? h->nsub : 0; }
+
+}  // extern "C"

@@ -1,0 +1,43 @@
+// Host-side set-up tables of the channel library (internal header).
+#pragma once
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+// Banded operators are stored row-major as [ny][7]: entry d of row i is the
+// coefficient of column i - 3 + d (zero outside the row's stencil).
+// LU factors of a (3,3)-banded matrix without pivoting are packed as
+// [ny][7]: l(i, i-3..i-1), u(i, i+1..i+3), 1/u(i, i).
+typedef struct chanh_tables {
+  int ny;
+  double* y;     // mesh
+  double* A2;    // second derivative:  A2 f'' = B2 f
+  double* B2;
+  double* A1;    // first derivative:   A1 f' = B1 f
+  double* B1;
+  double* lu1;   // LU of A1 (all rows)
+  double* lu2f;  // LU of A2 (all rows)
+  double* d0;    // row 0 of A1^-1 B1 (dv/dy at y = -1 as a dot product), [ny]
+  double* dN;    // row ny-1 of A1^-1 B1, [ny]
+  double* wq;    // trapezoid weights of the flux integral, [ny]
+} chanh_tables;
+
+// Build every table for an ny-point mesh clustered for grid_re (returns 0,
+// or -1 for bad arguments, -2 for allocation failure, -3 when a pivot of a
+// coefficient system or an LU vanishes).
+int chanh_build(int ny, double grid_re, double eta_w, chanh_tables* t);
+void chanh_free(chanh_tables* t);
+
+// The same mesh formula as the tables use (double[ny]).
+int chanh_ygrid(int ny, double grid_re, double eta_w, double* y);
+
+// Twiddles w_t = exp(-2 pi i t / L), t = 0..L-1, interleaved (re, im).
+void chanh_twiddles(int L, double* tw);
+
+// Radix plan of a 2^a 3^b length: radices 4, 2, 3 in execution order.
+// Returns the number of passes (<= 16) or -1 if L is not 2^a 3^b.
+int chanh_radix_plan(int L, int* radix);
+
+#ifdef __cplusplus
+}
+#endif

@@ -1,0 +1,97 @@
+// Internal declarations of the channel library (device state, kernel
+// launchers).  Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/chan.h"
+#include "chan_host.h"
+
+// Fourier fields: double2 arrays [Ny][M], M = Nz * (Nx/2), mode m = jz*nxh + kx.
+// Mixed fields (physical z, Fourier kx): [Ny][L3][nxh] of float2 or double2.
+// Wavenumber classes (shared LU factors): c = |kz| * nxh + kx, |kz| < Nz/2.
+
+#define CHAN_MAXFIELDS 12
+
+struct YTabs {            // mode-independent wall-normal tables (device)
+  const double* A2;       // [Ny][7]
+  const double* B2;
+  const double* B1;
+  const double* lu1;      // LU of A1
+  const double* lu2f;     // LU of A2 (all rows)
+  const double* d0;       // [Ny]
+  const double* dN;
+  const double* wq;
+};
+
+struct Geo {
+  int Nx, Ny, Nz, nxh, M, C, L1, L3;
+  double dt, nu;
+  const double* k1;       // [nxh]
+  const double* k3;       // [Nz]
+};
+
+struct FftPlan {
+  int L, np;
+  int radix[16];
+};
+
+struct chan_s {
+  // configuration
+  double re, Lx, Lz, dt, nu, eta_w, grid_re;
+  int Nx, Ny, Nz, nxh, M, C, L1, L3, prec;
+  cudaStream_t stream;
+  bool own_stream;
+  int device;
+  // host copies
+  std::vector<double> y, wq;
+  // state (device)
+  double2 *v, *om, *chi, *dv, *Nchi_p, *Nom_p;
+  double *U1, *U3, *H1m_p, *H3m_p;
+  double* scal;            // [0] f of last substep, [1] Q0
+  // tables (device)
+  double *tab_A2, *tab_B2, *tab_B1, *tab_lu1, *tab_lu2f, *tab_d0, *tab_dN, *tab_wq;
+  double *k1, *k3;
+  double* helm;            // [3][Ny][11][C]
+  double* pois;            // [Ny][7][C]
+  double* infl;            // [3][4][C]
+  void *tw1, *tw3;         // twiddles of L1, L3 in the FFT precision
+  // work (device)
+  double2* wf;             // Fourier work fields [NWF][Ny][M]
+  int nwf;
+  void* mixed;             // mixed fields [NMIX][Ny][L3][nxh]
+  int nmix;
+  double2* scr;            // wall-normal sweep scratch [2][Ny][M]
+  double* G;               // filter transfer [M]
+  double* stat;            // [CHAN_NSTAT][Ny] + [2] (utau, ubulk)
+  // bookkeeping
+  bool have_state, have_filter;
+  long long nsub;
+  double t;
+  size_t dev_bytes;
+  std::string err;
+  FftPlan p1, p3;
+  std::vector<void*> allocs;
+};
+
+// Kernel launchers (return cudaGetLastError()).
+cudaError_t launch_setup_tables(chan_s* h);
+cudaError_t launch_derive(chan_s* h);
+cudaError_t launch_pre(chan_s* h, double2* u1, double2* u3, double2* om1, double2* om3);
+cudaError_t launch_nonlin(chan_s* h, const double2* H1, const double2* H2, const double2* H3,
+                          double2* Nchi, double2* Nom);
+cudaError_t launch_helm(chan_s* h, const double2* Nchi, const double2* Nom, int s);
+cudaError_t launch_poisson(chan_s* h, int s);
+cudaError_t launch_mean(chan_s* h, const double2* H1, const double2* H3, int s);
+cudaError_t launch_filter_out(chan_s* h, const double2* const* u, const double2* const* puu,
+                              const double2* const* pbb, double2* ubar, double2* tau);
+cudaError_t launch_stats(chan_s* h, const double2* u1, const double2* u3, const double2* ubar,
+                         const double2* tau, int with_filter);
+
+// FFT passes.  in/out are arrays of nf device pointers.
+cudaError_t launch_zinv(chan_s* h, const double2* const* in, const int* apply_G, void* const* out, int nf);
+cudaError_t launch_xpass(chan_s* h, int mode, void* const* in, void* const* out);
+cudaError_t launch_zfwd(chan_s* h, void* const* in, double2* const* out, int nf);
+cudaError_t fft_configure(chan_s* h);

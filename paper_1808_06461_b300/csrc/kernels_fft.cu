@@ -1,0 +1,358 @@
+// Dealiased Fourier passes of the channel substep (Sec. 2.1 of
+// arXiv:1808.06461: 3/2-rule zero padding in x and z; Appendix C: the
+// non-linear terms H = u x omega are formed in physical space).
+//
+// One x-z plane at a time never leaves the device: a z-pass transforms the
+// columns of a plane (zero-padding kz from Nz to 3Nz/2), an x-pass turns two
+// physical z-rows at once into real space (two real rows packed into one
+// complex FFT), forms the products there and transforms them back, and a
+// final z-pass truncates to the stored modes.  All transforms are in-CTA
+// shared-memory Stockham FFTs with radix 4, 2 and 3 passes.
+#include <cstring>
+
+#include "chan_internal.cuh"
+
+namespace {
+
+template <typename T> struct V2;
+template <> struct V2<double> { typedef double2 t; };
+template <> struct V2<float> { typedef float2 t; };
+
+template <typename T2> struct Scal;
+template <> struct Scal<double2> { typedef double t; };
+template <> struct Scal<float2> { typedef float t; };
+
+template <typename T2> __device__ __forceinline__ T2 mk(double x, double y);
+template <> __device__ __forceinline__ double2 mk<double2>(double x, double y) { return make_double2(x, y); }
+template <> __device__ __forceinline__ float2 mk<float2>(double x, double y) { return make_float2((float)x, (float)y); }
+
+template <typename T2> __device__ __forceinline__ T2 cmul(T2 a, T2 b) {
+  T2 r;
+  r.x = a.x * b.x - a.y * b.y;
+  r.y = a.x * b.y + a.y * b.x;
+  return r;
+}
+template <typename T2> __device__ __forceinline__ T2 cadd(T2 a, T2 b) { T2 r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
+template <typename T2> __device__ __forceinline__ T2 csub(T2 a, T2 b) { T2 r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
+
+// Radix-R DFT in registers.  DIR = -1: exp(-2 pi i jk/R) (forward); +1: inverse.
+template <int DIR, typename T2> __device__ __forceinline__ void dft2(T2* v) {
+  T2 a = v[0], b = v[1];
+  v[0] = cadd(a, b);
+  v[1] = csub(a, b);
+}
+template <int DIR, typename T2> __device__ __forceinline__ void dft4(T2* v) {
+  T2 t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+  T2 t2 = cadd(v[1], v[3]), d = csub(v[1], v[3]);
+  T2 t3;  // DIR * i * d
+  if (DIR < 0) { t3.x = d.y; t3.y = -d.x; } else { t3.x = -d.y; t3.y = d.x; }
+  v[0] = cadd(t0, t2);
+  v[2] = csub(t0, t2);
+  v[1] = cadd(t1, t3);
+  v[3] = csub(t1, t3);
+}
+template <int DIR, typename T2> __device__ __forceinline__ void dft3(T2* v) {
+  typedef typename Scal<T2>::t T;
+  const T h = (T)0.86602540378443864676;  // sqrt(3)/2
+  T2 s = cadd(v[1], v[2]), d = csub(v[1], v[2]);
+  T2 y0 = cadd(v[0], s);
+  T2 mm;
+  mm.x = v[0].x - (T)0.5 * s.x;
+  mm.y = v[0].y - (T)0.5 * s.y;
+  // y1 = m + DIR * i * h * d, y2 = m - DIR * i * h * d
+  T2 r;
+  if (DIR < 0) { r.x = h * d.y; r.y = -h * d.x; } else { r.x = -h * d.y; r.y = h * d.x; }
+  v[0] = y0;
+  v[1] = cadd(mm, r);
+  v[2] = csub(mm, r);
+}
+
+// One Stockham pass of radix R over nb transforms of length L (p = product of
+// the radices already applied): butterfly i reads src[i + q L/R], twiddles
+// input q by w^(q k), k = i mod p, and writes dst[(i - k) R + k + q p].
+template <int R, int DIR, typename T2>
+__device__ __forceinline__ void fft_pass(const T2* __restrict__ a, T2* __restrict__ b, int L, int nb, int ld,
+                                         const T2* __restrict__ tw, int p) {
+  const int nbf = L / R;
+  const int tstep = L / (p * R);
+  const int total = nb * nbf;
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    const int bi = t / nbf;
+    const int i = t - bi * nbf;
+    const int k = i % p;
+    const T2* src = a + bi * ld;
+    T2* dst = b + bi * ld;
+    T2 v[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      T2 x = src[i + q * nbf];
+      if (q > 0 && k > 0) {
+        T2 w = tw[q * k * tstep];
+        if (DIR > 0) w.y = -w.y;
+        x = cmul(x, w);
+      }
+      v[q] = x;
+    }
+    if (R == 4) dft4<DIR>(v);
+    else if (R == 2) dft2<DIR>(v);
+    else dft3<DIR>(v);
+    const int base = (i - k) * R + k;
+#pragma unroll
+    for (int q = 0; q < R; ++q) dst[base + q * p] = v[q];
+  }
+}
+
+// Batched Stockham FFT of nb transforms of length L stored at a + b*ld.
+// Passes alternate between the two buffers; the return value holds the
+// result.  tw[t] = exp(-2 pi i t / L); inverse passes use its conjugate.
+template <int DIR, typename T2>
+__device__ T2* fft_batch(T2* a, T2* b, int L, int nb, int ld, const T2* __restrict__ tw, const FftPlan& pl) {
+  int p = 1;
+  for (int ps = 0; ps < pl.np; ++ps) {
+    const int R = pl.radix[ps];
+    if (R == 4) fft_pass<4, DIR>(a, b, L, nb, ld, tw, p);
+    else if (R == 2) fft_pass<2, DIR>(a, b, L, nb, ld, tw, p);
+    else fft_pass<3, DIR>(a, b, L, nb, ld, tw, p);
+    __syncthreads();
+    T2* tmp = a; a = b; b = tmp;
+    p *= R;
+  }
+  return a;
+}
+
+struct ZArgs {
+  const double2* in[CHAN_MAXFIELDS];
+  double2* outd[CHAN_MAXFIELDS];
+  void* out[CHAN_MAXFIELDS];
+  int applyG[CHAN_MAXFIELDS];
+  const double* G;
+  int Ny, Nz, nxh, M, L3, KB, ld;
+  FftPlan pl;
+};
+
+// Inverse z-pass: Fourier [Ny][Nz][nxh] (double) -> mixed [Ny][L3][nxh] (T),
+// kz zero-padded to 3Nz/2 (the kz Nyquist row is dropped), optional filter
+// transfer G applied on load.
+template <typename T>
+__global__ void __launch_bounds__(256) k_zinv(ZArgs A, const typename V2<T>::t* __restrict__ tw) {
+  typedef typename V2<T>::t T2;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T2* a = reinterpret_cast<T2*>(smraw);
+  T2* b = a + A.KB * A.ld;
+  const int f = blockIdx.z, y = blockIdx.y, kx0 = blockIdx.x * A.KB;
+  const int hz = A.Nz / 2;
+  for (int e = threadIdx.x; e < A.KB * A.ld; e += blockDim.x) a[e] = mk<T2>(0.0, 0.0);
+  __syncthreads();
+  const double2* in = A.in[f] + (size_t)y * A.M;
+  for (int e = threadIdx.x; e < A.Nz * A.KB; e += blockDim.x) {
+    const int jz = e / A.KB, kl = e - jz * A.KB, kx = kx0 + kl;
+    if (kx >= A.nxh || jz == hz) continue;
+    double2 val = in[jz * A.nxh + kx];
+    if (A.applyG[f]) {
+      const double gg = A.G[jz * A.nxh + kx];
+      val.x *= gg;
+      val.y *= gg;
+    }
+    const int pz = jz < hz ? jz : jz + (A.L3 - A.Nz);
+    a[kl * A.ld + pz] = mk<T2>(val.x, val.y);
+  }
+  __syncthreads();
+  T2* r = fft_batch<+1>(a, b, A.L3, A.KB, A.ld, tw, A.pl);
+  T2* out = reinterpret_cast<T2*>(A.out[f]) + (size_t)y * A.L3 * A.nxh;
+  for (int e = threadIdx.x; e < A.L3 * A.KB; e += blockDim.x) {
+    const int z = e / A.KB, kl = e - z * A.KB, kx = kx0 + kl;
+    if (kx < A.nxh) out[(size_t)z * A.nxh + kx] = r[kl * A.ld + z];
+  }
+}
+
+// Forward z-pass: mixed (T) -> Fourier (double), truncation to the stored kz.
+template <typename T>
+__global__ void __launch_bounds__(256) k_zfwd(ZArgs A, const typename V2<T>::t* __restrict__ tw) {
+  typedef typename V2<T>::t T2;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T2* a = reinterpret_cast<T2*>(smraw);
+  T2* b = a + A.KB * A.ld;
+  const int f = blockIdx.z, y = blockIdx.y, kx0 = blockIdx.x * A.KB;
+  const int hz = A.Nz / 2;
+  const T2* in = reinterpret_cast<const T2*>(A.out[f]) + (size_t)y * A.L3 * A.nxh;
+  for (int e = threadIdx.x; e < A.L3 * A.KB; e += blockDim.x) {
+    const int z = e / A.KB, kl = e - z * A.KB, kx = kx0 + kl;
+    a[kl * A.ld + z] = kx < A.nxh ? in[(size_t)z * A.nxh + kx] : mk<T2>(0.0, 0.0);
+  }
+  __syncthreads();
+  T2* r = fft_batch<-1>(a, b, A.L3, A.KB, A.ld, tw, A.pl);
+  double2* out = A.outd[f] + (size_t)y * A.M;
+  for (int e = threadIdx.x; e < A.Nz * A.KB; e += blockDim.x) {
+    const int jz = e / A.KB, kl = e - jz * A.KB, kx = kx0 + kl;
+    if (kx >= A.nxh) continue;
+    double2 val = make_double2(0.0, 0.0);
+    if (jz != hz) {
+      const int pz = jz < hz ? jz : jz + (A.L3 - A.Nz);
+      T2 x = r[kl * A.ld + pz];
+      val = make_double2((double)x.x, (double)x.y);
+    }
+    out[jz * A.nxh + kx] = val;
+  }
+}
+
+struct XArgs {
+  void* in[CHAN_MAXFIELDS];
+  void* out[CHAN_MAXFIELDS];
+  int nxh, L1, L3, ld;
+  double scale;  // 1 / (L1 L3): analysis normalisation of the padded grid
+  FftPlan pl;
+};
+
+// x-pass on the physical z-rows (z0, z0+1) of plane y.  MODE 0: inputs
+// (u1, u2, u3, w1, w2, w3) -> H = u x omega (3 outputs).  MODE 1: inputs
+// (u1, u2, u3) -> the six products u_i u_j (11, 22, 33, 12, 13, 23).
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256) k_xpass(XArgs A, const typename V2<T>::t* __restrict__ tw) {
+  typedef typename V2<T>::t T2;
+  constexpr int NIN = MODE == 0 ? 6 : 3;
+  constexpr int NOUT = MODE == 0 ? 3 : 6;
+  constexpr int NB = 6;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T2* a = reinterpret_cast<T2*>(smraw);
+  T2* b = a + NB * A.ld;
+  const int z0 = 2 * blockIdx.x, y = blockIdx.y;
+  const int L1 = A.L1, nxh = A.nxh, ld = A.ld;
+  for (int e = threadIdx.x; e < NIN * ld; e += blockDim.x) a[e] = mk<T2>(0.0, 0.0);
+  __syncthreads();
+  // pack rows z0 (real part) and z0+1 (imaginary part) with Hermitian extension in kx
+  for (int e = threadIdx.x; e < NIN * nxh; e += blockDim.x) {
+    const int f = e / nxh, k = e - f * nxh;
+    const T2* row = reinterpret_cast<const T2*>(A.in[f]) + ((size_t)y * A.L3 + z0) * nxh;
+    T2 P = row[k], Q = row[nxh + k];
+    T2* dstf = a + f * ld;
+    if (k == 0) {
+      dstf[0] = mk<T2>(P.x, Q.x);
+    } else {
+      T2 c1, c2;
+      c1.x = P.x - Q.y; c1.y = P.y + Q.x;      // P_k + i Q_k
+      c2.x = P.x + Q.y; c2.y = -P.y + Q.x;     // conj(P_k) + i conj(Q_k) at -k
+      dstf[k] = c1;
+      dstf[L1 - k] = c2;
+    }
+  }
+  __syncthreads();
+  T2* r = fft_batch<+1>(a, b, L1, NIN, ld, tw, A.pl);
+  T2* o = (r == a) ? b : a;
+  for (int x = threadIdx.x; x < L1; x += blockDim.x) {
+    T2 q[NIN];
+#pragma unroll
+    for (int f = 0; f < NIN; ++f) q[f] = r[f * ld + x];
+    if (MODE == 0) {
+      // H1 = u2 w3 - u3 w2, H2 = u3 w1 - u1 w3, H3 = u1 w2 - u2 w1 (both rows at once)
+      T2 h1, h2, h3;
+      h1.x = q[1].x * q[5].x - q[2].x * q[4].x; h1.y = q[1].y * q[5].y - q[2].y * q[4].y;
+      h2.x = q[2].x * q[3].x - q[0].x * q[5].x; h2.y = q[2].y * q[3].y - q[0].y * q[5].y;
+      h3.x = q[0].x * q[4].x - q[1].x * q[3].x; h3.y = q[0].y * q[4].y - q[1].y * q[3].y;
+      o[0 * ld + x] = h1;
+      o[1 * ld + x] = h2;
+      o[2 * ld + x] = h3;
+    } else {
+      const int pi[6] = {0, 1, 2, 0, 0, 1}, pj[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+      for (int p = 0; p < 6; ++p) {
+        T2 w;
+        w.x = q[pi[p]].x * q[pj[p]].x;
+        w.y = q[pi[p]].y * q[pj[p]].y;
+        o[p * ld + x] = w;
+      }
+    }
+  }
+  __syncthreads();
+  T2* s = fft_batch<-1>(o, r, L1, NOUT, ld, tw, A.pl);
+  const T half = (T)(0.5 * A.scale);
+  for (int e = threadIdx.x; e < NOUT * nxh; e += blockDim.x) {
+    const int gq = e / nxh, k = e - gq * nxh;
+    const T2 c = s[gq * ld + k];
+    const T2 cm = s[gq * ld + (k == 0 ? 0 : L1 - k)];
+    T2 F, G;
+    F.x = half * (c.x + cm.x); F.y = half * (c.y - cm.y);      // (C_k + conj C_-k) / 2
+    G.x = half * (c.y + cm.y); G.y = -half * (c.x - cm.x);     // (C_k - conj C_-k) / 2i
+    T2* row = reinterpret_cast<T2*>(A.out[gq]) + ((size_t)y * A.L3 + z0) * nxh;
+    row[k] = F;
+    row[nxh + k] = G;
+  }
+}
+
+template <typename T> size_t esize() { return sizeof(typename V2<T>::t); }
+
+int pick_kb(int nxh, int L3, size_t es) {
+  int kb = 1;
+  while (kb * 2 <= nxh && kb * 2 <= 16 && 2 * (size_t)(kb * 2) * (L3 + 1) * es <= 100 * 1024) kb *= 2;
+  return kb;
+}
+
+}  // namespace
+
+cudaError_t fft_configure(chan_s* h) {
+  const void* fns[] = {(const void*)k_zinv<double>, (const void*)k_zinv<float>, (const void*)k_zfwd<double>,
+                       (const void*)k_zfwd<float>, (const void*)k_xpass<double, 0>, (const void*)k_xpass<double, 1>,
+                       (const void*)k_xpass<float, 0>, (const void*)k_xpass<float, 1>};
+  for (const void* f : fns) {
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+static ZArgs zargs(chan_s* h, size_t es) {
+  ZArgs A;
+  memset(&A, 0, sizeof(A));
+  A.Ny = h->Ny; A.Nz = h->Nz; A.nxh = h->nxh; A.M = h->M; A.L3 = h->L3;
+  A.KB = pick_kb(h->nxh, h->L3, es);
+  A.ld = h->L3 + 1;
+  A.pl = h->p3;
+  A.G = h->G;
+  return A;
+}
+
+cudaError_t launch_zinv(chan_s* h, const double2* const* in, const int* apply_G, void* const* out, int nf) {
+  const bool dbl = h->prec == CHAN_PREC_FP64;
+  const size_t es = dbl ? sizeof(double2) : sizeof(float2);
+  ZArgs A = zargs(h, es);
+  for (int f = 0; f < nf; ++f) { A.in[f] = in[f]; A.out[f] = out[f]; A.applyG[f] = apply_G ? apply_G[f] : 0; }
+  dim3 grid((h->nxh + A.KB - 1) / A.KB, h->Ny, nf);
+  size_t sm = 2 * (size_t)A.KB * A.ld * es;
+  if (dbl) k_zinv<double><<<grid, 256, sm, h->stream>>>(A, (const double2*)h->tw3);
+  else k_zinv<float><<<grid, 256, sm, h->stream>>>(A, (const float2*)h->tw3);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zfwd(chan_s* h, void* const* in, double2* const* out, int nf) {
+  const bool dbl = h->prec == CHAN_PREC_FP64;
+  const size_t es = dbl ? sizeof(double2) : sizeof(float2);
+  ZArgs A = zargs(h, es);
+  for (int f = 0; f < nf; ++f) { A.out[f] = in[f]; A.outd[f] = out[f]; }
+  dim3 grid((h->nxh + A.KB - 1) / A.KB, h->Ny, nf);
+  size_t sm = 2 * (size_t)A.KB * A.ld * es;
+  if (dbl) k_zfwd<double><<<grid, 256, sm, h->stream>>>(A, (const double2*)h->tw3);
+  else k_zfwd<float><<<grid, 256, sm, h->stream>>>(A, (const float2*)h->tw3);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_xpass(chan_s* h, int mode, void* const* in, void* const* out) {
+  const bool dbl = h->prec == CHAN_PREC_FP64;
+  const size_t es = dbl ? sizeof(double2) : sizeof(float2);
+  XArgs A;
+  memset(&A, 0, sizeof(A));
+  const int nin = mode == 0 ? 6 : 3, nout = mode == 0 ? 3 : 6;
+  for (int f = 0; f < nin; ++f) A.in[f] = in[f];
+  for (int f = 0; f < nout; ++f) A.out[f] = out[f];
+  A.nxh = h->nxh; A.L1 = h->L1; A.L3 = h->L3; A.ld = h->L1 + 1;
+  A.scale = 1.0 / ((double)h->L1 * (double)h->L3);
+  A.pl = h->p1;
+  dim3 grid(h->L3 / 2, h->Ny);
+  size_t sm = 2 * 6 * (size_t)A.ld * es;
+  if (dbl) {
+    if (mode == 0) k_xpass<double, 0><<<grid, 256, sm, h->stream>>>(A, (const double2*)h->tw1);
+    else k_xpass<double, 1><<<grid, 256, sm, h->stream>>>(A, (const double2*)h->tw1);
+  } else {
+    if (mode == 0) k_xpass<float, 0><<<grid, 256, sm, h->stream>>>(A, (const float2*)h->tw1);
+    else k_xpass<float, 1><<<grid, 256, sm, h->stream>>>(A, (const float2*)h->tw1);
+  }
+  return cudaGetLastError();
+}

@@ -1,0 +1,124 @@
+// Filter epilogue and plane statistics of the channel substep.
+//   tau_ij = G P(u_i u_j) - P(ubar_i ubar_j), ubar_i = G u_i   (Sec. 3.1, arXiv:1808.06461)
+//   <u_i u_j>(y) by Parseval over the stored modes, U_i, u_tau   (Sec. 3.3)
+#include "chan_internal.cuh"
+
+namespace {
+
+struct FiltArgs {
+  const double2* u[3];
+  const double2* puu[6];
+  const double2* pbb[6];
+  double2* ubar;   // [3][Ny][M]
+  double2* tau;    // [6][Ny][M]
+  const double* G;
+  size_t n;        // Ny * M
+  int M;
+};
+
+__global__ void k_filter_out(FiltArgs A) {
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= A.n) return;
+  const double g = A.G[e % A.M];
+#pragma unroll
+  for (int f = 0; f < 3; ++f) {
+    double2 x = A.u[f][e];
+    A.ubar[(size_t)f * A.n + e] = make_double2(g * x.x, g * x.y);
+  }
+#pragma unroll
+  for (int p = 0; p < 6; ++p) {
+    double2 a = A.puu[p][e], b = A.pbb[p][e];
+    A.tau[(size_t)p * A.n + e] = make_double2(fma(g, a.x, -b.x), fma(g, a.y, -b.y));
+  }
+}
+
+struct StatArgs {
+  const double2* u[3];
+  const double2* ub[3];
+  const double2* tau;   // [6][Ny][M] or null
+  const double *U1, *U3, *d0, *dN, *wq;
+  double* out;          // [CHAN_NSTAT][Ny] + utau, ubulk
+  double nu;
+  int Ny, M, nxh, with_filter;
+};
+
+// Block j < Ny reduces plane j in a fixed order (thread-strided partial sums,
+// then a fixed shared-memory tree), so results do not depend on scheduling.
+__global__ void __launch_bounds__(256) k_stats(StatArgs A) {
+  __shared__ double red[12][256];
+  const int j = blockIdx.x;
+  const int Ny = A.Ny;
+  if (j == Ny) {
+    if (threadIdx.x == 0) {
+      double a = 0.0, b = 0.0, q = 0.0;
+      for (int i = 0; i < Ny; ++i) { a += A.d0[i] * A.U1[i]; b += A.dN[i] * A.U1[i]; q += A.wq[i] * A.U1[i]; }
+      A.out[CHAN_NSTAT * Ny] = sqrt(A.nu * 0.5 * (fabs(a) + fabs(b)));
+      A.out[CHAN_NSTAT * Ny + 1] = 0.5 * q;
+    }
+    return;
+  }
+  const int pi[6] = {0, 1, 2, 0, 0, 1}, pj[6] = {0, 1, 2, 1, 2, 2};
+  double acc[12];
+#pragma unroll
+  for (int p = 0; p < 12; ++p) acc[p] = 0.0;
+  const size_t base = (size_t)j * A.M;
+  for (int m = threadIdx.x; m < A.M; m += blockDim.x) {
+    const double w = (m % A.nxh) == 0 ? 1.0 : 2.0;
+    double2 q[3];
+#pragma unroll
+    for (int f = 0; f < 3; ++f) q[f] = A.u[f][base + m];
+#pragma unroll
+    for (int p = 0; p < 6; ++p) acc[p] += w * (q[pi[p]].x * q[pj[p]].x + q[pi[p]].y * q[pj[p]].y);
+    if (A.with_filter) {
+#pragma unroll
+      for (int f = 0; f < 3; ++f) q[f] = A.ub[f][base + m];
+#pragma unroll
+      for (int p = 0; p < 6; ++p) acc[6 + p] += w * (q[pi[p]].x * q[pj[p]].x + q[pi[p]].y * q[pj[p]].y);
+    }
+  }
+#pragma unroll
+  for (int p = 0; p < 12; ++p) red[p][threadIdx.x] = acc[p];
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s)
+      for (int p = 0; p < 12; ++p) red[p][threadIdx.x] += red[p][threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    A.out[0 * Ny + j] = A.U1[j];
+    A.out[1 * Ny + j] = A.U3[j];
+    for (int p = 0; p < 6; ++p) {
+      A.out[(2 + p) * Ny + j] = red[p][0];
+      A.out[(8 + p) * Ny + j] = A.with_filter ? red[6 + p][0] : 0.0;
+      A.out[(14 + p) * Ny + j] = A.with_filter ? A.tau[(size_t)p * Ny * A.M + base].x : 0.0;
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_filter_out(chan_s* h, const double2* const* u, const double2* const* puu, const double2* const* pbb,
+                              double2* ubar, double2* tau) {
+  FiltArgs A;
+  for (int f = 0; f < 3; ++f) A.u[f] = u[f];
+  for (int p = 0; p < 6; ++p) { A.puu[p] = puu[p]; A.pbb[p] = pbb[p]; }
+  A.ubar = ubar; A.tau = tau; A.G = h->G;
+  A.n = (size_t)h->Ny * h->M;
+  A.M = h->M;
+  k_filter_out<<<(unsigned)((A.n + 255) / 256), 256, 0, h->stream>>>(A);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stats(chan_s* h, const double2* u1, const double2* u3, const double2* ubar, const double2* tau,
+                         int with_filter) {
+  StatArgs A;
+  A.u[0] = u1; A.u[1] = h->v; A.u[2] = u3;
+  const size_t n = (size_t)h->Ny * h->M;
+  for (int f = 0; f < 3; ++f) A.ub[f] = ubar ? ubar + f * n : nullptr;
+  A.tau = tau;
+  A.U1 = h->U1; A.U3 = h->U3; A.d0 = h->tab_d0; A.dN = h->tab_dN; A.wq = h->tab_wq;
+  A.out = h->stat; A.nu = h->nu;
+  A.Ny = h->Ny; A.M = h->M; A.nxh = h->nxh; A.with_filter = with_filter;
+  k_stats<<<h->Ny + 1, 256, 0, h->stream>>>(A);
+  return cudaGetLastError();
+}

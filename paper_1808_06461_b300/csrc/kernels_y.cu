@@ -1,0 +1,714 @@
+// Wall-normal (y) kernels of the channel substep: one thread per Fourier
+// mode sweeps its y-pencil through (3,3)-banded compact operators.  The
+// Fourier layout [Ny][M] puts consecutive modes at consecutive addresses,
+// so each sweep step is a coalesced row load/store across a warp.
+//
+// Appendix A of arXiv:1808.06461: u_1, u_3 from continuity and omega_2;
+// N_chi, N_omega2 of Eq. (hghv); the semi-implicit RK3 steps (chi1), (psi);
+// the Poisson problem (chi2) with the influence-matrix wall correction; the
+// mean profiles with a constant mass flux (Sec. 2.1).
+#include "chan_internal.cuh"
+
+namespace {
+
+// Spalart-Moser-Rogers low-storage RK3: (gamma, zeta, alpha, beta) per substep.
+__constant__ double c_rk3[3][4] = {{8.0 / 15.0, 0.0, 29.0 / 96.0, 37.0 / 160.0},
+                                   {5.0 / 12.0, -17.0 / 60.0, -3.0 / 40.0, 5.0 / 24.0},
+                                   {3.0 / 4.0, -5.0 / 12.0, 1.0 / 6.0, 1.0 / 6.0}};
+const double h_rk3[3][4] = {{8.0 / 15.0, 0.0, 29.0 / 96.0, 37.0 / 160.0},
+                            {5.0 / 12.0, -17.0 / 60.0, -3.0 / 40.0, 5.0 / 24.0},
+                            {3.0 / 4.0, -5.0 / 12.0, 1.0 / 6.0, 1.0 / 6.0}};
+
+__device__ __forceinline__ double2 z2() { return make_double2(0.0, 0.0); }
+__device__ __forceinline__ double2 axpy(double a, double2 x, double2 y) {  // y + a x
+  return make_double2(fma(a, x.x, y.x), fma(a, x.y, y.y));
+}
+__device__ __forceinline__ double2 scl(double a, double2 x) { return make_double2(a * x.x, a * x.y); }
+__device__ __forceinline__ double2 sub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 add(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 itimes(double2 a) { return make_double2(-a.y, a.x); }  // i a
+
+template <int N>
+__device__ __forceinline__ void push(double2 (&w)[N], double2 x) {
+#pragma unroll
+  for (int d = 0; d < N - 1; ++d) w[d] = w[d + 1];
+  w[N - 1] = x;
+}
+
+// Banded row times window: sum_d c[d] w[d] (columns i-3..i+3).
+__device__ __forceinline__ double2 band7(const double* c, const double2 (&w)[7]) {
+  double2 r = z2();
+#pragma unroll
+  for (int d = 0; d < 7; ++d) r = axpy(c[d], w[d], r);
+  return r;
+}
+
+// Forward substitution of row i: z_i = r - sum_d l[d] z_{i-3+d}; hist = (z_{i-3}, z_{i-2}, z_{i-1}).
+__device__ __forceinline__ double2 fwd(double2 r, double l0, double l1, double l2, double2 (&hist)[3]) {
+  r = axpy(-l0, hist[0], r);
+  r = axpy(-l1, hist[1], r);
+  r = axpy(-l2, hist[2], r);
+  push(hist, r);
+  return r;
+}
+
+// Back substitution of row i: x_i = (z_i - sum_d u[d] x_{i+1+d}) dinv; nxt = (x_{i+1}, x_{i+2}, x_{i+3}).
+__device__ __forceinline__ double2 bwd(double2 z, double u0, double u1, double u2, double dinv, double2 (&nxt)[3]) {
+  z = axpy(-u0, nxt[0], z);
+  z = axpy(-u1, nxt[1], z);
+  z = axpy(-u2, nxt[2], z);
+  double2 x = scl(dinv, z);
+  nxt[2] = nxt[1];
+  nxt[1] = nxt[0];
+  nxt[0] = x;
+  return x;
+}
+
+__device__ __forceinline__ void load_tab(double* dst, const double* src, int n) {
+  for (int k = threadIdx.x; k < n; k += blockDim.x) dst[k] = src[k];
+}
+
+struct ModeInfo {
+  int jz, kx, c;
+  bool nyq;
+  double k1, k3, k2;
+};
+
+__device__ __forceinline__ ModeInfo mode_info(const Geo& g, int m) {
+  ModeInfo mi;
+  mi.jz = m / g.nxh;
+  mi.kx = m - mi.jz * g.nxh;
+  const int hz = g.Nz / 2;
+  mi.nyq = (mi.jz == hz);
+  int kza = mi.jz < hz ? mi.jz : g.Nz - mi.jz;
+  mi.c = mi.nyq ? 0 : kza * g.nxh + mi.kx;
+  mi.k1 = g.k1[mi.kx];
+  mi.k3 = g.k3[mi.jz];
+  mi.k2 = mi.k1 * mi.k1 + mi.k3 * mi.k3;
+  return mi;
+}
+
+// ---------------------------------------------------------------------------
+// a1: u_1, u_3, omega_1, omega_3 from (v, omega_2, dv/dy); two D1 sweeps.
+// dv/dy is part of the state (it is D1 v of the last Poisson solve).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_pre(Geo g, YTabs t, const double2* __restrict__ v,
+                                             const double2* __restrict__ om, const double2* __restrict__ dv,
+                                             const double* __restrict__ U1, const double* __restrict__ U3,
+                                             double2* u1o, double2* u3o, double2* om1o, double2* om3o) {
+  extern __shared__ double sm[];
+  const int Ny = g.Ny;
+  double* sB1 = sm;
+  double* sLU = sm + 7 * Ny;
+  load_tab(sB1, t.B1, 7 * Ny);
+  load_tab(sLU, t.lu1, 7 * Ny);
+  __syncthreads();
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= g.M) return;
+  const size_t M = g.M;
+  ModeInfo mi = mode_info(g, m);
+  if (mi.nyq) {
+    for (int i = 0; i < Ny; ++i) {
+      size_t o = (size_t)i * M + m;
+      u1o[o] = z2(); u3o[o] = z2(); om1o[o] = z2(); om3o[o] = z2();
+    }
+    return;
+  }
+  const bool mean = (m == 0);
+  double2 wx[7], ww[7], hx[3], hw[3];
+#pragma unroll
+  for (int d = 0; d < 7; ++d) { wx[d] = z2(); ww[d] = z2(); }
+#pragma unroll
+  for (int d = 0; d < 3; ++d) { hx[d] = z2(); hw[d] = z2(); }
+  // forward sweep of D1 = A1^-1 B1 on x = dv/dy (U1 for the mean) and w = omega_2 (U3)
+  for (int j = 0; j < Ny + 3; ++j) {
+    double2 nx = z2(), nw = z2();
+    if (j < Ny) {
+      if (mean) { nx.x = U1[j]; nw.x = U3[j]; }
+      else { nx = dv[(size_t)j * M + m]; nw = om[(size_t)j * M + m]; }
+    }
+    push(wx, nx);
+    push(ww, nw);
+    const int i = j - 3;
+    if (i < 0) continue;
+    const double* b = sB1 + 7 * i;
+    const double* l = sLU + 7 * i;
+    double2 zx = fwd(band7(b, wx), l[0], l[1], l[2], hx);
+    double2 zw = fwd(band7(b, ww), l[0], l[1], l[2], hw);
+    u1o[(size_t)i * M + m] = zx;   // parked here until the backward sweep
+    u3o[(size_t)i * M + m] = zw;
+  }
+  double2 px[3] = {z2(), z2(), z2()}, pw[3] = {z2(), z2(), z2()};
+  const double q1 = mean ? 0.0 : mi.k1 / mi.k2, q3 = mean ? 0.0 : mi.k3 / mi.k2;
+  for (int i = Ny - 1; i >= 0; --i) {
+    const size_t o = (size_t)i * M + m;
+    const double* lu = sLU + 7 * i;
+    double2 P = bwd(u1o[o], lu[3], lu[4], lu[5], lu[6], px);   // d2v/dy2 ... D1 of dv/dy
+    double2 Q = bwd(u3o[o], lu[3], lu[4], lu[5], lu[6], pw);   // D1 omega_2
+    double2 u1, u3, du1, du3;
+    double2 vi = z2();
+    if (mean) {
+      u1 = make_double2(U1[i], 0.0);
+      u3 = make_double2(U3[i], 0.0);
+      du1 = P;
+      du3 = Q;
+    } else {
+      double2 dvi = dv[o], omi = om[o];
+      vi = v[o];
+      u1 = itimes(make_double2(q1 * dvi.x - q3 * omi.x, q1 * dvi.y - q3 * omi.y));
+      u3 = itimes(make_double2(q3 * dvi.x + q1 * omi.x, q3 * dvi.y + q1 * omi.y));
+      du1 = itimes(make_double2(q1 * P.x - q3 * Q.x, q1 * P.y - q3 * Q.y));
+      du3 = itimes(make_double2(q3 * P.x + q1 * Q.x, q3 * P.y + q1 * Q.y));
+    }
+    // omega_1 = du3/dy - i k3 v, omega_3 = i k1 v - du1/dy
+    u1o[o] = u1;
+    u3o[o] = u3;
+    om1o[o] = make_double2(du3.x + mi.k3 * vi.y, du3.y - mi.k3 * vi.x);
+    om3o[o] = make_double2(-mi.k1 * vi.y - du1.x, mi.k1 * vi.x - du1.y);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// a5: N_omega2 = i k3 H1 - i k1 H3, N_chi = -D1(i k1 H1 + i k3 H3) - k^2 H2.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_nonlin(Geo g, YTabs t, const double2* __restrict__ H1,
+                                                const double2* __restrict__ H2, const double2* __restrict__ H3,
+                                                double2* Nchi, double2* Nom, double2* scr) {
+  extern __shared__ double sm[];
+  const int Ny = g.Ny;
+  double* sB1 = sm;
+  double* sLU = sm + 7 * Ny;
+  load_tab(sB1, t.B1, 7 * Ny);
+  load_tab(sLU, t.lu1, 7 * Ny);
+  __syncthreads();
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= g.M) return;
+  const size_t M = g.M;
+  ModeInfo mi = mode_info(g, m);
+  if (mi.nyq || m == 0) {
+    for (int i = 0; i < Ny; ++i) { Nchi[(size_t)i * M + m] = z2(); Nom[(size_t)i * M + m] = z2(); }
+    return;
+  }
+  double2 w[7], hz[3];
+#pragma unroll
+  for (int d = 0; d < 7; ++d) w[d] = z2();
+#pragma unroll
+  for (int d = 0; d < 3; ++d) hz[d] = z2();
+  for (int j = 0; j < Ny + 3; ++j) {
+    double2 f = z2();
+    if (j < Ny) {
+      const size_t o = (size_t)j * M + m;
+      double2 a = H1[o], b = H3[o];
+      f = itimes(make_double2(mi.k1 * a.x + mi.k3 * b.x, mi.k1 * a.y + mi.k3 * b.y));
+    }
+    push(w, f);
+    const int i = j - 3;
+    if (i < 0) continue;
+    const double* l = sLU + 7 * i;
+    scr[(size_t)i * M + m] = fwd(band7(sB1 + 7 * i, w), l[0], l[1], l[2], hz);
+  }
+  double2 nx[3] = {z2(), z2(), z2()};
+  for (int i = Ny - 1; i >= 0; --i) {
+    const size_t o = (size_t)i * M + m;
+    const double* lu = sLU + 7 * i;
+    double2 d = bwd(scr[o], lu[3], lu[4], lu[5], lu[6], nx);
+    double2 h2 = H2[o], h1 = H1[o], h3 = H3[o];
+    Nchi[o] = make_double2(-d.x - mi.k2 * h2.x, -d.y - mi.k2 * h2.y);
+    Nom[o] = itimes(make_double2(mi.k3 * h1.x - mi.k1 * h3.x, mi.k3 * h1.y - mi.k1 * h3.y));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// a6 + first half of a7: implicit RK3 Helmholtz steps of omega_2 and chi
+// (Eqs. (psi), (chi1)) multiplied through by A:
+//   [(1 + b dt nu k^2) A - b dt nu B] X+ = A[(1 - a dt nu k^2) X + dt(g N + z Nprev)] + a dt nu B X,
+// wall rows X+ = 0 (chi's are the particular solution).  Nprev <- N.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_helm(Geo g, YTabs t, const double* __restrict__ helm,
+                                              double2* om, double2* chi, const double2* __restrict__ Nchi,
+                                              const double2* __restrict__ Nom, double2* Nchi_p, double2* Nom_p,
+                                              double2* scr, int s) {
+  extern __shared__ double sm[];
+  const int Ny = g.Ny;
+  double* sA = sm;
+  double* sB = sm + 7 * Ny;
+  load_tab(sA, t.A2, 7 * Ny);
+  load_tab(sB, t.B2, 7 * Ny);
+  __syncthreads();
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= g.M) return;
+  const size_t M = g.M;
+  const size_t C = g.C;
+  ModeInfo mi = mode_info(g, m);
+  if (mi.nyq) {
+    for (int i = 0; i < Ny; ++i) {
+      size_t o = (size_t)i * M + m;
+      om[o] = z2(); chi[o] = z2(); Nchi_p[o] = z2(); Nom_p[o] = z2();
+    }
+    return;
+  }
+  const double gm = c_rk3[s][0], zt = c_rk3[s][1], al = c_rk3[s][2];
+  const double dt = g.dt, nu = g.nu;
+  const double c1 = 1.0 - al * dt * nu * mi.k2, cg = dt * gm, cz = dt * zt, ca = al * dt * nu;
+  const double* H = helm + (size_t)s * Ny * 11 * C + mi.c;
+  double2 wa[7], wx[7], wb[7], wy[7], ho[3], hc[3];
+#pragma unroll
+  for (int d = 0; d < 7; ++d) { wa[d] = z2(); wx[d] = z2(); wb[d] = z2(); wy[d] = z2(); }
+#pragma unroll
+  for (int d = 0; d < 3; ++d) { ho[d] = z2(); hc[d] = z2(); }
+  double2* scr2 = scr + (size_t)Ny * M;
+  for (int j = 0; j < Ny + 3; ++j) {
+    double2 ao = z2(), xo = z2(), ac = z2(), xc = z2();
+    if (j < Ny) {
+      const size_t o = (size_t)j * M + m;
+      xo = om[o];
+      xc = chi[o];
+      double2 no = Nom[o], nop = Nom_p[o], nc = Nchi[o], ncp = Nchi_p[o];
+      ao = axpy(cz, nop, axpy(cg, no, scl(c1, xo)));
+      ac = axpy(cz, ncp, axpy(cg, nc, scl(c1, xc)));
+      Nom_p[o] = no;
+      Nchi_p[o] = nc;
+    }
+    push(wa, ao); push(wx, xo); push(wb, ac); push(wy, xc);
+    const int i = j - 3;
+    if (i < 0) continue;
+    double2 ro = z2(), rc = z2();
+    if (i > 0 && i < Ny - 1) {
+      ro = axpy(ca, band7(sB + 7 * i, wx), band7(sA + 7 * i, wa));
+      rc = axpy(ca, band7(sB + 7 * i, wy), band7(sA + 7 * i, wb));
+    }
+    const double* Hi = H + (size_t)i * 11 * C;
+    const double l0 = Hi[0], l1 = Hi[C], l2 = Hi[2 * C];
+    scr[(size_t)i * M + m] = fwd(ro, l0, l1, l2, ho);
+    scr2[(size_t)i * M + m] = fwd(rc, l0, l1, l2, hc);
+  }
+  double2 no3[3] = {z2(), z2(), z2()}, nc3[3] = {z2(), z2(), z2()};
+  for (int i = Ny - 1; i >= 0; --i) {
+    const size_t o = (size_t)i * M + m;
+    const double* Hi = H + (size_t)i * 11 * C;
+    const double u0 = Hi[3 * C], u1 = Hi[4 * C], u2 = Hi[5 * C], dinv = Hi[6 * C];
+    om[o] = bwd(scr[o], u0, u1, u2, dinv, no3);
+    chi[o] = bwd(scr2[o], u0, u1, u2, dinv, nc3);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Second half of a7: (B - k^2 A) v_p = A chi_p, v_p(+-1) = 0 (Eq. (chi2));
+// v = v_p + c_a v_a + c_b v_b and chi likewise, with (c_a, c_b) making
+// dv/dy(+-1) = 0 through the precomputed influence matrix; then dv/dy = D1 v.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_poisson(Geo g, YTabs t, const double* __restrict__ helm,
+                                                 const double* __restrict__ pois, const double* __restrict__ infl,
+                                                 double2* v, double2* chi, double2* dv, double2* scr, int s) {
+  extern __shared__ double sm[];
+  const int Ny = g.Ny;
+  double* sA = sm;
+  double* sB1 = sm + 7 * Ny;
+  double* sLU = sm + 14 * Ny;
+  load_tab(sA, t.A2, 7 * Ny);
+  load_tab(sB1, t.B1, 7 * Ny);
+  load_tab(sLU, t.lu1, 7 * Ny);
+  __syncthreads();
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= g.M) return;
+  const size_t M = g.M;
+  const size_t C = g.C;
+  ModeInfo mi = mode_info(g, m);
+  if (mi.nyq) {
+    for (int i = 0; i < Ny; ++i) { size_t o = (size_t)i * M + m; v[o] = z2(); dv[o] = z2(); }
+    return;
+  }
+  const double* P = pois + mi.c;
+  const double* H = helm + (size_t)s * Ny * 11 * C + mi.c;
+  double2 w[7], hz[3];
+#pragma unroll
+  for (int d = 0; d < 7; ++d) w[d] = z2();
+#pragma unroll
+  for (int d = 0; d < 3; ++d) hz[d] = z2();
+  for (int j = 0; j < Ny + 3; ++j) {
+    push(w, j < Ny ? chi[(size_t)j * M + m] : z2());
+    const int i = j - 3;
+    if (i < 0) continue;
+    double2 r = (i > 0 && i < Ny - 1) ? band7(sA + 7 * i, w) : z2();
+    const double* Pi = P + (size_t)i * 7 * C;
+    scr[(size_t)i * M + m] = fwd(r, Pi[0], Pi[C], Pi[2 * C], hz);
+  }
+  double2 nx[3] = {z2(), z2(), z2()};
+  double2 s0 = z2(), sN = z2();
+  for (int i = Ny - 1; i >= 0; --i) {
+    const size_t o = (size_t)i * M + m;
+    const double* Pi = P + (size_t)i * 7 * C;
+    double2 vp = bwd(scr[o], Pi[3 * C], Pi[4 * C], Pi[5 * C], Pi[6 * C], nx);
+    v[o] = vp;
+    s0 = axpy(t.d0[i], vp, s0);
+    sN = axpy(t.dN[i], vp, sN);
+  }
+  const double* Gi = infl + (size_t)s * 4 * C + mi.c;
+  const double g11 = Gi[0], g12 = Gi[C], g21 = Gi[2 * C], g22 = Gi[3 * C];  // inverse influence matrix
+  const double2 cA = make_double2(-(g11 * s0.x + g12 * sN.x), -(g11 * s0.y + g12 * sN.y));
+  const double2 cB = make_double2(-(g21 * s0.x + g22 * sN.x), -(g21 * s0.y + g22 * sN.y));
+#pragma unroll
+  for (int d = 0; d < 7; ++d) w[d] = z2();
+#pragma unroll
+  for (int d = 0; d < 3; ++d) hz[d] = z2();
+  for (int j = 0; j < Ny + 3; ++j) {
+    double2 vj = z2();
+    if (j < Ny) {
+      const size_t o = (size_t)j * M + m;
+      const double* Hj = H + (size_t)j * 11 * C;
+      const double xa = Hj[7 * C], xb = Hj[8 * C], va = Hj[9 * C], vb = Hj[10 * C];
+      vj = axpy(vb, cB, axpy(va, cA, v[o]));
+      v[o] = vj;
+      chi[o] = axpy(xb, cB, axpy(xa, cA, chi[o]));
+    }
+    push(w, vj);
+    const int i = j - 3;
+    if (i < 0) continue;
+    const double* l = sLU + 7 * i;
+    scr[(size_t)i * M + m] = fwd(band7(sB1 + 7 * i, w), l[0], l[1], l[2], hz);
+  }
+  for (int d = 0; d < 3; ++d) nx[d] = z2();
+  for (int i = Ny - 1; i >= 0; --i) {
+    const size_t o = (size_t)i * M + m;
+    const double* lu = sLU + 7 * i;
+    dv[o] = bwd(scr[o], lu[3], lu[4], lu[5], lu[6], nx);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// a8: mean profiles.  One thread: the (0,0) Helmholtz factors (k = 0) of
+// substep s serve (A - b dt nu B) U+ = A[U + dt(g <H> + z <H>prev)] + a dt nu B U.
+// U_1 gets c U_h with U_h = (A - b dt nu B)^-1 A 1 so the trapezoid flux
+// stays Q0; f = c / ((a + b) dt).
+// ---------------------------------------------------------------------------
+__global__ void k_mean(Geo g, YTabs t, const double* __restrict__ helm, const double2* __restrict__ H1,
+                       const double2* __restrict__ H3, double* U1, double* U3, double* H1p, double* H3p,
+                       double* scal, int s) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  extern __shared__ double sm[];
+  const int Ny = g.Ny;
+  const size_t M = g.M, C = g.C;
+  double* u1s = sm;
+  double* u3s = sm + Ny;
+  double* uh = sm + 2 * Ny;
+  const double gm = c_rk3[s][0], zt = c_rk3[s][1], al = c_rk3[s][2], be = c_rk3[s][3];
+  const double dt = g.dt, nu = g.nu;
+  const double* H = helm + (size_t)s * Ny * 11 * C;  // class 0: k = 0
+  for (int f = 0; f < 3; ++f) {
+    double* out = f == 0 ? u1s : (f == 1 ? u3s : uh);
+    double hist[3] = {0, 0, 0};
+    for (int i = 0; i < Ny; ++i) {
+      double r = 0.0;
+      if (i > 0 && i < Ny - 1) {
+        for (int d = 0; d < 7; ++d) {
+          int j = i - 3 + d;
+          if (j < 0 || j >= Ny) continue;
+          double a, u;
+          if (f == 2) { a = 1.0; u = 0.0; }
+          else {
+            const double* U = f == 0 ? U1 : U3;
+            const double2* Hf = f == 0 ? H1 : H3;
+            const double* Hp = f == 0 ? H1p : H3p;
+            u = U[j];
+            a = u + dt * (gm * Hf[(size_t)j * M].x + zt * Hp[j]);
+          }
+          r += t.A2[7 * i + d] * a + al * dt * nu * t.B2[7 * i + d] * u;
+        }
+      }
+      const double* Hi = H + (size_t)i * 11 * C;
+      r -= Hi[0] * hist[0] + Hi[C] * hist[1] + Hi[2 * C] * hist[2];
+      hist[0] = hist[1]; hist[1] = hist[2]; hist[2] = r;
+      out[i] = r;
+    }
+    double nx[3] = {0, 0, 0};
+    for (int i = Ny - 1; i >= 0; --i) {
+      const double* Hi = H + (size_t)i * 11 * C;
+      double x = (out[i] - Hi[3 * C] * nx[0] - Hi[4 * C] * nx[1] - Hi[5 * C] * nx[2]) * Hi[6 * C];
+      nx[2] = nx[1]; nx[1] = nx[0]; nx[0] = x;
+      out[i] = x;
+    }
+  }
+  double q1 = 0.0, qh = 0.0;
+  for (int i = 0; i < Ny; ++i) { q1 += t.wq[i] * u1s[i]; qh += t.wq[i] * uh[i]; }
+  const double c = (scal[1] - q1) / qh;
+  for (int i = 0; i < Ny; ++i) {
+    U1[i] = u1s[i] + c * uh[i];
+    U3[i] = u3s[i];
+    H1p[i] = H1[(size_t)i * M].x;
+    H3p[i] = H3[(size_t)i * M].x;
+  }
+  scal[0] = c / ((al + be) * dt);
+}
+
+// ---------------------------------------------------------------------------
+// State derivation after a set_state: chi = A2^-1 (B2 - k^2 A2) v over all
+// rows, and dv/dy = D1 v.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_derive(Geo g, YTabs t, const double2* __restrict__ v, double2* chi,
+                                                double2* dv, double2* scr) {
+  extern __shared__ double sm[];
+  const int Ny = g.Ny;
+  double* sA = sm;
+  double* sB = sm + 7 * Ny;
+  double* sB1 = sm + 14 * Ny;
+  double* sLU1 = sm + 21 * Ny;
+  double* sLU2 = sm + 28 * Ny;
+  load_tab(sA, t.A2, 7 * Ny);
+  load_tab(sB, t.B2, 7 * Ny);
+  load_tab(sB1, t.B1, 7 * Ny);
+  load_tab(sLU1, t.lu1, 7 * Ny);
+  load_tab(sLU2, t.lu2f, 7 * Ny);
+  __syncthreads();
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= g.M) return;
+  const size_t M = g.M;
+  ModeInfo mi = mode_info(g, m);
+  double2 w[7], h2[3], h1[3];
+#pragma unroll
+  for (int d = 0; d < 7; ++d) w[d] = z2();
+#pragma unroll
+  for (int d = 0; d < 3; ++d) { h2[d] = z2(); h1[d] = z2(); }
+  double2* scr2 = scr + (size_t)Ny * M;
+  const bool zero = mi.nyq || m == 0;
+  for (int j = 0; j < Ny + 3; ++j) {
+    push(w, (j < Ny && !zero) ? v[(size_t)j * M + m] : z2());
+    const int i = j - 3;
+    if (i < 0) continue;
+    const double* a = sA + 7 * i;
+    const double* b = sB + 7 * i;
+    double2 r = z2();
+#pragma unroll
+    for (int d = 0; d < 7; ++d) r = axpy(b[d] - mi.k2 * a[d], w[d], r);
+    const double* l2 = sLU2 + 7 * i;
+    const double* l1 = sLU1 + 7 * i;
+    scr[(size_t)i * M + m] = fwd(r, l2[0], l2[1], l2[2], h2);
+    scr2[(size_t)i * M + m] = fwd(band7(sB1 + 7 * i, w), l1[0], l1[1], l1[2], h1);
+  }
+  double2 n2[3] = {z2(), z2(), z2()}, n1[3] = {z2(), z2(), z2()};
+  for (int i = Ny - 1; i >= 0; --i) {
+    const size_t o = (size_t)i * M + m;
+    const double* l2 = sLU2 + 7 * i;
+    const double* l1 = sLU1 + 7 * i;
+    chi[o] = bwd(scr[o], l2[3], l2[4], l2[5], l2[6], n2);
+    dv[o] = bwd(scr2[o], l1[3], l1[4], l1[5], l1[6], n1);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Set-up: LU factors (no pivoting) of the Poisson operator B - k^2 A per class
+// and of the RK3 Helmholtz operator per (class, substep), homogeneous
+// solutions chi_a, chi_b, v_a, v_b and the inverse influence matrix.
+// ---------------------------------------------------------------------------
+
+// One row of a (3,3)-banded Doolittle LU.  row[d]: column i-3+d.  Up[r][e] =
+// u(k, k+e) of the previous rows k = i-3+r.  Returns l (cols i-3..i-1) and
+// u (cols i..i+3).
+__device__ void lu_row(int i, const double row[7], const double Up[3][4], double l[3], double u[4]) {
+  for (int d = 0; d < 3; ++d) {
+    l[d] = 0.0;
+    const int j = i - 3 + d;
+    if (j < 0) continue;
+    double s = row[d];
+    for (int k = i - 3; k < j; ++k) {
+      if (k < 0) continue;
+      const int e = j - k;  // <= 3
+      s -= l[k - (i - 3)] * Up[k - (i - 3)][e];
+    }
+    l[d] = s / Up[d][0];
+  }
+  for (int e = 0; e < 4; ++e) {
+    const int j = i + e;
+    double s = row[3 + e];
+    for (int k = i - 3; k < i; ++k) {
+      if (k < 0) continue;
+      const int ee = j - k;
+      if (ee > 3) continue;
+      s -= l[k - (i - 3)] * Up[k - (i - 3)][ee];
+    }
+    u[e] = s;
+  }
+}
+
+// Factor rows of op(i, d) and store l, u, 1/u_ii at tab[(i*stride + q) * C].
+template <typename RowFn>
+__device__ void factor(int Ny, RowFn rowfn, double* tab, size_t stride, size_t C) {
+  double Up[3][4] = {{0}};
+  for (int i = 0; i < Ny; ++i) {
+    double row[7], l[3], u[4];
+    rowfn(i, row);
+    lu_row(i, row, Up, l, u);
+    double* o = tab + (size_t)i * stride * C;
+    o[0] = l[0]; o[C] = l[1]; o[2 * C] = l[2];
+    o[3 * C] = u[1]; o[4 * C] = u[2]; o[5 * C] = u[3];
+    o[6 * C] = 1.0 / u[0];
+    for (int e = 0; e < 4; ++e) { Up[0][e] = Up[1][e]; Up[1][e] = Up[2][e]; Up[2][e] = u[e]; }
+  }
+}
+
+__global__ void k_setup_pois(Geo g, YTabs t, double* pois) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.C) return;
+  const int kx = c % g.nxh, kza = c / g.nxh;
+  const double k2 = g.k1[kx] * g.k1[kx] + g.k3[kza] * g.k3[kza];
+  const int Ny = g.Ny;
+  factor(Ny, [&](int i, double* row) {
+    for (int d = 0; d < 7; ++d) row[d] = (i == 0 || i == Ny - 1) ? (d == 3 ? 1.0 : 0.0)
+                                                                 : t.B2[7 * i + d] - k2 * t.A2[7 * i + d];
+  }, pois + c, 7, g.C);
+}
+
+__global__ void k_setup_helm(Geo g, YTabs t, const double* __restrict__ pois, double* helm, double* infl) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= 3 * g.C) return;
+  const int s = idx / g.C, c = idx - s * g.C;
+  const int kx = c % g.nxh, kza = c / g.nxh;
+  const double k2 = g.k1[kx] * g.k1[kx] + g.k3[kza] * g.k3[kza];
+  const int Ny = g.Ny;
+  const size_t C = g.C;
+  const double hb = c_rk3[s][3] * g.dt * g.nu;
+  double* H = helm + (size_t)s * Ny * 11 * C + c;
+  factor(Ny, [&](int i, double* row) {
+    for (int d = 0; d < 7; ++d) row[d] = (i == 0 || i == Ny - 1) ? (d == 3 ? 1.0 : 0.0)
+                                                                 : (1.0 + hb * k2) * t.A2[7 * i + d] - hb * t.B2[7 * i + d];
+  }, H, 11, C);
+  // homogeneous chi_a (1 at y=-1), chi_b (1 at y=+1): forward sweeps park z in slots 9, 10
+  for (int q = 0; q < 2; ++q) {
+    double h[3] = {0, 0, 0};
+    for (int i = 0; i < Ny; ++i) {
+      const double* Hi = H + (size_t)i * 11 * C;
+      double r = (q == 0 ? (i == 0) : (i == Ny - 1)) ? 1.0 : 0.0;
+      r -= Hi[0] * h[0] + Hi[C] * h[1] + Hi[2 * C] * h[2];
+      h[0] = h[1]; h[1] = h[2]; h[2] = r;
+      H[((size_t)i * 11 + 9 + q) * C] = r;
+    }
+    double nx[3] = {0, 0, 0};
+    for (int i = Ny - 1; i >= 0; --i) {
+      const double* Hi = H + (size_t)i * 11 * C;
+      double x = (Hi[(9 + q) * C] - Hi[3 * C] * nx[0] - Hi[4 * C] * nx[1] - Hi[5 * C] * nx[2]) * Hi[6 * C];
+      nx[2] = nx[1]; nx[1] = nx[0]; nx[0] = x;
+      H[((size_t)i * 11 + 7 + q) * C] = x;
+    }
+  }
+  // v_a, v_b: (B - k^2 A) v = A chi, v(+-1) = 0
+  const double* P = pois + c;
+  double gm[2][2];
+  for (int q = 0; q < 2; ++q) {
+    double w[7] = {0, 0, 0, 0, 0, 0, 0}, h[3] = {0, 0, 0};
+    for (int j = 0; j < Ny + 3; ++j) {
+      for (int d = 0; d < 6; ++d) w[d] = w[d + 1];
+      w[6] = j < Ny ? H[((size_t)j * 11 + 7 + q) * C] : 0.0;
+      const int i = j - 3;
+      if (i < 0) continue;
+      double r = 0.0;
+      if (i > 0 && i < Ny - 1)
+        for (int d = 0; d < 7; ++d) r += t.A2[7 * i + d] * w[d];
+      const double* Pi = P + (size_t)i * 7 * C;
+      r -= Pi[0] * h[0] + Pi[C] * h[1] + Pi[2 * C] * h[2];
+      h[0] = h[1]; h[1] = h[2]; h[2] = r;
+      H[((size_t)i * 11 + 9 + q) * C] = r;
+    }
+    double nx[3] = {0, 0, 0}, s0 = 0.0, sN = 0.0;
+    for (int i = Ny - 1; i >= 0; --i) {
+      const double* Pi = P + (size_t)i * 7 * C;
+      double x = (H[((size_t)i * 11 + 9 + q) * C] - Pi[3 * C] * nx[0] - Pi[4 * C] * nx[1] - Pi[5 * C] * nx[2]) * Pi[6 * C];
+      nx[2] = nx[1]; nx[1] = nx[0]; nx[0] = x;
+      H[((size_t)i * 11 + 9 + q) * C] = x;
+      s0 += t.d0[i] * x;
+      sN += t.dN[i] * x;
+    }
+    gm[0][q] = s0;   // row: wall (0: y=-1, 1: y=+1); column: solution a/b
+    gm[1][q] = sN;
+  }
+  const double det = gm[0][0] * gm[1][1] - gm[0][1] * gm[1][0];
+  double* G = infl + (size_t)s * 4 * C + c;
+  G[0] = gm[1][1] / det;
+  G[C] = -gm[0][1] / det;
+  G[2 * C] = -gm[1][0] / det;
+  G[3 * C] = gm[0][0] / det;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+static Geo geo(const chan_s* h) {
+  Geo g;
+  g.Nx = h->Nx; g.Ny = h->Ny; g.Nz = h->Nz; g.nxh = h->nxh; g.M = h->M; g.C = h->C;
+  g.L1 = h->L1; g.L3 = h->L3; g.dt = h->dt; g.nu = h->nu; g.k1 = h->k1; g.k3 = h->k3;
+  return g;
+}
+static YTabs ytabs(const chan_s* h) {
+  YTabs t;
+  t.A2 = h->tab_A2; t.B2 = h->tab_B2; t.B1 = h->tab_B1; t.lu1 = h->tab_lu1; t.lu2f = h->tab_lu2f;
+  t.d0 = h->tab_d0; t.dN = h->tab_dN; t.wq = h->tab_wq;
+  return t;
+}
+static const int kYThreads = 128;
+static dim3 ygrid(const chan_s* h) { return dim3((h->M + kYThreads - 1) / kYThreads); }
+
+static cudaError_t smem_attr(const void* fn, size_t bytes) {
+  if (bytes > 48 * 1024) return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  return cudaSuccess;
+}
+
+cudaError_t launch_setup_tables(chan_s* h) {
+  Geo g = geo(h);
+  YTabs t = ytabs(h);
+  k_setup_pois<<<(h->C + 127) / 128, 128, 0, h->stream>>>(g, t, h->pois);
+  k_setup_helm<<<(3 * h->C + 127) / 128, 128, 0, h->stream>>>(g, t, h->pois, h->helm, h->infl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_derive(chan_s* h) {
+  size_t sm = sizeof(double) * 35 * h->Ny;
+  cudaError_t e = smem_attr((const void*)k_derive, sm);
+  if (e != cudaSuccess) return e;
+  k_derive<<<ygrid(h), kYThreads, sm, h->stream>>>(geo(h), ytabs(h), h->v, h->chi, h->dv, h->scr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pre(chan_s* h, double2* u1, double2* u3, double2* om1, double2* om3) {
+  size_t sm = sizeof(double) * 14 * h->Ny;
+  cudaError_t e = smem_attr((const void*)k_pre, sm);
+  if (e != cudaSuccess) return e;
+  k_pre<<<ygrid(h), kYThreads, sm, h->stream>>>(geo(h), ytabs(h), h->v, h->om, h->dv, h->U1, h->U3, u1, u3, om1, om3);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_nonlin(chan_s* h, const double2* H1, const double2* H2, const double2* H3, double2* Nchi,
+                          double2* Nom) {
+  size_t sm = sizeof(double) * 14 * h->Ny;
+  cudaError_t e = smem_attr((const void*)k_nonlin, sm);
+  if (e != cudaSuccess) return e;
+  k_nonlin<<<ygrid(h), kYThreads, sm, h->stream>>>(geo(h), ytabs(h), H1, H2, H3, Nchi, Nom, h->scr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_helm(chan_s* h, const double2* Nchi, const double2* Nom, int s) {
+  size_t sm = sizeof(double) * 14 * h->Ny;
+  cudaError_t e = smem_attr((const void*)k_helm, sm);
+  if (e != cudaSuccess) return e;
+  k_helm<<<ygrid(h), kYThreads, sm, h->stream>>>(geo(h), ytabs(h), h->helm, h->om, h->chi, Nchi, Nom, h->Nchi_p,
+                                                 h->Nom_p, h->scr, s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_poisson(chan_s* h, int s) {
+  size_t sm = sizeof(double) * 21 * h->Ny;
+  cudaError_t e = smem_attr((const void*)k_poisson, sm);
+  if (e != cudaSuccess) return e;
+  k_poisson<<<ygrid(h), kYThreads, sm, h->stream>>>(geo(h), ytabs(h), h->helm, h->pois, h->infl, h->v, h->chi, h->dv,
+                                                    h->scr, s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mean(chan_s* h, const double2* H1, const double2* H3, int s) {
+  size_t sm = sizeof(double) * 3 * h->Ny;
+  cudaError_t e = smem_attr((const void*)k_mean, sm);
+  if (e != cudaSuccess) return e;
+  k_mean<<<1, 32, sm, h->stream>>>(geo(h), ytabs(h), h->helm, H1, H3, h->U1, h->U3, h->H1m_p, h->H3m_p, h->scal, s);
+  return cudaGetLastError();
+}
+
+double chan_rk3_weight(int s) { return h_rk3[s][2] + h_rk3[s][3]; }

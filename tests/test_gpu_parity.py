@@ -1,0 +1,197 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerance: relative L2 (||gpu - oracle|| / ||oracle|| over every stored
+coefficient of a field) <= 1e-10 after 10 substeps for the FP64 path, the
+bar the method's FP64 result is held to.  Both sides evaluate the same
+discrete operators; they differ only in rounding order (banded LU sweeps
+vs. dense LAPACK solves, Stockham radix-4/2/3 FFTs vs. pocketfft).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synthetic as SY
+
+pytestmark = pytest.mark.gpu
+
+CASES = {
+    # the small channel workload: Re_tau 180 minimal box, 32 x 49 x 32, dt 1e-3
+    "re180_32x49x32": (180.0, math.pi, math.pi / 2, 32, 49, 32, 1e-3),
+    # non-square, ragged: Nx/2 = 12 (partial kx blocks), 3Nz/2 = 54 (radix 2.3.3.3), 3Nx/2 = 36
+    "re250_24x33x36": (250.0, 2.0, 1.3, 24, 33, 36, 1e-3),
+}
+TOL = 1e-10
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.ravel(a - b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def chan():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_1808_06461_b300 as chan
+    return chan
+
+
+_setups = {}
+
+
+def setup(name):
+    if name not in _setups:
+        re, Lx, Lz, Nx, Ny, Nz, dt = CASES[name]
+        _setups[name] = O.Setup(re, Lx, Lz, Nx, Ny, Nz, dt)
+    return _setups[name]
+
+
+def ic(name, seed=11, amp=0.1):
+    st = setup(name)
+    return SY.perturbed_poiseuille(st.y, st.re_tau, st.Lx, st.Lz, st.Nx, st.Nz, seed=seed, amp=amp)
+
+
+def make(chan, name, **kw):
+    re, Lx, Lz, Nx, Ny, Nz, dt = CASES[name]
+    return chan.Channel(re, Lx, Lz, Nx, Ny, Nz, dt, **kw)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_grid_matches_oracle(chan, name):
+    ch = make(chan, name)
+    assert np.abs(ch.grid() - setup(name).y).max() <= 2e-16
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_nonlinear_parity(chan, name):
+    """H = u x omega after the a1 - a4 passes (dealiased), per field."""
+    st = setup(name)
+    s0 = ic(name)
+    ch = make(chan, name)
+    ch.set_state(s0["v"], s0["omega2"], s0["U1"], s0["U3"])
+    H = ch.nonlinear()
+    S = O.initial_state(st, s0["v"], s0["omega2"], s0["U1"], s0["U3"])
+    Href = O.nonlinear(st, S)
+    for f in range(3):
+        assert rel(H[f], Href[f]) < 1e-12, (f, rel(H[f], Href[f]))
+
+
+@pytest.fixture(scope="module")
+def ten_steps():
+    out = {}
+    for name in CASES:
+        st = setup(name)
+        s0 = ic(name)
+        S = O.initial_state(st, s0["v"], s0["omega2"], s0["U1"], s0["U3"])
+        out[name] = (s0, O.run(st, S, 10))
+    return out
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_ten_substeps_parity(chan, name, ten_steps):
+    s0, ref = ten_steps[name]
+    ch = make(chan, name)
+    ch.set_state(s0["v"], s0["omega2"], s0["U1"], s0["U3"])
+    ch.step(10)
+    g = ch.get_state()
+    for k in ("v", "omega2", "U1"):
+        assert rel(g[k], ref[k]) < TOL, (k, rel(g[k], ref[k]))
+    assert np.abs(g["U3"] - ref["U3"]).max() < TOL * np.abs(ref["U1"]).max()
+    assert abs(ch.time() - ref["t"]) < 1e-15
+    assert ch.substeps() == 10
+
+
+@pytest.mark.parametrize("kind,p", [(0, (120.0, 60.0)), (1, (50.0, 50.0))])
+def test_filter_and_stats_parity(chan, kind, p, ten_steps):
+    name = "re180_32x49x32"
+    st = setup(name)
+    s0, ref = ten_steps[name]
+    ch = make(chan, name)
+    ch.set_state(s0["v"], s0["omega2"], s0["U1"], s0["U3"])
+    ch.step(10)
+    ub, tau = ch.filter_stresses(kind, *p)
+    ub_ref, tau_ref = O.filter_stresses(st, ref, kind, *p)
+    for f in range(3):
+        assert rel(ub[f], ub_ref[f]) < TOL
+    for q in range(6):
+        assert rel(tau[q], tau_ref[q]) < TOL, (q, rel(tau[q], tau_ref[q]))
+    out, utau, ubulk, f = ch.stats()
+    out_ref, utau_ref, ubulk_ref = O.stats(st, ref, ub_ref, tau_ref)
+    scale = np.abs(out_ref[2:8]).max()
+    assert np.abs(out - out_ref).max() < TOL * scale
+    assert abs(utau - utau_ref) < TOL * utau_ref and abs(ubulk - ubulk_ref) < TOL * ubulk_ref
+    assert abs(f - ref["f"]) < 1e-8 * abs(ref["f"])
+    # the second-order identity <u_i u_j> = <ubar_i ubar_j> + <tau_ij> on the device results
+    assert np.abs(out[2:8] - out[8:14] - out[14:20]).max() < 1e-12 * scale
+
+
+def test_poiseuille_steady_gpu(chan):
+    name = "re180_32x49x32"
+    s0 = ic(name, amp=0.0)
+    ch = make(chan, name)
+    ch.set_state(s0["v"], s0["omega2"], s0["U1"], s0["U3"])
+    ch.step(30)
+    g = ch.get_state()
+    assert np.abs(g["U1"] - s0["U1"]).max() <= 1e-13 * np.abs(s0["U1"]).max()
+    assert np.abs(g["v"]).max() == 0.0 and np.abs(g["omega2"]).max() == 0.0
+
+
+def test_invariants_after_steps(chan):
+    """Continuity, wall conditions, flux and Hermitian symmetry of the device state."""
+    name = "re250_24x33x36"
+    st = setup(name)
+    s0 = ic(name, seed=5)
+    ch = make(chan, name)
+    ch.set_state(s0["v"], s0["omega2"], s0["U1"], s0["U3"])
+    ch.step(12)
+    g = ch.get_state()
+    S = dict(v=g["v"], omega2=g["omega2"], U1=g["U1"], U3=g["U3"])
+    u1, v, u3, _, dv, _ = O.velocities(st, S)
+    scale = np.abs(u1[:, :, 1:]).max()
+    assert O.divergence(st, S) < 1e-12 * scale
+    assert np.abs(g["v"][[0, -1]]).max() < 1e-14 * scale
+    assert np.abs(dv[[0, -1]]).max() < 1e-11 * scale
+    assert abs(st.flux(g["U1"]) - st.flux(s0["U1"])) < 1e-13 * st.flux(s0["U1"])
+    F = g["v"]
+    for jz in range(1, st.Nz // 2):
+        assert np.abs(F[:, jz, 0] - np.conj(F[:, st.Nz - jz, 0])).max() < 1e-13 * np.abs(F).max()
+
+
+def test_orr_sommerfeld_growth_gpu(chan):
+    """The device substep reproduces the Re = 7500 Orr-Sommerfeld growth rate (1 %)."""
+    ch = chan.Channel(7500.0, 2 * math.pi, 1.0, 4, 97, 4, 0.02, grid_re=180.0)
+    y = ch.grid()
+    c_ref = 0.00223497
+    _, vprof = SY.orr_sommerfeld_mode(7500, 1.0, y)
+    s0 = SY.single_mode(y, 4, 4, 1, 0, v_profile=1e-6 * vprof, U1=1 - y ** 2)
+    ch.set_state(s0["v"], s0["omega2"], s0["U1"], s0["U3"])
+    wq = np.zeros_like(y)
+    wq[:-1] += 0.5 * np.diff(y)
+    wq[1:] += 0.5 * np.diff(y)
+    a0 = math.sqrt(np.sum(wq * np.abs(s0["v"][:, 0, 1]) ** 2))
+    ch.step(1500)
+    g = ch.get_state()
+    a1 = math.sqrt(np.sum(wq * np.abs(g["v"][:, 0, 1]) ** 2))
+    growth = math.log(a1 / a0) / ch.time()
+    assert abs(growth - c_ref) < 0.01 * c_ref, growth
+
+
+def test_mixed_precision_error(chan, ten_steps):
+    """FP32 transforms and products, FP64 y-solves: stated error against the FP64 oracle."""
+    name = "re180_32x49x32"
+    s0, ref = ten_steps[name]
+    ch = make(chan, name, precision=chan.CHAN_PREC_MIXED)
+    ch.set_state(s0["v"], s0["omega2"], s0["U1"], s0["U3"])
+    ch.step(10)
+    g = ch.get_state()
+    assert rel(g["v"], ref["v"]) < 1e-5
+    assert rel(g["omega2"], ref["omega2"]) < 1e-5
+    assert rel(g["U1"], ref["U1"]) < 1e-7
+
+
+def test_step_before_state_is_an_error(chan):
+    ch = make(chan, "re180_32x49x32")
+    with pytest.raises(chan.ChanError) as e:
+        ch.step(1)
+    assert e.value.code == chan.CHAN_ESTATE
