@@ -1,0 +1,383 @@
+#!/usr/bin/env python
+"""Throughput of the channel substep on B300: DNS Mpts.substep/s.
+
+Workload (default): Re_tau = 550, Lx = 2 pi, Lz = pi, 384 x 257 x 384
+collocation points, dt = 2e-4, FP64, seeded turbulent-like initial field
+(Reichardt mean + k^-5/3 random-phase fluctuations).  One bench "step" is
+one pass of the whole hot path: 50 RK3 substeps, then the filter with the
+filtered stresses (sharp cut-off l1c+ = 120, l3c+ = 60), then the plane
+statistics -- the cadence of that workload (filtered fields every 50
+substeps).  Throughput counts N1 N2 N3 points x 50 substeps per step.
+
+Launch: ``python bench.py [--gpus N --steps K --warmup W]``; for N > 1 under
+torch.distributed.run each rank runs an independent replica (the path has
+no data exchange: weak scaling, replicas only).  ``--impl reference`` times
+the FP64 CPU oracle on a bounded sample of the same workload instead.
+"""
+import argparse
+import copy
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+CONFIGS = {
+    "re550_384x257x384": dict(re=550.0, Lx=2 * math.pi, Lz=math.pi, Nx=384, Ny=257, Nz=384, dt=2e-4,
+                              sub_per_step=50, filt=(0, 120.0, 60.0)),
+    "re180_32x49x32": dict(re=180.0, Lx=math.pi, Lz=math.pi / 2, Nx=32, Ny=49, Nz=32, dt=1e-3,
+                           sub_per_step=10, filt=(1, 50.0, 50.0)),
+    "re1000_768x385x768": dict(re=1000.0, Lx=2 * math.pi, Lz=math.pi, Nx=768, Ny=385, Nz=768, dt=1e-4,
+                               sub_per_step=50, filt=(0, 120.0, 60.0)),
+}
+DEFAULT = "re550_384x257x384"
+
+
+# ---------------------------------------------------------------------------
+# Algorithmic FP64 flop counts of each kernel (per launch), from the steps the
+# kernels take: Stockham radix-4/2/3 FFTs (a radix-R butterfly costs its
+# DFT adds plus (R-1) twiddle complex multiplies of 6 flops unless its twiddle
+# index is 0) and the banded sweeps of the wall-normal solves (a real
+# coefficient times a complex value = 2 FMA = 4 flops).
+# ---------------------------------------------------------------------------
+def radix_plan(L):
+    r, out = L, []
+    while r % 4 == 0:
+        out.append(4); r //= 4
+    while r % 2 == 0:
+        out.append(2); r //= 2
+    while r % 3 == 0:
+        out.append(3); r //= 3
+    assert r == 1
+    return out
+
+
+def fft_flops(L):
+    dft = {2: 4, 4: 16, 3: 16}
+    p, tot = 1, 0
+    for R in radix_plan(L):
+        nb = L // R
+        tot += nb * dft[R] + nb * (1.0 - 1.0 / p) * (R - 1) * 6
+        p *= R
+    return tot
+
+
+# per mode-point flops of the wall-normal kernels (read off their sweeps)
+Y_FLOPS = {"k_pre": 140, "k_nonlin": 70, "k_helm": 192, "k_poisson": 132, "k_derive": 140}
+
+
+def kernel_flops(name, c, launches_by_mode):
+    Nx, Ny, Nz = c["Nx"], c["Ny"], c["Nz"]
+    nxh, L1, L3 = Nx // 2, 3 * Nx // 2, 3 * Nz // 2
+    M = nxh * Nz
+    if name in Y_FLOPS:
+        return Y_FLOPS[name] * M * Ny
+    if name in ("k_zinv", "k_zfwd"):
+        nf = launches_by_mode.get(name, 6 if name == "k_zinv" else 3)
+        return nf * Ny * nxh * fft_flops(L3)
+    if name == "k_xpass":
+        pairs = Ny * L3 // 2
+        return pairs * (9 * fft_flops(L1) + L1 * 18 + 3 * nxh * 16)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+def clocks_sampler(stop, out):
+    cmd = ["nvidia-smi", "--query-gpu=clocks.sm,clocks.max.sm,clocks_event_reasons.active,"
+           "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+           "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+           "--format=csv,noheader,nounits", "-i", str(int(os.environ.get("LOCAL_RANK", "0")))]
+    while not stop.is_set():
+        try:
+            r = subprocess.run(cmd, capture_output=True, text=True, timeout=5)
+            if r.returncode == 0 and r.stdout.strip():
+                out.append([x.strip() for x in r.stdout.strip().splitlines()[0].split(",")])
+        except Exception:
+            pass
+        stop.wait(0.2)
+
+
+def summarize_clocks(samples):
+    if not samples:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+    sm = [float(s[0]) for s in samples if s[0].replace(".", "").isdigit()]
+    mx = [float(s[1]) for s in samples if s[1].replace(".", "").isdigit()]
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    reasons = sorted({names[i] for s in samples for i in range(4) if len(s) > 3 + i and s[3 + i] == "Active"})
+    return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+            "reasons": reasons, "samples": len(samples)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return json.load(open(p))
+    except Exception:
+        return {}
+
+
+def fp64_peak_tflops(torch):
+    """Dense FP64 rate of this GPU, measured as a cuBLAS DGEMM (best of 3), TFLOP/s."""
+    n = 4096
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    torch.matmul(a, b)
+    best = 1e9
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    del a, b
+    return 2.0 * n ** 3 / (best * 1e-3) / 1e12
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle on a bounded sample (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+def oracle_sample_substep_seconds(c, n_planes=4, n_modes=512):
+    """Estimated oracle seconds per substep of the full workload, from a sample.
+
+    Timed: the wall-normal derivatives of the a1 step over all modes, the
+    a2-a4 transforms and products on ``n_planes`` x-z planes (scaled by
+    Ny / n_planes), the a5 terms over all modes, the a6-a7 implicit solves
+    on ``n_modes`` modes (scaled by M / n_modes) and the a8 mean flow.
+    """
+    import oracle as O
+    import synthetic as SY
+    st = O.Setup(c["re"], c["Lx"], c["Lz"], c["Nx"], c["Ny"], c["Nz"], c["dt"])
+    s0 = SY.turbulent_like(st.y, c["re"], c["Lx"], c["Lz"], c["Nx"], c["Nz"], seed=1)
+    S = O.initial_state(st, s0["v"], s0["omega2"], s0["U1"], s0["U3"])
+    M = st.Nz * st.nxh
+    t0 = time.perf_counter()
+    u1, v, u3, du1, dv, du3 = O.velocities(st, S)
+    t_vel = time.perf_counter() - t0
+    pl = np.linspace(0, st.Ny - 1, n_planes).astype(int)
+    t0 = time.perf_counter()
+    om1 = du3[pl] - 1j * st.K3 * v[pl]
+    om3 = 1j * st.K1 * v[pl] - du1[pl]
+    p = [O.to_physical(st, F) for F in (u1[pl], v[pl], u3[pl], om1, S["omega2"][pl], om3)]
+    H1 = p[1] * p[5] - p[2] * p[4]
+    H2 = p[2] * p[3] - p[0] * p[5]
+    H3 = p[0] * p[4] - p[1] * p[3]
+    Hs = [O.to_fourier(st, H) for H in (H1, H2, H3)]
+    t_fft = (time.perf_counter() - t0) * st.Ny / n_planes
+    H = [np.zeros_like(v) for _ in range(3)]
+    for k in range(3):
+        H[k][pl] = Hs[k]
+    t0 = time.perf_counter()
+    Nchi, Nom = O.rhs_terms(st, *H)
+    t_rhs = time.perf_counter() - t0
+    sel = np.linspace(0, M - 1, n_modes).astype(int)
+    sts = copy.copy(st)
+    for k in ("K1", "K3", "K2", "keep"):
+        setattr(sts, k, getattr(st, k).reshape(1, -1)[:, sel])
+    sub = lambda F: F.reshape(st.Ny, 1, M)[:, :, sel]
+    Ss = dict(S, v=sub(S["v"]), omega2=sub(S["omega2"]), chi=sub(S["chi"]),
+              Nchi_prev=sub(S["Nchi_prev"]), Nom_prev=sub(S["Nom_prev"]))
+    t0 = time.perf_counter()
+    O.channel.implicit_step(sts, Ss, sub(Nchi), sub(Nom), 0)
+    t_imp = (time.perf_counter() - t0) * M / n_modes
+    t0 = time.perf_counter()
+    O.channel.mean_flow_step(st, S, H[0][:, 0, 0].real, H[2][:, 0, 0].real, 0)
+    t_mean = time.perf_counter() - t0
+    return t_vel + t_fft + t_rhs + t_imp + t_mean, dict(planes=n_planes, modes=n_modes)
+
+
+def cpu_threads():
+    try:
+        import threadpoolctl
+        info = threadpoolctl.threadpool_info()
+        return max([i.get("num_threads", 1) for i in info] + [1])
+    except Exception:
+        return os.cpu_count()
+
+
+def run_reference(args, c, name):
+    """The oracle, as it stands, on a bounded sample of each step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    pts = c["Nx"] * c["Ny"] * c["Nz"]
+    per_sub = []
+    for k in range(args.warmup + args.steps):
+        t, sample = oracle_sample_substep_seconds(c)
+        if k >= args.warmup:
+            per_sub.append(t)
+    t_sub = float(np.median(per_sub))
+    value = pts / t_sub / 1e6
+    desc = ("oracle substep estimated from a sample: a2-a4 on %d of %d planes, a6-a7 on %d of %d modes, "
+            "a1/a5 y-derivatives and a8 over everything; per-step time = %d substeps (filter pass not "
+            "included)" % (sample["planes"], c["Ny"], sample["modes"], c["Nz"] * c["Nx"] // 2, c["sub_per_step"]))
+    line = {"impl": "reference", "metric": "DNS Mpts.substep/s", "value": value, "unit": "Mpts*substep/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t_sub * c["sub_per_step"] * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": name, "Nx": c["Nx"], "Ny": c["Ny"], "Nz": c["Nz"], "re_tau": c["re"],
+                       "substeps_per_step": c["sub_per_step"]},
+            "cpu_baseline": {"value": value, "unit": "Mpts*substep/s", "cores": cpu_threads(), "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": "Mpts*substep/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+def run_ours(args, c, name):
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import paper_1808_06461_b300 as chan
+    import synthetic as SY
+    prec = chan.CHAN_PREC_MIXED if args.precision == "mixed" else chan.CHAN_PREC_FP64
+    stream = torch.cuda.current_stream()
+    ch = chan.Channel(c["re"], c["Lx"], c["Lz"], c["Nx"], c["Ny"], c["Nz"], c["dt"], precision=prec,
+                      stream=stream.cuda_stream)
+    y = ch.grid()
+    s0 = SY.turbulent_like(y, c["re"], c["Lx"], c["Lz"], c["Nx"], c["Nz"], seed=1 + rank)
+    nsub = c["sub_per_step"]
+    kind, p1, p3 = c["filt"]
+    pts = c["Nx"] * c["Ny"] * c["Nz"]
+
+    def one_step():
+        ch.step(nsub)
+        ch.filter_stresses(kind, p1, p3, want=False)
+        ch.stats()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+            torch.cuda.synchronize()
+
+    # ---- device-resident throughput
+    ch.set_state(s0["v"], s0["omega2"], s0["U1"], s0["U3"])
+    for _ in range(args.warmup):
+        one_step()
+    peak64 = fp64_peak_tflops(torch)
+    barrier()
+    stop, samples = threading.Event(), []
+    th = threading.Thread(target=clocks_sampler, args=(stop, samples), daemon=True)
+    th.start()
+    ch.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        one_step()
+    e1.record(stream)
+    barrier()
+    stop.set()
+    th.join(timeout=10)
+    prof = ch.profile_read()
+    ch.profile(False)
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * args.steps * nsub * pts / (ms * 1e-3) / 1e6
+
+    # ---- end to end through the public API with pinned host buffers
+    shape = (c["Ny"], c["Nz"], c["Nx"] // 2)
+    pin = lambda n, dt: torch.empty(n, dtype=dt, pin_memory=True).numpy()
+    hv = pin(2 * s0["v"].size, torch.float64).view(np.complex128).reshape(shape)
+    ho = pin(2 * s0["v"].size, torch.float64).view(np.complex128).reshape(shape)
+    hv[...] = s0["v"]
+    ho[...] = s0["omega2"]
+    hU1 = pin(c["Ny"], torch.float64); hU1[...] = s0["U1"]
+    hU3 = pin(c["Ny"], torch.float64); hU3[...] = s0["U3"]
+    n = s0["v"].size
+    h2d = 2 * n * 16 + 2 * c["Ny"] * 8
+    d2h = (9 * n + 2 * n) * 16 + 2 * c["Ny"] * 8 + (20 * c["Ny"] + 3) * 8
+    e2e_steps = max(1, min(args.steps, 3))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ch.set_state(hv, ho, hU1, hU3)
+        ch.step(nsub)
+        ch.filter_stresses(kind, p1, p3, want=True)
+        ch.stats()
+        ch.get_state()
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = world * e2e_steps * nsub * pts / e2e_s / 1e6
+
+    # ---- roofline of the dominant kernel (FP64 ALU bound: see the design notes)
+    dom = max(prof, key=lambda k: prof[k][0])
+    dms, dn = prof[dom]
+    fl = kernel_flops(dom, c, {})
+    achieved = fl / (dms / dn * 1e-3) / 1e12 if dn else 0.0
+    launches = int(sum(v[1] for v in prof.values()))
+    kernels = {k: {"ms": round(v[0], 3), "launches": v[1], "share": round(v[0] / max(1e-9, sum(x[0] for x in prof.values())), 4)}
+               for k, v in prof.items() if v[1]}
+    peaks = measured_peaks()
+    line = {"metric": "DNS Mpts.substep/s", "value": value, "unit": "Mpts*substep/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == chan.CHAN_PREC_FP64 else "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": name, "Nx": c["Nx"], "Ny": c["Ny"], "Nz": c["Nz"], "re_tau": c["re"],
+                       "dt": c["dt"], "substeps_per_step": nsub, "filter": {"kind": "sharp" if kind == 0 else "box",
+                                                                           "p1": p1, "p3": p3},
+                       "precision": args.precision, "l2": "inputs larger than L2 (state %.1f GB)" %
+                       (6 * n * 16 / 1e9), "parallelism": "replicas" if world > 1 else "single"},
+            "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak64,
+                         "unit": "TFLOP/s", "frac": achieved / peak64, "traffic": None,
+                         "peak_source": "FP64 DGEMM measured in this run (cuBLAS, 4096^3)",
+                         "hbm_peak_gbs": peaks.get("hbm_gbs")},
+            "kernels": kernels,
+            "gpu_launches": launches,
+            "e2e": {"value": e2e, "unit": "Mpts*substep/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "steps": e2e_steps},
+            "clocks": summarize_clocks(samples)}
+    if rank == 0 and not args.no_cpu_baseline:
+        t_sub, sample = oracle_sample_substep_seconds(c)
+        line["cpu_baseline"] = {"value": pts / t_sub / 1e6, "unit": "Mpts*substep/s", "cores": cpu_threads(),
+                                "kind": "oracle",
+                                "sample": "one substep estimated from a2-a4 on %d of %d planes and a6-a7 on %d of %d "
+                                          "modes (scaled), a1/a5/a8 over everything" %
+                                          (sample["planes"], c["Ny"], sample["modes"], c["Nz"] * c["Nx"] // 2)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ch.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--config", choices=sorted(CONFIGS), default=DEFAULT)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    c = CONFIGS[args.config]
+    if args.impl == "reference":
+        run_reference(args, c, args.config)
+    else:
+        run_ours(args, c, args.config)
+
+
+if __name__ == "__main__":
+    main()

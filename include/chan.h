@@ -155,6 +155,20 @@ int chan_stats(chan_t h, double* out, double* utau, double* ubulk, double* f);
  */
 int chan_nonlinear(chan_t h, double* H);
 
+/*
+ * Per-kernel timing (tracing; the paper has no counterpart).  enable = 1
+ * resets the counters and brackets every subsequent kernel launch of the
+ * handle with CUDA events on its stream; enable = 0 stops recording.
+ * chan_profile_read synchronises and writes, for each kernel id
+ * k < CHAN_NKERNELS, the summed device time in ms and the launch count
+ * since the last reset (launches are counted even when timing is off).
+ * chan_kernel_name(k) names kernel k (NULL when out of range).
+ */
+#define CHAN_NKERNELS 11
+int chan_profile(chan_t h, int enable);
+int chan_profile_read(chan_t h, double* ms, long long* launches);
+const char* chan_kernel_name(int k);
+
 /* Wait for the handle's stream. */
 int chan_sync(chan_t h);
 

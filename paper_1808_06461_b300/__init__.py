@@ -28,7 +28,8 @@ SYMBOLS = ("chan_opts_default", "chan_init", "chan_init_ex", "chan_free", "chan_
            "chan_fourier_count", "chan_device_bytes", "chan_get_grid", "chan_set_state",
            "chan_set_state_device", "chan_get_state", "chan_get_state_device", "chan_step",
            "chan_filter_stresses", "chan_stats", "chan_nonlinear", "chan_sync", "chan_time",
-           "chan_substeps")
+           "chan_substeps", "chan_profile", "chan_profile_read", "chan_kernel_name")
+CHAN_NKERNELS = 11
 
 
 class chan_opts(ctypes.Structure):
@@ -71,6 +72,9 @@ def load_library(path=LIB_PATH):
         "chan_sync": (I, [P]),
         "chan_time": (D, [P]),
         "chan_substeps": (ctypes.c_longlong, [P]),
+        "chan_profile": (I, [P, I]),
+        "chan_profile_read": (I, [P, P, P]),
+        "chan_kernel_name": (ctypes.c_char_p, [I]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -140,6 +144,17 @@ class Channel:
 
     def substeps(self):
         return int(_lib.chan_substeps(self.h))
+
+    # ---- tracing
+    def profile(self, enable=True):
+        _check(self.h, _lib.chan_profile(self.h, 1 if enable else 0))
+
+    def profile_read(self):
+        """{kernel name: (total ms, launches)} since the last profile(True)."""
+        ms = np.zeros(CHAN_NKERNELS)
+        n = np.zeros(CHAN_NKERNELS, dtype=np.int64)
+        _check(self.h, _lib.chan_profile_read(self.h, _ptr(ms), _ptr(n)))
+        return {_lib.chan_kernel_name(k).decode(): (float(ms[k]), int(n[k])) for k in range(CHAN_NKERNELS)}
 
     # ---- state
     def set_state(self, v, omega2, U1, U3):

@@ -64,6 +64,30 @@ __global__ void k_flux(const double* U1, const double* wq, int Ny, double* scal)
 
 size_t fsize(const chan_s* h) { return (size_t)h->Ny * h->M; }
 
+const char* const kKernelNames[KID_COUNT] = {"k_pre", "k_zinv", "k_xpass", "k_zfwd", "k_nonlin", "k_helm",
+                                             "k_poisson", "k_mean", "k_filter_out", "k_stats", "k_derive"};
+
+// Launch bracket: counts the launch and, when tracing, records an event pair.
+struct Traced {
+  chan_s* h;
+  ProfRec* r;
+  Traced(chan_s* hh, int k) : h(hh), r(nullptr) {
+    h->launches[k] += 1;
+    if (!h->prof) return;
+    if (h->nrec == h->recs.size()) {
+      ProfRec n{k, nullptr, nullptr};
+      if (cudaEventCreate(&n.a) != cudaSuccess || cudaEventCreate(&n.b) != cudaSuccess) return;
+      h->recs.push_back(n);
+    }
+    r = &h->recs[h->nrec++];
+    r->k = k;
+    cudaEventRecord(r->a, h->stream);
+  }
+  ~Traced() {
+    if (r) cudaEventRecord(r->b, h->stream);
+  }
+};
+
 // Work-field slots (Fourier layout)
 enum { WF_U1 = 0, WF_U3 = 1, WF_OM1 = 2, WF_OM3 = 3, WF_H1 = 4, WF_H2 = 5, WF_H3 = 6, WF_NCHI = 7, WF_NOM = 8, NWF = 14 };
 
@@ -83,7 +107,7 @@ void clean_modes(chan_s* h, double2* f) {
 void after_state_upload(chan_s* h) {
   clean_modes(h, h->v);
   clean_modes(h, h->om);
-  CK(launch_derive(h));
+  { Traced t(h, KID_DERIVE); CK(launch_derive(h)); }
   CK(cudaMemsetAsync(h->Nchi_p, 0, fsize(h) * sizeof(double2), h->stream));
   CK(cudaMemsetAsync(h->Nom_p, 0, fsize(h) * sizeof(double2), h->stream));
   CK(cudaMemsetAsync(h->H1m_p, 0, h->Ny * sizeof(double), h->stream));
@@ -97,26 +121,29 @@ void after_state_upload(chan_s* h) {
 }
 
 // u_1, u_3, omega_1, omega_3 of the current state into the work slots.
-void run_pre(chan_s* h) { CK(launch_pre(h, wf(h, WF_U1), wf(h, WF_U3), wf(h, WF_OM1), wf(h, WF_OM3))); }
+void run_pre(chan_s* h) {
+  Traced t(h, KID_PRE);
+  CK(launch_pre(h, wf(h, WF_U1), wf(h, WF_U3), wf(h, WF_OM1), wf(h, WF_OM3)));
+}
 
 // H = u x omega of the current state into WF_H1..WF_H3 (after run_pre).
 void run_nonlinear(chan_s* h) {
   const double2* in[6] = {wf(h, WF_U1), h->v, wf(h, WF_U3), wf(h, WF_OM1), h->om, wf(h, WF_OM3)};
   void* mx[6] = {mixed(h, 0), mixed(h, 1), mixed(h, 2), mixed(h, 3), mixed(h, 4), mixed(h, 5)};
-  CK(launch_zinv(h, in, nullptr, mx, 6));
-  CK(launch_xpass(h, 0, mx, mx));
+  { Traced t(h, KID_ZINV); CK(launch_zinv(h, in, nullptr, mx, 6)); }
+  { Traced t(h, KID_XPASS); CK(launch_xpass(h, 0, mx, mx)); }
   double2* Hout[3] = {wf(h, WF_H1), wf(h, WF_H2), wf(h, WF_H3)};
-  CK(launch_zfwd(h, mx, Hout, 3));
+  { Traced t(h, KID_ZFWD); CK(launch_zfwd(h, mx, Hout, 3)); }
 }
 
 void run_substep(chan_s* h) {
   const int s = (int)(h->nsub % 3);
   run_pre(h);
   run_nonlinear(h);
-  CK(launch_nonlin(h, wf(h, WF_H1), wf(h, WF_H2), wf(h, WF_H3), wf(h, WF_NCHI), wf(h, WF_NOM)));
-  CK(launch_helm(h, wf(h, WF_NCHI), wf(h, WF_NOM), s));
-  CK(launch_poisson(h, s));
-  CK(launch_mean(h, wf(h, WF_H1), wf(h, WF_H3), s));
+  { Traced t(h, KID_NONLIN); CK(launch_nonlin(h, wf(h, WF_H1), wf(h, WF_H2), wf(h, WF_H3), wf(h, WF_NCHI), wf(h, WF_NOM))); }
+  { Traced t(h, KID_HELM); CK(launch_helm(h, wf(h, WF_NCHI), wf(h, WF_NOM), s)); }
+  { Traced t(h, KID_POISSON); CK(launch_poisson(h, s)); }
+  { Traced t(h, KID_MEAN); CK(launch_mean(h, wf(h, WF_H1), wf(h, WF_H3), s)); }
   h->t += chan_rk3_weight(s) * h->dt;
   h->nsub += 1;
 }
@@ -258,6 +285,7 @@ int chan_init_ex(chan_t* out, const chan_opts* o) {
 void chan_free(chan_t h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
+  for (ProfRec& r : h->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (void* p : h->allocs) cudaFree(p);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
@@ -383,16 +411,16 @@ int chan_filter_stresses(chan_t h, int kind, double p1, double p3, double* ubar,
     const int applyG[6] = {0, 0, 0, 1, 1, 1};
     void* mx[12];
     for (int k = 0; k < 12; ++k) mx[k] = mixed(h, k);
-    CK(launch_zinv(h, in, applyG, mx, 6));
-    CK(launch_xpass(h, 1, mx + 3, mx + 6));   // ubar_i ubar_j -> slots 6..11
-    CK(launch_xpass(h, 1, mx, mx));           // u_i u_j       -> slots 0..5
+    { Traced t(h, KID_ZINV); CK(launch_zinv(h, in, applyG, mx, 6)); }
+    { Traced t(h, KID_XPASS); CK(launch_xpass(h, 1, mx + 3, mx + 6)); }   // ubar_i ubar_j -> slots 6..11
+    { Traced t(h, KID_XPASS); CK(launch_xpass(h, 1, mx, mx)); }           // u_i u_j       -> slots 0..5
     double2* fo[12];
     for (int k = 0; k < 12; ++k) fo[k] = wf(h, 2 + k);
-    CK(launch_zfwd(h, mx, fo, 12));
+    { Traced t(h, KID_ZFWD); CK(launch_zfwd(h, mx, fo, 12)); }
     const double2* u[3] = {wf(h, WF_U1), h->v, wf(h, WF_U3)};
     const double2* puu[6] = {fo[0], fo[1], fo[2], fo[3], fo[4], fo[5]};
     const double2* pbb[6] = {fo[6], fo[7], fo[8], fo[9], fo[10], fo[11]};
-    CK(launch_filter_out(h, u, puu, pbb, filt(h, 0), filt(h, 3)));
+    { Traced t(h, KID_FILTER_OUT); CK(launch_filter_out(h, u, puu, pbb, filt(h, 0), filt(h, 3))); }
     const size_t n = fsize(h);
     if (ubar) CK(cudaMemcpyAsync(ubar, filt(h, 0), 3 * n * sizeof(double2), cudaMemcpyDeviceToHost, h->stream));
     if (tau) CK(cudaMemcpyAsync(tau, filt(h, 3), 6 * n * sizeof(double2), cudaMemcpyDeviceToHost, h->stream));
@@ -409,8 +437,11 @@ int chan_stats(chan_t h, double* out, double* utau, double* ubulk, double* f) {
   if (!h->have_state) return bad(h, "chan_stats: no state set", CHAN_ESTATE);
   try {
     run_pre(h);
-    CK(launch_stats(h, wf(h, WF_U1), wf(h, WF_U3), h->have_filter ? filt(h, 0) : nullptr,
-                    h->have_filter ? filt(h, 3) : nullptr, h->have_filter ? 1 : 0));
+    {
+      Traced t(h, KID_STATS);
+      CK(launch_stats(h, wf(h, WF_U1), wf(h, WF_U3), h->have_filter ? filt(h, 0) : nullptr,
+                      h->have_filter ? filt(h, 3) : nullptr, h->have_filter ? 1 : 0));
+    }
     std::vector<double> st(CHAN_NSTAT * (size_t)h->Ny + 2);
     double sc[2];
     CK(cudaMemcpyAsync(st.data(), h->stat, st.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
@@ -434,6 +465,34 @@ int chan_sync(chan_t h) {
   if (e != cudaSuccess) return bad(h, std::string("chan_sync: ") + cudaGetErrorString(e), CHAN_ECUDA);
   return CHAN_OK;
 }
+
+int chan_profile(chan_t h, int enable) {
+  if (!h) return bad(nullptr, "chan_profile: NULL handle");
+  if (enable) {
+    for (int k = 0; k < KID_COUNT; ++k) h->launches[k] = 0;
+    h->nrec = 0;
+  }
+  h->prof = enable != 0;
+  return CHAN_OK;
+}
+
+int chan_profile_read(chan_t h, double* ms, long long* launches) {
+  if (!h) return bad(nullptr, "chan_profile_read: NULL handle");
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return bad(h, std::string("chan_profile_read: ") + cudaGetErrorString(e), CHAN_ECUDA);
+  if (ms) {
+    for (int k = 0; k < KID_COUNT; ++k) ms[k] = 0.0;
+    for (size_t i = 0; i < h->nrec; ++i) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, h->recs[i].a, h->recs[i].b) == cudaSuccess) ms[h->recs[i].k] += t;
+    }
+  }
+  if (launches)
+    for (int k = 0; k < KID_COUNT; ++k) launches[k] = h->launches[k];
+  return CHAN_OK;
+}
+
+const char* chan_kernel_name(int k) { return (k >= 0 && k < KID_COUNT) ? kKernelNames[k] : nullptr; }
 
 double chan_time(chan_t h) { return h ? h->t : 0.0; }
 long long chan_substeps(chan_t h) { return h ? h->nsub : 0; }

@@ -38,6 +38,14 @@ struct FftPlan {
   int radix[16];
 };
 
+enum { KID_PRE = 0, KID_ZINV, KID_XPASS, KID_ZFWD, KID_NONLIN, KID_HELM, KID_POISSON, KID_MEAN,
+       KID_FILTER_OUT, KID_STATS, KID_DERIVE, KID_COUNT };
+
+struct ProfRec {
+  int k;
+  cudaEvent_t a, b;
+};
+
 struct chan_s {
   // configuration
   double re, Lx, Lz, dt, nu, eta_w, grid_re;
@@ -74,6 +82,11 @@ struct chan_s {
   std::string err;
   FftPlan p1, p3;
   std::vector<void*> allocs;
+  // tracing
+  bool prof;
+  long long launches[KID_COUNT];
+  std::vector<ProfRec> recs;     // event pairs recorded since the last reset
+  size_t nrec;                   // pairs in use
 };
 
 // Kernel launchers (return cudaGetLastError()).
