@@ -169,6 +169,15 @@ int chan_profile(chan_t h, int enable);
 int chan_profile_read(chan_t h, double* ms, long long* launches);
 const char* chan_kernel_name(int k);
 
+/*
+ * Non-linear terms of the v and omega_2 equations of the current state,
+ * Appendix A Eq. (hghv): N_chi = -d/dy(i k1 H1 + i k3 H3) - k^2 H2 and
+ * N_omega2 = i k3 H1 - i k1 H3 (the D1 derivative is the compact scheme).
+ * N receives 2 fields (N_chi, N_omega2), spectral layout, host.  Does not
+ * advance time; synchronises.
+ */
+int chan_rhs_terms(chan_t h, double* N);
+
 /* Wait for the handle's stream. */
 int chan_sync(chan_t h);
 

@@ -28,7 +28,8 @@ SYMBOLS = ("chan_opts_default", "chan_init", "chan_init_ex", "chan_free", "chan_
            "chan_fourier_count", "chan_device_bytes", "chan_get_grid", "chan_set_state",
            "chan_set_state_device", "chan_get_state", "chan_get_state_device", "chan_step",
            "chan_filter_stresses", "chan_stats", "chan_nonlinear", "chan_sync", "chan_time",
-           "chan_substeps", "chan_profile", "chan_profile_read", "chan_kernel_name")
+           "chan_substeps", "chan_profile", "chan_profile_read", "chan_kernel_name",
+           "chan_rhs_terms")
 CHAN_NKERNELS = 11
 
 
@@ -69,6 +70,7 @@ def load_library(path=LIB_PATH):
         "chan_filter_stresses": (I, [P, I, D, D, P, P]),
         "chan_stats": (I, [P, P, DP, DP, DP]),
         "chan_nonlinear": (I, [P, P]),
+        "chan_rhs_terms": (I, [P, P]),
         "chan_sync": (I, [P]),
         "chan_time": (D, [P]),
         "chan_substeps": (ctypes.c_longlong, [P]),
@@ -191,6 +193,12 @@ class Channel:
         H = np.empty((3,) + self.shape, dtype=np.complex128)
         _check(self.h, _lib.chan_nonlinear(self.h, _ptr(H)))
         return H
+
+    def rhs_terms(self):
+        """(N_chi, N_omega2) of the current state, shape (2, Ny, Nz, Nx/2)."""
+        N = np.empty((2,) + self.shape, dtype=np.complex128)
+        _check(self.h, _lib.chan_rhs_terms(self.h, _ptr(N)))
+        return N
 
     def filter_stresses(self, kind, p1, p3, want=True):
         ub = np.empty((3,) + self.shape, dtype=np.complex128) if want else None

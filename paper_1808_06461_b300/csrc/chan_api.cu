@@ -383,6 +383,21 @@ int chan_nonlinear(chan_t h, double* H) {
   return CHAN_OK;
 }
 
+int chan_rhs_terms(chan_t h, double* N) {
+  if (!h || !N) return bad(h, "chan_rhs_terms: NULL argument");
+  if (!h->have_state) return bad(h, "chan_rhs_terms: no state set", CHAN_ESTATE);
+  try {
+    run_pre(h);
+    run_nonlinear(h);
+    { Traced t(h, KID_NONLIN); CK(launch_nonlin(h, wf(h, WF_H1), wf(h, WF_H2), wf(h, WF_H3), wf(h, WF_NCHI), wf(h, WF_NOM))); }
+    CK(cudaMemcpyAsync(N, wf(h, WF_NCHI), 2 * fsize(h) * sizeof(double2), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+  } catch (Fail f) {
+    return f.code;
+  }
+  return CHAN_OK;
+}
+
 int chan_filter_stresses(chan_t h, int kind, double p1, double p3, double* ubar, double* tau) {
   if (!h) return bad(nullptr, "chan_filter_stresses: NULL handle");
   if (kind != CHAN_FILTER_SHARP && kind != CHAN_FILTER_BOX) return bad(h, "chan_filter_stresses: unknown kind");

@@ -77,6 +77,20 @@ def test_nonlinear_parity(chan, name):
         assert rel(H[f], Href[f]) < 1e-12, (f, rel(H[f], Href[f]))
 
 
+@pytest.mark.parametrize("name", list(CASES))
+def test_rhs_terms_parity(chan, name):
+    """N_chi and N_omega2 of Eq. (hghv) from the device H, per field."""
+    st = setup(name)
+    s0 = ic(name, seed=4)
+    ch = make(chan, name)
+    ch.set_state(s0["v"], s0["omega2"], s0["U1"], s0["U3"])
+    N = ch.rhs_terms()
+    S = O.initial_state(st, s0["v"], s0["omega2"], s0["U1"], s0["U3"])
+    Nref = O.rhs_terms(st, *O.nonlinear(st, S))
+    for f in range(2):
+        assert rel(N[f], Nref[f]) < 1e-12, (f, rel(N[f], Nref[f]))
+
+
 @pytest.fixture(scope="module")
 def ten_steps():
     out = {}
