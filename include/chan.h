@@ -178,6 +178,28 @@ const char* chan_kernel_name(int k);
  */
 int chan_rhs_terms(chan_t h, double* N);
 
+/*
+ * chan_rhs_terms_noalloc — the same N_chi, N_omega2 as chan_rhs_terms, but
+ * from caller device buffers and without allocating any device memory
+ * (the paper has no counterpart; this is a library interface).  For callers
+ * that cannot call cudaMalloc where they evaluate the terms: code running
+ * inside a memory pool it does not own, a latency-bound loop that cannot
+ * afford an allocation's implicit synchronisation, or a caller that has
+ * reserved all device memory for its own arena.
+ *   H: device, 3 fields (H1, H2, H3) in spectral layout, field-major.
+ *   N: device, 2 fields (N_chi, N_omega2) written in the same layout.
+ * Runs asynchronously on the handle's stream (chan_sync to wait); the
+ * current device must be the handle's.  Its only scratch is a fixed 32 MiB
+ * device array inside the library (held on every GPU that loads it until
+ * exit), so Ny * Nz * (Nx/2) must be <= 2097152, else CHAN_EINVAL.  The
+ * first call on a device looks up that array's address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the array and it keeps the last call's contents (the
+ * kernel writes every value before reading it, so nothing needs clearing);
+ * calls whose work overlaps on the GPU race on it.
+ */
+int chan_rhs_terms_noalloc(chan_t h, const void* H, void* N);
+
 /* Wait for the handle's stream. */
 int chan_sync(chan_t h);
 

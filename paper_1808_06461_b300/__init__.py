@@ -29,7 +29,7 @@ SYMBOLS = ("chan_opts_default", "chan_init", "chan_init_ex", "chan_free", "chan_
            "chan_set_state_device", "chan_get_state", "chan_get_state_device", "chan_step",
            "chan_filter_stresses", "chan_stats", "chan_nonlinear", "chan_sync", "chan_time",
            "chan_substeps", "chan_profile", "chan_profile_read", "chan_kernel_name",
-           "chan_rhs_terms")
+           "chan_rhs_terms", "chan_rhs_terms_noalloc")
 CHAN_NKERNELS = 11
 
 
@@ -71,6 +71,7 @@ def load_library(path=LIB_PATH):
         "chan_stats": (I, [P, P, DP, DP, DP]),
         "chan_nonlinear": (I, [P, P]),
         "chan_rhs_terms": (I, [P, P]),
+        "chan_rhs_terms_noalloc": (I, [P, P, P]),
         "chan_sync": (I, [P]),
         "chan_time": (D, [P]),
         "chan_substeps": (ctypes.c_longlong, [P]),

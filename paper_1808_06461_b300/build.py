@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libchan.so")
-CU = ["chan_api.cu", "kernels_y.cu", "kernels_fft.cu", "kernels_misc.cu"]
+CU = ["chan_api.cu", "kernels_y.cu", "kernels_fft.cu", "kernels_misc.cu", "noalloc.cu"]
 CPP = ["setup_host.cpp"]
 HEADERS = ["chan_internal.cuh", "chan_host.h"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",

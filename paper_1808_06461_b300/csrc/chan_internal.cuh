@@ -95,6 +95,9 @@ cudaError_t launch_derive(chan_s* h);
 cudaError_t launch_pre(chan_s* h, double2* u1, double2* u3, double2* om1, double2* om3);
 cudaError_t launch_nonlin(chan_s* h, const double2* H1, const double2* H2, const double2* H3,
                           double2* Nchi, double2* Nom);
+// k_nonlin with a caller-chosen scratch buffer of Ny * M double2.
+cudaError_t launch_nonlin_scratch(chan_s* h, const double2* H1, const double2* H2, const double2* H3,
+                                  double2* Nchi, double2* Nom, double2* scr);
 cudaError_t launch_helm(chan_s* h, const double2* Nchi, const double2* Nom, int s);
 cudaError_t launch_poisson(chan_s* h, int s);
 cudaError_t launch_mean(chan_s* h, const double2* H1, const double2* H3, int s);

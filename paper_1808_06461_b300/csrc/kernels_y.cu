@@ -685,6 +685,15 @@ cudaError_t launch_nonlin(chan_s* h, const double2* H1, const double2* H2, const
   return cudaGetLastError();
 }
 
+cudaError_t launch_nonlin_scratch(chan_s* h, const double2* H1, const double2* H2, const double2* H3, double2* Nchi,
+                                 double2* Nom, double2* scr) {
+  size_t sm = sizeof(double) * 14 * h->Ny;
+  cudaError_t e = smem_attr((const void*)k_nonlin, sm);
+  if (e != cudaSuccess) return e;
+  k_nonlin<<<ygrid(h), kYThreads, sm, h->stream>>>(geo(h), ytabs(h), H1, H2, H3, Nchi, Nom, scr);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_helm(chan_s* h, const double2* Nchi, const double2* Nom, int s) {
   size_t sm = sizeof(double) * 14 * h->Ny;
   cudaError_t e = smem_attr((const void*)k_helm, sm);
