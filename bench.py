@@ -34,6 +34,10 @@ CONFIGS = {
                               sub_per_step=50, filt=(0, 120.0, 60.0)),
     "re180_32x49x32": dict(re=180.0, Lx=math.pi, Lz=math.pi / 2, Nx=32, Ny=49, Nz=32, dt=1e-3,
                            sub_per_step=10, filt=(1, 50.0, 50.0)),
+    # profiling case: the same x-z planes as the Re 550 workload with 33 wall-normal points
+    # (inputs of one pass 0.35 GB > L2, about 2 GB on the device)
+    "re550_384x33x384": dict(re=550.0, Lx=2 * math.pi, Lz=math.pi, Nx=384, Ny=33, Nz=384, dt=2e-4,
+                             sub_per_step=10, filt=(0, 120.0, 60.0)),
     "re1000_768x385x768": dict(re=1000.0, Lx=2 * math.pi, Lz=math.pi, Nx=768, Ny=385, Nz=768, dt=1e-4,
                                sub_per_step=50, filt=(0, 120.0, 60.0)),
 }
@@ -303,7 +307,7 @@ def run_ours(args, c, name):
     n = s0["v"].size
     h2d = 2 * n * 16 + 2 * c["Ny"] * 8
     d2h = (9 * n + 2 * n) * 16 + 2 * c["Ny"] * 8 + (20 * c["Ny"] + 3) * 8
-    e2e_steps = max(1, min(args.steps, 3))
+    e2e_steps = 0 if args.no_e2e else max(1, min(args.steps, 3))
     barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
@@ -318,7 +322,7 @@ def run_ours(args, c, name):
         t = torch.tensor([e2e_s], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
-    e2e = world * e2e_steps * nsub * pts / e2e_s / 1e6
+    e2e = world * e2e_steps * nsub * pts / e2e_s / 1e6 if e2e_steps else None
 
     # ---- roofline of the dominant kernel (FP64 ALU bound: see the design notes)
     dom = max(prof, key=lambda k: prof[k][0])
@@ -371,6 +375,7 @@ def main():
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
     ap.add_argument("--config", choices=sorted(CONFIGS), default=DEFAULT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     args = ap.parse_args()
     c = CONFIGS[args.config]
     if args.impl == "reference":

@@ -242,6 +242,7 @@ int chan_init_ex(chan_t* out, const chan_opts* o) {
     h->pois = dalloc<double>(h, Ny * 7 * (size_t)h->C);
     h->helm = dalloc<double>(h, 3 * Ny * 11 * (size_t)h->C);
     h->infl = dalloc<double>(h, 3 * 4 * (size_t)h->C);
+    h->meanh = dalloc<double>(h, 3 * (Ny + 1));
     // twiddles in the transform precision
     for (int which = 0; which < 2; ++which) {
       const int L = which ? L3 : L1;

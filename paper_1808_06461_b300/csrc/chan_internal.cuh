@@ -65,6 +65,7 @@ struct chan_s {
   double* helm;            // [3][Ny][11][C]
   double* pois;            // [Ny][7][C]
   double* infl;            // [3][4][C]
+  double* meanh;           // [3][Ny+1]: U_h of each substep and its flux
   void *tw1, *tw3;         // twiddles of L1, L3 in the FFT precision
   // work (device)
   double2* wf;             // Fourier work fields [NWF][Ny][M]

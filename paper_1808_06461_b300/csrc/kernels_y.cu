@@ -376,68 +376,110 @@ __global__ void __launch_bounds__(128) k_poisson(Geo g, YTabs t, const double* _
 }
 
 // ---------------------------------------------------------------------------
-// a8: mean profiles.  One thread: the (0,0) Helmholtz factors (k = 0) of
-// substep s serve (A - b dt nu B) U+ = A[U + dt(g <H> + z <H>prev)] + a dt nu B U.
-// U_1 gets c U_h with U_h = (A - b dt nu B)^-1 A 1 so the trapezoid flux
-// stays Q0; f = c / ((a + b) dt).
+// a8: mean profiles.  The (0,0) Helmholtz factors (k = 0) of substep s serve
+//   (A - b dt nu B) U+ = A[U + dt(g <H> + z <H>prev)] + a dt nu B U,  U+(+-1) = 0.
+// U_1 gets c U_h with U_h = (A - b dt nu B)^-1 A 1 (precomputed per substep)
+// so the trapezoid flux stays Q0; f = c / ((a + b) dt).  One block: the
+// right-hand sides and the flux sums are row-parallel, the two banded
+// sweeps (U_1, U_3) run on two warps.
 // ---------------------------------------------------------------------------
-__global__ void k_mean(Geo g, YTabs t, const double* __restrict__ helm, const double2* __restrict__ H1,
-                       const double2* __restrict__ H3, double* U1, double* U3, double* H1p, double* H3p,
-                       double* scal, int s) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+__global__ void __launch_bounds__(256) k_mean(Geo g, YTabs t, const double* __restrict__ helm,
+                                              const double* __restrict__ meanh, const double2* __restrict__ H1,
+                                              const double2* __restrict__ H3, double* U1, double* U3, double* H1p,
+                                              double* H3p, double* scal, int s) {
   extern __shared__ double sm[];
   const int Ny = g.Ny;
   const size_t M = g.M, C = g.C;
-  double* u1s = sm;
-  double* u3s = sm + Ny;
-  double* uh = sm + 2 * Ny;
+  double* r1 = sm;            // right-hand sides, then the solutions
+  double* r3 = sm + Ny;
+  double* red = sm + 2 * Ny;  // [256]
   const double gm = c_rk3[s][0], zt = c_rk3[s][1], al = c_rk3[s][2], be = c_rk3[s][3];
   const double dt = g.dt, nu = g.nu;
-  const double* H = helm + (size_t)s * Ny * 11 * C;  // class 0: k = 0
-  for (int f = 0; f < 3; ++f) {
-    double* out = f == 0 ? u1s : (f == 1 ? u3s : uh);
-    double hist[3] = {0, 0, 0};
-    for (int i = 0; i < Ny; ++i) {
-      double r = 0.0;
-      if (i > 0 && i < Ny - 1) {
-        for (int d = 0; d < 7; ++d) {
-          int j = i - 3 + d;
-          if (j < 0 || j >= Ny) continue;
-          double a, u;
-          if (f == 2) { a = 1.0; u = 0.0; }
-          else {
-            const double* U = f == 0 ? U1 : U3;
-            const double2* Hf = f == 0 ? H1 : H3;
-            const double* Hp = f == 0 ? H1p : H3p;
-            u = U[j];
-            a = u + dt * (gm * Hf[(size_t)j * M].x + zt * Hp[j]);
-          }
-          r += t.A2[7 * i + d] * a + al * dt * nu * t.B2[7 * i + d] * u;
-        }
+  for (int i = threadIdx.x; i < Ny; i += blockDim.x) {
+    double a1 = 0.0, a3 = 0.0;
+    if (i > 0 && i < Ny - 1) {
+      for (int d = 0; d < 7; ++d) {
+        const int j = i - 3 + d;
+        if (j < 0 || j >= Ny) continue;
+        const double A = t.A2[7 * i + d], B = t.B2[7 * i + d];
+        const double u1 = U1[j], u3 = U3[j];
+        a1 += A * (u1 + dt * (gm * H1[(size_t)j * M].x + zt * H1p[j])) + al * dt * nu * B * u1;
+        a3 += A * (u3 + dt * (gm * H3[(size_t)j * M].x + zt * H3p[j])) + al * dt * nu * B * u3;
       }
+    }
+    r1[i] = a1;
+    r3[i] = a3;
+  }
+  __syncthreads();
+  const double* H = helm + (size_t)s * Ny * 11 * C;  // class 0: k = 0
+  if ((threadIdx.x & 31) == 0 && threadIdx.x < 64) {
+    double* r = threadIdx.x == 0 ? r1 : r3;
+    double h[3] = {0, 0, 0};
+    for (int i = 0; i < Ny; ++i) {
       const double* Hi = H + (size_t)i * 11 * C;
-      r -= Hi[0] * hist[0] + Hi[C] * hist[1] + Hi[2 * C] * hist[2];
-      hist[0] = hist[1]; hist[1] = hist[2]; hist[2] = r;
-      out[i] = r;
+      double x = r[i] - Hi[0] * h[0] - Hi[C] * h[1] - Hi[2 * C] * h[2];
+      h[0] = h[1]; h[1] = h[2]; h[2] = x;
+      r[i] = x;
     }
     double nx[3] = {0, 0, 0};
     for (int i = Ny - 1; i >= 0; --i) {
       const double* Hi = H + (size_t)i * 11 * C;
-      double x = (out[i] - Hi[3 * C] * nx[0] - Hi[4 * C] * nx[1] - Hi[5 * C] * nx[2]) * Hi[6 * C];
+      double x = (r[i] - Hi[3 * C] * nx[0] - Hi[4 * C] * nx[1] - Hi[5 * C] * nx[2]) * Hi[6 * C];
       nx[2] = nx[1]; nx[1] = nx[0]; nx[0] = x;
-      out[i] = x;
+      r[i] = x;
     }
   }
-  double q1 = 0.0, qh = 0.0;
-  for (int i = 0; i < Ny; ++i) { q1 += t.wq[i] * u1s[i]; qh += t.wq[i] * uh[i]; }
-  const double c = (scal[1] - q1) / qh;
-  for (int i = 0; i < Ny; ++i) {
-    U1[i] = u1s[i] + c * uh[i];
-    U3[i] = u3s[i];
+  __syncthreads();
+  // flux of U_1* (fixed-order block reduction)
+  double q = 0.0;
+  for (int i = threadIdx.x; i < Ny; i += blockDim.x) q += t.wq[i] * r1[i];
+  red[threadIdx.x] = q;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  const double* uh = meanh + (size_t)s * (Ny + 1);
+  const double c = (scal[1] - red[0]) / uh[Ny];
+  for (int i = threadIdx.x; i < Ny; i += blockDim.x) {
     H1p[i] = H1[(size_t)i * M].x;
     H3p[i] = H3[(size_t)i * M].x;
+    U1[i] = r1[i] + c * uh[i];
+    U3[i] = r3[i];
   }
-  scal[0] = c / ((al + be) * dt);
+  if (threadIdx.x == 0) scal[0] = c / ((al + be) * dt);
+}
+
+// U_h(s) = (A - b_s dt nu B)^-1 A 1 with zero wall values, and its trapezoid flux.
+__global__ void k_setup_mean(Geo g, YTabs t, const double* __restrict__ helm, double* meanh) {
+  const int s = threadIdx.x;
+  if (s >= 3 || blockIdx.x != 0) return;
+  const int Ny = g.Ny;
+  const size_t C = g.C;
+  const double* H = helm + (size_t)s * Ny * 11 * C;
+  double* out = meanh + (size_t)s * (Ny + 1);
+  double h[3] = {0, 0, 0};
+  for (int i = 0; i < Ny; ++i) {
+    double r = 0.0;
+    if (i > 0 && i < Ny - 1)
+      for (int d = 0; d < 7; ++d) {
+        const int j = i - 3 + d;
+        if (j >= 0 && j < Ny) r += t.A2[7 * i + d];
+      }
+    const double* Hi = H + (size_t)i * 11 * C;
+    r -= Hi[0] * h[0] + Hi[C] * h[1] + Hi[2 * C] * h[2];
+    h[0] = h[1]; h[1] = h[2]; h[2] = r;
+    out[i] = r;
+  }
+  double nx[3] = {0, 0, 0}, q = 0.0;
+  for (int i = Ny - 1; i >= 0; --i) {
+    const double* Hi = H + (size_t)i * 11 * C;
+    double x = (out[i] - Hi[3 * C] * nx[0] - Hi[4 * C] * nx[1] - Hi[5 * C] * nx[2]) * Hi[6 * C];
+    nx[2] = nx[1]; nx[1] = nx[0]; nx[0] = x;
+    out[i] = x;
+  }
+  for (int i = 0; i < Ny; ++i) q += t.wq[i] * out[i];
+  out[Ny] = q;
 }
 
 // ---------------------------------------------------------------------------
@@ -657,6 +699,7 @@ cudaError_t launch_setup_tables(chan_s* h) {
   YTabs t = ytabs(h);
   k_setup_pois<<<(h->C + 127) / 128, 128, 0, h->stream>>>(g, t, h->pois);
   k_setup_helm<<<(3 * h->C + 127) / 128, 128, 0, h->stream>>>(g, t, h->pois, h->helm, h->infl);
+  k_setup_mean<<<1, 32, 0, h->stream>>>(g, t, h->helm, h->meanh);
   return cudaGetLastError();
 }
 
@@ -713,10 +756,11 @@ cudaError_t launch_poisson(chan_s* h, int s) {
 }
 
 cudaError_t launch_mean(chan_s* h, const double2* H1, const double2* H3, int s) {
-  size_t sm = sizeof(double) * 3 * h->Ny;
+  size_t sm = sizeof(double) * (2 * h->Ny + 256);
   cudaError_t e = smem_attr((const void*)k_mean, sm);
   if (e != cudaSuccess) return e;
-  k_mean<<<1, 32, sm, h->stream>>>(geo(h), ytabs(h), h->helm, H1, H3, h->U1, h->U3, h->H1m_p, h->H3m_p, h->scal, s);
+  k_mean<<<1, 256, sm, h->stream>>>(geo(h), ytabs(h), h->helm, h->meanh, H1, H3, h->U1, h->U3, h->H1m_p, h->H3m_p,
+                                    h->scal, s);
   return cudaGetLastError();
 }
 
