@@ -52,24 +52,37 @@ DEFAULT = "re550_384x257x384"
 # coefficient times a complex value = 2 FMA = 4 flops).
 # ---------------------------------------------------------------------------
 def radix_plan(L):
+    """Decimation-in-frequency radix order of the library: 3s, then 4s, then one 2."""
     r, out = L, []
+    while r % 3 == 0:
+        out.append(3); r //= 3
     while r % 4 == 0:
         out.append(4); r //= 4
     while r % 2 == 0:
         out.append(2); r //= 2
-    while r % 3 == 0:
-        out.append(3); r //= 3
     assert r == 1
     return out
 
 
-def fft_flops(L):
+def fft_flops(L, pruned=True):
+    """Flops of one in-place mixed-radix transform of length L.
+
+    Stage with block Ls and span m = Ls/R: L/R butterflies; each costs its DFT
+    (radix 2: 4, radix 4: 16, radix 3: 16 flops) plus (R-1) twiddle complex
+    multiplies (6 flops) unless j = 0 (a 1/m fraction).  With the 3/2 padding
+    the first radix-3 stage of an inverse has a zero middle input (12 flops) and
+    the last one of a forward transform skips its middle output (14 flops):
+    both cost 13.5 on average over the pair, counted per transform as 12 + 14 / 2.
+    """
     dft = {2: 4, 4: 16, 3: 16}
-    p, tot = 1, 0
-    for R in radix_plan(L):
-        nb = L // R
-        tot += nb * dft[R] + nb * (1.0 - 1.0 / p) * (R - 1) * 6
-        p *= R
+    tot, Ls = 0.0, L
+    for s, R in enumerate(radix_plan(L)):
+        m = Ls // R
+        d = dft[R]
+        if pruned and s == 0:
+            d = 13.0
+        tot += (L // R) * (d + (1.0 - 1.0 / m) * (R - 1) * 6)
+        Ls //= R
     return tot
 
 

@@ -34,8 +34,9 @@ int chanh_ygrid(int ny, double grid_re, double eta_w, double* y);
 // Twiddles w_t = exp(-2 pi i t / L), t = 0..L-1, interleaved (re, im).
 void chanh_twiddles(int L, double* tw);
 
-// Radix plan of a 2^a 3^b length: radices 4, 2, 3 in execution order.
-// Returns the number of passes (<= 16) or -1 if L is not 2^a 3^b.
+// Radix plan of a 3^a 2^b length (a >= 1) in decimation-in-frequency order:
+// 3s first, then 4s, then at most one 2.  Returns the number of stages (<= 16)
+// or -1 if L is not of that form.
 int chanh_radix_plan(int L, int* radix);
 
 #ifdef __cplusplus

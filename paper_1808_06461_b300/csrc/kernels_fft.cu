@@ -66,58 +66,150 @@ template <int DIR, typename T2> __device__ __forceinline__ void dft3(T2* v) {
   v[1] = cadd(mm, r);
   v[2] = csub(mm, r);
 }
+// Radix 3 with v[1] = 0: y0 = v0 + v2, y1 = v0 + w^2 v2, y2 = v0 + w v2 (w = exp(DIR 2 pi i / 3)).
+template <int DIR, typename T2> __device__ __forceinline__ void dft3_zmid(T2* v) {
+  typedef typename Scal<T2>::t T;
+  const T h = (T)0.86602540378443864676;  // sqrt(3)/2
+  T2 c = v[2];
+  T2 mm;
+  mm.x = v[0].x - (T)0.5 * c.x;
+  mm.y = v[0].y - (T)0.5 * c.y;
+  T2 r;  // DIR * i * h * (v1 - v2) with v1 = 0
+  if (DIR < 0) { r.x = -h * c.y; r.y = h * c.x; } else { r.x = h * c.y; r.y = -h * c.x; }
+  v[0] = cadd(v[0], c);
+  v[1] = cadd(mm, r);
+  v[2] = csub(mm, r);
+}
+// Radix 3 without the middle output.
+template <int DIR, typename T2> __device__ __forceinline__ void dft3_nomid(T2* v) {
+  typedef typename Scal<T2>::t T;
+  const T h = (T)0.86602540378443864676;
+  T2 s = cadd(v[1], v[2]), d = csub(v[1], v[2]);
+  T2 mm;
+  mm.x = v[0].x - (T)0.5 * s.x;
+  mm.y = v[0].y - (T)0.5 * s.y;
+  T2 r;
+  if (DIR < 0) { r.x = h * d.y; r.y = -h * d.x; } else { r.x = -h * d.y; r.y = h * d.x; }
+  v[0] = cadd(v[0], s);
+  v[2] = csub(mm, r);
+}
 
-// One Stockham pass of radix R over nb transforms of length L (p = product of
-// the radices already applied): butterfly i reads src[i + q L/R], twiddles
-// input q by w^(q k), k = i mod p, and writes dst[(i - k) R + k + q p].
-template <int R, int DIR, typename T2>
-__device__ __forceinline__ void fft_pass(const T2* __restrict__ a, T2* __restrict__ b, int L, int nb, int ld,
-                                         const T2* __restrict__ tw, int p) {
+// In-place mixed-radix FFT stages.  The inverse transforms (spectral ->
+// physical) are decimation in frequency (DIF): natural-order input,
+// digit-reversed output.  The forward transforms are decimation in time
+// (DIT) with the radices in reverse order: digit-reversed input, natural
+// output.  Physical-space data (the z rows of the mixed buffer, the x
+// samples of the x-pass) therefore stay in digit-reversed order, which the
+// pointwise products do not care about.  Every butterfly reads and writes the
+// same R slots, so a stage needs one buffer and one barrier.
+//
+// The DIF plan starts with radix 3 and the DIT plan ends with it: with 3/2
+// zero padding the middle third of a DIF input is zero (the first stage skips
+// those loads and their additions) and the middle third of a DIT output is
+// discarded by the truncation (the last stage does not form it).
+
+// DIF stage of radix R on blocks of size Ls: butterfly j of block b reads
+// x[b Ls + j + r m] (m = Ls/R), forms y_q = sum_r x_r w_R^(DIR r q), scales
+// y_q by w_Ls^(DIR q j) and writes it back to slot q.
+template <int R, int DIR, bool ZMID, typename T2>
+__device__ __forceinline__ void dif_stage(T2* a, int L, int nb, int ld, const T2* __restrict__ tw, int Ls) {
+  const int m = Ls / R;
   const int nbf = L / R;
-  const int tstep = L / (p * R);
+  const int tmul = L / Ls;
   const int total = nb * nbf;
   for (int t = threadIdx.x; t < total; t += blockDim.x) {
     const int bi = t / nbf;
-    const int i = t - bi * nbf;
-    const int k = i % p;
-    const T2* src = a + bi * ld;
-    T2* dst = b + bi * ld;
+    const int u = t - bi * nbf;
+    const int blk = u / m;
+    const int j = u - blk * m;
+    T2* x = a + bi * ld + blk * Ls + j;
     T2 v[R];
 #pragma unroll
-    for (int q = 0; q < R; ++q) {
-      T2 x = src[i + q * nbf];
-      if (q > 0 && k > 0) {
-        T2 w = tw[q * k * tstep];
+    for (int q = 0; q < R; ++q) v[q] = (ZMID && q == 1) ? mk<T2>(0.0, 0.0) : x[q * m];
+    if (R == 4) dft4<DIR>(v);
+    else if (R == 2) dft2<DIR>(v);
+    else if (ZMID) dft3_zmid<DIR>(v);
+    else dft3<DIR>(v);
+    if (j > 0) {
+#pragma unroll
+      for (int q = 1; q < R; ++q) {
+        T2 w = tw[q * j * tmul];
         if (DIR > 0) w.y = -w.y;
-        x = cmul(x, w);
+        v[q] = cmul(v[q], w);
       }
-      v[q] = x;
+    }
+#pragma unroll
+    for (int q = 0; q < R; ++q) x[q * m] = v[q];
+  }
+  __syncthreads();
+}
+
+// DIT stage of radix R on blocks of size Ls: input r of butterfly j is scaled
+// by w_Ls^(DIR r j), then y_q = sum_r x_r w_R^(DIR r q) goes to slot q.  With
+// ZMID the middle output (q = 1) is neither formed nor stored.
+template <int R, int DIR, bool ZMID, typename T2>
+__device__ __forceinline__ void dit_stage(T2* a, int L, int nb, int ld, const T2* __restrict__ tw, int Ls) {
+  const int m = Ls / R;
+  const int nbf = L / R;
+  const int tmul = L / Ls;
+  const int total = nb * nbf;
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    const int bi = t / nbf;
+    const int u = t - bi * nbf;
+    const int blk = u / m;
+    const int j = u - blk * m;
+    T2* x = a + bi * ld + blk * Ls + j;
+    T2 v[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) v[q] = x[q * m];
+    if (j > 0) {
+#pragma unroll
+      for (int q = 1; q < R; ++q) {
+        T2 w = tw[q * j * tmul];
+        if (DIR > 0) w.y = -w.y;
+        v[q] = cmul(v[q], w);
+      }
     }
     if (R == 4) dft4<DIR>(v);
     else if (R == 2) dft2<DIR>(v);
+    else if (ZMID) dft3_nomid<DIR>(v);
     else dft3<DIR>(v);
-    const int base = (i - k) * R + k;
 #pragma unroll
-    for (int q = 0; q < R; ++q) dst[base + q * p] = v[q];
+    for (int q = 0; q < R; ++q)
+      if (!(ZMID && q == 1)) x[q * m] = v[q];
+  }
+  __syncthreads();
+}
+
+// Inverse (DIR = +1) transform of nb sequences: natural in, digit-reversed out.
+// pl.radix holds the DIF order (first radix 3); zmid: middle third of the input is zero.
+template <int DIR, typename T2>
+__device__ void fft_dif(T2* a, int L, int nb, int ld, const T2* __restrict__ tw, const FftPlan& pl, bool zmid) {
+  int Ls = L;
+  for (int s = 0; s < pl.np; ++s) {
+    const int R = pl.radix[s];
+    if (R == 4) dif_stage<4, DIR, false>(a, L, nb, ld, tw, Ls);
+    else if (R == 2) dif_stage<2, DIR, false>(a, L, nb, ld, tw, Ls);
+    else if (s == 0 && zmid) dif_stage<3, DIR, true>(a, L, nb, ld, tw, Ls);
+    else dif_stage<3, DIR, false>(a, L, nb, ld, tw, Ls);
+    Ls /= R;
   }
 }
 
-// Batched Stockham FFT of nb transforms of length L stored at a + b*ld.
-// Passes alternate between the two buffers; the return value holds the
-// result.  tw[t] = exp(-2 pi i t / L); inverse passes use its conjugate.
+// Forward (DIR = -1) transform: digit-reversed in (as fft_dif left it), natural
+// out.  Runs the DIF radices backwards; zmid: the middle third of the output is
+// not needed.
 template <int DIR, typename T2>
-__device__ T2* fft_batch(T2* a, T2* b, int L, int nb, int ld, const T2* __restrict__ tw, const FftPlan& pl) {
-  int p = 1;
-  for (int ps = 0; ps < pl.np; ++ps) {
-    const int R = pl.radix[ps];
-    if (R == 4) fft_pass<4, DIR>(a, b, L, nb, ld, tw, p);
-    else if (R == 2) fft_pass<2, DIR>(a, b, L, nb, ld, tw, p);
-    else fft_pass<3, DIR>(a, b, L, nb, ld, tw, p);
-    __syncthreads();
-    T2* tmp = a; a = b; b = tmp;
-    p *= R;
+__device__ void fft_dit(T2* a, int L, int nb, int ld, const T2* __restrict__ tw, const FftPlan& pl, bool zmid) {
+  int Ls = 1;
+  for (int s = pl.np - 1; s >= 0; --s) {
+    const int R = pl.radix[s];
+    Ls *= R;
+    if (R == 4) dit_stage<4, DIR, false>(a, L, nb, ld, tw, Ls);
+    else if (R == 2) dit_stage<2, DIR, false>(a, L, nb, ld, tw, Ls);
+    else if (s == 0 && zmid) dit_stage<3, DIR, true>(a, L, nb, ld, tw, Ls);
+    else dit_stage<3, DIR, false>(a, L, nb, ld, tw, Ls);
   }
-  return a;
 }
 
 struct ZArgs {
@@ -138,7 +230,6 @@ __global__ void __launch_bounds__(256) k_zinv(ZArgs A, const typename V2<T>::t* 
   typedef typename V2<T>::t T2;
   extern __shared__ __align__(16) unsigned char smraw[];
   T2* a = reinterpret_cast<T2*>(smraw);
-  T2* b = a + A.KB * A.ld;
   const int f = blockIdx.z, y = blockIdx.y, kx0 = blockIdx.x * A.KB;
   const int hz = A.Nz / 2;
   for (int e = threadIdx.x; e < A.KB * A.ld; e += blockDim.x) a[e] = mk<T2>(0.0, 0.0);
@@ -157,11 +248,13 @@ __global__ void __launch_bounds__(256) k_zinv(ZArgs A, const typename V2<T>::t* 
     a[kl * A.ld + pz] = mk<T2>(val.x, val.y);
   }
   __syncthreads();
-  T2* r = fft_batch<+1>(a, b, A.L3, A.KB, A.ld, tw, A.pl);
+  // the middle third of the padded column is zero: pruned first stage
+  fft_dif<+1>(a, A.L3, A.KB, A.ld, tw, A.pl, true);
+  // physical rows leave in digit-reversed z order (slot = position in the column)
   T2* out = reinterpret_cast<T2*>(A.out[f]) + (size_t)y * A.L3 * A.nxh;
   for (int e = threadIdx.x; e < A.L3 * A.KB; e += blockDim.x) {
     const int z = e / A.KB, kl = e - z * A.KB, kx = kx0 + kl;
-    if (kx < A.nxh) out[(size_t)z * A.nxh + kx] = r[kl * A.ld + z];
+    if (kx < A.nxh) out[(size_t)z * A.nxh + kx] = a[kl * A.ld + z];
   }
 }
 
@@ -171,7 +264,6 @@ __global__ void __launch_bounds__(256) k_zfwd(ZArgs A, const typename V2<T>::t* 
   typedef typename V2<T>::t T2;
   extern __shared__ __align__(16) unsigned char smraw[];
   T2* a = reinterpret_cast<T2*>(smraw);
-  T2* b = a + A.KB * A.ld;
   const int f = blockIdx.z, y = blockIdx.y, kx0 = blockIdx.x * A.KB;
   const int hz = A.Nz / 2;
   const T2* in = reinterpret_cast<const T2*>(A.out[f]) + (size_t)y * A.L3 * A.nxh;
@@ -180,7 +272,9 @@ __global__ void __launch_bounds__(256) k_zfwd(ZArgs A, const typename V2<T>::t* 
     a[kl * A.ld + z] = kx < A.nxh ? in[(size_t)z * A.nxh + kx] : mk<T2>(0.0, 0.0);
   }
   __syncthreads();
-  T2* r = fft_batch<-1>(a, b, A.L3, A.KB, A.ld, tw, A.pl);
+  // digit-reversed rows in, natural kz out; the middle third (truncated) is not formed
+  fft_dit<-1>(a, A.L3, A.KB, A.ld, tw, A.pl, true);
+  const T2* r = a;
   double2* out = A.outd[f] + (size_t)y * A.M;
   for (int e = threadIdx.x; e < A.Nz * A.KB; e += blockDim.x) {
     const int jz = e / A.KB, kl = e - jz * A.KB, kx = kx0 + kl;
@@ -214,7 +308,6 @@ __global__ void __launch_bounds__(256) k_xpass(XArgs A, const typename V2<T>::t*
   constexpr int NB = 6;
   extern __shared__ __align__(16) unsigned char smraw[];
   T2* a = reinterpret_cast<T2*>(smraw);
-  T2* b = a + NB * A.ld;
   const int z0 = 2 * blockIdx.x, y = blockIdx.y;
   const int L1 = A.L1, nxh = A.nxh, ld = A.ld;
   for (int e = threadIdx.x; e < NIN * ld; e += blockDim.x) a[e] = mk<T2>(0.0, 0.0);
@@ -236,8 +329,10 @@ __global__ void __launch_bounds__(256) k_xpass(XArgs A, const typename V2<T>::t*
     }
   }
   __syncthreads();
-  T2* r = fft_batch<+1>(a, b, L1, NIN, ld, tw, A.pl);
-  T2* o = (r == a) ? b : a;
+  // kx in [nxh, 2 nxh] is zero padding: pruned first stage; x samples leave digit-reversed
+  fft_dif<+1>(a, L1, NIN, ld, tw, A.pl, true);
+  T2* r = a;
+  T2* o = a;   // products overwrite their own sample slot (all fields share the order)
   for (int x = threadIdx.x; x < L1; x += blockDim.x) {
     T2 q[NIN];
 #pragma unroll
@@ -263,7 +358,9 @@ __global__ void __launch_bounds__(256) k_xpass(XArgs A, const typename V2<T>::t*
     }
   }
   __syncthreads();
-  T2* s = fft_batch<-1>(o, r, L1, NOUT, ld, tw, A.pl);
+  // back to natural kx order; the middle third of the spectrum is discarded, so not formed
+  fft_dit<-1>(a, L1, NOUT, ld, tw, A.pl, true);
+  const T2* s = a;
   const T half = (T)(0.5 * A.scale);
   for (int e = threadIdx.x; e < NOUT * nxh; e += blockDim.x) {
     const int gq = e / nxh, k = e - gq * nxh;
@@ -280,9 +377,10 @@ __global__ void __launch_bounds__(256) k_xpass(XArgs A, const typename V2<T>::t*
 
 template <typename T> size_t esize() { return sizeof(typename V2<T>::t); }
 
+// Columns per z-pass CTA: as many as fit 56 KB of shared memory (4 CTAs per SM), at most 16.
 int pick_kb(int nxh, int L3, size_t es) {
   int kb = 1;
-  while (kb * 2 <= nxh && kb * 2 <= 16 && 2 * (size_t)(kb * 2) * (L3 + 1) * es <= 100 * 1024) kb *= 2;
+  while (kb * 2 <= nxh && kb * 2 <= 16 && (size_t)(kb * 2) * (L3 + 1) * es <= 56 * 1024) kb *= 2;
   return kb;
 }
 
@@ -316,7 +414,7 @@ cudaError_t launch_zinv(chan_s* h, const double2* const* in, const int* apply_G,
   ZArgs A = zargs(h, es);
   for (int f = 0; f < nf; ++f) { A.in[f] = in[f]; A.out[f] = out[f]; A.applyG[f] = apply_G ? apply_G[f] : 0; }
   dim3 grid((h->nxh + A.KB - 1) / A.KB, h->Ny, nf);
-  size_t sm = 2 * (size_t)A.KB * A.ld * es;
+  size_t sm = (size_t)A.KB * A.ld * es;
   if (dbl) k_zinv<double><<<grid, 256, sm, h->stream>>>(A, (const double2*)h->tw3);
   else k_zinv<float><<<grid, 256, sm, h->stream>>>(A, (const float2*)h->tw3);
   return cudaGetLastError();
@@ -328,7 +426,7 @@ cudaError_t launch_zfwd(chan_s* h, void* const* in, double2* const* out, int nf)
   ZArgs A = zargs(h, es);
   for (int f = 0; f < nf; ++f) { A.out[f] = in[f]; A.outd[f] = out[f]; }
   dim3 grid((h->nxh + A.KB - 1) / A.KB, h->Ny, nf);
-  size_t sm = 2 * (size_t)A.KB * A.ld * es;
+  size_t sm = (size_t)A.KB * A.ld * es;
   if (dbl) k_zfwd<double><<<grid, 256, sm, h->stream>>>(A, (const double2*)h->tw3);
   else k_zfwd<float><<<grid, 256, sm, h->stream>>>(A, (const float2*)h->tw3);
   return cudaGetLastError();
@@ -346,7 +444,7 @@ cudaError_t launch_xpass(chan_s* h, int mode, void* const* in, void* const* out)
   A.scale = 1.0 / ((double)h->L1 * (double)h->L3);
   A.pl = h->p1;
   dim3 grid(h->L3 / 2, h->Ny);
-  size_t sm = 2 * 6 * (size_t)A.ld * es;
+  size_t sm = 6 * (size_t)A.ld * es;
   if (dbl) {
     if (mode == 0) k_xpass<double, 0><<<grid, 256, sm, h->stream>>>(A, (const double2*)h->tw1);
     else k_xpass<double, 1><<<grid, 256, sm, h->stream>>>(A, (const double2*)h->tw1);

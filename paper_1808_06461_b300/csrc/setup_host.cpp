@@ -215,11 +215,16 @@ void chanh_twiddles(int L, double* tw) {
   }
 }
 
+// Radix order of the decimation-in-frequency transforms: a radix-3 stage first
+// (it carries the zero middle third of a 3/2-padded spectrum), then the other
+// threes, fours and at most one two.  The decimation-in-time transforms run the
+// same list backwards.
 int chanh_radix_plan(int L, int* radix) {
   int n = 0, r = L;
+  if (r % 3 != 0) return -1;
+  while (r % 3 == 0) { radix[n++] = 3; r /= 3; }
   while (r % 4 == 0) { radix[n++] = 4; r /= 4; }
   while (r % 2 == 0) { radix[n++] = 2; r /= 2; }
-  while (r % 3 == 0) { radix[n++] = 3; r /= 3; }
   if (r != 1 || n > 16) return -1;
   return n;
 }
