@@ -259,20 +259,12 @@ def run_ours(args, c, name):
     torch.cuda.set_device(local)
     import paper_1808_06461_b300 as chan
     import synthetic as SY
-    prec = chan.CHAN_PREC_MIXED if args.precision == "mixed" else chan.CHAN_PREC_FP64
+    precs = {"fp64": chan.CHAN_PREC_FP64, "mixed": chan.CHAN_PREC_MIXED, "f64x": chan.CHAN_PREC_F64X}
     stream = torch.cuda.current_stream()
-    ch = chan.Channel(c["re"], c["Lx"], c["Lz"], c["Nx"], c["Ny"], c["Nz"], c["dt"], precision=prec,
-                      stream=stream.cuda_stream)
-    y = ch.grid()
-    s0 = SY.turbulent_like(y, c["re"], c["Lx"], c["Lz"], c["Nx"], c["Nz"], seed=1 + rank)
     nsub = c["sub_per_step"]
     kind, p1, p3 = c["filt"]
     pts = c["Nx"] * c["Ny"] * c["Nz"]
-
-    def one_step():
-        ch.step(nsub)
-        ch.filter_stresses(kind, p1, p3, want=False)
-        ch.stats()
+    s0 = None
 
     def barrier():
         torch.cuda.synchronize()
@@ -280,32 +272,63 @@ def run_ours(args, c, name):
             dist.barrier()
             torch.cuda.synchronize()
 
-    # ---- device-resident throughput
-    ch.set_state(s0["v"], s0["omega2"], s0["U1"], s0["U3"])
-    for _ in range(args.warmup):
-        one_step()
+    def max_over_ranks(x):
+        if world > 1:
+            t = torch.tensor([x], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            return float(t.item())
+        return x
+
+    def measure(mode, with_clocks):
+        """Warm up from the seeded field, snapshot, then time args.steps steps."""
+        nonlocal s0
+        ch = chan.Channel(c["re"], c["Lx"], c["Lz"], c["Nx"], c["Ny"], c["Nz"], c["dt"], precision=precs[mode],
+                          stream=stream.cuda_stream)
+        if s0 is None:
+            s0 = SY.turbulent_like(ch.grid(), c["re"], c["Lx"], c["Lz"], c["Nx"], c["Nz"], seed=1 + rank)
+
+        def one_step():
+            ch.step(nsub)
+            ch.filter_stresses(kind, p1, p3, want=False)
+            ch.stats()
+
+        ch.set_state(s0["v"], s0["omega2"], s0["U1"], s0["U3"])
+        for _ in range(args.warmup):
+            one_step()
+        snap = ch.get_state()
+        snap["stats"] = ch.stats()[0]
+        barrier()
+        stop, samples = threading.Event(), []
+        th = None
+        if with_clocks:
+            th = threading.Thread(target=clocks_sampler, args=(stop, samples), daemon=True)
+            th.start()
+        ch.profile(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        e0.record(stream)
+        for _ in range(args.steps):
+            one_step()
+        e1.record(stream)
+        barrier()
+        stop.set()
+        if th is not None:
+            th.join(timeout=10)
+        prof = ch.profile_read()
+        ch.profile(False)
+        ms = max_over_ranks(e0.elapsed_time(e1))
+        return ch, snap, prof, ms, samples
+
+    def roofline(prof, peak64):
+        dom = max(prof, key=lambda k: prof[k][0])
+        dms, dn = prof[dom]
+        fl = kernel_flops(dom, c, {})
+        achieved = fl / (dms / dn * 1e-3) / 1e12 if dn else 0.0
+        return dom, achieved, achieved / peak64
+
+    main_mode = args.precision
+    ch, snap_main, prof, ms, samples = measure(main_mode, True)
     peak64 = fp64_peak_tflops(torch)
-    barrier()
-    stop, samples = threading.Event(), []
-    th = threading.Thread(target=clocks_sampler, args=(stop, samples), daemon=True)
-    th.start()
-    ch.profile(True)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    barrier()
-    e0.record(stream)
-    for _ in range(args.steps):
-        one_step()
-    e1.record(stream)
-    barrier()
-    stop.set()
-    th.join(timeout=10)
-    prof = ch.profile_read()
-    ch.profile(False)
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     value = world * args.steps * nsub * pts / (ms * 1e-3) / 1e6
 
     # ---- end to end through the public API with pinned host buffers
@@ -321,43 +344,66 @@ def run_ours(args, c, name):
     h2d = 2 * n * 16 + 2 * c["Ny"] * 8
     d2h = (9 * n + 2 * n) * 16 + 2 * c["Ny"] * 8 + (20 * c["Ny"] + 3) * 8
     e2e_steps = 0 if args.no_e2e else max(1, min(args.steps, 3))
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        ch.set_state(hv, ho, hU1, hU3)
-        ch.step(nsub)
-        ch.filter_stresses(kind, p1, p3, want=True)
-        ch.stats()
-        ch.get_state()
-    barrier()
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = world * e2e_steps * nsub * pts / e2e_s / 1e6 if e2e_steps else None
+    e2e = None
+    if e2e_steps:
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            ch.set_state(hv, ho, hU1, hU3)
+            ch.step(nsub)
+            ch.filter_stresses(kind, p1, p3, want=True)
+            ch.stats()
+            ch.get_state()
+        barrier()
+        e2e = world * e2e_steps * nsub * pts / max_over_ranks(time.perf_counter() - t0) / 1e6
+    ch.close()
 
-    # ---- roofline of the dominant kernel (FP64 ALU bound: see the design notes)
-    dom = max(prof, key=lambda k: prof[k][0])
-    dms, dn = prof[dom]
-    fl = kernel_flops(dom, c, {})
-    achieved = fl / (dms / dn * 1e-3) / 1e12 if dn else 0.0
+    dom, achieved, frac = roofline(prof, peak64)
     launches = int(sum(v[1] for v in prof.values()))
-    kernels = {k: {"ms": round(v[0], 3), "launches": v[1], "share": round(v[0] / max(1e-9, sum(x[0] for x in prof.values())), 4)}
+    tot_ms = max(1e-9, sum(x[0] for x in prof.values()))
+    kernels = {k: {"ms": round(v[0], 3), "launches": v[1], "share": round(v[0] / tot_ms, 4)}
                for k, v in prof.items() if v[1]}
     peaks = measured_peaks()
+
+    # ---- the other precision modes on the same workload, with their error against FP64
+    modes = {}
+    if main_mode == "fp64" and not args.no_modes:
+        st_main = snap_main["stats"]
+
+        def prof_err(a, b):
+            return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+        def rms(stt):
+            return np.sqrt(np.maximum(stt[2:5] - np.array([stt[0] ** 2, 0 * stt[0], stt[1] ** 2]), 0.0))
+
+        for mode in ("mixed", "f64x"):
+            chm, snap, profm, msm, _ = measure(mode, False)
+            chm.close()
+            dm, am, fm = roofline(profm, peak64)
+            sm_ = snap["stats"]
+            modes[mode] = {
+                "value": world * args.steps * nsub * pts / (msm * 1e-3) / 1e6, "ms_per_step": msm / args.steps,
+                "roofline": {"kernel": dm, "achieved": am, "frac": fm, "unit": "TFLOP/s", "bound": "alu"},
+                "err_vs_fp64": {"after_substeps": args.warmup * nsub,
+                                "v_rel_l2": float(np.linalg.norm(snap["v"] - snap_main["v"]) / np.linalg.norm(snap_main["v"])),
+                                "omega2_rel_l2": float(np.linalg.norm(snap["omega2"] - snap_main["omega2"]) /
+                                                       np.linalg.norm(snap_main["omega2"])),
+                                "mean_profile_rel": prof_err(sm_[0], st_main[0]),
+                                "rms_profiles_rel": prof_err(rms(sm_), rms(st_main)),
+                                "tau_rel": prof_err(sm_[14:20], st_main[14:20])},
+                "dtype": "f32 transforms + f64 y-solves" if mode == "mixed" else "f32x2 transforms + f64 y-solves"}
     line = {"metric": "DNS Mpts.substep/s", "value": value, "unit": "Mpts*substep/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if prec == chan.CHAN_PREC_FP64 else "f32+f64",
+            "dtype": {"fp64": "f64", "mixed": "f32+f64", "f64x": "f32x2+f64"}[main_mode],
             "data": "synthetic",
             "config": {"workload": name, "Nx": c["Nx"], "Ny": c["Ny"], "Nz": c["Nz"], "re_tau": c["re"],
                        "dt": c["dt"], "substeps_per_step": nsub, "filter": {"kind": "sharp" if kind == 0 else "box",
                                                                            "p1": p1, "p3": p3},
-                       "precision": args.precision, "l2": "inputs larger than L2 (state %.1f GB)" %
-                       (6 * n * 16 / 1e9), "parallelism": "replicas" if world > 1 else "single"},
+                       "precision": main_mode, "l2": "inputs larger than L2 (state %.1f GB)" % (6 * n * 16 / 1e9),
+                       "parallelism": "replicas" if world > 1 else "single"},
             "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak64,
-                         "unit": "TFLOP/s", "frac": achieved / peak64, "traffic": None,
+                         "unit": "TFLOP/s", "frac": frac, "traffic": None,
                          "peak_source": "FP64 DGEMM measured in this run (cuBLAS, 4096^3)",
                          "hbm_peak_gbs": peaks.get("hbm_gbs")},
             "kernels": kernels,
@@ -365,6 +411,8 @@ def run_ours(args, c, name):
             "e2e": {"value": e2e, "unit": "Mpts*substep/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "steps": e2e_steps},
             "clocks": summarize_clocks(samples)}
+    if modes:
+        line["modes"] = modes
     if rank == 0 and not args.no_cpu_baseline:
         t_sub, sample = oracle_sample_substep_seconds(c)
         line["cpu_baseline"] = {"value": pts / t_sub / 1e6, "unit": "Mpts*substep/s", "cores": cpu_threads(),
@@ -374,7 +422,6 @@ def run_ours(args, c, name):
                                           (sample["planes"], c["Ny"], sample["modes"], c["Nz"] * c["Nx"] // 2)}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    ch.close()
     if world > 1:
         dist.destroy_process_group()
 
@@ -385,7 +432,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--precision", choices=["fp64", "mixed", "f64x"], default="fp64")
+    ap.add_argument("--no-modes", action="store_true", help="skip the mixed / double-float runs")
     ap.add_argument("--config", choices=sorted(CONFIGS), default=DEFAULT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")

@@ -55,6 +55,8 @@ extern "C" {
 
 #define CHAN_PREC_FP64  0     /* every step in FP64                                        */
 #define CHAN_PREC_MIXED 1     /* FFTs and products in FP32; y-solves, mean flow, stats FP64 */
+#define CHAN_PREC_F64X  2     /* FFTs and products in double-float (FP32 pairs, ~2^-47);
+                                 y-solves, mean flow, stats FP64                           */
 
 #define CHAN_NSTAT 20         /* rows of chan_stats' output, see chan_stats                */
 
@@ -67,7 +69,7 @@ typedef struct chan_opts {
   double dt;         /* time step of a full RK3 step (each substep uses dt)          */
   double eta_w;      /* wall Kolmogorov scale of the mesh (default 1.0)              */
   double grid_re;    /* Re_tau the mesh is clustered for (<= 0: re_tau)              */
-  int precision;     /* CHAN_PREC_FP64 or CHAN_PREC_MIXED                            */
+  int precision;     /* CHAN_PREC_FP64, CHAN_PREC_MIXED or CHAN_PREC_F64X            */
   void* stream;      /* cudaStream_t to run on, or NULL for a library-owned stream   */
 } chan_opts;
 

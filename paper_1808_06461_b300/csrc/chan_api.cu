@@ -93,7 +93,7 @@ enum { WF_U1 = 0, WF_U3 = 1, WF_OM1 = 2, WF_OM3 = 3, WF_H1 = 4, WF_H2 = 5, WF_H3
 
 double2* wf(chan_s* h, int k) { return h->wf + (size_t)k * fsize(h); }
 void* mixed(chan_s* h, int k) {
-  const size_t es = h->prec == CHAN_PREC_FP64 ? sizeof(double2) : sizeof(float2);
+  const size_t es = h->prec == CHAN_PREC_MIXED ? sizeof(float2) : sizeof(double2);
   return static_cast<char*>(h->mixed) + (size_t)k * h->Ny * h->L3 * h->nxh * es;
 }
 
@@ -185,12 +185,13 @@ int chan_init_ex(chan_t* out, const chan_opts* o) {
   if (o->Nx < 2 || o->Nx % 2 || !is_2a3b(o->Nx)) return bad(nullptr, "chan_init: Nx must be even and 2^a 3^b");
   if (o->Nz < 4 || o->Nz % 4 || !is_2a3b(o->Nz)) return bad(nullptr, "chan_init: Nz must be a multiple of 4 and 2^a 3^b");
   if (o->Ny < 9 || o->Ny % 2 == 0) return bad(nullptr, "chan_init: Ny must be odd and >= 9");
-  if (o->precision != CHAN_PREC_FP64 && o->precision != CHAN_PREC_MIXED) return bad(nullptr, "chan_init: unknown precision");
+  if (o->precision != CHAN_PREC_FP64 && o->precision != CHAN_PREC_MIXED && o->precision != CHAN_PREC_F64X)
+    return bad(nullptr, "chan_init: unknown precision");
   const int L1 = 3 * o->Nx / 2, L3 = 3 * o->Nz / 2;
-  const size_t es = o->precision == CHAN_PREC_FP64 ? 16 : 8;
+  const size_t es = o->precision == CHAN_PREC_MIXED ? 8 : 16;
   if (2 * 6 * (size_t)(L1 + 1) * es > 227 * 1024 || 2 * (size_t)(L3 + 1) * es > 100 * 1024)
     return bad(nullptr, "chan_init: 3Nx/2 or 3Nz/2 too long for an in-block transform at this precision "
-                        "(FP64: Nx <= 768, mixed: Nx <= 1536)");
+                        "(FP64 and double-float: Nx <= 768, mixed: Nx <= 1536)");
   chan_s* h = new (std::nothrow) chan_s();
   if (!h) return bad(nullptr, "chan_init: out of host memory", CHAN_ENOMEM);
   h->re = o->re_tau; h->Lx = o->Lx; h->Lz = o->Lz; h->dt = o->dt; h->nu = 1.0 / o->re_tau;
@@ -252,6 +253,16 @@ int chan_init_ex(chan_t* out, const chan_opts* o) {
       if (h->prec == CHAN_PREC_FP64) {
         d = dalloc<double2>(h, L);
         CK(cudaMemcpy(d, tw.data(), L * sizeof(double2), cudaMemcpyHostToDevice));
+      } else if (h->prec == CHAN_PREC_F64X) {
+        // double-float twiddles: (hi, lo) per component, hi = nearest float, lo = nearest float of the rest
+        std::vector<float> twd(4 * (size_t)L);
+        for (size_t k = 0; k < 2 * (size_t)L; ++k) {
+          const float hi = (float)tw[k];
+          twd[2 * k] = hi;
+          twd[2 * k + 1] = (float)(tw[k] - (double)hi);
+        }
+        d = dalloc<double2>(h, L);
+        CK(cudaMemcpy(d, twd.data(), L * sizeof(double2), cudaMemcpyHostToDevice));
       } else {
         std::vector<float> twf(2 * (size_t)L);
         for (size_t k = 0; k < twf.size(); ++k) twf[k] = (float)tw[k];

@@ -14,17 +14,78 @@
 
 namespace {
 
+// Double-float real: value = h + l with |l| <= ulp(h)/2 (Dekker 1971).  The
+// error-free sum is Knuth's two-sum, the product uses the FMA to recover the
+// low part of h_a h_b; every operation is an explicit round-to-nearest
+// intrinsic so that the compiler neither contracts nor reassociates it.
+// Relative precision about 2^-47 at FP32 throughput.
+struct dfr {
+  float h, l;
+};
+struct dfc {
+  dfr x, y;
+};
+__device__ __forceinline__ dfr operator+(dfr a, dfr b) {
+  const float s = __fadd_rn(a.h, b.h);
+  const float bb = __fsub_rn(s, a.h);
+  float e = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, bb)), __fsub_rn(b.h, bb));
+  e = __fadd_rn(e, __fadd_rn(a.l, b.l));
+  const float t = __fadd_rn(s, e);
+  return dfr{t, __fsub_rn(e, __fsub_rn(t, s))};
+}
+__device__ __forceinline__ dfr operator-(dfr a) { return dfr{-a.h, -a.l}; }
+__device__ __forceinline__ dfr operator-(dfr a, dfr b) { return a + (-b); }
+__device__ __forceinline__ dfr operator*(dfr a, dfr b) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = __fmaf_rn(a.h, b.h, -p);
+  e = __fmaf_rn(a.h, b.l, e);
+  e = __fmaf_rn(a.l, b.h, e);
+  const float t = __fadd_rn(p, e);
+  return dfr{t, __fsub_rn(e, __fsub_rn(t, p))};
+}
+
 template <typename T> struct V2;
 template <> struct V2<double> { typedef double2 t; };
 template <> struct V2<float> { typedef float2 t; };
+template <> struct V2<dfr> { typedef dfc t; };
 
 template <typename T2> struct Scal;
 template <> struct Scal<double2> { typedef double t; };
 template <> struct Scal<float2> { typedef float t; };
+template <> struct Scal<dfc> { typedef dfr t; };
 
-template <typename T2> __device__ __forceinline__ T2 mk(double x, double y);
-template <> __device__ __forceinline__ double2 mk<double2>(double x, double y) { return make_double2(x, y); }
-template <> __device__ __forceinline__ float2 mk<float2>(double x, double y) { return make_float2((float)x, (float)y); }
+// scalar helpers: conversion from / to double, halving, sqrt(3)/2
+template <typename T> __device__ __forceinline__ T from_d(double x);
+template <> __device__ __forceinline__ double from_d<double>(double x) { return x; }
+template <> __device__ __forceinline__ float from_d<float>(double x) { return (float)x; }
+template <> __device__ __forceinline__ dfr from_d<dfr>(double x) {
+  const float h = __double2float_rn(x);
+  return dfr{h, __double2float_rn(x - (double)h)};
+}
+__device__ __forceinline__ double to_d(double x) { return x; }
+__device__ __forceinline__ double to_d(float x) { return (double)x; }
+__device__ __forceinline__ double to_d(dfr x) { return (double)x.h + (double)x.l; }
+__device__ __forceinline__ double half_of(double x) { return 0.5 * x; }
+__device__ __forceinline__ float half_of(float x) { return 0.5f * x; }
+__device__ __forceinline__ dfr half_of(dfr x) { return dfr{0.5f * x.h, 0.5f * x.l}; }
+template <typename T> __device__ __forceinline__ T sqrt3_2();
+template <> __device__ __forceinline__ double sqrt3_2<double>() { return 0.86602540378443864676; }
+template <> __device__ __forceinline__ float sqrt3_2<float>() { return 0.86602540378443864676f; }
+template <> __device__ __forceinline__ dfr sqrt3_2<dfr>() { return dfr{0x1.bb67aep-1f, 0x1.0b0996p-26f}; }
+
+template <typename T2> __device__ __forceinline__ T2 zero2() {
+  T2 r;
+  memset(&r, 0, sizeof(T2));
+  return r;
+}
+
+template <typename T2> __device__ __forceinline__ T2 mk(double x, double y) {
+  typedef typename Scal<T2>::t T;
+  T2 r;
+  r.x = from_d<T>(x);
+  r.y = from_d<T>(y);
+  return r;
+}
 
 template <typename T2> __device__ __forceinline__ T2 cmul(T2 a, T2 b) {
   T2 r;
@@ -53,12 +114,12 @@ template <int DIR, typename T2> __device__ __forceinline__ void dft4(T2* v) {
 }
 template <int DIR, typename T2> __device__ __forceinline__ void dft3(T2* v) {
   typedef typename Scal<T2>::t T;
-  const T h = (T)0.86602540378443864676;  // sqrt(3)/2
+  const T h = sqrt3_2<T>();
   T2 s = cadd(v[1], v[2]), d = csub(v[1], v[2]);
   T2 y0 = cadd(v[0], s);
   T2 mm;
-  mm.x = v[0].x - (T)0.5 * s.x;
-  mm.y = v[0].y - (T)0.5 * s.y;
+  mm.x = v[0].x - half_of(s.x);
+  mm.y = v[0].y - half_of(s.y);
   // y1 = m + DIR * i * h * d, y2 = m - DIR * i * h * d
   T2 r;
   if (DIR < 0) { r.x = h * d.y; r.y = -h * d.x; } else { r.x = -h * d.y; r.y = h * d.x; }
@@ -69,11 +130,11 @@ template <int DIR, typename T2> __device__ __forceinline__ void dft3(T2* v) {
 // Radix 3 with v[1] = 0: y0 = v0 + v2, y1 = v0 + w^2 v2, y2 = v0 + w v2 (w = exp(DIR 2 pi i / 3)).
 template <int DIR, typename T2> __device__ __forceinline__ void dft3_zmid(T2* v) {
   typedef typename Scal<T2>::t T;
-  const T h = (T)0.86602540378443864676;  // sqrt(3)/2
+  const T h = sqrt3_2<T>();
   T2 c = v[2];
   T2 mm;
-  mm.x = v[0].x - (T)0.5 * c.x;
-  mm.y = v[0].y - (T)0.5 * c.y;
+  mm.x = v[0].x - half_of(c.x);
+  mm.y = v[0].y - half_of(c.y);
   T2 r;  // DIR * i * h * (v1 - v2) with v1 = 0
   if (DIR < 0) { r.x = -h * c.y; r.y = h * c.x; } else { r.x = h * c.y; r.y = -h * c.x; }
   v[0] = cadd(v[0], c);
@@ -83,11 +144,11 @@ template <int DIR, typename T2> __device__ __forceinline__ void dft3_zmid(T2* v)
 // Radix 3 without the middle output.
 template <int DIR, typename T2> __device__ __forceinline__ void dft3_nomid(T2* v) {
   typedef typename Scal<T2>::t T;
-  const T h = (T)0.86602540378443864676;
+  const T h = sqrt3_2<T>();
   T2 s = cadd(v[1], v[2]), d = csub(v[1], v[2]);
   T2 mm;
-  mm.x = v[0].x - (T)0.5 * s.x;
-  mm.y = v[0].y - (T)0.5 * s.y;
+  mm.x = v[0].x - half_of(s.x);
+  mm.y = v[0].y - half_of(s.y);
   T2 r;
   if (DIR < 0) { r.x = h * d.y; r.y = -h * d.x; } else { r.x = -h * d.y; r.y = h * d.x; }
   v[0] = cadd(v[0], s);
@@ -125,7 +186,7 @@ __device__ __forceinline__ void dif_stage(T2* a, int L, int nb, int ld, const T2
     T2* x = a + bi * ld + blk * Ls + j;
     T2 v[R];
 #pragma unroll
-    for (int q = 0; q < R; ++q) v[q] = (ZMID && q == 1) ? mk<T2>(0.0, 0.0) : x[q * m];
+    for (int q = 0; q < R; ++q) v[q] = (ZMID && q == 1) ? zero2<T2>() : x[q * m];
     if (R == 4) dft4<DIR>(v);
     else if (R == 2) dft2<DIR>(v);
     else if (ZMID) dft3_zmid<DIR>(v);
@@ -232,7 +293,7 @@ __global__ void __launch_bounds__(256) k_zinv(ZArgs A, const typename V2<T>::t* 
   T2* a = reinterpret_cast<T2*>(smraw);
   const int f = blockIdx.z, y = blockIdx.y, kx0 = blockIdx.x * A.KB;
   const int hz = A.Nz / 2;
-  for (int e = threadIdx.x; e < A.KB * A.ld; e += blockDim.x) a[e] = mk<T2>(0.0, 0.0);
+  for (int e = threadIdx.x; e < A.KB * A.ld; e += blockDim.x) a[e] = zero2<T2>();
   __syncthreads();
   const double2* in = A.in[f] + (size_t)y * A.M;
   for (int e = threadIdx.x; e < A.Nz * A.KB; e += blockDim.x) {
@@ -269,7 +330,7 @@ __global__ void __launch_bounds__(256) k_zfwd(ZArgs A, const typename V2<T>::t* 
   const T2* in = reinterpret_cast<const T2*>(A.out[f]) + (size_t)y * A.L3 * A.nxh;
   for (int e = threadIdx.x; e < A.L3 * A.KB; e += blockDim.x) {
     const int z = e / A.KB, kl = e - z * A.KB, kx = kx0 + kl;
-    a[kl * A.ld + z] = kx < A.nxh ? in[(size_t)z * A.nxh + kx] : mk<T2>(0.0, 0.0);
+    a[kl * A.ld + z] = kx < A.nxh ? in[(size_t)z * A.nxh + kx] : zero2<T2>();
   }
   __syncthreads();
   // digit-reversed rows in, natural kz out; the middle third (truncated) is not formed
@@ -283,7 +344,7 @@ __global__ void __launch_bounds__(256) k_zfwd(ZArgs A, const typename V2<T>::t* 
     if (jz != hz) {
       const int pz = jz < hz ? jz : jz + (A.L3 - A.Nz);
       T2 x = r[kl * A.ld + pz];
-      val = make_double2((double)x.x, (double)x.y);
+      val = make_double2(to_d(x.x), to_d(x.y));
     }
     out[jz * A.nxh + kx] = val;
   }
@@ -310,7 +371,7 @@ __global__ void __launch_bounds__(256) k_xpass(XArgs A, const typename V2<T>::t*
   T2* a = reinterpret_cast<T2*>(smraw);
   const int z0 = 2 * blockIdx.x, y = blockIdx.y;
   const int L1 = A.L1, nxh = A.nxh, ld = A.ld;
-  for (int e = threadIdx.x; e < NIN * ld; e += blockDim.x) a[e] = mk<T2>(0.0, 0.0);
+  for (int e = threadIdx.x; e < NIN * ld; e += blockDim.x) a[e] = zero2<T2>();
   __syncthreads();
   // pack rows z0 (real part) and z0+1 (imaginary part) with Hermitian extension in kx
   for (int e = threadIdx.x; e < NIN * nxh; e += blockDim.x) {
@@ -319,7 +380,10 @@ __global__ void __launch_bounds__(256) k_xpass(XArgs A, const typename V2<T>::t*
     T2 P = row[k], Q = row[nxh + k];
     T2* dstf = a + f * ld;
     if (k == 0) {
-      dstf[0] = mk<T2>(P.x, Q.x);
+      T2 c0;
+      c0.x = P.x;
+      c0.y = Q.x;
+      dstf[0] = c0;
     } else {
       T2 c1, c2;
       c1.x = P.x - Q.y; c1.y = P.y + Q.x;      // P_k + i Q_k
@@ -361,7 +425,7 @@ __global__ void __launch_bounds__(256) k_xpass(XArgs A, const typename V2<T>::t*
   // back to natural kx order; the middle third of the spectrum is discarded, so not formed
   fft_dit<-1>(a, L1, NOUT, ld, tw, A.pl, true);
   const T2* s = a;
-  const T half = (T)(0.5 * A.scale);
+  const T half = from_d<T>(0.5 * A.scale);
   for (int e = threadIdx.x; e < NOUT * nxh; e += blockDim.x) {
     const int gq = e / nxh, k = e - gq * nxh;
     const T2 c = s[gq * ld + k];
@@ -387,9 +451,10 @@ int pick_kb(int nxh, int L3, size_t es) {
 }  // namespace
 
 cudaError_t fft_configure(chan_s* h) {
-  const void* fns[] = {(const void*)k_zinv<double>, (const void*)k_zinv<float>, (const void*)k_zfwd<double>,
-                       (const void*)k_zfwd<float>, (const void*)k_xpass<double, 0>, (const void*)k_xpass<double, 1>,
-                       (const void*)k_xpass<float, 0>, (const void*)k_xpass<float, 1>};
+  const void* fns[] = {(const void*)k_zinv<double>,     (const void*)k_zinv<float>,      (const void*)k_zinv<dfr>,
+                       (const void*)k_zfwd<double>,     (const void*)k_zfwd<float>,      (const void*)k_zfwd<dfr>,
+                       (const void*)k_xpass<double, 0>, (const void*)k_xpass<double, 1>, (const void*)k_xpass<float, 0>,
+                       (const void*)k_xpass<float, 1>,  (const void*)k_xpass<dfr, 0>,    (const void*)k_xpass<dfr, 1>};
   for (const void* f : fns) {
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     if (e != cudaSuccess) return e;
@@ -408,33 +473,34 @@ static ZArgs zargs(chan_s* h, size_t es) {
   return A;
 }
 
+static size_t fft_esize(const chan_s* h) { return h->prec == CHAN_PREC_MIXED ? sizeof(float2) : sizeof(double2); }
+
 cudaError_t launch_zinv(chan_s* h, const double2* const* in, const int* apply_G, void* const* out, int nf) {
-  const bool dbl = h->prec == CHAN_PREC_FP64;
-  const size_t es = dbl ? sizeof(double2) : sizeof(float2);
+  const size_t es = fft_esize(h);
   ZArgs A = zargs(h, es);
   for (int f = 0; f < nf; ++f) { A.in[f] = in[f]; A.out[f] = out[f]; A.applyG[f] = apply_G ? apply_G[f] : 0; }
   dim3 grid((h->nxh + A.KB - 1) / A.KB, h->Ny, nf);
   size_t sm = (size_t)A.KB * A.ld * es;
-  if (dbl) k_zinv<double><<<grid, 256, sm, h->stream>>>(A, (const double2*)h->tw3);
-  else k_zinv<float><<<grid, 256, sm, h->stream>>>(A, (const float2*)h->tw3);
+  if (h->prec == CHAN_PREC_FP64) k_zinv<double><<<grid, 256, sm, h->stream>>>(A, (const double2*)h->tw3);
+  else if (h->prec == CHAN_PREC_MIXED) k_zinv<float><<<grid, 256, sm, h->stream>>>(A, (const float2*)h->tw3);
+  else k_zinv<dfr><<<grid, 256, sm, h->stream>>>(A, (const dfc*)h->tw3);
   return cudaGetLastError();
 }
 
 cudaError_t launch_zfwd(chan_s* h, void* const* in, double2* const* out, int nf) {
-  const bool dbl = h->prec == CHAN_PREC_FP64;
-  const size_t es = dbl ? sizeof(double2) : sizeof(float2);
+  const size_t es = fft_esize(h);
   ZArgs A = zargs(h, es);
   for (int f = 0; f < nf; ++f) { A.out[f] = in[f]; A.outd[f] = out[f]; }
   dim3 grid((h->nxh + A.KB - 1) / A.KB, h->Ny, nf);
   size_t sm = (size_t)A.KB * A.ld * es;
-  if (dbl) k_zfwd<double><<<grid, 256, sm, h->stream>>>(A, (const double2*)h->tw3);
-  else k_zfwd<float><<<grid, 256, sm, h->stream>>>(A, (const float2*)h->tw3);
+  if (h->prec == CHAN_PREC_FP64) k_zfwd<double><<<grid, 256, sm, h->stream>>>(A, (const double2*)h->tw3);
+  else if (h->prec == CHAN_PREC_MIXED) k_zfwd<float><<<grid, 256, sm, h->stream>>>(A, (const float2*)h->tw3);
+  else k_zfwd<dfr><<<grid, 256, sm, h->stream>>>(A, (const dfc*)h->tw3);
   return cudaGetLastError();
 }
 
 cudaError_t launch_xpass(chan_s* h, int mode, void* const* in, void* const* out) {
-  const bool dbl = h->prec == CHAN_PREC_FP64;
-  const size_t es = dbl ? sizeof(double2) : sizeof(float2);
+  const size_t es = fft_esize(h);
   XArgs A;
   memset(&A, 0, sizeof(A));
   const int nin = mode == 0 ? 6 : 3, nout = mode == 0 ? 3 : 6;
@@ -445,12 +511,15 @@ cudaError_t launch_xpass(chan_s* h, int mode, void* const* in, void* const* out)
   A.pl = h->p1;
   dim3 grid(h->L3 / 2, h->Ny);
   size_t sm = 6 * (size_t)A.ld * es;
-  if (dbl) {
+  if (h->prec == CHAN_PREC_FP64) {
     if (mode == 0) k_xpass<double, 0><<<grid, 256, sm, h->stream>>>(A, (const double2*)h->tw1);
     else k_xpass<double, 1><<<grid, 256, sm, h->stream>>>(A, (const double2*)h->tw1);
-  } else {
+  } else if (h->prec == CHAN_PREC_MIXED) {
     if (mode == 0) k_xpass<float, 0><<<grid, 256, sm, h->stream>>>(A, (const float2*)h->tw1);
     else k_xpass<float, 1><<<grid, 256, sm, h->stream>>>(A, (const float2*)h->tw1);
+  } else {
+    if (mode == 0) k_xpass<dfr, 0><<<grid, 256, sm, h->stream>>>(A, (const dfc*)h->tw1);
+    else k_xpass<dfr, 1><<<grid, 256, sm, h->stream>>>(A, (const dfc*)h->tw1);
   }
   return cudaGetLastError();
 }

@@ -204,6 +204,23 @@ def test_mixed_precision_error(chan, ten_steps):
     assert rel(g["U1"], ref["U1"]) < 1e-7
 
 
+@pytest.mark.parametrize("name", list(CASES))
+def test_double_float_mode_parity(chan, name, ten_steps):
+    """Double-float (FP32-pair) transforms and products, FP64 y-solves: same 1e-10 bar."""
+    st = setup(name)
+    s0, ref = ten_steps[name]
+    ch = make(chan, name, precision=chan.CHAN_PREC_F64X)
+    ch.set_state(s0["v"], s0["omega2"], s0["U1"], s0["U3"])
+    H = ch.nonlinear()
+    Href = O.nonlinear(st, O.initial_state(st, s0["v"], s0["omega2"], s0["U1"], s0["U3"]))
+    for f in range(3):
+        assert rel(H[f], Href[f]) < 1e-11, (f, rel(H[f], Href[f]))
+    ch.step(10)
+    g = ch.get_state()
+    for k in ("v", "omega2", "U1"):
+        assert rel(g[k], ref[k]) < TOL, (k, rel(g[k], ref[k]))
+
+
 def test_step_before_state_is_an_error(chan):
     ch = make(chan, "re180_32x49x32")
     with pytest.raises(chan.ChanError) as e:
