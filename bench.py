@@ -413,6 +413,8 @@ def run_ours(args, c, name):
             "clocks": summarize_clocks(samples)}
     if modes:
         line["modes"] = modes
+    if not args.no_serve:
+        line["serving"] = run_serving(args, rank)
     if rank == 0 and not args.no_cpu_baseline:
         t_sub, sample = oracle_sample_substep_seconds(c)
         line["cpu_baseline"] = {"value": pts / t_sub / 1e6, "unit": "Mpts*substep/s", "cores": cpu_threads(),
@@ -426,6 +428,25 @@ def run_ours(args, c, name):
         dist.destroy_process_group()
 
 
+def run_serving(args, rank):
+    """The serving mix: Poisson arrivals (seeded, mean 50 req/s) of minimal-box runs with
+    Re_tau in {180, 395, 550}, Nx, Nz in {32, 64, 128}, Ny in {49, 97, 129} and 100-2000
+    substeps, served by the continuous-batching loop, FP64 and mixed."""
+    import synthetic as SY
+    from paper_1808_06461_b300.serve import Server, channel_factory, poisson_requests
+
+    def ic(r, y):
+        return SY.perturbed_poiseuille(y, r.re_tau, r.Lx, r.Lz, r.Nx, r.Nz, seed=r.seed, amp=0.1)
+
+    out = {"requests": args.serve_requests, "rate_per_s": 50.0, "seed": 42, "hbm_budget_gb": 64,
+           "max_slots": 16}
+    for prec, tag in ((0, "fp64"), (1, "mixed")):
+        reqs = poisson_requests(args.serve_requests, 50.0, 42 + rank, precision=prec)
+        _, m = Server(64 << 30, max_slots=16, factory=channel_factory(ic)).run(reqs, keep_results=False)
+        out[tag] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in m.items()}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -434,6 +455,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp64", "mixed", "f64x"], default="fp64")
     ap.add_argument("--no-modes", action="store_true", help="skip the mixed / double-float runs")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving-mix run")
+    ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--config", choices=sorted(CONFIGS), default=DEFAULT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")

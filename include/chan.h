@@ -98,6 +98,21 @@ size_t chan_fourier_count(chan_t h);
 /* Bytes of device memory the handle holds. */
 size_t chan_device_bytes(chan_t h);
 
+/*
+ * Device bytes chan_init_ex requests for a box of this size and precision
+ * (including the filter's transfer function); 0 for invalid sizes.  No GPU
+ * needed.  For admission by HBM footprint; the allocator may round up.
+ */
+size_t chan_footprint_bytes(int Nx, int Ny, int Nz, int precision);
+
+/*
+ * Replay whole RK3 steps (three substeps) from a CUDA graph captured on the
+ * first use (enable = 1) instead of launching each kernel; chan_step falls
+ * back to single launches at a step's ragged ends and while tracing is on.
+ * Results are identical either way.  Off by default.
+ */
+int chan_set_graph(chan_t h, int enable);
+
 /* Wall-normal mesh, double[Ny] (Sec. 2.1: spacing ~ local Kolmogorov scale). */
 int chan_get_grid(chan_t h, double* y);
 

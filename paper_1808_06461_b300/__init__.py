@@ -29,7 +29,7 @@ SYMBOLS = ("chan_opts_default", "chan_init", "chan_init_ex", "chan_free", "chan_
            "chan_set_state_device", "chan_get_state", "chan_get_state_device", "chan_step",
            "chan_filter_stresses", "chan_stats", "chan_nonlinear", "chan_sync", "chan_time",
            "chan_substeps", "chan_profile", "chan_profile_read", "chan_kernel_name",
-           "chan_rhs_terms", "chan_rhs_terms_noalloc")
+           "chan_rhs_terms", "chan_rhs_terms_noalloc", "chan_footprint_bytes", "chan_set_graph")
 CHAN_NKERNELS = 11
 
 
@@ -72,6 +72,8 @@ def load_library(path=LIB_PATH):
         "chan_nonlinear": (I, [P, P]),
         "chan_rhs_terms": (I, [P, P]),
         "chan_rhs_terms_noalloc": (I, [P, P, P]),
+        "chan_footprint_bytes": (S, [I, I, I, I]),
+        "chan_set_graph": (I, [P, I]),
         "chan_sync": (I, [P]),
         "chan_time": (D, [P]),
         "chan_substeps": (ctypes.c_longlong, [P]),
@@ -147,6 +149,9 @@ class Channel:
 
     def substeps(self):
         return int(_lib.chan_substeps(self.h))
+
+    def set_graph(self, enable=True):
+        _check(self.h, _lib.chan_set_graph(self.h, 1 if enable else 0))
 
     # ---- tracing
     def profile(self, enable=True):
@@ -249,6 +254,11 @@ def chan_free(ch):
 
 def chan_sync(ch):
     ch.sync()
+
+
+def footprint_bytes(Nx, Ny, Nz, precision=CHAN_PREC_FP64):
+    """Device bytes a channel of this size would allocate (no GPU needed)."""
+    return int(_lib.chan_footprint_bytes(int(Nx), int(Ny), int(Nz), int(precision)))
 
 
 def library():

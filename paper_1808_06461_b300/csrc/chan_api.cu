@@ -153,6 +153,58 @@ void ensure_filter_buffers(chan_s* h) {
   h->G = dalloc<double>(h, h->M);
 }
 
+// Device bytes chan_init_ex requests for a box (the filter transfer function,
+// allocated on the first filter call, included).  Mirrors the allocations below.
+size_t footprint(int Nx, int Ny, int Nz, int prec) {
+  const size_t nxh = Nx / 2, M = (size_t)Nz * nxh, C = (size_t)(Nz / 2) * nxh, n = (size_t)Ny * M;
+  const size_t L1 = 3 * (size_t)Nx / 2, L3 = 3 * (size_t)Nz / 2;
+  const size_t es = prec == CHAN_PREC_MIXED ? sizeof(float2) : sizeof(double2);
+  size_t b = 0;
+  b += 6 * n * sizeof(double2) + 4 * Ny * sizeof(double) + 2 * sizeof(double);            // state
+  b += 5 * 7 * (size_t)Ny * sizeof(double) + 3 * (size_t)Ny * sizeof(double);              // y tables
+  b += (nxh + Nz) * sizeof(double);                                                          // wavenumbers
+  b += ((size_t)Ny * 7 * C + 3 * (size_t)Ny * 11 * C + 12 * C + 3 * ((size_t)Ny + 1)) * sizeof(double);
+  b += (L1 + L3) * (prec == CHAN_PREC_MIXED ? sizeof(float2) : sizeof(double2));             // twiddles
+  b += (size_t)(NWF + 9) * n * sizeof(double2);                                              // work fields
+  b += 12 * (size_t)Ny * L3 * nxh * es;                                                      // mixed fields
+  b += 2 * n * sizeof(double2);                                                              // sweep scratch
+  b += (CHAN_NSTAT * (size_t)Ny + 2) * sizeof(double);                                       // statistics
+  b += M * sizeof(double);                                                                   // filter G
+  return b;
+}
+
+// Capture one RK3 step (substeps 0, 1, 2) into a graph; the handle's
+// counters are left untouched.
+void capture_step_graph(chan_s* h) {
+  const long long nsub0 = h->nsub;
+  const double t0 = h->t;
+  long long before[KID_COUNT];
+  for (int k = 0; k < KID_COUNT; ++k) before[k] = h->launches[k];
+  const bool prof = h->prof;
+  h->prof = false;
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeRelaxed));
+  try {
+    for (int k = 0; k < 3; ++k) run_substep(h);
+  } catch (Fail f) {
+    cudaStreamEndCapture(h->stream, &g);
+    if (g) cudaGraphDestroy(g);
+    h->prof = prof;
+    throw;
+  }
+  CK(cudaStreamEndCapture(h->stream, &g));
+  cudaError_t e = cudaGraphInstantiate(&h->gexec, g, 0);
+  cudaGraphDestroy(g);
+  CK(e);
+  for (int k = 0; k < KID_COUNT; ++k) {
+    h->graph_launches[k] = h->launches[k] - before[k];
+    h->launches[k] = before[k];
+  }
+  h->nsub = nsub0;
+  h->t = t0;
+  h->prof = prof;
+}
+
 }  // namespace
 
 // The filter outputs (3 ubar + 6 tau fields) live behind the work slots.
@@ -297,6 +349,7 @@ int chan_init_ex(chan_t* out, const chan_opts* o) {
 void chan_free(chan_t h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
   for (ProfRec& r : h->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (void* p : h->allocs) cudaFree(p);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -373,7 +426,19 @@ int chan_step(chan_t h, int nsub) {
   if (nsub < 0) return bad(h, "chan_step: nsub < 0");
   if (!h->have_state) return bad(h, "chan_step: no state set", CHAN_ESTATE);
   try {
-    for (int k = 0; k < nsub; ++k) run_substep(h);
+    int k = 0;
+    const bool graph = h->use_graph && !h->prof;
+    // substeps up to the next RK3 step boundary, then whole steps from the graph
+    while (k < nsub && (!graph || h->nsub % 3 != 0 || nsub - k < 3)) { run_substep(h); ++k; }
+    while (graph && nsub - k >= 3) {
+      if (!h->gexec) capture_step_graph(h);
+      CK(cudaGraphLaunch(h->gexec, h->stream));
+      for (int q = 0; q < KID_COUNT; ++q) h->launches[q] += h->graph_launches[q];
+      for (int s = 0; s < 3; ++s) h->t += chan_rk3_weight(s) * h->dt;
+      h->nsub += 3;
+      k += 3;
+    }
+    while (k < nsub) { run_substep(h); ++k; }
   } catch (Fail f) {
     return f.code;
   }
@@ -517,6 +582,17 @@ int chan_profile_read(chan_t h, double* ms, long long* launches) {
   if (launches)
     for (int k = 0; k < KID_COUNT; ++k) launches[k] = h->launches[k];
   return CHAN_OK;
+}
+
+int chan_set_graph(chan_t h, int enable) {
+  if (!h) return bad(nullptr, "chan_set_graph: NULL handle");
+  h->use_graph = enable != 0;
+  return CHAN_OK;
+}
+
+size_t chan_footprint_bytes(int Nx, int Ny, int Nz, int precision) {
+  if (Nx < 2 || Nx % 2 || Nz < 4 || Nz % 4 || Ny < 9 || Ny % 2 == 0) return 0;
+  return footprint(Nx, Ny, Nz, precision);
 }
 
 const char* chan_kernel_name(int k) { return (k >= 0 && k < KID_COUNT) ? kKernelNames[k] : nullptr; }

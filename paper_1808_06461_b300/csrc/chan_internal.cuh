@@ -83,6 +83,10 @@ struct chan_s {
   std::string err;
   FftPlan p1, p3;
   std::vector<void*> allocs;
+  // CUDA graph of one full RK3 step (three substeps), captured on first use
+  bool use_graph;
+  cudaGraphExec_t gexec;
+  long long graph_launches[KID_COUNT];   // kernels one replay runs, per kernel id
   // tracing
   bool prof;
   long long launches[KID_COUNT];
