@@ -86,6 +86,17 @@ def fft_flops(L, pruned=True):
     return tot
 
 
+# DRAM bytes per wall-normal plane of each kernel launch, from ncu on the 384 x 33 x 384
+# profiling case (profiles/*_re550_384x33x384.md: dram__bytes_read.sum + dram__bytes_write.sum
+# divided by 33); valid for Nx = Nz = 384 only and only while the kernels are as captured.
+NCU_BYTES_PER_PLANE = {("k_xpass", "fp64"): (350.834688e6 + 130.674432e6) / 33,
+                       ("k_xpass", "f64x"): (350.442752e6 + 128.765184e6) / 33,
+                       ("k_helm", "fp64"): (373.894656e6 + 193.170944e6) / 33,
+                       ("k_zinv", "fp64"): (233.095936e6 + 298.214912e6) / 33}
+NCU_PIPE = {("k_xpass", "fp64"): ("fp64", 0.8593), ("k_xpass", "f64x"): ("issue", 0.7508),
+            ("k_helm", "fp64"): ("fp64", 0.8079), ("k_zinv", "fp64"): ("fp64", 0.8530)}
+
+
 # per mode-point flops of the wall-normal kernels (read off their sweeps)
 Y_FLOPS = {"k_pre": 140, "k_nonlin": 70, "k_helm": 192, "k_poisson": 132, "k_derive": 140}
 
@@ -359,6 +370,9 @@ def run_ours(args, c, name):
     ch.close()
 
     dom, achieved, frac = roofline(prof, peak64)
+    key = (dom, "fp64" if dom in ("k_helm", "k_pre", "k_poisson", "k_nonlin", "k_mean") else main_mode)
+    traffic = (NCU_BYTES_PER_PLANE[key] * c["Ny"]
+               if key in NCU_BYTES_PER_PLANE and c["Nx"] == 384 and c["Nz"] == 384 else None)
     launches = int(sum(v[1] for v in prof.values()))
     tot_ms = max(1e-9, sum(x[0] for x in prof.values()))
     kernels = {k: {"ms": round(v[0], 3), "launches": v[1], "share": round(v[0] / tot_ms, 4)}
@@ -403,7 +417,9 @@ def run_ours(args, c, name):
                        "precision": main_mode, "l2": "inputs larger than L2 (state %.1f GB)" % (6 * n * 16 / 1e9),
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak64,
-                         "unit": "TFLOP/s", "frac": frac, "traffic": None,
+                         "unit": "TFLOP/s", "frac": frac, "traffic": traffic,
+                         "traffic_source": "ncu dram bytes per plane on 384x33x384, scaled to Ny planes",
+                         "pipe_busy_ncu": NCU_PIPE.get(key),
                          "peak_source": "FP64 DGEMM measured in this run (cuBLAS, 4096^3)",
                          "hbm_peak_gbs": peaks.get("hbm_gbs")},
             "kernels": kernels,

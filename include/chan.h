@@ -155,6 +155,14 @@ int chan_step(chan_t h, int nsub);
 int chan_filter_stresses(chan_t h, int kind, double p1, double p3, double* ubar, double* tau);
 
 /*
+ * Filtered enstrophy filt(omega_i omega_i) = G P(omega_i omega_i) of the
+ * current state, the tenth variable of the paper's database (Sec. 3.1);
+ * kind and (p1, p3) as for chan_filter_stresses.  ens receives one field,
+ * spectral layout, host.  Does not advance time; synchronises.
+ */
+int chan_filtered_enstrophy(chan_t h, int kind, double p1, double p3, double* ens);
+
+/*
  * Plane statistics of the current state (Sec. 3.3), double[CHAN_NSTAT][Ny]:
  * rows 0-1 U1, U3; rows 2-7 <u_i u_j> (11,22,33,12,13,23, Parseval over
  * all stored modes, means included); rows 8-13 <ubar_i ubar_j> and rows
@@ -181,7 +189,7 @@ int chan_nonlinear(chan_t h, double* H);
  * since the last reset (launches are counted even when timing is off).
  * chan_kernel_name(k) names kernel k (NULL when out of range).
  */
-#define CHAN_NKERNELS 11
+#define CHAN_NKERNELS 12
 int chan_profile(chan_t h, int enable);
 int chan_profile_read(chan_t h, double* ms, long long* launches);
 const char* chan_kernel_name(int k);

@@ -480,6 +480,15 @@ def filter_stresses(st, S, kind, p1, p3):
     return np.stack(ub), np.stack(tau)
 
 
+def filtered_enstrophy(st, S, kind, p1, p3):
+    """filt(omega_i omega_i) = G . P(omega_i omega_i), the tenth database variable (Sec. 3.1)."""
+    G = filter_transfer(st, kind, p1, p3)
+    u1, v, u3, du1, dv, du3 = velocities(st, S)
+    om1, om2, om3 = vorticity(st, S, u1, v, u3, du1, du3)
+    p = [to_physical(st, F) for F in (om1, om2, om3)]
+    return G * to_fourier(st, p[0] ** 2 + p[1] ** 2 + p[2] ** 2)
+
+
 # --------------------------------------------------------------------------
 # Statistics (Sec. 3.3) and invariants
 # --------------------------------------------------------------------------

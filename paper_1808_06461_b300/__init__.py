@@ -29,8 +29,9 @@ SYMBOLS = ("chan_opts_default", "chan_init", "chan_init_ex", "chan_free", "chan_
            "chan_set_state_device", "chan_get_state", "chan_get_state_device", "chan_step",
            "chan_filter_stresses", "chan_stats", "chan_nonlinear", "chan_sync", "chan_time",
            "chan_substeps", "chan_profile", "chan_profile_read", "chan_kernel_name",
-           "chan_rhs_terms", "chan_rhs_terms_noalloc", "chan_footprint_bytes", "chan_set_graph")
-CHAN_NKERNELS = 11
+           "chan_rhs_terms", "chan_rhs_terms_noalloc", "chan_footprint_bytes", "chan_set_graph",
+           "chan_filtered_enstrophy")
+CHAN_NKERNELS = 12
 
 
 class chan_opts(ctypes.Structure):
@@ -74,6 +75,7 @@ def load_library(path=LIB_PATH):
         "chan_rhs_terms_noalloc": (I, [P, P, P]),
         "chan_footprint_bytes": (S, [I, I, I, I]),
         "chan_set_graph": (I, [P, I]),
+        "chan_filtered_enstrophy": (I, [P, I, D, D, P]),
         "chan_sync": (I, [P]),
         "chan_time": (D, [P]),
         "chan_substeps": (ctypes.c_longlong, [P]),
@@ -211,6 +213,12 @@ class Channel:
         tau = np.empty((6,) + self.shape, dtype=np.complex128) if want else None
         _check(self.h, _lib.chan_filter_stresses(self.h, int(kind), float(p1), float(p3), _ptr(ub), _ptr(tau)))
         return ub, tau
+
+    def filtered_enstrophy(self, kind, p1, p3):
+        """filt(omega_i omega_i), shape (Ny, Nz, Nx/2)."""
+        ens = np.empty(self.shape, dtype=np.complex128)
+        _check(self.h, _lib.chan_filtered_enstrophy(self.h, int(kind), float(p1), float(p3), _ptr(ens)))
+        return ens
 
     def stats(self):
         out = np.empty((CHAN_NSTAT, self.Ny))

@@ -64,8 +64,9 @@ __global__ void k_flux(const double* U1, const double* wq, int Ny, double* scal)
 
 size_t fsize(const chan_s* h) { return (size_t)h->Ny * h->M; }
 
-const char* const kKernelNames[KID_COUNT] = {"k_pre", "k_zinv", "k_xpass", "k_zfwd", "k_nonlin", "k_helm",
-                                             "k_poisson", "k_mean", "k_filter_out", "k_stats", "k_derive"};
+const char* const kKernelNames[KID_COUNT] = {"k_pre",     "k_zinv",       "k_xpass", "k_zfwd",
+                                             "k_nonlin",  "k_helm",       "k_poisson", "k_mean",
+                                             "k_filter_out", "k_stats",   "k_derive", "k_apply_G"};
 
 // Launch bracket: counts the launch and, when tracing, records an event pair.
 struct Traced {
@@ -151,6 +152,31 @@ void run_substep(chan_s* h) {
 void ensure_filter_buffers(chan_s* h) {
   if (h->G) return;
   h->G = dalloc<double>(h, h->M);
+}
+
+// Filter transfer function on the stored modes (Sec. 3.1; kz Nyquist row zero) into h->G.
+void set_filter(chan_s* h, int kind, double p1, double p3) {
+  ensure_filter_buffers(h);
+  if (h->g_kind == kind && h->g_p1 == p1 && h->g_p3 == p3) return;   // already on the device
+  std::vector<double> G(h->M);
+  for (int jz = 0; jz < h->Nz; ++jz)
+    for (int kx = 0; kx < h->nxh; ++kx) {
+      const double k1 = 2.0 * M_PI / h->Lx * kx;
+      const double k3 = 2.0 * M_PI / h->Lz * (jz < h->Nz / 2 ? jz : jz - h->Nz);
+      double g;
+      if (kind == CHAN_FILTER_SHARP) {
+        g = (std::fabs(k1) < M_PI * h->re / p1 && std::fabs(k3) < M_PI * h->re / p3) ? 1.0 : 0.0;
+      } else {
+        const double a = 0.5 * k1 * p1 / h->re, b = 0.5 * k3 * p3 / h->re;
+        g = (a == 0.0 ? 1.0 : std::sin(a) / a) * (b == 0.0 ? 1.0 : std::sin(b) / b);
+      }
+      G[(size_t)jz * h->nxh + kx] = (jz == h->Nz / 2) ? 0.0 : g;
+    }
+  CK(cudaMemcpyAsync(h->G, G.data(), h->M * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));   // the host vector dies here
+  h->g_kind = kind;
+  h->g_p1 = p1;
+  h->g_p3 = p3;
 }
 
 // Device bytes chan_init_ex requests for a box (the filter transfer function,
@@ -255,6 +281,7 @@ int chan_init_ex(chan_t* out, const chan_opts* o) {
   h->have_state = h->have_filter = false;
   h->nsub = 0; h->t = 0.0; h->dev_bytes = 0;
   h->G = nullptr;
+  h->g_kind = -1;
   int rc = CHAN_OK;
   chanh_tables tb;
   std::memset(&tb, 0, sizeof(tb));
@@ -481,23 +508,7 @@ int chan_filter_stresses(chan_t h, int kind, double p1, double p3, double* ubar,
   if (!(p1 > 0) || !(p3 > 0)) return bad(h, "chan_filter_stresses: widths must be positive");
   if (!h->have_state) return bad(h, "chan_filter_stresses: no state set", CHAN_ESTATE);
   try {
-    ensure_filter_buffers(h);
-    // transfer function on the stored modes (Nyquist row zero)
-    std::vector<double> G(h->M);
-    for (int jz = 0; jz < h->Nz; ++jz)
-      for (int kx = 0; kx < h->nxh; ++kx) {
-        const double k1 = 2.0 * M_PI / h->Lx * kx;
-        const double k3 = 2.0 * M_PI / h->Lz * (jz < h->Nz / 2 ? jz : jz - h->Nz);
-        double g;
-        if (kind == CHAN_FILTER_SHARP) {
-          g = (std::fabs(k1) < M_PI * h->re / p1 && std::fabs(k3) < M_PI * h->re / p3) ? 1.0 : 0.0;
-        } else {
-          const double a = 0.5 * k1 * p1 / h->re, b = 0.5 * k3 * p3 / h->re;
-          g = (a == 0.0 ? 1.0 : std::sin(a) / a) * (b == 0.0 ? 1.0 : std::sin(b) / b);
-        }
-        G[(size_t)jz * h->nxh + kx] = (jz == h->Nz / 2) ? 0.0 : g;
-      }
-    CK(cudaMemcpyAsync(h->G, G.data(), h->M * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    set_filter(h, kind, p1, p3);
     run_pre(h);
     const double2* in[6] = {wf(h, WF_U1), h->v, wf(h, WF_U3), wf(h, WF_U1), h->v, wf(h, WF_U3)};
     const int applyG[6] = {0, 0, 0, 1, 1, 1};
@@ -518,6 +529,29 @@ int chan_filter_stresses(chan_t h, int kind, double p1, double p3, double* ubar,
     if (tau) CK(cudaMemcpyAsync(tau, filt(h, 3), 6 * n * sizeof(double2), cudaMemcpyDeviceToHost, h->stream));
     if (ubar || tau) CK(cudaStreamSynchronize(h->stream));
     h->have_filter = true;
+  } catch (Fail f) {
+    return f.code;
+  }
+  return CHAN_OK;
+}
+
+int chan_filtered_enstrophy(chan_t h, int kind, double p1, double p3, double* ens) {
+  if (!h || !ens) return bad(h, "chan_filtered_enstrophy: NULL argument");
+  if (kind != CHAN_FILTER_SHARP && kind != CHAN_FILTER_BOX) return bad(h, "chan_filtered_enstrophy: unknown kind");
+  if (!(p1 > 0) || !(p3 > 0)) return bad(h, "chan_filtered_enstrophy: widths must be positive");
+  if (!h->have_state) return bad(h, "chan_filtered_enstrophy: no state set", CHAN_ESTATE);
+  try {
+    set_filter(h, kind, p1, p3);
+    run_pre(h);
+    const double2* in[3] = {wf(h, WF_OM1), h->om, wf(h, WF_OM3)};
+    void* mx[3] = {mixed(h, 0), mixed(h, 1), mixed(h, 2)};
+    { Traced t(h, KID_ZINV); CK(launch_zinv(h, in, nullptr, mx, 3)); }
+    { Traced t(h, KID_XPASS); CK(launch_xpass(h, 2, mx, mx)); }
+    double2* fo[1] = {wf(h, 4)};
+    { Traced t(h, KID_ZFWD); CK(launch_zfwd(h, mx, fo, 1)); }
+    { Traced t(h, KID_APPLY_G); CK(launch_apply_G(h, wf(h, 4), wf(h, 5))); }
+    CK(cudaMemcpyAsync(ens, wf(h, 5), fsize(h) * sizeof(double2), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
   } catch (Fail f) {
     return f.code;
   }

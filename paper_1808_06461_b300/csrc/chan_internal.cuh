@@ -39,7 +39,7 @@ struct FftPlan {
 };
 
 enum { KID_PRE = 0, KID_ZINV, KID_XPASS, KID_ZFWD, KID_NONLIN, KID_HELM, KID_POISSON, KID_MEAN,
-       KID_FILTER_OUT, KID_STATS, KID_DERIVE, KID_COUNT };
+       KID_FILTER_OUT, KID_STATS, KID_DERIVE, KID_APPLY_G, KID_COUNT };
 
 struct ProfRec {
   int k;
@@ -74,6 +74,8 @@ struct chan_s {
   int nmix;
   double2* scr;            // wall-normal sweep scratch [2][Ny][M]
   double* G;               // filter transfer [M]
+  int g_kind;              // filter whose transfer function G holds (-1: none)
+  double g_p1, g_p3;
   double* stat;            // [CHAN_NSTAT][Ny] + [2] (utau, ubulk)
   // bookkeeping
   bool have_state, have_filter;
@@ -108,6 +110,7 @@ cudaError_t launch_poisson(chan_s* h, int s);
 cudaError_t launch_mean(chan_s* h, const double2* H1, const double2* H3, int s);
 cudaError_t launch_filter_out(chan_s* h, const double2* const* u, const double2* const* puu,
                               const double2* const* pbb, double2* ubar, double2* tau);
+cudaError_t launch_apply_G(chan_s* h, const double2* in, double2* out);
 cudaError_t launch_stats(chan_s* h, const double2* u1, const double2* u3, const double2* ubar,
                          const double2* tau, int with_filter);
 

@@ -361,11 +361,12 @@ struct XArgs {
 // x-pass on the physical z-rows (z0, z0+1) of plane y.  MODE 0: inputs
 // (u1, u2, u3, w1, w2, w3) -> H = u x omega (3 outputs).  MODE 1: inputs
 // (u1, u2, u3) -> the six products u_i u_j (11, 22, 33, 12, 13, 23).
+// MODE 2: inputs (w1, w2, w3) -> w_i w_i (1 output).
 template <typename T, int MODE>
 __global__ void __launch_bounds__(256) k_xpass(XArgs A, const typename V2<T>::t* __restrict__ tw) {
   typedef typename V2<T>::t T2;
   constexpr int NIN = MODE == 0 ? 6 : 3;
-  constexpr int NOUT = MODE == 0 ? 3 : 6;
+  constexpr int NOUT = MODE == 0 ? 3 : (MODE == 1 ? 6 : 1);
   constexpr int NB = 6;
   extern __shared__ __align__(16) unsigned char smraw[];
   T2* a = reinterpret_cast<T2*>(smraw);
@@ -410,6 +411,11 @@ __global__ void __launch_bounds__(256) k_xpass(XArgs A, const typename V2<T>::t*
       o[0 * ld + x] = h1;
       o[1 * ld + x] = h2;
       o[2 * ld + x] = h3;
+    } else if (MODE == 2) {
+      T2 w;
+      w.x = q[0].x * q[0].x + q[1].x * q[1].x + q[2].x * q[2].x;
+      w.y = q[0].y * q[0].y + q[1].y * q[1].y + q[2].y * q[2].y;
+      o[x] = w;
     } else {
       const int pi[6] = {0, 1, 2, 0, 0, 1}, pj[6] = {0, 1, 2, 1, 2, 2};
 #pragma unroll
@@ -454,7 +460,8 @@ cudaError_t fft_configure(chan_s* h) {
   const void* fns[] = {(const void*)k_zinv<double>,     (const void*)k_zinv<float>,      (const void*)k_zinv<dfr>,
                        (const void*)k_zfwd<double>,     (const void*)k_zfwd<float>,      (const void*)k_zfwd<dfr>,
                        (const void*)k_xpass<double, 0>, (const void*)k_xpass<double, 1>, (const void*)k_xpass<float, 0>,
-                       (const void*)k_xpass<float, 1>,  (const void*)k_xpass<dfr, 0>,    (const void*)k_xpass<dfr, 1>};
+                       (const void*)k_xpass<float, 1>,  (const void*)k_xpass<dfr, 0>,    (const void*)k_xpass<dfr, 1>,
+                       (const void*)k_xpass<double, 2>, (const void*)k_xpass<float, 2>,  (const void*)k_xpass<dfr, 2>};
   for (const void* f : fns) {
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     if (e != cudaSuccess) return e;
@@ -503,7 +510,7 @@ cudaError_t launch_xpass(chan_s* h, int mode, void* const* in, void* const* out)
   const size_t es = fft_esize(h);
   XArgs A;
   memset(&A, 0, sizeof(A));
-  const int nin = mode == 0 ? 6 : 3, nout = mode == 0 ? 3 : 6;
+  const int nin = mode == 0 ? 6 : 3, nout = mode == 0 ? 3 : (mode == 1 ? 6 : 1);
   for (int f = 0; f < nin; ++f) A.in[f] = in[f];
   for (int f = 0; f < nout; ++f) A.out[f] = out[f];
   A.nxh = h->nxh; A.L1 = h->L1; A.L3 = h->L3; A.ld = h->L1 + 1;
@@ -512,14 +519,20 @@ cudaError_t launch_xpass(chan_s* h, int mode, void* const* in, void* const* out)
   dim3 grid(h->L3 / 2, h->Ny);
   size_t sm = 6 * (size_t)A.ld * es;
   if (h->prec == CHAN_PREC_FP64) {
-    if (mode == 0) k_xpass<double, 0><<<grid, 256, sm, h->stream>>>(A, (const double2*)h->tw1);
-    else k_xpass<double, 1><<<grid, 256, sm, h->stream>>>(A, (const double2*)h->tw1);
+    const double2* tw = (const double2*)h->tw1;
+    if (mode == 0) k_xpass<double, 0><<<grid, 256, sm, h->stream>>>(A, tw);
+    else if (mode == 1) k_xpass<double, 1><<<grid, 256, sm, h->stream>>>(A, tw);
+    else k_xpass<double, 2><<<grid, 256, sm, h->stream>>>(A, tw);
   } else if (h->prec == CHAN_PREC_MIXED) {
-    if (mode == 0) k_xpass<float, 0><<<grid, 256, sm, h->stream>>>(A, (const float2*)h->tw1);
-    else k_xpass<float, 1><<<grid, 256, sm, h->stream>>>(A, (const float2*)h->tw1);
+    const float2* tw = (const float2*)h->tw1;
+    if (mode == 0) k_xpass<float, 0><<<grid, 256, sm, h->stream>>>(A, tw);
+    else if (mode == 1) k_xpass<float, 1><<<grid, 256, sm, h->stream>>>(A, tw);
+    else k_xpass<float, 2><<<grid, 256, sm, h->stream>>>(A, tw);
   } else {
-    if (mode == 0) k_xpass<dfr, 0><<<grid, 256, sm, h->stream>>>(A, (const dfc*)h->tw1);
-    else k_xpass<dfr, 1><<<grid, 256, sm, h->stream>>>(A, (const dfc*)h->tw1);
+    const dfc* tw = (const dfc*)h->tw1;
+    if (mode == 0) k_xpass<dfr, 0><<<grid, 256, sm, h->stream>>>(A, tw);
+    else if (mode == 1) k_xpass<dfr, 1><<<grid, 256, sm, h->stream>>>(A, tw);
+    else k_xpass<dfr, 2><<<grid, 256, sm, h->stream>>>(A, tw);
   }
   return cudaGetLastError();
 }

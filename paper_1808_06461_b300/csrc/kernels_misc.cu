@@ -32,6 +32,15 @@ __global__ void k_filter_out(FiltArgs A) {
   }
 }
 
+__global__ void k_apply_G(const double2* __restrict__ in, const double* __restrict__ G, double2* out, size_t n,
+                          int M) {
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const double g = G[e % M];
+  const double2 x = in[e];
+  out[e] = make_double2(g * x.x, g * x.y);
+}
+
 struct StatArgs {
   const double2* u[3];
   const double2* ub[3];
@@ -106,6 +115,12 @@ cudaError_t launch_filter_out(chan_s* h, const double2* const* u, const double2*
   A.n = (size_t)h->Ny * h->M;
   A.M = h->M;
   k_filter_out<<<(unsigned)((A.n + 255) / 256), 256, 0, h->stream>>>(A);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_apply_G(chan_s* h, const double2* in, double2* out) {
+  const size_t n = (size_t)h->Ny * h->M;
+  k_apply_G<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(in, h->G, out, n, h->M);
   return cudaGetLastError();
 }
 

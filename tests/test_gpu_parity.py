@@ -140,6 +140,18 @@ def test_filter_and_stats_parity(chan, kind, p, ten_steps):
     assert np.abs(out[2:8] - out[8:14] - out[14:20]).max() < 1e-12 * scale
 
 
+@pytest.mark.parametrize("kind,p", [(0, (120.0, 60.0)), (1, (50.0, 50.0))])
+def test_filtered_enstrophy_parity(chan, kind, p, ten_steps):
+    name = "re180_32x49x32"
+    st = setup(name)
+    s0, ref = ten_steps[name]
+    ch = make(chan, name)
+    ch.set_state(s0["v"], s0["omega2"], s0["U1"], s0["U3"])
+    ch.step(10)
+    ens = ch.filtered_enstrophy(kind, *p)
+    assert rel(ens, O.filtered_enstrophy(st, ref, kind, *p)) < TOL
+
+
 def test_poiseuille_steady_gpu(chan):
     name = "re180_32x49x32"
     s0 = ic(name, amp=0.0)

@@ -328,3 +328,17 @@ def test_second_order_identity(c1, c1_run, kind, p):
     pu = O.to_physical(c1, u1)
     assert np.abs(O.to_fourier(c1, pu * pu)[:, 0, 0].real - out[2]).max() < 1e-13 * scale
     assert utau > 0 and ubulk > 0
+
+
+def test_filtered_enstrophy_mean_is_parseval(c1, c1_run):
+    """The (0,0) mode of filt(omega_i omega_i) (G(0) = 1) equals the Parseval plane mean of |omega|^2."""
+    _, S = c1_run
+    ens = O.filtered_enstrophy(c1, S, O.BOX, 50, 50)
+    u1, v, u3, du1, dv, du3 = O.velocities(c1, S)
+    om1 = du3 - 1j * c1.K3 * v
+    om3 = 1j * c1.K1 * v - du1
+    par = sum(O.channel.plane_mean_product(c1, F, F) for F in (om1, S["omega2"], om3))
+    assert np.abs(ens[:, 0, 0].real - par).max() < 1e-12 * np.abs(par).max()
+    G = O.filter_transfer(c1, O.SHARP, 120, 60)
+    ens_s = O.filtered_enstrophy(c1, S, O.SHARP, 120, 60)
+    assert np.abs(ens_s[:, ~(G > 0)]).max() == 0.0     # the sharp filter removes the cut modes exactly
