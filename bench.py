@@ -457,10 +457,60 @@ def run_serving(args, rank):
     out = {"requests": args.serve_requests, "rate_per_s": 50.0, "seed": 42, "hbm_budget_gb": 64,
            "max_slots": 16}
     for prec, tag in ((0, "fp64"), (1, "mixed")):
-        reqs = poisson_requests(args.serve_requests, 50.0, 42 + rank, precision=prec)
-        _, m = Server(64 << 30, max_slots=16, factory=channel_factory(ic)).run(reqs, keep_results=False)
-        out[tag] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in m.items()}
+        for packed in (False, True):
+            reqs = poisson_requests(args.serve_requests, 50.0, 42 + rank, precision=prec)
+            _, m = Server(64 << 30, max_slots=16, factory=channel_factory(ic), packed=packed).run(
+                reqs, keep_results=False)
+            out[tag + ("_packed" if packed else "_streams")] = {
+                k: (round(v, 4) if isinstance(v, float) else v) for k, v in m.items()}
     return out
+
+
+def run_precision_study(args, c, name):
+    """FP64, mixed and double-float runs of ``--precision-study`` substeps from the same seeded
+    field; errors of the plane statistics (mean, rms, tau_ij after the filter) against FP64."""
+    import torch
+    import paper_1808_06461_b300 as chan
+    import synthetic as SY
+    kind, p1, p3 = c["filt"]
+    res, times = {}, {}
+    s0 = None
+    for tag, prec in (("fp64", chan.CHAN_PREC_FP64), ("mixed", chan.CHAN_PREC_MIXED), ("f64x", chan.CHAN_PREC_F64X)):
+        ch = chan.Channel(c["re"], c["Lx"], c["Lz"], c["Nx"], c["Ny"], c["Nz"], c["dt"], precision=prec,
+                          stream=torch.cuda.current_stream().cuda_stream)
+        if s0 is None:
+            s0 = SY.turbulent_like(ch.grid(), c["re"], c["Lx"], c["Lz"], c["Nx"], c["Nz"], seed=1)
+        ch.set_state(s0["v"], s0["omega2"], s0["U1"], s0["U3"])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ch.step(args.precision_study)
+        ch.sync()
+        times[tag] = time.perf_counter() - t0
+        ch.filter_stresses(kind, p1, p3, want=False)
+        st, utau, ub, f = ch.stats()
+        g = ch.get_state()
+        res[tag] = dict(stats=st, v=g["v"], om=g["omega2"], utau=utau)
+        ch.close()
+    ref = res["fp64"]["stats"]
+
+    def rel_prof(a, b):
+        return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+    def rms(stt):
+        return np.sqrt(np.maximum(stt[2:5] - np.array([stt[0] ** 2, 0 * stt[0], stt[1] ** 2]), 0.0))
+
+    out = {"workload": name, "substeps": args.precision_study, "filter": c["filt"], "seconds": times,
+           "mpts_substep_per_s": {k: c["Nx"] * c["Ny"] * c["Nz"] * args.precision_study / v / 1e6 for k, v in times.items()}}
+    for tag in ("mixed", "f64x"):
+        st = res[tag]["stats"]
+        out[tag + "_vs_fp64"] = {
+            "mean_profile_rel": rel_prof(st[0], ref[0]),
+            "rms_profiles_rel": rel_prof(rms(st), rms(ref)),
+            "tau_profiles_rel": rel_prof(st[14:20], ref[14:20]),
+            "uu_profiles_rel": rel_prof(st[2:8], ref[2:8]),
+            "v_rel_l2": float(np.linalg.norm(res[tag]["v"] - res["fp64"]["v"]) / np.linalg.norm(res["fp64"]["v"])),
+            "utau_rel": abs(res[tag]["utau"] - res["fp64"]["utau"]) / res["fp64"]["utau"]}
+    print(json.dumps(out), flush=True)
 
 
 def main():
@@ -473,12 +523,16 @@ def main():
     ap.add_argument("--no-modes", action="store_true", help="skip the mixed / double-float runs")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-mix run")
     ap.add_argument("--serve-requests", type=int, default=24)
+    ap.add_argument("--precision-study", type=int, default=0,
+                    help="run FP64 / mixed / double-float for this many substeps and report profile errors")
     ap.add_argument("--config", choices=sorted(CONFIGS), default=DEFAULT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     args = ap.parse_args()
     c = CONFIGS[args.config]
-    if args.impl == "reference":
+    if args.precision_study:
+        run_precision_study(args, c, args.config)
+    elif args.impl == "reference":
         run_reference(args, c, args.config)
     else:
         run_ours(args, c, args.config)
