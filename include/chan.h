@@ -106,6 +106,18 @@ size_t chan_device_bytes(chan_t h);
 size_t chan_footprint_bytes(int Nx, int Ny, int Nz, int precision);
 
 /*
+ * Autotuner (no paper counterpart): times the z-pass with 1, 2, 4, 8 and 16
+ * columns per CTA and the x-pass with 128, 256 and 512 threads per CTA on
+ * the current state, keeps the fastest, and caches the choice for every
+ * later handle of the same (Nx, Ny, Nz, precision) in the process.  The
+ * choices only regroup identical per-column arithmetic, so results are
+ * bitwise unchanged.  Needs a state; overwrites only scratch; synchronises.
+ * chan_tuned_shape reports the shapes in use.
+ */
+int chan_autotune(chan_t h);
+int chan_tuned_shape(chan_t h, int* kb_z, int* xthreads);
+
+/*
  * Replay whole RK3 steps (three substeps) from a CUDA graph captured on the
  * first use (enable = 1) instead of launching each kernel; chan_step falls
  * back to single launches at a step's ragged ends and while tracing is on.
@@ -224,6 +236,27 @@ int chan_rhs_terms(chan_t h, double* N);
  * calls whose work overlaps on the GPU race on it.
  */
 int chan_rhs_terms_noalloc(chan_t h, const void* H, void* N);
+
+/*
+ * Packed stepping of several independent channels (the serving mode; the
+ * paper has no counterpart).  A batch holds n >= 1 handles of one precision
+ * on one device, each with its state set; they may differ in every size and
+ * be at different RK3 phases.  chan_batch_step advances every run by nsub
+ * substeps with one launch per kernel covering all runs (at most 8 runs per
+ * launch; more runs take more launches), on the batch's stream (the given
+ * stream, or a stream of its own when NULL).  It first makes the batch stream
+ * wait for each run's stream and afterwards makes each run's stream wait for
+ * the batch, so per-run calls stay ordered.  Whole RK3 steps are replayed from
+ * a CUDA graph captured on first use when all runs sit at a step boundary.
+ * Each run's result is bitwise the one chan_step gives.  The handles must
+ * outlive the batch and must not be stepped elsewhere while a batch step
+ * is in flight.
+ */
+typedef struct chan_batch_s* chan_batch_t;
+int chan_batch_create(chan_batch_t* out, chan_t* runs, int n, void* stream);
+int chan_batch_step(chan_batch_t b, int nsub);
+const char* chan_batch_last_error(chan_batch_t b);
+void chan_batch_free(chan_batch_t b);
 
 /* Wait for the handle's stream. */
 int chan_sync(chan_t h);

@@ -30,7 +30,8 @@ SYMBOLS = ("chan_opts_default", "chan_init", "chan_init_ex", "chan_free", "chan_
            "chan_filter_stresses", "chan_stats", "chan_nonlinear", "chan_sync", "chan_time",
            "chan_substeps", "chan_profile", "chan_profile_read", "chan_kernel_name",
            "chan_rhs_terms", "chan_rhs_terms_noalloc", "chan_footprint_bytes", "chan_set_graph",
-           "chan_filtered_enstrophy")
+           "chan_filtered_enstrophy", "chan_batch_create", "chan_batch_step", "chan_batch_last_error",
+           "chan_batch_free", "chan_autotune", "chan_tuned_shape")
 CHAN_NKERNELS = 12
 
 
@@ -76,6 +77,12 @@ def load_library(path=LIB_PATH):
         "chan_footprint_bytes": (S, [I, I, I, I]),
         "chan_set_graph": (I, [P, I]),
         "chan_filtered_enstrophy": (I, [P, I, D, D, P]),
+        "chan_batch_create": (I, [ctypes.POINTER(P), ctypes.POINTER(P), I, P]),
+        "chan_batch_step": (I, [P, I]),
+        "chan_batch_last_error": (ctypes.c_char_p, [P]),
+        "chan_batch_free": (None, [P]),
+        "chan_autotune": (I, [P]),
+        "chan_tuned_shape": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I)]),
         "chan_sync": (I, [P]),
         "chan_time": (D, [P]),
         "chan_substeps": (ctypes.c_longlong, [P]),
@@ -152,6 +159,13 @@ class Channel:
     def substeps(self):
         return int(_lib.chan_substeps(self.h))
 
+    def autotune(self):
+        """Pick z-pass columns per CTA and x-pass threads for this shape (results unchanged)."""
+        _check(self.h, _lib.chan_autotune(self.h))
+        kb, nt = ctypes.c_int(), ctypes.c_int()
+        _check(self.h, _lib.chan_tuned_shape(self.h, ctypes.byref(kb), ctypes.byref(nt)))
+        return kb.value, nt.value
+
     def set_graph(self, enable=True):
         _check(self.h, _lib.chan_set_graph(self.h, 1 if enable else 0))
 
@@ -225,6 +239,35 @@ class Channel:
         ut, ub, f = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
         _check(self.h, _lib.chan_stats(self.h, _ptr(out), ctypes.byref(ut), ctypes.byref(ub), ctypes.byref(f)))
         return out, ut.value, ub.value, f.value
+
+
+class ChannelBatch:
+    """Packed stepping of several Channels of one precision (one launch per kernel for all)."""
+
+    def __init__(self, channels, stream=None):
+        self.channels = list(channels)
+        arr = (ctypes.c_void_p * len(self.channels))(*[c.h.value for c in self.channels])
+        b = ctypes.c_void_p()
+        rc = _lib.chan_batch_create(ctypes.byref(b), arr, len(self.channels), stream)
+        if rc != CHAN_OK:
+            raise ChanError(rc, _lib.chan_batch_last_error(None).decode())
+        self.b = b
+
+    def step(self, nsub):
+        rc = _lib.chan_batch_step(self.b, int(nsub))
+        if rc != CHAN_OK:
+            raise ChanError(rc, _lib.chan_batch_last_error(self.b).decode())
+
+    def close(self):
+        if getattr(self, "b", None):
+            _lib.chan_batch_free(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # Module-level functions with the C names, for callers that prefer them.

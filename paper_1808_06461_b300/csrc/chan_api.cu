@@ -3,8 +3,11 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
+#include <tuple>
 
 #include "chan_internal.cuh"
 
@@ -229,6 +232,61 @@ void capture_step_graph(chan_s* h) {
   h->nsub = nsub0;
   h->t = t0;
   h->prof = prof;
+}
+
+BatchWork batch_work(chan_s* h) {
+  BatchWork w;
+  w.u1 = wf(h, WF_U1); w.u3 = wf(h, WF_U3); w.om1 = wf(h, WF_OM1); w.om3 = wf(h, WF_OM3);
+  w.H1 = wf(h, WF_H1); w.H2 = wf(h, WF_H2); w.H3 = wf(h, WF_H3); w.Nchi = wf(h, WF_NCHI); w.Nom = wf(h, WF_NOM);
+  for (int f = 0; f < 6; ++f) w.mixed[f] = mixed(h, f);
+  return w;
+}
+
+}  // namespace
+
+struct chan_batch_s {
+  std::vector<chan_s*> runs;
+  cudaStream_t stream;
+  bool own_stream;
+  std::vector<cudaEvent_t> ev;   // one per run (join) + one (fork)
+  cudaGraphExec_t gexec;
+  std::string err;
+};
+
+namespace {
+
+#define BK(call)                                                                        \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess) {                                                            \
+      b->err = std::string(#call) + ": " + cudaGetErrorString(e_);                     \
+      throw Fail{CHAN_ECUDA};                                                           \
+    }                                                                                   \
+  } while (0)
+
+// One substep of every run of the batch, in packed launches of up to
+// CHAN_MAXBATCH runs each (all runs are at their own RK3 phase).
+void batch_substep(chan_batch_s* b) {
+  const int n = (int)b->runs.size();
+  for (int r0 = 0; r0 < n; r0 += CHAN_MAXBATCH) {
+    const int m = n - r0 < CHAN_MAXBATCH ? n - r0 : CHAN_MAXBATCH;
+    chan_s* const* hs = b->runs.data() + r0;
+    BatchWork w[CHAN_MAXBATCH];
+    for (int r = 0; r < m; ++r) w[r] = batch_work(hs[r]);
+    BK(launch_pre_batch(hs, m, w, b->stream));
+    BK(launch_zinv_batch(hs, m, w, b->stream));
+    BK(launch_xpass_batch(hs, m, w, b->stream));
+    BK(launch_zfwd_batch(hs, m, w, b->stream));
+    BK(launch_nonlin_batch(hs, m, w, b->stream));
+    BK(launch_helm_batch(hs, m, w, b->stream));
+    BK(launch_poisson_batch(hs, m, w, b->stream));
+    BK(launch_mean_batch(hs, m, w, b->stream));
+  }
+  for (chan_s* h : b->runs) {
+    h->t += chan_rk3_weight((int)(h->nsub % 3)) * h->dt;
+    h->nsub += 1;
+    h->have_filter = false;
+  }
 }
 
 }  // namespace
@@ -618,6 +676,84 @@ int chan_profile_read(chan_t h, double* ms, long long* launches) {
   return CHAN_OK;
 }
 
+// Launch shapes found by chan_autotune, per (Nx, Ny, Nz, precision), shared by the process.
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int, int, int, int>, std::pair<int, int>> g_tune;
+
+int chan_autotune(chan_t h) {
+  if (!h) return bad(nullptr, "chan_autotune: NULL handle");
+  if (!h->have_state) return bad(h, "chan_autotune: no state set", CHAN_ESTATE);
+  const auto key = std::make_tuple(h->Nx, h->Ny, h->Nz, h->prec);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      h->kb_z = it->second.first;
+      h->xthreads = it->second.second;
+      return CHAN_OK;
+    }
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  try {
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    const size_t es = h->prec == CHAN_PREC_MIXED ? sizeof(float2) : sizeof(double2);
+    run_pre(h);
+    const double2* in[6] = {wf(h, WF_U1), h->v, wf(h, WF_U3), wf(h, WF_OM1), h->om, wf(h, WF_OM3)};
+    void* mx[6] = {mixed(h, 0), mixed(h, 1), mixed(h, 2), mixed(h, 3), mixed(h, 4), mixed(h, 5)};
+    auto timed = [&](auto fn) {
+      float best = 1e30f;
+      for (int rep = 0; rep < 3; ++rep) {
+        CK(cudaEventRecord(e0, h->stream));
+        fn();
+        CK(cudaEventRecord(e1, h->stream));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        best = ms < best ? ms : best;
+      }
+      return best;
+    };
+    int best_kb = pick_kb(h->nxh, h->L3, es), best_nt = 256;
+    float best_t = 1e30f;
+    for (int kb = 1; kb <= 16 && kb <= h->nxh; kb *= 2) {
+      if ((size_t)kb * (h->L3 + 1) * es > 110 * 1024) break;
+      h->kb_z = kb;
+      float t = timed([&] { CK(launch_zinv(h, in, nullptr, mx, 6)); });
+      if (t < best_t) { best_t = t; best_kb = kb; }
+    }
+    h->kb_z = best_kb;
+    CK(launch_zinv(h, in, nullptr, mx, 6));   // fresh inputs for the x-pass timings
+    best_t = 1e30f;
+    for (int nt : {128, 256, 512}) {
+      h->xthreads = nt;
+      float t = timed([&] { CK(launch_xpass(h, 0, mx, mx)); CK(launch_zinv(h, in, nullptr, mx, 6)); });
+      if (t < best_t) { best_t = t; best_nt = nt; }
+    }
+    h->xthreads = best_nt;
+    CK(cudaStreamSynchronize(h->stream));
+  } catch (Fail f) {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    h->kb_z = 0;
+    h->xthreads = 0;
+    return f.code;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[key] = std::make_pair(h->kb_z, h->xthreads);
+  return CHAN_OK;
+}
+
+int chan_tuned_shape(chan_t h, int* kb_z, int* xthreads) {
+  if (!h) return bad(nullptr, "chan_tuned_shape: NULL handle");
+  const size_t es = h->prec == CHAN_PREC_MIXED ? sizeof(float2) : sizeof(double2);
+  if (kb_z) *kb_z = h->kb_z > 0 ? h->kb_z : pick_kb(h->nxh, h->L3, es);
+  if (xthreads) *xthreads = h->xthreads > 0 ? h->xthreads : 256;
+  return CHAN_OK;
+}
+
 int chan_set_graph(chan_t h, int enable) {
   if (!h) return bad(nullptr, "chan_set_graph: NULL handle");
   h->use_graph = enable != 0;
@@ -630,6 +766,104 @@ size_t chan_footprint_bytes(int Nx, int Ny, int Nz, int precision) {
 }
 
 const char* chan_kernel_name(int k) { return (k >= 0 && k < KID_COUNT) ? kKernelNames[k] : nullptr; }
+
+int chan_batch_create(chan_batch_t* out, chan_t* runs, int n, void* stream) {
+  if (!out) return bad(nullptr, "chan_batch_create: out is NULL");
+  *out = nullptr;
+  if (!runs || n < 1) return bad(nullptr, "chan_batch_create: no runs");
+  for (int r = 0; r < n; ++r) {
+    if (!runs[r]) return bad(nullptr, "chan_batch_create: NULL run");
+    if (!runs[r]->have_state) return bad(nullptr, "chan_batch_create: a run has no state", CHAN_ESTATE);
+    if (runs[r]->prec != runs[0]->prec || runs[r]->device != runs[0]->device)
+      return bad(nullptr, "chan_batch_create: runs differ in precision or device");
+    for (int q = 0; q < r; ++q)
+      if (runs[q] == runs[r]) return bad(nullptr, "chan_batch_create: a run appears twice");
+  }
+  chan_batch_s* b = new (std::nothrow) chan_batch_s();
+  if (!b) return bad(nullptr, "chan_batch_create: out of host memory", CHAN_ENOMEM);
+  b->runs.assign(runs, runs + n);
+  b->gexec = nullptr;
+  if (stream) { b->stream = (cudaStream_t)stream; b->own_stream = false; }
+  else if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    delete b;
+    return bad(nullptr, "chan_batch_create: cudaStreamCreate failed", CHAN_ECUDA);
+  } else {
+    b->own_stream = true;
+  }
+  b->ev.resize(n + 1, nullptr);
+  for (int r = 0; r <= n; ++r)
+    if (cudaEventCreateWithFlags(&b->ev[r], cudaEventDisableTiming) != cudaSuccess) {
+      chan_batch_free(b);
+      return bad(nullptr, "chan_batch_create: cudaEventCreate failed", CHAN_ECUDA);
+    }
+  *out = b;
+  return CHAN_OK;
+}
+
+int chan_batch_step(chan_batch_t b, int nsub) {
+  if (!b) return bad(nullptr, "chan_batch_step: NULL batch");
+  if (nsub < 0) { b->err = "chan_batch_step: nsub < 0"; return CHAN_EINVAL; }
+  const int n = (int)b->runs.size();
+  try {
+    for (int r = 0; r < n; ++r) {   // join: the batch stream waits for each run's stream
+      BK(cudaEventRecord(b->ev[r], b->runs[r]->stream));
+      BK(cudaStreamWaitEvent(b->stream, b->ev[r], 0));
+    }
+    int k = 0;
+    auto aligned = [&]() {
+      for (chan_s* h : b->runs)
+        if (h->nsub % 3 != 0) return false;
+      return true;
+    };
+    while (k < nsub && (!aligned() || nsub - k < 3)) { batch_substep(b); ++k; }
+    while (nsub - k >= 3) {
+      if (!b->gexec) {   // capture one packed RK3 step; counters restored afterwards
+        std::vector<long long> ns(n);
+        std::vector<double> ts(n);
+        for (int r = 0; r < n; ++r) { ns[r] = b->runs[r]->nsub; ts[r] = b->runs[r]->t; }
+        cudaGraph_t g = nullptr;
+        BK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeRelaxed));
+        try {
+          for (int q = 0; q < 3; ++q) batch_substep(b);
+        } catch (Fail) {
+          cudaStreamEndCapture(b->stream, &g);
+          if (g) cudaGraphDestroy(g);
+          throw;
+        }
+        BK(cudaStreamEndCapture(b->stream, &g));
+        cudaError_t e = cudaGraphInstantiate(&b->gexec, g, 0);
+        cudaGraphDestroy(g);
+        BK(e);
+        for (int r = 0; r < n; ++r) { b->runs[r]->nsub = ns[r]; b->runs[r]->t = ts[r]; }
+      }
+      BK(cudaGraphLaunch(b->gexec, b->stream));
+      for (chan_s* h : b->runs) {
+        for (int q = 0; q < 3; ++q) h->t += chan_rk3_weight(q) * h->dt;
+        h->nsub += 3;
+        h->have_filter = false;
+      }
+      k += 3;
+    }
+    while (k < nsub) { batch_substep(b); ++k; }
+    BK(cudaEventRecord(b->ev[n], b->stream));   // fork: each run's stream waits for the batch
+    for (int r = 0; r < n; ++r) BK(cudaStreamWaitEvent(b->runs[r]->stream, b->ev[n], 0));
+  } catch (Fail f) {
+    return f.code;
+  }
+  return CHAN_OK;
+}
+
+const char* chan_batch_last_error(chan_batch_t b) { return b ? b->err.c_str() : g_init_err.c_str(); }
+
+void chan_batch_free(chan_batch_t b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  for (cudaEvent_t e : b->ev)
+    if (e) cudaEventDestroy(e);
+  if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
 
 double chan_time(chan_t h) { return h ? h->t : 0.0; }
 long long chan_substeps(chan_t h) { return h ? h->nsub : 0; }

@@ -14,6 +14,7 @@
 // Wavenumber classes (shared LU factors): c = |kz| * nxh + kx, |kz| < Nz/2.
 
 #define CHAN_MAXFIELDS 12
+#define CHAN_MAXBATCH 8   // runs per packed launch
 
 struct YTabs {            // mode-independent wall-normal tables (device)
   const double* A2;       // [Ny][7]
@@ -85,6 +86,9 @@ struct chan_s {
   std::string err;
   FftPlan p1, p3;
   std::vector<void*> allocs;
+  // launch shapes (0: default), set by chan_autotune
+  int kb_z;                // columns per z-pass CTA
+  int xthreads;            // threads per x-pass CTA
   // CUDA graph of one full RK3 step (three substeps), captured on first use
   bool use_graph;
   cudaGraphExec_t gexec;
@@ -94,6 +98,12 @@ struct chan_s {
   long long launches[KID_COUNT];
   std::vector<ProfRec> recs;     // event pairs recorded since the last reset
   size_t nrec;                   // pairs in use
+};
+
+// Work-field pointers of one run in a packed substep.
+struct BatchWork {
+  double2 *u1, *u3, *om1, *om3, *H1, *H2, *H3, *Nchi, *Nom;
+  void* mixed[6];
 };
 
 // Kernel launchers (return cudaGetLastError()).
@@ -114,8 +124,20 @@ cudaError_t launch_apply_G(chan_s* h, const double2* in, double2* out);
 cudaError_t launch_stats(chan_s* h, const double2* u1, const double2* u3, const double2* ubar,
                          const double2* tau, int with_filter);
 
+// Packed launches over n <= CHAN_MAXBATCH runs of one precision, on `st`.
+cudaError_t launch_pre_batch(chan_s* const* hs, int n, const BatchWork* w, cudaStream_t st);
+cudaError_t launch_nonlin_batch(chan_s* const* hs, int n, const BatchWork* w, cudaStream_t st);
+cudaError_t launch_helm_batch(chan_s* const* hs, int n, const BatchWork* w, cudaStream_t st);
+cudaError_t launch_poisson_batch(chan_s* const* hs, int n, const BatchWork* w, cudaStream_t st);
+cudaError_t launch_mean_batch(chan_s* const* hs, int n, const BatchWork* w, cudaStream_t st);
+cudaError_t launch_zinv_batch(chan_s* const* hs, int n, const BatchWork* w, cudaStream_t st);
+cudaError_t launch_xpass_batch(chan_s* const* hs, int n, const BatchWork* w, cudaStream_t st);
+cudaError_t launch_zfwd_batch(chan_s* const* hs, int n, const BatchWork* w, cudaStream_t st);
+
 // FFT passes.  in/out are arrays of nf device pointers.
 cudaError_t launch_zinv(chan_s* h, const double2* const* in, const int* apply_G, void* const* out, int nf);
 cudaError_t launch_xpass(chan_s* h, int mode, void* const* in, void* const* out);
 cudaError_t launch_zfwd(chan_s* h, void* const* in, double2* const* out, int nf);
 cudaError_t fft_configure(chan_s* h);
+// Default z-pass columns per CTA: as many as fit 56 KB of shared memory, at most 16.
+int pick_kb(int nxh, int L3, size_t es);

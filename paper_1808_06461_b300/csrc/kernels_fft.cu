@@ -287,11 +287,12 @@ struct ZArgs {
 // kz zero-padded to 3Nz/2 (the kz Nyquist row is dropped), optional filter
 // transfer G applied on load.
 template <typename T>
-__global__ void __launch_bounds__(256) k_zinv(ZArgs A, const typename V2<T>::t* __restrict__ tw) {
+__device__ __forceinline__ void zinv_body(const ZArgs& A, const typename V2<T>::t* __restrict__ tw, int bx, int by,
+                                          int bz) {
   typedef typename V2<T>::t T2;
   extern __shared__ __align__(16) unsigned char smraw[];
   T2* a = reinterpret_cast<T2*>(smraw);
-  const int f = blockIdx.z, y = blockIdx.y, kx0 = blockIdx.x * A.KB;
+  const int f = bz, y = by, kx0 = bx * A.KB;
   const int hz = A.Nz / 2;
   for (int e = threadIdx.x; e < A.KB * A.ld; e += blockDim.x) a[e] = zero2<T2>();
   __syncthreads();
@@ -319,13 +320,20 @@ __global__ void __launch_bounds__(256) k_zinv(ZArgs A, const typename V2<T>::t* 
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(256) k_zinv(ZArgs A, const typename V2<T>::t* __restrict__ tw) {
+  zinv_body<T>(A, tw, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+
 // Forward z-pass: mixed (T) -> Fourier (double), truncation to the stored kz.
 template <typename T>
-__global__ void __launch_bounds__(256) k_zfwd(ZArgs A, const typename V2<T>::t* __restrict__ tw) {
+__device__ __forceinline__ void zfwd_body(const ZArgs& A, const typename V2<T>::t* __restrict__ tw, int bx, int by,
+                                          int bz) {
   typedef typename V2<T>::t T2;
   extern __shared__ __align__(16) unsigned char smraw[];
   T2* a = reinterpret_cast<T2*>(smraw);
-  const int f = blockIdx.z, y = blockIdx.y, kx0 = blockIdx.x * A.KB;
+  const int f = bz, y = by, kx0 = bx * A.KB;
   const int hz = A.Nz / 2;
   const T2* in = reinterpret_cast<const T2*>(A.out[f]) + (size_t)y * A.L3 * A.nxh;
   for (int e = threadIdx.x; e < A.L3 * A.KB; e += blockDim.x) {
@@ -350,6 +358,12 @@ __global__ void __launch_bounds__(256) k_zfwd(ZArgs A, const typename V2<T>::t* 
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(256) k_zfwd(ZArgs A, const typename V2<T>::t* __restrict__ tw) {
+  zfwd_body<T>(A, tw, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+
 struct XArgs {
   void* in[CHAN_MAXFIELDS];
   void* out[CHAN_MAXFIELDS];
@@ -363,14 +377,14 @@ struct XArgs {
 // (u1, u2, u3) -> the six products u_i u_j (11, 22, 33, 12, 13, 23).
 // MODE 2: inputs (w1, w2, w3) -> w_i w_i (1 output).
 template <typename T, int MODE>
-__global__ void __launch_bounds__(256) k_xpass(XArgs A, const typename V2<T>::t* __restrict__ tw) {
+__device__ __forceinline__ void xpass_body(const XArgs& A, const typename V2<T>::t* __restrict__ tw, int bx, int by) {
   typedef typename V2<T>::t T2;
   constexpr int NIN = MODE == 0 ? 6 : 3;
   constexpr int NOUT = MODE == 0 ? 3 : (MODE == 1 ? 6 : 1);
   constexpr int NB = 6;
   extern __shared__ __align__(16) unsigned char smraw[];
   T2* a = reinterpret_cast<T2*>(smraw);
-  const int z0 = 2 * blockIdx.x, y = blockIdx.y;
+  const int z0 = 2 * bx, y = by;
   const int L1 = A.L1, nxh = A.nxh, ld = A.ld;
   for (int e = threadIdx.x; e < NIN * ld; e += blockDim.x) a[e] = zero2<T2>();
   __syncthreads();
@@ -445,14 +459,63 @@ __global__ void __launch_bounds__(256) k_xpass(XArgs A, const typename V2<T>::t*
   }
 }
 
+template <typename T, int MODE>
+__global__ void __launch_bounds__(512) k_xpass(XArgs A, const typename V2<T>::t* __restrict__ tw) {
+  xpass_body<T, MODE>(A, tw, blockIdx.x, blockIdx.y);
+}
+
+
+
+// Packed launches: one grid over several runs (same precision, any sizes).
+struct ZBatch {
+  ZArgs a[CHAN_MAXBATCH];
+  const void* tw[CHAN_MAXBATCH];
+  int gx[CHAN_MAXBATCH], gy[CHAN_MAXBATCH];
+  int begin[CHAN_MAXBATCH + 1];
+  int n;
+};
+struct XBatch {
+  XArgs a[CHAN_MAXBATCH];
+  const void* tw[CHAN_MAXBATCH];
+  int gx[CHAN_MAXBATCH];
+  int begin[CHAN_MAXBATCH + 1];
+  int n;
+};
+__device__ __forceinline__ int run_of(const int* begin, int n, int b) {
+  int r = 0;
+  while (r + 1 < n && b >= begin[r + 1]) ++r;
+  return r;
+}
+template <typename T, bool INV>
+__global__ void __launch_bounds__(256) kb_z(ZBatch B) {
+  typedef typename V2<T>::t T2;
+  const int r = run_of(B.begin, B.n, blockIdx.x);
+  const int l = blockIdx.x - B.begin[r];
+  const int bx = l % B.gx[r], t = l / B.gx[r];
+  const int by = t % B.gy[r], bz = t / B.gy[r];
+  if (INV) zinv_body<T>(B.a[r], (const T2*)B.tw[r], bx, by, bz);
+  else zfwd_body<T>(B.a[r], (const T2*)B.tw[r], bx, by, bz);
+}
+template <typename T>
+__global__ void __launch_bounds__(256) kb_xpass(XBatch B) {
+  typedef typename V2<T>::t T2;
+  const int r = run_of(B.begin, B.n, blockIdx.x);
+  const int l = blockIdx.x - B.begin[r];
+  xpass_body<T, 0>(B.a[r], (const T2*)B.tw[r], l % B.gx[r], l / B.gx[r]);
+}
+
 template <typename T> size_t esize() { return sizeof(typename V2<T>::t); }
 
 // Columns per z-pass CTA: as many as fit 56 KB of shared memory (4 CTAs per SM), at most 16.
+}  // namespace
+
 int pick_kb(int nxh, int L3, size_t es) {
   int kb = 1;
   while (kb * 2 <= nxh && kb * 2 <= 16 && (size_t)(kb * 2) * (L3 + 1) * es <= 56 * 1024) kb *= 2;
   return kb;
 }
+
+namespace {
 
 }  // namespace
 
@@ -461,7 +524,10 @@ cudaError_t fft_configure(chan_s* h) {
                        (const void*)k_zfwd<double>,     (const void*)k_zfwd<float>,      (const void*)k_zfwd<dfr>,
                        (const void*)k_xpass<double, 0>, (const void*)k_xpass<double, 1>, (const void*)k_xpass<float, 0>,
                        (const void*)k_xpass<float, 1>,  (const void*)k_xpass<dfr, 0>,    (const void*)k_xpass<dfr, 1>,
-                       (const void*)k_xpass<double, 2>, (const void*)k_xpass<float, 2>,  (const void*)k_xpass<dfr, 2>};
+                       (const void*)k_xpass<double, 2>, (const void*)k_xpass<float, 2>,  (const void*)k_xpass<dfr, 2>,
+                       (const void*)kb_z<double, true>, (const void*)kb_z<float, true>,  (const void*)kb_z<dfr, true>,
+                       (const void*)kb_z<double, false>, (const void*)kb_z<float, false>, (const void*)kb_z<dfr, false>,
+                       (const void*)kb_xpass<double>,   (const void*)kb_xpass<float>,    (const void*)kb_xpass<dfr>};
   for (const void* f : fns) {
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     if (e != cudaSuccess) return e;
@@ -473,7 +539,7 @@ static ZArgs zargs(chan_s* h, size_t es) {
   ZArgs A;
   memset(&A, 0, sizeof(A));
   A.Ny = h->Ny; A.Nz = h->Nz; A.nxh = h->nxh; A.M = h->M; A.L3 = h->L3;
-  A.KB = pick_kb(h->nxh, h->L3, es);
+  A.KB = h->kb_z > 0 ? h->kb_z : pick_kb(h->nxh, h->L3, es);
   A.ld = h->L3 + 1;
   A.pl = h->p3;
   A.G = h->G;
@@ -518,21 +584,113 @@ cudaError_t launch_xpass(chan_s* h, int mode, void* const* in, void* const* out)
   A.pl = h->p1;
   dim3 grid(h->L3 / 2, h->Ny);
   size_t sm = 6 * (size_t)A.ld * es;
+  const int nt = h->xthreads > 0 ? h->xthreads : 256;
   if (h->prec == CHAN_PREC_FP64) {
     const double2* tw = (const double2*)h->tw1;
-    if (mode == 0) k_xpass<double, 0><<<grid, 256, sm, h->stream>>>(A, tw);
-    else if (mode == 1) k_xpass<double, 1><<<grid, 256, sm, h->stream>>>(A, tw);
-    else k_xpass<double, 2><<<grid, 256, sm, h->stream>>>(A, tw);
+    if (mode == 0) k_xpass<double, 0><<<grid, nt, sm, h->stream>>>(A, tw);
+    else if (mode == 1) k_xpass<double, 1><<<grid, nt, sm, h->stream>>>(A, tw);
+    else k_xpass<double, 2><<<grid, nt, sm, h->stream>>>(A, tw);
   } else if (h->prec == CHAN_PREC_MIXED) {
     const float2* tw = (const float2*)h->tw1;
-    if (mode == 0) k_xpass<float, 0><<<grid, 256, sm, h->stream>>>(A, tw);
-    else if (mode == 1) k_xpass<float, 1><<<grid, 256, sm, h->stream>>>(A, tw);
-    else k_xpass<float, 2><<<grid, 256, sm, h->stream>>>(A, tw);
+    if (mode == 0) k_xpass<float, 0><<<grid, nt, sm, h->stream>>>(A, tw);
+    else if (mode == 1) k_xpass<float, 1><<<grid, nt, sm, h->stream>>>(A, tw);
+    else k_xpass<float, 2><<<grid, nt, sm, h->stream>>>(A, tw);
   } else {
     const dfc* tw = (const dfc*)h->tw1;
-    if (mode == 0) k_xpass<dfr, 0><<<grid, 256, sm, h->stream>>>(A, tw);
-    else if (mode == 1) k_xpass<dfr, 1><<<grid, 256, sm, h->stream>>>(A, tw);
-    else k_xpass<dfr, 2><<<grid, 256, sm, h->stream>>>(A, tw);
+    if (mode == 0) k_xpass<dfr, 0><<<grid, nt, sm, h->stream>>>(A, tw);
+    else if (mode == 1) k_xpass<dfr, 1><<<grid, nt, sm, h->stream>>>(A, tw);
+    else k_xpass<dfr, 2><<<grid, nt, sm, h->stream>>>(A, tw);
   }
+  return cudaGetLastError();
+}
+
+
+// ---------------------------------------------------------------------------
+// Packed FFT launchers (see launch_pre_batch)
+// ---------------------------------------------------------------------------
+cudaError_t launch_zinv_batch(chan_s* const* hs, int n, const BatchWork* w, cudaStream_t st) {
+  ZBatch B;
+  memset(&B, 0, sizeof(B));
+  B.n = n;
+  size_t sm = 0;
+  int acc = 0;
+  for (int r = 0; r < n; ++r) {
+    chan_s* h = hs[r];
+    ZArgs A = zargs(h, fft_esize(h));
+    const double2* in[6] = {w[r].u1, h->v, w[r].u3, w[r].om1, h->om, w[r].om3};
+    for (int f = 0; f < 6; ++f) { A.in[f] = in[f]; A.out[f] = w[r].mixed[f]; A.applyG[f] = 0; }
+    B.a[r] = A;
+    B.tw[r] = h->tw3;
+    B.gx[r] = (h->nxh + A.KB - 1) / A.KB;
+    B.gy[r] = h->Ny;
+    B.begin[r] = acc;
+    acc += B.gx[r] * B.gy[r] * 6;
+    const size_t smr = (size_t)A.KB * A.ld * fft_esize(h);
+    sm = smr > sm ? smr : sm;
+  }
+  B.begin[n] = acc;
+  const int prec = hs[0]->prec;
+  if (prec == CHAN_PREC_FP64) kb_z<double, true><<<acc, 256, sm, st>>>(B);
+  else if (prec == CHAN_PREC_MIXED) kb_z<float, true><<<acc, 256, sm, st>>>(B);
+  else kb_z<dfr, true><<<acc, 256, sm, st>>>(B);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zfwd_batch(chan_s* const* hs, int n, const BatchWork* w, cudaStream_t st) {
+  ZBatch B;
+  memset(&B, 0, sizeof(B));
+  B.n = n;
+  size_t sm = 0;
+  int acc = 0;
+  for (int r = 0; r < n; ++r) {
+    chan_s* h = hs[r];
+    ZArgs A = zargs(h, fft_esize(h));
+    double2* outs[3] = {w[r].H1, w[r].H2, w[r].H3};
+    for (int f = 0; f < 3; ++f) { A.out[f] = w[r].mixed[f]; A.outd[f] = outs[f]; }
+    B.a[r] = A;
+    B.tw[r] = h->tw3;
+    B.gx[r] = (h->nxh + A.KB - 1) / A.KB;
+    B.gy[r] = h->Ny;
+    B.begin[r] = acc;
+    acc += B.gx[r] * B.gy[r] * 3;
+    const size_t smr = (size_t)A.KB * A.ld * fft_esize(h);
+    sm = smr > sm ? smr : sm;
+  }
+  B.begin[n] = acc;
+  const int prec = hs[0]->prec;
+  if (prec == CHAN_PREC_FP64) kb_z<double, false><<<acc, 256, sm, st>>>(B);
+  else if (prec == CHAN_PREC_MIXED) kb_z<float, false><<<acc, 256, sm, st>>>(B);
+  else kb_z<dfr, false><<<acc, 256, sm, st>>>(B);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_xpass_batch(chan_s* const* hs, int n, const BatchWork* w, cudaStream_t st) {
+  XBatch B;
+  memset(&B, 0, sizeof(B));
+  B.n = n;
+  size_t sm = 0;
+  int acc = 0;
+  for (int r = 0; r < n; ++r) {
+    chan_s* h = hs[r];
+    XArgs A;
+    memset(&A, 0, sizeof(A));
+    for (int f = 0; f < 6; ++f) A.in[f] = w[r].mixed[f];
+    for (int f = 0; f < 3; ++f) A.out[f] = w[r].mixed[f];
+    A.nxh = h->nxh; A.L1 = h->L1; A.L3 = h->L3; A.ld = h->L1 + 1;
+    A.scale = 1.0 / ((double)h->L1 * (double)h->L3);
+    A.pl = h->p1;
+    B.a[r] = A;
+    B.tw[r] = h->tw1;
+    B.gx[r] = h->L3 / 2;   // packed launches use 256 threads whatever a run's tuned shape
+    B.begin[r] = acc;
+    acc += B.gx[r] * h->Ny;
+    const size_t smr = 6 * (size_t)A.ld * fft_esize(h);
+    sm = smr > sm ? smr : sm;
+  }
+  B.begin[n] = acc;
+  const int prec = hs[0]->prec;
+  if (prec == CHAN_PREC_FP64) kb_xpass<double><<<acc, 256, sm, st>>>(B);
+  else if (prec == CHAN_PREC_MIXED) kb_xpass<float><<<acc, 256, sm, st>>>(B);
+  else kb_xpass<dfr><<<acc, 256, sm, st>>>(B);
   return cudaGetLastError();
 }

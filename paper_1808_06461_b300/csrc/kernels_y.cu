@@ -92,10 +92,10 @@ __device__ __forceinline__ ModeInfo mode_info(const Geo& g, int m) {
 // a1: u_1, u_3, omega_1, omega_3 from (v, omega_2, dv/dy); two D1 sweeps.
 // dv/dy is part of the state (it is D1 v of the last Poisson solve).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_pre(Geo g, YTabs t, const double2* __restrict__ v,
+__device__ __forceinline__ void pre_body(Geo g, YTabs t, const double2* __restrict__ v,
                                              const double2* __restrict__ om, const double2* __restrict__ dv,
                                              const double* __restrict__ U1, const double* __restrict__ U3,
-                                             double2* u1o, double2* u3o, double2* om1o, double2* om3o) {
+                                             double2* u1o, double2* u3o, double2* om1o, double2* om3o, int bid) {
   extern __shared__ double sm[];
   const int Ny = g.Ny;
   double* sB1 = sm;
@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(128) k_pre(Geo g, YTabs t, const double2* __re
   load_tab(sB1, t.B1, 7 * Ny);
   load_tab(sLU, t.lu1, 7 * Ny);
   __syncthreads();
-  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  const int m = bid * blockDim.x + threadIdx.x;
   if (m >= g.M) return;
   const size_t M = g.M;
   ModeInfo mi = mode_info(g, m);
@@ -168,12 +168,18 @@ __global__ void __launch_bounds__(128) k_pre(Geo g, YTabs t, const double2* __re
   }
 }
 
+__global__ void __launch_bounds__(128) k_pre(Geo g, YTabs t, const double2* __restrict__ v,
+                                             const double2* __restrict__ om, const double2* __restrict__ dv,
+                                             const double* __restrict__ U1, const double* __restrict__ U3,
+                                             double2* u1o, double2* u3o, double2* om1o, double2* om3o) { pre_body(g, t, v, om, dv, U1, U3, u1o, u3o, om1o, om3o, blockIdx.x); }
+
+
 // ---------------------------------------------------------------------------
 // a5: N_omega2 = i k3 H1 - i k1 H3, N_chi = -D1(i k1 H1 + i k3 H3) - k^2 H2.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_nonlin(Geo g, YTabs t, const double2* __restrict__ H1,
+__device__ __forceinline__ void nonlin_body(Geo g, YTabs t, const double2* __restrict__ H1,
                                                 const double2* __restrict__ H2, const double2* __restrict__ H3,
-                                                double2* Nchi, double2* Nom, double2* scr) {
+                                                double2* Nchi, double2* Nom, double2* scr, int bid) {
   extern __shared__ double sm[];
   const int Ny = g.Ny;
   double* sB1 = sm;
@@ -181,7 +187,7 @@ __global__ void __launch_bounds__(128) k_nonlin(Geo g, YTabs t, const double2* _
   load_tab(sB1, t.B1, 7 * Ny);
   load_tab(sLU, t.lu1, 7 * Ny);
   __syncthreads();
-  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  const int m = bid * blockDim.x + threadIdx.x;
   if (m >= g.M) return;
   const size_t M = g.M;
   ModeInfo mi = mode_info(g, m);
@@ -218,16 +224,21 @@ __global__ void __launch_bounds__(128) k_nonlin(Geo g, YTabs t, const double2* _
   }
 }
 
+__global__ void __launch_bounds__(128) k_nonlin(Geo g, YTabs t, const double2* __restrict__ H1,
+                                                const double2* __restrict__ H2, const double2* __restrict__ H3,
+                                                double2* Nchi, double2* Nom, double2* scr) { nonlin_body(g, t, H1, H2, H3, Nchi, Nom, scr, blockIdx.x); }
+
+
 // ---------------------------------------------------------------------------
 // a6 + first half of a7: implicit RK3 Helmholtz steps of omega_2 and chi
 // (Eqs. (psi), (chi1)) multiplied through by A:
 //   [(1 + b dt nu k^2) A - b dt nu B] X+ = A[(1 - a dt nu k^2) X + dt(g N + z Nprev)] + a dt nu B X,
 // wall rows X+ = 0 (chi's are the particular solution).  Nprev <- N.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_helm(Geo g, YTabs t, const double* __restrict__ helm,
+__device__ __forceinline__ void helm_body(Geo g, YTabs t, const double* __restrict__ helm,
                                               double2* om, double2* chi, const double2* __restrict__ Nchi,
                                               const double2* __restrict__ Nom, double2* Nchi_p, double2* Nom_p,
-                                              double2* scr, int s) {
+                                              double2* scr, int s, int bid) {
   extern __shared__ double sm[];
   const int Ny = g.Ny;
   double* sA = sm;
@@ -235,7 +246,7 @@ __global__ void __launch_bounds__(128) k_helm(Geo g, YTabs t, const double* __re
   load_tab(sA, t.A2, 7 * Ny);
   load_tab(sB, t.B2, 7 * Ny);
   __syncthreads();
-  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  const int m = bid * blockDim.x + threadIdx.x;
   if (m >= g.M) return;
   const size_t M = g.M;
   const size_t C = g.C;
@@ -292,14 +303,20 @@ __global__ void __launch_bounds__(128) k_helm(Geo g, YTabs t, const double* __re
   }
 }
 
+__global__ void __launch_bounds__(128) k_helm(Geo g, YTabs t, const double* __restrict__ helm,
+                                              double2* om, double2* chi, const double2* __restrict__ Nchi,
+                                              const double2* __restrict__ Nom, double2* Nchi_p, double2* Nom_p,
+                                              double2* scr, int s) { helm_body(g, t, helm, om, chi, Nchi, Nom, Nchi_p, Nom_p, scr, s, blockIdx.x); }
+
+
 // ---------------------------------------------------------------------------
 // Second half of a7: (B - k^2 A) v_p = A chi_p, v_p(+-1) = 0 (Eq. (chi2));
 // v = v_p + c_a v_a + c_b v_b and chi likewise, with (c_a, c_b) making
 // dv/dy(+-1) = 0 through the precomputed influence matrix; then dv/dy = D1 v.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_poisson(Geo g, YTabs t, const double* __restrict__ helm,
+__device__ __forceinline__ void poisson_body(Geo g, YTabs t, const double* __restrict__ helm,
                                                  const double* __restrict__ pois, const double* __restrict__ infl,
-                                                 double2* v, double2* chi, double2* dv, double2* scr, int s) {
+                                                 double2* v, double2* chi, double2* dv, double2* scr, int s, int bid) {
   extern __shared__ double sm[];
   const int Ny = g.Ny;
   double* sA = sm;
@@ -309,7 +326,7 @@ __global__ void __launch_bounds__(128) k_poisson(Geo g, YTabs t, const double* _
   load_tab(sB1, t.B1, 7 * Ny);
   load_tab(sLU, t.lu1, 7 * Ny);
   __syncthreads();
-  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  const int m = bid * blockDim.x + threadIdx.x;
   if (m >= g.M) return;
   const size_t M = g.M;
   const size_t C = g.C;
@@ -375,6 +392,11 @@ __global__ void __launch_bounds__(128) k_poisson(Geo g, YTabs t, const double* _
   }
 }
 
+__global__ void __launch_bounds__(128) k_poisson(Geo g, YTabs t, const double* __restrict__ helm,
+                                                 const double* __restrict__ pois, const double* __restrict__ infl,
+                                                 double2* v, double2* chi, double2* dv, double2* scr, int s) { poisson_body(g, t, helm, pois, infl, v, chi, dv, scr, s, blockIdx.x); }
+
+
 // ---------------------------------------------------------------------------
 // a8: mean profiles.  The (0,0) Helmholtz factors (k = 0) of substep s serve
 //   (A - b dt nu B) U+ = A[U + dt(g <H> + z <H>prev)] + a dt nu B U,  U+(+-1) = 0.
@@ -383,10 +405,10 @@ __global__ void __launch_bounds__(128) k_poisson(Geo g, YTabs t, const double* _
 // right-hand sides and the flux sums are row-parallel, the two banded
 // sweeps (U_1, U_3) run on two warps.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_mean(Geo g, YTabs t, const double* __restrict__ helm,
+__device__ __forceinline__ void mean_body(Geo g, YTabs t, const double* __restrict__ helm,
                                               const double* __restrict__ meanh, const double2* __restrict__ H1,
                                               const double2* __restrict__ H3, double* U1, double* U3, double* H1p,
-                                              double* H3p, double* scal, int s) {
+                                              double* H3p, double* scal, int s, int bid) {
   extern __shared__ double sm[];
   const int Ny = g.Ny;
   const size_t M = g.M, C = g.C;
@@ -449,6 +471,12 @@ __global__ void __launch_bounds__(256) k_mean(Geo g, YTabs t, const double* __re
   }
   if (threadIdx.x == 0) scal[0] = c / ((al + be) * dt);
 }
+
+__global__ void __launch_bounds__(256) k_mean(Geo g, YTabs t, const double* __restrict__ helm,
+                                              const double* __restrict__ meanh, const double2* __restrict__ H1,
+                                              const double2* __restrict__ H3, double* U1, double* U3, double* H1p,
+                                              double* H3p, double* scal, int s) { mean_body(g, t, helm, meanh, H1, H3, U1, U3, H1p, H3p, scal, s, blockIdx.x); }
+
 
 // U_h(s) = (A - b_s dt nu B)^-1 A 1 with zero wall values, and its trapezoid flux.
 __global__ void k_setup_mean(Geo g, YTabs t, const double* __restrict__ helm, double* meanh) {
@@ -669,6 +697,55 @@ __global__ void k_setup_helm(Geo g, YTabs t, const double* __restrict__ pois, do
   G[3 * C] = gm[0][0] / det;
 }
 
+
+// ---------------------------------------------------------------------------
+// Packed launches over several channels: one grid covers the blocks of every
+// run; a block finds its run from the per-run block offsets and executes the
+// same body with its local block index.  Runs may differ in size and RK3 phase.
+// ---------------------------------------------------------------------------
+struct PreP { Geo g; YTabs t; const double2 *v, *om, *dv; const double *U1, *U3; double2 *u1o, *u3o, *om1o, *om3o; };
+struct NonlinP { Geo g; YTabs t; const double2 *H1, *H2, *H3; double2 *Nchi, *Nom, *scr; };
+struct HelmP { Geo g; YTabs t; const double* helm; double2 *om, *chi; const double2 *Nchi, *Nom; double2 *Nchi_p, *Nom_p, *scr; int s; };
+struct PoisP { Geo g; YTabs t; const double *helm, *pois, *infl; double2 *v, *chi, *dv, *scr; int s; };
+struct MeanP { Geo g; YTabs t; const double *helm, *meanh; const double2 *H1, *H3; double *U1, *U3, *H1p, *H3p, *scal; int s; };
+
+template <class P> struct YBatch {
+  P p[CHAN_MAXBATCH];
+  int begin[CHAN_MAXBATCH + 1];
+  int n;
+};
+
+__device__ __forceinline__ int batch_run(const int* begin, int n, int b) {
+  int r = 0;
+  while (r + 1 < n && b >= begin[r + 1]) ++r;
+  return r;
+}
+
+__global__ void __launch_bounds__(128) kb_pre(YBatch<PreP> B) {
+  const int r = batch_run(B.begin, B.n, blockIdx.x);
+  const PreP& p = B.p[r];
+  pre_body(p.g, p.t, p.v, p.om, p.dv, p.U1, p.U3, p.u1o, p.u3o, p.om1o, p.om3o, blockIdx.x - B.begin[r]);
+}
+__global__ void __launch_bounds__(128) kb_nonlin(YBatch<NonlinP> B) {
+  const int r = batch_run(B.begin, B.n, blockIdx.x);
+  const NonlinP& p = B.p[r];
+  nonlin_body(p.g, p.t, p.H1, p.H2, p.H3, p.Nchi, p.Nom, p.scr, blockIdx.x - B.begin[r]);
+}
+__global__ void __launch_bounds__(128) kb_helm(YBatch<HelmP> B) {
+  const int r = batch_run(B.begin, B.n, blockIdx.x);
+  const HelmP& p = B.p[r];
+  helm_body(p.g, p.t, p.helm, p.om, p.chi, p.Nchi, p.Nom, p.Nchi_p, p.Nom_p, p.scr, p.s, blockIdx.x - B.begin[r]);
+}
+__global__ void __launch_bounds__(128) kb_poisson(YBatch<PoisP> B) {
+  const int r = batch_run(B.begin, B.n, blockIdx.x);
+  const PoisP& p = B.p[r];
+  poisson_body(p.g, p.t, p.helm, p.pois, p.infl, p.v, p.chi, p.dv, p.scr, p.s, blockIdx.x - B.begin[r]);
+}
+__global__ void __launch_bounds__(256) kb_mean(YBatch<MeanP> B) {
+  const MeanP& p = B.p[blockIdx.x];
+  mean_body(p.g, p.t, p.helm, p.meanh, p.H1, p.H3, p.U1, p.U3, p.H1p, p.H3p, p.scal, p.s, 0);
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -761,6 +838,101 @@ cudaError_t launch_mean(chan_s* h, const double2* H1, const double2* H3, int s) 
   if (e != cudaSuccess) return e;
   k_mean<<<1, 256, sm, h->stream>>>(geo(h), ytabs(h), h->helm, h->meanh, H1, H3, h->U1, h->U3, h->H1m_p, h->H3m_p,
                                     h->scal, s);
+  return cudaGetLastError();
+}
+
+
+// ---------------------------------------------------------------------------
+// Packed launchers: the runs of hs[0..n) (n <= CHAN_MAXBATCH) in one grid on
+// `stream`; w[r] holds run r's work-field pointers (see batch_step in chan_api).
+// ---------------------------------------------------------------------------
+template <class P>
+static int fill_begin(YBatch<P>& B, chan_s* const* hs, int n) {
+  B.n = n;
+  int acc = 0;
+  for (int r = 0; r < n; ++r) {
+    B.begin[r] = acc;
+    acc += (hs[r]->M + kYThreads - 1) / kYThreads;
+  }
+  B.begin[n] = acc;
+  return acc;
+}
+static int max_ny(chan_s* const* hs, int n) {
+  int m = 0;
+  for (int r = 0; r < n; ++r) m = hs[r]->Ny > m ? hs[r]->Ny : m;
+  return m;
+}
+
+cudaError_t launch_pre_batch(chan_s* const* hs, int n, const BatchWork* w, cudaStream_t st) {
+  YBatch<PreP> B;
+  for (int r = 0; r < n; ++r) {
+    chan_s* h = hs[r];
+    B.p[r] = PreP{geo(h), ytabs(h), h->v, h->om, h->dv, h->U1, h->U3, w[r].u1, w[r].u3, w[r].om1, w[r].om3};
+  }
+  const int blocks = fill_begin(B, hs, n);
+  const size_t sm = sizeof(double) * 14 * max_ny(hs, n);
+  cudaError_t e = smem_attr((const void*)kb_pre, sm);
+  if (e != cudaSuccess) return e;
+  kb_pre<<<blocks, kYThreads, sm, st>>>(B);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_nonlin_batch(chan_s* const* hs, int n, const BatchWork* w, cudaStream_t st) {
+  YBatch<NonlinP> B;
+  for (int r = 0; r < n; ++r) {
+    chan_s* h = hs[r];
+    B.p[r] = NonlinP{geo(h), ytabs(h), w[r].H1, w[r].H2, w[r].H3, w[r].Nchi, w[r].Nom, h->scr};
+  }
+  const int blocks = fill_begin(B, hs, n);
+  const size_t sm = sizeof(double) * 14 * max_ny(hs, n);
+  cudaError_t e = smem_attr((const void*)kb_nonlin, sm);
+  if (e != cudaSuccess) return e;
+  kb_nonlin<<<blocks, kYThreads, sm, st>>>(B);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_helm_batch(chan_s* const* hs, int n, const BatchWork* w, cudaStream_t st) {
+  YBatch<HelmP> B;
+  for (int r = 0; r < n; ++r) {
+    chan_s* h = hs[r];
+    B.p[r] = HelmP{geo(h), ytabs(h), h->helm, h->om, h->chi, w[r].Nchi, w[r].Nom, h->Nchi_p, h->Nom_p, h->scr,
+                   (int)(h->nsub % 3)};
+  }
+  const int blocks = fill_begin(B, hs, n);
+  const size_t sm = sizeof(double) * 14 * max_ny(hs, n);
+  cudaError_t e = smem_attr((const void*)kb_helm, sm);
+  if (e != cudaSuccess) return e;
+  kb_helm<<<blocks, kYThreads, sm, st>>>(B);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_poisson_batch(chan_s* const* hs, int n, const BatchWork* w, cudaStream_t st) {
+  (void)w;
+  YBatch<PoisP> B;
+  for (int r = 0; r < n; ++r) {
+    chan_s* h = hs[r];
+    B.p[r] = PoisP{geo(h), ytabs(h), h->helm, h->pois, h->infl, h->v, h->chi, h->dv, h->scr, (int)(h->nsub % 3)};
+  }
+  const int blocks = fill_begin(B, hs, n);
+  const size_t sm = sizeof(double) * 21 * max_ny(hs, n);
+  cudaError_t e = smem_attr((const void*)kb_poisson, sm);
+  if (e != cudaSuccess) return e;
+  kb_poisson<<<blocks, kYThreads, sm, st>>>(B);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mean_batch(chan_s* const* hs, int n, const BatchWork* w, cudaStream_t st) {
+  YBatch<MeanP> B;
+  B.n = n;
+  for (int r = 0; r < n; ++r) {
+    chan_s* h = hs[r];
+    B.p[r] = MeanP{geo(h), ytabs(h), h->helm, h->meanh, w[r].H1, w[r].H3, h->U1, h->U3, h->H1m_p, h->H3m_p,
+                   h->scal, (int)(h->nsub % 3)};
+  }
+  const size_t sm = sizeof(double) * (2 * max_ny(hs, n) + 256);
+  cudaError_t e = smem_attr((const void*)kb_mean, sm);
+  if (e != cudaSuccess) return e;
+  kb_mean<<<n, 256, sm, st>>>(B);
   return cudaGetLastError();
 }
 

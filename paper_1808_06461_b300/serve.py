@@ -11,9 +11,15 @@ overlaps on the GPU; a run's arithmetic does not depend on what else runs
 (every kernel is deterministic and its launch shape depends on the run's own
 sizes only), so a result is bitwise the same alone and in the mix.
 
+With ``packed=True`` the admitted runs of one precision advance together:
+one RK3 step of all of them is one launch per kernel (``chan_batch_step``,
+graph-replayed), on a single batch stream; a run's last partial step runs on
+its own stream.
+
 Per-step latency is the device time between CUDA events recorded around each
-step on the run's stream (contention included); request latency is arrival
-to completion on the host clock.
+RK3 step (contention included; in packed mode the packed step's time counts
+once for every run in it); request latency is arrival to completion on the
+host clock.
 """
 import collections
 import math
@@ -21,7 +27,7 @@ import time
 
 import numpy as np
 
-from . import CHAN_PREC_FP64, Channel, footprint_bytes
+from . import CHAN_PREC_FP64, Channel, ChannelBatch, footprint_bytes
 
 
 class Request:
@@ -80,6 +86,7 @@ class _Slot:
         self.req, self.ch, self.stream, self.fp, self.t_admit = req, ch, stream, fp, t_admit
         self.remaining = req.nsub
         self.inflight = collections.deque()
+        self.packed_pending = 0
 
 
 class Server:
@@ -92,7 +99,8 @@ class Server:
     """
 
     def __init__(self, hbm_budget, max_slots=16, chunk=3, max_inflight=2, factory=None, footprint=None,
-                 make_stream=None, make_event=None, clock=time.perf_counter, idle_sleep=2e-4):
+                 make_stream=None, make_event=None, clock=time.perf_counter, idle_sleep=2e-4, packed=False,
+                 make_batch=None):
         self.hbm_budget, self.max_slots, self.chunk, self.max_inflight = int(hbm_budget), max_slots, chunk, max_inflight
         if factory is None:
             raise ValueError("a channel factory is required (see channel_factory)")
@@ -101,6 +109,8 @@ class Server:
         self.make_stream = make_stream or _torch_stream
         self.make_event = make_event or _torch_event
         self.clock, self.idle_sleep = clock, idle_sleep
+        self.packed = packed
+        self.make_batch = make_batch or (lambda chans, stream: ChannelBatch(chans, stream=stream.cuda_stream))
 
     def run(self, requests, keep_results=True):
         for r in requests:
@@ -112,6 +122,7 @@ class Server:
         used = 0
         results, done = {}, {}
         step_ms, max_conc, conc_samples = [], 0, []
+        bstream, binflight, batches = None, collections.deque(), {}
         t0 = self.clock()
         while pending or waiting or active:
             now = self.clock() - t0
@@ -128,8 +139,40 @@ class Server:
                 active.append(_Slot(r, ch, stream, fp, self.clock() - t0))
                 progressed = True
             max_conc = max(max_conc, len(active))
+            # packed issue: one RK3 step of every full-step run of a precision in one launch per kernel
+            if self.packed:
+                if bstream is None:
+                    bstream = self.make_stream()
+                groups = collections.defaultdict(list)
+                for sl in active:
+                    if sl.remaining >= self.chunk:
+                        groups[sl.req.precision].append(sl)
+                for prec, sls in groups.items():
+                    if len(binflight) >= self.max_inflight:
+                        break
+                    key = tuple(sl.req.rid for sl in sls)
+                    if key not in batches:
+                        batches[key] = self.make_batch([sl.ch for sl in sls], bstream)
+                    e0, e1 = self.make_event(), self.make_event()
+                    e0.record(bstream)
+                    batches[key].step(self.chunk)
+                    e1.record(bstream)
+                    binflight.append((e0, e1, sls))
+                    for sl in sls:
+                        sl.remaining -= self.chunk
+                        sl.packed_pending += 1
+                    progressed = True
+                while binflight and binflight[0][1].query():
+                    e0, e1, sls = binflight.popleft()
+                    t = e0.elapsed_time(e1)
+                    for sl in sls:
+                        sl.packed_pending -= 1
+                        step_ms.append(t)
+                    progressed = True
             # issue: one RK3 step per run, up to max_inflight steps queued per stream
             for sl in active:
+                if self.packed and (sl.remaining >= self.chunk or sl.packed_pending):
+                    continue
                 while sl.remaining > 0 and len(sl.inflight) < self.max_inflight:
                     k = min(self.chunk, sl.remaining)
                     e0, e1 = self.make_event(), self.make_event()
@@ -147,7 +190,7 @@ class Server:
                     if k == self.chunk:
                         step_ms.append(e0.elapsed_time(e1))
                     progressed = True
-                if sl.remaining == 0 and not sl.inflight:
+                if sl.remaining == 0 and not sl.inflight and not sl.packed_pending:
                     if keep_results:
                         results[sl.req.rid] = sl.ch.get_state()
                     sl.ch.close()
@@ -162,9 +205,11 @@ class Server:
             if not progressed:
                 time.sleep(self.idle_sleep)
         wall = self.clock() - t0
+        for b in batches.values():
+            b.close()
         work = sum(r.points * r.nsub for r in requests)
         lat = [d["latency"] for d in done.values()]
-        metrics = dict(requests=len(requests), wall_s=wall, mpts_substep_per_s=work / wall / 1e6,
+        metrics = dict(requests=len(requests), wall_s=wall, packed=self.packed, batches_built=len(batches), mpts_substep_per_s=work / wall / 1e6,
                        step_ms_p50=_pct(step_ms, 50), step_ms_p99=_pct(step_ms, 99), steps_timed=len(step_ms),
                        request_s_p50=_pct(lat, 50), request_s_p99=_pct(lat, 99), max_concurrency=max_conc,
                        mean_concurrency=float(np.mean(conc_samples)) if conc_samples else 0.0)
@@ -181,9 +226,10 @@ def _torch_event():
     return torch.cuda.Event(enable_timing=True)
 
 
-def channel_factory(make_ic, use_graph=True):
-    """Factory for Server: a Channel on the run's stream (graph replay on), state from
-    ``make_ic(request, y) -> dict(v, omega2, U1, U3)`` with y the run's mesh."""
+def channel_factory(make_ic, use_graph=True, autotune=True):
+    """Factory for Server: a Channel on the run's stream (graph replay on, launch shapes
+    autotuned per shape), state from ``make_ic(request, y) -> dict(v, omega2, U1, U3)``
+    with y the run's mesh."""
 
     def make(r, stream):
         ch = Channel(r.re_tau, r.Lx, r.Lz, r.Nx, r.Ny, r.Nz, r.dt, precision=r.precision,
@@ -191,6 +237,8 @@ def channel_factory(make_ic, use_graph=True):
         ch.set_graph(use_graph)
         s0 = make_ic(r, ch.grid())
         ch.set_state(s0["v"], s0["omega2"], s0["U1"], s0["U3"])
+        if autotune:
+            ch.autotune()
         return ch
 
     return make

@@ -108,3 +108,31 @@ def test_serving_mix_and_dt():
     assert serving_dt(180.0, np.pi, np.pi / 2, 32, 32) <= 1e-3
     again = poisson_requests(50, rate=50.0, seed=42)
     assert [(r.Nx, r.Ny, r.nsub) for r in again] == [(r.Nx, r.Ny, r.nsub) for r in reqs]
+
+
+class FakeBatch:
+    built = 0
+
+    def __init__(self, chans, stream):
+        self.chans, self.stream = chans, stream
+        FakeBatch.built += 1
+
+    def step(self, k):
+        for ch in self.chans:
+            ch.steps += k
+        self.stream.busy_until = max(self.stream.busy_until, self.stream.clock.t) + 1e-3 * k
+
+    def close(self):
+        pass
+
+
+def test_packed_mode_completes_every_run_exactly():
+    clock, log = Clock(), []
+    reqs = poisson_requests(15, rate=50.0, seed=3, length=(10, 40))
+    srv = _server(10 ** 9, 6, clock, log)
+    srv.packed = True
+    srv.make_batch = lambda chans, stream: FakeBatch(chans, stream)
+    res, m = srv.run(reqs)
+    for r in reqs:
+        assert res[r.rid]["steps"] == r.nsub      # packed steps plus the per-run tail add up
+    assert m["packed"] and m["batches_built"] >= 1
