@@ -170,6 +170,25 @@ def fp64_peak_tflops(torch):
 
 
 # ---------------------------------------------------------------------------
+# Replicas (N > 1 under torch.distributed.run): every rank runs its own box;
+# the job's time is the slowest rank's and its throughput counts every rank.
+# ---------------------------------------------------------------------------
+def max_over_ranks(x, dist=None, device="cpu"):
+    """Largest value of x over the ranks of the default process group (x itself alone)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(world, steps, substeps_per_step, points, max_ms):
+    """Weak scaling: all ranks' point-substeps over the slowest rank's time, in Mpts.substep/s."""
+    return world * steps * substeps_per_step * points / (max_ms * 1e-3) / 1e6
+
+
+# ---------------------------------------------------------------------------
 # CPU oracle on a bounded sample (reference arm and cpu_baseline)
 # ---------------------------------------------------------------------------
 def oracle_sample_substep_seconds(c, n_planes=4, n_modes=512):
@@ -283,12 +302,8 @@ def run_ours(args, c, name):
             dist.barrier()
             torch.cuda.synchronize()
 
-    def max_over_ranks(x):
-        if world > 1:
-            t = torch.tensor([x], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            return float(t.item())
-        return x
+    def ranks_max(x):
+        return max_over_ranks(x, dist if world > 1 else None, "cuda")
 
     def measure(mode, with_clocks):
         """Warm up from the seeded field, snapshot, then time args.steps steps."""
@@ -327,7 +342,7 @@ def run_ours(args, c, name):
             th.join(timeout=10)
         prof = ch.profile_read()
         ch.profile(False)
-        ms = max_over_ranks(e0.elapsed_time(e1))
+        ms = ranks_max(e0.elapsed_time(e1))
         return ch, snap, prof, ms, samples
 
     def roofline(prof, peak64):
@@ -340,7 +355,7 @@ def run_ours(args, c, name):
     main_mode = args.precision
     ch, snap_main, prof, ms, samples = measure(main_mode, True)
     peak64 = fp64_peak_tflops(torch)
-    value = world * args.steps * nsub * pts / (ms * 1e-3) / 1e6
+    value = replica_throughput(world, args.steps, nsub, pts, ms)
 
     # ---- end to end through the public API with pinned host buffers
     shape = (c["Ny"], c["Nz"], c["Nx"] // 2)
@@ -366,7 +381,7 @@ def run_ours(args, c, name):
             ch.stats()
             ch.get_state()
         barrier()
-        e2e = world * e2e_steps * nsub * pts / max_over_ranks(time.perf_counter() - t0) / 1e6
+        e2e = replica_throughput(world, e2e_steps, nsub, pts, ranks_max(time.perf_counter() - t0) * 1e3)
     ch.close()
 
     dom, achieved, frac = roofline(prof, peak64)
@@ -396,7 +411,7 @@ def run_ours(args, c, name):
             dm, am, fm = roofline(profm, peak64)
             sm_ = snap["stats"]
             modes[mode] = {
-                "value": world * args.steps * nsub * pts / (msm * 1e-3) / 1e6, "ms_per_step": msm / args.steps,
+                "value": replica_throughput(world, args.steps, nsub, pts, msm), "ms_per_step": msm / args.steps,
                 "roofline": {"kernel": dm, "achieved": am, "frac": fm, "unit": "TFLOP/s", "bound": "alu"},
                 "err_vs_fp64": {"after_substeps": args.warmup * nsub,
                                 "v_rel_l2": float(np.linalg.norm(snap["v"] - snap_main["v"]) / np.linalg.norm(snap_main["v"])),
