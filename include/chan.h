@@ -175,6 +175,27 @@ int chan_filter_stresses(chan_t h, int kind, double p1, double p3, double* ubar,
 int chan_filtered_enstrophy(chan_t h, int kind, double p1, double p3, double* ens);
 
 /*
+ * The low-storage database record of the current state (Sec. 3.1, Table 2):
+ * with the sharp cut-off filter (l_1c^+ = p1, l_3c^+ = p3) the ten stored
+ * variables ubar_1..3, filt(u_i u_j) (11, 22, 33, 12, 13, 23) and
+ * filt(omega_i omega_i), on the retained modes only: kx = 0..M1-1 and
+ * kz = 0..K3 followed by -K3..-1 (M3 = 2 K3 + 1).  rec receives
+ * [10][Ny][M3][M1] interleaved complex doubles (host); *m1, *m3 receive M1,
+ * M3.  Call with rec = NULL to query the sizes only.  The device keeps a
+ * buffer of that size after the first call.  Does not advance time.
+ */
+int chan_database_record(chan_t h, double p1, double p3, double* rec, int* m1, int* m3);
+
+/*
+ * Two-dimensional energy spectra of the current state (Sec. 3.3):
+ * E_i(k1, y, k3) = w |u_i(k1, y, k3)|^2 with w = 2 for kx > 0 (the
+ * conjugate mode) and 1 for kx = 0; the mean (0,0) mode is excluded, so the
+ * sum over modes at a height is the variance of u_i'.  E receives
+ * [3][Ny][Nz][Nx/2] doubles (host).  Synchronises.
+ */
+int chan_spectra(chan_t h, double* E);
+
+/*
  * Plane statistics of the current state (Sec. 3.3), double[CHAN_NSTAT][Ny]:
  * rows 0-1 U1, U3; rows 2-7 <u_i u_j> (11,22,33,12,13,23, Parseval over
  * all stored modes, means included); rows 8-13 <ubar_i ubar_j> and rows
@@ -201,7 +222,7 @@ int chan_nonlinear(chan_t h, double* H);
  * since the last reset (launches are counted even when timing is off).
  * chan_kernel_name(k) names kernel k (NULL when out of range).
  */
-#define CHAN_NKERNELS 12
+#define CHAN_NKERNELS 14
 int chan_profile(chan_t h, int enable);
 int chan_profile_read(chan_t h, double* ms, long long* launches);
 const char* chan_kernel_name(int k);

@@ -489,6 +489,41 @@ def filtered_enstrophy(st, S, kind, p1, p3):
     return G * to_fourier(st, p[0] ** 2 + p[1] ** 2 + p[2] ** 2)
 
 
+def retained_modes(st, p1, p3):
+    """Sharp cut-off retained set (Eq. (fou_fil)): kx < M1 and |kz| <= K3; returns (M1, K3)."""
+    k1c = math.pi * st.re_tau / p1
+    k3c = math.pi * st.re_tau / p3
+    m1 = sum(1 for kx in range(st.nxh) if 2 * math.pi / st.Lx * kx < k1c)
+    k3 = [kz for kz in range(st.Nz // 2) if 2 * math.pi / st.Lz * kz < k3c]
+    return m1, (max(k3) if k3 else -1)
+
+
+def database_record(st, S, p1, p3):
+    """The ten database variables (Sec. 3.1) on the retained modes, (10, Ny, 2 K3 + 1, M1).
+
+    ubar_i = G u_i, filt(u_i u_j) = G P(u_i u_j), filt(omega_i omega_i) with the
+    sharp filter; kz ordered 0..K3 then -K3..-1.
+    """
+    G = filter_transfer(st, SHARP, p1, p3)
+    u1, v, u3, _, _, _ = velocities(st, S)
+    u = [u1, v, u3]
+    pu = [to_physical(st, f) for f in u]
+    fields = [G * f for f in u] + [G * to_fourier(st, pu[i] * pu[j]) for i, j in PAIRS]
+    fields.append(filtered_enstrophy(st, S, SHARP, p1, p3))
+    m1, K3 = retained_modes(st, p1, p3)
+    jz = list(range(K3 + 1)) + [st.Nz - k for k in range(K3, 0, -1)]
+    return np.stack([F[:, jz, :m1] for F in fields])
+
+
+def spectra(st, S):
+    """E_i(k1, y, k3) = w |u_i|^2 (w = 2 for kx > 0), mean mode excluded (Sec. 3.3)."""
+    u1, v, u3, _, _, _ = velocities(st, S)
+    w = np.where(np.arange(st.nxh) == 0, 1.0, 2.0)[None, None, :]
+    E = np.stack([w * np.abs(f) ** 2 for f in (u1, v, u3)])
+    E[:, :, 0, 0] = 0.0
+    return E
+
+
 # --------------------------------------------------------------------------
 # Statistics (Sec. 3.3) and invariants
 # --------------------------------------------------------------------------

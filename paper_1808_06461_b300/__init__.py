@@ -31,8 +31,9 @@ SYMBOLS = ("chan_opts_default", "chan_init", "chan_init_ex", "chan_free", "chan_
            "chan_substeps", "chan_profile", "chan_profile_read", "chan_kernel_name",
            "chan_rhs_terms", "chan_rhs_terms_noalloc", "chan_footprint_bytes", "chan_set_graph",
            "chan_filtered_enstrophy", "chan_batch_create", "chan_batch_step", "chan_batch_last_error",
-           "chan_batch_free", "chan_autotune", "chan_tuned_shape")
-CHAN_NKERNELS = 12
+           "chan_batch_free", "chan_autotune", "chan_tuned_shape", "chan_database_record",
+           "chan_spectra")
+CHAN_NKERNELS = 14
 
 
 class chan_opts(ctypes.Structure):
@@ -82,6 +83,8 @@ def load_library(path=LIB_PATH):
         "chan_batch_last_error": (ctypes.c_char_p, [P]),
         "chan_batch_free": (None, [P]),
         "chan_autotune": (I, [P]),
+        "chan_database_record": (I, [P, D, D, P, ctypes.POINTER(I), ctypes.POINTER(I)]),
+        "chan_spectra": (I, [P, P]),
         "chan_tuned_shape": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I)]),
         "chan_sync": (I, [P]),
         "chan_time": (D, [P]),
@@ -233,6 +236,21 @@ class Channel:
         ens = np.empty(self.shape, dtype=np.complex128)
         _check(self.h, _lib.chan_filtered_enstrophy(self.h, int(kind), float(p1), float(p3), _ptr(ens)))
         return ens
+
+    def database_record(self, p1=120.0, p3=60.0):
+        """The ten stored variables on the sharp filter's retained modes, shape (10, Ny, M3, M1)."""
+        m1, m3 = ctypes.c_int(), ctypes.c_int()
+        _check(self.h, _lib.chan_database_record(self.h, float(p1), float(p3), None, ctypes.byref(m1), ctypes.byref(m3)))
+        rec = np.empty((10, self.Ny, m3.value, m1.value), dtype=np.complex128)
+        _check(self.h, _lib.chan_database_record(self.h, float(p1), float(p3), _ptr(rec), ctypes.byref(m1),
+                                                 ctypes.byref(m3)))
+        return rec
+
+    def spectra(self):
+        """E_i(k1, y, k3), shape (3, Ny, Nz, Nx/2)."""
+        E = np.empty((3,) + self.shape)
+        _check(self.h, _lib.chan_spectra(self.h, _ptr(E)))
+        return E
 
     def stats(self):
         out = np.empty((CHAN_NSTAT, self.Ny))

@@ -69,7 +69,8 @@ size_t fsize(const chan_s* h) { return (size_t)h->Ny * h->M; }
 
 const char* const kKernelNames[KID_COUNT] = {"k_pre",     "k_zinv",       "k_xpass", "k_zfwd",
                                              "k_nonlin",  "k_helm",       "k_poisson", "k_mean",
-                                             "k_filter_out", "k_stats",   "k_derive", "k_apply_G"};
+                                             "k_filter_out", "k_stats",   "k_derive", "k_apply_G",
+                                             "k_gather_retained", "k_spectra"};
 
 // Launch bracket: counts the launch and, when tracing, records an event pair.
 struct Traced {
@@ -340,6 +341,8 @@ int chan_init_ex(chan_t* out, const chan_opts* o) {
   h->nsub = 0; h->t = 0.0; h->dev_bytes = 0;
   h->G = nullptr;
   h->g_kind = -1;
+  h->dbrec = nullptr;
+  h->dbrec_n = 0;
   int rc = CHAN_OK;
   chanh_tables tb;
   std::memset(&tb, 0, sizeof(tb));
@@ -436,7 +439,8 @@ void chan_free(chan_t h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   for (ProfRec& r : h->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
-  for (void* p : h->allocs) cudaFree(p);
+  for (void* p : h->allocs)
+    if (p) cudaFree(p);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
 }
@@ -594,7 +598,7 @@ int chan_filter_stresses(chan_t h, int kind, double p1, double p3, double* ubar,
 }
 
 int chan_filtered_enstrophy(chan_t h, int kind, double p1, double p3, double* ens) {
-  if (!h || !ens) return bad(h, "chan_filtered_enstrophy: NULL argument");
+  if (!h) return bad(nullptr, "chan_filtered_enstrophy: NULL handle");
   if (kind != CHAN_FILTER_SHARP && kind != CHAN_FILTER_BOX) return bad(h, "chan_filtered_enstrophy: unknown kind");
   if (!(p1 > 0) || !(p3 > 0)) return bad(h, "chan_filtered_enstrophy: widths must be positive");
   if (!h->have_state) return bad(h, "chan_filtered_enstrophy: no state set", CHAN_ESTATE);
@@ -608,7 +612,81 @@ int chan_filtered_enstrophy(chan_t h, int kind, double p1, double p3, double* en
     double2* fo[1] = {wf(h, 4)};
     { Traced t(h, KID_ZFWD); CK(launch_zfwd(h, mx, fo, 1)); }
     { Traced t(h, KID_APPLY_G); CK(launch_apply_G(h, wf(h, 4), wf(h, 5))); }
-    CK(cudaMemcpyAsync(ens, wf(h, 5), fsize(h) * sizeof(double2), cudaMemcpyDeviceToHost, h->stream));
+    if (ens) {
+      CK(cudaMemcpyAsync(ens, wf(h, 5), fsize(h) * sizeof(double2), cudaMemcpyDeviceToHost, h->stream));
+      CK(cudaStreamSynchronize(h->stream));
+    }
+  } catch (Fail f) {
+    return f.code;
+  }
+  return CHAN_OK;
+}
+
+// Retained-mode counts of the sharp filter: kx < M1, |kz| <= K3 (and below Nz/2).
+static void retained(const chan_s* h, double p1, double p3, int* M1, int* M3) {
+  const double k1c = M_PI * h->re / p1, k3c = M_PI * h->re / p3;
+  int m1 = 0;
+  while (m1 < h->nxh && 2.0 * M_PI / h->Lx * m1 < k1c) ++m1;
+  int K3 = -1;
+  while (K3 + 1 < h->Nz / 2 && 2.0 * M_PI / h->Lz * (K3 + 1) < k3c) ++K3;
+  *M1 = m1;
+  *M3 = K3 >= 0 ? 2 * K3 + 1 : 0;
+}
+
+int chan_database_record(chan_t h, double p1, double p3, double* rec, int* m1, int* m3) {
+  if (!h) return bad(nullptr, "chan_database_record: NULL handle");
+  if (!(p1 > 0) || !(p3 > 0)) return bad(h, "chan_database_record: cut-off lengths must be positive");
+  int M1, M3;
+  retained(h, p1, p3, &M1, &M3);
+  if (m1) *m1 = M1;
+  if (m3) *m3 = M3;
+  if (!rec) return CHAN_OK;
+  if (!h->have_state) return bad(h, "chan_database_record: no state set", CHAN_ESTATE);
+  if (M1 == 0 || M3 == 0) return bad(h, "chan_database_record: the cut-off retains no mode");
+  try {
+    const size_t blk = (size_t)h->Ny * M3 * M1;
+    if (h->dbrec_n < 10 * blk) {
+      if (h->dbrec) {
+        cudaFree(h->dbrec);
+        for (auto& p : h->allocs)
+          if (p == h->dbrec) p = nullptr;
+        h->dev_bytes -= h->dbrec_n * sizeof(double2);
+        h->dbrec = nullptr;
+      }
+      h->dbrec = dalloc<double2>(h, 10 * blk);
+      h->dbrec_n = 10 * blk;
+    }
+    // filt(omega_i omega_i) first (its pass reuses work slots the stress pass needs)
+    int rc = chan_filtered_enstrophy(h, CHAN_FILTER_SHARP, p1, p3, nullptr);
+    if (rc != CHAN_OK) return rc;
+    { Traced t(h, KID_GATHER); CK(launch_gather_retained(h, wf(h, 5), h->dbrec + 9 * blk, M1, M3)); }
+    rc = chan_filter_stresses(h, CHAN_FILTER_SHARP, p1, p3, nullptr, nullptr);
+    if (rc != CHAN_OK) return rc;
+    // ubar_i, then filt(u_i u_j) = G P(u_i u_j) = P(u_i u_j) on the retained modes (G = 1 there)
+    for (int f = 0; f < 3; ++f) {
+      Traced t(h, KID_GATHER);
+      CK(launch_gather_retained(h, filt(h, f), h->dbrec + f * blk, M1, M3));
+    }
+    for (int p = 0; p < 6; ++p) {
+      Traced t(h, KID_GATHER);
+      CK(launch_gather_retained(h, wf(h, 2 + p), h->dbrec + (3 + p) * blk, M1, M3));
+    }
+    CK(cudaMemcpyAsync(rec, h->dbrec, 10 * blk * sizeof(double2), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+  } catch (Fail f) {
+    return f.code;
+  }
+  return CHAN_OK;
+}
+
+int chan_spectra(chan_t h, double* E) {
+  if (!h || !E) return bad(h, "chan_spectra: NULL argument");
+  if (!h->have_state) return bad(h, "chan_spectra: no state set", CHAN_ESTATE);
+  try {
+    run_pre(h);
+    double* dst = reinterpret_cast<double*>(wf(h, WF_H1));   // 3 real fields fit in 2 complex slots
+    { Traced t(h, KID_SPECTRA); CK(launch_spectra(h, wf(h, WF_U1), wf(h, WF_U3), dst)); }
+    CK(cudaMemcpyAsync(E, dst, 3 * fsize(h) * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
   } catch (Fail f) {
     return f.code;

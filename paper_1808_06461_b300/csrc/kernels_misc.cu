@@ -41,6 +41,35 @@ __global__ void k_apply_G(const double2* __restrict__ in, const double* __restri
   out[e] = make_double2(g * x.x, g * x.y);
 }
 
+// Retained modes of the sharp filter in a compact [Ny][M3][M1] block: kx < M1,
+// kz = 0..K3 then -K3..-1 (M3 = 2 K3 + 1).
+__global__ void k_gather_retained(const double2* __restrict__ src, double2* dst, int Ny, int Nz, int nxh, int M1,
+                                  int M3) {
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t n = (size_t)Ny * M3 * M1;
+  if (e >= n) return;
+  const int j1 = (int)(e % M1);
+  const size_t t = e / M1;
+  const int j3 = (int)(t % M3);
+  const int y = (int)(t / M3);
+  const int K3 = (M3 - 1) / 2;
+  const int jz = j3 <= K3 ? j3 : Nz - (M3 - j3);
+  dst[e] = src[((size_t)y * Nz + jz) * nxh + j1];
+}
+
+// E_i(k1, y, k3) = w |u_i|^2 (w = 2 for kx > 0 counts the conjugate), mean mode excluded.
+__global__ void k_spectra(const double2* __restrict__ u1, const double2* __restrict__ v,
+                          const double2* __restrict__ u3, double* E, size_t n, int M, int nxh) {
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const int m = (int)(e % M);
+  const double w = m == 0 ? 0.0 : ((m % nxh) == 0 ? 1.0 : 2.0);
+  const double2 a = u1[e], b = v[e], c = u3[e];
+  E[e] = w * (a.x * a.x + a.y * a.y);
+  E[n + e] = w * (b.x * b.x + b.y * b.y);
+  E[2 * n + e] = w * (c.x * c.x + c.y * c.y);
+}
+
 struct StatArgs {
   const double2* u[3];
   const double2* ub[3];
@@ -121,6 +150,18 @@ cudaError_t launch_filter_out(chan_s* h, const double2* const* u, const double2*
 cudaError_t launch_apply_G(chan_s* h, const double2* in, double2* out) {
   const size_t n = (size_t)h->Ny * h->M;
   k_apply_G<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(in, h->G, out, n, h->M);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_retained(chan_s* h, const double2* src, double2* dst, int M1, int M3) {
+  const size_t n = (size_t)h->Ny * M3 * M1;
+  k_gather_retained<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(src, dst, h->Ny, h->Nz, h->nxh, M1, M3);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_spectra(chan_s* h, const double2* u1, const double2* u3, double* E) {
+  const size_t n = (size_t)h->Ny * h->M;
+  k_spectra<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(u1, h->v, u3, E, n, h->M, h->nxh);
   return cudaGetLastError();
 }
 

@@ -152,6 +152,22 @@ def test_filtered_enstrophy_parity(chan, kind, p, ten_steps):
     assert rel(ens, O.filtered_enstrophy(st, ref, kind, *p)) < TOL
 
 
+def test_database_record_and_spectra_parity(chan, ten_steps):
+    name = "re180_32x49x32"
+    st = setup(name)
+    s0, ref = ten_steps[name]
+    ch = make(chan, name)
+    ch.set_state(s0["v"], s0["omega2"], s0["U1"], s0["U3"])
+    ch.step(10)
+    rec = ch.database_record(120.0, 60.0)
+    rec_ref = O.database_record(st, ref, 120.0, 60.0)
+    assert rec.shape == rec_ref.shape
+    for f in range(10):
+        assert rel(rec[f], rec_ref[f]) < TOL, (f, rel(rec[f], rec_ref[f]))
+    E = ch.spectra()
+    assert rel(E, O.spectra(st, ref)) < TOL
+
+
 def test_poiseuille_steady_gpu(chan):
     name = "re180_32x49x32"
     s0 = ic(name, amp=0.0)

@@ -342,3 +342,31 @@ def test_filtered_enstrophy_mean_is_parseval(c1, c1_run):
     G = O.filter_transfer(c1, O.SHARP, 120, 60)
     ens_s = O.filtered_enstrophy(c1, S, O.SHARP, 120, 60)
     assert np.abs(ens_s[:, ~(G > 0)]).max() == 0.0     # the sharp filter removes the cut modes exactly
+
+
+def test_database_record_holds_exactly_the_retained_modes(c1, c1_run):
+    """The compact record's modes are exactly those the sharp filter keeps, and its
+    filtered fields are the filtered fields (Sec. 3.1, Eq. (fou_fil))."""
+    _, S = c1_run
+    G = O.filter_transfer(c1, O.SHARP, 120, 60)
+    m1, K3 = O.retained_modes(c1, 120, 60)
+    assert int((G > 0).sum()) == m1 * (2 * K3 + 1)
+    rec = O.database_record(c1, S, 120, 60)
+    ub, tau = O.filter_stresses(c1, S, O.SHARP, 120, 60)
+    jz = list(range(K3 + 1)) + [c1.Nz - k for k in range(K3, 0, -1)]
+    assert np.array_equal(rec[1], ub[1][:, jz, :m1])
+    # filt(u_i u_j) - ubar_i ubar_j is tau on the retained modes
+    u1, v, u3, _, _, _ = O.velocities(c1, S)
+    pb = [O.to_physical(c1, f) for f in ub]
+    for p, (i, j) in enumerate(O.PAIRS):
+        bb = O.to_fourier(c1, pb[i] * pb[j])[:, jz, :m1]
+        assert np.abs(rec[3 + p] - bb - tau[p][:, jz, :m1]).max() < 1e-12 * np.abs(rec[3 + p]).max()
+
+
+def test_spectra_sum_to_the_variances(c1, c1_run):
+    """Parseval: the spectrum summed over modes is <u_i u_i> - U_i^2 at every height."""
+    _, S = c1_run
+    E = O.spectra(c1, S)
+    out, _, _ = O.stats(c1, S)
+    var = out[2:5] - np.array([S["U1"] ** 2, 0 * S["U1"], S["U3"] ** 2])
+    assert np.abs(E.sum(axis=(2, 3)) - var).max() < 1e-12 * np.abs(out[2:5]).max()
