@@ -41,6 +41,7 @@ T* dalloc(chan_s* h, size_t n) {
   void* p = nullptr;
   cudaError_t e = cudaMalloc(&p, n * sizeof(T));
   if (e != cudaSuccess) {
+    cudaGetLastError();   // a failed allocation must not surface later as a launch error
     h->err = std::string("cudaMalloc of ") + std::to_string(n * sizeof(T)) + " bytes: " + cudaGetErrorString(e);
     throw Fail{CHAN_ENOMEM};
   }

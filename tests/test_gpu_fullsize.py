@@ -60,11 +60,10 @@ def test_fullsize_nonlinear_sampled_planes(big):
         assert rel(H[f][planes], ref[f]) < 1e-12, (f, rel(H[f][planes], ref[f]))
 
 
-def test_fullsize_one_substep_sampled_modes(big):
+@pytest.fixture(scope="module")
+def one_substep_ref(big):
+    """The oracle's first substep on sampled modes (H of every plane, chunk by chunk)."""
     st, s0, S, ch = big
-    ch.set_state(s0["v"], s0["omega2"], s0["U1"], s0["U3"])
-    ch.step(1)
-    g = ch.get_state()
     vel = O.velocities(st, S)
     H = [np.zeros_like(S["v"]) for _ in range(3)]
     for c0 in range(0, st.Ny, 32):
@@ -83,11 +82,29 @@ def test_fullsize_one_substep_sampled_modes(big):
     Ss = dict(S, v=sub(S["v"]), omega2=sub(S["omega2"]), chi=sub(S["chi"]),
               Nchi_prev=sub(S["Nchi_prev"]), Nom_prev=sub(S["Nom_prev"]))
     om, chi, v = O.channel.implicit_step(sts, Ss, sub(Nchi), sub(Nom), 0)
-    assert rel(sub(g["v"]), v) < TOL
-    assert rel(sub(g["omega2"]), om) < TOL
     U1, U3, f = O.channel.mean_flow_step(st, S, H[0][:, 0, 0].real, H[2][:, 0, 0].real, 0)
-    assert rel(g["U1"], U1) < TOL
-    assert np.abs(g["U3"] - U3).max() < TOL * np.abs(U1).max()
+    return sub, dict(v=v, omega2=om, U1=U1, U3=U3)
+
+
+@pytest.mark.parametrize("prec,tol", [(0, TOL), (2, TOL), (1, 1e-5)])
+def test_fullsize_one_substep_sampled_modes(big, one_substep_ref, prec, tol):
+    """One substep at full size against the oracle on sampled modes: FP64 and double-float
+    at the 1e-10 bar, mixed (FP32 transforms) at 1e-5."""
+    import torch
+    import paper_1808_06461_b300 as chan
+    st, s0, S, ch = big
+    sub, ref = one_substep_ref
+    if prec != 0:
+        ch = chan.Channel(*CFG, precision=prec, stream=torch.cuda.current_stream().cuda_stream)
+    ch.set_state(s0["v"], s0["omega2"], s0["U1"], s0["U3"])
+    ch.step(1)
+    g = ch.get_state()
+    if prec != 0:
+        ch.close()
+    assert rel(sub(g["v"]), ref["v"]) < tol
+    assert rel(sub(g["omega2"]), ref["omega2"]) < tol
+    assert rel(g["U1"], ref["U1"]) < tol
+    assert np.abs(g["U3"] - ref["U3"]).max() < tol * np.abs(ref["U1"]).max()
 
 
 def test_fullsize_invariants_after_substeps(big):
