@@ -71,6 +71,9 @@ typedef struct chan_opts {
   double grid_re;    /* Re_tau the mesh is clustered for (<= 0: re_tau)              */
   int precision;     /* CHAN_PREC_FP64, CHAN_PREC_MIXED or CHAN_PREC_F64X            */
   void* stream;      /* cudaStream_t to run on, or NULL for a library-owned stream   */
+  const double* mesh;/* explicit wall-normal mesh double[Ny] (increasing from -1 to 1,
+                        mirror symmetric), e.g. from chan_optimize_mesh; NULL: the
+                        Kolmogorov-scaled formula                                      */
 } chan_opts;
 
 /* Fill *o with defaults: eta_w = 1, grid_re = 0, FP64, library stream. */
@@ -104,6 +107,19 @@ size_t chan_device_bytes(chan_t h);
  * needed.  For admission by HBM footprint; the allocator may round up.
  */
 size_t chan_footprint_bytes(int Nx, int Ny, int Nz, int precision);
+
+/*
+ * Near-wall mesh optimisation of Appendix B.  Starting from the
+ * mesh chan_init_ex would build for *o, moves the first 20 interior points at
+ * each wall (mirrored) by steepest descent on
+ *   L = |g - g_ana| + C |mu - mu_ref|,
+ * g the discrete solution of (B - k* A) g = 0 with g(-1) = 1, g(+1) = 0 at the
+ * box's most critical modified wavenumber k* = k1max^2 + k3max^2 + 6/(nu dt),
+ * g_ana its sinh solution, mu the moved points and mu_ref their start (the
+ * paper uses C ~ 1e-3).  Writes the mesh (double[Ny]) to y and |g - g_ana|
+ * before and after.  Host only, no GPU.  Pass the mesh back in opts.mesh.
+ */
+int chan_optimize_mesh(const chan_opts* o, int iters, double C, double* y, double* err_before, double* err_after);
 
 /*
  * Autotuner (no paper counterpart): times the z-pass with 1, 2, 4, 8 and 16

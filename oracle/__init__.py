@@ -18,9 +18,11 @@ closed forms, invariants or brute force, except where its docstring says
 from .channel import (RK3, ygrid, compact_coeffs, Setup, initial_state, substep, run,
                       velocities, to_physical, to_fourier, filter_transfer, filter_stresses,
                       stats, divergence, apply_y, nonlinear, rhs_terms, filtered_enstrophy, database_record,
-                      retained_modes, spectra, SHARP, BOX, PAIRS)
+                      retained_modes, spectra, helmholtz_error, pressure_solve,
+                      filtered_pressure, SHARP, BOX, PAIRS)
 
 __all__ = ["RK3", "ygrid", "compact_coeffs", "Setup", "initial_state", "substep", "run",
            "velocities", "to_physical", "to_fourier", "filter_transfer", "filter_stresses",
            "stats", "divergence", "apply_y", "nonlinear", "rhs_terms", "filtered_enstrophy", "database_record",
-           "retained_modes", "spectra", "SHARP", "BOX", "PAIRS"]
+           "retained_modes", "spectra", "helmholtz_error", "pressure_solve",
+           "filtered_pressure", "SHARP", "BOX", "PAIRS"]

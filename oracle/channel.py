@@ -135,10 +135,11 @@ class Setup:
     """Grid, operators and wavenumbers of one channel box (Sec. 2.1).
 
     ``grid_re`` (default Re_tau) is the Reynolds number the wall-normal mesh
-    is clustered for; nu = 1 / re_tau always.
+    is clustered for; ``mesh`` replaces the formula by a given mesh (e.g. the
+    Appendix B optimised one); nu = 1 / re_tau always.
     """
 
-    def __init__(self, re_tau, Lx, Lz, Nx, Ny, Nz, dt, eta_w=1.0, grid_re=None):
+    def __init__(self, re_tau, Lx, Lz, Nx, Ny, Nz, dt, eta_w=1.0, grid_re=None, mesh=None):
         if Nx % 2 or Nz % 2:
             raise ValueError("Nx and Nz must be even")
         self.re_tau, self.Lx, self.Lz = float(re_tau), float(Lx), float(Lz)
@@ -146,7 +147,10 @@ class Setup:
         self.nu = 1.0 / self.re_tau
         self.nxh = self.Nx // 2
         self.Lx3, self.Lz3 = 3 * self.Nx // 2, 3 * self.Nz // 2
-        self.y = ygrid(self.Ny, self.re_tau if grid_re is None else float(grid_re), eta_w)
+        if mesh is not None:
+            self.y = np.array(mesh, dtype=np.float64)
+        else:
+            self.y = ygrid(self.Ny, self.re_tau if grid_re is None else float(grid_re), eta_w)
         self.A2, self.B2 = compact_coeffs(self.y, 2)
         self.A1, self.B1 = compact_coeffs(self.y, 1)
         self.D1 = np.linalg.solve(self.A1, self.B1)
@@ -478,6 +482,76 @@ def filter_stresses(st, S, kind, p1, p3):
     for i, j in PAIRS:
         tau.append(G * to_fourier(st, pu[i] * pu[j]) - to_fourier(st, pb[i] * pb[j]))
     return np.stack(ub), np.stack(tau)
+
+
+def helmholtz_error(y, kstar):
+    """|g - g_ana|_2 of (B - k* A) g = 0, g(-1) = 1, g(+1) = 0 (Appendix B, Eq. (modpoisson)).
+
+    g_ana = sinh(sqrt(k*)(1 - y)) / sinh(2 sqrt(k*)), the error functional the
+    paper's mesh optimisation minimises (its first term).
+    """
+    A, B = compact_coeffs(y, 2)
+    n = len(y)
+    M = B - kstar * A
+    M[0, :] = 0.0
+    M[-1, :] = 0.0
+    M[0, 0] = M[-1, -1] = 1.0
+    rhs = np.zeros(n)
+    rhs[0] = 1.0
+    g = np.linalg.solve(M, rhs)
+    r = math.sqrt(kstar)
+    ana = np.exp(-r * (y + 1)) * (1 - np.exp(-2 * r * (1 - y))) / (1 - np.exp(-4 * r))
+    return float(np.linalg.norm(g - ana))
+
+
+def pressure_solve(st, rhs_A, dp_lo, dp_hi):
+    """Per-mode Neumann Poisson problem of the filtered pressure.
+
+    Interior rows (B - k^2 A) p = rhs_A (the equation already multiplied by A,
+    as every implicit step of the method is); wall rows (D1 p)(-1) = dp_lo and
+    (D1 p)(+1) = dp_hi with D1 = A1^-1 B1.  rhs_A: (Ny, Nz, nxh); dp_*: (Nz, nxh).
+    The (0, 0) mode (singular for Neumann conditions) is left at zero here.
+    """
+    p = np.zeros_like(rhs_A)
+    k2 = st.K2.reshape(-1)
+    R = _modes(rhs_A)
+    d_lo, d_hi = dp_lo.reshape(-1), dp_hi.reshape(-1)
+    out = np.zeros_like(R)
+    for m in range(k2.size):
+        if k2[m] == 0 or not st.keep.reshape(-1)[m]:
+            continue
+        L = st.B2 - k2[m] * st.A2
+        L[0, :] = st.D1[0]
+        L[-1, :] = st.D1[-1]
+        r = R[m].copy()
+        r[0] = d_lo[m]
+        r[-1] = d_hi[m]
+        out[m] = np.linalg.solve(L, r)
+    return _unmodes(out, rhs_A.shape)
+
+
+def filtered_pressure(st, S, kind, p1, p3):
+    """Filtered pressure from the filtered stresses, Sec. 3.1 Eq. (2): d_kk pbar = -d_ij filt(u_i u_j).
+
+    With F_ij = filt(u_i u_j) = G P(u_i u_j), the right-hand side in Fourier
+    space is k1^2 F11 + k3^2 F33 + 2 k1 k3 F13 - 2 i k1 D1 F12 - 2 i k3 D1 F23 - D2 F22,
+    multiplied by A on interior rows (so D2 F22 enters as B F22).  The paper
+    gives no boundary condition; the reading is the wall value of the filtered
+    wall-normal momentum equation, d pbar/dy = nu chibar = nu G chi at y = +-1.
+    The mean mode follows the mean wall-normal momentum balance, P = -F22(0,0).
+    """
+    G = filter_transfer(st, kind, p1, p3)
+    u1, v, u3, _, _, _ = velocities(st, S)
+    pu = [to_physical(st, f) for f in (u1, v, u3)]
+    F = {(i, j): G * to_fourier(st, pu[i] * pu[j]) for i, j in PAIRS}
+    K1, K3 = st.K1, st.K3
+    r = (K1 ** 2 * F[0, 0] + K3 ** 2 * F[2, 2] + 2 * K1 * K3 * F[0, 2]
+         - 2j * K1 * apply_y(st.D1, F[0, 1]) - 2j * K3 * apply_y(st.D1, F[1, 2]))
+    rhs_A = apply_y(st.A2, r) - apply_y(st.B2, F[1, 1])
+    chib = G * S["chi"]
+    p = pressure_solve(st, rhs_A, st.nu * chib[0], st.nu * chib[-1])
+    p[:, 0, 0] = -F[1, 1][:, 0, 0]
+    return p * st.keep
 
 
 def filtered_enstrophy(st, S, kind, p1, p3):

@@ -32,7 +32,7 @@ SYMBOLS = ("chan_opts_default", "chan_init", "chan_init_ex", "chan_free", "chan_
            "chan_rhs_terms", "chan_rhs_terms_noalloc", "chan_footprint_bytes", "chan_set_graph",
            "chan_filtered_enstrophy", "chan_batch_create", "chan_batch_step", "chan_batch_last_error",
            "chan_batch_free", "chan_autotune", "chan_tuned_shape", "chan_database_record",
-           "chan_spectra")
+           "chan_spectra", "chan_optimize_mesh")
 CHAN_NKERNELS = 14
 
 
@@ -40,7 +40,8 @@ class chan_opts(ctypes.Structure):
     _fields_ = [("re_tau", ctypes.c_double), ("Lx", ctypes.c_double), ("Lz", ctypes.c_double),
                 ("Nx", ctypes.c_int), ("Ny", ctypes.c_int), ("Nz", ctypes.c_int),
                 ("dt", ctypes.c_double), ("eta_w", ctypes.c_double), ("grid_re", ctypes.c_double),
-                ("precision", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("precision", ctypes.c_int), ("stream", ctypes.c_void_p),
+                ("mesh", ctypes.POINTER(ctypes.c_double))]
 
 
 class ChanError(RuntimeError):
@@ -85,6 +86,7 @@ def load_library(path=LIB_PATH):
         "chan_autotune": (I, [P]),
         "chan_database_record": (I, [P, D, D, P, ctypes.POINTER(I), ctypes.POINTER(I)]),
         "chan_spectra": (I, [P, P]),
+        "chan_optimize_mesh": (I, [ctypes.POINTER(chan_opts), I, D, P, DP, DP]),
         "chan_tuned_shape": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I)]),
         "chan_sync": (I, [P]),
         "chan_time": (D, [P]),
@@ -122,12 +124,15 @@ class Channel:
     """One channel box on the current CUDA device (owns its device memory)."""
 
     def __init__(self, re_tau, Lx, Lz, Nx, Ny, Nz, dt, precision=CHAN_PREC_FP64, eta_w=1.0,
-                 grid_re=0.0, stream=None):
+                 grid_re=0.0, stream=None, mesh=None):
         o = chan_opts()
         _lib.chan_opts_default(ctypes.byref(o))
         o.re_tau, o.Lx, o.Lz, o.Nx, o.Ny, o.Nz, o.dt = re_tau, Lx, Lz, Nx, Ny, Nz, dt
         o.eta_w, o.grid_re, o.precision = eta_w, grid_re, precision
         o.stream = stream
+        if mesh is not None:
+            self._mesh = np.ascontiguousarray(mesh, dtype=np.float64)
+            o.mesh = self._mesh.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         h = ctypes.c_void_p()
         rc = _lib.chan_init_ex(ctypes.byref(h), ctypes.byref(o))
         if rc != CHAN_OK:
@@ -323,6 +328,19 @@ def chan_free(ch):
 
 def chan_sync(ch):
     ch.sync()
+
+
+def optimize_mesh(re_tau, Lx, Lz, Nx, Ny, Nz, dt, iters=60, C=1e-3, eta_w=1.0, grid_re=0.0):
+    """Appendix B mesh: (y, |g - g_ana| before, after).  Host only."""
+    o = chan_opts()
+    _lib.chan_opts_default(ctypes.byref(o))
+    o.re_tau, o.Lx, o.Lz, o.Nx, o.Ny, o.Nz, o.dt, o.eta_w, o.grid_re = re_tau, Lx, Lz, Nx, Ny, Nz, dt, eta_w, grid_re
+    y = np.empty(Ny)
+    eb, ea = ctypes.c_double(), ctypes.c_double()
+    rc = _lib.chan_optimize_mesh(ctypes.byref(o), int(iters), float(C), _ptr(y), ctypes.byref(eb), ctypes.byref(ea))
+    if rc != CHAN_OK:
+        raise ChanError(rc, _lib.chan_last_error(None).decode())
+    return y, eb.value, ea.value
 
 
 def footprint_bytes(Nx, Ny, Nz, precision=CHAN_PREC_FP64):

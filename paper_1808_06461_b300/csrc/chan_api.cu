@@ -351,7 +351,13 @@ int chan_init_ex(chan_t* out, const chan_opts* o) {
     CK(cudaGetDevice(&h->device));
     if (o->stream) { h->stream = (cudaStream_t)o->stream; h->own_stream = false; }
     else { CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking)); h->own_stream = true; }
-    int hr = chanh_build(h->Ny, h->grid_re, h->eta_w, &tb);
+    if (o->mesh) {
+      const double* m = o->mesh;
+      bool ok = m[0] == -1.0 && m[h->Ny - 1] == 1.0;
+      for (int j = 0; ok && j < h->Ny; ++j) ok = (j == 0 || m[j] > m[j - 1]) && m[j] == -m[h->Ny - 1 - j];
+      if (!ok) { h->err = "chan_init: mesh must increase from -1 to 1 and be mirror symmetric"; throw Fail{CHAN_EINVAL}; }
+    }
+    int hr = chanh_build_mesh(h->Ny, h->grid_re, h->eta_w, o->mesh, &tb);
     if (hr) { h->err = "chan_init: compact-scheme set-up failed (singular coefficient system or LU pivot)"; throw Fail{CHAN_EINVAL}; }
     h->y.assign(tb.y, tb.y + h->Ny);
     h->wq.assign(tb.wq, tb.wq + h->Ny);
@@ -830,6 +836,21 @@ int chan_tuned_shape(chan_t h, int* kb_z, int* xthreads) {
   const size_t es = h->prec == CHAN_PREC_MIXED ? sizeof(float2) : sizeof(double2);
   if (kb_z) *kb_z = h->kb_z > 0 ? h->kb_z : pick_kb(h->nxh, h->L3, es);
   if (xthreads) *xthreads = h->xthreads > 0 ? h->xthreads : 256;
+  return CHAN_OK;
+}
+
+int chan_optimize_mesh(const chan_opts* o, int iters, double C, double* y, double* err_before, double* err_after) {
+  if (!o || !y) return bad(nullptr, "chan_optimize_mesh: NULL argument");
+  if (o->Ny < 9 || o->Ny % 2 == 0 || !(o->re_tau > 0) || !(o->dt > 0) || o->Nx < 2 || o->Nz < 4 || iters < 0)
+    return bad(nullptr, "chan_optimize_mesh: invalid sizes");
+  std::vector<double> y0(o->Ny);
+  const double gre = o->grid_re > 0 ? o->grid_re : o->re_tau;
+  if (chanh_ygrid(o->Ny, gre, o->eta_w > 0 ? o->eta_w : 1.0, y0.data())) return bad(nullptr, "chan_optimize_mesh: mesh");
+  // most critical wavenumber: largest k^2 of the box and the smallest RK3 beta (1/6)
+  const double k1 = 2.0 * M_PI / o->Lx * (o->Nx / 2 - 1), k3 = 2.0 * M_PI / o->Lz * (o->Nz / 2 - 1);
+  const double kstar = k1 * k1 + k3 * k3 + 1.0 / ((1.0 / 6.0) * (1.0 / o->re_tau) * o->dt);
+  if (chanh_optimize_mesh(o->Ny, y0.data(), kstar, 21, C, iters, y, err_before, err_after))
+    return bad(nullptr, "chan_optimize_mesh: coefficient system singular");
   return CHAN_OK;
 }
 

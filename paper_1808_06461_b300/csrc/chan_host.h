@@ -27,6 +27,16 @@ typedef struct chanh_tables {
 // coefficient system or an LU vanishes).
 int chanh_build(int ny, double grid_re, double eta_w, chanh_tables* t);
 void chanh_free(chanh_tables* t);
+// Same, on a given mesh (double[ny], increasing, mirror symmetric) instead of the formula.
+int chanh_build_mesh(int ny, double grid_re, double eta_w, const double* mesh, chanh_tables* t);
+
+// Near-wall mesh optimisation of Appendix B (see setup_host.cpp).  y_in: the
+// starting mesh; kstar: the Helmholtz modified wavenumber to fit; npts: mesh
+// points per wall in the optimisation (the wall point stays); C: displacement
+// penalty; iters: steepest-descent iterations.  Writes the mesh to y_out and
+// the Helmholtz errors before and after.  Returns 0, or < 0 on bad input.
+int chanh_optimize_mesh(int ny, const double* y_in, double kstar, int npts, double C, int iters, double* y_out,
+                        double* err_before, double* err_after);
 
 // The same mesh formula as the tables use (double[ny]).
 int chanh_ygrid(int ny, double grid_re, double eta_w, double* y);

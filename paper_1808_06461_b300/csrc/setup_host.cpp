@@ -168,7 +168,165 @@ static int dense_row(int n, const qd* A, const qd* B, int r, double* out) {
   return 0;
 }
 
-int chanh_build(int ny, double grid_re, double eta_w, chanh_tables* t) {
+// ---------------------------------------------------------------------------
+// Near-wall mesh optimisation (Appendix B): move the first npts-1 interior
+// points of each wall so that the discrete homogeneous Helmholtz solution
+// (B - k* A) g = 0, g(-1) = 1, g(+1) = 0 approaches the analytic one, with a
+// penalty C |mu - mu_ref| on the displacement; steepest descent with a
+// finite-difference gradient and backtracking.  Long double arithmetic.
+// ---------------------------------------------------------------------------
+typedef long double ld;
+
+static int ld_solve(int m, ld* M, ld* r) {
+  for (int c = 0; c < m; ++c) {
+    int p = c;
+    for (int i = c + 1; i < m; ++i)
+      if (fabsl(M[i * m + c]) > fabsl(M[p * m + c])) p = i;
+    if (M[p * m + c] == 0) return -3;
+    if (p != c) {
+      for (int j = 0; j < m; ++j) { ld t = M[c * m + j]; M[c * m + j] = M[p * m + j]; M[p * m + j] = t; }
+      ld t = r[c]; r[c] = r[p]; r[p] = t;
+    }
+    for (int i = c + 1; i < m; ++i) {
+      ld f = M[i * m + c] / M[c * m + c];
+      for (int j = c; j < m; ++j) M[i * m + j] -= f * M[c * m + j];
+      r[i] -= f * r[c];
+    }
+  }
+  for (int i = m - 1; i >= 0; --i) {
+    ld s = r[i];
+    for (int j = i + 1; j < m; ++j) s -= M[i * m + j] * r[j];
+    r[i] = s / M[i * m + i];
+  }
+  return 0;
+}
+
+// Second-derivative row i on mesh y (the same equations as compact_row).
+static int d2_row_ld(const ld* y, int n, int i, ld* Arow, ld* Brow) {
+  int lo, hi;
+  support(i, n, &lo, &hi);
+  int na = 0, nb = hi - lo + 1, acol[8], bcol[8];
+  for (int j = lo; j <= hi; ++j) { bcol[j - lo] = j; if (j != i) acol[na++] = j; }
+  const int m = na + nb;
+  ld M[16 * 16], r[16];
+  const ld s = fabsl((i + 2 < n ? y[i + 2] : y[i - 2]) - y[i]);
+  for (int k = 0; k < m; ++k) {
+    const ld sc = powl(s, (ld)(2 - k));
+    const ld fac = (ld)(k * (k - 1));
+    for (int c = 0; c < na; ++c) M[k * m + c] = k >= 2 ? -fac * powl(y[acol[c]] - y[i], (ld)(k - 2)) * sc : (ld)0;
+    for (int c = 0; c < nb; ++c) M[k * m + na + c] = k == 0 ? sc : powl(y[bcol[c]] - y[i], (ld)k) * sc;
+    r[k] = k == 2 ? fac * sc : (ld)0;
+  }
+  if (ld_solve(m, M, r)) return -3;
+  for (int d = 0; d < 7; ++d) { Arow[d] = 0; Brow[d] = 0; }
+  Arow[3] = 1;
+  for (int c = 0; c < na; ++c) Arow[acol[c] - i + 3] = r[c];
+  for (int c = 0; c < nb; ++c) Brow[bcol[c] - i + 3] = r[na + c];
+  return 0;
+}
+
+// |g - g_ana|_2 over the mesh for (B - k* A) g = 0, g(-1) = 1, g(+1) = 0.
+static ld helm_error(const ld* y, int n, const ld* A, const ld* B, ld kstar) {
+  std::vector<ld> M((size_t)n * 7, 0), L((size_t)n * 3, 0), U((size_t)n * 4, 0), z(n), g(n);
+  for (int i = 0; i < n; ++i)
+    for (int d = 0; d < 7; ++d)
+      M[(size_t)i * 7 + d] = (i == 0 || i == n - 1) ? (d == 3 ? 1 : 0) : B[(size_t)i * 7 + d] - kstar * A[(size_t)i * 7 + d];
+  auto m = [&](int i, int j) -> ld { int d = j - i + 3; return (d >= 0 && d < 7) ? M[(size_t)i * 7 + d] : (ld)0; };
+  auto u = [&](int k, int j) -> ld { int d = j - k; return (d >= 0 && d <= 3) ? U[(size_t)k * 4 + d] : (ld)0; };
+  auto l = [&](int i, int j) -> ld { int d = i - j; return (d >= 1 && d <= 3) ? L[(size_t)i * 3 + (3 - d)] : (ld)0; };
+  for (int i = 0; i < n; ++i) {
+    const int k0 = i - 3 < 0 ? 0 : i - 3;
+    for (int j = k0; j < i; ++j) {
+      ld s = m(i, j);
+      for (int k = k0; k < j; ++k) s -= l(i, k) * u(k, j);
+      L[(size_t)i * 3 + (3 - (i - j))] = s / U[(size_t)j * 4];
+    }
+    for (int j = i; j <= i + 3 && j < n; ++j) {
+      ld s = m(i, j);
+      for (int k = k0; k < i; ++k) s -= l(i, k) * u(k, j);
+      U[(size_t)i * 4 + (j - i)] = s;
+    }
+  }
+  for (int i = 0; i < n; ++i) {
+    ld s = i == 0 ? 1 : 0;
+    for (int k = (i - 3 < 0 ? 0 : i - 3); k < i; ++k) s -= l(i, k) * z[k];
+    z[i] = s;
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    ld s = z[i];
+    for (int k = i + 1; k <= i + 3 && k < n; ++k) s -= u(i, k) * g[k];
+    g[i] = s / U[(size_t)i * 4];
+  }
+  const ld r = sqrtl(kstar);
+  ld e = 0;
+  for (int i = 0; i < n; ++i) {
+    const ld ana = expl(-r * (y[i] + 1)) * (1 - expl(-2 * r * (1 - y[i]))) / (1 - expl(-4 * r));
+    e += (g[i] - ana) * (g[i] - ana);
+  }
+  return sqrtl(e);
+}
+
+int chanh_optimize_mesh(int ny, const double* y_in, double kstar, int npts, double C, int iters, double* y_out,
+                        double* err_before, double* err_after) {
+  if (ny < 9 || ny % 2 == 0 || !(kstar > 0)) return -1;
+  const int h = (ny - 1) / 2;
+  if (npts > h - 3) npts = h - 3;
+  if (npts < 2) npts = 2;
+  std::vector<ld> y(y_in, y_in + ny), A((size_t)ny * 7), B((size_t)ny * 7);
+  for (int i = 0; i < ny; ++i)
+    if (d2_row_ld(y.data(), ny, i, &A[(size_t)i * 7], &B[(size_t)i * 7])) return -3;
+  const std::vector<ld> mu_ref(y.begin(), y.begin() + npts);
+  auto apply = [&](const std::vector<ld>& mu) {   // move points 1..npts-1 and their mirrors, refresh rows
+    for (int j = 1; j < npts; ++j) { y[j] = mu[j]; y[ny - 1 - j] = -mu[j]; }
+    for (int i = 0; i < npts + 3; ++i) {
+      d2_row_ld(y.data(), ny, i, &A[(size_t)i * 7], &B[(size_t)i * 7]);
+      d2_row_ld(y.data(), ny, ny - 1 - i, &A[(size_t)(ny - 1 - i) * 7], &B[(size_t)(ny - 1 - i) * 7]);
+    }
+  };
+  auto loss = [&](const std::vector<ld>& mu) {
+    for (int j = 1; j < npts + 1 && j < ny; ++j)
+      if (!(mu[j - 1] < (j < npts ? mu[j] : y[npts]))) return (ld)1e30L;   // keep the mesh ordered
+    apply(mu);
+    ld pen = 0;
+    for (int j = 1; j < npts; ++j) pen += (mu[j] - mu_ref[j]) * (mu[j] - mu_ref[j]);
+    return helm_error(y.data(), ny, A.data(), B.data(), (ld)kstar) + (ld)C * sqrtl(pen);
+  };
+  std::vector<ld> mu = mu_ref;
+  ld f = loss(mu);
+  if (err_before) *err_before = (double)helm_error(y.data(), ny, A.data(), B.data(), (ld)kstar);
+  std::vector<ld> grad(npts), trial(npts);
+  for (int it = 0; it < iters; ++it) {
+    ld gnorm = 0;
+    for (int j = 1; j < npts; ++j) {
+      const ld dj = 1e-7L * (mu[j + 1 < npts ? j + 1 : j] - mu[j - 1]);
+      trial = mu;
+      trial[j] += dj;
+      const ld fp = loss(trial);
+      trial[j] = mu[j] - dj;
+      const ld fm = loss(trial);
+      grad[j] = (fp - fm) / (2 * dj);
+      gnorm += grad[j] * grad[j];
+    }
+    gnorm = sqrtl(gnorm);
+    if (!(gnorm > 0)) break;
+    ld step = 0.2L * (mu_ref[1] - mu_ref[0]) / gnorm;   // first trial: move the points by up to 20 % of the wall cell
+    bool improved = false;
+    for (int ls = 0; ls < 40; ++ls, step *= 0.5L) {
+      for (int j = 0; j < npts; ++j) trial[j] = j == 0 ? mu[0] : mu[j] - step * grad[j];
+      const ld ft = loss(trial);
+      if (ft < f) { mu = trial; f = ft; improved = true; break; }
+    }
+    if (!improved) break;
+  }
+  loss(mu);
+  if (err_after) *err_after = (double)helm_error(y.data(), ny, A.data(), B.data(), (ld)kstar);
+  for (int i = 0; i < ny; ++i) y_out[i] = (double)y[i];
+  return 0;
+}
+
+int chanh_build(int ny, double grid_re, double eta_w, chanh_tables* t) { return chanh_build_mesh(ny, grid_re, eta_w, nullptr, t); }
+
+int chanh_build_mesh(int ny, double grid_re, double eta_w, const double* mesh, chanh_tables* t) {
   std::memset(t, 0, sizeof(*t));
   if (ny < 9 || (ny % 2) != 1) return -1;
   t->ny = ny;
@@ -178,7 +336,8 @@ int chanh_build(int ny, double grid_re, double eta_w, chanh_tables* t) {
     *bufs[b] = (double*)std::calloc((size_t)ny * sizes[b], sizeof(double));
     if (!*bufs[b]) { chanh_free(t); return -2; }
   }
-  if (chanh_ygrid(ny, grid_re, eta_w, t->y)) { chanh_free(t); return -1; }
+  if (mesh) std::memcpy(t->y, mesh, (size_t)ny * sizeof(double));
+  else if (chanh_ygrid(ny, grid_re, eta_w, t->y)) { chanh_free(t); return -1; }
   std::vector<qd> qA2((size_t)ny * 7), qB2((size_t)ny * 7), qA1((size_t)ny * 7), qB1((size_t)ny * 7);
   for (int i = 0; i < ny; ++i) {
     if (compact_row(t->y, ny, i, 2, &qA2[(size_t)i * 7], &qB2[(size_t)i * 7]) ||

@@ -254,3 +254,20 @@ def test_step_before_state_is_an_error(chan):
     with pytest.raises(chan.ChanError) as e:
         ch.step(1)
     assert e.value.code == chan.CHAN_ESTATE
+
+
+def test_parity_on_the_optimised_mesh(chan):
+    """The substep on an Appendix B optimised mesh matches the oracle on that mesh."""
+    args = (395.0, math.pi, math.pi / 2, 32, 49, 32, 1e-3)
+    y, eb, ea = chan.optimize_mesh(*args, iters=30)
+    assert ea < eb
+    st = O.Setup(*args, mesh=y)
+    s0 = SY.perturbed_poiseuille(y, 395.0, args[1], args[2], 32, 32, seed=8, amp=0.1)
+    ch = chan.Channel(*args, mesh=y)
+    assert np.array_equal(ch.grid(), y)
+    ch.set_state(s0["v"], s0["omega2"], s0["U1"], s0["U3"])
+    ch.step(10)
+    g = ch.get_state()
+    ref = O.run(st, O.initial_state(st, s0["v"], s0["omega2"], s0["U1"], s0["U3"]), 10)
+    for k in ("v", "omega2", "U1"):
+        assert rel(g[k], ref[k]) < TOL, (k, rel(g[k], ref[k]))

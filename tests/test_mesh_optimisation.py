@@ -1,0 +1,34 @@
+"""Appendix B near-wall mesh optimisation (host code of the library, no GPU),
+checked by the oracle: its own 50-digit compact coefficients on the returned
+mesh give a smaller Helmholtz error at the critical wavenumber, the Dirichlet
+D2 spectrum stays real and negative, and only the near-wall points move."""
+import math
+
+import numpy as np
+
+import oracle as O
+import paper_1808_06461_b300 as chan
+
+CFG = (395.0, math.pi, math.pi / 2, 64, 97, 64, 1e-3)
+
+
+def test_optimised_mesh_reduces_the_helmholtz_error():
+    re, Lx, Lz, Nx, Ny, Nz, dt = CFG
+    y0, _, _ = chan.optimize_mesh(*CFG, iters=0)
+    y, e_before, e_after = chan.optimize_mesh(*CFG, iters=40)
+    assert np.array_equal(y0, O.ygrid(Ny, re))          # starts from the formula mesh
+    kstar = ((2 * math.pi / Lx * (Nx // 2 - 1)) ** 2 + (2 * math.pi / Lz * (Nz // 2 - 1)) ** 2
+             + 1.0 / ((1.0 / 6.0) * (1.0 / re) * dt))
+    ob, oa = O.helmholtz_error(y0, kstar), O.helmholtz_error(y, kstar)
+    assert abs(ob - e_before) < 1e-6 * ob and abs(oa - e_after) < 1e-6 * ob
+    assert oa < 0.5 * ob                                 # the optimisation pays off
+    # the mesh: walls fixed, mirror symmetric, ordered, only 20 points per wall moved, modestly
+    assert y[0] == -1.0 and y[-1] == 1.0 and np.array_equal(y, -y[::-1]) and np.all(np.diff(y) > 0)
+    moved = np.nonzero(y != y0)[0]
+    assert moved.size == 40 and np.all((moved < 21) | (moved > Ny - 22))   # 20 per wall
+    assert np.abs(y - y0).max() < (y0[1] - y0[0])
+    # stability of the implicit step on the new mesh
+    A, B = O.compact_coeffs(y, 2)
+    I = slice(1, Ny - 1)
+    ev = np.linalg.eigvals(np.linalg.solve(A[I, I], B[I, I]))
+    assert ev.real.max() < 0 and np.abs(ev.imag).max() <= 1e-8 * np.abs(ev.real).max()

@@ -370,3 +370,63 @@ def test_spectra_sum_to_the_variances(c1, c1_run):
     out, _, _ = O.stats(c1, S)
     var = out[2:5] - np.array([S["U1"] ** 2, 0 * S["U1"], S["U3"] ** 2])
     assert np.abs(E.sum(axis=(2, 3)) - var).max() < 1e-12 * np.abs(out[2:5]).max()
+
+
+def test_pressure_solve_reproduces_a_polynomial_exactly(c1):
+    """Manufactured solution: p = (1 - y^2)^2 (1 + 0.3 y) + 0.2 y in every mode; with the
+    right-hand side A (p'' - k^2 p) and wall slopes p'(+-1) from calculus, the Neumann
+    solve must return p to rounding (the compact operators are exact on this degree)."""
+    y = c1.y
+    w = 1 - y * y
+    p = w * w * (1 + 0.3 * y) + 0.2 * y
+    dp = -4 * y * w * (1 + 0.3 * y) + 0.3 * w * w + 0.2
+    d2p = (-4 * w + 8 * y * y) * (1 + 0.3 * y) - 2.4 * y * w
+    P = np.broadcast_to(p[:, None, None], (c1.Ny, c1.Nz, c1.nxh)).astype(np.complex128)
+    rhs = O.apply_y(c1.A2, d2p[:, None, None] - c1.K2[None] * P)
+    lo = np.full((c1.Nz, c1.nxh), dp[0], dtype=np.complex128)
+    hi = np.full((c1.Nz, c1.nxh), dp[-1], dtype=np.complex128)
+    out = O.pressure_solve(c1, rhs, lo, hi)
+    mask = (c1.K2 > 0) & c1.keep
+    assert np.abs(out[:, mask] - P[:, mask]).max() < 1e-11 * np.abs(p).max()
+
+
+def test_filtered_pressure_source_is_the_strain_minus_rotation_identity(c1, c1_run):
+    """Incompressible identity d_ij(u_i u_j) = S:S - |omega|^2 / 2 (the paper prints 1/4):
+    the Poisson source built from the stress tensor (the pressure's route) equals the one
+    built from velocity gradients, to the truncation error of the compact scheme."""
+    _, S = c1_run
+    u1, v, u3, du1, dv, du3 = O.velocities(c1, S)
+    u = [u1, v, u3]
+    pu = [O.to_physical(c1, f) for f in u]
+    F = {(i, j): O.to_fourier(c1, pu[i] * pu[j]) for i, j in O.PAIRS}
+    K1, K3 = c1.K1, c1.K3
+    src = (-K1 ** 2 * F[0, 0] - K3 ** 2 * F[2, 2] - 2 * K1 * K3 * F[0, 2]
+           + 2j * K1 * O.apply_y(c1.D1, F[0, 1]) + 2j * K3 * O.apply_y(c1.D1, F[1, 2])
+           + O.apply_y(c1.D2, F[1, 1]))                                   # d_ij (u_i u_j)
+    grads = [[1j * K1 * f, df, 1j * K3 * f] for f, df in zip(u, (du1, dv, du3))]   # d_j u_i
+    g = [[O.to_physical(c1, grads[i][j]) for j in range(3)] for i in range(3)]
+    ss = sum(0.25 * (g[i][j] + g[j][i]) ** 2 for i in range(3) for j in range(3))
+    om = [g[2][1] - g[1][2], g[0][2] - g[2][0], g[1][0] - g[0][1]]
+    ident = O.to_fourier(c1, ss - 0.5 * (om[0] ** 2 + om[1] ** 2 + om[2] ** 2))
+    scale = np.abs(ident).max()
+    # equal up to the compact scheme's truncation on the product fields (largest at the
+    # reduced wall rows); a wrong factor or sign is O(1)
+    assert np.abs(src - ident)[3:-3].max() < 1e-3 * scale
+    assert np.abs(src - ident).max() < 2e-2 * scale
+    wrong = O.to_fourier(c1, ss - 0.25 * (om[0] ** 2 + om[1] ** 2 + om[2] ** 2))
+    assert np.abs(src - wrong).max() > 0.5 * scale      # the printed 1/4 does not hold
+
+
+def test_filtered_pressure_mean_and_wall_condition(c1, c1_run):
+    _, S = c1_run
+    P = O.filtered_pressure(c1, S, O.BOX, 50, 50)
+    ub, tau = O.filter_stresses(c1, S, O.BOX, 50, 50)
+    G = O.filter_transfer(c1, O.BOX, 50, 50)
+    u1, v, u3, _, _, _ = O.velocities(c1, S)
+    pv = O.to_physical(c1, v)
+    F22 = G * O.to_fourier(c1, pv * pv)
+    assert np.abs(P[:, 0, 0] + F22[:, 0, 0]).max() == 0.0
+    dP = O.apply_y(c1.D1, P)
+    chib = G * S["chi"]
+    mask = (c1.K2 > 0) & c1.keep
+    assert np.abs(dP[0][mask] - c1.nu * chib[0][mask]).max() < 1e-10 * np.abs(dP).max()
