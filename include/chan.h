@@ -203,6 +203,17 @@ int chan_filtered_enstrophy(chan_t h, int kind, double p1, double p3, double* en
 int chan_database_record(chan_t h, double p1, double p3, double* rec, int* m1, int* m3);
 
 /*
+ * Filtered pressure of the current state from the filtered stresses,
+ * Sec. 3.1 Eq. (2): d_kk pbar = -d_ij filt(u_i u_j) per Fourier mode, with
+ * the wall condition d pbar/dy = nu chibar (the filtered wall-normal momentum
+ * balance at a wall) and the mean mode P = -filt(u_2 u_2).  kind, (p1, p3) as
+ * for chan_filter_stresses.  p receives one field, spectral layout, host.
+ * The first call builds per-wavenumber tables (2 Ny doubles per class) kept
+ * on the device.  Does not advance time; synchronises.
+ */
+int chan_filtered_pressure(chan_t h, int kind, double p1, double p3, double* p);
+
+/*
  * Two-dimensional energy spectra of the current state (Sec. 3.3):
  * E_i(k1, y, k3) = w |u_i(k1, y, k3)|^2 with w = 2 for kx > 0 (the
  * conjugate mode) and 1 for kx = 0; the mean (0,0) mode is excluded, so the
@@ -238,7 +249,7 @@ int chan_nonlinear(chan_t h, double* H);
  * since the last reset (launches are counted even when timing is off).
  * chan_kernel_name(k) names kernel k (NULL when out of range).
  */
-#define CHAN_NKERNELS 14
+#define CHAN_NKERNELS 15
 int chan_profile(chan_t h, int enable);
 int chan_profile_read(chan_t h, double* ms, long long* launches);
 const char* chan_kernel_name(int k);

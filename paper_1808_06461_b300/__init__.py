@@ -32,8 +32,8 @@ SYMBOLS = ("chan_opts_default", "chan_init", "chan_init_ex", "chan_free", "chan_
            "chan_rhs_terms", "chan_rhs_terms_noalloc", "chan_footprint_bytes", "chan_set_graph",
            "chan_filtered_enstrophy", "chan_batch_create", "chan_batch_step", "chan_batch_last_error",
            "chan_batch_free", "chan_autotune", "chan_tuned_shape", "chan_database_record",
-           "chan_spectra", "chan_optimize_mesh")
-CHAN_NKERNELS = 14
+           "chan_spectra", "chan_optimize_mesh", "chan_filtered_pressure")
+CHAN_NKERNELS = 15
 
 
 class chan_opts(ctypes.Structure):
@@ -86,6 +86,7 @@ def load_library(path=LIB_PATH):
         "chan_autotune": (I, [P]),
         "chan_database_record": (I, [P, D, D, P, ctypes.POINTER(I), ctypes.POINTER(I)]),
         "chan_spectra": (I, [P, P]),
+        "chan_filtered_pressure": (I, [P, I, D, D, P]),
         "chan_optimize_mesh": (I, [ctypes.POINTER(chan_opts), I, D, P, DP, DP]),
         "chan_tuned_shape": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I)]),
         "chan_sync": (I, [P]),
@@ -250,6 +251,12 @@ class Channel:
         _check(self.h, _lib.chan_database_record(self.h, float(p1), float(p3), _ptr(rec), ctypes.byref(m1),
                                                  ctypes.byref(m3)))
         return rec
+
+    def filtered_pressure(self, kind, p1, p3):
+        """pbar from the filtered stresses (Sec. 3.1, Eq. (2)), shape (Ny, Nz, Nx/2)."""
+        pr = np.empty(self.shape, dtype=np.complex128)
+        _check(self.h, _lib.chan_filtered_pressure(self.h, int(kind), float(p1), float(p3), _ptr(pr)))
+        return pr
 
     def spectra(self):
         """E_i(k1, y, k3), shape (3, Ny, Nz, Nx/2)."""

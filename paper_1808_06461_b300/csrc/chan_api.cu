@@ -71,7 +71,7 @@ size_t fsize(const chan_s* h) { return (size_t)h->Ny * h->M; }
 const char* const kKernelNames[KID_COUNT] = {"k_pre",     "k_zinv",       "k_xpass", "k_zfwd",
                                              "k_nonlin",  "k_helm",       "k_poisson", "k_mean",
                                              "k_filter_out", "k_stats",   "k_derive", "k_apply_G",
-                                             "k_gather_retained", "k_spectra"};
+                                             "k_gather_retained", "k_spectra", "k_pressure"};
 
 // Launch bracket: counts the launch and, when tracing, records an event pair.
 struct Traced {
@@ -344,6 +344,8 @@ int chan_init_ex(chan_t* out, const chan_opts* o) {
   h->g_kind = -1;
   h->dbrec = nullptr;
   h->dbrec_n = 0;
+  h->prs = nullptr;
+  h->prsinv = nullptr;
   int rc = CHAN_OK;
   chanh_tables tb;
   std::memset(&tb, 0, sizeof(tb));
@@ -679,6 +681,27 @@ int chan_database_record(chan_t h, double p1, double p3, double* rec, int* m1, i
       CK(launch_gather_retained(h, wf(h, 2 + p), h->dbrec + (3 + p) * blk, M1, M3));
     }
     CK(cudaMemcpyAsync(rec, h->dbrec, 10 * blk * sizeof(double2), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+  } catch (Fail f) {
+    return f.code;
+  }
+  return CHAN_OK;
+}
+
+int chan_filtered_pressure(chan_t h, int kind, double p1, double p3, double* pr) {
+  if (!h) return bad(nullptr, "chan_filtered_pressure: NULL handle");
+  if (!pr) return bad(h, "chan_filtered_pressure: NULL output");
+  int rc = chan_filter_stresses(h, kind, p1, p3, nullptr, nullptr);   // G P(u_i u_j) in work slots 2..7
+  if (rc != CHAN_OK) return rc;
+  try {
+    if (!h->prs) {
+      h->prs = dalloc<double>(h, (size_t)h->Ny * 2 * h->C);
+      h->prsinv = dalloc<double>(h, 4 * (size_t)h->C);
+      CK(launch_setup_pressure(h));
+    }
+    const double2* P[6] = {wf(h, 2), wf(h, 3), wf(h, 4), wf(h, 5), wf(h, 6), wf(h, 7)};   // 11 22 33 12 13 23
+    { Traced t(h, KID_PRESSURE); CK(launch_pressure(h, P, wf(h, 8))); }
+    CK(cudaMemcpyAsync(pr, wf(h, 8), fsize(h) * sizeof(double2), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
   } catch (Fail f) {
     return f.code;

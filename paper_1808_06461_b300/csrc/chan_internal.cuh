@@ -40,7 +40,7 @@ struct FftPlan {
 };
 
 enum { KID_PRE = 0, KID_ZINV, KID_XPASS, KID_ZFWD, KID_NONLIN, KID_HELM, KID_POISSON, KID_MEAN,
-       KID_FILTER_OUT, KID_STATS, KID_DERIVE, KID_APPLY_G, KID_GATHER, KID_SPECTRA, KID_COUNT };
+       KID_FILTER_OUT, KID_STATS, KID_DERIVE, KID_APPLY_G, KID_GATHER, KID_SPECTRA, KID_PRESSURE, KID_COUNT };
 
 struct ProfRec {
   int k;
@@ -75,6 +75,8 @@ struct chan_s {
   int nmix;
   double2* scr;            // wall-normal sweep scratch [2][Ny][M]
   double* G;               // filter transfer [M]
+  double* prs;             // filtered-pressure homogeneous solutions [Ny][2][C] (lazy)
+  double* prsinv;          // their inverse wall-derivative matrices [4][C]
   double2* dbrec;          // compact database record (lazily allocated)
   size_t dbrec_n;          // its capacity in complex values
   int g_kind;              // filter whose transfer function G holds (-1: none)
@@ -123,6 +125,8 @@ cudaError_t launch_mean(chan_s* h, const double2* H1, const double2* H3, int s);
 cudaError_t launch_filter_out(chan_s* h, const double2* const* u, const double2* const* puu,
                               const double2* const* pbb, double2* ubar, double2* tau);
 cudaError_t launch_apply_G(chan_s* h, const double2* in, double2* out);
+cudaError_t launch_pressure(chan_s* h, const double2* const* P, double2* out);
+cudaError_t launch_setup_pressure(chan_s* h);
 cudaError_t launch_gather_retained(chan_s* h, const double2* src, double2* dst, int M1, int M3);
 cudaError_t launch_spectra(chan_s* h, const double2* u1, const double2* u3, double* E);
 cudaError_t launch_stats(chan_s* h, const double2* u1, const double2* u3, const double2* ubar,

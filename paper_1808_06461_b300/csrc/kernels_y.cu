@@ -699,6 +699,155 @@ __global__ void k_setup_helm(Geo g, YTabs t, const double* __restrict__ pois, do
 
 
 // ---------------------------------------------------------------------------
+// Filtered pressure (Sec. 3.1, Eq. (2)): interior rows
+//   (B - k^2 A) p = A r - B F22,  r = k1^2 F11 + k3^2 F33 + 2 k1 k3 F13 - 2 i k1 D1 F12 - 2 i k3 D1 F23,
+// wall rows dp/dy = nu G chi; F_ij = G P(u_i u_j).  Particular solution with
+// p(+-1) = 0 (Poisson factors), then the homogeneous pair p_a, p_b meets the
+// Neumann conditions through the inverse influence matrix.  Mean mode: P = -F22.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_pressure(Geo g, YTabs t, const double* __restrict__ pois,
+                                                  const double* __restrict__ prs, const double* __restrict__ prsinv,
+                                                  const double2* __restrict__ P11, const double2* __restrict__ P22,
+                                                  const double2* __restrict__ P33, const double2* __restrict__ P12,
+                                                  const double2* __restrict__ P13, const double2* __restrict__ P23,
+                                                  const double* __restrict__ G, const double2* __restrict__ chi,
+                                                  double2* pout, double2* scr) {
+  extern __shared__ double sm[];
+  const int Ny = g.Ny;
+  double* sA = sm;
+  double* sB = sm + 7 * Ny;
+  double* sB1 = sm + 14 * Ny;
+  double* sLU = sm + 21 * Ny;
+  load_tab(sA, t.A2, 7 * Ny);
+  load_tab(sB, t.B2, 7 * Ny);
+  load_tab(sB1, t.B1, 7 * Ny);
+  load_tab(sLU, t.lu1, 7 * Ny);
+  __syncthreads();
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= g.M) return;
+  const size_t M = g.M, C = g.C;
+  ModeInfo mi = mode_info(g, m);
+  const double gm = G[m];
+  if (mi.nyq) {
+    for (int i = 0; i < Ny; ++i) pout[(size_t)i * M + m] = z2();
+    return;
+  }
+  if (m == 0) {
+    for (int i = 0; i < Ny; ++i) pout[(size_t)i * M] = scl(-gm, P22[(size_t)i * M]);
+    return;
+  }
+  double2* s2 = scr + (size_t)Ny * M;
+  double2 wa[7], wb[7], ha[3], hb[3];
+#pragma unroll
+  for (int d = 0; d < 7; ++d) { wa[d] = z2(); wb[d] = z2(); }
+#pragma unroll
+  for (int d = 0; d < 3; ++d) { ha[d] = z2(); hb[d] = z2(); }
+  // D1 of F12 and F23: forward sweeps
+  for (int j = 0; j < Ny + 3; ++j) {
+    push(wa, j < Ny ? scl(gm, P12[(size_t)j * M + m]) : z2());
+    push(wb, j < Ny ? scl(gm, P23[(size_t)j * M + m]) : z2());
+    const int i = j - 3;
+    if (i < 0) continue;
+    const double* l = sLU + 7 * i;
+    scr[(size_t)i * M + m] = fwd(band7(sB1 + 7 * i, wa), l[0], l[1], l[2], ha);
+    s2[(size_t)i * M + m] = fwd(band7(sB1 + 7 * i, wb), l[0], l[1], l[2], hb);
+  }
+  // backward sweeps; assemble r in place of the first scratch field
+  double2 na[3] = {z2(), z2(), z2()}, nb[3] = {z2(), z2(), z2()};
+  const double k1 = mi.k1, k3 = mi.k3;
+  for (int i = Ny - 1; i >= 0; --i) {
+    const size_t o = (size_t)i * M + m;
+    const double* lu = sLU + 7 * i;
+    const double2 d12 = bwd(scr[o], lu[3], lu[4], lu[5], lu[6], na);
+    const double2 d23 = bwd(s2[o], lu[3], lu[4], lu[5], lu[6], nb);
+    double2 r = scl(gm * k1 * k1, P11[o]);
+    r = axpy(gm * k3 * k3, P33[o], r);
+    r = axpy(2.0 * gm * k1 * k3, P13[o], r);
+    // - 2 i (k1 d12 + k3 d23)
+    const double2 q = make_double2(k1 * d12.x + k3 * d23.x, k1 * d12.y + k3 * d23.y);
+    r.x += 2.0 * q.y;
+    r.y -= 2.0 * q.x;
+    scr[o] = r;
+  }
+  // A r - B F22 and the Poisson forward sweep
+  const double* P = pois + mi.c;
+#pragma unroll
+  for (int d = 0; d < 7; ++d) { wa[d] = z2(); wb[d] = z2(); }
+#pragma unroll
+  for (int d = 0; d < 3; ++d) ha[d] = z2();
+  for (int j = 0; j < Ny + 3; ++j) {
+    push(wa, j < Ny ? scr[(size_t)j * M + m] : z2());
+    push(wb, j < Ny ? scl(gm, P22[(size_t)j * M + m]) : z2());
+    const int i = j - 3;
+    if (i < 0) continue;
+    double2 rhs = z2();
+    if (i > 0 && i < Ny - 1) rhs = sub(band7(sA + 7 * i, wa), band7(sB + 7 * i, wb));
+    const double* Pi = P + (size_t)i * 7 * C;
+    s2[(size_t)i * M + m] = fwd(rhs, Pi[0], Pi[C], Pi[2 * C], ha);
+  }
+  double2 nx[3] = {z2(), z2(), z2()}, s0 = z2(), sN = z2();
+  for (int i = Ny - 1; i >= 0; --i) {
+    const size_t o = (size_t)i * M + m;
+    const double* Pi = P + (size_t)i * 7 * C;
+    const double2 pp = bwd(s2[o], Pi[3 * C], Pi[4 * C], Pi[5 * C], Pi[6 * C], nx);
+    pout[o] = pp;
+    s0 = axpy(t.d0[i], pp, s0);
+    sN = axpy(t.dN[i], pp, sN);
+  }
+  // Neumann conditions dp/dy(+-1) = nu G chi(+-1)
+  const double2 b0 = sub(scl(g.nu * gm, chi[m]), s0);
+  const double2 bN = sub(scl(g.nu * gm, chi[(size_t)(Ny - 1) * M + m]), sN);
+  const double* Gi = prsinv + mi.c;
+  const double g11 = Gi[0], g12 = Gi[C], g21 = Gi[2 * C], g22 = Gi[3 * C];
+  const double2 cA = make_double2(g11 * b0.x + g12 * bN.x, g11 * b0.y + g12 * bN.y);
+  const double2 cB = make_double2(g21 * b0.x + g22 * bN.x, g21 * b0.y + g22 * bN.y);
+  for (int i = 0; i < Ny; ++i) {
+    const size_t o = (size_t)i * M + m;
+    const double pa = prs[((size_t)i * 2) * C + mi.c], pb = prs[((size_t)i * 2 + 1) * C + mi.c];
+    pout[o] = axpy(pb, cB, axpy(pa, cA, pout[o]));
+  }
+}
+
+// Homogeneous Dirichlet solutions of (B - k^2 A) p = 0 (p_a = 1 at y = -1, p_b = 1 at
+// y = +1) per class, and the inverse of their wall-derivative matrix (class 0, whose
+// Neumann problem is singular, is left at zero and never used).
+__global__ void k_setup_pressure(Geo g, YTabs t, const double* __restrict__ pois, double* prs, double* prsinv) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.C) return;
+  const int Ny = g.Ny;
+  const size_t C = g.C;
+  const double* P = pois + c;
+  double dm[2][2];
+  for (int q = 0; q < 2; ++q) {
+    double h[3] = {0, 0, 0};
+    for (int i = 0; i < Ny; ++i) {
+      const double* Pi = P + (size_t)i * 7 * C;
+      double r = (q == 0 ? i == 0 : i == Ny - 1) ? 1.0 : 0.0;
+      r -= Pi[0] * h[0] + Pi[C] * h[1] + Pi[2 * C] * h[2];
+      h[0] = h[1]; h[1] = h[2]; h[2] = r;
+      prs[((size_t)i * 2 + q) * C + c] = r;
+    }
+    double nx[3] = {0, 0, 0}, s0 = 0, sN = 0;
+    for (int i = Ny - 1; i >= 0; --i) {
+      const double* Pi = P + (size_t)i * 7 * C;
+      double x = (prs[((size_t)i * 2 + q) * C + c] - Pi[3 * C] * nx[0] - Pi[4 * C] * nx[1] - Pi[5 * C] * nx[2]) * Pi[6 * C];
+      nx[2] = nx[1]; nx[1] = nx[0]; nx[0] = x;
+      prs[((size_t)i * 2 + q) * C + c] = x;
+      s0 += t.d0[i] * x;
+      sN += t.dN[i] * x;
+    }
+    dm[0][q] = s0;
+    dm[1][q] = sN;
+  }
+  const double det = dm[0][0] * dm[1][1] - dm[0][1] * dm[1][0];
+  const bool ok = c != 0 && det != 0.0;
+  prsinv[c] = ok ? dm[1][1] / det : 0.0;
+  prsinv[C + c] = ok ? -dm[0][1] / det : 0.0;
+  prsinv[2 * C + c] = ok ? -dm[1][0] / det : 0.0;
+  prsinv[3 * C + c] = ok ? dm[0][0] / det : 0.0;
+}
+
+// ---------------------------------------------------------------------------
 // Packed launches over several channels: one grid covers the blocks of every
 // run; a block finds its run from the per-run block offsets and executes the
 // same body with its local block index.  Runs may differ in size and RK3 phase.
@@ -933,6 +1082,21 @@ cudaError_t launch_mean_batch(chan_s* const* hs, int n, const BatchWork* w, cuda
   cudaError_t e = smem_attr((const void*)kb_mean, sm);
   if (e != cudaSuccess) return e;
   kb_mean<<<n, 256, sm, st>>>(B);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pressure(chan_s* h, const double2* const* P, double2* out) {
+  if (!h->prs) return cudaErrorInvalidValue;
+  size_t sm = sizeof(double) * 28 * h->Ny;
+  cudaError_t e = smem_attr((const void*)k_pressure, sm);
+  if (e != cudaSuccess) return e;
+  k_pressure<<<ygrid(h), kYThreads, sm, h->stream>>>(geo(h), ytabs(h), h->pois, h->prs, h->prsinv, P[0], P[1], P[2],
+                                                     P[3], P[4], P[5], h->G, h->chi, out, h->scr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_setup_pressure(chan_s* h) {
+  k_setup_pressure<<<(h->C + 127) / 128, 128, 0, h->stream>>>(geo(h), ytabs(h), h->pois, h->prs, h->prsinv);
   return cudaGetLastError();
 }
 

@@ -168,6 +168,18 @@ def test_database_record_and_spectra_parity(chan, ten_steps):
     assert rel(E, O.spectra(st, ref)) < TOL
 
 
+@pytest.mark.parametrize("kind,p", [(0, (120.0, 60.0)), (1, (50.0, 50.0))])
+def test_filtered_pressure_parity(chan, kind, p, ten_steps):
+    name = "re180_32x49x32"
+    st = setup(name)
+    s0, ref = ten_steps[name]
+    ch = make(chan, name)
+    ch.set_state(s0["v"], s0["omega2"], s0["U1"], s0["U3"])
+    ch.step(10)
+    pr = ch.filtered_pressure(kind, *p)
+    assert rel(pr, O.filtered_pressure(st, ref, kind, *p)) < TOL
+
+
 def test_poiseuille_steady_gpu(chan):
     name = "re180_32x49x32"
     s0 = ic(name, amp=0.0)
