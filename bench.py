@@ -420,7 +420,7 @@ def run_ours(args, c, name):
                                 "mean_profile_rel": prof_err(sm_[0], st_main[0]),
                                 "rms_profiles_rel": prof_err(rms(sm_), rms(st_main)),
                                 "tau_rel": prof_err(sm_[14:20], st_main[14:20])},
-                "dtype": "f32 transforms + f64 y-solves" if mode == "mixed" else "f32x2 transforms + f64 y-solves"}
+                "dtype": "f32 transforms + f64 y-solves" if mode == "mixed" else "f32x2 transforms and y-sweeps, f64 state and mean solve"}
     line = {"metric": "DNS Mpts.substep/s", "value": value, "unit": "Mpts*substep/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,

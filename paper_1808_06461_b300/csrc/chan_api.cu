@@ -195,6 +195,7 @@ size_t footprint(int Nx, int Ny, int Nz, int prec) {
   b += 5 * 7 * (size_t)Ny * sizeof(double) + 3 * (size_t)Ny * sizeof(double);              // y tables
   b += (nxh + Nz) * sizeof(double);                                                          // wavenumbers
   b += ((size_t)Ny * 7 * C + 3 * (size_t)Ny * 11 * C + 12 * C + 3 * ((size_t)Ny + 1)) * sizeof(double);
+  if (prec == CHAN_PREC_F64X) b += ((size_t)Ny * 7 * C + 3 * (size_t)Ny * 11 * C + 12 * C) * sizeof(dfr);
   b += (L1 + L3) * (prec == CHAN_PREC_MIXED ? sizeof(float2) : sizeof(double2));             // twiddles
   b += (size_t)(NWF + 9) * n * sizeof(double2);                                              // work fields
   b += 12 * (size_t)Ny * L3 * nxh * es;                                                      // mixed fields
@@ -363,8 +364,23 @@ int chan_init_ex(chan_t* out, const chan_opts* o) {
     if (hr) { h->err = "chan_init: compact-scheme set-up failed (singular coefficient system or LU pivot)"; throw Fail{CHAN_EINVAL}; }
     h->y.assign(tb.y, tb.y + h->Ny);
     h->wq.assign(tb.wq, tb.wq + h->Ny);
-    h->p1.L = L1; h->p1.np = chanh_radix_plan(L1, h->p1.radix);
-    h->p3.L = L3; h->p3.np = chanh_radix_plan(L3, h->p3.radix);
+    for (FftPlan* pl : {&h->p1, &h->p3}) {
+      pl->L = pl == &h->p1 ? L1 : L3;
+      pl->np = chanh_radix_plan(pl->L, pl->radix);
+      // ceil(2^32 / d) for d >= 2; 0 marks d = 1, whose quotient the kernels take as is
+      auto mag = [](int d) { return d == 1 ? 0u : (unsigned)((((unsigned long long)1 << 32) + d - 1) / d); };
+      int Ls = pl->L;
+      for (int s = 0; s < pl->np; ++s) {         // DIF stages: block Ls shrinks
+        pl->mag_nbf[s] = mag(pl->L / pl->radix[s]);
+        pl->mag_mdif[s] = mag(Ls / pl->radix[s]);
+        Ls /= pl->radix[s];
+      }
+      Ls = 1;
+      for (int s = pl->np - 1; s >= 0; --s) {    // DIT stages: block grows
+        Ls *= pl->radix[s];
+        pl->mag_mdit[s] = mag(Ls / pl->radix[s]);
+      }
+    }
     const size_t n = fsize(h), Ny = h->Ny;
     // state
     h->v = dalloc<double2>(h, n); h->om = dalloc<double2>(h, n); h->chi = dalloc<double2>(h, n);
@@ -393,6 +409,11 @@ int chan_init_ex(chan_t* out, const chan_opts* o) {
     h->helm = dalloc<double>(h, 3 * Ny * 11 * (size_t)h->C);
     h->infl = dalloc<double>(h, 3 * 4 * (size_t)h->C);
     h->meanh = dalloc<double>(h, 3 * (Ny + 1));
+    if (h->prec == CHAN_PREC_F64X) {
+      h->pois_df = dalloc<dfr>(h, Ny * 7 * (size_t)h->C);
+      h->helm_df = dalloc<dfr>(h, 3 * Ny * 11 * (size_t)h->C);
+      h->infl_df = dalloc<dfr>(h, 3 * 4 * (size_t)h->C);
+    }
     // twiddles in the transform precision
     for (int which = 0; which < 2; ++which) {
       const int L = which ? L3 : L1;

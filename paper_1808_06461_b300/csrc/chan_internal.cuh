@@ -8,6 +8,7 @@
 
 #include "../../include/chan.h"
 #include "chan_host.h"
+#include "df.cuh"
 
 // Fourier fields: double2 arrays [Ny][M], M = Nz * (Nx/2), mode m = jz*nxh + kx.
 // Mixed fields (physical z, Fourier kx): [Ny][L3][nxh] of float2 or double2.
@@ -37,6 +38,10 @@ struct Geo {
 struct FftPlan {
   int L, np;
   int radix[16];
+  // ceil(2^32 / d) for the divisors of each stage (exact quotients via __umulhi for
+  // operand n and divisor d with n d < 2^32; 0 stands for d = 1): L/R, and the span
+  // Ls/R of the DIF and DIT stage
+  unsigned mag_nbf[16], mag_mdif[16], mag_mdit[16];
 };
 
 enum { KID_PRE = 0, KID_ZINV, KID_XPASS, KID_ZFWD, KID_NONLIN, KID_HELM, KID_POISSON, KID_MEAN,
@@ -66,6 +71,7 @@ struct chan_s {
   double* helm;            // [3][Ny][11][C]
   double* pois;            // [Ny][7][C]
   double* infl;            // [3][4][C]
+  dfr *helm_df, *pois_df, *infl_df;   // pair copies for the double-float y-kernels (that mode only)
   double* meanh;           // [3][Ny+1]: U_h of each substep and its flux
   void *tw1, *tw3;         // twiddles of L1, L3 in the FFT precision
   // work (device)

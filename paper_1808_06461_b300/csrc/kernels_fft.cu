@@ -11,38 +11,9 @@
 #include <cstring>
 
 #include "chan_internal.cuh"
+#include "df.cuh"
 
 namespace {
-
-// Double-float real: value = h + l with |l| <= ulp(h)/2 (Dekker 1971).  The
-// error-free sum is Knuth's two-sum, the product uses the FMA to recover the
-// low part of h_a h_b; every operation is an explicit round-to-nearest
-// intrinsic so that the compiler neither contracts nor reassociates it.
-// Relative precision about 2^-47 at FP32 throughput.
-struct dfr {
-  float h, l;
-};
-struct dfc {
-  dfr x, y;
-};
-__device__ __forceinline__ dfr operator+(dfr a, dfr b) {
-  const float s = __fadd_rn(a.h, b.h);
-  const float bb = __fsub_rn(s, a.h);
-  float e = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, bb)), __fsub_rn(b.h, bb));
-  e = __fadd_rn(e, __fadd_rn(a.l, b.l));
-  const float t = __fadd_rn(s, e);
-  return dfr{t, __fsub_rn(e, __fsub_rn(t, s))};
-}
-__device__ __forceinline__ dfr operator-(dfr a) { return dfr{-a.h, -a.l}; }
-__device__ __forceinline__ dfr operator-(dfr a, dfr b) { return a + (-b); }
-__device__ __forceinline__ dfr operator*(dfr a, dfr b) {
-  const float p = __fmul_rn(a.h, b.h);
-  float e = __fmaf_rn(a.h, b.h, -p);
-  e = __fmaf_rn(a.h, b.l, e);
-  e = __fmaf_rn(a.l, b.h, e);
-  const float t = __fadd_rn(p, e);
-  return dfr{t, __fsub_rn(e, __fsub_rn(t, p))};
-}
 
 template <typename T> struct V2;
 template <> struct V2<double> { typedef double2 t; };
@@ -173,15 +144,16 @@ template <int DIR, typename T2> __device__ __forceinline__ void dft3_nomid(T2* v
 // x[b Ls + j + r m] (m = Ls/R), forms y_q = sum_r x_r w_R^(DIR r q), scales
 // y_q by w_Ls^(DIR q j) and writes it back to slot q.
 template <int R, int DIR, bool ZMID, typename T2>
-__device__ __forceinline__ void dif_stage(T2* a, int L, int nb, int ld, const T2* __restrict__ tw, int Ls) {
+__device__ __forceinline__ void dif_stage(T2* a, int L, int nb, int ld, const T2* __restrict__ tw, int Ls,
+                                          unsigned mag_nbf, unsigned mag_m) {
   const int m = Ls / R;
   const int nbf = L / R;
   const int tmul = L / Ls;
   const int total = nb * nbf;
   for (int t = threadIdx.x; t < total; t += blockDim.x) {
-    const int bi = t / nbf;
+    const int bi = (int)__umulhi((unsigned)t, mag_nbf);   // t / nbf (exact while t nbf < 2^32)
     const int u = t - bi * nbf;
-    const int blk = u / m;
+    const int blk = mag_m ? (int)__umulhi((unsigned)u, mag_m) : u;   // u / m (mag 0: m = 1)
     const int j = u - blk * m;
     T2* x = a + bi * ld + blk * Ls + j;
     T2 v[R];
@@ -209,15 +181,16 @@ __device__ __forceinline__ void dif_stage(T2* a, int L, int nb, int ld, const T2
 // by w_Ls^(DIR r j), then y_q = sum_r x_r w_R^(DIR r q) goes to slot q.  With
 // ZMID the middle output (q = 1) is neither formed nor stored.
 template <int R, int DIR, bool ZMID, typename T2>
-__device__ __forceinline__ void dit_stage(T2* a, int L, int nb, int ld, const T2* __restrict__ tw, int Ls) {
+__device__ __forceinline__ void dit_stage(T2* a, int L, int nb, int ld, const T2* __restrict__ tw, int Ls,
+                                          unsigned mag_nbf, unsigned mag_m) {
   const int m = Ls / R;
   const int nbf = L / R;
   const int tmul = L / Ls;
   const int total = nb * nbf;
   for (int t = threadIdx.x; t < total; t += blockDim.x) {
-    const int bi = t / nbf;
+    const int bi = (int)__umulhi((unsigned)t, mag_nbf);   // t / nbf (exact while t nbf < 2^32)
     const int u = t - bi * nbf;
-    const int blk = u / m;
+    const int blk = mag_m ? (int)__umulhi((unsigned)u, mag_m) : u;   // u / m (mag 0: m = 1)
     const int j = u - blk * m;
     T2* x = a + bi * ld + blk * Ls + j;
     T2 v[R];
@@ -249,10 +222,11 @@ __device__ void fft_dif(T2* a, int L, int nb, int ld, const T2* __restrict__ tw,
   int Ls = L;
   for (int s = 0; s < pl.np; ++s) {
     const int R = pl.radix[s];
-    if (R == 4) dif_stage<4, DIR, false>(a, L, nb, ld, tw, Ls);
-    else if (R == 2) dif_stage<2, DIR, false>(a, L, nb, ld, tw, Ls);
-    else if (s == 0 && zmid) dif_stage<3, DIR, true>(a, L, nb, ld, tw, Ls);
-    else dif_stage<3, DIR, false>(a, L, nb, ld, tw, Ls);
+    const unsigned mn = pl.mag_nbf[s], mm = pl.mag_mdif[s];
+    if (R == 4) dif_stage<4, DIR, false>(a, L, nb, ld, tw, Ls, mn, mm);
+    else if (R == 2) dif_stage<2, DIR, false>(a, L, nb, ld, tw, Ls, mn, mm);
+    else if (s == 0 && zmid) dif_stage<3, DIR, true>(a, L, nb, ld, tw, Ls, mn, mm);
+    else dif_stage<3, DIR, false>(a, L, nb, ld, tw, Ls, mn, mm);
     Ls /= R;
   }
 }
@@ -266,10 +240,11 @@ __device__ void fft_dit(T2* a, int L, int nb, int ld, const T2* __restrict__ tw,
   for (int s = pl.np - 1; s >= 0; --s) {
     const int R = pl.radix[s];
     Ls *= R;
-    if (R == 4) dit_stage<4, DIR, false>(a, L, nb, ld, tw, Ls);
-    else if (R == 2) dit_stage<2, DIR, false>(a, L, nb, ld, tw, Ls);
-    else if (s == 0 && zmid) dit_stage<3, DIR, true>(a, L, nb, ld, tw, Ls);
-    else dit_stage<3, DIR, false>(a, L, nb, ld, tw, Ls);
+    const unsigned mn = pl.mag_nbf[s], mm = pl.mag_mdit[s];
+    if (R == 4) dit_stage<4, DIR, false>(a, L, nb, ld, tw, Ls, mn, mm);
+    else if (R == 2) dit_stage<2, DIR, false>(a, L, nb, ld, tw, Ls, mn, mm);
+    else if (s == 0 && zmid) dit_stage<3, DIR, true>(a, L, nb, ld, tw, Ls, mn, mm);
+    else dit_stage<3, DIR, false>(a, L, nb, ld, tw, Ls, mn, mm);
   }
 }
 

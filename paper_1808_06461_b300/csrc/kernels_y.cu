@@ -8,6 +8,7 @@
 // the Poisson problem (chi2) with the influence-matrix wall correction; the
 // mean profiles with a constant mass flux (Sec. 2.1).
 #include "chan_internal.cuh"
+#include "df.cuh"
 
 namespace {
 
@@ -68,6 +69,78 @@ __device__ __forceinline__ void load_tab(double* dst, const double* src, int n) 
   for (int k = threadIdx.x; k < n; k += blockDim.x) dst[k] = src[k];
 }
 
+
+// Arithmetic of the four substep y-kernels, chosen per precision mode: FP64, or
+// double-float (FP32 pairs, about 2^-47) in the double-float mode.  Storage is
+// FP64 in both; the double-float kernels split on load and merge on store.
+struct YF64 {
+  typedef double R;
+  typedef double2 C;
+  __device__ static __forceinline__ R r(double x) { return x; }
+  __device__ static __forceinline__ C c(double2 x) { return x; }
+  __device__ static __forceinline__ double2 d(C x) { return x; }
+  __device__ static __forceinline__ C zero() { return make_double2(0.0, 0.0); }
+  __device__ static __forceinline__ C mk(R x, R y) { return make_double2(x, y); }
+  __device__ static __forceinline__ C axpy(R a, C x, C y) { return make_double2(fma(a, x.x, y.x), fma(a, x.y, y.y)); }
+  __device__ static __forceinline__ C scl(R a, C x) { return make_double2(a * x.x, a * x.y); }
+  __device__ static __forceinline__ C sub(C a, C b) { return make_double2(a.x - b.x, a.y - b.y); }
+  __device__ static __forceinline__ C itimes(C a) { return make_double2(-a.y, a.x); }
+  __device__ static __forceinline__ R neg(R a) { return -a; }
+};
+struct YDF {
+  typedef dfr R;
+  typedef dfc C;
+  __device__ static __forceinline__ R r(double x) { return df_split(x); }
+  __device__ static __forceinline__ C c(double2 x) { return dfc{df_split(x.x), df_split(x.y)}; }
+  __device__ static __forceinline__ double2 d(C x) { return make_double2(df_merge(x.x), df_merge(x.y)); }
+  __device__ static __forceinline__ C zero() { return dfc{dfr{0.f, 0.f}, dfr{0.f, 0.f}}; }
+  __device__ static __forceinline__ C mk(R x, R y) { return dfc{x, y}; }
+  __device__ static __forceinline__ C axpy(R a, C x, C y) { return dfc{y.x + a * x.x, y.y + a * x.y}; }
+  __device__ static __forceinline__ C scl(R a, C x) { return dfc{a * x.x, a * x.y}; }
+  __device__ static __forceinline__ C sub(C a, C b) { return dfc{a.x - b.x, a.y - b.y}; }
+  __device__ static __forceinline__ C itimes(C a) { return dfc{-a.y, a.x}; }
+  __device__ static __forceinline__ R neg(R a) { return -a; }
+};
+
+template <class Y, int N>
+__device__ __forceinline__ void ypush(typename Y::C (&w)[N], typename Y::C x) {
+#pragma unroll
+  for (int d = 0; d < N - 1; ++d) w[d] = w[d + 1];
+  w[N - 1] = x;
+}
+template <class Y>
+__device__ __forceinline__ typename Y::C yband7(const typename Y::R* c, const typename Y::C (&w)[7]) {
+  typename Y::C r = Y::zero();
+#pragma unroll
+  for (int d = 0; d < 7; ++d) r = Y::axpy(c[d], w[d], r);
+  return r;
+}
+template <class Y>
+__device__ __forceinline__ typename Y::C yfwd(typename Y::C r, typename Y::R l0, typename Y::R l1, typename Y::R l2,
+                                              typename Y::C (&hist)[3]) {
+  r = Y::axpy(Y::neg(l0), hist[0], r);
+  r = Y::axpy(Y::neg(l1), hist[1], r);
+  r = Y::axpy(Y::neg(l2), hist[2], r);
+  ypush<Y>(hist, r);
+  return r;
+}
+template <class Y>
+__device__ __forceinline__ typename Y::C ybwd(typename Y::C z, typename Y::R u0, typename Y::R u1, typename Y::R u2,
+                                              typename Y::R dinv, typename Y::C (&nxt)[3]) {
+  z = Y::axpy(Y::neg(u0), nxt[0], z);
+  z = Y::axpy(Y::neg(u1), nxt[1], z);
+  z = Y::axpy(Y::neg(u2), nxt[2], z);
+  typename Y::C x = Y::scl(dinv, z);
+  nxt[2] = nxt[1];
+  nxt[1] = nxt[0];
+  nxt[0] = x;
+  return x;
+}
+template <class Y>
+__device__ __forceinline__ void yload_tab(typename Y::R* dst, const double* src, int n) {
+  for (int k = threadIdx.x; k < n; k += blockDim.x) dst[k] = Y::r(src[k]);
+}
+
 struct ModeInfo {
   int jz, kx, c;
   bool nyq;
@@ -92,16 +165,19 @@ __device__ __forceinline__ ModeInfo mode_info(const Geo& g, int m) {
 // a1: u_1, u_3, omega_1, omega_3 from (v, omega_2, dv/dy); two D1 sweeps.
 // dv/dy is part of the state (it is D1 v of the last Poisson solve).
 // ---------------------------------------------------------------------------
+template <class Y>
 __device__ __forceinline__ void pre_body(Geo g, YTabs t, const double2* __restrict__ v,
-                                             const double2* __restrict__ om, const double2* __restrict__ dv,
-                                             const double* __restrict__ U1, const double* __restrict__ U3,
-                                             double2* u1o, double2* u3o, double2* om1o, double2* om3o, int bid) {
+                                         const double2* __restrict__ om, const double2* __restrict__ dv,
+                                         const double* __restrict__ U1, const double* __restrict__ U3,
+                                         double2* u1o, double2* u3o, double2* om1o, double2* om3o, int bid) {
+  typedef typename Y::R R;
+  typedef typename Y::C C;
   extern __shared__ double sm[];
   const int Ny = g.Ny;
-  double* sB1 = sm;
-  double* sLU = sm + 7 * Ny;
-  load_tab(sB1, t.B1, 7 * Ny);
-  load_tab(sLU, t.lu1, 7 * Ny);
+  R* sB1 = reinterpret_cast<R*>(sm);
+  R* sLU = sB1 + 7 * Ny;
+  yload_tab<Y>(sB1, t.B1, 7 * Ny);
+  yload_tab<Y>(sLU, t.lu1, 7 * Ny);
   __syncthreads();
   const int m = bid * blockDim.x + threadIdx.x;
   if (m >= g.M) return;
@@ -115,77 +191,83 @@ __device__ __forceinline__ void pre_body(Geo g, YTabs t, const double2* __restri
     return;
   }
   const bool mean = (m == 0);
-  double2 wx[7], ww[7], hx[3], hw[3];
+  C* pk1 = reinterpret_cast<C*>(u1o);   // forward-sweep values parked in the outputs
+  C* pk3 = reinterpret_cast<C*>(u3o);
+  C wx[7], ww[7], hx[3], hw[3];
 #pragma unroll
-  for (int d = 0; d < 7; ++d) { wx[d] = z2(); ww[d] = z2(); }
+  for (int d = 0; d < 7; ++d) { wx[d] = Y::zero(); ww[d] = Y::zero(); }
 #pragma unroll
-  for (int d = 0; d < 3; ++d) { hx[d] = z2(); hw[d] = z2(); }
+  for (int d = 0; d < 3; ++d) { hx[d] = Y::zero(); hw[d] = Y::zero(); }
   // forward sweep of D1 = A1^-1 B1 on x = dv/dy (U1 for the mean) and w = omega_2 (U3)
   for (int j = 0; j < Ny + 3; ++j) {
-    double2 nx = z2(), nw = z2();
+    C nx = Y::zero(), nw = Y::zero();
     if (j < Ny) {
-      if (mean) { nx.x = U1[j]; nw.x = U3[j]; }
-      else { nx = dv[(size_t)j * M + m]; nw = om[(size_t)j * M + m]; }
+      if (mean) { nx = Y::c(make_double2(U1[j], 0.0)); nw = Y::c(make_double2(U3[j], 0.0)); }
+      else { nx = Y::c(dv[(size_t)j * M + m]); nw = Y::c(om[(size_t)j * M + m]); }
     }
-    push(wx, nx);
-    push(ww, nw);
+    ypush<Y>(wx, nx);
+    ypush<Y>(ww, nw);
     const int i = j - 3;
     if (i < 0) continue;
-    const double* b = sB1 + 7 * i;
-    const double* l = sLU + 7 * i;
-    double2 zx = fwd(band7(b, wx), l[0], l[1], l[2], hx);
-    double2 zw = fwd(band7(b, ww), l[0], l[1], l[2], hw);
-    u1o[(size_t)i * M + m] = zx;   // parked here until the backward sweep
-    u3o[(size_t)i * M + m] = zw;
+    const R* b = sB1 + 7 * i;
+    const R* l = sLU + 7 * i;
+    pk1[(size_t)i * M + m] = yfwd<Y>(yband7<Y>(b, wx), l[0], l[1], l[2], hx);
+    pk3[(size_t)i * M + m] = yfwd<Y>(yband7<Y>(b, ww), l[0], l[1], l[2], hw);
   }
-  double2 px[3] = {z2(), z2(), z2()}, pw[3] = {z2(), z2(), z2()};
-  const double q1 = mean ? 0.0 : mi.k1 / mi.k2, q3 = mean ? 0.0 : mi.k3 / mi.k2;
+  C px[3] = {Y::zero(), Y::zero(), Y::zero()}, pw[3] = {Y::zero(), Y::zero(), Y::zero()};
+  const R q1 = Y::r(mean ? 0.0 : mi.k1 / mi.k2), q3 = Y::r(mean ? 0.0 : mi.k3 / mi.k2);
+  const R k1 = Y::r(mi.k1), k3 = Y::r(mi.k3);
   for (int i = Ny - 1; i >= 0; --i) {
     const size_t o = (size_t)i * M + m;
-    const double* lu = sLU + 7 * i;
-    double2 P = bwd(u1o[o], lu[3], lu[4], lu[5], lu[6], px);   // d2v/dy2 ... D1 of dv/dy
-    double2 Q = bwd(u3o[o], lu[3], lu[4], lu[5], lu[6], pw);   // D1 omega_2
-    double2 u1, u3, du1, du3;
-    double2 vi = z2();
+    const R* lu = sLU + 7 * i;
+    const C P = ybwd<Y>(pk1[o], lu[3], lu[4], lu[5], lu[6], px);   // D1 of dv/dy
+    const C Q = ybwd<Y>(pk3[o], lu[3], lu[4], lu[5], lu[6], pw);   // D1 omega_2
+    C u1, u3, du1, du3, vi = Y::zero();
     if (mean) {
-      u1 = make_double2(U1[i], 0.0);
-      u3 = make_double2(U3[i], 0.0);
+      u1 = Y::c(make_double2(U1[i], 0.0));
+      u3 = Y::c(make_double2(U3[i], 0.0));
       du1 = P;
       du3 = Q;
     } else {
-      double2 dvi = dv[o], omi = om[o];
-      vi = v[o];
-      u1 = itimes(make_double2(q1 * dvi.x - q3 * omi.x, q1 * dvi.y - q3 * omi.y));
-      u3 = itimes(make_double2(q3 * dvi.x + q1 * omi.x, q3 * dvi.y + q1 * omi.y));
-      du1 = itimes(make_double2(q1 * P.x - q3 * Q.x, q1 * P.y - q3 * Q.y));
-      du3 = itimes(make_double2(q3 * P.x + q1 * Q.x, q3 * P.y + q1 * Q.y));
+      const C dvi = Y::c(dv[o]), omi = Y::c(om[o]);
+      vi = Y::c(v[o]);
+      u1 = Y::itimes(Y::axpy(Y::neg(q3), omi, Y::scl(q1, dvi)));
+      u3 = Y::itimes(Y::axpy(q1, omi, Y::scl(q3, dvi)));
+      du1 = Y::itimes(Y::axpy(Y::neg(q3), Q, Y::scl(q1, P)));
+      du3 = Y::itimes(Y::axpy(q1, Q, Y::scl(q3, P)));
     }
     // omega_1 = du3/dy - i k3 v, omega_3 = i k1 v - du1/dy
-    u1o[o] = u1;
-    u3o[o] = u3;
-    om1o[o] = make_double2(du3.x + mi.k3 * vi.y, du3.y - mi.k3 * vi.x);
-    om3o[o] = make_double2(-mi.k1 * vi.y - du1.x, mi.k1 * vi.x - du1.y);
+    u1o[o] = Y::d(u1);
+    u3o[o] = Y::d(u3);
+    om1o[o] = Y::d(Y::sub(du3, Y::itimes(Y::scl(k3, vi))));
+    om3o[o] = Y::d(Y::sub(Y::itimes(Y::scl(k1, vi)), du1));
   }
 }
 
 __global__ void __launch_bounds__(128) k_pre(Geo g, YTabs t, const double2* __restrict__ v,
                                              const double2* __restrict__ om, const double2* __restrict__ dv,
                                              const double* __restrict__ U1, const double* __restrict__ U3,
-                                             double2* u1o, double2* u3o, double2* om1o, double2* om3o) { pre_body(g, t, v, om, dv, U1, U3, u1o, u3o, om1o, om3o, blockIdx.x); }
-
+                                             double2* u1o, double2* u3o, double2* om1o, double2* om3o) { pre_body<YF64>(g, t, v, om, dv, U1, U3, u1o, u3o, om1o, om3o, blockIdx.x); }
+__global__ void __launch_bounds__(128) k_pre_df(Geo g, YTabs t, const double2* __restrict__ v,
+                                                const double2* __restrict__ om, const double2* __restrict__ dv,
+                                                const double* __restrict__ U1, const double* __restrict__ U3,
+                                                double2* u1o, double2* u3o, double2* om1o, double2* om3o) { pre_body<YDF>(g, t, v, om, dv, U1, U3, u1o, u3o, om1o, om3o, blockIdx.x); }
 
 // ---------------------------------------------------------------------------
 // a5: N_omega2 = i k3 H1 - i k1 H3, N_chi = -D1(i k1 H1 + i k3 H3) - k^2 H2.
 // ---------------------------------------------------------------------------
+template <class Y>
 __device__ __forceinline__ void nonlin_body(Geo g, YTabs t, const double2* __restrict__ H1,
-                                                const double2* __restrict__ H2, const double2* __restrict__ H3,
-                                                double2* Nchi, double2* Nom, double2* scr, int bid) {
+                                            const double2* __restrict__ H2, const double2* __restrict__ H3,
+                                            double2* Nchi, double2* Nom, double2* scr_, int bid) {
+  typedef typename Y::R R;
+  typedef typename Y::C C;
   extern __shared__ double sm[];
   const int Ny = g.Ny;
-  double* sB1 = sm;
-  double* sLU = sm + 7 * Ny;
-  load_tab(sB1, t.B1, 7 * Ny);
-  load_tab(sLU, t.lu1, 7 * Ny);
+  R* sB1 = reinterpret_cast<R*>(sm);
+  R* sLU = sB1 + 7 * Ny;
+  yload_tab<Y>(sB1, t.B1, 7 * Ny);
+  yload_tab<Y>(sLU, t.lu1, 7 * Ny);
   __syncthreads();
   const int m = bid * blockDim.x + threadIdx.x;
   if (m >= g.M) return;
@@ -195,39 +277,42 @@ __device__ __forceinline__ void nonlin_body(Geo g, YTabs t, const double2* __res
     for (int i = 0; i < Ny; ++i) { Nchi[(size_t)i * M + m] = z2(); Nom[(size_t)i * M + m] = z2(); }
     return;
   }
-  double2 w[7], hz[3];
+  C* scr = reinterpret_cast<C*>(scr_);
+  const R k1 = Y::r(mi.k1), k3 = Y::r(mi.k3), mk2 = Y::r(-mi.k2);
+  C w[7], hz[3];
 #pragma unroll
-  for (int d = 0; d < 7; ++d) w[d] = z2();
+  for (int d = 0; d < 7; ++d) w[d] = Y::zero();
 #pragma unroll
-  for (int d = 0; d < 3; ++d) hz[d] = z2();
+  for (int d = 0; d < 3; ++d) hz[d] = Y::zero();
   for (int j = 0; j < Ny + 3; ++j) {
-    double2 f = z2();
+    C f = Y::zero();
     if (j < Ny) {
       const size_t o = (size_t)j * M + m;
-      double2 a = H1[o], b = H3[o];
-      f = itimes(make_double2(mi.k1 * a.x + mi.k3 * b.x, mi.k1 * a.y + mi.k3 * b.y));
+      f = Y::itimes(Y::axpy(k3, Y::c(H3[o]), Y::scl(k1, Y::c(H1[o]))));   // i k1 H1 + i k3 H3
     }
-    push(w, f);
+    ypush<Y>(w, f);
     const int i = j - 3;
     if (i < 0) continue;
-    const double* l = sLU + 7 * i;
-    scr[(size_t)i * M + m] = fwd(band7(sB1 + 7 * i, w), l[0], l[1], l[2], hz);
+    const R* l = sLU + 7 * i;
+    scr[(size_t)i * M + m] = yfwd<Y>(yband7<Y>(sB1 + 7 * i, w), l[0], l[1], l[2], hz);
   }
-  double2 nx[3] = {z2(), z2(), z2()};
+  C nx[3] = {Y::zero(), Y::zero(), Y::zero()};
   for (int i = Ny - 1; i >= 0; --i) {
     const size_t o = (size_t)i * M + m;
-    const double* lu = sLU + 7 * i;
-    double2 d = bwd(scr[o], lu[3], lu[4], lu[5], lu[6], nx);
-    double2 h2 = H2[o], h1 = H1[o], h3 = H3[o];
-    Nchi[o] = make_double2(-d.x - mi.k2 * h2.x, -d.y - mi.k2 * h2.y);
-    Nom[o] = itimes(make_double2(mi.k3 * h1.x - mi.k1 * h3.x, mi.k3 * h1.y - mi.k1 * h3.y));
+    const R* lu = sLU + 7 * i;
+    const C d = ybwd<Y>(scr[o], lu[3], lu[4], lu[5], lu[6], nx);
+    const C h2 = Y::c(H2[o]), h1 = Y::c(H1[o]), h3 = Y::c(H3[o]);
+    Nchi[o] = Y::d(Y::axpy(mk2, h2, Y::sub(Y::zero(), d)));                 // -D1 f - k^2 H2
+    Nom[o] = Y::d(Y::itimes(Y::axpy(Y::neg(k1), h3, Y::scl(k3, h1))));      // i k3 H1 - i k1 H3
   }
 }
 
 __global__ void __launch_bounds__(128) k_nonlin(Geo g, YTabs t, const double2* __restrict__ H1,
                                                 const double2* __restrict__ H2, const double2* __restrict__ H3,
-                                                double2* Nchi, double2* Nom, double2* scr) { nonlin_body(g, t, H1, H2, H3, Nchi, Nom, scr, blockIdx.x); }
-
+                                                double2* Nchi, double2* Nom, double2* scr) { nonlin_body<YF64>(g, t, H1, H2, H3, Nchi, Nom, scr, blockIdx.x); }
+__global__ void __launch_bounds__(128) k_nonlin_df(Geo g, YTabs t, const double2* __restrict__ H1,
+                                                   const double2* __restrict__ H2, const double2* __restrict__ H3,
+                                                   double2* Nchi, double2* Nom, double2* scr) { nonlin_body<YDF>(g, t, H1, H2, H3, Nchi, Nom, scr, blockIdx.x); }
 
 // ---------------------------------------------------------------------------
 // a6 + first half of a7: implicit RK3 Helmholtz steps of omega_2 and chi
@@ -235,21 +320,24 @@ __global__ void __launch_bounds__(128) k_nonlin(Geo g, YTabs t, const double2* _
 //   [(1 + b dt nu k^2) A - b dt nu B] X+ = A[(1 - a dt nu k^2) X + dt(g N + z Nprev)] + a dt nu B X,
 // wall rows X+ = 0 (chi's are the particular solution).  Nprev <- N.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void helm_body(Geo g, YTabs t, const double* __restrict__ helm,
-                                              double2* om, double2* chi, const double2* __restrict__ Nchi,
-                                              const double2* __restrict__ Nom, double2* Nchi_p, double2* Nom_p,
-                                              double2* scr, int s, int bid) {
+template <class Y>
+__device__ __forceinline__ void helm_body(Geo g, YTabs t, const typename Y::R* __restrict__ helm,
+                                          double2* om, double2* chi, const double2* __restrict__ Nchi,
+                                          const double2* __restrict__ Nom, double2* Nchi_p, double2* Nom_p,
+                                          double2* scr_, int s, int bid) {
+  typedef typename Y::R R;
+  typedef typename Y::C C;
   extern __shared__ double sm[];
   const int Ny = g.Ny;
-  double* sA = sm;
-  double* sB = sm + 7 * Ny;
-  load_tab(sA, t.A2, 7 * Ny);
-  load_tab(sB, t.B2, 7 * Ny);
+  R* sA = reinterpret_cast<R*>(sm);
+  R* sB = sA + 7 * Ny;
+  yload_tab<Y>(sA, t.A2, 7 * Ny);
+  yload_tab<Y>(sB, t.B2, 7 * Ny);
   __syncthreads();
   const int m = bid * blockDim.x + threadIdx.x;
   if (m >= g.M) return;
   const size_t M = g.M;
-  const size_t C = g.C;
+  const size_t NC = g.C;
   ModeInfo mi = mode_info(g, m);
   if (mi.nyq) {
     for (int i = 0; i < Ny; ++i) {
@@ -260,53 +348,55 @@ __device__ __forceinline__ void helm_body(Geo g, YTabs t, const double* __restri
   }
   const double gm = c_rk3[s][0], zt = c_rk3[s][1], al = c_rk3[s][2];
   const double dt = g.dt, nu = g.nu;
-  const double c1 = 1.0 - al * dt * nu * mi.k2, cg = dt * gm, cz = dt * zt, ca = al * dt * nu;
-  const double* H = helm + (size_t)s * Ny * 11 * C + mi.c;
-  double2 wa[7], wx[7], wb[7], wy[7], ho[3], hc[3];
+  const R c1 = Y::r(1.0 - al * dt * nu * mi.k2), cg = Y::r(dt * gm), cz = Y::r(dt * zt), ca = Y::r(al * dt * nu);
+  const R* H = helm + (size_t)s * Ny * 11 * NC + mi.c;
+  C* scr = reinterpret_cast<C*>(scr_);
+  C* scr2 = scr + (size_t)Ny * M;
+  C wa[7], wx[7], wb[7], wy[7], ho[3], hc[3];
 #pragma unroll
-  for (int d = 0; d < 7; ++d) { wa[d] = z2(); wx[d] = z2(); wb[d] = z2(); wy[d] = z2(); }
+  for (int d = 0; d < 7; ++d) { wa[d] = Y::zero(); wx[d] = Y::zero(); wb[d] = Y::zero(); wy[d] = Y::zero(); }
 #pragma unroll
-  for (int d = 0; d < 3; ++d) { ho[d] = z2(); hc[d] = z2(); }
-  double2* scr2 = scr + (size_t)Ny * M;
+  for (int d = 0; d < 3; ++d) { ho[d] = Y::zero(); hc[d] = Y::zero(); }
   for (int j = 0; j < Ny + 3; ++j) {
-    double2 ao = z2(), xo = z2(), ac = z2(), xc = z2();
+    C ao = Y::zero(), xo = Y::zero(), ac = Y::zero(), xc = Y::zero();
     if (j < Ny) {
       const size_t o = (size_t)j * M + m;
-      xo = om[o];
-      xc = chi[o];
-      double2 no = Nom[o], nop = Nom_p[o], nc = Nchi[o], ncp = Nchi_p[o];
-      ao = axpy(cz, nop, axpy(cg, no, scl(c1, xo)));
-      ac = axpy(cz, ncp, axpy(cg, nc, scl(c1, xc)));
+      const double2 no = Nom[o], nc = Nchi[o];
+      xo = Y::c(om[o]);
+      xc = Y::c(chi[o]);
+      ao = Y::axpy(cz, Y::c(Nom_p[o]), Y::axpy(cg, Y::c(no), Y::scl(c1, xo)));
+      ac = Y::axpy(cz, Y::c(Nchi_p[o]), Y::axpy(cg, Y::c(nc), Y::scl(c1, xc)));
       Nom_p[o] = no;
       Nchi_p[o] = nc;
     }
-    push(wa, ao); push(wx, xo); push(wb, ac); push(wy, xc);
+    ypush<Y>(wa, ao); ypush<Y>(wx, xo); ypush<Y>(wb, ac); ypush<Y>(wy, xc);
     const int i = j - 3;
     if (i < 0) continue;
-    double2 ro = z2(), rc = z2();
+    C ro = Y::zero(), rc = Y::zero();
     if (i > 0 && i < Ny - 1) {
-      ro = axpy(ca, band7(sB + 7 * i, wx), band7(sA + 7 * i, wa));
-      rc = axpy(ca, band7(sB + 7 * i, wy), band7(sA + 7 * i, wb));
+      ro = Y::axpy(ca, yband7<Y>(sB + 7 * i, wx), yband7<Y>(sA + 7 * i, wa));
+      rc = Y::axpy(ca, yband7<Y>(sB + 7 * i, wy), yband7<Y>(sA + 7 * i, wb));
     }
-    const double* Hi = H + (size_t)i * 11 * C;
-    const double l0 = Hi[0], l1 = Hi[C], l2 = Hi[2 * C];
-    scr[(size_t)i * M + m] = fwd(ro, l0, l1, l2, ho);
-    scr2[(size_t)i * M + m] = fwd(rc, l0, l1, l2, hc);
+    const R* Hi = H + (size_t)i * 11 * NC;
+    const R l0 = Hi[0], l1 = Hi[NC], l2 = Hi[2 * NC];
+    scr[(size_t)i * M + m] = yfwd<Y>(ro, l0, l1, l2, ho);
+    scr2[(size_t)i * M + m] = yfwd<Y>(rc, l0, l1, l2, hc);
   }
-  double2 no3[3] = {z2(), z2(), z2()}, nc3[3] = {z2(), z2(), z2()};
+  C no3[3] = {Y::zero(), Y::zero(), Y::zero()}, nc3[3] = {Y::zero(), Y::zero(), Y::zero()};
   for (int i = Ny - 1; i >= 0; --i) {
     const size_t o = (size_t)i * M + m;
-    const double* Hi = H + (size_t)i * 11 * C;
-    const double u0 = Hi[3 * C], u1 = Hi[4 * C], u2 = Hi[5 * C], dinv = Hi[6 * C];
-    om[o] = bwd(scr[o], u0, u1, u2, dinv, no3);
-    chi[o] = bwd(scr2[o], u0, u1, u2, dinv, nc3);
+    const R* Hi = H + (size_t)i * 11 * NC;
+    const R u0 = Hi[3 * NC], u1 = Hi[4 * NC], u2 = Hi[5 * NC], dinv = Hi[6 * NC];
+    om[o] = Y::d(ybwd<Y>(scr[o], u0, u1, u2, dinv, no3));
+    chi[o] = Y::d(ybwd<Y>(scr2[o], u0, u1, u2, dinv, nc3));
   }
 }
 
-__global__ void __launch_bounds__(128) k_helm(Geo g, YTabs t, const double* __restrict__ helm,
+template <class Y>
+__global__ void __launch_bounds__(128) k_helm(Geo g, YTabs t, const typename Y::R* __restrict__ helm,
                                               double2* om, double2* chi, const double2* __restrict__ Nchi,
                                               const double2* __restrict__ Nom, double2* Nchi_p, double2* Nom_p,
-                                              double2* scr, int s) { helm_body(g, t, helm, om, chi, Nchi, Nom, Nchi_p, Nom_p, scr, s, blockIdx.x); }
+                                              double2* scr, int s) { helm_body<Y>(g, t, helm, om, chi, Nchi, Nom, Nchi_p, Nom_p, scr, s, blockIdx.x); }
 
 
 // ---------------------------------------------------------------------------
@@ -314,87 +404,99 @@ __global__ void __launch_bounds__(128) k_helm(Geo g, YTabs t, const double* __re
 // v = v_p + c_a v_a + c_b v_b and chi likewise, with (c_a, c_b) making
 // dv/dy(+-1) = 0 through the precomputed influence matrix; then dv/dy = D1 v.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void poisson_body(Geo g, YTabs t, const double* __restrict__ helm,
-                                                 const double* __restrict__ pois, const double* __restrict__ infl,
-                                                 double2* v, double2* chi, double2* dv, double2* scr, int s, int bid) {
+template <class Y>
+__device__ __forceinline__ void poisson_body(Geo g, YTabs t, const typename Y::R* __restrict__ helm,
+                                             const typename Y::R* __restrict__ pois,
+                                             const typename Y::R* __restrict__ infl, double2* v, double2* chi,
+                                             double2* dv, double2* scr_, int s, int bid) {
+  typedef typename Y::R R;
+  typedef typename Y::C C;
   extern __shared__ double sm[];
   const int Ny = g.Ny;
-  double* sA = sm;
-  double* sB1 = sm + 7 * Ny;
-  double* sLU = sm + 14 * Ny;
-  load_tab(sA, t.A2, 7 * Ny);
-  load_tab(sB1, t.B1, 7 * Ny);
-  load_tab(sLU, t.lu1, 7 * Ny);
+  R* sA = reinterpret_cast<R*>(sm);
+  R* sB1 = sA + 7 * Ny;
+  R* sLU = sA + 14 * Ny;
+  R* sd0 = sA + 21 * Ny;
+  R* sdN = sA + 22 * Ny;
+  yload_tab<Y>(sA, t.A2, 7 * Ny);
+  yload_tab<Y>(sB1, t.B1, 7 * Ny);
+  yload_tab<Y>(sLU, t.lu1, 7 * Ny);
+  yload_tab<Y>(sd0, t.d0, Ny);
+  yload_tab<Y>(sdN, t.dN, Ny);
   __syncthreads();
   const int m = bid * blockDim.x + threadIdx.x;
   if (m >= g.M) return;
   const size_t M = g.M;
-  const size_t C = g.C;
+  const size_t NC = g.C;
   ModeInfo mi = mode_info(g, m);
   if (mi.nyq) {
     for (int i = 0; i < Ny; ++i) { size_t o = (size_t)i * M + m; v[o] = z2(); dv[o] = z2(); }
     return;
   }
-  const double* P = pois + mi.c;
-  const double* H = helm + (size_t)s * Ny * 11 * C + mi.c;
-  double2 w[7], hz[3];
+  const R* P = pois + mi.c;
+  const R* H = helm + (size_t)s * Ny * 11 * NC + mi.c;
+  C* scr = reinterpret_cast<C*>(scr_);
+  C w[7], hz[3];
 #pragma unroll
-  for (int d = 0; d < 7; ++d) w[d] = z2();
+  for (int d = 0; d < 7; ++d) w[d] = Y::zero();
 #pragma unroll
-  for (int d = 0; d < 3; ++d) hz[d] = z2();
+  for (int d = 0; d < 3; ++d) hz[d] = Y::zero();
   for (int j = 0; j < Ny + 3; ++j) {
-    push(w, j < Ny ? chi[(size_t)j * M + m] : z2());
+    ypush<Y>(w, j < Ny ? Y::c(chi[(size_t)j * M + m]) : Y::zero());
     const int i = j - 3;
     if (i < 0) continue;
-    double2 r = (i > 0 && i < Ny - 1) ? band7(sA + 7 * i, w) : z2();
-    const double* Pi = P + (size_t)i * 7 * C;
-    scr[(size_t)i * M + m] = fwd(r, Pi[0], Pi[C], Pi[2 * C], hz);
+    C r = (i > 0 && i < Ny - 1) ? yband7<Y>(sA + 7 * i, w) : Y::zero();
+    const R* Pi = P + (size_t)i * 7 * NC;
+    scr[(size_t)i * M + m] = yfwd<Y>(r, Pi[0], Pi[NC], Pi[2 * NC], hz);
   }
-  double2 nx[3] = {z2(), z2(), z2()};
-  double2 s0 = z2(), sN = z2();
+  C nx[3] = {Y::zero(), Y::zero(), Y::zero()};
+  C s0 = Y::zero(), sN = Y::zero();
   for (int i = Ny - 1; i >= 0; --i) {
     const size_t o = (size_t)i * M + m;
-    const double* Pi = P + (size_t)i * 7 * C;
-    double2 vp = bwd(scr[o], Pi[3 * C], Pi[4 * C], Pi[5 * C], Pi[6 * C], nx);
-    v[o] = vp;
-    s0 = axpy(t.d0[i], vp, s0);
-    sN = axpy(t.dN[i], vp, sN);
+    const R* Pi = P + (size_t)i * 7 * NC;
+    const C vp = ybwd<Y>(scr[o], Pi[3 * NC], Pi[4 * NC], Pi[5 * NC], Pi[6 * NC], nx);
+    scr[o] = vp;   // v_p parked in the scratch until the wall correction is known
+    s0 = Y::axpy(sd0[i], vp, s0);
+    sN = Y::axpy(sdN[i], vp, sN);
   }
-  const double* Gi = infl + (size_t)s * 4 * C + mi.c;
-  const double g11 = Gi[0], g12 = Gi[C], g21 = Gi[2 * C], g22 = Gi[3 * C];  // inverse influence matrix
-  const double2 cA = make_double2(-(g11 * s0.x + g12 * sN.x), -(g11 * s0.y + g12 * sN.y));
-  const double2 cB = make_double2(-(g21 * s0.x + g22 * sN.x), -(g21 * s0.y + g22 * sN.y));
+  const R* Gi = infl + (size_t)s * 4 * NC + mi.c;
+  const R g11 = Gi[0], g12 = Gi[NC], g21 = Gi[2 * NC], g22 = Gi[3 * NC];  // inverse influence matrix
+  const C cA = Y::sub(Y::zero(), Y::axpy(g12, sN, Y::scl(g11, s0)));
+  const C cB = Y::sub(Y::zero(), Y::axpy(g22, sN, Y::scl(g21, s0)));
+  C* scr2 = scr + (size_t)Ny * M;
 #pragma unroll
-  for (int d = 0; d < 7; ++d) w[d] = z2();
+  for (int d = 0; d < 7; ++d) w[d] = Y::zero();
 #pragma unroll
-  for (int d = 0; d < 3; ++d) hz[d] = z2();
+  for (int d = 0; d < 3; ++d) hz[d] = Y::zero();
   for (int j = 0; j < Ny + 3; ++j) {
-    double2 vj = z2();
+    C vj = Y::zero();
     if (j < Ny) {
       const size_t o = (size_t)j * M + m;
-      const double* Hj = H + (size_t)j * 11 * C;
-      const double xa = Hj[7 * C], xb = Hj[8 * C], va = Hj[9 * C], vb = Hj[10 * C];
-      vj = axpy(vb, cB, axpy(va, cA, v[o]));
-      v[o] = vj;
-      chi[o] = axpy(xb, cB, axpy(xa, cA, chi[o]));
+      const R* Hj = H + (size_t)j * 11 * NC;
+      const R xa = Hj[7 * NC], xb = Hj[8 * NC], va = Hj[9 * NC], vb = Hj[10 * NC];
+      vj = Y::axpy(vb, cB, Y::axpy(va, cA, scr[o]));
+      v[o] = Y::d(vj);
+      chi[o] = Y::d(Y::axpy(xb, cB, Y::axpy(xa, cA, Y::c(chi[o]))));
     }
-    push(w, vj);
+    ypush<Y>(w, vj);
     const int i = j - 3;
     if (i < 0) continue;
-    const double* l = sLU + 7 * i;
-    scr[(size_t)i * M + m] = fwd(band7(sB1 + 7 * i, w), l[0], l[1], l[2], hz);
+    const R* l = sLU + 7 * i;
+    scr2[(size_t)i * M + m] = yfwd<Y>(yband7<Y>(sB1 + 7 * i, w), l[0], l[1], l[2], hz);
   }
-  for (int d = 0; d < 3; ++d) nx[d] = z2();
+  for (int d = 0; d < 3; ++d) nx[d] = Y::zero();
   for (int i = Ny - 1; i >= 0; --i) {
     const size_t o = (size_t)i * M + m;
-    const double* lu = sLU + 7 * i;
-    dv[o] = bwd(scr[o], lu[3], lu[4], lu[5], lu[6], nx);
+    const R* lu = sLU + 7 * i;
+    dv[o] = Y::d(ybwd<Y>(scr2[o], lu[3], lu[4], lu[5], lu[6], nx));
   }
 }
 
-__global__ void __launch_bounds__(128) k_poisson(Geo g, YTabs t, const double* __restrict__ helm,
-                                                 const double* __restrict__ pois, const double* __restrict__ infl,
-                                                 double2* v, double2* chi, double2* dv, double2* scr, int s) { poisson_body(g, t, helm, pois, infl, v, chi, dv, scr, s, blockIdx.x); }
+template <class Y>
+__global__ void __launch_bounds__(128) k_poisson(Geo g, YTabs t, const typename Y::R* __restrict__ helm,
+                                                 const typename Y::R* __restrict__ pois,
+                                                 const typename Y::R* __restrict__ infl, double2* v, double2* chi,
+                                                 double2* dv, double2* scr, int s) { poisson_body<Y>(g, t, helm, pois, infl, v, chi, dv, scr, s, blockIdx.x); }
 
 
 // ---------------------------------------------------------------------------
@@ -854,8 +956,8 @@ __global__ void k_setup_pressure(Geo g, YTabs t, const double* __restrict__ pois
 // ---------------------------------------------------------------------------
 struct PreP { Geo g; YTabs t; const double2 *v, *om, *dv; const double *U1, *U3; double2 *u1o, *u3o, *om1o, *om3o; };
 struct NonlinP { Geo g; YTabs t; const double2 *H1, *H2, *H3; double2 *Nchi, *Nom, *scr; };
-struct HelmP { Geo g; YTabs t; const double* helm; double2 *om, *chi; const double2 *Nchi, *Nom; double2 *Nchi_p, *Nom_p, *scr; int s; };
-struct PoisP { Geo g; YTabs t; const double *helm, *pois, *infl; double2 *v, *chi, *dv, *scr; int s; };
+struct HelmP { Geo g; YTabs t; const void* helm; double2 *om, *chi; const double2 *Nchi, *Nom; double2 *Nchi_p, *Nom_p, *scr; int s; };
+struct PoisP { Geo g; YTabs t; const void *helm, *pois, *infl; double2 *v, *chi, *dv, *scr; int s; };
 struct MeanP { Geo g; YTabs t; const double *helm, *meanh; const double2 *H1, *H3; double *U1, *U3, *H1p, *H3p, *scal; int s; };
 
 template <class P> struct YBatch {
@@ -870,29 +972,43 @@ __device__ __forceinline__ int batch_run(const int* begin, int n, int b) {
   return r;
 }
 
+template <class Y>
 __global__ void __launch_bounds__(128) kb_pre(YBatch<PreP> B) {
   const int r = batch_run(B.begin, B.n, blockIdx.x);
   const PreP& p = B.p[r];
-  pre_body(p.g, p.t, p.v, p.om, p.dv, p.U1, p.U3, p.u1o, p.u3o, p.om1o, p.om3o, blockIdx.x - B.begin[r]);
+  pre_body<Y>(p.g, p.t, p.v, p.om, p.dv, p.U1, p.U3, p.u1o, p.u3o, p.om1o, p.om3o, blockIdx.x - B.begin[r]);
 }
+template <class Y>
 __global__ void __launch_bounds__(128) kb_nonlin(YBatch<NonlinP> B) {
   const int r = batch_run(B.begin, B.n, blockIdx.x);
   const NonlinP& p = B.p[r];
-  nonlin_body(p.g, p.t, p.H1, p.H2, p.H3, p.Nchi, p.Nom, p.scr, blockIdx.x - B.begin[r]);
+  nonlin_body<Y>(p.g, p.t, p.H1, p.H2, p.H3, p.Nchi, p.Nom, p.scr, blockIdx.x - B.begin[r]);
 }
+template <class Y>
 __global__ void __launch_bounds__(128) kb_helm(YBatch<HelmP> B) {
+  typedef typename Y::R R;
   const int r = batch_run(B.begin, B.n, blockIdx.x);
   const HelmP& p = B.p[r];
-  helm_body(p.g, p.t, p.helm, p.om, p.chi, p.Nchi, p.Nom, p.Nchi_p, p.Nom_p, p.scr, p.s, blockIdx.x - B.begin[r]);
+  helm_body<Y>(p.g, p.t, static_cast<const R*>(p.helm), p.om, p.chi, p.Nchi, p.Nom, p.Nchi_p, p.Nom_p, p.scr, p.s,
+               blockIdx.x - B.begin[r]);
 }
+template <class Y>
 __global__ void __launch_bounds__(128) kb_poisson(YBatch<PoisP> B) {
+  typedef typename Y::R R;
   const int r = batch_run(B.begin, B.n, blockIdx.x);
   const PoisP& p = B.p[r];
-  poisson_body(p.g, p.t, p.helm, p.pois, p.infl, p.v, p.chi, p.dv, p.scr, p.s, blockIdx.x - B.begin[r]);
+  poisson_body<Y>(p.g, p.t, static_cast<const R*>(p.helm), static_cast<const R*>(p.pois),
+                  static_cast<const R*>(p.infl), p.v, p.chi, p.dv, p.scr, p.s, blockIdx.x - B.begin[r]);
 }
 __global__ void __launch_bounds__(256) kb_mean(YBatch<MeanP> B) {
   const MeanP& p = B.p[blockIdx.x];
   mean_body(p.g, p.t, p.helm, p.meanh, p.H1, p.H3, p.U1, p.U3, p.H1p, p.H3p, p.scal, p.s, 0);
+}
+
+// Pair copy of the per-class tables for the double-float y-kernels.
+__global__ void k_split_tab(const double* __restrict__ src, dfr* dst, size_t n) {
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) dst[e] = df_split(src[e]);
 }
 
 }  // namespace
@@ -926,8 +1042,18 @@ cudaError_t launch_setup_tables(chan_s* h) {
   k_setup_pois<<<(h->C + 127) / 128, 128, 0, h->stream>>>(g, t, h->pois);
   k_setup_helm<<<(3 * h->C + 127) / 128, 128, 0, h->stream>>>(g, t, h->pois, h->helm, h->infl);
   k_setup_mean<<<1, 32, 0, h->stream>>>(g, t, h->helm, h->meanh);
+  if (h->prec == CHAN_PREC_F64X) {
+    const size_t C = h->C, Ny = h->Ny;
+    const double* src[3] = {h->pois, h->helm, h->infl};
+    dfr* dst[3] = {h->pois_df, h->helm_df, h->infl_df};
+    const size_t cnt[3] = {Ny * 7 * C, 3 * Ny * 11 * C, 12 * C};
+    for (int k = 0; k < 3; ++k)
+      k_split_tab<<<(unsigned)((cnt[k] + 255) / 256), 256, 0, h->stream>>>(src[k], dst[k], cnt[k]);
+  }
   return cudaGetLastError();
 }
+
+static bool use_df(const chan_s* h) { return h->prec == CHAN_PREC_F64X; }
 
 cudaError_t launch_derive(chan_s* h) {
   size_t sm = sizeof(double) * 35 * h->Ny;
@@ -939,18 +1065,26 @@ cudaError_t launch_derive(chan_s* h) {
 
 cudaError_t launch_pre(chan_s* h, double2* u1, double2* u3, double2* om1, double2* om3) {
   size_t sm = sizeof(double) * 14 * h->Ny;
-  cudaError_t e = smem_attr((const void*)k_pre, sm);
+  const void* fn = use_df(h) ? (const void*)k_pre_df : (const void*)k_pre;
+  cudaError_t e = smem_attr(fn, sm);
   if (e != cudaSuccess) return e;
-  k_pre<<<ygrid(h), kYThreads, sm, h->stream>>>(geo(h), ytabs(h), h->v, h->om, h->dv, h->U1, h->U3, u1, u3, om1, om3);
+  if (use_df(h))
+    k_pre_df<<<ygrid(h), kYThreads, sm, h->stream>>>(geo(h), ytabs(h), h->v, h->om, h->dv, h->U1, h->U3, u1, u3, om1, om3);
+  else
+    k_pre<<<ygrid(h), kYThreads, sm, h->stream>>>(geo(h), ytabs(h), h->v, h->om, h->dv, h->U1, h->U3, u1, u3, om1, om3);
   return cudaGetLastError();
 }
 
 cudaError_t launch_nonlin(chan_s* h, const double2* H1, const double2* H2, const double2* H3, double2* Nchi,
                           double2* Nom) {
   size_t sm = sizeof(double) * 14 * h->Ny;
-  cudaError_t e = smem_attr((const void*)k_nonlin, sm);
+  const void* fn = use_df(h) ? (const void*)k_nonlin_df : (const void*)k_nonlin;
+  cudaError_t e = smem_attr(fn, sm);
   if (e != cudaSuccess) return e;
-  k_nonlin<<<ygrid(h), kYThreads, sm, h->stream>>>(geo(h), ytabs(h), H1, H2, H3, Nchi, Nom, h->scr);
+  if (use_df(h))
+    k_nonlin_df<<<ygrid(h), kYThreads, sm, h->stream>>>(geo(h), ytabs(h), H1, H2, H3, Nchi, Nom, h->scr);
+  else
+    k_nonlin<<<ygrid(h), kYThreads, sm, h->stream>>>(geo(h), ytabs(h), H1, H2, H3, Nchi, Nom, h->scr);
   return cudaGetLastError();
 }
 
@@ -965,19 +1099,29 @@ cudaError_t launch_nonlin_scratch(chan_s* h, const double2* H1, const double2* H
 
 cudaError_t launch_helm(chan_s* h, const double2* Nchi, const double2* Nom, int s) {
   size_t sm = sizeof(double) * 14 * h->Ny;
-  cudaError_t e = smem_attr((const void*)k_helm, sm);
+  const void* fn = use_df(h) ? (const void*)k_helm<YDF> : (const void*)k_helm<YF64>;
+  cudaError_t e = smem_attr(fn, sm);
   if (e != cudaSuccess) return e;
-  k_helm<<<ygrid(h), kYThreads, sm, h->stream>>>(geo(h), ytabs(h), h->helm, h->om, h->chi, Nchi, Nom, h->Nchi_p,
-                                                 h->Nom_p, h->scr, s);
+  if (use_df(h))
+    k_helm<YDF><<<ygrid(h), kYThreads, sm, h->stream>>>(geo(h), ytabs(h), h->helm_df, h->om, h->chi, Nchi, Nom,
+                                                        h->Nchi_p, h->Nom_p, h->scr, s);
+  else
+    k_helm<YF64><<<ygrid(h), kYThreads, sm, h->stream>>>(geo(h), ytabs(h), h->helm, h->om, h->chi, Nchi, Nom,
+                                                         h->Nchi_p, h->Nom_p, h->scr, s);
   return cudaGetLastError();
 }
 
 cudaError_t launch_poisson(chan_s* h, int s) {
-  size_t sm = sizeof(double) * 21 * h->Ny;
-  cudaError_t e = smem_attr((const void*)k_poisson, sm);
+  size_t sm = sizeof(double) * 23 * h->Ny;
+  const void* fn = use_df(h) ? (const void*)k_poisson<YDF> : (const void*)k_poisson<YF64>;
+  cudaError_t e = smem_attr(fn, sm);
   if (e != cudaSuccess) return e;
-  k_poisson<<<ygrid(h), kYThreads, sm, h->stream>>>(geo(h), ytabs(h), h->helm, h->pois, h->infl, h->v, h->chi, h->dv,
-                                                    h->scr, s);
+  if (use_df(h))
+    k_poisson<YDF><<<ygrid(h), kYThreads, sm, h->stream>>>(geo(h), ytabs(h), h->helm_df, h->pois_df, h->infl_df,
+                                                           h->v, h->chi, h->dv, h->scr, s);
+  else
+    k_poisson<YF64><<<ygrid(h), kYThreads, sm, h->stream>>>(geo(h), ytabs(h), h->helm, h->pois, h->infl, h->v,
+                                                            h->chi, h->dv, h->scr, s);
   return cudaGetLastError();
 }
 
@@ -1020,9 +1164,11 @@ cudaError_t launch_pre_batch(chan_s* const* hs, int n, const BatchWork* w, cudaS
   }
   const int blocks = fill_begin(B, hs, n);
   const size_t sm = sizeof(double) * 14 * max_ny(hs, n);
-  cudaError_t e = smem_attr((const void*)kb_pre, sm);
+  const bool df = use_df(hs[0]);
+  cudaError_t e = smem_attr(df ? (const void*)kb_pre<YDF> : (const void*)kb_pre<YF64>, sm);
   if (e != cudaSuccess) return e;
-  kb_pre<<<blocks, kYThreads, sm, st>>>(B);
+  if (df) kb_pre<YDF><<<blocks, kYThreads, sm, st>>>(B);
+  else kb_pre<YF64><<<blocks, kYThreads, sm, st>>>(B);
   return cudaGetLastError();
 }
 
@@ -1034,9 +1180,11 @@ cudaError_t launch_nonlin_batch(chan_s* const* hs, int n, const BatchWork* w, cu
   }
   const int blocks = fill_begin(B, hs, n);
   const size_t sm = sizeof(double) * 14 * max_ny(hs, n);
-  cudaError_t e = smem_attr((const void*)kb_nonlin, sm);
+  const bool df = use_df(hs[0]);
+  cudaError_t e = smem_attr(df ? (const void*)kb_nonlin<YDF> : (const void*)kb_nonlin<YF64>, sm);
   if (e != cudaSuccess) return e;
-  kb_nonlin<<<blocks, kYThreads, sm, st>>>(B);
+  if (df) kb_nonlin<YDF><<<blocks, kYThreads, sm, st>>>(B);
+  else kb_nonlin<YF64><<<blocks, kYThreads, sm, st>>>(B);
   return cudaGetLastError();
 }
 
@@ -1044,14 +1192,16 @@ cudaError_t launch_helm_batch(chan_s* const* hs, int n, const BatchWork* w, cuda
   YBatch<HelmP> B;
   for (int r = 0; r < n; ++r) {
     chan_s* h = hs[r];
-    B.p[r] = HelmP{geo(h), ytabs(h), h->helm, h->om, h->chi, w[r].Nchi, w[r].Nom, h->Nchi_p, h->Nom_p, h->scr,
+    B.p[r] = HelmP{geo(h), ytabs(h), use_df(h) ? (const void*)h->helm_df : (const void*)h->helm, h->om, h->chi, w[r].Nchi, w[r].Nom, h->Nchi_p, h->Nom_p, h->scr,
                    (int)(h->nsub % 3)};
   }
   const int blocks = fill_begin(B, hs, n);
   const size_t sm = sizeof(double) * 14 * max_ny(hs, n);
-  cudaError_t e = smem_attr((const void*)kb_helm, sm);
+  const bool df = use_df(hs[0]);
+  cudaError_t e = smem_attr(df ? (const void*)kb_helm<YDF> : (const void*)kb_helm<YF64>, sm);
   if (e != cudaSuccess) return e;
-  kb_helm<<<blocks, kYThreads, sm, st>>>(B);
+  if (df) kb_helm<YDF><<<blocks, kYThreads, sm, st>>>(B);
+  else kb_helm<YF64><<<blocks, kYThreads, sm, st>>>(B);
   return cudaGetLastError();
 }
 
@@ -1060,13 +1210,17 @@ cudaError_t launch_poisson_batch(chan_s* const* hs, int n, const BatchWork* w, c
   YBatch<PoisP> B;
   for (int r = 0; r < n; ++r) {
     chan_s* h = hs[r];
-    B.p[r] = PoisP{geo(h), ytabs(h), h->helm, h->pois, h->infl, h->v, h->chi, h->dv, h->scr, (int)(h->nsub % 3)};
+    const bool df = use_df(h);
+    B.p[r] = PoisP{geo(h), ytabs(h), df ? (const void*)h->helm_df : (const void*)h->helm,
+                   df ? (const void*)h->pois_df : (const void*)h->pois, df ? (const void*)h->infl_df : (const void*)h->infl, h->v, h->chi, h->dv, h->scr, (int)(h->nsub % 3)};
   }
   const int blocks = fill_begin(B, hs, n);
-  const size_t sm = sizeof(double) * 21 * max_ny(hs, n);
-  cudaError_t e = smem_attr((const void*)kb_poisson, sm);
+  const size_t sm = sizeof(double) * 23 * max_ny(hs, n);
+  const bool df = use_df(hs[0]);
+  cudaError_t e = smem_attr(df ? (const void*)kb_poisson<YDF> : (const void*)kb_poisson<YF64>, sm);
   if (e != cudaSuccess) return e;
-  kb_poisson<<<blocks, kYThreads, sm, st>>>(B);
+  if (df) kb_poisson<YDF><<<blocks, kYThreads, sm, st>>>(B);
+  else kb_poisson<YF64><<<blocks, kYThreads, sm, st>>>(B);
   return cudaGetLastError();
 }
 
