@@ -413,6 +413,8 @@ def run_ours(args, c, name):
             modes[mode] = {
                 "value": replica_throughput(world, args.steps, nsub, pts, msm), "ms_per_step": msm / args.steps,
                 "roofline": {"kernel": dm, "achieved": am, "frac": fm, "unit": "TFLOP/s", "bound": "alu"},
+                "kernel_shares": {k: round(v[0] / max(1e-9, sum(x[0] for x in profm.values())), 4)
+                                  for k, v in profm.items() if v[1]},
                 "err_vs_fp64": {"after_substeps": args.warmup * nsub,
                                 "v_rel_l2": float(np.linalg.norm(snap["v"] - snap_main["v"]) / np.linalg.norm(snap_main["v"])),
                                 "omega2_rel_l2": float(np.linalg.norm(snap["omega2"] - snap_main["omega2"]) /

@@ -74,6 +74,10 @@ typedef struct chan_opts {
   const double* mesh;/* explicit wall-normal mesh double[Ny] (increasing from -1 to 1,
                         mirror symmetric), e.g. from chan_optimize_mesh; NULL: the
                         Kolmogorov-scaled formula                                      */
+  int slab_planes;   /* planes per slab of the plane-local transform passes (0: all Ny
+                        planes unless the twelve mixed-layout transform fields would
+                        pass 16 GiB, then the fewest equal slabs below that).  Results
+                        do not depend on it; only the transform buffers scale with it */
 } chan_opts;
 
 /* Fill *o with defaults: eta_w = 1, grid_re = 0, FP64, library stream. */

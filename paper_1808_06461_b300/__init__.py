@@ -41,7 +41,7 @@ class chan_opts(ctypes.Structure):
                 ("Nx", ctypes.c_int), ("Ny", ctypes.c_int), ("Nz", ctypes.c_int),
                 ("dt", ctypes.c_double), ("eta_w", ctypes.c_double), ("grid_re", ctypes.c_double),
                 ("precision", ctypes.c_int), ("stream", ctypes.c_void_p),
-                ("mesh", ctypes.POINTER(ctypes.c_double))]
+                ("mesh", ctypes.POINTER(ctypes.c_double)), ("slab_planes", ctypes.c_int)]
 
 
 class ChanError(RuntimeError):
@@ -125,11 +125,12 @@ class Channel:
     """One channel box on the current CUDA device (owns its device memory)."""
 
     def __init__(self, re_tau, Lx, Lz, Nx, Ny, Nz, dt, precision=CHAN_PREC_FP64, eta_w=1.0,
-                 grid_re=0.0, stream=None, mesh=None):
+                 grid_re=0.0, stream=None, mesh=None, slab_planes=0):
         o = chan_opts()
         _lib.chan_opts_default(ctypes.byref(o))
         o.re_tau, o.Lx, o.Lz, o.Nx, o.Ny, o.Nz, o.dt = re_tau, Lx, Lz, Nx, Ny, Nz, dt
         o.eta_w, o.grid_re, o.precision = eta_w, grid_re, precision
+        o.slab_planes = int(slab_planes)
         o.stream = stream
         if mesh is not None:
             self._mesh = np.ascontiguousarray(mesh, dtype=np.float64)

@@ -95,12 +95,26 @@ struct Traced {
 };
 
 // Work-field slots (Fourier layout)
-enum { WF_U1 = 0, WF_U3 = 1, WF_OM1 = 2, WF_OM3 = 3, WF_H1 = 4, WF_H2 = 5, WF_H3 = 6, WF_NCHI = 7, WF_NOM = 8, NWF = 14 };
+// (u_1, u_3 double as the sweep scratch once the transforms have read them; the
+// filter pass puts P(u_i u_j) in slots 2..7 and the filtered pressure its output in 8)
+enum { WF_U1 = 0, WF_U3 = 1, WF_OM1 = 2, WF_OM3 = 3, WF_H1 = 4, WF_H2 = 5, WF_H3 = 6, WF_NCHI = 7, WF_NOM = 8, NWF = 9 };
 
 double2* wf(chan_s* h, int k) { return h->wf + (size_t)k * fsize(h); }
 void* mixed(chan_s* h, int k) {
   const size_t es = h->prec == CHAN_PREC_MIXED ? sizeof(float2) : sizeof(double2);
-  return static_cast<char*>(h->mixed) + (size_t)k * h->Ny * h->L3 * h->nxh * es;
+  return static_cast<char*>(h->mixed) + (size_t)k * h->slab * h->L3 * h->nxh * es;
+}
+
+// Planes per slab of the transform passes (see chan_opts.slab_planes).
+int slab_planes(int Nx, int Ny, int Nz, int prec, int req) {
+  if (req > 0) return req < Ny ? req : Ny;
+  const size_t es = prec == CHAN_PREC_MIXED ? sizeof(float2) : sizeof(double2);
+  const size_t plane = 12 * (size_t)(3 * Nz / 2) * (size_t)(Nx / 2) * es;
+  size_t smax = ((size_t)16 << 30) / plane;
+  if (smax < 1) smax = 1;
+  if ((size_t)Ny <= smax) return Ny;
+  const size_t nslab = (Ny + smax - 1) / smax;
+  return (int)((Ny + nslab - 1) / nslab);
 }
 
 void clean_modes(chan_s* h, double2* f) {
@@ -133,13 +147,18 @@ void run_pre(chan_s* h) {
 }
 
 // H = u x omega of the current state into WF_H1..WF_H3 (after run_pre).
+// The transforms are plane-local: slab by slab through the mixed buffers.
 void run_nonlinear(chan_s* h) {
-  const double2* in[6] = {wf(h, WF_U1), h->v, wf(h, WF_U3), wf(h, WF_OM1), h->om, wf(h, WF_OM3)};
   void* mx[6] = {mixed(h, 0), mixed(h, 1), mixed(h, 2), mixed(h, 3), mixed(h, 4), mixed(h, 5)};
-  { Traced t(h, KID_ZINV); CK(launch_zinv(h, in, nullptr, mx, 6)); }
-  { Traced t(h, KID_XPASS); CK(launch_xpass(h, 0, mx, mx)); }
-  double2* Hout[3] = {wf(h, WF_H1), wf(h, WF_H2), wf(h, WF_H3)};
-  { Traced t(h, KID_ZFWD); CK(launch_zfwd(h, mx, Hout, 3)); }
+  for (int y0 = 0; y0 < h->Ny; y0 += h->slab) {
+    const int ny = h->Ny - y0 < h->slab ? h->Ny - y0 : h->slab;
+    const size_t o = (size_t)y0 * h->M;
+    const double2* in[6] = {wf(h, WF_U1) + o, h->v + o, wf(h, WF_U3) + o, wf(h, WF_OM1) + o, h->om + o, wf(h, WF_OM3) + o};
+    { Traced t(h, KID_ZINV); CK(launch_zinv(h, in, nullptr, mx, 6, ny)); }
+    { Traced t(h, KID_XPASS); CK(launch_xpass(h, 0, mx, mx, ny)); }
+    double2* Hout[3] = {wf(h, WF_H1) + o, wf(h, WF_H2) + o, wf(h, WF_H3) + o};
+    { Traced t(h, KID_ZFWD); CK(launch_zfwd(h, mx, Hout, 3, ny)); }
+  }
 }
 
 void run_substep(chan_s* h) {
@@ -186,7 +205,7 @@ void set_filter(chan_s* h, int kind, double p1, double p3) {
 
 // Device bytes chan_init_ex requests for a box (the filter transfer function,
 // allocated on the first filter call, included).  Mirrors the allocations below.
-size_t footprint(int Nx, int Ny, int Nz, int prec) {
+size_t footprint(int Nx, int Ny, int Nz, int prec) {   // with the automatic slab
   const size_t nxh = Nx / 2, M = (size_t)Nz * nxh, C = (size_t)(Nz / 2) * nxh, n = (size_t)Ny * M;
   const size_t L1 = 3 * (size_t)Nx / 2, L3 = 3 * (size_t)Nz / 2;
   const size_t es = prec == CHAN_PREC_MIXED ? sizeof(float2) : sizeof(double2);
@@ -197,9 +216,10 @@ size_t footprint(int Nx, int Ny, int Nz, int prec) {
   b += ((size_t)Ny * 7 * C + 3 * (size_t)Ny * 11 * C + 12 * C + 3 * ((size_t)Ny + 1)) * sizeof(double);
   if (prec == CHAN_PREC_F64X) b += ((size_t)Ny * 7 * C + 3 * (size_t)Ny * 11 * C + 12 * C) * sizeof(dfr);
   b += (L1 + L3) * (prec == CHAN_PREC_MIXED ? sizeof(float2) : sizeof(double2));             // twiddles
+  const size_t S = slab_planes(Nx, Ny, Nz, prec, 0);
   b += (size_t)(NWF + 9) * n * sizeof(double2);                                              // work fields
-  b += 12 * (size_t)Ny * L3 * nxh * es;                                                      // mixed fields
-  b += 2 * n * sizeof(double2);                                                              // sweep scratch
+  b += 12 * S * L3 * nxh * es;                                                               // mixed fields
+  b += 6 * S * M * sizeof(double2);                                                          // filter products
   b += (CHAN_NSTAT * (size_t)Ny + 2) * sizeof(double);                                       // statistics
   b += M * sizeof(double);                                                                   // filter G
   return b;
@@ -326,6 +346,7 @@ int chan_init_ex(chan_t* out, const chan_opts* o) {
   if (o->Ny < 9 || o->Ny % 2 == 0) return bad(nullptr, "chan_init: Ny must be odd and >= 9");
   if (o->precision != CHAN_PREC_FP64 && o->precision != CHAN_PREC_MIXED && o->precision != CHAN_PREC_F64X)
     return bad(nullptr, "chan_init: unknown precision");
+  if (o->slab_planes < 0) return bad(nullptr, "chan_init: slab_planes must be >= 0");
   const int L1 = 3 * o->Nx / 2, L3 = 3 * o->Nz / 2;
   const size_t es = o->precision == CHAN_PREC_MIXED ? 8 : 16;
   if (2 * 6 * (size_t)(L1 + 1) * es > 227 * 1024 || 2 * (size_t)(L3 + 1) * es > 100 * 1024)
@@ -445,8 +466,10 @@ int chan_init_ex(chan_t* out, const chan_opts* o) {
     h->nwf = NWF + 9;
     h->wf = dalloc<double2>(h, (size_t)h->nwf * n);
     h->nmix = 12;
-    h->mixed = dalloc<unsigned char>(h, (size_t)h->nmix * Ny * L3 * h->nxh * es);
-    h->scr = dalloc<double2>(h, 2 * n);
+    h->slab = slab_planes(h->Nx, h->Ny, h->Nz, h->prec, o->slab_planes);
+    h->mixed = dalloc<unsigned char>(h, (size_t)h->nmix * h->slab * L3 * h->nxh * es);
+    h->pbb = dalloc<double2>(h, 6 * (size_t)h->slab * h->M);
+    h->scr = wf(h, WF_U1);   // [2][Ny][M]: the u_1, u_3 slots
     h->stat = dalloc<double>(h, CHAN_NSTAT * Ny + 2);
     CK(fft_configure(h));
     CK(launch_setup_tables(h));
@@ -602,20 +625,30 @@ int chan_filter_stresses(chan_t h, int kind, double p1, double p3, double* ubar,
   try {
     set_filter(h, kind, p1, p3);
     run_pre(h);
-    const double2* in[6] = {wf(h, WF_U1), h->v, wf(h, WF_U3), wf(h, WF_U1), h->v, wf(h, WF_U3)};
     const int applyG[6] = {0, 0, 0, 1, 1, 1};
     void* mx[12];
     for (int k = 0; k < 12; ++k) mx[k] = mixed(h, k);
-    { Traced t(h, KID_ZINV); CK(launch_zinv(h, in, applyG, mx, 6)); }
-    { Traced t(h, KID_XPASS); CK(launch_xpass(h, 1, mx + 3, mx + 6)); }   // ubar_i ubar_j -> slots 6..11
-    { Traced t(h, KID_XPASS); CK(launch_xpass(h, 1, mx, mx)); }           // u_i u_j       -> slots 0..5
-    double2* fo[12];
-    for (int k = 0; k < 12; ++k) fo[k] = wf(h, 2 + k);
-    { Traced t(h, KID_ZFWD); CK(launch_zfwd(h, mx, fo, 12)); }
-    const double2* u[3] = {wf(h, WF_U1), h->v, wf(h, WF_U3)};
-    const double2* puu[6] = {fo[0], fo[1], fo[2], fo[3], fo[4], fo[5]};
-    const double2* pbb[6] = {fo[6], fo[7], fo[8], fo[9], fo[10], fo[11]};
-    { Traced t(h, KID_FILTER_OUT); CK(launch_filter_out(h, u, puu, pbb, filt(h, 0), filt(h, 3))); }
+    // slab by slab: P(u_i u_j) to work slots 2..7 (kept for the pressure and the
+    // database record), P(ubar_i ubar_j) to the slab buffer, then ubar_i and tau_ij
+    for (int y0 = 0; y0 < h->Ny; y0 += h->slab) {
+      const int ny = h->Ny - y0 < h->slab ? h->Ny - y0 : h->slab;
+      const size_t o = (size_t)y0 * h->M, sn = (size_t)h->slab * h->M;
+      const double2* u[3] = {wf(h, WF_U1) + o, h->v + o, wf(h, WF_U3) + o};
+      const double2* in[6] = {u[0], u[1], u[2], u[0], u[1], u[2]};
+      { Traced t(h, KID_ZINV); CK(launch_zinv(h, in, applyG, mx, 6, ny)); }
+      { Traced t(h, KID_XPASS); CK(launch_xpass(h, 1, mx + 3, mx + 6, ny)); }   // ubar_i ubar_j -> slots 6..11
+      { Traced t(h, KID_XPASS); CK(launch_xpass(h, 1, mx, mx, ny)); }           // u_i u_j       -> slots 0..5
+      double2* fo[12];
+      for (int k = 0; k < 6; ++k) { fo[k] = wf(h, 2 + k) + o; fo[6 + k] = h->pbb + k * sn; }
+      { Traced t(h, KID_ZFWD); CK(launch_zfwd(h, mx, fo, 12, ny)); }
+      const double2* puu[6] = {fo[0], fo[1], fo[2], fo[3], fo[4], fo[5]};
+      const double2* pbb[6] = {fo[6], fo[7], fo[8], fo[9], fo[10], fo[11]};
+      double2* ub[3];
+      double2* ta[6];
+      for (int k = 0; k < 3; ++k) ub[k] = filt(h, k) + o;
+      for (int k = 0; k < 6; ++k) ta[k] = filt(h, 3 + k) + o;
+      { Traced t(h, KID_FILTER_OUT); CK(launch_filter_out(h, u, puu, pbb, ub, ta, ny)); }
+    }
     const size_t n = fsize(h);
     if (ubar) CK(cudaMemcpyAsync(ubar, filt(h, 0), 3 * n * sizeof(double2), cudaMemcpyDeviceToHost, h->stream));
     if (tau) CK(cudaMemcpyAsync(tau, filt(h, 3), 6 * n * sizeof(double2), cudaMemcpyDeviceToHost, h->stream));
@@ -635,12 +668,16 @@ int chan_filtered_enstrophy(chan_t h, int kind, double p1, double p3, double* en
   try {
     set_filter(h, kind, p1, p3);
     run_pre(h);
-    const double2* in[3] = {wf(h, WF_OM1), h->om, wf(h, WF_OM3)};
     void* mx[3] = {mixed(h, 0), mixed(h, 1), mixed(h, 2)};
-    { Traced t(h, KID_ZINV); CK(launch_zinv(h, in, nullptr, mx, 3)); }
-    { Traced t(h, KID_XPASS); CK(launch_xpass(h, 2, mx, mx)); }
-    double2* fo[1] = {wf(h, 4)};
-    { Traced t(h, KID_ZFWD); CK(launch_zfwd(h, mx, fo, 1)); }
+    for (int y0 = 0; y0 < h->Ny; y0 += h->slab) {
+      const int ny = h->Ny - y0 < h->slab ? h->Ny - y0 : h->slab;
+      const size_t o = (size_t)y0 * h->M;
+      const double2* in[3] = {wf(h, WF_OM1) + o, h->om + o, wf(h, WF_OM3) + o};
+      { Traced t(h, KID_ZINV); CK(launch_zinv(h, in, nullptr, mx, 3, ny)); }
+      { Traced t(h, KID_XPASS); CK(launch_xpass(h, 2, mx, mx, ny)); }
+      double2* fo[1] = {wf(h, 4) + o};
+      { Traced t(h, KID_ZFWD); CK(launch_zfwd(h, mx, fo, 1, ny)); }
+    }
     { Traced t(h, KID_APPLY_G); CK(launch_apply_G(h, wf(h, 4), wf(h, 5))); }
     if (ens) {
       CK(cudaMemcpyAsync(ens, wf(h, 5), fsize(h) * sizeof(double2), cudaMemcpyDeviceToHost, h->stream));
@@ -830,6 +867,7 @@ int chan_autotune(chan_t h) {
     run_pre(h);
     const double2* in[6] = {wf(h, WF_U1), h->v, wf(h, WF_U3), wf(h, WF_OM1), h->om, wf(h, WF_OM3)};
     void* mx[6] = {mixed(h, 0), mixed(h, 1), mixed(h, 2), mixed(h, 3), mixed(h, 4), mixed(h, 5)};
+    const int ny = h->slab;   // timed on the first slab
     auto timed = [&](auto fn) {
       float best = 1e30f;
       for (int rep = 0; rep < 3; ++rep) {
@@ -848,15 +886,15 @@ int chan_autotune(chan_t h) {
     for (int kb = 1; kb <= 16 && kb <= h->nxh; kb *= 2) {
       if ((size_t)kb * (h->L3 + 1) * es > 110 * 1024) break;
       h->kb_z = kb;
-      float t = timed([&] { CK(launch_zinv(h, in, nullptr, mx, 6)); });
+      float t = timed([&] { CK(launch_zinv(h, in, nullptr, mx, 6, ny)); });
       if (t < best_t) { best_t = t; best_kb = kb; }
     }
     h->kb_z = best_kb;
-    CK(launch_zinv(h, in, nullptr, mx, 6));   // fresh inputs for the x-pass timings
+    CK(launch_zinv(h, in, nullptr, mx, 6, ny));   // fresh inputs for the x-pass timings
     best_t = 1e30f;
     for (int nt : {128, 256, 512}) {
       h->xthreads = nt;
-      float t = timed([&] { CK(launch_xpass(h, 0, mx, mx)); CK(launch_zinv(h, in, nullptr, mx, 6)); });
+      float t = timed([&] { CK(launch_xpass(h, 0, mx, mx, ny)); CK(launch_zinv(h, in, nullptr, mx, 6, ny)); });
       if (t < best_t) { best_t = t; best_nt = nt; }
     }
     h->xthreads = best_nt;
@@ -922,6 +960,8 @@ int chan_batch_create(chan_batch_t* out, chan_t* runs, int n, void* stream) {
       return bad(nullptr, "chan_batch_create: runs differ in precision or device");
     for (int q = 0; q < r; ++q)
       if (runs[q] == runs[r]) return bad(nullptr, "chan_batch_create: a run appears twice");
+    if (runs[r]->slab != runs[r]->Ny)
+      return bad(nullptr, "chan_batch_create: a run's transforms are split into slabs (too large to pack)");
   }
   chan_batch_s* b = new (std::nothrow) chan_batch_s();
   if (!b) return bad(nullptr, "chan_batch_create: out of host memory", CHAN_ENOMEM);

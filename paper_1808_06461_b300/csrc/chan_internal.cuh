@@ -77,9 +77,11 @@ struct chan_s {
   // work (device)
   double2* wf;             // Fourier work fields [NWF][Ny][M]
   int nwf;
-  void* mixed;             // mixed fields [NMIX][Ny][L3][nxh]
+  void* mixed;             // mixed fields of one slab [NMIX][slab][L3][nxh]
   int nmix;
-  double2* scr;            // wall-normal sweep scratch [2][Ny][M]
+  int slab;                // planes per transform slab (Ny unless the mixed fields would pass 16 GiB)
+  double2* pbb;            // filter pass: products of the filtered velocities of one slab [6][slab][M]
+  double2* scr;            // wall-normal sweep scratch [2][Ny][M] (aliases the u_1, u_3 work slots)
   double* G;               // filter transfer [M]
   double* prs;             // filtered-pressure homogeneous solutions [Ny][2][C] (lazy)
   double* prsinv;          // their inverse wall-derivative matrices [4][C]
@@ -128,8 +130,9 @@ cudaError_t launch_nonlin_scratch(chan_s* h, const double2* H1, const double2* H
 cudaError_t launch_helm(chan_s* h, const double2* Nchi, const double2* Nom, int s);
 cudaError_t launch_poisson(chan_s* h, int s);
 cudaError_t launch_mean(chan_s* h, const double2* H1, const double2* H3, int s);
+// Filter epilogue over ny planes (pointers at the slab's first plane).
 cudaError_t launch_filter_out(chan_s* h, const double2* const* u, const double2* const* puu,
-                              const double2* const* pbb, double2* ubar, double2* tau);
+                              const double2* const* pbb, double2* const* ubar, double2* const* tau, int ny);
 cudaError_t launch_apply_G(chan_s* h, const double2* in, double2* out);
 cudaError_t launch_pressure(chan_s* h, const double2* const* P, double2* out);
 cudaError_t launch_setup_pressure(chan_s* h);
@@ -149,9 +152,10 @@ cudaError_t launch_xpass_batch(chan_s* const* hs, int n, const BatchWork* w, cud
 cudaError_t launch_zfwd_batch(chan_s* const* hs, int n, const BatchWork* w, cudaStream_t st);
 
 // FFT passes.  in/out are arrays of nf device pointers.
-cudaError_t launch_zinv(chan_s* h, const double2* const* in, const int* apply_G, void* const* out, int nf);
-cudaError_t launch_xpass(chan_s* h, int mode, void* const* in, void* const* out);
-cudaError_t launch_zfwd(chan_s* h, void* const* in, double2* const* out, int nf);
+// Transform passes over ny planes; the pointers address the first plane of the slab.
+cudaError_t launch_zinv(chan_s* h, const double2* const* in, const int* apply_G, void* const* out, int nf, int ny);
+cudaError_t launch_xpass(chan_s* h, int mode, void* const* in, void* const* out, int ny);
+cudaError_t launch_zfwd(chan_s* h, void* const* in, double2* const* out, int nf, int ny);
 cudaError_t fft_configure(chan_s* h);
 // Default z-pass columns per CTA: as many as fit 56 KB of shared memory, at most 16.
 int pick_kb(int nxh, int L3, size_t es);

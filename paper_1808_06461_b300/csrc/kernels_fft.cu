@@ -523,11 +523,11 @@ static ZArgs zargs(chan_s* h, size_t es) {
 
 static size_t fft_esize(const chan_s* h) { return h->prec == CHAN_PREC_MIXED ? sizeof(float2) : sizeof(double2); }
 
-cudaError_t launch_zinv(chan_s* h, const double2* const* in, const int* apply_G, void* const* out, int nf) {
+cudaError_t launch_zinv(chan_s* h, const double2* const* in, const int* apply_G, void* const* out, int nf, int ny) {
   const size_t es = fft_esize(h);
   ZArgs A = zargs(h, es);
   for (int f = 0; f < nf; ++f) { A.in[f] = in[f]; A.out[f] = out[f]; A.applyG[f] = apply_G ? apply_G[f] : 0; }
-  dim3 grid((h->nxh + A.KB - 1) / A.KB, h->Ny, nf);
+  dim3 grid((h->nxh + A.KB - 1) / A.KB, ny, nf);
   size_t sm = (size_t)A.KB * A.ld * es;
   if (h->prec == CHAN_PREC_FP64) k_zinv<double><<<grid, 256, sm, h->stream>>>(A, (const double2*)h->tw3);
   else if (h->prec == CHAN_PREC_MIXED) k_zinv<float><<<grid, 256, sm, h->stream>>>(A, (const float2*)h->tw3);
@@ -535,11 +535,11 @@ cudaError_t launch_zinv(chan_s* h, const double2* const* in, const int* apply_G,
   return cudaGetLastError();
 }
 
-cudaError_t launch_zfwd(chan_s* h, void* const* in, double2* const* out, int nf) {
+cudaError_t launch_zfwd(chan_s* h, void* const* in, double2* const* out, int nf, int ny) {
   const size_t es = fft_esize(h);
   ZArgs A = zargs(h, es);
   for (int f = 0; f < nf; ++f) { A.out[f] = in[f]; A.outd[f] = out[f]; }
-  dim3 grid((h->nxh + A.KB - 1) / A.KB, h->Ny, nf);
+  dim3 grid((h->nxh + A.KB - 1) / A.KB, ny, nf);
   size_t sm = (size_t)A.KB * A.ld * es;
   if (h->prec == CHAN_PREC_FP64) k_zfwd<double><<<grid, 256, sm, h->stream>>>(A, (const double2*)h->tw3);
   else if (h->prec == CHAN_PREC_MIXED) k_zfwd<float><<<grid, 256, sm, h->stream>>>(A, (const float2*)h->tw3);
@@ -547,7 +547,7 @@ cudaError_t launch_zfwd(chan_s* h, void* const* in, double2* const* out, int nf)
   return cudaGetLastError();
 }
 
-cudaError_t launch_xpass(chan_s* h, int mode, void* const* in, void* const* out) {
+cudaError_t launch_xpass(chan_s* h, int mode, void* const* in, void* const* out, int ny) {
   const size_t es = fft_esize(h);
   XArgs A;
   memset(&A, 0, sizeof(A));
@@ -557,7 +557,7 @@ cudaError_t launch_xpass(chan_s* h, int mode, void* const* in, void* const* out)
   A.nxh = h->nxh; A.L1 = h->L1; A.L3 = h->L3; A.ld = h->L1 + 1;
   A.scale = 1.0 / ((double)h->L1 * (double)h->L3);
   A.pl = h->p1;
-  dim3 grid(h->L3 / 2, h->Ny);
+  dim3 grid(h->L3 / 2, ny);
   size_t sm = 6 * (size_t)A.ld * es;
   const int nt = h->xthreads > 0 ? h->xthreads : 256;
   if (h->prec == CHAN_PREC_FP64) {

@@ -9,10 +9,10 @@ struct FiltArgs {
   const double2* u[3];
   const double2* puu[6];
   const double2* pbb[6];
-  double2* ubar;   // [3][Ny][M]
-  double2* tau;    // [6][Ny][M]
+  double2* ubar[3];
+  double2* tau[6];
   const double* G;
-  size_t n;        // Ny * M
+  size_t n;        // planes * M
   int M;
 };
 
@@ -23,12 +23,12 @@ __global__ void k_filter_out(FiltArgs A) {
 #pragma unroll
   for (int f = 0; f < 3; ++f) {
     double2 x = A.u[f][e];
-    A.ubar[(size_t)f * A.n + e] = make_double2(g * x.x, g * x.y);
+    A.ubar[f][e] = make_double2(g * x.x, g * x.y);
   }
 #pragma unroll
   for (int p = 0; p < 6; ++p) {
     double2 a = A.puu[p][e], b = A.pbb[p][e];
-    A.tau[(size_t)p * A.n + e] = make_double2(fma(g, a.x, -b.x), fma(g, a.y, -b.y));
+    A.tau[p][e] = make_double2(fma(g, a.x, -b.x), fma(g, a.y, -b.y));
   }
 }
 
@@ -136,12 +136,12 @@ __global__ void __launch_bounds__(256) k_stats(StatArgs A) {
 }  // namespace
 
 cudaError_t launch_filter_out(chan_s* h, const double2* const* u, const double2* const* puu, const double2* const* pbb,
-                              double2* ubar, double2* tau) {
+                              double2* const* ubar, double2* const* tau, int ny) {
   FiltArgs A;
-  for (int f = 0; f < 3; ++f) A.u[f] = u[f];
-  for (int p = 0; p < 6; ++p) { A.puu[p] = puu[p]; A.pbb[p] = pbb[p]; }
-  A.ubar = ubar; A.tau = tau; A.G = h->G;
-  A.n = (size_t)h->Ny * h->M;
+  for (int f = 0; f < 3; ++f) { A.u[f] = u[f]; A.ubar[f] = ubar[f]; }
+  for (int p = 0; p < 6; ++p) { A.puu[p] = puu[p]; A.pbb[p] = pbb[p]; A.tau[p] = tau[p]; }
+  A.G = h->G;
+  A.n = (size_t)ny * h->M;
   A.M = h->M;
   k_filter_out<<<(unsigned)((A.n + 255) / 256), 256, 0, h->stream>>>(A);
   return cudaGetLastError();

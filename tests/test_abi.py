@@ -50,3 +50,26 @@ def test_null_handle_calls_fail_cleanly():
     assert lib.chan_sync(None) == chan.CHAN_EINVAL
     assert lib.chan_fourier_count(None) == 0
     lib.chan_free(None)
+
+
+def test_init_rejects_a_negative_slab():
+    lib = chan.library()
+    o = chan.chan_opts()
+    lib.chan_opts_default(ctypes.byref(o))
+    o.re_tau, o.Lx, o.Lz, o.Nx, o.Ny, o.Nz, o.dt = 180.0, 3.14, 1.57, 32, 49, 32, 1e-3
+    o.slab_planes = -1
+    h = ctypes.c_void_p()
+    assert lib.chan_init_ex(ctypes.byref(h), ctypes.byref(o)) == chan.CHAN_EINVAL
+    assert not h.value
+    assert "slab" in lib.chan_last_error(None).decode()
+
+
+def test_footprint_of_the_large_grids():
+    """The transform buffers are slab-sized: the Re_tau 1000 grid (768 x 385 x 768) in FP64 and
+    in mixed precision stays below 90 GB; the 12 mixed fields of one slab stay below 16 GiB."""
+    for prec in (chan.CHAN_PREC_FP64, chan.CHAN_PREC_MIXED):
+        assert chan.footprint_bytes(768, 385, 768, prec) < 90e9
+    # the slab share of the footprint: FP64 384 x 257 x 384 holds all 257 planes at once
+    small = chan.footprint_bytes(384, 257, 384, chan.CHAN_PREC_FP64)
+    n = 257 * 384 * 192
+    assert small > (6 + 18) * n * 16 + 12 * 257 * 576 * 192 * 16
