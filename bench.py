@@ -89,12 +89,8 @@ def fft_flops(L, pruned=True):
 # DRAM bytes per wall-normal plane of each kernel launch, from ncu on the 384 x 33 x 384
 # profiling case (profiles/*_re550_384x33x384.md: dram__bytes_read.sum + dram__bytes_write.sum
 # divided by 33); valid for Nx = Nz = 384 only and only while the kernels are as captured.
-NCU_BYTES_PER_PLANE = {("k_xpass", "fp64"): (350.834688e6 + 130.674432e6) / 33,
-                       ("k_xpass", "f64x"): (350.442752e6 + 128.765184e6) / 33,
-                       ("k_helm", "fp64"): (373.894656e6 + 193.170944e6) / 33,
-                       ("k_zinv", "fp64"): (233.095936e6 + 298.214912e6) / 33}
-NCU_PIPE = {("k_xpass", "fp64"): ("fp64", 0.8593), ("k_xpass", "f64x"): ("issue", 0.7508),
-            ("k_helm", "fp64"): ("fp64", 0.8079), ("k_zinv", "fp64"): ("fp64", 0.8530)}
+NCU_BYTES_PER_PLANE = {("k_xpass", "fp64"): (350.394624e6 + 131.588608e6) / 33}
+NCU_PIPE = {("k_xpass", "fp64"): ("fp64", 0.8574)}
 
 
 # per mode-point flops of the wall-normal kernels (read off their sweeps)
