@@ -128,6 +128,8 @@ void after_state_upload(chan_s* h) {
   clean_modes(h, h->v);
   clean_modes(h, h->om);
   { Traced t(h, KID_DERIVE); CK(launch_derive(h)); }
+  if (h->prec == CHAN_PREC_F64X)   // the substep keeps its Fourier fields as FP32 pairs
+    for (double2* f : {h->v, h->om, h->chi, h->dv}) CK(launch_to_pairs(h, f, fsize(h)));
   CK(cudaMemsetAsync(h->Nchi_p, 0, fsize(h) * sizeof(double2), h->stream));
   CK(cudaMemsetAsync(h->Nom_p, 0, fsize(h) * sizeof(double2), h->stream));
   CK(cudaMemsetAsync(h->H1m_p, 0, h->Ny * sizeof(double), h->stream));
@@ -157,7 +159,7 @@ void run_nonlinear(chan_s* h) {
     { Traced t(h, KID_ZINV); CK(launch_zinv(h, in, nullptr, mx, 6, ny)); }
     { Traced t(h, KID_XPASS); CK(launch_xpass(h, 0, mx, mx, ny)); }
     double2* Hout[3] = {wf(h, WF_H1) + o, wf(h, WF_H2) + o, wf(h, WF_H3) + o};
-    { Traced t(h, KID_ZFWD); CK(launch_zfwd(h, mx, Hout, 3, ny)); }
+    { Traced t(h, KID_ZFWD); CK(launch_zfwd(h, mx, Hout, 3, ny, 1)); }
   }
 }
 
@@ -538,8 +540,16 @@ static int get_state_impl(chan_t h, void* v, void* om, void* U1, void* U3, cudaM
   if (!h->have_state) return bad(h, "chan_get_state: no state set", CHAN_ESTATE);
   try {
     const size_t n = fsize(h);
-    if (v) CK(cudaMemcpyAsync(v, h->v, n * sizeof(double2), k, h->stream));
-    if (om) CK(cudaMemcpyAsync(om, h->om, n * sizeof(double2), k, h->stream));
+    const double2* sv = h->v;
+    const double2* so = h->om;
+    if (h->prec == CHAN_PREC_F64X) {   // pairs back to FP64: into the caller's device arrays, or the u_1, u_3 slots
+      double2* dv_ = k == cudaMemcpyDeviceToDevice ? static_cast<double2*>(v) : wf(h, WF_U1);
+      double2* do_ = k == cudaMemcpyDeviceToDevice ? static_cast<double2*>(om) : wf(h, WF_U3);
+      if (v) { CK(launch_from_pairs(h, h->v, dv_, n)); sv = dv_; }
+      if (om) { CK(launch_from_pairs(h, h->om, do_, n)); so = do_; }
+    }
+    if (v && sv != v) CK(cudaMemcpyAsync(v, sv, n * sizeof(double2), k, h->stream));
+    if (om && so != om) CK(cudaMemcpyAsync(om, so, n * sizeof(double2), k, h->stream));
     if (U1) CK(cudaMemcpyAsync(U1, h->U1, h->Ny * sizeof(double), k, h->stream));
     if (U3) CK(cudaMemcpyAsync(U3, h->U3, h->Ny * sizeof(double), k, h->stream));
     if (k == cudaMemcpyDeviceToHost) {
@@ -594,6 +604,7 @@ int chan_nonlinear(chan_t h, double* H) {
   try {
     run_pre(h);
     run_nonlinear(h);
+    if (h->prec == CHAN_PREC_F64X) CK(launch_from_pairs(h, wf(h, WF_H1), wf(h, WF_H1), 3 * fsize(h)));
     CK(cudaMemcpyAsync(H, wf(h, WF_H1), 3 * fsize(h) * sizeof(double2), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
   } catch (Fail f) {
@@ -609,6 +620,7 @@ int chan_rhs_terms(chan_t h, double* N) {
     run_pre(h);
     run_nonlinear(h);
     { Traced t(h, KID_NONLIN); CK(launch_nonlin(h, wf(h, WF_H1), wf(h, WF_H2), wf(h, WF_H3), wf(h, WF_NCHI), wf(h, WF_NOM))); }
+    if (h->prec == CHAN_PREC_F64X) CK(launch_from_pairs(h, wf(h, WF_NCHI), wf(h, WF_NCHI), 2 * fsize(h)));
     CK(cudaMemcpyAsync(N, wf(h, WF_NCHI), 2 * fsize(h) * sizeof(double2), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
   } catch (Fail f) {
@@ -640,7 +652,7 @@ int chan_filter_stresses(chan_t h, int kind, double p1, double p3, double* ubar,
       { Traced t(h, KID_XPASS); CK(launch_xpass(h, 1, mx, mx, ny)); }           // u_i u_j       -> slots 0..5
       double2* fo[12];
       for (int k = 0; k < 6; ++k) { fo[k] = wf(h, 2 + k) + o; fo[6 + k] = h->pbb + k * sn; }
-      { Traced t(h, KID_ZFWD); CK(launch_zfwd(h, mx, fo, 12, ny)); }
+      { Traced t(h, KID_ZFWD); CK(launch_zfwd(h, mx, fo, 12, ny, 0)); }
       const double2* puu[6] = {fo[0], fo[1], fo[2], fo[3], fo[4], fo[5]};
       const double2* pbb[6] = {fo[6], fo[7], fo[8], fo[9], fo[10], fo[11]};
       double2* ub[3];
@@ -676,7 +688,7 @@ int chan_filtered_enstrophy(chan_t h, int kind, double p1, double p3, double* en
       { Traced t(h, KID_ZINV); CK(launch_zinv(h, in, nullptr, mx, 3, ny)); }
       { Traced t(h, KID_XPASS); CK(launch_xpass(h, 2, mx, mx, ny)); }
       double2* fo[1] = {wf(h, 4) + o};
-      { Traced t(h, KID_ZFWD); CK(launch_zfwd(h, mx, fo, 1, ny)); }
+      { Traced t(h, KID_ZFWD); CK(launch_zfwd(h, mx, fo, 1, ny, 0)); }
     }
     { Traced t(h, KID_APPLY_G); CK(launch_apply_G(h, wf(h, 4), wf(h, 5))); }
     if (ens) {

@@ -30,6 +30,7 @@ struct YTabs {            // mode-independent wall-normal tables (device)
 
 struct Geo {
   int Nx, Ny, Nz, nxh, M, C, L1, L3;
+  int pair;               // Fourier fields hold FP32 (hi, lo) pairs (double-float mode)
   double dt, nu;
   const double* k1;       // [nxh]
   const double* k3;       // [Nz]
@@ -134,6 +135,10 @@ cudaError_t launch_mean(chan_s* h, const double2* H1, const double2* H3, int s);
 cudaError_t launch_filter_out(chan_s* h, const double2* const* u, const double2* const* puu,
                               const double2* const* pbb, double2* const* ubar, double2* const* tau, int ny);
 cudaError_t launch_apply_G(chan_s* h, const double2* in, double2* out);
+// Double-float storage: n complex values to (hi, lo) pairs in place; pairs back to FP64
+// (src == dst allowed).
+cudaError_t launch_to_pairs(chan_s* h, double2* p, size_t n);
+cudaError_t launch_from_pairs(chan_s* h, const double2* src, double2* dst, size_t n);
 cudaError_t launch_pressure(chan_s* h, const double2* const* P, double2* out);
 cudaError_t launch_setup_pressure(chan_s* h);
 cudaError_t launch_gather_retained(chan_s* h, const double2* src, double2* dst, int M1, int M3);
@@ -155,7 +160,8 @@ cudaError_t launch_zfwd_batch(chan_s* const* hs, int n, const BatchWork* w, cuda
 // Transform passes over ny planes; the pointers address the first plane of the slab.
 cudaError_t launch_zinv(chan_s* h, const double2* const* in, const int* apply_G, void* const* out, int nf, int ny);
 cudaError_t launch_xpass(chan_s* h, int mode, void* const* in, void* const* out, int ny);
-cudaError_t launch_zfwd(chan_s* h, void* const* in, double2* const* out, int nf, int ny);
+// pair_out: in the double-float mode write (hi, lo) pairs (substep fields) instead of FP64.
+cudaError_t launch_zfwd(chan_s* h, void* const* in, double2* const* out, int nf, int ny, int pair_out);
 cudaError_t fft_configure(chan_s* h);
 // Default z-pass columns per CTA: as many as fit 56 KB of shared memory, at most 16.
 int pick_kb(int nxh, int L3, size_t es);

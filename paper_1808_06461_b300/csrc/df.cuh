@@ -39,3 +39,18 @@ __device__ __forceinline__ dfr df_split(double x) {
   return dfr{h, __double2float_rn(x - (double)h)};
 }
 __device__ __forceinline__ double df_merge(dfr a) { return (double)a.h + (double)a.l; }
+
+// Stored Fourier values.  In the double-float mode a complex field holds, in the
+// 16 bytes of each complex double, the pairs (re.h, re.l, im.h, im.l) as floats.
+// These read a stored value back as FP64 (pair: the exact sum of its floats,
+// rounded once).
+__device__ __forceinline__ double2 load_c(const double2* p, size_t o, int pair) {
+  if (!pair) return p[o];
+  const float4 q = reinterpret_cast<const float4*>(p)[o];
+  return make_double2((double)q.x + (double)q.y, (double)q.z + (double)q.w);
+}
+__device__ __forceinline__ double load_re(const double2* p, size_t o, int pair) {
+  if (!pair) return p[o].x;
+  const float2 q = reinterpret_cast<const float2*>(p)[2 * o];
+  return (double)q.x + (double)q.y;
+}

@@ -58,6 +58,34 @@ template <typename T2> __device__ __forceinline__ T2 mk(double x, double y) {
   return r;
 }
 
+// A stored Fourier value in the transform type, optionally times the real filter
+// factor g.  FP64 storage is converted (g applied in FP64); in the double-float
+// mode the fields hold (hi, lo) float pairs, taken as they are (g as a pair).
+template <typename T2> __device__ __forceinline__ T2 ld_fourier(const double2* p, size_t o, bool useg, double g) {
+  double2 v = p[o];
+  if (useg) { v.x *= g; v.y *= g; }
+  return mk<T2>(v.x, v.y);
+}
+template <> __device__ __forceinline__ dfc ld_fourier<dfc>(const double2* p, size_t o, bool useg, double g) {
+  const float4 q = reinterpret_cast<const float4*>(p)[o];
+  dfc v{dfr{q.x, q.y}, dfr{q.z, q.w}};
+  if (useg) {
+    const dfr gg = from_d<dfr>(g);
+    v.x = v.x * gg;
+    v.y = v.y * gg;
+  }
+  return v;
+}
+// Store a transform value as a Fourier value: FP64, or (pair) the raw (hi, lo) pairs.
+template <typename T2> __device__ __forceinline__ void st_fourier(double2* p, size_t o, T2 x, int pair) {
+  (void)pair;
+  p[o] = make_double2(to_d(x.x), to_d(x.y));
+}
+template <> __device__ __forceinline__ void st_fourier<dfc>(double2* p, size_t o, dfc x, int pair) {
+  if (pair) reinterpret_cast<float4*>(p)[o] = make_float4(x.x.h, x.x.l, x.y.h, x.y.l);
+  else p[o] = make_double2(to_d(x.x), to_d(x.y));
+}
+
 template <typename T2> __device__ __forceinline__ T2 cmul(T2 a, T2 b) {
   T2 r;
   r.x = a.x * b.x - a.y * b.y;
@@ -255,6 +283,7 @@ struct ZArgs {
   int applyG[CHAN_MAXFIELDS];
   const double* G;
   int Ny, Nz, nxh, M, L3, KB, ld;
+  int pair_out;   // double-float mode: the forward pass writes (hi, lo) pairs
   FftPlan pl;
 };
 
@@ -275,14 +304,10 @@ __device__ __forceinline__ void zinv_body(const ZArgs& A, const typename V2<T>::
   for (int e = threadIdx.x; e < A.Nz * A.KB; e += blockDim.x) {
     const int jz = e / A.KB, kl = e - jz * A.KB, kx = kx0 + kl;
     if (kx >= A.nxh || jz == hz) continue;
-    double2 val = in[jz * A.nxh + kx];
-    if (A.applyG[f]) {
-      const double gg = A.G[jz * A.nxh + kx];
-      val.x *= gg;
-      val.y *= gg;
-    }
+    const int q = jz * A.nxh + kx;
+    const bool useg = A.applyG[f] != 0;
     const int pz = jz < hz ? jz : jz + (A.L3 - A.Nz);
-    a[kl * A.ld + pz] = mk<T2>(val.x, val.y);
+    a[kl * A.ld + pz] = ld_fourier<T2>(in, q, useg, useg ? A.G[q] : 0.0);
   }
   __syncthreads();
   // the middle third of the padded column is zero: pruned first stage
@@ -323,13 +348,12 @@ __device__ __forceinline__ void zfwd_body(const ZArgs& A, const typename V2<T>::
   for (int e = threadIdx.x; e < A.Nz * A.KB; e += blockDim.x) {
     const int jz = e / A.KB, kl = e - jz * A.KB, kx = kx0 + kl;
     if (kx >= A.nxh) continue;
-    double2 val = make_double2(0.0, 0.0);
     if (jz != hz) {
       const int pz = jz < hz ? jz : jz + (A.L3 - A.Nz);
-      T2 x = r[kl * A.ld + pz];
-      val = make_double2(to_d(x.x), to_d(x.y));
+      st_fourier<T2>(out, jz * A.nxh + kx, r[kl * A.ld + pz], A.pair_out);
+    } else {
+      out[jz * A.nxh + kx] = make_double2(0.0, 0.0);
     }
-    out[jz * A.nxh + kx] = val;
   }
 }
 
@@ -535,9 +559,10 @@ cudaError_t launch_zinv(chan_s* h, const double2* const* in, const int* apply_G,
   return cudaGetLastError();
 }
 
-cudaError_t launch_zfwd(chan_s* h, void* const* in, double2* const* out, int nf, int ny) {
+cudaError_t launch_zfwd(chan_s* h, void* const* in, double2* const* out, int nf, int ny, int pair_out) {
   const size_t es = fft_esize(h);
   ZArgs A = zargs(h, es);
+  A.pair_out = pair_out && h->prec == CHAN_PREC_F64X;
   for (int f = 0; f < nf; ++f) { A.out[f] = in[f]; A.outd[f] = out[f]; }
   dim3 grid((h->nxh + A.KB - 1) / A.KB, ny, nf);
   size_t sm = (size_t)A.KB * A.ld * es;
@@ -622,6 +647,7 @@ cudaError_t launch_zfwd_batch(chan_s* const* hs, int n, const BatchWork* w, cuda
     ZArgs A = zargs(h, fft_esize(h));
     double2* outs[3] = {w[r].H1, w[r].H2, w[r].H3};
     for (int f = 0; f < 3; ++f) { A.out[f] = w[r].mixed[f]; A.outd[f] = outs[f]; }
+    A.pair_out = h->prec == CHAN_PREC_F64X;   // H of the substep
     B.a[r] = A;
     B.tw[r] = h->tw3;
     B.gx[r] = (h->nxh + A.KB - 1) / A.KB;

@@ -14,6 +14,7 @@ struct FiltArgs {
   const double* G;
   size_t n;        // planes * M
   int M;
+  int pair;        // u_i stored as FP32 pairs (double-float mode)
 };
 
 __global__ void k_filter_out(FiltArgs A) {
@@ -22,7 +23,7 @@ __global__ void k_filter_out(FiltArgs A) {
   const double g = A.G[e % A.M];
 #pragma unroll
   for (int f = 0; f < 3; ++f) {
-    double2 x = A.u[f][e];
+    double2 x = load_c(A.u[f], e, A.pair);
     A.ubar[f][e] = make_double2(g * x.x, g * x.y);
   }
 #pragma unroll
@@ -59,12 +60,12 @@ __global__ void k_gather_retained(const double2* __restrict__ src, double2* dst,
 
 // E_i(k1, y, k3) = w |u_i|^2 (w = 2 for kx > 0 counts the conjugate), mean mode excluded.
 __global__ void k_spectra(const double2* __restrict__ u1, const double2* __restrict__ v,
-                          const double2* __restrict__ u3, double* E, size_t n, int M, int nxh) {
+                          const double2* __restrict__ u3, double* E, size_t n, int M, int nxh, int pair) {
   const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n) return;
   const int m = (int)(e % M);
   const double w = m == 0 ? 0.0 : ((m % nxh) == 0 ? 1.0 : 2.0);
-  const double2 a = u1[e], b = v[e], c = u3[e];
+  const double2 a = load_c(u1, e, pair), b = load_c(v, e, pair), c = load_c(u3, e, pair);
   E[e] = w * (a.x * a.x + a.y * a.y);
   E[n + e] = w * (b.x * b.x + b.y * b.y);
   E[2 * n + e] = w * (c.x * c.x + c.y * c.y);
@@ -78,6 +79,7 @@ struct StatArgs {
   double* out;          // [CHAN_NSTAT][Ny] + utau, ubulk
   double nu;
   int Ny, M, nxh, with_filter;
+  int pair;             // u_i stored as FP32 pairs (double-float mode)
 };
 
 // Block j < Ny reduces plane j in a fixed order (thread-strided partial sums,
@@ -104,7 +106,7 @@ __global__ void __launch_bounds__(256) k_stats(StatArgs A) {
     const double w = (m % A.nxh) == 0 ? 1.0 : 2.0;
     double2 q[3];
 #pragma unroll
-    for (int f = 0; f < 3; ++f) q[f] = A.u[f][base + m];
+    for (int f = 0; f < 3; ++f) q[f] = load_c(A.u[f], base + m, A.pair);
 #pragma unroll
     for (int p = 0; p < 6; ++p) acc[p] += w * (q[pi[p]].x * q[pj[p]].x + q[pi[p]].y * q[pj[p]].y);
     if (A.with_filter) {
@@ -133,7 +135,31 @@ __global__ void __launch_bounds__(256) k_stats(StatArgs A) {
   }
 }
 
+// Double-float storage: FP64 values to (hi, lo) float pairs in place, and back.
+__global__ void k_to_pairs(double2* p, size_t n) {
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const double2 v = p[e];
+  const dfr a = df_split(v.x), b = df_split(v.y);
+  reinterpret_cast<float4*>(p)[e] = make_float4(a.h, a.l, b.h, b.l);
+}
+__global__ void k_from_pairs(const double2* src, double2* dst, size_t n) {
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  dst[e] = load_c(src, e, 1);
+}
+
 }  // namespace
+
+cudaError_t launch_to_pairs(chan_s* h, double2* p, size_t n) {
+  if (n) k_to_pairs<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(p, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_from_pairs(chan_s* h, const double2* src, double2* dst, size_t n) {
+  if (n) k_from_pairs<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(src, dst, n);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_filter_out(chan_s* h, const double2* const* u, const double2* const* puu, const double2* const* pbb,
                               double2* const* ubar, double2* const* tau, int ny) {
@@ -142,6 +168,7 @@ cudaError_t launch_filter_out(chan_s* h, const double2* const* u, const double2*
   for (int p = 0; p < 6; ++p) { A.puu[p] = puu[p]; A.pbb[p] = pbb[p]; A.tau[p] = tau[p]; }
   A.G = h->G;
   A.n = (size_t)ny * h->M;
+  A.pair = h->prec == CHAN_PREC_F64X;
   A.M = h->M;
   k_filter_out<<<(unsigned)((A.n + 255) / 256), 256, 0, h->stream>>>(A);
   return cudaGetLastError();
@@ -161,7 +188,8 @@ cudaError_t launch_gather_retained(chan_s* h, const double2* src, double2* dst, 
 
 cudaError_t launch_spectra(chan_s* h, const double2* u1, const double2* u3, double* E) {
   const size_t n = (size_t)h->Ny * h->M;
-  k_spectra<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(u1, h->v, u3, E, n, h->M, h->nxh);
+  k_spectra<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(u1, h->v, u3, E, n, h->M, h->nxh,
+                                                                 h->prec == CHAN_PREC_F64X);
   return cudaGetLastError();
 }
 
@@ -175,6 +203,7 @@ cudaError_t launch_stats(chan_s* h, const double2* u1, const double2* u3, const 
   A.U1 = h->U1; A.U3 = h->U3; A.d0 = h->tab_d0; A.dN = h->tab_dN; A.wq = h->tab_wq;
   A.out = h->stat; A.nu = h->nu;
   A.Ny = h->Ny; A.M = h->M; A.nxh = h->nxh; A.with_filter = with_filter;
+  A.pair = h->prec == CHAN_PREC_F64X;
   k_stats<<<h->Ny + 1, 256, 0, h->stream>>>(A);
   return cudaGetLastError();
 }

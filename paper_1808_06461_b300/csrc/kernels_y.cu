@@ -70,9 +70,10 @@ __device__ __forceinline__ void load_tab(double* dst, const double* src, int n) 
 }
 
 
-// Arithmetic of the four substep y-kernels, chosen per precision mode: FP64, or
-// double-float (FP32 pairs, about 2^-47) in the double-float mode.  Storage is
-// FP64 in both; the double-float kernels split on load and merge on store.
+// Arithmetic and storage of the four substep y-kernels, chosen per precision
+// mode: FP64, or double-float (FP32 pairs, about 2^-47) in the double-float mode,
+// where every Fourier field holds (hi, lo) float pairs in the 16 bytes of a
+// complex double (ld / st move them as one 128-bit access).
 struct YF64 {
   typedef double R;
   typedef double2 C;
@@ -86,6 +87,8 @@ struct YF64 {
   __device__ static __forceinline__ C sub(C a, C b) { return make_double2(a.x - b.x, a.y - b.y); }
   __device__ static __forceinline__ C itimes(C a) { return make_double2(-a.y, a.x); }
   __device__ static __forceinline__ R neg(R a) { return -a; }
+  __device__ static __forceinline__ C ld(const double2* p, size_t o) { return p[o]; }
+  __device__ static __forceinline__ void st(double2* p, size_t o, C x) { p[o] = x; }
 };
 struct YDF {
   typedef dfr R;
@@ -100,6 +103,13 @@ struct YDF {
   __device__ static __forceinline__ C sub(C a, C b) { return dfc{a.x - b.x, a.y - b.y}; }
   __device__ static __forceinline__ C itimes(C a) { return dfc{-a.y, a.x}; }
   __device__ static __forceinline__ R neg(R a) { return -a; }
+  __device__ static __forceinline__ C ld(const double2* p, size_t o) {
+    const float4 q = reinterpret_cast<const float4*>(p)[o];
+    return dfc{dfr{q.x, q.y}, dfr{q.z, q.w}};
+  }
+  __device__ static __forceinline__ void st(double2* p, size_t o, C x) {
+    reinterpret_cast<float4*>(p)[o] = make_float4(x.x.h, x.x.l, x.y.h, x.y.l);
+  }
 };
 
 template <class Y, int N>
@@ -190,9 +200,7 @@ __device__ __forceinline__ void pre_body(Geo g, YTabs t, const double2* __restri
     }
     return;
   }
-  const bool mean = (m == 0);
-  C* pk1 = reinterpret_cast<C*>(u1o);   // forward-sweep values parked in the outputs
-  C* pk3 = reinterpret_cast<C*>(u3o);
+  const bool mean = (m == 0);   // forward-sweep values parked in the u_1, u_3 outputs
   C wx[7], ww[7], hx[3], hw[3];
 #pragma unroll
   for (int d = 0; d < 7; ++d) { wx[d] = Y::zero(); ww[d] = Y::zero(); }
@@ -203,7 +211,7 @@ __device__ __forceinline__ void pre_body(Geo g, YTabs t, const double2* __restri
     C nx = Y::zero(), nw = Y::zero();
     if (j < Ny) {
       if (mean) { nx = Y::c(make_double2(U1[j], 0.0)); nw = Y::c(make_double2(U3[j], 0.0)); }
-      else { nx = Y::c(dv[(size_t)j * M + m]); nw = Y::c(om[(size_t)j * M + m]); }
+      else { nx = Y::ld(dv, (size_t)j * M + m); nw = Y::ld(om, (size_t)j * M + m); }
     }
     ypush<Y>(wx, nx);
     ypush<Y>(ww, nw);
@@ -211,8 +219,8 @@ __device__ __forceinline__ void pre_body(Geo g, YTabs t, const double2* __restri
     if (i < 0) continue;
     const R* b = sB1 + 7 * i;
     const R* l = sLU + 7 * i;
-    pk1[(size_t)i * M + m] = yfwd<Y>(yband7<Y>(b, wx), l[0], l[1], l[2], hx);
-    pk3[(size_t)i * M + m] = yfwd<Y>(yband7<Y>(b, ww), l[0], l[1], l[2], hw);
+    Y::st(u1o, (size_t)i * M + m, yfwd<Y>(yband7<Y>(b, wx), l[0], l[1], l[2], hx));
+    Y::st(u3o, (size_t)i * M + m, yfwd<Y>(yband7<Y>(b, ww), l[0], l[1], l[2], hw));
   }
   C px[3] = {Y::zero(), Y::zero(), Y::zero()}, pw[3] = {Y::zero(), Y::zero(), Y::zero()};
   const R q1 = Y::r(mean ? 0.0 : mi.k1 / mi.k2), q3 = Y::r(mean ? 0.0 : mi.k3 / mi.k2);
@@ -220,8 +228,8 @@ __device__ __forceinline__ void pre_body(Geo g, YTabs t, const double2* __restri
   for (int i = Ny - 1; i >= 0; --i) {
     const size_t o = (size_t)i * M + m;
     const R* lu = sLU + 7 * i;
-    const C P = ybwd<Y>(pk1[o], lu[3], lu[4], lu[5], lu[6], px);   // D1 of dv/dy
-    const C Q = ybwd<Y>(pk3[o], lu[3], lu[4], lu[5], lu[6], pw);   // D1 omega_2
+    const C P = ybwd<Y>(Y::ld(u1o, o), lu[3], lu[4], lu[5], lu[6], px);   // D1 of dv/dy
+    const C Q = ybwd<Y>(Y::ld(u3o, o), lu[3], lu[4], lu[5], lu[6], pw);   // D1 omega_2
     C u1, u3, du1, du3, vi = Y::zero();
     if (mean) {
       u1 = Y::c(make_double2(U1[i], 0.0));
@@ -229,18 +237,18 @@ __device__ __forceinline__ void pre_body(Geo g, YTabs t, const double2* __restri
       du1 = P;
       du3 = Q;
     } else {
-      const C dvi = Y::c(dv[o]), omi = Y::c(om[o]);
-      vi = Y::c(v[o]);
+      const C dvi = Y::ld(dv, o), omi = Y::ld(om, o);
+      vi = Y::ld(v, o);
       u1 = Y::itimes(Y::axpy(Y::neg(q3), omi, Y::scl(q1, dvi)));
       u3 = Y::itimes(Y::axpy(q1, omi, Y::scl(q3, dvi)));
       du1 = Y::itimes(Y::axpy(Y::neg(q3), Q, Y::scl(q1, P)));
       du3 = Y::itimes(Y::axpy(q1, Q, Y::scl(q3, P)));
     }
     // omega_1 = du3/dy - i k3 v, omega_3 = i k1 v - du1/dy
-    u1o[o] = Y::d(u1);
-    u3o[o] = Y::d(u3);
-    om1o[o] = Y::d(Y::sub(du3, Y::itimes(Y::scl(k3, vi))));
-    om3o[o] = Y::d(Y::sub(Y::itimes(Y::scl(k1, vi)), du1));
+    Y::st(u1o, o, u1);
+    Y::st(u3o, o, u3);
+    Y::st(om1o, o, Y::sub(du3, Y::itimes(Y::scl(k3, vi))));
+    Y::st(om3o, o, Y::sub(Y::itimes(Y::scl(k1, vi)), du1));
   }
 }
 
@@ -277,7 +285,7 @@ __device__ __forceinline__ void nonlin_body(Geo g, YTabs t, const double2* __res
     for (int i = 0; i < Ny; ++i) { Nchi[(size_t)i * M + m] = z2(); Nom[(size_t)i * M + m] = z2(); }
     return;
   }
-  C* scr = reinterpret_cast<C*>(scr_);
+  double2* scr = scr_;
   const R k1 = Y::r(mi.k1), k3 = Y::r(mi.k3), mk2 = Y::r(-mi.k2);
   C w[7], hz[3];
 #pragma unroll
@@ -288,22 +296,22 @@ __device__ __forceinline__ void nonlin_body(Geo g, YTabs t, const double2* __res
     C f = Y::zero();
     if (j < Ny) {
       const size_t o = (size_t)j * M + m;
-      f = Y::itimes(Y::axpy(k3, Y::c(H3[o]), Y::scl(k1, Y::c(H1[o]))));   // i k1 H1 + i k3 H3
+      f = Y::itimes(Y::axpy(k3, Y::ld(H3, o), Y::scl(k1, Y::ld(H1, o))));   // i k1 H1 + i k3 H3
     }
     ypush<Y>(w, f);
     const int i = j - 3;
     if (i < 0) continue;
     const R* l = sLU + 7 * i;
-    scr[(size_t)i * M + m] = yfwd<Y>(yband7<Y>(sB1 + 7 * i, w), l[0], l[1], l[2], hz);
+    Y::st(scr, (size_t)i * M + m, yfwd<Y>(yband7<Y>(sB1 + 7 * i, w), l[0], l[1], l[2], hz));
   }
   C nx[3] = {Y::zero(), Y::zero(), Y::zero()};
   for (int i = Ny - 1; i >= 0; --i) {
     const size_t o = (size_t)i * M + m;
     const R* lu = sLU + 7 * i;
-    const C d = ybwd<Y>(scr[o], lu[3], lu[4], lu[5], lu[6], nx);
-    const C h2 = Y::c(H2[o]), h1 = Y::c(H1[o]), h3 = Y::c(H3[o]);
-    Nchi[o] = Y::d(Y::axpy(mk2, h2, Y::sub(Y::zero(), d)));                 // -D1 f - k^2 H2
-    Nom[o] = Y::d(Y::itimes(Y::axpy(Y::neg(k1), h3, Y::scl(k3, h1))));      // i k3 H1 - i k1 H3
+    const C d = ybwd<Y>(Y::ld(scr, o), lu[3], lu[4], lu[5], lu[6], nx);
+    const C h2 = Y::ld(H2, o), h1 = Y::ld(H1, o), h3 = Y::ld(H3, o);
+    Y::st(Nchi, o, Y::axpy(mk2, h2, Y::sub(Y::zero(), d)));                 // -D1 f - k^2 H2
+    Y::st(Nom, o, Y::itimes(Y::axpy(Y::neg(k1), h3, Y::scl(k3, h1))));      // i k3 H1 - i k1 H3
   }
 }
 
@@ -350,8 +358,8 @@ __device__ __forceinline__ void helm_body(Geo g, YTabs t, const typename Y::R* _
   const double dt = g.dt, nu = g.nu;
   const R c1 = Y::r(1.0 - al * dt * nu * mi.k2), cg = Y::r(dt * gm), cz = Y::r(dt * zt), ca = Y::r(al * dt * nu);
   const R* H = helm + (size_t)s * Ny * 11 * NC + mi.c;
-  C* scr = reinterpret_cast<C*>(scr_);
-  C* scr2 = scr + (size_t)Ny * M;
+  double2* scr = scr_;
+  double2* scr2 = scr + (size_t)Ny * M;
   C wa[7], wx[7], wb[7], wy[7], ho[3], hc[3];
 #pragma unroll
   for (int d = 0; d < 7; ++d) { wa[d] = Y::zero(); wx[d] = Y::zero(); wb[d] = Y::zero(); wy[d] = Y::zero(); }
@@ -361,13 +369,13 @@ __device__ __forceinline__ void helm_body(Geo g, YTabs t, const typename Y::R* _
     C ao = Y::zero(), xo = Y::zero(), ac = Y::zero(), xc = Y::zero();
     if (j < Ny) {
       const size_t o = (size_t)j * M + m;
-      const double2 no = Nom[o], nc = Nchi[o];
-      xo = Y::c(om[o]);
-      xc = Y::c(chi[o]);
-      ao = Y::axpy(cz, Y::c(Nom_p[o]), Y::axpy(cg, Y::c(no), Y::scl(c1, xo)));
-      ac = Y::axpy(cz, Y::c(Nchi_p[o]), Y::axpy(cg, Y::c(nc), Y::scl(c1, xc)));
-      Nom_p[o] = no;
-      Nchi_p[o] = nc;
+      const C no = Y::ld(Nom, o), nc = Y::ld(Nchi, o);
+      xo = Y::ld(om, o);
+      xc = Y::ld(chi, o);
+      ao = Y::axpy(cz, Y::ld(Nom_p, o), Y::axpy(cg, no, Y::scl(c1, xo)));
+      ac = Y::axpy(cz, Y::ld(Nchi_p, o), Y::axpy(cg, nc, Y::scl(c1, xc)));
+      Y::st(Nom_p, o, no);
+      Y::st(Nchi_p, o, nc);
     }
     ypush<Y>(wa, ao); ypush<Y>(wx, xo); ypush<Y>(wb, ac); ypush<Y>(wy, xc);
     const int i = j - 3;
@@ -379,16 +387,16 @@ __device__ __forceinline__ void helm_body(Geo g, YTabs t, const typename Y::R* _
     }
     const R* Hi = H + (size_t)i * 11 * NC;
     const R l0 = Hi[0], l1 = Hi[NC], l2 = Hi[2 * NC];
-    scr[(size_t)i * M + m] = yfwd<Y>(ro, l0, l1, l2, ho);
-    scr2[(size_t)i * M + m] = yfwd<Y>(rc, l0, l1, l2, hc);
+    Y::st(scr, (size_t)i * M + m, yfwd<Y>(ro, l0, l1, l2, ho));
+    Y::st(scr2, (size_t)i * M + m, yfwd<Y>(rc, l0, l1, l2, hc));
   }
   C no3[3] = {Y::zero(), Y::zero(), Y::zero()}, nc3[3] = {Y::zero(), Y::zero(), Y::zero()};
   for (int i = Ny - 1; i >= 0; --i) {
     const size_t o = (size_t)i * M + m;
     const R* Hi = H + (size_t)i * 11 * NC;
     const R u0 = Hi[3 * NC], u1 = Hi[4 * NC], u2 = Hi[5 * NC], dinv = Hi[6 * NC];
-    om[o] = Y::d(ybwd<Y>(scr[o], u0, u1, u2, dinv, no3));
-    chi[o] = Y::d(ybwd<Y>(scr2[o], u0, u1, u2, dinv, nc3));
+    Y::st(om, o, ybwd<Y>(Y::ld(scr, o), u0, u1, u2, dinv, no3));
+    Y::st(chi, o, ybwd<Y>(Y::ld(scr2, o), u0, u1, u2, dinv, nc3));
   }
 }
 
@@ -435,27 +443,27 @@ __device__ __forceinline__ void poisson_body(Geo g, YTabs t, const typename Y::R
   }
   const R* P = pois + mi.c;
   const R* H = helm + (size_t)s * Ny * 11 * NC + mi.c;
-  C* scr = reinterpret_cast<C*>(scr_);
+  double2* scr = scr_;
   C w[7], hz[3];
 #pragma unroll
   for (int d = 0; d < 7; ++d) w[d] = Y::zero();
 #pragma unroll
   for (int d = 0; d < 3; ++d) hz[d] = Y::zero();
   for (int j = 0; j < Ny + 3; ++j) {
-    ypush<Y>(w, j < Ny ? Y::c(chi[(size_t)j * M + m]) : Y::zero());
+    ypush<Y>(w, j < Ny ? Y::ld(chi, (size_t)j * M + m) : Y::zero());
     const int i = j - 3;
     if (i < 0) continue;
     C r = (i > 0 && i < Ny - 1) ? yband7<Y>(sA + 7 * i, w) : Y::zero();
     const R* Pi = P + (size_t)i * 7 * NC;
-    scr[(size_t)i * M + m] = yfwd<Y>(r, Pi[0], Pi[NC], Pi[2 * NC], hz);
+    Y::st(scr, (size_t)i * M + m, yfwd<Y>(r, Pi[0], Pi[NC], Pi[2 * NC], hz));
   }
   C nx[3] = {Y::zero(), Y::zero(), Y::zero()};
   C s0 = Y::zero(), sN = Y::zero();
   for (int i = Ny - 1; i >= 0; --i) {
     const size_t o = (size_t)i * M + m;
     const R* Pi = P + (size_t)i * 7 * NC;
-    const C vp = ybwd<Y>(scr[o], Pi[3 * NC], Pi[4 * NC], Pi[5 * NC], Pi[6 * NC], nx);
-    scr[o] = vp;   // v_p parked in the scratch until the wall correction is known
+    const C vp = ybwd<Y>(Y::ld(scr, o), Pi[3 * NC], Pi[4 * NC], Pi[5 * NC], Pi[6 * NC], nx);
+    Y::st(scr, o, vp);   // v_p parked in the scratch until the wall correction is known
     s0 = Y::axpy(sd0[i], vp, s0);
     sN = Y::axpy(sdN[i], vp, sN);
   }
@@ -463,7 +471,7 @@ __device__ __forceinline__ void poisson_body(Geo g, YTabs t, const typename Y::R
   const R g11 = Gi[0], g12 = Gi[NC], g21 = Gi[2 * NC], g22 = Gi[3 * NC];  // inverse influence matrix
   const C cA = Y::sub(Y::zero(), Y::axpy(g12, sN, Y::scl(g11, s0)));
   const C cB = Y::sub(Y::zero(), Y::axpy(g22, sN, Y::scl(g21, s0)));
-  C* scr2 = scr + (size_t)Ny * M;
+  double2* scr2 = scr + (size_t)Ny * M;
 #pragma unroll
   for (int d = 0; d < 7; ++d) w[d] = Y::zero();
 #pragma unroll
@@ -474,21 +482,21 @@ __device__ __forceinline__ void poisson_body(Geo g, YTabs t, const typename Y::R
       const size_t o = (size_t)j * M + m;
       const R* Hj = H + (size_t)j * 11 * NC;
       const R xa = Hj[7 * NC], xb = Hj[8 * NC], va = Hj[9 * NC], vb = Hj[10 * NC];
-      vj = Y::axpy(vb, cB, Y::axpy(va, cA, scr[o]));
-      v[o] = Y::d(vj);
-      chi[o] = Y::d(Y::axpy(xb, cB, Y::axpy(xa, cA, Y::c(chi[o]))));
+      vj = Y::axpy(vb, cB, Y::axpy(va, cA, Y::ld(scr, o)));
+      Y::st(v, o, vj);
+      Y::st(chi, o, Y::axpy(xb, cB, Y::axpy(xa, cA, Y::ld(chi, o))));
     }
     ypush<Y>(w, vj);
     const int i = j - 3;
     if (i < 0) continue;
     const R* l = sLU + 7 * i;
-    scr2[(size_t)i * M + m] = yfwd<Y>(yband7<Y>(sB1 + 7 * i, w), l[0], l[1], l[2], hz);
+    Y::st(scr2, (size_t)i * M + m, yfwd<Y>(yband7<Y>(sB1 + 7 * i, w), l[0], l[1], l[2], hz));
   }
   for (int d = 0; d < 3; ++d) nx[d] = Y::zero();
   for (int i = Ny - 1; i >= 0; --i) {
     const size_t o = (size_t)i * M + m;
     const R* lu = sLU + 7 * i;
-    dv[o] = Y::d(ybwd<Y>(scr2[o], lu[3], lu[4], lu[5], lu[6], nx));
+    Y::st(dv, o, ybwd<Y>(Y::ld(scr2, o), lu[3], lu[4], lu[5], lu[6], nx));
   }
 }
 
@@ -527,8 +535,8 @@ __device__ __forceinline__ void mean_body(Geo g, YTabs t, const double* __restri
         if (j < 0 || j >= Ny) continue;
         const double A = t.A2[7 * i + d], B = t.B2[7 * i + d];
         const double u1 = U1[j], u3 = U3[j];
-        a1 += A * (u1 + dt * (gm * H1[(size_t)j * M].x + zt * H1p[j])) + al * dt * nu * B * u1;
-        a3 += A * (u3 + dt * (gm * H3[(size_t)j * M].x + zt * H3p[j])) + al * dt * nu * B * u3;
+        a1 += A * (u1 + dt * (gm * load_re(H1, (size_t)j * M, g.pair) + zt * H1p[j])) + al * dt * nu * B * u1;
+        a3 += A * (u3 + dt * (gm * load_re(H3, (size_t)j * M, g.pair) + zt * H3p[j])) + al * dt * nu * B * u3;
       }
     }
     r1[i] = a1;
@@ -566,8 +574,8 @@ __device__ __forceinline__ void mean_body(Geo g, YTabs t, const double* __restri
   const double* uh = meanh + (size_t)s * (Ny + 1);
   const double c = (scal[1] - red[0]) / uh[Ny];
   for (int i = threadIdx.x; i < Ny; i += blockDim.x) {
-    H1p[i] = H1[(size_t)i * M].x;
-    H3p[i] = H3[(size_t)i * M].x;
+    H1p[i] = load_re(H1, (size_t)i * M, g.pair);
+    H3p[i] = load_re(H3, (size_t)i * M, g.pair);
     U1[i] = r1[i] + c * uh[i];
     U3[i] = r3[i];
   }
@@ -897,8 +905,8 @@ __global__ void __launch_bounds__(128) k_pressure(Geo g, YTabs t, const double* 
     sN = axpy(t.dN[i], pp, sN);
   }
   // Neumann conditions dp/dy(+-1) = nu G chi(+-1)
-  const double2 b0 = sub(scl(g.nu * gm, chi[m]), s0);
-  const double2 bN = sub(scl(g.nu * gm, chi[(size_t)(Ny - 1) * M + m]), sN);
+  const double2 b0 = sub(scl(g.nu * gm, load_c(chi, m, g.pair)), s0);
+  const double2 bN = sub(scl(g.nu * gm, load_c(chi, (size_t)(Ny - 1) * M + m, g.pair)), sN);
   const double* Gi = prsinv + mi.c;
   const double g11 = Gi[0], g12 = Gi[C], g21 = Gi[2 * C], g22 = Gi[3 * C];
   const double2 cA = make_double2(g11 * b0.x + g12 * bN.x, g11 * b0.y + g12 * bN.y);
@@ -1020,6 +1028,7 @@ static Geo geo(const chan_s* h) {
   Geo g;
   g.Nx = h->Nx; g.Ny = h->Ny; g.Nz = h->Nz; g.nxh = h->nxh; g.M = h->M; g.C = h->C;
   g.L1 = h->L1; g.L3 = h->L3; g.dt = h->dt; g.nu = h->nu; g.k1 = h->k1; g.k3 = h->k3;
+  g.pair = h->prec == CHAN_PREC_F64X;
   return g;
 }
 static YTabs ytabs(const chan_s* h) {
