@@ -363,6 +363,10 @@ def run_ours(args, c, name):
     hU1 = pin(c["Ny"], torch.float64); hU1[...] = s0["U1"]
     hU3 = pin(c["Ny"], torch.float64); hU3[...] = s0["U3"]
     n = s0["v"].size
+    # pinned destinations for everything a step reads back (filled in place by the API)
+    cpin = lambda shp: pin(2 * int(np.prod(shp)), torch.float64).view(np.complex128).reshape(shp)
+    out_state = dict(v=cpin(shape), omega2=cpin(shape), U1=pin(c["Ny"], torch.float64), U3=pin(c["Ny"], torch.float64))
+    out_filt = (cpin((3,) + shape), cpin((6,) + shape))
     h2d = 2 * n * 16 + 2 * c["Ny"] * 8
     d2h = (9 * n + 2 * n) * 16 + 2 * c["Ny"] * 8 + (20 * c["Ny"] + 3) * 8
     e2e_steps = 0 if args.no_e2e else max(1, min(args.steps, 3))
@@ -373,9 +377,9 @@ def run_ours(args, c, name):
         for _ in range(e2e_steps):
             ch.set_state(hv, ho, hU1, hU3)
             ch.step(nsub)
-            ch.filter_stresses(kind, p1, p3, want=True)
+            ch.filter_stresses(kind, p1, p3, out=out_filt)
             ch.stats()
-            ch.get_state()
+            ch.get_state(out=out_state)
         barrier()
         e2e = replica_throughput(world, e2e_steps, nsub, pts, ranks_max(time.perf_counter() - t0) * 1e3)
     ch.close()

@@ -116,6 +116,12 @@ def _ptr(a):
     return ctypes.c_void_p(int(a.data_ptr()))   # torch tensor on the device
 
 
+def _need(a, shape, dtype):
+    if not (isinstance(a, np.ndarray) and a.shape == tuple(shape) and a.dtype == dtype and a.flags.c_contiguous
+            and a.flags.writeable):
+        raise ValueError("output array must be a writeable C-contiguous %s array of shape %s" % (np.dtype(dtype), shape))
+
+
 def _check(h, rc):
     if rc != CHAN_OK:
         raise ChanError(rc, _lib.chan_last_error(h).decode())
@@ -203,13 +209,19 @@ class Channel:
     def set_state_device(self, v, omega2, U1, U3):
         _check(self.h, _lib.chan_set_state_device(self.h, _ptr(v), _ptr(omega2), _ptr(U1), _ptr(U3)))
 
-    def get_state(self):
-        v = np.empty(self.shape, dtype=np.complex128)
-        om = np.empty(self.shape, dtype=np.complex128)
-        U1 = np.empty(self.Ny)
-        U3 = np.empty(self.Ny)
-        _check(self.h, _lib.chan_get_state(self.h, _ptr(v), _ptr(om), _ptr(U1), _ptr(U3)))
-        return dict(v=v, omega2=om, U1=U1, U3=U3)
+    def get_state(self, out=None):
+        """The state (v, omega2, U1, U3) in host arrays; ``out`` (a dict of C-contiguous arrays
+        of the right shapes and dtypes, e.g. in pinned memory) is filled instead of new arrays."""
+        if out is None:
+            out = dict(v=np.empty(self.shape, dtype=np.complex128), omega2=np.empty(self.shape, dtype=np.complex128),
+                       U1=np.empty(self.Ny), U3=np.empty(self.Ny))
+        _need(out["v"], self.shape, np.complex128)
+        _need(out["omega2"], self.shape, np.complex128)
+        _need(out["U1"], (self.Ny,), np.float64)
+        _need(out["U3"], (self.Ny,), np.float64)
+        _check(self.h, _lib.chan_get_state(self.h, _ptr(out["v"]), _ptr(out["omega2"]), _ptr(out["U1"]),
+                                           _ptr(out["U3"])))
+        return out
 
     def get_state_device(self, v, omega2, U1, U3):
         _check(self.h, _lib.chan_get_state_device(self.h, _ptr(v), _ptr(omega2), _ptr(U1), _ptr(U3)))
@@ -232,9 +244,15 @@ class Channel:
         _check(self.h, _lib.chan_rhs_terms(self.h, _ptr(N)))
         return N
 
-    def filter_stresses(self, kind, p1, p3, want=True):
-        ub = np.empty((3,) + self.shape, dtype=np.complex128) if want else None
-        tau = np.empty((6,) + self.shape, dtype=np.complex128) if want else None
+    def filter_stresses(self, kind, p1, p3, want=True, out=None):
+        """(ubar, tau) of shapes (3,) + shape and (6,) + shape; ``out`` = (ubar, tau) arrays to fill."""
+        if out is not None:
+            ub, tau = out
+            _need(ub, (3,) + self.shape, np.complex128)
+            _need(tau, (6,) + self.shape, np.complex128)
+        else:
+            ub = np.empty((3,) + self.shape, dtype=np.complex128) if want else None
+            tau = np.empty((6,) + self.shape, dtype=np.complex128) if want else None
         _check(self.h, _lib.chan_filter_stresses(self.h, int(kind), float(p1), float(p3), _ptr(ub), _ptr(tau)))
         return ub, tau
 
