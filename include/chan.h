@@ -78,6 +78,11 @@ typedef struct chan_opts {
                         planes unless the twelve mixed-layout transform fields would
                         pass 16 GiB, then the fewest equal slabs below that).  Results
                         do not depend on it; only the transform buffers scale with it */
+  int lean_tables;   /* 1: keep the implicit-step LU factors and homogeneous solutions of
+                        one RK3 substep only and recompute them at each substep (a third
+                        of the table memory, more FP64 work); -1: keep all three; 0: lean
+                        only when the box would otherwise need more than 200 GB.  Results
+                        do not depend on it                                              */
 } chan_opts;
 
 /* Fill *o with defaults: eta_w = 1, grid_re = 0, FP64, library stream. */
@@ -253,7 +258,7 @@ int chan_nonlinear(chan_t h, double* H);
  * since the last reset (launches are counted even when timing is off).
  * chan_kernel_name(k) names kernel k (NULL when out of range).
  */
-#define CHAN_NKERNELS 15
+#define CHAN_NKERNELS 16
 int chan_profile(chan_t h, int enable);
 int chan_profile_read(chan_t h, double* ms, long long* launches);
 const char* chan_kernel_name(int k);

@@ -33,7 +33,7 @@ SYMBOLS = ("chan_opts_default", "chan_init", "chan_init_ex", "chan_free", "chan_
            "chan_filtered_enstrophy", "chan_batch_create", "chan_batch_step", "chan_batch_last_error",
            "chan_batch_free", "chan_autotune", "chan_tuned_shape", "chan_database_record",
            "chan_spectra", "chan_optimize_mesh", "chan_filtered_pressure")
-CHAN_NKERNELS = 15
+CHAN_NKERNELS = 16
 
 
 class chan_opts(ctypes.Structure):
@@ -41,7 +41,8 @@ class chan_opts(ctypes.Structure):
                 ("Nx", ctypes.c_int), ("Ny", ctypes.c_int), ("Nz", ctypes.c_int),
                 ("dt", ctypes.c_double), ("eta_w", ctypes.c_double), ("grid_re", ctypes.c_double),
                 ("precision", ctypes.c_int), ("stream", ctypes.c_void_p),
-                ("mesh", ctypes.POINTER(ctypes.c_double)), ("slab_planes", ctypes.c_int)]
+                ("mesh", ctypes.POINTER(ctypes.c_double)), ("slab_planes", ctypes.c_int),
+                ("lean_tables", ctypes.c_int)]
 
 
 class ChanError(RuntimeError):
@@ -131,12 +132,13 @@ class Channel:
     """One channel box on the current CUDA device (owns its device memory)."""
 
     def __init__(self, re_tau, Lx, Lz, Nx, Ny, Nz, dt, precision=CHAN_PREC_FP64, eta_w=1.0,
-                 grid_re=0.0, stream=None, mesh=None, slab_planes=0):
+                 grid_re=0.0, stream=None, mesh=None, slab_planes=0, lean_tables=0):
         o = chan_opts()
         _lib.chan_opts_default(ctypes.byref(o))
         o.re_tau, o.Lx, o.Lz, o.Nx, o.Ny, o.Nz, o.dt = re_tau, Lx, Lz, Nx, Ny, Nz, dt
         o.eta_w, o.grid_re, o.precision = eta_w, grid_re, precision
         o.slab_planes = int(slab_planes)
+        o.lean_tables = int(lean_tables)
         o.stream = stream
         if mesh is not None:
             self._mesh = np.ascontiguousarray(mesh, dtype=np.float64)

@@ -71,7 +71,7 @@ size_t fsize(const chan_s* h) { return (size_t)h->Ny * h->M; }
 const char* const kKernelNames[KID_COUNT] = {"k_pre",     "k_zinv",       "k_xpass", "k_zfwd",
                                              "k_nonlin",  "k_helm",       "k_poisson", "k_mean",
                                              "k_filter_out", "k_stats",   "k_derive", "k_apply_G",
-                                             "k_gather_retained", "k_spectra", "k_pressure"};
+                                             "k_gather_retained", "k_spectra", "k_pressure", "k_setup_helm"};
 
 // Launch bracket: counts the launch and, when tracing, records an event pair.
 struct Traced {
@@ -165,6 +165,7 @@ void run_nonlinear(chan_s* h) {
 
 void run_substep(chan_s* h) {
   const int s = (int)(h->nsub % 3);
+  if (h->lean) { Traced t(h, KID_TABLES); CK(launch_setup_substep(h, s)); }
   run_pre(h);
   run_nonlinear(h);
   { Traced t(h, KID_NONLIN); CK(launch_nonlin(h, wf(h, WF_H1), wf(h, WF_H2), wf(h, WF_H3), wf(h, WF_NCHI), wf(h, WF_NOM))); }
@@ -207,24 +208,35 @@ void set_filter(chan_s* h, int kind, double p1, double p3) {
 
 // Device bytes chan_init_ex requests for a box (the filter transfer function,
 // allocated on the first filter call, included).  Mirrors the allocations below.
-size_t footprint(int Nx, int Ny, int Nz, int prec) {   // with the automatic slab
+size_t footprint_ex(int Nx, int Ny, int Nz, int prec, int slab_req, int lean) {
   const size_t nxh = Nx / 2, M = (size_t)Nz * nxh, C = (size_t)(Nz / 2) * nxh, n = (size_t)Ny * M;
+  const size_t nslot = lean ? 1 : 3;
   const size_t L1 = 3 * (size_t)Nx / 2, L3 = 3 * (size_t)Nz / 2;
   const size_t es = prec == CHAN_PREC_MIXED ? sizeof(float2) : sizeof(double2);
   size_t b = 0;
   b += 6 * n * sizeof(double2) + 4 * Ny * sizeof(double) + 2 * sizeof(double);            // state
   b += 5 * 7 * (size_t)Ny * sizeof(double) + 3 * (size_t)Ny * sizeof(double);              // y tables
   b += (nxh + Nz) * sizeof(double);                                                          // wavenumbers
-  b += ((size_t)Ny * 7 * C + 3 * (size_t)Ny * 11 * C + 12 * C + 3 * ((size_t)Ny + 1)) * sizeof(double);
-  if (prec == CHAN_PREC_F64X) b += ((size_t)Ny * 7 * C + 3 * (size_t)Ny * 11 * C + 12 * C) * sizeof(dfr);
+  b += ((size_t)Ny * 7 * C + nslot * (size_t)Ny * 11 * C + nslot * 4 * C + 3 * ((size_t)Ny + 1)) * sizeof(double);
+  if (prec == CHAN_PREC_F64X) b += ((size_t)Ny * 7 * C + nslot * (size_t)Ny * 11 * C + nslot * 4 * C) * sizeof(dfr);
   b += (L1 + L3) * (prec == CHAN_PREC_MIXED ? sizeof(float2) : sizeof(double2));             // twiddles
-  const size_t S = slab_planes(Nx, Ny, Nz, prec, 0);
-  b += (size_t)(NWF + 9) * n * sizeof(double2);                                              // work fields
+  const size_t S = slab_planes(Nx, Ny, Nz, prec, slab_req);
+  b += (size_t)NWF * n * sizeof(double2);                                                    // work fields
   b += 12 * S * L3 * nxh * es;                                                               // mixed fields
-  b += 6 * S * M * sizeof(double2);                                                          // filter products
+  b += (6 + 9) * S * M * sizeof(double2);                                                    // filter products, outputs
   b += (CHAN_NSTAT * (size_t)Ny + 2) * sizeof(double);                                       // statistics
   b += M * sizeof(double);                                                                   // filter G
   return b;
+}
+
+// Lean tables when asked, or automatically when the box would pass 200 GB with all three.
+int lean_tables(int Nx, int Ny, int Nz, int prec, int slab_req, int req) {
+  if (req != 0) return req > 0;
+  return footprint_ex(Nx, Ny, Nz, prec, slab_req, 0) > (size_t)200e9;
+}
+
+size_t footprint(int Nx, int Ny, int Nz, int prec) {   // automatic slab and table choice
+  return footprint_ex(Nx, Ny, Nz, prec, 0, lean_tables(Nx, Ny, Nz, prec, 0, 0));
 }
 
 // Capture one RK3 step (substeps 0, 1, 2) into a graph; the handle's
@@ -316,8 +328,61 @@ void batch_substep(chan_batch_s* b) {
 
 }  // namespace
 
-// The filter outputs (3 ubar + 6 tau fields) live behind the work slots.
-static double2* filt(chan_s* h, int k) { return h->wf + (size_t)(NWF + k) * fsize(h); }
+// The filter outputs of one slab: ubar_i (k = 0..2) and tau_ij (k = 3..8), [slab][M] each.
+static double2* filt(chan_s* h, int k) { return h->fout + (size_t)k * h->slab * h->M; }
+
+// The filter pass (Sec. 3.1), slab by slab: P(u_i u_j) to work slots 2..7 (kept for the
+// filtered pressure and the database record), P(ubar_i ubar_j) to the slab buffer, then
+// ubar_i and tau_ij of the slab, which leave for the host arrays (when given), for the
+// filtered statistics rows and, when a database record is being built (rec != NULL),
+// for its ubar_i blocks on the retained modes (M1 x M3).
+static void filter_pass(chan_s* h, int kind, double p1, double p3, double* host_ubar, double* host_tau,
+                        double2* rec, int M1, int M3) {
+  set_filter(h, kind, p1, p3);
+  run_pre(h);
+  const int applyG[6] = {0, 0, 0, 1, 1, 1};
+  void* mx[12];
+  for (int k = 0; k < 12; ++k) mx[k] = mixed(h, k);
+  const size_t n = fsize(h), sn = (size_t)h->slab * h->M;
+  for (int y0 = 0; y0 < h->Ny; y0 += h->slab) {
+    const int ny = h->Ny - y0 < h->slab ? h->Ny - y0 : h->slab;
+    const size_t o = (size_t)y0 * h->M;
+    const double2* u[3] = {wf(h, WF_U1) + o, h->v + o, wf(h, WF_U3) + o};
+    const double2* in[6] = {u[0], u[1], u[2], u[0], u[1], u[2]};
+    { Traced t(h, KID_ZINV); CK(launch_zinv(h, in, applyG, mx, 6, ny)); }
+    { Traced t(h, KID_XPASS); CK(launch_xpass(h, 1, mx + 3, mx + 6, ny)); }   // ubar_i ubar_j -> slots 6..11
+    { Traced t(h, KID_XPASS); CK(launch_xpass(h, 1, mx, mx, ny)); }           // u_i u_j       -> slots 0..5
+    double2* fo[12];
+    for (int k = 0; k < 6; ++k) { fo[k] = wf(h, 2 + k) + o; fo[6 + k] = h->pbb + k * sn; }
+    { Traced t(h, KID_ZFWD); CK(launch_zfwd(h, mx, fo, 12, ny, 0)); }
+    const double2* puu[6] = {fo[0], fo[1], fo[2], fo[3], fo[4], fo[5]};
+    const double2* pbb[6] = {fo[6], fo[7], fo[8], fo[9], fo[10], fo[11]};
+    double2* ub[3];
+    double2* ta[6];
+    for (int k = 0; k < 3; ++k) ub[k] = filt(h, k);
+    for (int k = 0; k < 6; ++k) ta[k] = filt(h, 3 + k);
+    { Traced t(h, KID_FILTER_OUT); CK(launch_filter_out(h, u, puu, pbb, ub, ta, ny)); }
+    const double2* cub[3] = {ub[0], ub[1], ub[2]};
+    const double2* cta[6] = {ta[0], ta[1], ta[2], ta[3], ta[4], ta[5]};
+    { Traced t(h, KID_STATS); CK(launch_stats_filtered(h, cub, cta, y0, ny)); }
+    const size_t bytes = (size_t)ny * h->M * sizeof(double2);
+    for (int k = 0; k < 3 && host_ubar; ++k)
+      CK(cudaMemcpyAsync(reinterpret_cast<double2*>(host_ubar) + k * n + o, ub[k], bytes, cudaMemcpyDeviceToHost,
+                         h->stream));
+    for (int k = 0; k < 6 && host_tau; ++k)
+      CK(cudaMemcpyAsync(reinterpret_cast<double2*>(host_tau) + k * n + o, ta[k], bytes, cudaMemcpyDeviceToHost,
+                         h->stream));
+    if (rec) {
+      const size_t blk = (size_t)h->Ny * M3 * M1;
+      for (int k = 0; k < 3; ++k) {
+        Traced t(h, KID_GATHER);
+        CK(launch_gather_retained(h, ub[k], rec + k * blk + (size_t)y0 * M3 * M1, M1, M3, ny));
+      }
+    }
+  }
+  if (host_ubar || host_tau) CK(cudaStreamSynchronize(h->stream));
+  h->have_filter = true;
+}
 
 extern "C" {
 
@@ -428,14 +493,16 @@ int chan_init_ex(chan_t* out, const chan_opts* o) {
     h->k1 = dalloc<double>(h, h->nxh); h->k3 = dalloc<double>(h, h->Nz);
     CK(cudaMemcpy(h->k1, k1.data(), h->nxh * sizeof(double), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(h->k3, k3.data(), h->Nz * sizeof(double), cudaMemcpyHostToDevice));
+    h->lean = lean_tables(h->Nx, h->Ny, h->Nz, h->prec, o->slab_planes, o->lean_tables);
+    const size_t nslot = h->lean ? 1 : 3;
     h->pois = dalloc<double>(h, Ny * 7 * (size_t)h->C);
-    h->helm = dalloc<double>(h, 3 * Ny * 11 * (size_t)h->C);
-    h->infl = dalloc<double>(h, 3 * 4 * (size_t)h->C);
+    h->helm = dalloc<double>(h, nslot * Ny * 11 * (size_t)h->C);
+    h->infl = dalloc<double>(h, nslot * 4 * (size_t)h->C);
     h->meanh = dalloc<double>(h, 3 * (Ny + 1));
     if (h->prec == CHAN_PREC_F64X) {
       h->pois_df = dalloc<dfr>(h, Ny * 7 * (size_t)h->C);
-      h->helm_df = dalloc<dfr>(h, 3 * Ny * 11 * (size_t)h->C);
-      h->infl_df = dalloc<dfr>(h, 3 * 4 * (size_t)h->C);
+      h->helm_df = dalloc<dfr>(h, nslot * Ny * 11 * (size_t)h->C);
+      h->infl_df = dalloc<dfr>(h, nslot * 4 * (size_t)h->C);
     }
     // twiddles in the transform precision
     for (int which = 0; which < 2; ++which) {
@@ -465,12 +532,13 @@ int chan_init_ex(chan_t* out, const chan_opts* o) {
       (which ? h->tw3 : h->tw1) = d;
     }
     // work
-    h->nwf = NWF + 9;
+    h->nwf = NWF;
     h->wf = dalloc<double2>(h, (size_t)h->nwf * n);
     h->nmix = 12;
     h->slab = slab_planes(h->Nx, h->Ny, h->Nz, h->prec, o->slab_planes);
     h->mixed = dalloc<unsigned char>(h, (size_t)h->nmix * h->slab * L3 * h->nxh * es);
     h->pbb = dalloc<double2>(h, 6 * (size_t)h->slab * h->M);
+    h->fout = dalloc<double2>(h, 9 * (size_t)h->slab * h->M);
     h->scr = wf(h, WF_U1);   // [2][Ny][M]: the u_1, u_3 slots
     h->stat = dalloc<double>(h, CHAN_NSTAT * Ny + 2);
     CK(fft_configure(h));
@@ -635,37 +703,7 @@ int chan_filter_stresses(chan_t h, int kind, double p1, double p3, double* ubar,
   if (!(p1 > 0) || !(p3 > 0)) return bad(h, "chan_filter_stresses: widths must be positive");
   if (!h->have_state) return bad(h, "chan_filter_stresses: no state set", CHAN_ESTATE);
   try {
-    set_filter(h, kind, p1, p3);
-    run_pre(h);
-    const int applyG[6] = {0, 0, 0, 1, 1, 1};
-    void* mx[12];
-    for (int k = 0; k < 12; ++k) mx[k] = mixed(h, k);
-    // slab by slab: P(u_i u_j) to work slots 2..7 (kept for the pressure and the
-    // database record), P(ubar_i ubar_j) to the slab buffer, then ubar_i and tau_ij
-    for (int y0 = 0; y0 < h->Ny; y0 += h->slab) {
-      const int ny = h->Ny - y0 < h->slab ? h->Ny - y0 : h->slab;
-      const size_t o = (size_t)y0 * h->M, sn = (size_t)h->slab * h->M;
-      const double2* u[3] = {wf(h, WF_U1) + o, h->v + o, wf(h, WF_U3) + o};
-      const double2* in[6] = {u[0], u[1], u[2], u[0], u[1], u[2]};
-      { Traced t(h, KID_ZINV); CK(launch_zinv(h, in, applyG, mx, 6, ny)); }
-      { Traced t(h, KID_XPASS); CK(launch_xpass(h, 1, mx + 3, mx + 6, ny)); }   // ubar_i ubar_j -> slots 6..11
-      { Traced t(h, KID_XPASS); CK(launch_xpass(h, 1, mx, mx, ny)); }           // u_i u_j       -> slots 0..5
-      double2* fo[12];
-      for (int k = 0; k < 6; ++k) { fo[k] = wf(h, 2 + k) + o; fo[6 + k] = h->pbb + k * sn; }
-      { Traced t(h, KID_ZFWD); CK(launch_zfwd(h, mx, fo, 12, ny, 0)); }
-      const double2* puu[6] = {fo[0], fo[1], fo[2], fo[3], fo[4], fo[5]};
-      const double2* pbb[6] = {fo[6], fo[7], fo[8], fo[9], fo[10], fo[11]};
-      double2* ub[3];
-      double2* ta[6];
-      for (int k = 0; k < 3; ++k) ub[k] = filt(h, k) + o;
-      for (int k = 0; k < 6; ++k) ta[k] = filt(h, 3 + k) + o;
-      { Traced t(h, KID_FILTER_OUT); CK(launch_filter_out(h, u, puu, pbb, ub, ta, ny)); }
-    }
-    const size_t n = fsize(h);
-    if (ubar) CK(cudaMemcpyAsync(ubar, filt(h, 0), 3 * n * sizeof(double2), cudaMemcpyDeviceToHost, h->stream));
-    if (tau) CK(cudaMemcpyAsync(tau, filt(h, 3), 6 * n * sizeof(double2), cudaMemcpyDeviceToHost, h->stream));
-    if (ubar || tau) CK(cudaStreamSynchronize(h->stream));
-    h->have_filter = true;
+    filter_pass(h, kind, p1, p3, ubar, tau, nullptr, 0, 0);
   } catch (Fail f) {
     return f.code;
   }
@@ -738,17 +776,13 @@ int chan_database_record(chan_t h, double p1, double p3, double* rec, int* m1, i
     // filt(omega_i omega_i) first (its pass reuses work slots the stress pass needs)
     int rc = chan_filtered_enstrophy(h, CHAN_FILTER_SHARP, p1, p3, nullptr);
     if (rc != CHAN_OK) return rc;
-    { Traced t(h, KID_GATHER); CK(launch_gather_retained(h, wf(h, 5), h->dbrec + 9 * blk, M1, M3)); }
-    rc = chan_filter_stresses(h, CHAN_FILTER_SHARP, p1, p3, nullptr, nullptr);
-    if (rc != CHAN_OK) return rc;
-    // ubar_i, then filt(u_i u_j) = G P(u_i u_j) = P(u_i u_j) on the retained modes (G = 1 there)
-    for (int f = 0; f < 3; ++f) {
-      Traced t(h, KID_GATHER);
-      CK(launch_gather_retained(h, filt(h, f), h->dbrec + f * blk, M1, M3));
-    }
+    { Traced t(h, KID_GATHER); CK(launch_gather_retained(h, wf(h, 5), h->dbrec + 9 * blk, M1, M3, h->Ny)); }
+    // ubar_i (gathered slab by slab inside the pass), then filt(u_i u_j) = G P(u_i u_j) =
+    // P(u_i u_j) on the retained modes (G = 1 there)
+    filter_pass(h, CHAN_FILTER_SHARP, p1, p3, nullptr, nullptr, h->dbrec, M1, M3);
     for (int p = 0; p < 6; ++p) {
       Traced t(h, KID_GATHER);
-      CK(launch_gather_retained(h, wf(h, 2 + p), h->dbrec + (3 + p) * blk, M1, M3));
+      CK(launch_gather_retained(h, wf(h, 2 + p), h->dbrec + (3 + p) * blk, M1, M3, h->Ny));
     }
     CK(cudaMemcpyAsync(rec, h->dbrec, 10 * blk * sizeof(double2), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
@@ -801,8 +835,7 @@ int chan_stats(chan_t h, double* out, double* utau, double* ubulk, double* f) {
     run_pre(h);
     {
       Traced t(h, KID_STATS);
-      CK(launch_stats(h, wf(h, WF_U1), wf(h, WF_U3), h->have_filter ? filt(h, 0) : nullptr,
-                      h->have_filter ? filt(h, 3) : nullptr, h->have_filter ? 1 : 0));
+      CK(launch_stats(h, wf(h, WF_U1), wf(h, WF_U3), h->have_filter ? 0 : 1));
     }
     std::vector<double> st(CHAN_NSTAT * (size_t)h->Ny + 2);
     double sc[2];
@@ -972,8 +1005,9 @@ int chan_batch_create(chan_batch_t* out, chan_t* runs, int n, void* stream) {
       return bad(nullptr, "chan_batch_create: runs differ in precision or device");
     for (int q = 0; q < r; ++q)
       if (runs[q] == runs[r]) return bad(nullptr, "chan_batch_create: a run appears twice");
-    if (runs[r]->slab != runs[r]->Ny)
-      return bad(nullptr, "chan_batch_create: a run's transforms are split into slabs (too large to pack)");
+    if (runs[r]->slab != runs[r]->Ny || runs[r]->lean)
+      return bad(nullptr, "chan_batch_create: a run's transforms are split into slabs or its tables are per "
+                          "substep (too large to pack)");
   }
   chan_batch_s* b = new (std::nothrow) chan_batch_s();
   if (!b) return bad(nullptr, "chan_batch_create: out of host memory", CHAN_ENOMEM);

@@ -46,7 +46,8 @@ struct FftPlan {
 };
 
 enum { KID_PRE = 0, KID_ZINV, KID_XPASS, KID_ZFWD, KID_NONLIN, KID_HELM, KID_POISSON, KID_MEAN,
-       KID_FILTER_OUT, KID_STATS, KID_DERIVE, KID_APPLY_G, KID_GATHER, KID_SPECTRA, KID_PRESSURE, KID_COUNT };
+       KID_FILTER_OUT, KID_STATS, KID_DERIVE, KID_APPLY_G, KID_GATHER, KID_SPECTRA, KID_PRESSURE, KID_TABLES,
+       KID_COUNT };
 
 struct ProfRec {
   int k;
@@ -69,9 +70,11 @@ struct chan_s {
   // tables (device)
   double *tab_A2, *tab_B2, *tab_B1, *tab_lu1, *tab_lu2f, *tab_d0, *tab_dN, *tab_wq;
   double *k1, *k3;
-  double* helm;            // [3][Ny][11][C]
+  double* helm;            // [3][Ny][11][C], or [1][Ny][11][C] refilled per substep (lean)
   double* pois;            // [Ny][7][C]
-  double* infl;            // [3][4][C]
+  double* infl;            // [3][4][C] (lean: [1][4][C])
+  int lean;                // per-substep Helmholtz tables (one slot, refilled each substep)
+  int lean_slot;           // the substep whose tables the slot holds
   dfr *helm_df, *pois_df, *infl_df;   // pair copies for the double-float y-kernels (that mode only)
   double* meanh;           // [3][Ny+1]: U_h of each substep and its flux
   void *tw1, *tw3;         // twiddles of L1, L3 in the FFT precision
@@ -82,6 +85,7 @@ struct chan_s {
   int nmix;
   int slab;                // planes per transform slab (Ny unless the mixed fields would pass 16 GiB)
   double2* pbb;            // filter pass: products of the filtered velocities of one slab [6][slab][M]
+  double2* fout;           // filter pass: ubar_i, tau_ij of one slab [9][slab][M]
   double2* scr;            // wall-normal sweep scratch [2][Ny][M] (aliases the u_1, u_3 work slots)
   double* G;               // filter transfer [M]
   double* prs;             // filtered-pressure homogeneous solutions [Ny][2][C] (lazy)
@@ -121,6 +125,8 @@ struct BatchWork {
 
 // Kernel launchers (return cudaGetLastError()).
 cudaError_t launch_setup_tables(chan_s* h);
+// Lean tables: refill the single Helmholtz slot for substep s (no-op otherwise).
+cudaError_t launch_setup_substep(chan_s* h, int s);
 cudaError_t launch_derive(chan_s* h);
 cudaError_t launch_pre(chan_s* h, double2* u1, double2* u3, double2* om1, double2* om3);
 cudaError_t launch_nonlin(chan_s* h, const double2* H1, const double2* H2, const double2* H3,
@@ -141,10 +147,12 @@ cudaError_t launch_to_pairs(chan_s* h, double2* p, size_t n);
 cudaError_t launch_from_pairs(chan_s* h, const double2* src, double2* dst, size_t n);
 cudaError_t launch_pressure(chan_s* h, const double2* const* P, double2* out);
 cudaError_t launch_setup_pressure(chan_s* h);
-cudaError_t launch_gather_retained(chan_s* h, const double2* src, double2* dst, int M1, int M3);
+// Retained modes of ny planes (src at the first plane, dst at its first row).
+cudaError_t launch_gather_retained(chan_s* h, const double2* src, double2* dst, int M1, int M3, int ny);
 cudaError_t launch_spectra(chan_s* h, const double2* u1, const double2* u3, double* E);
-cudaError_t launch_stats(chan_s* h, const double2* u1, const double2* u3, const double2* ubar,
-                         const double2* tau, int with_filter);
+cudaError_t launch_stats(chan_s* h, const double2* u1, const double2* u3, int zero_filtered);
+// <ubar_i ubar_j> and <tau_ij> rows of planes y0 .. y0+ny-1 from the slab's filter outputs.
+cudaError_t launch_stats_filtered(chan_s* h, const double2* const* ubar, const double2* const* tau, int y0, int ny);
 
 // Packed launches over n <= CHAN_MAXBATCH runs of one precision, on `st`.
 cudaError_t launch_pre_batch(chan_s* const* hs, int n, const BatchWork* w, cudaStream_t st);

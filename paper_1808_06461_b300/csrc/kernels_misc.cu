@@ -1,6 +1,8 @@
 // Filter epilogue and plane statistics of the channel substep.
 //   tau_ij = G P(u_i u_j) - P(ubar_i ubar_j), ubar_i = G u_i   (Sec. 3.1, arXiv:1808.06461)
 //   <u_i u_j>(y) by Parseval over the stored modes, U_i, u_tau   (Sec. 3.3)
+#include <cstring>
+
 #include "chan_internal.cuh"
 
 namespace {
@@ -72,24 +74,27 @@ __global__ void k_spectra(const double2* __restrict__ u1, const double2* __restr
 }
 
 struct StatArgs {
-  const double2* u[3];
-  const double2* ub[3];
-  const double2* tau;   // [6][Ny][M] or null
+  const double2* u[3];   // full fields, rows y0 + j (what & 1)
+  const double2* ub[3];  // filtered velocities of the slab, plane j (what & 2)
+  const double2* tau[6]; // filtered stresses of the slab, plane j (what & 2)
   const double *U1, *U3, *d0, *dN, *wq;
   double* out;          // [CHAN_NSTAT][Ny] + utau, ubulk
   double nu;
-  int Ny, M, nxh, with_filter;
+  int Ny, M, nxh;
+  int y0, nplanes;      // planes y0 .. y0 + nplanes - 1
+  int what;             // 1: U_i, <u_i u_j>, u_tau, U_b (rows 0-7); 2: <ubar_i ubar_j>, <tau_ij> (rows 8-19)
+  int zero_filtered;    // with what 1: rows 8-19 set to zero (no filter output since the last step)
   int pair;             // u_i stored as FP32 pairs (double-float mode)
 };
 
-// Block j < Ny reduces plane j in a fixed order (thread-strided partial sums,
+// Block j < nplanes reduces plane y0 + j in a fixed order (thread-strided partial sums,
 // then a fixed shared-memory tree), so results do not depend on scheduling.
 __global__ void __launch_bounds__(256) k_stats(StatArgs A) {
-  __shared__ double red[12][256];
+  __shared__ double red[6][256];
   const int j = blockIdx.x;
   const int Ny = A.Ny;
-  if (j == Ny) {
-    if (threadIdx.x == 0) {
+  if (j == A.nplanes) {
+    if ((A.what & 1) && threadIdx.x == 0) {
       double a = 0.0, b = 0.0, q = 0.0;
       for (int i = 0; i < Ny; ++i) { a += A.d0[i] * A.U1[i]; b += A.dN[i] * A.U1[i]; q += A.wq[i] * A.U1[i]; }
       A.out[CHAN_NSTAT * Ny] = sqrt(A.nu * 0.5 * (fabs(a) + fabs(b)));
@@ -97,40 +102,41 @@ __global__ void __launch_bounds__(256) k_stats(StatArgs A) {
     }
     return;
   }
+  const int y = A.y0 + j;
   const int pi[6] = {0, 1, 2, 0, 0, 1}, pj[6] = {0, 1, 2, 1, 2, 2};
-  double acc[12];
+  double acc[6];
 #pragma unroll
-  for (int p = 0; p < 12; ++p) acc[p] = 0.0;
-  const size_t base = (size_t)j * A.M;
+  for (int p = 0; p < 6; ++p) acc[p] = 0.0;
+  const bool filt = A.what == 2;
+  const size_t base = (size_t)(filt ? j : y) * A.M;
   for (int m = threadIdx.x; m < A.M; m += blockDim.x) {
     const double w = (m % A.nxh) == 0 ? 1.0 : 2.0;
     double2 q[3];
 #pragma unroll
-    for (int f = 0; f < 3; ++f) q[f] = load_c(A.u[f], base + m, A.pair);
+    for (int f = 0; f < 3; ++f) q[f] = filt ? A.ub[f][base + m] : load_c(A.u[f], base + m, A.pair);
 #pragma unroll
     for (int p = 0; p < 6; ++p) acc[p] += w * (q[pi[p]].x * q[pj[p]].x + q[pi[p]].y * q[pj[p]].y);
-    if (A.with_filter) {
-#pragma unroll
-      for (int f = 0; f < 3; ++f) q[f] = A.ub[f][base + m];
-#pragma unroll
-      for (int p = 0; p < 6; ++p) acc[6 + p] += w * (q[pi[p]].x * q[pj[p]].x + q[pi[p]].y * q[pj[p]].y);
-    }
   }
 #pragma unroll
-  for (int p = 0; p < 12; ++p) red[p][threadIdx.x] = acc[p];
+  for (int p = 0; p < 6; ++p) red[p][threadIdx.x] = acc[p];
   __syncthreads();
   for (int s = blockDim.x / 2; s > 0; s >>= 1) {
     if (threadIdx.x < s)
-      for (int p = 0; p < 12; ++p) red[p][threadIdx.x] += red[p][threadIdx.x + s];
+      for (int p = 0; p < 6; ++p) red[p][threadIdx.x] += red[p][threadIdx.x + s];
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    A.out[0 * Ny + j] = A.U1[j];
-    A.out[1 * Ny + j] = A.U3[j];
-    for (int p = 0; p < 6; ++p) {
-      A.out[(2 + p) * Ny + j] = red[p][0];
-      A.out[(8 + p) * Ny + j] = A.with_filter ? red[6 + p][0] : 0.0;
-      A.out[(14 + p) * Ny + j] = A.with_filter ? A.tau[(size_t)p * Ny * A.M + base].x : 0.0;
+    if (!filt) {
+      A.out[0 * Ny + y] = A.U1[y];
+      A.out[1 * Ny + y] = A.U3[y];
+      for (int p = 0; p < 6; ++p) A.out[(2 + p) * Ny + y] = red[p][0];
+      if (A.zero_filtered)
+        for (int p = 0; p < 12; ++p) A.out[(8 + p) * Ny + y] = 0.0;
+    } else {
+      for (int p = 0; p < 6; ++p) {
+        A.out[(8 + p) * Ny + y] = red[p][0];
+        A.out[(14 + p) * Ny + y] = A.tau[p][base].x;
+      }
     }
   }
 }
@@ -180,9 +186,9 @@ cudaError_t launch_apply_G(chan_s* h, const double2* in, double2* out) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_gather_retained(chan_s* h, const double2* src, double2* dst, int M1, int M3) {
-  const size_t n = (size_t)h->Ny * M3 * M1;
-  k_gather_retained<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(src, dst, h->Ny, h->Nz, h->nxh, M1, M3);
+cudaError_t launch_gather_retained(chan_s* h, const double2* src, double2* dst, int M1, int M3, int ny) {
+  const size_t n = (size_t)ny * M3 * M1;
+  k_gather_retained<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(src, dst, ny, h->Nz, h->nxh, M1, M3);
   return cudaGetLastError();
 }
 
@@ -193,17 +199,27 @@ cudaError_t launch_spectra(chan_s* h, const double2* u1, const double2* u3, doub
   return cudaGetLastError();
 }
 
-cudaError_t launch_stats(chan_s* h, const double2* u1, const double2* u3, const double2* ubar, const double2* tau,
-                         int with_filter) {
+cudaError_t launch_stats(chan_s* h, const double2* u1, const double2* u3, int zero_filtered) {
   StatArgs A;
+  memset(&A, 0, sizeof(A));
   A.u[0] = u1; A.u[1] = h->v; A.u[2] = u3;
-  const size_t n = (size_t)h->Ny * h->M;
-  for (int f = 0; f < 3; ++f) A.ub[f] = ubar ? ubar + f * n : nullptr;
-  A.tau = tau;
   A.U1 = h->U1; A.U3 = h->U3; A.d0 = h->tab_d0; A.dN = h->tab_dN; A.wq = h->tab_wq;
   A.out = h->stat; A.nu = h->nu;
-  A.Ny = h->Ny; A.M = h->M; A.nxh = h->nxh; A.with_filter = with_filter;
+  A.Ny = h->Ny; A.M = h->M; A.nxh = h->nxh;
+  A.y0 = 0; A.nplanes = h->Ny; A.what = 1; A.zero_filtered = zero_filtered;
   A.pair = h->prec == CHAN_PREC_F64X;
   k_stats<<<h->Ny + 1, 256, 0, h->stream>>>(A);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stats_filtered(chan_s* h, const double2* const* ubar, const double2* const* tau, int y0, int ny) {
+  StatArgs A;
+  memset(&A, 0, sizeof(A));
+  for (int f = 0; f < 3; ++f) A.ub[f] = ubar[f];
+  for (int p = 0; p < 6; ++p) A.tau[p] = tau[p];
+  A.out = h->stat; A.nu = h->nu;
+  A.Ny = h->Ny; A.M = h->M; A.nxh = h->nxh;
+  A.y0 = y0; A.nplanes = ny; A.what = 2;
+  k_stats<<<ny, 256, 0, h->stream>>>(A);
   return cudaGetLastError();
 }

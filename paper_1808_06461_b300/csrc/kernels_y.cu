@@ -357,7 +357,7 @@ __device__ __forceinline__ void helm_body(Geo g, YTabs t, const typename Y::R* _
   const double gm = c_rk3[s][0], zt = c_rk3[s][1], al = c_rk3[s][2];
   const double dt = g.dt, nu = g.nu;
   const R c1 = Y::r(1.0 - al * dt * nu * mi.k2), cg = Y::r(dt * gm), cz = Y::r(dt * zt), ca = Y::r(al * dt * nu);
-  const R* H = helm + (size_t)s * Ny * 11 * NC + mi.c;
+  const R* H = helm + mi.c;   // the substep's slot
   double2* scr = scr_;
   double2* scr2 = scr + (size_t)Ny * M;
   C wa[7], wx[7], wb[7], wy[7], ho[3], hc[3];
@@ -442,7 +442,7 @@ __device__ __forceinline__ void poisson_body(Geo g, YTabs t, const typename Y::R
     return;
   }
   const R* P = pois + mi.c;
-  const R* H = helm + (size_t)s * Ny * 11 * NC + mi.c;
+  const R* H = helm + mi.c;   // the substep's slot
   double2* scr = scr_;
   C w[7], hz[3];
 #pragma unroll
@@ -467,7 +467,7 @@ __device__ __forceinline__ void poisson_body(Geo g, YTabs t, const typename Y::R
     s0 = Y::axpy(sd0[i], vp, s0);
     sN = Y::axpy(sdN[i], vp, sN);
   }
-  const R* Gi = infl + (size_t)s * 4 * NC + mi.c;
+  const R* Gi = infl + mi.c;
   const R g11 = Gi[0], g12 = Gi[NC], g21 = Gi[2 * NC], g22 = Gi[3 * NC];  // inverse influence matrix
   const C cA = Y::sub(Y::zero(), Y::axpy(g12, sN, Y::scl(g11, s0)));
   const C cB = Y::sub(Y::zero(), Y::axpy(g22, sN, Y::scl(g21, s0)));
@@ -543,7 +543,7 @@ __device__ __forceinline__ void mean_body(Geo g, YTabs t, const double* __restri
     r3[i] = a3;
   }
   __syncthreads();
-  const double* H = helm + (size_t)s * Ny * 11 * C;  // class 0: k = 0
+  const double* H = helm;  // the substep's slot, class 0: k = 0
   if ((threadIdx.x & 31) == 0 && threadIdx.x < 64) {
     double* r = threadIdx.x == 0 ? r1 : r3;
     double h[3] = {0, 0, 0};
@@ -588,14 +588,13 @@ __global__ void __launch_bounds__(256) k_mean(Geo g, YTabs t, const double* __re
                                               double* H3p, double* scal, int s) { mean_body(g, t, helm, meanh, H1, H3, U1, U3, H1p, H3p, scal, s, blockIdx.x); }
 
 
-// U_h(s) = (A - b_s dt nu B)^-1 A 1 with zero wall values, and its trapezoid flux.
-__global__ void k_setup_mean(Geo g, YTabs t, const double* __restrict__ helm, double* meanh) {
-  const int s = threadIdx.x;
-  if (s >= 3 || blockIdx.x != 0) return;
+// U_h(s) = (A - b_s dt nu B)^-1 A 1 with zero wall values, and its trapezoid flux, from the
+// substep's Helmholtz factors (helm at its slot) into out[Ny + 1].
+__global__ void k_setup_mean(Geo g, YTabs t, const double* __restrict__ helm, double* out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const int Ny = g.Ny;
   const size_t C = g.C;
-  const double* H = helm + (size_t)s * Ny * 11 * C;
-  double* out = meanh + (size_t)s * (Ny + 1);
+  const double* H = helm;
   double h[3] = {0, 0, 0};
   for (int i = 0; i < Ny; ++i) {
     double r = 0.0;
@@ -737,16 +736,18 @@ __global__ void k_setup_pois(Geo g, YTabs t, double* pois) {
   }, pois + c, 7, g.C);
 }
 
-__global__ void k_setup_helm(Geo g, YTabs t, const double* __restrict__ pois, double* helm, double* infl) {
+// Substeps s0 .. s0 + ns - 1 into table slots 0 .. ns - 1.
+__global__ void k_setup_helm(Geo g, YTabs t, const double* __restrict__ pois, double* helm, double* infl, int s0,
+                             int ns) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= 3 * g.C) return;
-  const int s = idx / g.C, c = idx - s * g.C;
+  if (idx >= ns * g.C) return;
+  const int slot = idx / g.C, c = idx - slot * g.C, s = s0 + slot;
   const int kx = c % g.nxh, kza = c / g.nxh;
   const double k2 = g.k1[kx] * g.k1[kx] + g.k3[kza] * g.k3[kza];
   const int Ny = g.Ny;
   const size_t C = g.C;
   const double hb = c_rk3[s][3] * g.dt * g.nu;
-  double* H = helm + (size_t)s * Ny * 11 * C + c;
+  double* H = helm + (size_t)slot * Ny * 11 * C + c;
   factor(Ny, [&](int i, double* row) {
     for (int d = 0; d < 7; ++d) row[d] = (i == 0 || i == Ny - 1) ? (d == 3 ? 1.0 : 0.0)
                                                                  : (1.0 + hb * k2) * t.A2[7 * i + d] - hb * t.B2[7 * i + d];
@@ -800,7 +801,7 @@ __global__ void k_setup_helm(Geo g, YTabs t, const double* __restrict__ pois, do
     gm[1][q] = sN;
   }
   const double det = gm[0][0] * gm[1][1] - gm[0][1] * gm[1][0];
-  double* G = infl + (size_t)s * 4 * C + c;
+  double* G = infl + (size_t)slot * 4 * C + c;
   G[0] = gm[1][1] / det;
   G[C] = -gm[0][1] / det;
   G[2 * C] = -gm[1][0] / det;
@@ -1037,6 +1038,21 @@ static YTabs ytabs(const chan_s* h) {
   t.d0 = h->tab_d0; t.dN = h->tab_dN; t.wq = h->tab_wq;
   return t;
 }
+// Tables of substep s: slot s, or the single slot refilled per substep (lean tables).
+static double* helm_slot(const chan_s* h, int s) {
+  return h->helm + (h->lean ? 0 : (size_t)s * h->Ny * 11 * h->C);
+}
+static const void* helm_slot_y(const chan_s* h, int s) {
+  const size_t o = h->lean ? 0 : (size_t)s * h->Ny * 11 * h->C;
+  return h->prec == CHAN_PREC_F64X ? (const void*)(h->helm_df + o) : (const void*)(h->helm + o);
+}
+static const void* infl_slot_y(const chan_s* h, int s) {
+  const size_t o = h->lean ? 0 : (size_t)s * 4 * h->C;
+  return h->prec == CHAN_PREC_F64X ? (const void*)(h->infl_df + o) : (const void*)(h->infl + o);
+}
+static const void* pois_y(const chan_s* h) {
+  return h->prec == CHAN_PREC_F64X ? (const void*)h->pois_df : (const void*)h->pois;
+}
 static const int kYThreads = 128;
 static dim3 ygrid(const chan_s* h) { return dim3((h->M + kYThreads - 1) / kYThreads); }
 
@@ -1045,24 +1061,53 @@ static cudaError_t smem_attr(const void* fn, size_t bytes) {
   return cudaSuccess;
 }
 
-cudaError_t launch_setup_tables(chan_s* h) {
+static bool use_df(const chan_s* h) { return h->prec == CHAN_PREC_F64X; }
+
+// Helmholtz factors, homogeneous solutions and influence matrices of substeps
+// s0 .. s0+ns-1 into slots 0 .. ns-1 (and their pair copies in the double-float mode).
+static cudaError_t setup_helm_slots(chan_s* h, int s0, int ns) {
   Geo g = geo(h);
   YTabs t = ytabs(h);
-  k_setup_pois<<<(h->C + 127) / 128, 128, 0, h->stream>>>(g, t, h->pois);
-  k_setup_helm<<<(3 * h->C + 127) / 128, 128, 0, h->stream>>>(g, t, h->pois, h->helm, h->infl);
-  k_setup_mean<<<1, 32, 0, h->stream>>>(g, t, h->helm, h->meanh);
-  if (h->prec == CHAN_PREC_F64X) {
-    const size_t C = h->C, Ny = h->Ny;
-    const double* src[3] = {h->pois, h->helm, h->infl};
-    dfr* dst[3] = {h->pois_df, h->helm_df, h->infl_df};
-    const size_t cnt[3] = {Ny * 7 * C, 3 * Ny * 11 * C, 12 * C};
-    for (int k = 0; k < 3; ++k)
-      k_split_tab<<<(unsigned)((cnt[k] + 255) / 256), 256, 0, h->stream>>>(src[k], dst[k], cnt[k]);
+  k_setup_helm<<<(ns * h->C + 127) / 128, 128, 0, h->stream>>>(g, t, h->pois, h->helm, h->infl, s0, ns);
+  if (use_df(h)) {
+    const size_t nh = (size_t)ns * h->Ny * 11 * h->C, ni = (size_t)ns * 4 * h->C;
+    k_split_tab<<<(unsigned)((nh + 255) / 256), 256, 0, h->stream>>>(h->helm, h->helm_df, nh);
+    k_split_tab<<<(unsigned)((ni + 255) / 256), 256, 0, h->stream>>>(h->infl, h->infl_df, ni);
   }
   return cudaGetLastError();
 }
 
-static bool use_df(const chan_s* h) { return h->prec == CHAN_PREC_F64X; }
+cudaError_t launch_setup_tables(chan_s* h) {
+  Geo g = geo(h);
+  YTabs t = ytabs(h);
+  k_setup_pois<<<(h->C + 127) / 128, 128, 0, h->stream>>>(g, t, h->pois);
+  if (use_df(h)) {
+    const size_t np = (size_t)h->Ny * 7 * h->C;
+    k_split_tab<<<(unsigned)((np + 255) / 256), 256, 0, h->stream>>>(h->pois, h->pois_df, np);
+  }
+  cudaError_t e;
+  if (!h->lean) {
+    if ((e = setup_helm_slots(h, 0, 3)) != cudaSuccess) return e;
+    for (int s = 0; s < 3; ++s)
+      k_setup_mean<<<1, 32, 0, h->stream>>>(g, t, helm_slot(h, s), h->meanh + (size_t)s * (h->Ny + 1));
+  } else {   // one slot: U_h of each substep from its factors, then the slot is refilled per substep
+    for (int s = 0; s < 3; ++s) {
+      if ((e = setup_helm_slots(h, s, 1)) != cudaSuccess) return e;
+      k_setup_mean<<<1, 32, 0, h->stream>>>(g, t, h->helm, h->meanh + (size_t)s * (h->Ny + 1));
+    }
+    h->lean_slot = 2;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_setup_substep(chan_s* h, int s) {
+  if (!h->lean) return cudaSuccess;
+  const cudaError_t e = setup_helm_slots(h, s, 1);
+  h->lean_slot = s;
+  return e;
+}
+
+
 
 cudaError_t launch_derive(chan_s* h) {
   size_t sm = sizeof(double) * 35 * h->Ny;
@@ -1112,11 +1157,11 @@ cudaError_t launch_helm(chan_s* h, const double2* Nchi, const double2* Nom, int 
   cudaError_t e = smem_attr(fn, sm);
   if (e != cudaSuccess) return e;
   if (use_df(h))
-    k_helm<YDF><<<ygrid(h), kYThreads, sm, h->stream>>>(geo(h), ytabs(h), h->helm_df, h->om, h->chi, Nchi, Nom,
-                                                        h->Nchi_p, h->Nom_p, h->scr, s);
+    k_helm<YDF><<<ygrid(h), kYThreads, sm, h->stream>>>(geo(h), ytabs(h), (const dfr*)helm_slot_y(h, s), h->om,
+                                                        h->chi, Nchi, Nom, h->Nchi_p, h->Nom_p, h->scr, s);
   else
-    k_helm<YF64><<<ygrid(h), kYThreads, sm, h->stream>>>(geo(h), ytabs(h), h->helm, h->om, h->chi, Nchi, Nom,
-                                                         h->Nchi_p, h->Nom_p, h->scr, s);
+    k_helm<YF64><<<ygrid(h), kYThreads, sm, h->stream>>>(geo(h), ytabs(h), (const double*)helm_slot_y(h, s), h->om,
+                                                         h->chi, Nchi, Nom, h->Nchi_p, h->Nom_p, h->scr, s);
   return cudaGetLastError();
 }
 
@@ -1126,11 +1171,13 @@ cudaError_t launch_poisson(chan_s* h, int s) {
   cudaError_t e = smem_attr(fn, sm);
   if (e != cudaSuccess) return e;
   if (use_df(h))
-    k_poisson<YDF><<<ygrid(h), kYThreads, sm, h->stream>>>(geo(h), ytabs(h), h->helm_df, h->pois_df, h->infl_df,
+    k_poisson<YDF><<<ygrid(h), kYThreads, sm, h->stream>>>(geo(h), ytabs(h), (const dfr*)helm_slot_y(h, s),
+                                                           (const dfr*)pois_y(h), (const dfr*)infl_slot_y(h, s),
                                                            h->v, h->chi, h->dv, h->scr, s);
   else
-    k_poisson<YF64><<<ygrid(h), kYThreads, sm, h->stream>>>(geo(h), ytabs(h), h->helm, h->pois, h->infl, h->v,
-                                                            h->chi, h->dv, h->scr, s);
+    k_poisson<YF64><<<ygrid(h), kYThreads, sm, h->stream>>>(geo(h), ytabs(h), (const double*)helm_slot_y(h, s),
+                                                            (const double*)pois_y(h), (const double*)infl_slot_y(h, s),
+                                                            h->v, h->chi, h->dv, h->scr, s);
   return cudaGetLastError();
 }
 
@@ -1138,8 +1185,8 @@ cudaError_t launch_mean(chan_s* h, const double2* H1, const double2* H3, int s) 
   size_t sm = sizeof(double) * (2 * h->Ny + 256);
   cudaError_t e = smem_attr((const void*)k_mean, sm);
   if (e != cudaSuccess) return e;
-  k_mean<<<1, 256, sm, h->stream>>>(geo(h), ytabs(h), h->helm, h->meanh, H1, H3, h->U1, h->U3, h->H1m_p, h->H3m_p,
-                                    h->scal, s);
+  k_mean<<<1, 256, sm, h->stream>>>(geo(h), ytabs(h), helm_slot(h, s), h->meanh, H1, H3, h->U1, h->U3, h->H1m_p,
+                                    h->H3m_p, h->scal, s);
   return cudaGetLastError();
 }
 
@@ -1201,7 +1248,7 @@ cudaError_t launch_helm_batch(chan_s* const* hs, int n, const BatchWork* w, cuda
   YBatch<HelmP> B;
   for (int r = 0; r < n; ++r) {
     chan_s* h = hs[r];
-    B.p[r] = HelmP{geo(h), ytabs(h), use_df(h) ? (const void*)h->helm_df : (const void*)h->helm, h->om, h->chi, w[r].Nchi, w[r].Nom, h->Nchi_p, h->Nom_p, h->scr,
+    B.p[r] = HelmP{geo(h), ytabs(h), helm_slot_y(h, (int)(h->nsub % 3)), h->om, h->chi, w[r].Nchi, w[r].Nom, h->Nchi_p, h->Nom_p, h->scr,
                    (int)(h->nsub % 3)};
   }
   const int blocks = fill_begin(B, hs, n);
@@ -1219,9 +1266,8 @@ cudaError_t launch_poisson_batch(chan_s* const* hs, int n, const BatchWork* w, c
   YBatch<PoisP> B;
   for (int r = 0; r < n; ++r) {
     chan_s* h = hs[r];
-    const bool df = use_df(h);
-    B.p[r] = PoisP{geo(h), ytabs(h), df ? (const void*)h->helm_df : (const void*)h->helm,
-                   df ? (const void*)h->pois_df : (const void*)h->pois, df ? (const void*)h->infl_df : (const void*)h->infl, h->v, h->chi, h->dv, h->scr, (int)(h->nsub % 3)};
+    const int s = (int)(h->nsub % 3);
+    B.p[r] = PoisP{geo(h), ytabs(h), helm_slot_y(h, s), pois_y(h), infl_slot_y(h, s), h->v, h->chi, h->dv, h->scr, (int)(h->nsub % 3)};
   }
   const int blocks = fill_begin(B, hs, n);
   const size_t sm = sizeof(double) * 23 * max_ny(hs, n);
@@ -1238,7 +1284,7 @@ cudaError_t launch_mean_batch(chan_s* const* hs, int n, const BatchWork* w, cuda
   B.n = n;
   for (int r = 0; r < n; ++r) {
     chan_s* h = hs[r];
-    B.p[r] = MeanP{geo(h), ytabs(h), h->helm, h->meanh, w[r].H1, w[r].H3, h->U1, h->U3, h->H1m_p, h->H3m_p,
+    B.p[r] = MeanP{geo(h), ytabs(h), helm_slot(h, (int)(h->nsub % 3)), h->meanh, w[r].H1, w[r].H3, h->U1, h->U3, h->H1m_p, h->H3m_p,
                    h->scal, (int)(h->nsub % 3)};
   }
   const size_t sm = sizeof(double) * (2 * max_ny(hs, n) + 256);

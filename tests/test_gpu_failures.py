@@ -40,10 +40,10 @@ def test_nan_in_the_state_is_reported():
 def test_allocation_beyond_the_device_is_an_error_not_a_fault():
     import paper_1808_06461_b300 as chan
     lib = chan.library()
-    need = chan.footprint_bytes(768, 2049, 768, chan.CHAN_PREC_FP64)
-    assert need > 300e9                  # more than the 288 GB (275,040 MiB) of HBM
+    need = chan.footprint_bytes(768, 4097, 768, chan.CHAN_PREC_FP64)
+    assert need > 400e9                  # more than the 288 GB (275,040 MiB) of HBM
     h = ctypes.c_void_p()
-    rc = lib.chan_init(ctypes.byref(h), 180.0, math.pi, math.pi / 2, 768, 2049, 768, 1e-3)
+    rc = lib.chan_init(ctypes.byref(h), 180.0, math.pi, math.pi / 2, 768, 4097, 768, 1e-3)
     assert rc == chan.CHAN_ENOMEM and not h.value
     assert "cudaMalloc" in lib.chan_last_error(None).decode()
     ch, s0 = _channel(chan)              # the device is fine afterwards
