@@ -42,7 +42,7 @@ class chan_opts(ctypes.Structure):
                 ("dt", ctypes.c_double), ("eta_w", ctypes.c_double), ("grid_re", ctypes.c_double),
                 ("precision", ctypes.c_int), ("stream", ctypes.c_void_p),
                 ("mesh", ctypes.POINTER(ctypes.c_double)), ("slab_planes", ctypes.c_int),
-                ("lean_tables", ctypes.c_int)]
+                ("lean_tables", ctypes.c_int), ("y_tables", ctypes.c_int)]
 
 
 class ChanError(RuntimeError):
@@ -89,7 +89,7 @@ def load_library(path=LIB_PATH):
         "chan_spectra": (I, [P, P]),
         "chan_filtered_pressure": (I, [P, I, D, D, P]),
         "chan_optimize_mesh": (I, [ctypes.POINTER(chan_opts), I, D, P, DP, DP]),
-        "chan_tuned_shape": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I)]),
+        "chan_tuned_shape": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]),
         "chan_sync": (I, [P]),
         "chan_time": (D, [P]),
         "chan_substeps": (ctypes.c_longlong, [P]),
@@ -132,13 +132,14 @@ class Channel:
     """One channel box on the current CUDA device (owns its device memory)."""
 
     def __init__(self, re_tau, Lx, Lz, Nx, Ny, Nz, dt, precision=CHAN_PREC_FP64, eta_w=1.0,
-                 grid_re=0.0, stream=None, mesh=None, slab_planes=0, lean_tables=0):
+                 grid_re=0.0, stream=None, mesh=None, slab_planes=0, lean_tables=0, y_tables=0):
         o = chan_opts()
         _lib.chan_opts_default(ctypes.byref(o))
         o.re_tau, o.Lx, o.Lz, o.Nx, o.Ny, o.Nz, o.dt = re_tau, Lx, Lz, Nx, Ny, Nz, dt
         o.eta_w, o.grid_re, o.precision = eta_w, grid_re, precision
         o.slab_planes = int(slab_planes)
         o.lean_tables = int(lean_tables)
+        o.y_tables = int(y_tables)
         o.stream = stream
         if mesh is not None:
             self._mesh = np.ascontiguousarray(mesh, dtype=np.float64)
@@ -178,11 +179,15 @@ class Channel:
         return int(_lib.chan_substeps(self.h))
 
     def autotune(self):
-        """Pick z-pass columns per CTA and x-pass threads for this shape (results unchanged)."""
+        """Pick z-pass columns per CTA, x-pass threads and the y-table placement for this shape
+        (results unchanged); returns (kb_z, xthreads, ytab_global)."""
         _check(self.h, _lib.chan_autotune(self.h))
-        kb, nt = ctypes.c_int(), ctypes.c_int()
-        _check(self.h, _lib.chan_tuned_shape(self.h, ctypes.byref(kb), ctypes.byref(nt)))
-        return kb.value, nt.value
+        return self.tuned_shape()
+
+    def tuned_shape(self):
+        kb, nt, yt = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(self.h, _lib.chan_tuned_shape(self.h, ctypes.byref(kb), ctypes.byref(nt), ctypes.byref(yt)))
+        return kb.value, nt.value, yt.value
 
     def set_graph(self, enable=True):
         _check(self.h, _lib.chan_set_graph(self.h, 1 if enable else 0))

@@ -218,7 +218,8 @@ size_t footprint_ex(int Nx, int Ny, int Nz, int prec, int slab_req, int lean) {
   b += 5 * 7 * (size_t)Ny * sizeof(double) + 3 * (size_t)Ny * sizeof(double);              // y tables
   b += (nxh + Nz) * sizeof(double);                                                          // wavenumbers
   b += ((size_t)Ny * 7 * C + nslot * (size_t)Ny * 11 * C + nslot * 4 * C + 3 * ((size_t)Ny + 1)) * sizeof(double);
-  if (prec == CHAN_PREC_F64X) b += ((size_t)Ny * 7 * C + nslot * (size_t)Ny * 11 * C + nslot * 4 * C) * sizeof(dfr);
+  if (prec == CHAN_PREC_F64X)
+    b += ((size_t)Ny * 7 * C + nslot * (size_t)Ny * 11 * C + nslot * 4 * C + 30 * (size_t)Ny) * sizeof(dfr);
   b += (L1 + L3) * (prec == CHAN_PREC_MIXED ? sizeof(float2) : sizeof(double2));             // twiddles
   const size_t S = slab_planes(Nx, Ny, Nz, prec, slab_req);
   b += (size_t)NWF * n * sizeof(double2);                                                    // work fields
@@ -414,6 +415,7 @@ int chan_init_ex(chan_t* out, const chan_opts* o) {
   if (o->precision != CHAN_PREC_FP64 && o->precision != CHAN_PREC_MIXED && o->precision != CHAN_PREC_F64X)
     return bad(nullptr, "chan_init: unknown precision");
   if (o->slab_planes < 0) return bad(nullptr, "chan_init: slab_planes must be >= 0");
+  if (o->y_tables < 0 || o->y_tables > 2) return bad(nullptr, "chan_init: y_tables must be 0, 1 or 2");
   const int L1 = 3 * o->Nx / 2, L3 = 3 * o->Nz / 2;
   const size_t es = o->precision == CHAN_PREC_MIXED ? 8 : 16;
   if (2 * 6 * (size_t)(L1 + 1) * es > 227 * 1024 || 2 * (size_t)(L3 + 1) * es > 100 * 1024)
@@ -493,6 +495,7 @@ int chan_init_ex(chan_t* out, const chan_opts* o) {
     h->k1 = dalloc<double>(h, h->nxh); h->k3 = dalloc<double>(h, h->Nz);
     CK(cudaMemcpy(h->k1, k1.data(), h->nxh * sizeof(double), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(h->k3, k3.data(), h->Nz * sizeof(double), cudaMemcpyHostToDevice));
+    h->ytab = o->y_tables == 1 ? 1 : (o->y_tables == 2 ? 0 : -1);
     h->lean = lean_tables(h->Nx, h->Ny, h->Nz, h->prec, o->slab_planes, o->lean_tables);
     const size_t nslot = h->lean ? 1 : 3;
     h->pois = dalloc<double>(h, Ny * 7 * (size_t)h->C);
@@ -500,6 +503,7 @@ int chan_init_ex(chan_t* out, const chan_opts* o) {
     h->infl = dalloc<double>(h, nslot * 4 * (size_t)h->C);
     h->meanh = dalloc<double>(h, 3 * (Ny + 1));
     if (h->prec == CHAN_PREC_F64X) {
+      h->tab_pairs = dalloc<dfr>(h, 30 * Ny);
       h->pois_df = dalloc<dfr>(h, Ny * 7 * (size_t)h->C);
       h->helm_df = dalloc<dfr>(h, nslot * Ny * 11 * (size_t)h->C);
       h->infl_df = dalloc<dfr>(h, nslot * 4 * (size_t)h->C);
@@ -889,7 +893,7 @@ int chan_profile_read(chan_t h, double* ms, long long* launches) {
 
 // Launch shapes found by chan_autotune, per (Nx, Ny, Nz, precision), shared by the process.
 static std::mutex g_tune_mu;
-static std::map<std::tuple<int, int, int, int>, std::pair<int, int>> g_tune;
+static std::map<std::tuple<int, int, int, int>, std::tuple<int, int, int>> g_tune;
 
 int chan_autotune(chan_t h) {
   if (!h) return bad(nullptr, "chan_autotune: NULL handle");
@@ -899,8 +903,7 @@ int chan_autotune(chan_t h) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune.find(key);
     if (it != g_tune.end()) {
-      h->kb_z = it->second.first;
-      h->xthreads = it->second.second;
+      std::tie(h->kb_z, h->xthreads, h->ytab) = it->second;
       return CHAN_OK;
     }
   }
@@ -943,26 +946,41 @@ int chan_autotune(chan_t h) {
       if (t < best_t) { best_t = t; best_nt = nt; }
     }
     h->xthreads = best_nt;
+    // wall-normal sweeps: y tables staged in shared memory or read in place (work slots only)
+    best_t = 1e30f;
+    int best_yt = 0;
+    for (int yt : {0, 1}) {
+      h->ytab = yt;
+      float t = timed([&] {
+        CK(launch_pre(h, wf(h, WF_U1), wf(h, WF_U3), wf(h, WF_OM1), wf(h, WF_OM3)));
+        CK(launch_nonlin(h, wf(h, WF_H1), wf(h, WF_H2), wf(h, WF_H3), wf(h, WF_NCHI), wf(h, WF_NOM)));
+      });
+      if (t < best_t) { best_t = t; best_yt = yt; }
+    }
+    h->ytab = best_yt;
     CK(cudaStreamSynchronize(h->stream));
   } catch (Fail f) {
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     h->kb_z = 0;
     h->xthreads = 0;
+    h->ytab = -1;
     return f.code;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  g_tune[key] = std::make_pair(h->kb_z, h->xthreads);
+  g_tune[key] = std::make_tuple(h->kb_z, h->xthreads, h->ytab);
   return CHAN_OK;
 }
 
-int chan_tuned_shape(chan_t h, int* kb_z, int* xthreads) {
+int chan_tuned_shape(chan_t h, int* kb_z, int* xthreads, int* ytab_global) {
   if (!h) return bad(nullptr, "chan_tuned_shape: NULL handle");
   const size_t es = h->prec == CHAN_PREC_MIXED ? sizeof(float2) : sizeof(double2);
   if (kb_z) *kb_z = h->kb_z > 0 ? h->kb_z : pick_kb(h->nxh, h->L3, es);
   if (xthreads) *xthreads = h->xthreads > 0 ? h->xthreads : 256;
+  if (ytab_global)
+    *ytab_global = h->ytab > 0 || (h->ytab < 0 && 23 * (size_t)h->Ny * sizeof(double) > 48 * 1024) ? 1 : 0;
   return CHAN_OK;
 }
 

@@ -26,11 +26,14 @@ struct YTabs {            // mode-independent wall-normal tables (device)
   const double* d0;       // [Ny]
   const double* dN;
   const double* wq;
+  // FP32-pair copies for the double-float sweeps (that mode only)
+  const dfr *A2p, *B2p, *B1p, *lu1p, *d0p, *dNp;
 };
 
 struct Geo {
   int Nx, Ny, Nz, nxh, M, C, L1, L3;
   int pair;               // Fourier fields hold FP32 (hi, lo) pairs (double-float mode)
+  int gtab;               // sweeps read the y tables from global memory (L1) instead of staging them
   double dt, nu;
   const double* k1;       // [nxh]
   const double* k3;       // [Nz]
@@ -69,6 +72,7 @@ struct chan_s {
   double* scal;            // [0] f of last substep, [1] Q0
   // tables (device)
   double *tab_A2, *tab_B2, *tab_B1, *tab_lu1, *tab_lu2f, *tab_d0, *tab_dN, *tab_wq;
+  dfr* tab_pairs;          // double-float mode: A2, B2, B1, lu1 ([Ny][7] each), d0, dN as pairs
   double *k1, *k3;
   double* helm;            // [3][Ny][11][C], or [1][Ny][11][C] refilled per substep (lean)
   double* pois;            // [Ny][7][C]
@@ -106,6 +110,8 @@ struct chan_s {
   // launch shapes (0: default), set by chan_autotune
   int kb_z;                // columns per z-pass CTA
   int xthreads;            // threads per x-pass CTA
+  int ytab;                // y sweeps: 1 read tables from global memory, 0 stage them in shared memory,
+                           // -1 (default) stage them unless that needs more than 48 KB per CTA
   // CUDA graph of one full RK3 step (three substeps), captured on first use
   bool use_graph;
   cudaGraphExec_t gexec;

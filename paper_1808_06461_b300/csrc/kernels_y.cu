@@ -89,6 +89,12 @@ struct YF64 {
   __device__ static __forceinline__ R neg(R a) { return -a; }
   __device__ static __forceinline__ C ld(const double2* p, size_t o) { return p[o]; }
   __device__ static __forceinline__ void st(double2* p, size_t o, C x) { p[o] = x; }
+  __device__ static __forceinline__ const R* A2(const YTabs& t) { return t.A2; }
+  __device__ static __forceinline__ const R* B2(const YTabs& t) { return t.B2; }
+  __device__ static __forceinline__ const R* B1(const YTabs& t) { return t.B1; }
+  __device__ static __forceinline__ const R* LU1(const YTabs& t) { return t.lu1; }
+  __device__ static __forceinline__ const R* D0(const YTabs& t) { return t.d0; }
+  __device__ static __forceinline__ const R* DN(const YTabs& t) { return t.dN; }
 };
 struct YDF {
   typedef dfr R;
@@ -110,6 +116,12 @@ struct YDF {
   __device__ static __forceinline__ void st(double2* p, size_t o, C x) {
     reinterpret_cast<float4*>(p)[o] = make_float4(x.x.h, x.x.l, x.y.h, x.y.l);
   }
+  __device__ static __forceinline__ const R* A2(const YTabs& t) { return t.A2p; }
+  __device__ static __forceinline__ const R* B2(const YTabs& t) { return t.B2p; }
+  __device__ static __forceinline__ const R* B1(const YTabs& t) { return t.B1p; }
+  __device__ static __forceinline__ const R* LU1(const YTabs& t) { return t.lu1p; }
+  __device__ static __forceinline__ const R* D0(const YTabs& t) { return t.d0p; }
+  __device__ static __forceinline__ const R* DN(const YTabs& t) { return t.dNp; }
 };
 
 template <class Y, int N>
@@ -146,9 +158,16 @@ __device__ __forceinline__ typename Y::C ybwd(typename Y::C z, typename Y::R u0,
   nxt[0] = x;
   return x;
 }
+// A mode-independent y table: staged in shared memory (when stage), else read in place
+// from global memory (every thread of a warp reads the same row: L1 broadcasts).
 template <class Y>
-__device__ __forceinline__ void yload_tab(typename Y::R* dst, const double* src, int n) {
-  for (int k = threadIdx.x; k < n; k += blockDim.x) dst[k] = Y::r(src[k]);
+__device__ __forceinline__ const typename Y::R* ystage(typename Y::R*& dst, const typename Y::R* src, int n,
+                                                       bool stage) {
+  if (!stage) return src;
+  typename Y::R* d = dst;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) d[k] = src[k];
+  dst += n;
+  return d;
 }
 
 struct ModeInfo {
@@ -184,11 +203,10 @@ __device__ __forceinline__ void pre_body(Geo g, YTabs t, const double2* __restri
   typedef typename Y::C C;
   extern __shared__ double sm[];
   const int Ny = g.Ny;
-  R* sB1 = reinterpret_cast<R*>(sm);
-  R* sLU = sB1 + 7 * Ny;
-  yload_tab<Y>(sB1, t.B1, 7 * Ny);
-  yload_tab<Y>(sLU, t.lu1, 7 * Ny);
-  __syncthreads();
+  R* sp = reinterpret_cast<R*>(sm);
+  const R* sB1 = ystage<Y>(sp, Y::B1(t), 7 * Ny, !g.gtab);
+  const R* sLU = ystage<Y>(sp, Y::LU1(t), 7 * Ny, !g.gtab);
+  if (!g.gtab) __syncthreads();
   const int m = bid * blockDim.x + threadIdx.x;
   if (m >= g.M) return;
   const size_t M = g.M;
@@ -272,11 +290,10 @@ __device__ __forceinline__ void nonlin_body(Geo g, YTabs t, const double2* __res
   typedef typename Y::C C;
   extern __shared__ double sm[];
   const int Ny = g.Ny;
-  R* sB1 = reinterpret_cast<R*>(sm);
-  R* sLU = sB1 + 7 * Ny;
-  yload_tab<Y>(sB1, t.B1, 7 * Ny);
-  yload_tab<Y>(sLU, t.lu1, 7 * Ny);
-  __syncthreads();
+  R* sp = reinterpret_cast<R*>(sm);
+  const R* sB1 = ystage<Y>(sp, Y::B1(t), 7 * Ny, !g.gtab);
+  const R* sLU = ystage<Y>(sp, Y::LU1(t), 7 * Ny, !g.gtab);
+  if (!g.gtab) __syncthreads();
   const int m = bid * blockDim.x + threadIdx.x;
   if (m >= g.M) return;
   const size_t M = g.M;
@@ -337,11 +354,10 @@ __device__ __forceinline__ void helm_body(Geo g, YTabs t, const typename Y::R* _
   typedef typename Y::C C;
   extern __shared__ double sm[];
   const int Ny = g.Ny;
-  R* sA = reinterpret_cast<R*>(sm);
-  R* sB = sA + 7 * Ny;
-  yload_tab<Y>(sA, t.A2, 7 * Ny);
-  yload_tab<Y>(sB, t.B2, 7 * Ny);
-  __syncthreads();
+  R* sp = reinterpret_cast<R*>(sm);
+  const R* sA = ystage<Y>(sp, Y::A2(t), 7 * Ny, !g.gtab);
+  const R* sB = ystage<Y>(sp, Y::B2(t), 7 * Ny, !g.gtab);
+  if (!g.gtab) __syncthreads();
   const int m = bid * blockDim.x + threadIdx.x;
   if (m >= g.M) return;
   const size_t M = g.M;
@@ -421,17 +437,13 @@ __device__ __forceinline__ void poisson_body(Geo g, YTabs t, const typename Y::R
   typedef typename Y::C C;
   extern __shared__ double sm[];
   const int Ny = g.Ny;
-  R* sA = reinterpret_cast<R*>(sm);
-  R* sB1 = sA + 7 * Ny;
-  R* sLU = sA + 14 * Ny;
-  R* sd0 = sA + 21 * Ny;
-  R* sdN = sA + 22 * Ny;
-  yload_tab<Y>(sA, t.A2, 7 * Ny);
-  yload_tab<Y>(sB1, t.B1, 7 * Ny);
-  yload_tab<Y>(sLU, t.lu1, 7 * Ny);
-  yload_tab<Y>(sd0, t.d0, Ny);
-  yload_tab<Y>(sdN, t.dN, Ny);
-  __syncthreads();
+  R* sp = reinterpret_cast<R*>(sm);
+  const R* sA = ystage<Y>(sp, Y::A2(t), 7 * Ny, !g.gtab);
+  const R* sB1 = ystage<Y>(sp, Y::B1(t), 7 * Ny, !g.gtab);
+  const R* sLU = ystage<Y>(sp, Y::LU1(t), 7 * Ny, !g.gtab);
+  const R* sd0 = ystage<Y>(sp, Y::D0(t), Ny, !g.gtab);
+  const R* sdN = ystage<Y>(sp, Y::DN(t), Ny, !g.gtab);
+  if (!g.gtab) __syncthreads();
   const int m = bid * blockDim.x + threadIdx.x;
   if (m >= g.M) return;
   const size_t M = g.M;
@@ -1030,12 +1042,17 @@ static Geo geo(const chan_s* h) {
   g.Nx = h->Nx; g.Ny = h->Ny; g.Nz = h->Nz; g.nxh = h->nxh; g.M = h->M; g.C = h->C;
   g.L1 = h->L1; g.L3 = h->L3; g.dt = h->dt; g.nu = h->nu; g.k1 = h->k1; g.k3 = h->k3;
   g.pair = h->prec == CHAN_PREC_F64X;
+  g.gtab = h->ytab > 0 || (h->ytab < 0 && 23 * (size_t)h->Ny * sizeof(double) > 48 * 1024);
   return g;
 }
 static YTabs ytabs(const chan_s* h) {
   YTabs t;
   t.A2 = h->tab_A2; t.B2 = h->tab_B2; t.B1 = h->tab_B1; t.lu1 = h->tab_lu1; t.lu2f = h->tab_lu2f;
   t.d0 = h->tab_d0; t.dN = h->tab_dN; t.wq = h->tab_wq;
+  const dfr* p = h->tab_pairs;
+  const size_t r7 = 7 * (size_t)h->Ny;
+  t.A2p = p; t.B2p = p ? p + r7 : nullptr; t.B1p = p ? p + 2 * r7 : nullptr; t.lu1p = p ? p + 3 * r7 : nullptr;
+  t.d0p = p ? p + 4 * r7 : nullptr; t.dNp = p ? p + 4 * r7 + h->Ny : nullptr;
   return t;
 }
 // Tables of substep s: slot s, or the single slot refilled per substep (lean tables).
@@ -1054,6 +1071,16 @@ static const void* pois_y(const chan_s* h) {
   return h->prec == CHAN_PREC_F64X ? (const void*)h->pois_df : (const void*)h->pois;
 }
 static const int kYThreads = 128;
+// Shared memory of a sweep kernel that stages per_y table values per y point (0 when
+// the tables are read in place).
+static size_t ysm(const chan_s* h, int per_y) {
+  return geo(h).gtab ? 0 : sizeof(double) * per_y * (size_t)h->Ny;
+}
+static size_t ysm_batch(chan_s* const* hs, int n, int per_y) {
+  size_t m = 0;
+  for (int r = 0; r < n; ++r) m = ysm(hs[r], per_y) > m ? ysm(hs[r], per_y) : m;
+  return m;
+}
 static dim3 ygrid(const chan_s* h) { return dim3((h->M + kYThreads - 1) / kYThreads); }
 
 static cudaError_t smem_attr(const void* fn, size_t bytes) {
@@ -1084,6 +1111,14 @@ cudaError_t launch_setup_tables(chan_s* h) {
   if (use_df(h)) {
     const size_t np = (size_t)h->Ny * 7 * h->C;
     k_split_tab<<<(unsigned)((np + 255) / 256), 256, 0, h->stream>>>(h->pois, h->pois_df, np);
+    const double* src[6] = {h->tab_A2, h->tab_B2, h->tab_B1, h->tab_lu1, h->tab_d0, h->tab_dN};
+    const size_t cnt[6] = {7 * (size_t)h->Ny, 7 * (size_t)h->Ny, 7 * (size_t)h->Ny, 7 * (size_t)h->Ny,
+                           (size_t)h->Ny, (size_t)h->Ny};
+    dfr* dst = h->tab_pairs;
+    for (int k = 0; k < 6; ++k) {
+      k_split_tab<<<(unsigned)((cnt[k] + 255) / 256), 256, 0, h->stream>>>(src[k], dst, cnt[k]);
+      dst += cnt[k];
+    }
   }
   cudaError_t e;
   if (!h->lean) {
@@ -1118,7 +1153,7 @@ cudaError_t launch_derive(chan_s* h) {
 }
 
 cudaError_t launch_pre(chan_s* h, double2* u1, double2* u3, double2* om1, double2* om3) {
-  size_t sm = sizeof(double) * 14 * h->Ny;
+  size_t sm = ysm(h, 14);
   const void* fn = use_df(h) ? (const void*)k_pre_df : (const void*)k_pre;
   cudaError_t e = smem_attr(fn, sm);
   if (e != cudaSuccess) return e;
@@ -1131,7 +1166,7 @@ cudaError_t launch_pre(chan_s* h, double2* u1, double2* u3, double2* om1, double
 
 cudaError_t launch_nonlin(chan_s* h, const double2* H1, const double2* H2, const double2* H3, double2* Nchi,
                           double2* Nom) {
-  size_t sm = sizeof(double) * 14 * h->Ny;
+  size_t sm = ysm(h, 14);
   const void* fn = use_df(h) ? (const void*)k_nonlin_df : (const void*)k_nonlin;
   cudaError_t e = smem_attr(fn, sm);
   if (e != cudaSuccess) return e;
@@ -1144,7 +1179,7 @@ cudaError_t launch_nonlin(chan_s* h, const double2* H1, const double2* H2, const
 
 cudaError_t launch_nonlin_scratch(chan_s* h, const double2* H1, const double2* H2, const double2* H3, double2* Nchi,
                                  double2* Nom, double2* scr) {
-  size_t sm = sizeof(double) * 14 * h->Ny;
+  size_t sm = ysm(h, 14);
   cudaError_t e = smem_attr((const void*)k_nonlin, sm);
   if (e != cudaSuccess) return e;
   k_nonlin<<<ygrid(h), kYThreads, sm, h->stream>>>(geo(h), ytabs(h), H1, H2, H3, Nchi, Nom, scr);
@@ -1152,7 +1187,7 @@ cudaError_t launch_nonlin_scratch(chan_s* h, const double2* H1, const double2* H
 }
 
 cudaError_t launch_helm(chan_s* h, const double2* Nchi, const double2* Nom, int s) {
-  size_t sm = sizeof(double) * 14 * h->Ny;
+  size_t sm = ysm(h, 14);
   const void* fn = use_df(h) ? (const void*)k_helm<YDF> : (const void*)k_helm<YF64>;
   cudaError_t e = smem_attr(fn, sm);
   if (e != cudaSuccess) return e;
@@ -1166,7 +1201,7 @@ cudaError_t launch_helm(chan_s* h, const double2* Nchi, const double2* Nom, int 
 }
 
 cudaError_t launch_poisson(chan_s* h, int s) {
-  size_t sm = sizeof(double) * 23 * h->Ny;
+  size_t sm = ysm(h, 23);
   const void* fn = use_df(h) ? (const void*)k_poisson<YDF> : (const void*)k_poisson<YF64>;
   cudaError_t e = smem_attr(fn, sm);
   if (e != cudaSuccess) return e;
@@ -1219,7 +1254,7 @@ cudaError_t launch_pre_batch(chan_s* const* hs, int n, const BatchWork* w, cudaS
     B.p[r] = PreP{geo(h), ytabs(h), h->v, h->om, h->dv, h->U1, h->U3, w[r].u1, w[r].u3, w[r].om1, w[r].om3};
   }
   const int blocks = fill_begin(B, hs, n);
-  const size_t sm = sizeof(double) * 14 * max_ny(hs, n);
+  const size_t sm = ysm_batch(hs, n, 14);
   const bool df = use_df(hs[0]);
   cudaError_t e = smem_attr(df ? (const void*)kb_pre<YDF> : (const void*)kb_pre<YF64>, sm);
   if (e != cudaSuccess) return e;
@@ -1235,7 +1270,7 @@ cudaError_t launch_nonlin_batch(chan_s* const* hs, int n, const BatchWork* w, cu
     B.p[r] = NonlinP{geo(h), ytabs(h), w[r].H1, w[r].H2, w[r].H3, w[r].Nchi, w[r].Nom, h->scr};
   }
   const int blocks = fill_begin(B, hs, n);
-  const size_t sm = sizeof(double) * 14 * max_ny(hs, n);
+  const size_t sm = ysm_batch(hs, n, 14);
   const bool df = use_df(hs[0]);
   cudaError_t e = smem_attr(df ? (const void*)kb_nonlin<YDF> : (const void*)kb_nonlin<YF64>, sm);
   if (e != cudaSuccess) return e;
@@ -1252,7 +1287,7 @@ cudaError_t launch_helm_batch(chan_s* const* hs, int n, const BatchWork* w, cuda
                    (int)(h->nsub % 3)};
   }
   const int blocks = fill_begin(B, hs, n);
-  const size_t sm = sizeof(double) * 14 * max_ny(hs, n);
+  const size_t sm = ysm_batch(hs, n, 14);
   const bool df = use_df(hs[0]);
   cudaError_t e = smem_attr(df ? (const void*)kb_helm<YDF> : (const void*)kb_helm<YF64>, sm);
   if (e != cudaSuccess) return e;
@@ -1270,7 +1305,7 @@ cudaError_t launch_poisson_batch(chan_s* const* hs, int n, const BatchWork* w, c
     B.p[r] = PoisP{geo(h), ytabs(h), helm_slot_y(h, s), pois_y(h), infl_slot_y(h, s), h->v, h->chi, h->dv, h->scr, (int)(h->nsub % 3)};
   }
   const int blocks = fill_begin(B, hs, n);
-  const size_t sm = sizeof(double) * 23 * max_ny(hs, n);
+  const size_t sm = ysm_batch(hs, n, 23);
   const bool df = use_df(hs[0]);
   cudaError_t e = smem_attr(df ? (const void*)kb_poisson<YDF> : (const void*)kb_poisson<YF64>, sm);
   if (e != cudaSuccess) return e;

@@ -76,3 +76,14 @@ def test_footprint_of_the_large_grids():
     small = chan.footprint_bytes(384, 257, 384, chan.CHAN_PREC_FP64)
     n = 257 * 384 * 192
     assert small > (6 + 18) * n * 16 + 12 * 257 * 576 * 192 * 16
+
+
+def test_init_rejects_an_unknown_table_placement():
+    lib = chan.library()
+    o = chan.chan_opts()
+    lib.chan_opts_default(ctypes.byref(o))
+    o.re_tau, o.Lx, o.Lz, o.Nx, o.Ny, o.Nz, o.dt = 180.0, 3.14, 1.57, 32, 49, 32, 1e-3
+    o.y_tables = 3
+    h = ctypes.c_void_p()
+    assert lib.chan_init_ex(ctypes.byref(h), ctypes.byref(o)) == chan.CHAN_EINVAL
+    assert "y_tables" in lib.chan_last_error(None).decode()

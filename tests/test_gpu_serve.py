@@ -106,8 +106,8 @@ def test_autotuned_shapes_leave_results_unchanged():
         s0 = SY.perturbed_poiseuille(ch.grid(), 395.0, math.pi, math.pi / 2, 64, 96, seed=4, amp=0.1)
         ch.set_state(s0["v"], s0["omega2"], s0["U1"], s0["U3"])
         if tune:
-            kb, nt = ch.autotune()
-            assert kb in (1, 2, 4, 8, 16) and nt in (128, 256, 512)
+            kb, nt, yt = ch.autotune()
+            assert kb in (1, 2, 4, 8, 16) and nt in (128, 256, 512) and yt in (0, 1)
         ch.step(6)
         out.append(ch.get_state())
         ch.close()
