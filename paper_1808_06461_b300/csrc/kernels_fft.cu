@@ -179,7 +179,7 @@ __device__ __forceinline__ void dif_stage(T2* a, int L, int nb, int ld, const T2
   const int tmul = L / Ls;
   const int total = nb * nbf;
   for (int t = threadIdx.x; t < total; t += blockDim.x) {
-    const int bi = (int)__umulhi((unsigned)t, mag_nbf);   // t / nbf (exact while t nbf < 2^32)
+    const int bi = mag_nbf ? (int)__umulhi((unsigned)t, mag_nbf) : t;   // t / nbf (exact while t nbf < 2^32)
     const int u = t - bi * nbf;
     const int blk = mag_m ? (int)__umulhi((unsigned)u, mag_m) : u;   // u / m (mag 0: m = 1)
     const int j = u - blk * m;
@@ -216,7 +216,7 @@ __device__ __forceinline__ void dit_stage(T2* a, int L, int nb, int ld, const T2
   const int tmul = L / Ls;
   const int total = nb * nbf;
   for (int t = threadIdx.x; t < total; t += blockDim.x) {
-    const int bi = (int)__umulhi((unsigned)t, mag_nbf);   // t / nbf (exact while t nbf < 2^32)
+    const int bi = mag_nbf ? (int)__umulhi((unsigned)t, mag_nbf) : t;   // t / nbf (exact while t nbf < 2^32)
     const int u = t - bi * nbf;
     const int blk = mag_m ? (int)__umulhi((unsigned)u, mag_m) : u;   // u / m (mag 0: m = 1)
     const int j = u - blk * m;
