@@ -472,7 +472,7 @@ def run_ours(args, c, name):
 def run_serving(args, rank):
     """The serving mix: Poisson arrivals (seeded, mean 50 req/s) of minimal-box runs with
     Re_tau in {180, 395, 550}, Nx, Nz in {32, 64, 128}, Ny in {49, 97, 129} and 100-2000
-    substeps, served by the continuous-batching loop, FP64 and mixed."""
+    substeps, served by the continuous-batching loop, in each precision mode."""
     import synthetic as SY
     from paper_1808_06461_b300.serve import Server, channel_factory, poisson_requests
 
@@ -481,7 +481,7 @@ def run_serving(args, rank):
 
     out = {"requests": args.serve_requests, "rate_per_s": 50.0, "seed": 42, "hbm_budget_gb": 64,
            "max_slots": 16}
-    for prec, tag in ((0, "fp64"), (1, "mixed")):
+    for prec, tag in ((0, "fp64"), (1, "mixed"), (2, "f64x")):
         for packed in (False, True):
             reqs = poisson_requests(args.serve_requests, 50.0, 42 + rank, precision=prec)
             _, m = Server(64 << 30, max_slots=16, factory=channel_factory(ic), packed=packed).run(

@@ -306,7 +306,7 @@ int chan_rhs_terms_noalloc(chan_t h, const void* H, void* N);
  * paper has no counterpart).  A batch holds n >= 1 handles of one precision
  * on one device, each with its state set; they may differ in every size and
  * be at different RK3 phases.  chan_batch_step advances every run by nsub
- * substeps with one launch per kernel covering all runs (at most 8 runs per
+ * substeps with one launch per kernel covering all runs (at most 16 runs per
  * launch; more runs take more launches), on the batch's stream (the given
  * stream, or a stream of its own when NULL).  It first makes the batch stream
  * wait for each run's stream and afterwards makes each run's stream wait for

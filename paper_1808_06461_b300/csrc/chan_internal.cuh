@@ -15,7 +15,7 @@
 // Wavenumber classes (shared LU factors): c = |kz| * nxh + kx, |kz| < Nz/2.
 
 #define CHAN_MAXFIELDS 12
-#define CHAN_MAXBATCH 8   // runs per packed launch
+#define CHAN_MAXBATCH 16  // runs per packed launch (kernel parameters stay below 32 KB)
 
 struct YTabs {            // mode-independent wall-normal tables (device)
   const double* A2;       // [Ny][7]
