@@ -63,6 +63,7 @@ __global__ void k_flux(const double* U1, const double* wq, int Ny, double* scal)
     for (int i = 0; i < Ny; ++i) q += wq[i] * U1[i];
     scal[1] = q;
     scal[0] = 0.0;
+    scal[2] = 0.0;   // no Helmholtz right-hand sides of a previous substep yet
   }
 }
 
@@ -214,7 +215,7 @@ size_t footprint_ex(int Nx, int Ny, int Nz, int prec, int slab_req, int lean) {
   const size_t L1 = 3 * (size_t)Nx / 2, L3 = 3 * (size_t)Nz / 2;
   const size_t es = prec == CHAN_PREC_MIXED ? sizeof(float2) : sizeof(double2);
   size_t b = 0;
-  b += 6 * n * sizeof(double2) + 4 * Ny * sizeof(double) + 2 * sizeof(double);            // state
+  b += 8 * n * sizeof(double2) + 4 * Ny * sizeof(double) + 3 * sizeof(double);            // state
   b += 5 * 7 * (size_t)Ny * sizeof(double) + 3 * (size_t)Ny * sizeof(double);              // y tables
   b += (nxh + Nz) * sizeof(double);                                                          // wavenumbers
   b += ((size_t)Ny * 7 * C + nslot * (size_t)Ny * 11 * C + nslot * 4 * C + 3 * ((size_t)Ny + 1)) * sizeof(double);
@@ -475,9 +476,10 @@ int chan_init_ex(chan_t* out, const chan_opts* o) {
     // state
     h->v = dalloc<double2>(h, n); h->om = dalloc<double2>(h, n); h->chi = dalloc<double2>(h, n);
     h->dv = dalloc<double2>(h, n); h->Nchi_p = dalloc<double2>(h, n); h->Nom_p = dalloc<double2>(h, n);
+    h->Rom = dalloc<double2>(h, n); h->Rchi = dalloc<double2>(h, n);
     h->U1 = dalloc<double>(h, Ny); h->U3 = dalloc<double>(h, Ny);
     h->H1m_p = dalloc<double>(h, Ny); h->H3m_p = dalloc<double>(h, Ny);
-    h->scal = dalloc<double>(h, 2);
+    h->scal = dalloc<double>(h, 3);
     // tables
     double** dst[] = {&h->tab_A2, &h->tab_B2, &h->tab_B1, &h->tab_lu1, &h->tab_lu2f};
     const double* src[] = {tb.A2, tb.B2, tb.B1, tb.lu1, tb.lu2f};

@@ -68,8 +68,9 @@ struct chan_s {
   std::vector<double> y, wq;
   // state (device)
   double2 *v, *om, *chi, *dv, *Nchi_p, *Nom_p;
+  double2 *Rom, *Rchi;     // interior right-hand sides of the last Helmholtz solves (valid when scal[2] != 0)
   double *U1, *U3, *H1m_p, *H3m_p;
-  double* scal;            // [0] f of last substep, [1] Q0
+  double* scal;            // [0] f of last substep, [1] Q0, [2] Rom / Rchi valid
   // tables (device)
   double *tab_A2, *tab_B2, *tab_B1, *tab_lu1, *tab_lu2f, *tab_d0, *tab_dN, *tab_wq;
   dfr* tab_pairs;          // double-float mode: A2, B2, B1, lu1 ([Ny][7] each), d0, dN as pairs

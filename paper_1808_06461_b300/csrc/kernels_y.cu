@@ -344,11 +344,18 @@ __global__ void __launch_bounds__(128) k_nonlin_df(Geo g, YTabs t, const double2
 // (Eqs. (psi), (chi1)) multiplied through by A:
 //   [(1 + b dt nu k^2) A - b dt nu B] X+ = A[(1 - a dt nu k^2) X + dt(g N + z Nprev)] + a dt nu B X,
 // wall rows X+ = 0 (chi's are the particular solution).  Nprev <- N.
+// The interior right-hand side R of each solve is kept; in the next substep
+// (coefficients b' of the previous one) B X follows from it, since
+// [(1 + b' dt nu k^2) A - b' dt nu B] X = R' on interior rows (the wall
+// corrections of chi leave interior rows unchanged), and the right-hand side
+// becomes A[(1 + a/b') X + dt(g N + z Nprev)] - (a/b') R' with no B product.
+// The first substep after a state upload (flag scal[2] = 0) uses B X directly.
 // ---------------------------------------------------------------------------
 template <class Y>
 __device__ __forceinline__ void helm_body(Geo g, YTabs t, const typename Y::R* __restrict__ helm,
                                           double2* om, double2* chi, const double2* __restrict__ Nchi,
                                           const double2* __restrict__ Nom, double2* Nchi_p, double2* Nom_p,
+                                          double2* Rom, double2* Rchi, const double* __restrict__ scal,
                                           double2* scr_, int s, int bid) {
   typedef typename Y::R R;
   typedef typename Y::C C;
@@ -372,7 +379,10 @@ __device__ __forceinline__ void helm_body(Geo g, YTabs t, const typename Y::R* _
   }
   const double gm = c_rk3[s][0], zt = c_rk3[s][1], al = c_rk3[s][2];
   const double dt = g.dt, nu = g.nu;
-  const R c1 = Y::r(1.0 - al * dt * nu * mi.k2), cg = Y::r(dt * gm), cz = Y::r(dt * zt), ca = Y::r(al * dt * nu);
+  const bool prev = scal[2] != 0.0;   // the previous substep's right-hand sides are valid
+  const double bp = c_rk3[(s + 2) % 3][3];
+  const R c1 = Y::r(prev ? 1.0 + al / bp : 1.0 - al * dt * nu * mi.k2), cg = Y::r(dt * gm), cz = Y::r(dt * zt);
+  const R ca = Y::r(al * dt * nu), qp = Y::r(-al / bp);
   const R* H = helm + mi.c;   // the substep's slot
   double2* scr = scr_;
   double2* scr2 = scr + (size_t)Ny * M;
@@ -398,8 +408,16 @@ __device__ __forceinline__ void helm_body(Geo g, YTabs t, const typename Y::R* _
     if (i < 0) continue;
     C ro = Y::zero(), rc = Y::zero();
     if (i > 0 && i < Ny - 1) {
-      ro = Y::axpy(ca, yband7<Y>(sB + 7 * i, wx), yband7<Y>(sA + 7 * i, wa));
-      rc = Y::axpy(ca, yband7<Y>(sB + 7 * i, wy), yband7<Y>(sA + 7 * i, wb));
+      const size_t oi = (size_t)i * M + m;
+      if (prev) {
+        ro = Y::axpy(qp, Y::ld(Rom, oi), yband7<Y>(sA + 7 * i, wa));
+        rc = Y::axpy(qp, Y::ld(Rchi, oi), yband7<Y>(sA + 7 * i, wb));
+      } else {
+        ro = Y::axpy(ca, yband7<Y>(sB + 7 * i, wx), yband7<Y>(sA + 7 * i, wa));
+        rc = Y::axpy(ca, yband7<Y>(sB + 7 * i, wy), yband7<Y>(sA + 7 * i, wb));
+      }
+      Y::st(Rom, oi, ro);
+      Y::st(Rchi, oi, rc);
     }
     const R* Hi = H + (size_t)i * 11 * NC;
     const R l0 = Hi[0], l1 = Hi[NC], l2 = Hi[2 * NC];
@@ -420,7 +438,10 @@ template <class Y>
 __global__ void __launch_bounds__(128) k_helm(Geo g, YTabs t, const typename Y::R* __restrict__ helm,
                                               double2* om, double2* chi, const double2* __restrict__ Nchi,
                                               const double2* __restrict__ Nom, double2* Nchi_p, double2* Nom_p,
-                                              double2* scr, int s) { helm_body<Y>(g, t, helm, om, chi, Nchi, Nom, Nchi_p, Nom_p, scr, s, blockIdx.x); }
+                                              double2* Rom, double2* Rchi, const double* __restrict__ scal,
+                                              double2* scr, int s) {
+  helm_body<Y>(g, t, helm, om, chi, Nchi, Nom, Nchi_p, Nom_p, Rom, Rchi, scal, scr, s, blockIdx.x);
+}
 
 
 // ---------------------------------------------------------------------------
@@ -591,7 +612,10 @@ __device__ __forceinline__ void mean_body(Geo g, YTabs t, const double* __restri
     U1[i] = r1[i] + c * uh[i];
     U3[i] = r3[i];
   }
-  if (threadIdx.x == 0) scal[0] = c / ((al + be) * dt);
+  if (threadIdx.x == 0) {
+    scal[0] = c / ((al + be) * dt);
+    scal[2] = 1.0;   // the Helmholtz right-hand sides of this substep are in place
+  }
 }
 
 __global__ void __launch_bounds__(256) k_mean(Geo g, YTabs t, const double* __restrict__ helm,
@@ -977,7 +1001,7 @@ __global__ void k_setup_pressure(Geo g, YTabs t, const double* __restrict__ pois
 // ---------------------------------------------------------------------------
 struct PreP { Geo g; YTabs t; const double2 *v, *om, *dv; const double *U1, *U3; double2 *u1o, *u3o, *om1o, *om3o; };
 struct NonlinP { Geo g; YTabs t; const double2 *H1, *H2, *H3; double2 *Nchi, *Nom, *scr; };
-struct HelmP { Geo g; YTabs t; const void* helm; double2 *om, *chi; const double2 *Nchi, *Nom; double2 *Nchi_p, *Nom_p, *scr; int s; };
+struct HelmP { Geo g; YTabs t; const void* helm; double2 *om, *chi; const double2 *Nchi, *Nom; double2 *Nchi_p, *Nom_p, *Rom, *Rchi; const double* scal; double2* scr; int s; };
 struct PoisP { Geo g; YTabs t; const void *helm, *pois, *infl; double2 *v, *chi, *dv, *scr; int s; };
 struct MeanP { Geo g; YTabs t; const double *helm, *meanh; const double2 *H1, *H3; double *U1, *U3, *H1p, *H3p, *scal; int s; };
 
@@ -1010,8 +1034,8 @@ __global__ void __launch_bounds__(128) kb_helm(YBatch<HelmP> B) {
   typedef typename Y::R R;
   const int r = batch_run(B.begin, B.n, blockIdx.x);
   const HelmP& p = B.p[r];
-  helm_body<Y>(p.g, p.t, static_cast<const R*>(p.helm), p.om, p.chi, p.Nchi, p.Nom, p.Nchi_p, p.Nom_p, p.scr, p.s,
-               blockIdx.x - B.begin[r]);
+  helm_body<Y>(p.g, p.t, static_cast<const R*>(p.helm), p.om, p.chi, p.Nchi, p.Nom, p.Nchi_p, p.Nom_p, p.Rom, p.Rchi,
+               p.scal, p.scr, p.s, blockIdx.x - B.begin[r]);
 }
 template <class Y>
 __global__ void __launch_bounds__(128) kb_poisson(YBatch<PoisP> B) {
@@ -1193,10 +1217,12 @@ cudaError_t launch_helm(chan_s* h, const double2* Nchi, const double2* Nom, int 
   if (e != cudaSuccess) return e;
   if (use_df(h))
     k_helm<YDF><<<ygrid(h), kYThreads, sm, h->stream>>>(geo(h), ytabs(h), (const dfr*)helm_slot_y(h, s), h->om,
-                                                        h->chi, Nchi, Nom, h->Nchi_p, h->Nom_p, h->scr, s);
+                                                        h->chi, Nchi, Nom, h->Nchi_p, h->Nom_p, h->Rom, h->Rchi,
+                                                        h->scal, h->scr, s);
   else
     k_helm<YF64><<<ygrid(h), kYThreads, sm, h->stream>>>(geo(h), ytabs(h), (const double*)helm_slot_y(h, s), h->om,
-                                                         h->chi, Nchi, Nom, h->Nchi_p, h->Nom_p, h->scr, s);
+                                                         h->chi, Nchi, Nom, h->Nchi_p, h->Nom_p, h->Rom, h->Rchi,
+                                                         h->scal, h->scr, s);
   return cudaGetLastError();
 }
 
@@ -1283,8 +1309,8 @@ cudaError_t launch_helm_batch(chan_s* const* hs, int n, const BatchWork* w, cuda
   YBatch<HelmP> B;
   for (int r = 0; r < n; ++r) {
     chan_s* h = hs[r];
-    B.p[r] = HelmP{geo(h), ytabs(h), helm_slot_y(h, (int)(h->nsub % 3)), h->om, h->chi, w[r].Nchi, w[r].Nom, h->Nchi_p, h->Nom_p, h->scr,
-                   (int)(h->nsub % 3)};
+    B.p[r] = HelmP{geo(h), ytabs(h), helm_slot_y(h, (int)(h->nsub % 3)), h->om, h->chi, w[r].Nchi, w[r].Nom, h->Nchi_p, h->Nom_p,
+                   h->Rom, h->Rchi, h->scal, h->scr, (int)(h->nsub % 3)};
   }
   const int blocks = fill_begin(B, hs, n);
   const size_t sm = ysm_batch(hs, n, 14);

@@ -1,5 +1,5 @@
 """The Re_tau = 2000 relaxed-resolution workload (Lx = 2 pi, Lz = pi, 1536 x 633 x
-1152, dt = 5e-5) in mixed precision, the mode it is run in: about 218 GB on the
+1152, dt = 5e-5) in mixed precision, the mode it is run in: about 236 GB on the
 device, with the transforms in slabs and the implicit-step tables recomputed
 each substep.
 
@@ -83,7 +83,7 @@ def test_re2000_mixed_nonlinear_sampled_planes_and_invariants(ref):
     st, s0, Href = ref
     ch = chan.Channel(*CFG, precision=chan.CHAN_PREC_MIXED, stream=torch.cuda.current_stream().cuda_stream)
     try:
-        assert ch.device_bytes() < 230e9
+        assert ch.device_bytes() < 240e9
         ch.set_state(s0["v"], s0["omega2"], s0["U1"], s0["U3"])
         H = ch.nonlinear()
         for f in range(3):
