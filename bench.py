@@ -51,7 +51,7 @@ DEFAULT = "re550_384x257x384"
 
 # ---------------------------------------------------------------------------
 # Algorithmic FP64 flop counts of each kernel (per launch), from the steps the
-# kernels take: Stockham radix-4/2/3 FFTs (a radix-R butterfly costs its
+# kernels take: in-place mixed-radix 3/4/2 FFTs (a radix-R butterfly costs its
 # DFT adds plus (R-1) twiddle complex multiplies of 6 flops unless its twiddle
 # index is 0) and the banded sweeps of the wall-normal solves (a real
 # coefficient times a complex value = 2 FMA = 4 flops).
@@ -99,7 +99,8 @@ NCU_PIPE = {("k_xpass", "fp64"): ("fp64", 0.8574)}
 
 
 # per mode-point flops of the wall-normal kernels (read off their sweeps)
-Y_FLOPS = {"k_pre": 140, "k_nonlin": 70, "k_helm": 192, "k_poisson": 132, "k_derive": 140}
+# (k_helm: the right-hand side from the previous substep's solve, A and no B product)
+Y_FLOPS = {"k_pre": 140, "k_nonlin": 70, "k_helm": 136, "k_poisson": 132, "k_derive": 140}
 
 
 def kernel_flops(name, c, launches_by_mode):

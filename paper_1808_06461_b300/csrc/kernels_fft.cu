@@ -6,8 +6,9 @@
 // columns of a plane (zero-padding kz from Nz to 3Nz/2), an x-pass turns two
 // physical z-rows at once into real space (two real rows packed into one
 // complex FFT), forms the products there and transforms them back, and a
-// final z-pass truncates to the stored modes.  All transforms are in-CTA
-// shared-memory Stockham FFTs with radix 4, 2 and 3 passes.
+// final z-pass truncates to the stored modes.  All transforms are in-CTA,
+// in-place mixed-radix (3, 4, 2) shared-memory FFTs: decimation in frequency
+// for the inverse transforms, decimation in time for the forward ones.
 #include <cstring>
 
 #include "chan_internal.cuh"

@@ -4,7 +4,7 @@ Tolerance: relative L2 (||gpu - oracle|| / ||oracle|| over every stored
 coefficient of a field) <= 1e-10 after 10 substeps for the FP64 path, the
 bar the method's FP64 result is held to.  Both sides evaluate the same
 discrete operators; they differ only in rounding order (banded LU sweeps
-vs. dense LAPACK solves, Stockham radix-4/2/3 FFTs vs. pocketfft).
+vs. dense LAPACK solves, in-place mixed-radix 3/4/2 FFTs vs. pocketfft).
 """
 import math
 
