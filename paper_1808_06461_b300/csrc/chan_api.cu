@@ -143,21 +143,46 @@ void after_state_upload(chan_s* h) {
   h->t = 0.0;
 }
 
-// u_1, u_3, omega_1, omega_3 of the current state into the work slots.
-void run_pre(chan_s* h) {
+}  // namespace
+
+int substep_inputs(const chan_s* h, double2* u1, double2* u3, double2* om1, double2* om3, size_t y0,
+                   const double2** in) {
+  const size_t o = y0 * h->M, nf = fsize(h);
+  in[1] = h->v + o;
+  in[4] = h->om + o;
+  if (h->prec != CHAN_PREC_MIXED) {
+    in[0] = u1 + o; in[2] = u3 + o; in[3] = om1 + o; in[5] = om3 + o;
+    return 0;
+  }
+  const float2* fu = reinterpret_cast<const float2*>(om1);
+  const float2* fw = reinterpret_cast<const float2*>(om3);
+  in[0] = reinterpret_cast<const double2*>(fu + o);
+  in[2] = reinterpret_cast<const double2*>(fu + nf + o);
+  in[3] = reinterpret_cast<const double2*>(fw + o);
+  in[5] = reinterpret_cast<const double2*>(fw + nf + o);
+  return (1 << 0) | (1 << 2) | (1 << 3) | (1 << 5);
+}
+
+namespace {
+
+// u_1, u_3, omega_1, omega_3 of the current state into the work slots (f32: the mixed
+// mode's substep layout, see substep_inputs).
+void run_pre(chan_s* h, bool f32 = false) {
   Traced t(h, KID_PRE);
-  CK(launch_pre(h, wf(h, WF_U1), wf(h, WF_U3), wf(h, WF_OM1), wf(h, WF_OM3)));
+  CK(launch_pre(h, wf(h, WF_U1), wf(h, WF_U3), wf(h, WF_OM1), wf(h, WF_OM3), f32));
 }
 
 // H = u x omega of the current state into WF_H1..WF_H3 (after run_pre).
-// The transforms are plane-local: slab by slab through the mixed buffers.
+// The transforms are plane-local: slab by slab through the mixed buffers (after
+// run_pre(h, true)).
 void run_nonlinear(chan_s* h) {
   void* mx[6] = {mixed(h, 0), mixed(h, 1), mixed(h, 2), mixed(h, 3), mixed(h, 4), mixed(h, 5)};
   for (int y0 = 0; y0 < h->Ny; y0 += h->slab) {
     const int ny = h->Ny - y0 < h->slab ? h->Ny - y0 : h->slab;
     const size_t o = (size_t)y0 * h->M;
-    const double2* in[6] = {wf(h, WF_U1) + o, h->v + o, wf(h, WF_U3) + o, wf(h, WF_OM1) + o, h->om + o, wf(h, WF_OM3) + o};
-    { Traced t(h, KID_ZINV); CK(launch_zinv(h, in, nullptr, mx, 6, ny)); }
+    const double2* in[6];
+    const int mask = substep_inputs(h, wf(h, WF_U1), wf(h, WF_U3), wf(h, WF_OM1), wf(h, WF_OM3), (size_t)y0, in);
+    { Traced t(h, KID_ZINV); CK(launch_zinv(h, in, nullptr, mx, 6, ny, mask)); }
     { Traced t(h, KID_XPASS); CK(launch_xpass(h, 0, mx, mx, ny)); }
     double2* Hout[3] = {wf(h, WF_H1) + o, wf(h, WF_H2) + o, wf(h, WF_H3) + o};
     { Traced t(h, KID_ZFWD); CK(launch_zfwd(h, mx, Hout, 3, ny, 1)); }
@@ -167,7 +192,7 @@ void run_nonlinear(chan_s* h) {
 void run_substep(chan_s* h) {
   const int s = (int)(h->nsub % 3);
   if (h->lean) { Traced t(h, KID_TABLES); CK(launch_setup_substep(h, s)); }
-  run_pre(h);
+  run_pre(h, true);
   run_nonlinear(h);
   { Traced t(h, KID_NONLIN); CK(launch_nonlin(h, wf(h, WF_H1), wf(h, WF_H2), wf(h, WF_H3), wf(h, WF_NCHI), wf(h, WF_NOM))); }
   { Traced t(h, KID_HELM); CK(launch_helm(h, wf(h, WF_NCHI), wf(h, WF_NOM), s)); }
@@ -351,7 +376,7 @@ static void filter_pass(chan_s* h, int kind, double p1, double p3, double* host_
     const size_t o = (size_t)y0 * h->M;
     const double2* u[3] = {wf(h, WF_U1) + o, h->v + o, wf(h, WF_U3) + o};
     const double2* in[6] = {u[0], u[1], u[2], u[0], u[1], u[2]};
-    { Traced t(h, KID_ZINV); CK(launch_zinv(h, in, applyG, mx, 6, ny)); }
+    { Traced t(h, KID_ZINV); CK(launch_zinv(h, in, applyG, mx, 6, ny, 0)); }
     { Traced t(h, KID_XPASS); CK(launch_xpass(h, 1, mx + 3, mx + 6, ny)); }   // ubar_i ubar_j -> slots 6..11
     { Traced t(h, KID_XPASS); CK(launch_xpass(h, 1, mx, mx, ny)); }           // u_i u_j       -> slots 0..5
     double2* fo[12];
@@ -676,7 +701,7 @@ int chan_nonlinear(chan_t h, double* H) {
   if (!h || !H) return bad(h, "chan_nonlinear: NULL argument");
   if (!h->have_state) return bad(h, "chan_nonlinear: no state set", CHAN_ESTATE);
   try {
-    run_pre(h);
+    run_pre(h, true);
     run_nonlinear(h);
     if (h->prec == CHAN_PREC_F64X) CK(launch_from_pairs(h, wf(h, WF_H1), wf(h, WF_H1), 3 * fsize(h)));
     CK(cudaMemcpyAsync(H, wf(h, WF_H1), 3 * fsize(h) * sizeof(double2), cudaMemcpyDeviceToHost, h->stream));
@@ -691,7 +716,7 @@ int chan_rhs_terms(chan_t h, double* N) {
   if (!h || !N) return bad(h, "chan_rhs_terms: NULL argument");
   if (!h->have_state) return bad(h, "chan_rhs_terms: no state set", CHAN_ESTATE);
   try {
-    run_pre(h);
+    run_pre(h, true);
     run_nonlinear(h);
     { Traced t(h, KID_NONLIN); CK(launch_nonlin(h, wf(h, WF_H1), wf(h, WF_H2), wf(h, WF_H3), wf(h, WF_NCHI), wf(h, WF_NOM))); }
     if (h->prec == CHAN_PREC_F64X) CK(launch_from_pairs(h, wf(h, WF_NCHI), wf(h, WF_NCHI), 2 * fsize(h)));
@@ -729,7 +754,7 @@ int chan_filtered_enstrophy(chan_t h, int kind, double p1, double p3, double* en
       const int ny = h->Ny - y0 < h->slab ? h->Ny - y0 : h->slab;
       const size_t o = (size_t)y0 * h->M;
       const double2* in[3] = {wf(h, WF_OM1) + o, h->om + o, wf(h, WF_OM3) + o};
-      { Traced t(h, KID_ZINV); CK(launch_zinv(h, in, nullptr, mx, 3, ny)); }
+      { Traced t(h, KID_ZINV); CK(launch_zinv(h, in, nullptr, mx, 3, ny, 0)); }
       { Traced t(h, KID_XPASS); CK(launch_xpass(h, 2, mx, mx, ny)); }
       double2* fo[1] = {wf(h, 4) + o};
       { Traced t(h, KID_ZFWD); CK(launch_zfwd(h, mx, fo, 1, ny, 0)); }
@@ -936,15 +961,15 @@ int chan_autotune(chan_t h) {
     for (int kb = 1; kb <= 16 && kb <= h->nxh; kb *= 2) {
       if ((size_t)kb * (h->L3 + 1) * es > 110 * 1024) break;
       h->kb_z = kb;
-      float t = timed([&] { CK(launch_zinv(h, in, nullptr, mx, 6, ny)); });
+      float t = timed([&] { CK(launch_zinv(h, in, nullptr, mx, 6, ny, 0)); });
       if (t < best_t) { best_t = t; best_kb = kb; }
     }
     h->kb_z = best_kb;
-    CK(launch_zinv(h, in, nullptr, mx, 6, ny));   // fresh inputs for the x-pass timings
+    CK(launch_zinv(h, in, nullptr, mx, 6, ny, 0));   // fresh inputs for the x-pass timings
     best_t = 1e30f;
     for (int nt : {128, 256, 512}) {
       h->xthreads = nt;
-      float t = timed([&] { CK(launch_xpass(h, 0, mx, mx, ny)); CK(launch_zinv(h, in, nullptr, mx, 6, ny)); });
+      float t = timed([&] { CK(launch_xpass(h, 0, mx, mx, ny)); CK(launch_zinv(h, in, nullptr, mx, 6, ny, 0)); });
       if (t < best_t) { best_t = t; best_nt = nt; }
     }
     h->xthreads = best_nt;

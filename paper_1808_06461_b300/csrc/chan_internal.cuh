@@ -135,7 +135,8 @@ cudaError_t launch_setup_tables(chan_s* h);
 // Lean tables: refill the single Helmholtz slot for substep s (no-op otherwise).
 cudaError_t launch_setup_substep(chan_s* h, int s);
 cudaError_t launch_derive(chan_s* h);
-cudaError_t launch_pre(chan_s* h, double2* u1, double2* u3, double2* om1, double2* om3);
+// f32: the mixed mode's substep variant (float2 transform inputs, see substep_inputs).
+cudaError_t launch_pre(chan_s* h, double2* u1, double2* u3, double2* om1, double2* om3, bool f32 = false);
 cudaError_t launch_nonlin(chan_s* h, const double2* H1, const double2* H2, const double2* H3,
                           double2* Nchi, double2* Nom);
 // k_nonlin with a caller-chosen scratch buffer of Ny * M double2.
@@ -173,7 +174,15 @@ cudaError_t launch_zfwd_batch(chan_s* const* hs, int n, const BatchWork* w, cuda
 
 // FFT passes.  in/out are arrays of nf device pointers.
 // Transform passes over ny planes; the pointers address the first plane of the slab.
-cudaError_t launch_zinv(chan_s* h, const double2* const* in, const int* apply_G, void* const* out, int nf, int ny);
+// f32_mask (mixed mode only): bit f set = input f is stored as float2 [Ny][M].
+cudaError_t launch_zinv(chan_s* h, const double2* const* in, const int* apply_G, void* const* out, int nf, int ny,
+                        int f32_mask);
+// The six substep transform inputs (u1, v, u3, w1, w2, w3) from plane y0 on, given the
+// work slots of the pre kernel's outputs, and their float2 mask: in the mixed mode the
+// substep's pre kernel leaves u1, u3 as float2 [2][Ny][M] in the w1 slot and w1, w3 in
+// the w3 slot (its u1, u3 slots hold the forward sweep).
+int substep_inputs(const chan_s* h, double2* u1, double2* u3, double2* om1, double2* om3, size_t y0,
+                   const double2** in);
 cudaError_t launch_xpass(chan_s* h, int mode, void* const* in, void* const* out, int ny);
 // pair_out: in the double-float mode write (hi, lo) pairs (substep fields) instead of FP64.
 cudaError_t launch_zfwd(chan_s* h, void* const* in, double2* const* out, int nf, int ny, int pair_out);

@@ -10,6 +10,7 @@
 // in-place mixed-radix (3, 4, 2) shared-memory FFTs: decimation in frequency
 // for the inverse transforms, decimation in time for the forward ones.
 #include <cstring>
+#include <type_traits>
 
 #include "chan_internal.cuh"
 #include "df.cuh"
@@ -75,6 +76,12 @@ template <> __device__ __forceinline__ dfc ld_fourier<dfc>(const double2* p, siz
     v.x = v.x * gg;
     v.y = v.y * gg;
   }
+  return v;
+}
+// A Fourier value stored as float2 (the mixed mode's transform inputs), times g.
+__device__ __forceinline__ float2 ld_fourier_f32(const float2* p, size_t o, bool useg, double g) {
+  float2 v = p[o];
+  if (useg) { const float gg = (float)g; v.x *= gg; v.y *= gg; }
   return v;
 }
 // Store a transform value as a Fourier value: FP64, or (pair) the raw (hi, lo) pairs.
@@ -285,6 +292,7 @@ struct ZArgs {
   const double* G;
   int Ny, Nz, nxh, M, L3, KB, ld;
   int pair_out;   // double-float mode: the forward pass writes (hi, lo) pairs
+  int f32_mask;   // inverse pass: bit f set = field f is stored as float2 (mixed mode)
   FftPlan pl;
 };
 
@@ -301,14 +309,21 @@ __device__ __forceinline__ void zinv_body(const ZArgs& A, const typename V2<T>::
   const int hz = A.Nz / 2;
   for (int e = threadIdx.x; e < A.KB * A.ld; e += blockDim.x) a[e] = zero2<T2>();
   __syncthreads();
+  const bool f32 = (A.f32_mask >> f) & 1;
   const double2* in = A.in[f] + (size_t)y * A.M;
+  const float2* in32 = reinterpret_cast<const float2*>(A.in[f]) + (size_t)y * A.M;
   for (int e = threadIdx.x; e < A.Nz * A.KB; e += blockDim.x) {
     const int jz = e / A.KB, kl = e - jz * A.KB, kx = kx0 + kl;
     if (kx >= A.nxh || jz == hz) continue;
     const int q = jz * A.nxh + kx;
     const bool useg = A.applyG[f] != 0;
     const int pz = jz < hz ? jz : jz + (A.L3 - A.Nz);
-    a[kl * A.ld + pz] = ld_fourier<T2>(in, q, useg, useg ? A.G[q] : 0.0);
+    if constexpr (std::is_same<T2, float2>::value) {
+      a[kl * A.ld + pz] = f32 ? ld_fourier_f32(in32, q, useg, useg ? A.G[q] : 0.0)
+                              : ld_fourier<T2>(in, q, useg, useg ? A.G[q] : 0.0);
+    } else {
+      a[kl * A.ld + pz] = ld_fourier<T2>(in, q, useg, useg ? A.G[q] : 0.0);
+    }
   }
   __syncthreads();
   // the middle third of the padded column is zero: pruned first stage
@@ -548,9 +563,11 @@ static ZArgs zargs(chan_s* h, size_t es) {
 
 static size_t fft_esize(const chan_s* h) { return h->prec == CHAN_PREC_MIXED ? sizeof(float2) : sizeof(double2); }
 
-cudaError_t launch_zinv(chan_s* h, const double2* const* in, const int* apply_G, void* const* out, int nf, int ny) {
+cudaError_t launch_zinv(chan_s* h, const double2* const* in, const int* apply_G, void* const* out, int nf, int ny,
+                        int f32_mask) {
   const size_t es = fft_esize(h);
   ZArgs A = zargs(h, es);
+  A.f32_mask = h->prec == CHAN_PREC_MIXED ? f32_mask : 0;
   for (int f = 0; f < nf; ++f) { A.in[f] = in[f]; A.out[f] = out[f]; A.applyG[f] = apply_G ? apply_G[f] : 0; }
   dim3 grid((h->nxh + A.KB - 1) / A.KB, ny, nf);
   size_t sm = (size_t)A.KB * A.ld * es;
@@ -618,7 +635,8 @@ cudaError_t launch_zinv_batch(chan_s* const* hs, int n, const BatchWork* w, cuda
   for (int r = 0; r < n; ++r) {
     chan_s* h = hs[r];
     ZArgs A = zargs(h, fft_esize(h));
-    const double2* in[6] = {w[r].u1, h->v, w[r].u3, w[r].om1, h->om, w[r].om3};
+    const double2* in[6];
+    A.f32_mask = substep_inputs(h, w[r].u1, w[r].u3, w[r].om1, w[r].om3, 0, in);
     for (int f = 0; f < 6; ++f) { A.in[f] = in[f]; A.out[f] = w[r].mixed[f]; A.applyG[f] = 0; }
     B.a[r] = A;
     B.tw[r] = h->tw3;

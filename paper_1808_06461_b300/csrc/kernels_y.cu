@@ -194,7 +194,13 @@ __device__ __forceinline__ ModeInfo mode_info(const Geo& g, int m) {
 // a1: u_1, u_3, omega_1, omega_3 from (v, omega_2, dv/dy); two D1 sweeps.
 // dv/dy is part of the state (it is D1 v of the last Poisson solve).
 // ---------------------------------------------------------------------------
-template <class Y>
+// F32OUT (mixed mode, substep path): the two D1 sweeps stay FP64; u_1, u_3, omega_1,
+// omega_3, which only feed the FP32 transforms, are formed in FP32 from the FP64
+// values and stored as float2: u_1, u_3 in the omega_1 slot ([2][Ny][M] float2),
+// omega_1, omega_3 in the omega_3 slot; the u_1, u_3 slots keep the forward sweep.
+__device__ __forceinline__ float2 tof(double2 x) { return make_float2((float)x.x, (float)x.y); }
+
+template <class Y, bool F32OUT = false>
 __device__ __forceinline__ void pre_body(Geo g, YTabs t, const double2* __restrict__ v,
                                          const double2* __restrict__ om, const double2* __restrict__ dv,
                                          const double* __restrict__ U1, const double* __restrict__ U3,
@@ -211,10 +217,18 @@ __device__ __forceinline__ void pre_body(Geo g, YTabs t, const double2* __restri
   if (m >= g.M) return;
   const size_t M = g.M;
   ModeInfo mi = mode_info(g, m);
+  const size_t nf = (size_t)Ny * M;
+  float2* fu = reinterpret_cast<float2*>(om1o);   // F32OUT: u_1 [0, nf), u_3 [nf, 2 nf)
+  float2* fw = reinterpret_cast<float2*>(om3o);   //         omega_1, omega_3
   if (mi.nyq) {
     for (int i = 0; i < Ny; ++i) {
       size_t o = (size_t)i * M + m;
-      u1o[o] = z2(); u3o[o] = z2(); om1o[o] = z2(); om3o[o] = z2();
+      if (F32OUT) {
+        const float2 z = make_float2(0.f, 0.f);
+        fu[o] = z; fu[nf + o] = z; fw[o] = z; fw[nf + o] = z;
+      } else {
+        u1o[o] = z2(); u3o[o] = z2(); om1o[o] = z2(); om3o[o] = z2();
+      }
     }
     return;
   }
@@ -243,11 +257,36 @@ __device__ __forceinline__ void pre_body(Geo g, YTabs t, const double2* __restri
   C px[3] = {Y::zero(), Y::zero(), Y::zero()}, pw[3] = {Y::zero(), Y::zero(), Y::zero()};
   const R q1 = Y::r(mean ? 0.0 : mi.k1 / mi.k2), q3 = Y::r(mean ? 0.0 : mi.k3 / mi.k2);
   const R k1 = Y::r(mi.k1), k3 = Y::r(mi.k3);
+  const float q1f = mean ? 0.f : (float)(mi.k1 / mi.k2), q3f = mean ? 0.f : (float)(mi.k3 / mi.k2);
+  const float k1f = (float)mi.k1, k3f = (float)mi.k3;
   for (int i = Ny - 1; i >= 0; --i) {
     const size_t o = (size_t)i * M + m;
     const R* lu = sLU + 7 * i;
     const C P = ybwd<Y>(Y::ld(u1o, o), lu[3], lu[4], lu[5], lu[6], px);   // D1 of dv/dy
     const C Q = ybwd<Y>(Y::ld(u3o, o), lu[3], lu[4], lu[5], lu[6], pw);   // D1 omega_2
+    if constexpr (F32OUT) {
+      const float2 fP = tof(Y::d(P)), fQ = tof(Y::d(Q));
+      float2 a1, a3, d1, d3, fv = make_float2(0.f, 0.f);
+      if (mean) {
+        a1 = make_float2((float)U1[i], 0.f);
+        a3 = make_float2((float)U3[i], 0.f);
+        d1 = fP;
+        d3 = fQ;
+      } else {
+        const float2 fd = tof(dv[o]), fo = tof(om[o]);
+        fv = tof(v[o]);
+        // u_1 = i (q1 dv - q3 om), u_3 = i (q3 dv + q1 om), likewise d/dy from (P, Q)
+        a1 = make_float2(-(q1f * fd.y - q3f * fo.y), q1f * fd.x - q3f * fo.x);
+        a3 = make_float2(-(q3f * fd.y + q1f * fo.y), q3f * fd.x + q1f * fo.x);
+        d1 = make_float2(-(q1f * fP.y - q3f * fQ.y), q1f * fP.x - q3f * fQ.x);
+        d3 = make_float2(-(q3f * fP.y + q1f * fQ.y), q3f * fP.x + q1f * fQ.x);
+      }
+      fu[o] = a1;
+      fu[nf + o] = a3;
+      fw[o] = make_float2(d3.x + k3f * fv.y, d3.y - k3f * fv.x);        // du3/dy - i k3 v
+      fw[nf + o] = make_float2(-k1f * fv.y - d1.x, k1f * fv.x - d1.y);  // i k1 v - du1/dy
+      continue;
+    }
     C u1, u3, du1, du3, vi = Y::zero();
     if (mean) {
       u1 = Y::c(make_double2(U1[i], 0.0));
@@ -274,6 +313,10 @@ __global__ void __launch_bounds__(128) k_pre(Geo g, YTabs t, const double2* __re
                                              const double2* __restrict__ om, const double2* __restrict__ dv,
                                              const double* __restrict__ U1, const double* __restrict__ U3,
                                              double2* u1o, double2* u3o, double2* om1o, double2* om3o) { pre_body<YF64>(g, t, v, om, dv, U1, U3, u1o, u3o, om1o, om3o, blockIdx.x); }
+__global__ void __launch_bounds__(128) k_pre_f32(Geo g, YTabs t, const double2* __restrict__ v,
+                                                 const double2* __restrict__ om, const double2* __restrict__ dv,
+                                                 const double* __restrict__ U1, const double* __restrict__ U3,
+                                                 double2* u1o, double2* u3o, double2* om1o, double2* om3o) { pre_body<YF64, true>(g, t, v, om, dv, U1, U3, u1o, u3o, om1o, om3o, blockIdx.x); }
 __global__ void __launch_bounds__(128) k_pre_df(Geo g, YTabs t, const double2* __restrict__ v,
                                                 const double2* __restrict__ om, const double2* __restrict__ dv,
                                                 const double* __restrict__ U1, const double* __restrict__ U3,
@@ -1017,11 +1060,11 @@ __device__ __forceinline__ int batch_run(const int* begin, int n, int b) {
   return r;
 }
 
-template <class Y>
+template <class Y, bool F32OUT = false>
 __global__ void __launch_bounds__(128) kb_pre(YBatch<PreP> B) {
   const int r = batch_run(B.begin, B.n, blockIdx.x);
   const PreP& p = B.p[r];
-  pre_body<Y>(p.g, p.t, p.v, p.om, p.dv, p.U1, p.U3, p.u1o, p.u3o, p.om1o, p.om3o, blockIdx.x - B.begin[r]);
+  pre_body<Y, F32OUT>(p.g, p.t, p.v, p.om, p.dv, p.U1, p.U3, p.u1o, p.u3o, p.om1o, p.om3o, blockIdx.x - B.begin[r]);
 }
 template <class Y>
 __global__ void __launch_bounds__(128) kb_nonlin(YBatch<NonlinP> B) {
@@ -1176,13 +1219,16 @@ cudaError_t launch_derive(chan_s* h) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_pre(chan_s* h, double2* u1, double2* u3, double2* om1, double2* om3) {
+cudaError_t launch_pre(chan_s* h, double2* u1, double2* u3, double2* om1, double2* om3, bool f32) {
   size_t sm = ysm(h, 14);
-  const void* fn = use_df(h) ? (const void*)k_pre_df : (const void*)k_pre;
+  f32 = f32 && h->prec == CHAN_PREC_MIXED;
+  const void* fn = use_df(h) ? (const void*)k_pre_df : (f32 ? (const void*)k_pre_f32 : (const void*)k_pre);
   cudaError_t e = smem_attr(fn, sm);
   if (e != cudaSuccess) return e;
   if (use_df(h))
     k_pre_df<<<ygrid(h), kYThreads, sm, h->stream>>>(geo(h), ytabs(h), h->v, h->om, h->dv, h->U1, h->U3, u1, u3, om1, om3);
+  else if (f32)
+    k_pre_f32<<<ygrid(h), kYThreads, sm, h->stream>>>(geo(h), ytabs(h), h->v, h->om, h->dv, h->U1, h->U3, u1, u3, om1, om3);
   else
     k_pre<<<ygrid(h), kYThreads, sm, h->stream>>>(geo(h), ytabs(h), h->v, h->om, h->dv, h->U1, h->U3, u1, u3, om1, om3);
   return cudaGetLastError();
@@ -1281,10 +1327,12 @@ cudaError_t launch_pre_batch(chan_s* const* hs, int n, const BatchWork* w, cudaS
   }
   const int blocks = fill_begin(B, hs, n);
   const size_t sm = ysm_batch(hs, n, 14);
-  const bool df = use_df(hs[0]);
-  cudaError_t e = smem_attr(df ? (const void*)kb_pre<YDF> : (const void*)kb_pre<YF64>, sm);
+  const bool df = use_df(hs[0]), f32 = hs[0]->prec == CHAN_PREC_MIXED;
+  const void* fn = df ? (const void*)kb_pre<YDF> : (f32 ? (const void*)kb_pre<YF64, true> : (const void*)kb_pre<YF64>);
+  cudaError_t e = smem_attr(fn, sm);
   if (e != cudaSuccess) return e;
   if (df) kb_pre<YDF><<<blocks, kYThreads, sm, st>>>(B);
+  else if (f32) kb_pre<YF64, true><<<blocks, kYThreads, sm, st>>>(B);
   else kb_pre<YF64><<<blocks, kYThreads, sm, st>>>(B);
   return cudaGetLastError();
 }
