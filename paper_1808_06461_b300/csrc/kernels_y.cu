@@ -394,14 +394,60 @@ __global__ void __launch_bounds__(128) k_nonlin_df(Geo g, YTabs t, const double2
 // becomes A[(1 + a/b') X + dt(g N + z Nprev)] - (a/b') R' with no B product.
 // The first substep after a state upload (flag scal[2] = 0) uses B X directly.
 // ---------------------------------------------------------------------------
+// One field (omega_2 or chi) of one mode: right-hand side, forward and backward sweeps.
 template <class Y>
+__device__ __forceinline__ void helm_one(int Ny, size_t M, size_t NC, int m, const typename Y::R* sA,
+                                         const typename Y::R* sB, const typename Y::R* __restrict__ H, double2* X,
+                                         const double2* __restrict__ N, double2* Np, double2* Rf, double2* scr,
+                                         bool prev, typename Y::R c1, typename Y::R cg, typename Y::R cz,
+                                         typename Y::R ca, typename Y::R qp) {
+  typedef typename Y::R R;
+  typedef typename Y::C C;
+  C wa[7], wx[7], hz[3];
+#pragma unroll
+  for (int d = 0; d < 7; ++d) { wa[d] = Y::zero(); wx[d] = Y::zero(); }
+#pragma unroll
+  for (int d = 0; d < 3; ++d) hz[d] = Y::zero();
+  for (int j = 0; j < Ny + 3; ++j) {
+    C a = Y::zero(), x = Y::zero();
+    if (j < Ny) {
+      const size_t o = (size_t)j * M + m;
+      const C n = Y::ld(N, o);
+      x = Y::ld(X, o);
+      a = Y::axpy(cz, Y::ld(Np, o), Y::axpy(cg, n, Y::scl(c1, x)));
+      Y::st(Np, o, n);
+    }
+    ypush<Y>(wa, a);
+    ypush<Y>(wx, x);
+    const int i = j - 3;
+    if (i < 0) continue;
+    C r = Y::zero();
+    if (i > 0 && i < Ny - 1) {
+      const size_t oi = (size_t)i * M + m;
+      r = prev ? Y::axpy(qp, Y::ld(Rf, oi), yband7<Y>(sA + 7 * i, wa))
+               : Y::axpy(ca, yband7<Y>(sB + 7 * i, wx), yband7<Y>(sA + 7 * i, wa));
+      Y::st(Rf, oi, r);
+    }
+    const R* Hi = H + (size_t)i * 11 * NC;
+    Y::st(scr, (size_t)i * M + m, yfwd<Y>(r, Hi[0], Hi[NC], Hi[2 * NC], hz));
+  }
+  C nx[3] = {Y::zero(), Y::zero(), Y::zero()};
+  for (int i = Ny - 1; i >= 0; --i) {
+    const size_t o = (size_t)i * M + m;
+    const R* Hi = H + (size_t)i * 11 * NC;
+    Y::st(X, o, ybwd<Y>(Y::ld(scr, o), Hi[3 * NC], Hi[4 * NC], Hi[5 * NC], Hi[6 * NC], nx));
+  }
+}
+
+// FS: 0 omega_2 only, 1 chi only, 2 both (one after the other).  Each field's arithmetic
+// is the same in every form, so one thread per (mode, field) and one per mode agree bitwise.
+template <class Y, int FS>
 __device__ __forceinline__ void helm_body(Geo g, YTabs t, const typename Y::R* __restrict__ helm,
                                           double2* om, double2* chi, const double2* __restrict__ Nchi,
                                           const double2* __restrict__ Nom, double2* Nchi_p, double2* Nom_p,
                                           double2* Rom, double2* Rchi, const double* __restrict__ scal,
                                           double2* scr_, int s, int bid) {
   typedef typename Y::R R;
-  typedef typename Y::C C;
   extern __shared__ double sm[];
   const int Ny = g.Ny;
   R* sp = reinterpret_cast<R*>(sm);
@@ -416,7 +462,8 @@ __device__ __forceinline__ void helm_body(Geo g, YTabs t, const typename Y::R* _
   if (mi.nyq) {
     for (int i = 0; i < Ny; ++i) {
       size_t o = (size_t)i * M + m;
-      om[o] = z2(); chi[o] = z2(); Nchi_p[o] = z2(); Nom_p[o] = z2();
+      if (FS != 1) { om[o] = z2(); Nom_p[o] = z2(); }
+      if (FS != 0) { chi[o] = z2(); Nchi_p[o] = z2(); }
     }
     return;
   }
@@ -427,63 +474,21 @@ __device__ __forceinline__ void helm_body(Geo g, YTabs t, const typename Y::R* _
   const R c1 = Y::r(prev ? 1.0 + al / bp : 1.0 - al * dt * nu * mi.k2), cg = Y::r(dt * gm), cz = Y::r(dt * zt);
   const R ca = Y::r(al * dt * nu), qp = Y::r(-al / bp);
   const R* H = helm + mi.c;   // the substep's slot
-  double2* scr = scr_;
-  double2* scr2 = scr + (size_t)Ny * M;
-  C wa[7], wx[7], wb[7], wy[7], ho[3], hc[3];
-#pragma unroll
-  for (int d = 0; d < 7; ++d) { wa[d] = Y::zero(); wx[d] = Y::zero(); wb[d] = Y::zero(); wy[d] = Y::zero(); }
-#pragma unroll
-  for (int d = 0; d < 3; ++d) { ho[d] = Y::zero(); hc[d] = Y::zero(); }
-  for (int j = 0; j < Ny + 3; ++j) {
-    C ao = Y::zero(), xo = Y::zero(), ac = Y::zero(), xc = Y::zero();
-    if (j < Ny) {
-      const size_t o = (size_t)j * M + m;
-      const C no = Y::ld(Nom, o), nc = Y::ld(Nchi, o);
-      xo = Y::ld(om, o);
-      xc = Y::ld(chi, o);
-      ao = Y::axpy(cz, Y::ld(Nom_p, o), Y::axpy(cg, no, Y::scl(c1, xo)));
-      ac = Y::axpy(cz, Y::ld(Nchi_p, o), Y::axpy(cg, nc, Y::scl(c1, xc)));
-      Y::st(Nom_p, o, no);
-      Y::st(Nchi_p, o, nc);
-    }
-    ypush<Y>(wa, ao); ypush<Y>(wx, xo); ypush<Y>(wb, ac); ypush<Y>(wy, xc);
-    const int i = j - 3;
-    if (i < 0) continue;
-    C ro = Y::zero(), rc = Y::zero();
-    if (i > 0 && i < Ny - 1) {
-      const size_t oi = (size_t)i * M + m;
-      if (prev) {
-        ro = Y::axpy(qp, Y::ld(Rom, oi), yband7<Y>(sA + 7 * i, wa));
-        rc = Y::axpy(qp, Y::ld(Rchi, oi), yband7<Y>(sA + 7 * i, wb));
-      } else {
-        ro = Y::axpy(ca, yband7<Y>(sB + 7 * i, wx), yband7<Y>(sA + 7 * i, wa));
-        rc = Y::axpy(ca, yband7<Y>(sB + 7 * i, wy), yband7<Y>(sA + 7 * i, wb));
-      }
-      Y::st(Rom, oi, ro);
-      Y::st(Rchi, oi, rc);
-    }
-    const R* Hi = H + (size_t)i * 11 * NC;
-    const R l0 = Hi[0], l1 = Hi[NC], l2 = Hi[2 * NC];
-    Y::st(scr, (size_t)i * M + m, yfwd<Y>(ro, l0, l1, l2, ho));
-    Y::st(scr2, (size_t)i * M + m, yfwd<Y>(rc, l0, l1, l2, hc));
-  }
-  C no3[3] = {Y::zero(), Y::zero(), Y::zero()}, nc3[3] = {Y::zero(), Y::zero(), Y::zero()};
-  for (int i = Ny - 1; i >= 0; --i) {
-    const size_t o = (size_t)i * M + m;
-    const R* Hi = H + (size_t)i * 11 * NC;
-    const R u0 = Hi[3 * NC], u1 = Hi[4 * NC], u2 = Hi[5 * NC], dinv = Hi[6 * NC];
-    Y::st(om, o, ybwd<Y>(Y::ld(scr, o), u0, u1, u2, dinv, no3));
-    Y::st(chi, o, ybwd<Y>(Y::ld(scr2, o), u0, u1, u2, dinv, nc3));
-  }
+  if (FS != 1)
+    helm_one<Y>(Ny, M, NC, m, sA, sB, H, om, Nom, Nom_p, Rom, scr_, prev, c1, cg, cz, ca, qp);
+  if (FS != 0)
+    helm_one<Y>(Ny, M, NC, m, sA, sB, H, chi, Nchi, Nchi_p, Rchi, scr_ + (size_t)Ny * M, prev, c1, cg, cz, ca, qp);
 }
 
+// One thread per (mode, field): blockIdx.y = 0 omega_2, 1 chi.
 template <class Y>
 __global__ void __launch_bounds__(128) k_helm(Geo g, YTabs t, const typename Y::R* __restrict__ helm,
                                               double2* om, double2* chi, const double2* __restrict__ Nchi,
                                               const double2* __restrict__ Nom, double2* Nchi_p, double2* Nom_p,
                                               double2* Rom, double2* Rchi, const double* __restrict__ scal,
                                               double2* scr, int s) {
-  helm_body<Y>(g, t, helm, om, chi, Nchi, Nom, Nchi_p, Nom_p, Rom, Rchi, scal, scr, s, blockIdx.x);
+  if (blockIdx.y == 0) helm_body<Y, 0>(g, t, helm, om, chi, Nchi, Nom, Nchi_p, Nom_p, Rom, Rchi, scal, scr, s, blockIdx.x);
+  else helm_body<Y, 1>(g, t, helm, om, chi, Nchi, Nom, Nchi_p, Nom_p, Rom, Rchi, scal, scr, s, blockIdx.x);
 }
 
 
@@ -1077,8 +1082,8 @@ __global__ void __launch_bounds__(128) kb_helm(YBatch<HelmP> B) {
   typedef typename Y::R R;
   const int r = batch_run(B.begin, B.n, blockIdx.x);
   const HelmP& p = B.p[r];
-  helm_body<Y>(p.g, p.t, static_cast<const R*>(p.helm), p.om, p.chi, p.Nchi, p.Nom, p.Nchi_p, p.Nom_p, p.Rom, p.Rchi,
-               p.scal, p.scr, p.s, blockIdx.x - B.begin[r]);
+  helm_body<Y, 2>(p.g, p.t, static_cast<const R*>(p.helm), p.om, p.chi, p.Nchi, p.Nom, p.Nchi_p, p.Nom_p, p.Rom,
+                  p.Rchi, p.scal, p.scr, p.s, blockIdx.x - B.begin[r]);
 }
 template <class Y>
 __global__ void __launch_bounds__(128) kb_poisson(YBatch<PoisP> B) {
@@ -1262,11 +1267,11 @@ cudaError_t launch_helm(chan_s* h, const double2* Nchi, const double2* Nom, int 
   cudaError_t e = smem_attr(fn, sm);
   if (e != cudaSuccess) return e;
   if (use_df(h))
-    k_helm<YDF><<<ygrid(h), kYThreads, sm, h->stream>>>(geo(h), ytabs(h), (const dfr*)helm_slot_y(h, s), h->om,
+    k_helm<YDF><<<dim3(ygrid(h).x, 2), kYThreads, sm, h->stream>>>(geo(h), ytabs(h), (const dfr*)helm_slot_y(h, s), h->om,
                                                         h->chi, Nchi, Nom, h->Nchi_p, h->Nom_p, h->Rom, h->Rchi,
                                                         h->scal, h->scr, s);
   else
-    k_helm<YF64><<<ygrid(h), kYThreads, sm, h->stream>>>(geo(h), ytabs(h), (const double*)helm_slot_y(h, s), h->om,
+    k_helm<YF64><<<dim3(ygrid(h).x, 2), kYThreads, sm, h->stream>>>(geo(h), ytabs(h), (const double*)helm_slot_y(h, s), h->om,
                                                          h->chi, Nchi, Nom, h->Nchi_p, h->Nom_p, h->Rom, h->Rchi,
                                                          h->scal, h->scr, s);
   return cudaGetLastError();
