@@ -291,6 +291,7 @@ struct ZArgs {
   int applyG[CHAN_MAXFIELDS];
   const double* G;
   int Ny, Nz, nxh, M, L3, KB, ld;
+  int lgKB;       // KB = 2^lgKB columns per CTA
   int pair_out;   // double-float mode: the forward pass writes (hi, lo) pairs
   int f32_mask;   // inverse pass: bit f set = field f is stored as float2 (mixed mode)
   FftPlan pl;
@@ -313,7 +314,7 @@ __device__ __forceinline__ void zinv_body(const ZArgs& A, const typename V2<T>::
   const double2* in = A.in[f] + (size_t)y * A.M;
   const float2* in32 = reinterpret_cast<const float2*>(A.in[f]) + (size_t)y * A.M;
   for (int e = threadIdx.x; e < A.Nz * A.KB; e += blockDim.x) {
-    const int jz = e / A.KB, kl = e - jz * A.KB, kx = kx0 + kl;
+    const int jz = e >> A.lgKB, kl = e & (A.KB - 1), kx = kx0 + kl;
     if (kx >= A.nxh || jz == hz) continue;
     const int q = jz * A.nxh + kx;
     const bool useg = A.applyG[f] != 0;
@@ -331,7 +332,7 @@ __device__ __forceinline__ void zinv_body(const ZArgs& A, const typename V2<T>::
   // physical rows leave in digit-reversed z order (slot = position in the column)
   T2* out = reinterpret_cast<T2*>(A.out[f]) + (size_t)y * A.L3 * A.nxh;
   for (int e = threadIdx.x; e < A.L3 * A.KB; e += blockDim.x) {
-    const int z = e / A.KB, kl = e - z * A.KB, kx = kx0 + kl;
+    const int z = e >> A.lgKB, kl = e & (A.KB - 1), kx = kx0 + kl;
     if (kx < A.nxh) out[(size_t)z * A.nxh + kx] = a[kl * A.ld + z];
   }
 }
@@ -353,7 +354,7 @@ __device__ __forceinline__ void zfwd_body(const ZArgs& A, const typename V2<T>::
   const int hz = A.Nz / 2;
   const T2* in = reinterpret_cast<const T2*>(A.out[f]) + (size_t)y * A.L3 * A.nxh;
   for (int e = threadIdx.x; e < A.L3 * A.KB; e += blockDim.x) {
-    const int z = e / A.KB, kl = e - z * A.KB, kx = kx0 + kl;
+    const int z = e >> A.lgKB, kl = e & (A.KB - 1), kx = kx0 + kl;
     a[kl * A.ld + z] = kx < A.nxh ? in[(size_t)z * A.nxh + kx] : zero2<T2>();
   }
   __syncthreads();
@@ -362,7 +363,7 @@ __device__ __forceinline__ void zfwd_body(const ZArgs& A, const typename V2<T>::
   const T2* r = a;
   double2* out = A.outd[f] + (size_t)y * A.M;
   for (int e = threadIdx.x; e < A.Nz * A.KB; e += blockDim.x) {
-    const int jz = e / A.KB, kl = e - jz * A.KB, kx = kx0 + kl;
+    const int jz = e >> A.lgKB, kl = e & (A.KB - 1), kx = kx0 + kl;
     if (kx >= A.nxh) continue;
     if (jz != hz) {
       const int pz = jz < hz ? jz : jz + (A.L3 - A.Nz);
@@ -384,6 +385,7 @@ struct XArgs {
   void* out[CHAN_MAXFIELDS];
   int nxh, L1, L3, ld;
   double scale;  // 1 / (L1 L3): analysis normalisation of the padded grid
+  unsigned mag_nxh;  // ceil(2^32 / nxh) for nxh >= 2 (exact below e nxh < 2^32), 0 for nxh = 1
   FftPlan pl;
 };
 
@@ -405,7 +407,7 @@ __device__ __forceinline__ void xpass_body(const XArgs& A, const typename V2<T>:
   __syncthreads();
   // pack rows z0 (real part) and z0+1 (imaginary part) with Hermitian extension in kx
   for (int e = threadIdx.x; e < NIN * nxh; e += blockDim.x) {
-    const int f = e / nxh, k = e - f * nxh;
+    const int f = A.mag_nxh ? (int)__umulhi((unsigned)e, A.mag_nxh) : e, k = e - f * nxh;   // e / nxh
     const T2* row = reinterpret_cast<const T2*>(A.in[f]) + ((size_t)y * A.L3 + z0) * nxh;
     T2 P = row[k], Q = row[nxh + k];
     T2* dstf = a + f * ld;
@@ -462,7 +464,7 @@ __device__ __forceinline__ void xpass_body(const XArgs& A, const typename V2<T>:
   const T2* s = a;
   const T half = from_d<T>(0.5 * A.scale);
   for (int e = threadIdx.x; e < NOUT * nxh; e += blockDim.x) {
-    const int gq = e / nxh, k = e - gq * nxh;
+    const int gq = A.mag_nxh ? (int)__umulhi((unsigned)e, A.mag_nxh) : e, k = e - gq * nxh;   // e / nxh
     const T2 c = s[gq * ld + k];
     const T2 cm = s[gq * ld + (k == 0 ? 0 : L1 - k)];
     T2 F, G;
@@ -555,6 +557,8 @@ static ZArgs zargs(chan_s* h, size_t es) {
   memset(&A, 0, sizeof(A));
   A.Ny = h->Ny; A.Nz = h->Nz; A.nxh = h->nxh; A.M = h->M; A.L3 = h->L3;
   A.KB = h->kb_z > 0 ? h->kb_z : pick_kb(h->nxh, h->L3, es);
+  A.lgKB = 0;
+  while ((1 << A.lgKB) < A.KB) ++A.lgKB;
   A.ld = h->L3 + 1;
   A.pl = h->p3;
   A.G = h->G;
@@ -598,6 +602,7 @@ cudaError_t launch_xpass(chan_s* h, int mode, void* const* in, void* const* out,
   for (int f = 0; f < nin; ++f) A.in[f] = in[f];
   for (int f = 0; f < nout; ++f) A.out[f] = out[f];
   A.nxh = h->nxh; A.L1 = h->L1; A.L3 = h->L3; A.ld = h->L1 + 1;
+  A.mag_nxh = h->nxh == 1 ? 0u : (unsigned)((((unsigned long long)1 << 32) + h->nxh - 1) / h->nxh);
   A.scale = 1.0 / ((double)h->L1 * (double)h->L3);
   A.pl = h->p1;
   dim3 grid(h->L3 / 2, ny);
@@ -697,6 +702,7 @@ cudaError_t launch_xpass_batch(chan_s* const* hs, int n, const BatchWork* w, cud
     for (int f = 0; f < 6; ++f) A.in[f] = w[r].mixed[f];
     for (int f = 0; f < 3; ++f) A.out[f] = w[r].mixed[f];
     A.nxh = h->nxh; A.L1 = h->L1; A.L3 = h->L3; A.ld = h->L1 + 1;
+  A.mag_nxh = h->nxh == 1 ? 0u : (unsigned)((((unsigned long long)1 << 32) + h->nxh - 1) / h->nxh);
     A.scale = 1.0 / ((double)h->L1 * (double)h->L3);
     A.pl = h->p1;
     B.a[r] = A;
