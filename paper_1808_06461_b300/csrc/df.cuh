@@ -54,3 +54,29 @@ __device__ __forceinline__ double load_re(const double2* p, size_t o, int pair) 
   const float2 q = reinterpret_cast<const float2*>(p)[2 * o];
   return (double)q.x + (double)q.y;
 }
+
+// FP32 <-> FP64 conversions on the integer pipe (the hardware conversions issue on the
+// FP64 pipe, the bottleneck of the mixed mode's sweeps).  f2d_int is exact for zero,
+// normal floats, infinities and NaNs, and flushes float subnormals to zero.  d2f_int
+// rounds the 52-bit mantissa to 23 bits, ties away from zero, for |x| in the float
+// normal range; smaller magnitudes flush to zero, larger ones (and NaN) give infinity.
+__device__ __forceinline__ double f2d_int(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned sign = u & 0x80000000u, ex = (u >> 23) & 0xffu, mant = u & 0x7fffffu;
+  unsigned hi = sign, lo = 0u;
+  if (ex != 0u) {
+    const unsigned e = ex == 255u ? 2047u : ex + 896u;
+    hi = sign | (e << 20) | (mant >> 3);
+    lo = mant << 29;
+  }
+  return __hiloint2double((int)hi, (int)lo);
+}
+__device__ __forceinline__ float d2f_int(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(b >> 32);
+  const int ex = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
+  const unsigned m = (unsigned)((b >> 29) & 0x7fffffu), rb = (unsigned)(b >> 28) & 1u;
+  unsigned r = ((unsigned)ex << 23) + m + rb;   // a carry out of the mantissa bumps the exponent
+  r = ex <= 0 ? 0u : (ex >= 255 ? 0x7f800000u : r);
+  return __uint_as_float((hi & 0x80000000u) | r);
+}

@@ -68,6 +68,11 @@ template <typename T2> __device__ __forceinline__ T2 ld_fourier(const double2* p
   if (useg) { v.x *= g; v.y *= g; }
   return mk<T2>(v.x, v.y);
 }
+template <> __device__ __forceinline__ float2 ld_fourier<float2>(const double2* p, size_t o, bool useg, double g) {
+  double2 v = p[o];
+  if (useg) { v.x *= g; v.y *= g; }
+  return make_float2(d2f_int(v.x), d2f_int(v.y));
+}
 template <> __device__ __forceinline__ dfc ld_fourier<dfc>(const double2* p, size_t o, bool useg, double g) {
   const float4 q = reinterpret_cast<const float4*>(p)[o];
   dfc v{dfr{q.x, q.y}, dfr{q.z, q.w}};
@@ -88,6 +93,10 @@ __device__ __forceinline__ float2 ld_fourier_f32(const float2* p, size_t o, bool
 template <typename T2> __device__ __forceinline__ void st_fourier(double2* p, size_t o, T2 x, int pair) {
   (void)pair;
   p[o] = make_double2(to_d(x.x), to_d(x.y));
+}
+template <> __device__ __forceinline__ void st_fourier<float2>(double2* p, size_t o, float2 x, int pair) {
+  (void)pair;
+  p[o] = make_double2(f2d_int(x.x), f2d_int(x.y));
 }
 template <> __device__ __forceinline__ void st_fourier<dfc>(double2* p, size_t o, dfc x, int pair) {
   if (pair) reinterpret_cast<float4*>(p)[o] = make_float4(x.x.h, x.x.l, x.y.h, x.y.l);

@@ -198,7 +198,7 @@ __device__ __forceinline__ ModeInfo mode_info(const Geo& g, int m) {
 // omega_3, which only feed the FP32 transforms, are formed in FP32 from the FP64
 // values and stored as float2: u_1, u_3 in the omega_1 slot ([2][Ny][M] float2),
 // omega_1, omega_3 in the omega_3 slot; the u_1, u_3 slots keep the forward sweep.
-__device__ __forceinline__ float2 tof(double2 x) { return make_float2((float)x.x, (float)x.y); }
+__device__ __forceinline__ float2 tof(double2 x) { return make_float2(d2f_int(x.x), d2f_int(x.y)); }
 
 template <class Y, bool F32OUT = false>
 __device__ __forceinline__ void pre_body(Geo g, YTabs t, const double2* __restrict__ v,
@@ -268,8 +268,8 @@ __device__ __forceinline__ void pre_body(Geo g, YTabs t, const double2* __restri
       const float2 fP = tof(Y::d(P)), fQ = tof(Y::d(Q));
       float2 a1, a3, d1, d3, fv = make_float2(0.f, 0.f);
       if (mean) {
-        a1 = make_float2((float)U1[i], 0.f);
-        a3 = make_float2((float)U3[i], 0.f);
+        a1 = make_float2(d2f_int(U1[i]), 0.f);
+        a3 = make_float2(d2f_int(U3[i]), 0.f);
         d1 = fP;
         d3 = fQ;
       } else {
