@@ -32,6 +32,17 @@ __device__ __forceinline__ dfr operator*(dfr a, dfr b) {
   return dfr{t, __fsub_rn(e, __fsub_rn(t, p))};
 }
 
+// Product left unnormalised, (p, e) with p = fl(a.h b.h) and e its FMA residual plus the
+// cross terms: the same value as a * b without the final fast two-sum, for products that
+// feed an addition straight away (the addition's two-sum takes the whole low part).
+__device__ __forceinline__ dfr mul_u(dfr a, dfr b) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = __fmaf_rn(a.h, b.h, -p);
+  e = __fmaf_rn(a.h, b.l, e);
+  e = __fmaf_rn(a.l, b.h, e);
+  return dfr{p, e};
+}
+
 // Split a double into the nearest float and the float nearest to the rest
 // (one FP64 subtraction; the conversions do not use the FP64 pipe).
 __device__ __forceinline__ dfr df_split(double x) {

@@ -103,10 +103,15 @@ template <> __device__ __forceinline__ void st_fourier<dfc>(double2* p, size_t o
   else p[o] = make_double2(to_d(x.x), to_d(x.y));
 }
 
+// A product that feeds an addition: plain for double and float, unnormalised pairs for dfr.
+__device__ __forceinline__ double mulu(double a, double b) { return a * b; }
+__device__ __forceinline__ float mulu(float a, float b) { return a * b; }
+__device__ __forceinline__ dfr mulu(dfr a, dfr b) { return mul_u(a, b); }
+
 template <typename T2> __device__ __forceinline__ T2 cmul(T2 a, T2 b) {
   T2 r;
-  r.x = a.x * b.x - a.y * b.y;
-  r.y = a.x * b.y + a.y * b.x;
+  r.x = mulu(a.x, b.x) - mulu(a.y, b.y);
+  r.y = mulu(a.x, b.y) + mulu(a.y, b.x);
   return r;
 }
 template <typename T2> __device__ __forceinline__ T2 cadd(T2 a, T2 b) { T2 r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
@@ -138,7 +143,7 @@ template <int DIR, typename T2> __device__ __forceinline__ void dft3(T2* v) {
   mm.y = v[0].y - half_of(s.y);
   // y1 = m + DIR * i * h * d, y2 = m - DIR * i * h * d
   T2 r;
-  if (DIR < 0) { r.x = h * d.y; r.y = -h * d.x; } else { r.x = -h * d.y; r.y = h * d.x; }
+  if (DIR < 0) { r.x = mulu(h, d.y); r.y = -mulu(h, d.x); } else { r.x = -mulu(h, d.y); r.y = mulu(h, d.x); }
   v[0] = y0;
   v[1] = cadd(mm, r);
   v[2] = csub(mm, r);
@@ -152,7 +157,7 @@ template <int DIR, typename T2> __device__ __forceinline__ void dft3_zmid(T2* v)
   mm.x = v[0].x - half_of(c.x);
   mm.y = v[0].y - half_of(c.y);
   T2 r;  // DIR * i * h * (v1 - v2) with v1 = 0
-  if (DIR < 0) { r.x = -h * c.y; r.y = h * c.x; } else { r.x = h * c.y; r.y = -h * c.x; }
+  if (DIR < 0) { r.x = -mulu(h, c.y); r.y = mulu(h, c.x); } else { r.x = mulu(h, c.y); r.y = -mulu(h, c.x); }
   v[0] = cadd(v[0], c);
   v[1] = cadd(mm, r);
   v[2] = csub(mm, r);
@@ -166,7 +171,7 @@ template <int DIR, typename T2> __device__ __forceinline__ void dft3_nomid(T2* v
   mm.x = v[0].x - half_of(s.x);
   mm.y = v[0].y - half_of(s.y);
   T2 r;
-  if (DIR < 0) { r.x = h * d.y; r.y = -h * d.x; } else { r.x = -h * d.y; r.y = h * d.x; }
+  if (DIR < 0) { r.x = mulu(h, d.y); r.y = -mulu(h, d.x); } else { r.x = -mulu(h, d.y); r.y = mulu(h, d.x); }
   v[0] = cadd(v[0], s);
   v[2] = csub(mm, r);
 }
@@ -445,9 +450,9 @@ __device__ __forceinline__ void xpass_body(const XArgs& A, const typename V2<T>:
     if (MODE == 0) {
       // H1 = u2 w3 - u3 w2, H2 = u3 w1 - u1 w3, H3 = u1 w2 - u2 w1 (both rows at once)
       T2 h1, h2, h3;
-      h1.x = q[1].x * q[5].x - q[2].x * q[4].x; h1.y = q[1].y * q[5].y - q[2].y * q[4].y;
-      h2.x = q[2].x * q[3].x - q[0].x * q[5].x; h2.y = q[2].y * q[3].y - q[0].y * q[5].y;
-      h3.x = q[0].x * q[4].x - q[1].x * q[3].x; h3.y = q[0].y * q[4].y - q[1].y * q[3].y;
+      h1.x = mulu(q[1].x, q[5].x) - mulu(q[2].x, q[4].x); h1.y = mulu(q[1].y, q[5].y) - mulu(q[2].y, q[4].y);
+      h2.x = mulu(q[2].x, q[3].x) - mulu(q[0].x, q[5].x); h2.y = mulu(q[2].y, q[3].y) - mulu(q[0].y, q[5].y);
+      h3.x = mulu(q[0].x, q[4].x) - mulu(q[1].x, q[3].x); h3.y = mulu(q[0].y, q[4].y) - mulu(q[1].y, q[3].y);
       o[0 * ld + x] = h1;
       o[1 * ld + x] = h2;
       o[2 * ld + x] = h3;

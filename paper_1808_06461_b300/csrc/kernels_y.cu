@@ -104,7 +104,7 @@ struct YDF {
   __device__ static __forceinline__ double2 d(C x) { return make_double2(df_merge(x.x), df_merge(x.y)); }
   __device__ static __forceinline__ C zero() { return dfc{dfr{0.f, 0.f}, dfr{0.f, 0.f}}; }
   __device__ static __forceinline__ C mk(R x, R y) { return dfc{x, y}; }
-  __device__ static __forceinline__ C axpy(R a, C x, C y) { return dfc{y.x + a * x.x, y.y + a * x.y}; }
+  __device__ static __forceinline__ C axpy(R a, C x, C y) { return dfc{y.x + mul_u(a, x.x), y.y + mul_u(a, x.y)}; }
   __device__ static __forceinline__ C scl(R a, C x) { return dfc{a * x.x, a * x.y}; }
   __device__ static __forceinline__ C sub(C a, C b) { return dfc{a.x - b.x, a.y - b.y}; }
   __device__ static __forceinline__ C itimes(C a) { return dfc{-a.y, a.x}; }
