@@ -32,6 +32,17 @@ __device__ __forceinline__ dfr operator*(dfr a, dfr b) {
   return dfr{t, __fsub_rn(e, __fsub_rn(t, p))};
 }
 
+// Sum left unnormalised: Knuth's two-sum of the high parts (exact) plus both low parts,
+// without the final fast two-sum.  For sums that feed another addition or product
+// straight away; the value is the one a + b represents before its renormalisation.
+__device__ __forceinline__ dfr add_u(dfr a, dfr b) {
+  const float s = __fadd_rn(a.h, b.h);
+  const float bb = __fsub_rn(s, a.h);
+  float e = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, bb)), __fsub_rn(b.h, bb));
+  e = __fadd_rn(e, __fadd_rn(a.l, b.l));
+  return dfr{s, e};
+}
+
 // Product left unnormalised, (p, e) with p = fl(a.h b.h) and e its FMA residual plus the
 // cross terms: the same value as a * b without the final fast two-sum, for products that
 // feed an addition straight away (the addition's two-sum takes the whole low part).

@@ -108,14 +108,22 @@ __device__ __forceinline__ double mulu(double a, double b) { return a * b; }
 __device__ __forceinline__ float mulu(float a, float b) { return a * b; }
 __device__ __forceinline__ dfr mulu(dfr a, dfr b) { return mul_u(a, b); }
 
-template <typename T2> __device__ __forceinline__ T2 cmul(T2 a, T2 b) {
+// A sum that feeds another operation inside the butterfly: plain, or unnormalised pairs.
+__device__ __forceinline__ double addu(double a, double b) { return a + b; }
+__device__ __forceinline__ float addu(float a, float b) { return a + b; }
+__device__ __forceinline__ dfr addu(dfr a, dfr b) { return add_u(a, b); }
+
+template <typename T2> __device__ __forceinline__ T2 cmul(T2 a, T2 b) {   // feeds the butterfly
   T2 r;
-  r.x = mulu(a.x, b.x) - mulu(a.y, b.y);
-  r.y = mulu(a.x, b.y) + mulu(a.y, b.x);
+  r.x = addu(mulu(a.x, b.x), -mulu(a.y, b.y));
+  r.y = addu(mulu(a.x, b.y), mulu(a.y, b.x));
   return r;
 }
 template <typename T2> __device__ __forceinline__ T2 cadd(T2 a, T2 b) { T2 r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
 template <typename T2> __device__ __forceinline__ T2 csub(T2 a, T2 b) { T2 r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
+// inner sums of a butterfly (the outputs are formed with cadd / csub)
+template <typename T2> __device__ __forceinline__ T2 caddu(T2 a, T2 b) { T2 r; r.x = addu(a.x, b.x); r.y = addu(a.y, b.y); return r; }
+template <typename T2> __device__ __forceinline__ T2 csubu(T2 a, T2 b) { T2 r; r.x = addu(a.x, -b.x); r.y = addu(a.y, -b.y); return r; }
 
 // Radix-R DFT in registers.  DIR = -1: exp(-2 pi i jk/R) (forward); +1: inverse.
 template <int DIR, typename T2> __device__ __forceinline__ void dft2(T2* v) {
@@ -124,8 +132,8 @@ template <int DIR, typename T2> __device__ __forceinline__ void dft2(T2* v) {
   v[1] = csub(a, b);
 }
 template <int DIR, typename T2> __device__ __forceinline__ void dft4(T2* v) {
-  T2 t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
-  T2 t2 = cadd(v[1], v[3]), d = csub(v[1], v[3]);
+  T2 t0 = caddu(v[0], v[2]), t1 = csubu(v[0], v[2]);
+  T2 t2 = caddu(v[1], v[3]), d = csubu(v[1], v[3]);
   T2 t3;  // DIR * i * d
   if (DIR < 0) { t3.x = d.y; t3.y = -d.x; } else { t3.x = -d.y; t3.y = d.x; }
   v[0] = cadd(t0, t2);
@@ -136,11 +144,11 @@ template <int DIR, typename T2> __device__ __forceinline__ void dft4(T2* v) {
 template <int DIR, typename T2> __device__ __forceinline__ void dft3(T2* v) {
   typedef typename Scal<T2>::t T;
   const T h = sqrt3_2<T>();
-  T2 s = cadd(v[1], v[2]), d = csub(v[1], v[2]);
+  T2 s = caddu(v[1], v[2]), d = csubu(v[1], v[2]);
   T2 y0 = cadd(v[0], s);
   T2 mm;
-  mm.x = v[0].x - half_of(s.x);
-  mm.y = v[0].y - half_of(s.y);
+  mm.x = addu(v[0].x, -half_of(s.x));
+  mm.y = addu(v[0].y, -half_of(s.y));
   // y1 = m + DIR * i * h * d, y2 = m - DIR * i * h * d
   T2 r;
   if (DIR < 0) { r.x = mulu(h, d.y); r.y = -mulu(h, d.x); } else { r.x = -mulu(h, d.y); r.y = mulu(h, d.x); }
@@ -154,8 +162,8 @@ template <int DIR, typename T2> __device__ __forceinline__ void dft3_zmid(T2* v)
   const T h = sqrt3_2<T>();
   T2 c = v[2];
   T2 mm;
-  mm.x = v[0].x - half_of(c.x);
-  mm.y = v[0].y - half_of(c.y);
+  mm.x = addu(v[0].x, -half_of(c.x));
+  mm.y = addu(v[0].y, -half_of(c.y));
   T2 r;  // DIR * i * h * (v1 - v2) with v1 = 0
   if (DIR < 0) { r.x = -mulu(h, c.y); r.y = mulu(h, c.x); } else { r.x = mulu(h, c.y); r.y = -mulu(h, c.x); }
   v[0] = cadd(v[0], c);
@@ -166,10 +174,10 @@ template <int DIR, typename T2> __device__ __forceinline__ void dft3_zmid(T2* v)
 template <int DIR, typename T2> __device__ __forceinline__ void dft3_nomid(T2* v) {
   typedef typename Scal<T2>::t T;
   const T h = sqrt3_2<T>();
-  T2 s = cadd(v[1], v[2]), d = csub(v[1], v[2]);
+  T2 s = caddu(v[1], v[2]), d = csubu(v[1], v[2]);
   T2 mm;
-  mm.x = v[0].x - half_of(s.x);
-  mm.y = v[0].y - half_of(s.y);
+  mm.x = addu(v[0].x, -half_of(s.x));
+  mm.y = addu(v[0].y, -half_of(s.y));
   T2 r;
   if (DIR < 0) { r.x = mulu(h, d.y); r.y = -mulu(h, d.x); } else { r.x = -mulu(h, d.y); r.y = mulu(h, d.x); }
   v[0] = cadd(v[0], s);
