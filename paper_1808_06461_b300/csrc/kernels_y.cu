@@ -606,8 +606,13 @@ __device__ __forceinline__ void mean_body(Geo g, YTabs t, const double* __restri
   double* r1 = sm;            // right-hand sides, then the solutions
   double* r3 = sm + Ny;
   double* red = sm + 2 * Ny;  // [256]
+  double* sH = red + 256;     // [Ny][7] the k = 0 factors, staged by all threads for the serial sweeps
   const double gm = c_rk3[s][0], zt = c_rk3[s][1], al = c_rk3[s][2], be = c_rk3[s][3];
   const double dt = g.dt, nu = g.nu;
+  for (int k = threadIdx.x; k < 7 * Ny; k += blockDim.x) {
+    const int i = k / 7, q = k - 7 * i;
+    sH[k] = helm[((size_t)i * 11 + q) * C];
+  }
   for (int i = threadIdx.x; i < Ny; i += blockDim.x) {
     double a1 = 0.0, a3 = 0.0;
     if (i > 0 && i < Ny - 1) {
@@ -624,20 +629,19 @@ __device__ __forceinline__ void mean_body(Geo g, YTabs t, const double* __restri
     r3[i] = a3;
   }
   __syncthreads();
-  const double* H = helm;  // the substep's slot, class 0: k = 0
   if ((threadIdx.x & 31) == 0 && threadIdx.x < 64) {
     double* r = threadIdx.x == 0 ? r1 : r3;
     double h[3] = {0, 0, 0};
     for (int i = 0; i < Ny; ++i) {
-      const double* Hi = H + (size_t)i * 11 * C;
-      double x = r[i] - Hi[0] * h[0] - Hi[C] * h[1] - Hi[2 * C] * h[2];
+      const double* Hi = sH + 7 * i;
+      double x = r[i] - Hi[0] * h[0] - Hi[1] * h[1] - Hi[2] * h[2];
       h[0] = h[1]; h[1] = h[2]; h[2] = x;
       r[i] = x;
     }
     double nx[3] = {0, 0, 0};
     for (int i = Ny - 1; i >= 0; --i) {
-      const double* Hi = H + (size_t)i * 11 * C;
-      double x = (r[i] - Hi[3 * C] * nx[0] - Hi[4 * C] * nx[1] - Hi[5 * C] * nx[2]) * Hi[6 * C];
+      const double* Hi = sH + 7 * i;
+      double x = (r[i] - Hi[3] * nx[0] - Hi[4] * nx[1] - Hi[5] * nx[2]) * Hi[6];
       nx[2] = nx[1]; nx[1] = nx[0]; nx[0] = x;
       r[i] = x;
     }
@@ -1294,7 +1298,7 @@ cudaError_t launch_poisson(chan_s* h, int s) {
 }
 
 cudaError_t launch_mean(chan_s* h, const double2* H1, const double2* H3, int s) {
-  size_t sm = sizeof(double) * (2 * h->Ny + 256);
+  size_t sm = sizeof(double) * (9 * h->Ny + 256);
   cudaError_t e = smem_attr((const void*)k_mean, sm);
   if (e != cudaSuccess) return e;
   k_mean<<<1, 256, sm, h->stream>>>(geo(h), ytabs(h), helm_slot(h, s), h->meanh, H1, H3, h->U1, h->U3, h->H1m_p,
@@ -1401,7 +1405,7 @@ cudaError_t launch_mean_batch(chan_s* const* hs, int n, const BatchWork* w, cuda
     B.p[r] = MeanP{geo(h), ytabs(h), helm_slot(h, (int)(h->nsub % 3)), h->meanh, w[r].H1, w[r].H3, h->U1, h->U3, h->H1m_p, h->H3m_p,
                    h->scal, (int)(h->nsub % 3)};
   }
-  const size_t sm = sizeof(double) * (2 * max_ny(hs, n) + 256);
+  const size_t sm = sizeof(double) * (9 * max_ny(hs, n) + 256);
   cudaError_t e = smem_attr((const void*)kb_mean, sm);
   if (e != cudaSuccess) return e;
   kb_mean<<<n, 256, sm, st>>>(B);
