@@ -94,8 +94,8 @@ def fft_flops(L, pruned=True):
 # DRAM bytes per wall-normal plane of each kernel launch, from ncu on the 384 x 33 x 384
 # profiling case (profiles/*_re550_384x33x384.md: dram__bytes_read.sum + dram__bytes_write.sum
 # divided by 33); valid for Nx = Nz = 384 only and only while the kernels are as captured.
-NCU_BYTES_PER_PLANE = {("k_xpass", "fp64"): (350.394624e6 + 131.588608e6) / 33}
-NCU_PIPE = {("k_xpass", "fp64"): ("fp64", 0.8574)}
+NCU_BYTES_PER_PLANE = {("k_xpass", "fp64"): (351.300352e6 + 131.277568e6) / 33}
+NCU_PIPE = {("k_xpass", "fp64"): ("fp64", 0.8597)}
 
 
 # per mode-point flops of the wall-normal kernels (read off their sweeps)
