@@ -16,7 +16,7 @@ CU = ["chan_api.cu", "kernels_y.cu", "kernels_fft.cu", "kernels_misc.cu", "noall
 CPP = ["setup_host.cpp"]
 HEADERS = ["chan_internal.cuh", "chan_host.h", "df.cuh"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
-              "-Xcompiler", "-fPIC", "-diag-suppress", "177"]
+              "-Xcompiler", "-fPIC"]
 
 
 def _nvcc():

@@ -26,8 +26,6 @@ __device__ __forceinline__ double2 axpy(double a, double2 x, double2 y) {  // y 
 }
 __device__ __forceinline__ double2 scl(double a, double2 x) { return make_double2(a * x.x, a * x.y); }
 __device__ __forceinline__ double2 sub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ double2 add(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ double2 itimes(double2 a) { return make_double2(-a.y, a.x); }  // i a
 
 template <int N>
 __device__ __forceinline__ void push(double2 (&w)[N], double2 x) {
@@ -81,7 +79,6 @@ struct YF64 {
   __device__ static __forceinline__ C c(double2 x) { return x; }
   __device__ static __forceinline__ double2 d(C x) { return x; }
   __device__ static __forceinline__ C zero() { return make_double2(0.0, 0.0); }
-  __device__ static __forceinline__ C mk(R x, R y) { return make_double2(x, y); }
   __device__ static __forceinline__ C axpy(R a, C x, C y) { return make_double2(fma(a, x.x, y.x), fma(a, x.y, y.y)); }
   __device__ static __forceinline__ C scl(R a, C x) { return make_double2(a * x.x, a * x.y); }
   __device__ static __forceinline__ C sub(C a, C b) { return make_double2(a.x - b.x, a.y - b.y); }
@@ -101,9 +98,7 @@ struct YDF {
   typedef dfc C;
   __device__ static __forceinline__ R r(double x) { return df_split(x); }
   __device__ static __forceinline__ C c(double2 x) { return dfc{df_split(x.x), df_split(x.y)}; }
-  __device__ static __forceinline__ double2 d(C x) { return make_double2(df_merge(x.x), df_merge(x.y)); }
   __device__ static __forceinline__ C zero() { return dfc{dfr{0.f, 0.f}, dfr{0.f, 0.f}}; }
-  __device__ static __forceinline__ C mk(R x, R y) { return dfc{x, y}; }
   __device__ static __forceinline__ C axpy(R a, C x, C y) { return dfc{y.x + mul_u(a, x.x), y.y + mul_u(a, x.y)}; }
   __device__ static __forceinline__ C scl(R a, C x) { return dfc{a * x.x, a * x.y}; }
   __device__ static __forceinline__ C sub(C a, C b) { return dfc{a.x - b.x, a.y - b.y}; }
