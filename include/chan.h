@@ -177,6 +177,22 @@ int chan_get_state(chan_t h, double* v, double* omega2, double* U1, double* U3);
 int chan_get_state_device(chan_t h, void* v, void* omega2, void* U1, void* U3);
 
 /*
+ * Checkpoint and restart (no paper counterpart; the paper restarts its runs from
+ * stored full fields, Sec. 3).  A checkpoint holds everything the next substep
+ * reads: v, omega_2, chi, dv/dy, the previous non-linear terms and implicit
+ * right-hand sides, U_1, U_3 and their previous <H>, the flux target, the RK3
+ * phase and time, in the handle's storage format, so a run restarted from it
+ * continues bitwise as the original would (a state upload re-derives chi and
+ * starts a fresh RK3 step instead).  chan_checkpoint_bytes gives the size;
+ * _save copies it into the caller's host buffer (synchronises); _load checks that
+ * the buffer was written by a handle of the same box, grid, time step and
+ * precision (CHAN_EINVAL otherwise) and installs it.
+ */
+size_t chan_checkpoint_bytes(chan_t h);
+int chan_checkpoint_save(chan_t h, void* buf);
+int chan_checkpoint_load(chan_t h, const void* buf);
+
+/*
  * Advance nsub RK3 substeps (Appendix A, Eqs. (chi1), (chi2), (psi); order of
  * operations of Appendix C): u_1, u_3 and their y-derivatives from
  * (v, omega_2); vorticity; dealiased H = u x omega; N_chi and N_omega2

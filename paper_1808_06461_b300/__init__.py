@@ -32,7 +32,8 @@ SYMBOLS = ("chan_opts_default", "chan_init", "chan_init_ex", "chan_free", "chan_
            "chan_rhs_terms", "chan_rhs_terms_noalloc", "chan_footprint_bytes", "chan_set_graph",
            "chan_filtered_enstrophy", "chan_batch_create", "chan_batch_step", "chan_batch_last_error",
            "chan_batch_free", "chan_autotune", "chan_tuned_shape", "chan_database_record",
-           "chan_spectra", "chan_optimize_mesh", "chan_filtered_pressure")
+           "chan_spectra", "chan_optimize_mesh", "chan_filtered_pressure", "chan_checkpoint_bytes",
+           "chan_checkpoint_save", "chan_checkpoint_load")
 CHAN_NKERNELS = 16
 
 
@@ -71,6 +72,9 @@ def load_library(path=LIB_PATH):
         "chan_set_state_device": (I, [P, P, P, P, P]),
         "chan_get_state": (I, [P, P, P, P, P]),
         "chan_get_state_device": (I, [P, P, P, P, P]),
+        "chan_checkpoint_bytes": (ctypes.c_size_t, [P]),
+        "chan_checkpoint_save": (I, [P, P]),
+        "chan_checkpoint_load": (I, [P, P]),
         "chan_step": (I, [P, I]),
         "chan_filter_stresses": (I, [P, I, D, D, P, P]),
         "chan_stats": (I, [P, P, DP, DP, DP]),
@@ -229,6 +233,20 @@ class Channel:
         _check(self.h, _lib.chan_get_state(self.h, _ptr(out["v"]), _ptr(out["omega2"]), _ptr(out["U1"]),
                                            _ptr(out["U3"])))
         return out
+
+    def checkpoint(self, out=None):
+        """Everything the next substep reads, as bytes (a uint8 array; ``out`` to fill one)."""
+        n = int(_lib.chan_checkpoint_bytes(self.h))
+        buf = np.empty(n, dtype=np.uint8) if out is None else out
+        if buf.nbytes < n or buf.dtype != np.uint8 or not buf.flags.c_contiguous:
+            raise ValueError("checkpoint buffer must be a C-contiguous uint8 array of at least %d bytes" % n)
+        _check(self.h, _lib.chan_checkpoint_save(self.h, buf.ctypes.data_as(ctypes.c_void_p)))
+        return buf
+
+    def restore(self, buf):
+        """Continue from a checkpoint of a handle with the same box, grid, dt and precision."""
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        _check(self.h, _lib.chan_checkpoint_load(self.h, buf.ctypes.data_as(ctypes.c_void_p)))
 
     def get_state_device(self, v, omega2, U1, U3):
         _check(self.h, _lib.chan_get_state_device(self.h, _ptr(v), _ptr(omega2), _ptr(U1), _ptr(U3)))
