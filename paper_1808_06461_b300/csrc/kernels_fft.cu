@@ -82,12 +82,6 @@ template <> __device__ __forceinline__ dfc ld_fourier<dfc>(const double2* p, siz
   }
   return v;
 }
-// A Fourier value stored as float2 (the mixed mode's transform inputs), times g.
-__device__ __forceinline__ float2 ld_fourier_f32(const float2* p, size_t o, bool useg, double g) {
-  float2 v = p[o];
-  if (useg) { const float gg = (float)g; v.x *= gg; v.y *= gg; }
-  return v;
-}
 // Store a transform value as a Fourier value: FP64, or (pair) the raw (hi, lo) pairs.
 template <typename T2> __device__ __forceinline__ void st_fourier(double2* p, size_t o, T2 x, int pair) {
   (void)pair;
@@ -321,6 +315,23 @@ struct ZArgs {
 // Inverse z-pass: Fourier [Ny][Nz][nxh] (double) -> mixed [Ny][L3][nxh] (T),
 // kz zero-padded to 3Nz/2 (the kz Nyquist row is dropped), optional filter
 // transfer G applied on load.
+// Load a column chunk of one Fourier field into the padded transform buffer.  KIND 0: stored
+// as the state is stored; 1: times the filter transfer G; 2: stored as float2 (mixed mode).
+template <typename T2, int KIND>
+__device__ __forceinline__ void zinv_load(const ZArgs& A, T2* a, const double2* in, const float2* in32, int kx0, int hz) {
+  for (int e = threadIdx.x; e < A.Nz * A.KB; e += blockDim.x) {
+    const int jz = e >> A.lgKB, kl = e & (A.KB - 1), kx = kx0 + kl;
+    if (kx >= A.nxh || jz == hz) continue;
+    const int q = jz * A.nxh + kx;
+    const int pz = jz < hz ? jz : jz + (A.L3 - A.Nz);
+    if constexpr (KIND == 2) {
+      if constexpr (std::is_same<T2, float2>::value) a[kl * A.ld + pz] = in32[q];
+    } else {
+      a[kl * A.ld + pz] = ld_fourier<T2>(in, q, KIND == 1, KIND == 1 ? A.G[q] : 0.0);
+    }
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ void zinv_body(const ZArgs& A, const typename V2<T>::t* __restrict__ tw, int bx, int by,
                                           int bz) {
@@ -334,19 +345,10 @@ __device__ __forceinline__ void zinv_body(const ZArgs& A, const typename V2<T>::
   const bool f32 = (A.f32_mask >> f) & 1;
   const double2* in = A.in[f] + (size_t)y * A.M;
   const float2* in32 = reinterpret_cast<const float2*>(A.in[f]) + (size_t)y * A.M;
-  for (int e = threadIdx.x; e < A.Nz * A.KB; e += blockDim.x) {
-    const int jz = e >> A.lgKB, kl = e & (A.KB - 1), kx = kx0 + kl;
-    if (kx >= A.nxh || jz == hz) continue;
-    const int q = jz * A.nxh + kx;
-    const bool useg = A.applyG[f] != 0;
-    const int pz = jz < hz ? jz : jz + (A.L3 - A.Nz);
-    if constexpr (std::is_same<T2, float2>::value) {
-      a[kl * A.ld + pz] = f32 ? ld_fourier_f32(in32, q, useg, useg ? A.G[q] : 0.0)
-                              : ld_fourier<T2>(in, q, useg, useg ? A.G[q] : 0.0);
-    } else {
-      a[kl * A.ld + pz] = ld_fourier<T2>(in, q, useg, useg ? A.G[q] : 0.0);
-    }
-  }
+  // one loop per input kind, so that no branch of another kind is issued (predicated) per element
+  if (f32) zinv_load<T2, 2>(A, a, in, in32, kx0, hz);   // (float2 inputs are never filtered)
+  else if (A.applyG[f]) zinv_load<T2, 1>(A, a, in, in32, kx0, hz);
+  else zinv_load<T2, 0>(A, a, in, in32, kx0, hz);
   __syncthreads();
   // the middle third of the padded column is zero: pruned first stage
   fft_dif<+1>(a, A.L3, A.KB, A.ld, tw, A.pl, true);
@@ -354,7 +356,7 @@ __device__ __forceinline__ void zinv_body(const ZArgs& A, const typename V2<T>::
   T2* out = reinterpret_cast<T2*>(A.out[f]) + (size_t)y * A.L3 * A.nxh;
   for (int e = threadIdx.x; e < A.L3 * A.KB; e += blockDim.x) {
     const int z = e >> A.lgKB, kl = e & (A.KB - 1), kx = kx0 + kl;
-    if (kx < A.nxh) out[(size_t)z * A.nxh + kx] = a[kl * A.ld + z];
+    if (kx < A.nxh) out[z * A.nxh + kx] = a[kl * A.ld + z];   // 32-bit index within the plane
   }
 }
 
@@ -365,6 +367,20 @@ __global__ void __launch_bounds__(256) k_zinv(ZArgs A, const typename V2<T>::t* 
 
 
 // Forward z-pass: mixed (T) -> Fourier (double), truncation to the stored kz.
+template <typename T2, int PAIR>
+__device__ __forceinline__ void zfwd_store(const ZArgs& A, const T2* r, double2* out, int kx0, int hz) {
+  for (int e = threadIdx.x; e < A.Nz * A.KB; e += blockDim.x) {
+    const int jz = e >> A.lgKB, kl = e & (A.KB - 1), kx = kx0 + kl;
+    if (kx >= A.nxh) continue;
+    if (jz != hz) {
+      const int pz = jz < hz ? jz : jz + (A.L3 - A.Nz);
+      st_fourier<T2>(out, jz * A.nxh + kx, r[kl * A.ld + pz], PAIR);
+    } else {
+      out[jz * A.nxh + kx] = make_double2(0.0, 0.0);
+    }
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ void zfwd_body(const ZArgs& A, const typename V2<T>::t* __restrict__ tw, int bx, int by,
                                           int bz) {
@@ -376,23 +392,14 @@ __device__ __forceinline__ void zfwd_body(const ZArgs& A, const typename V2<T>::
   const T2* in = reinterpret_cast<const T2*>(A.out[f]) + (size_t)y * A.L3 * A.nxh;
   for (int e = threadIdx.x; e < A.L3 * A.KB; e += blockDim.x) {
     const int z = e >> A.lgKB, kl = e & (A.KB - 1), kx = kx0 + kl;
-    a[kl * A.ld + z] = kx < A.nxh ? in[(size_t)z * A.nxh + kx] : zero2<T2>();
+    a[kl * A.ld + z] = kx < A.nxh ? in[z * A.nxh + kx] : zero2<T2>();
   }
   __syncthreads();
   // digit-reversed rows in, natural kz out; the middle third (truncated) is not formed
   fft_dit<-1>(a, A.L3, A.KB, A.ld, tw, A.pl, true);
-  const T2* r = a;
   double2* out = A.outd[f] + (size_t)y * A.M;
-  for (int e = threadIdx.x; e < A.Nz * A.KB; e += blockDim.x) {
-    const int jz = e >> A.lgKB, kl = e & (A.KB - 1), kx = kx0 + kl;
-    if (kx >= A.nxh) continue;
-    if (jz != hz) {
-      const int pz = jz < hz ? jz : jz + (A.L3 - A.Nz);
-      st_fourier<T2>(out, jz * A.nxh + kx, r[kl * A.ld + pz], A.pair_out);
-    } else {
-      out[jz * A.nxh + kx] = make_double2(0.0, 0.0);
-    }
-  }
+  if (A.pair_out) zfwd_store<T2, 1>(A, a, out, kx0, hz);   // one store loop per output form
+  else zfwd_store<T2, 0>(A, a, out, kx0, hz);
 }
 
 template <typename T>
@@ -423,12 +430,13 @@ __device__ __forceinline__ void xpass_body(const XArgs& A, const typename V2<T>:
   T2* a = reinterpret_cast<T2*>(smraw);
   const int z0 = 2 * bx, y = by;
   const int L1 = A.L1, nxh = A.nxh, ld = A.ld;
+  const size_t rowoff = ((size_t)y * A.L3 + z0) * nxh;   // rows z0, z0 + 1 of plane y
   for (int e = threadIdx.x; e < NIN * ld; e += blockDim.x) a[e] = zero2<T2>();
   __syncthreads();
   // pack rows z0 (real part) and z0+1 (imaginary part) with Hermitian extension in kx
   for (int e = threadIdx.x; e < NIN * nxh; e += blockDim.x) {
     const int f = A.mag_nxh ? (int)__umulhi((unsigned)e, A.mag_nxh) : e, k = e - f * nxh;   // e / nxh
-    const T2* row = reinterpret_cast<const T2*>(A.in[f]) + ((size_t)y * A.L3 + z0) * nxh;
+    const T2* row = reinterpret_cast<const T2*>(A.in[f]) + rowoff;
     T2 P = row[k], Q = row[nxh + k];
     T2* dstf = a + f * ld;
     if (k == 0) {
@@ -490,7 +498,7 @@ __device__ __forceinline__ void xpass_body(const XArgs& A, const typename V2<T>:
     T2 F, G;
     F.x = half * (c.x + cm.x); F.y = half * (c.y - cm.y);      // (C_k + conj C_-k) / 2
     G.x = half * (c.y + cm.y); G.y = -half * (c.x - cm.x);     // (C_k - conj C_-k) / 2i
-    T2* row = reinterpret_cast<T2*>(A.out[gq]) + ((size_t)y * A.L3 + z0) * nxh;
+    T2* row = reinterpret_cast<T2*>(A.out[gq]) + rowoff;
     row[k] = F;
     row[nxh + k] = G;
   }

@@ -390,11 +390,11 @@ __global__ void __launch_bounds__(128) k_nonlin_df(Geo g, YTabs t, const double2
 // The first substep after a state upload (flag scal[2] = 0) uses B X directly.
 // ---------------------------------------------------------------------------
 // One field (omega_2 or chi) of one mode: right-hand side, forward and backward sweeps.
-template <class Y>
+template <class Y, bool PREV>
 __device__ __forceinline__ void helm_one(int Ny, size_t M, size_t NC, int m, const typename Y::R* sA,
                                          const typename Y::R* sB, const typename Y::R* __restrict__ H, double2* X,
                                          const double2* __restrict__ N, double2* Np, double2* Rf, double2* scr,
-                                         bool prev, typename Y::R c1, typename Y::R cg, typename Y::R cz,
+                                         typename Y::R c1, typename Y::R cg, typename Y::R cz,
                                          typename Y::R ca, typename Y::R qp) {
   typedef typename Y::R R;
   typedef typename Y::C C;
@@ -419,8 +419,8 @@ __device__ __forceinline__ void helm_one(int Ny, size_t M, size_t NC, int m, con
     C r = Y::zero();
     if (i > 0 && i < Ny - 1) {
       const size_t oi = (size_t)i * M + m;
-      r = prev ? Y::axpy(qp, Y::ld(Rf, oi), yband7<Y>(sA + 7 * i, wa))
-               : Y::axpy(ca, yband7<Y>(sB + 7 * i, wx), yband7<Y>(sA + 7 * i, wa));
+      if constexpr (PREV) r = Y::axpy(qp, Y::ld(Rf, oi), yband7<Y>(sA + 7 * i, wa));
+      else r = Y::axpy(ca, yband7<Y>(sB + 7 * i, wx), yband7<Y>(sA + 7 * i, wa));
       Y::st(Rf, oi, r);
     }
     const R* Hi = H + (size_t)i * 11 * NC;
@@ -469,10 +469,15 @@ __device__ __forceinline__ void helm_body(Geo g, YTabs t, const typename Y::R* _
   const R c1 = Y::r(prev ? 1.0 + al / bp : 1.0 - al * dt * nu * mi.k2), cg = Y::r(dt * gm), cz = Y::r(dt * zt);
   const R ca = Y::r(al * dt * nu), qp = Y::r(-al / bp);
   const R* H = helm + mi.c;   // the substep's slot
-  if (FS != 1)
-    helm_one<Y>(Ny, M, NC, m, sA, sB, H, om, Nom, Nom_p, Rom, scr_, prev, c1, cg, cz, ca, qp);
-  if (FS != 0)
-    helm_one<Y>(Ny, M, NC, m, sA, sB, H, chi, Nchi, Nchi_p, Rchi, scr_ + (size_t)Ny * M, prev, c1, cg, cz, ca, qp);
+  // separate instantiations: the B product of the first substep is not issued under a predicate
+  double2* scr2 = scr_ + (size_t)Ny * M;
+  if (prev) {
+    if (FS != 1) helm_one<Y, true>(Ny, M, NC, m, sA, sB, H, om, Nom, Nom_p, Rom, scr_, c1, cg, cz, ca, qp);
+    if (FS != 0) helm_one<Y, true>(Ny, M, NC, m, sA, sB, H, chi, Nchi, Nchi_p, Rchi, scr2, c1, cg, cz, ca, qp);
+  } else {
+    if (FS != 1) helm_one<Y, false>(Ny, M, NC, m, sA, sB, H, om, Nom, Nom_p, Rom, scr_, c1, cg, cz, ca, qp);
+    if (FS != 0) helm_one<Y, false>(Ny, M, NC, m, sA, sB, H, chi, Nchi, Nchi_p, Rchi, scr2, c1, cg, cz, ca, qp);
+  }
 }
 
 // One thread per (mode, field): blockIdx.y = 0 omega_2, 1 chi.
