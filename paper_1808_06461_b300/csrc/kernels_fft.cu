@@ -193,10 +193,14 @@ template <int DIR, typename T2> __device__ __forceinline__ void dft3_nomid(T2* v
 
 // DIF stage of radix R on blocks of size Ls: butterfly j of block b reads
 // x[b Ls + j + r m] (m = Ls/R), forms y_q = sum_r x_r w_R^(DIR r q), scales
-// y_q by w_Ls^(DIR q j) and writes it back to slot q.
-template <int R, int DIR, bool ZMID, typename T2>
-__device__ __forceinline__ void dif_stage(T2* a, int L, int nb, int ld, const T2* __restrict__ tw, int Ls,
-                                          unsigned mag_nbf, unsigned mag_m) {
+// y_q by w_Ls^(DIR q j) and writes it back to slot q.  TW = false is the stage
+// with m = 1 (every j is 0).  With m > 1 the butterflies with j = 0 multiply by
+// tw[0] = 1 (exact) rather than branch: a warp holding one of them would run the
+// twiddles for the others anyway, and the compiler predicates a short branch,
+// which still takes FP64 issue slots.
+template <int R, int DIR, bool ZMID, bool TW, typename T2>
+__device__ __forceinline__ void dif_loop(T2* a, int L, int nb, int ld, const T2* __restrict__ tw, int Ls,
+                                         unsigned mag_nbf, unsigned mag_m) {
   const int m = Ls / R;
   const int nbf = L / R;
   const int tmul = L / Ls;
@@ -204,7 +208,7 @@ __device__ __forceinline__ void dif_stage(T2* a, int L, int nb, int ld, const T2
   for (int t = threadIdx.x; t < total; t += blockDim.x) {
     const int bi = mag_nbf ? (int)__umulhi((unsigned)t, mag_nbf) : t;   // t / nbf (exact while t nbf < 2^32)
     const int u = t - bi * nbf;
-    const int blk = mag_m ? (int)__umulhi((unsigned)u, mag_m) : u;   // u / m (mag 0: m = 1)
+    const int blk = TW ? (int)__umulhi((unsigned)u, mag_m) : u;   // u / m
     const int j = u - blk * m;
     T2* x = a + bi * ld + blk * Ls + j;
     T2 v[R];
@@ -214,7 +218,7 @@ __device__ __forceinline__ void dif_stage(T2* a, int L, int nb, int ld, const T2
     else if (R == 2) dft2<DIR>(v);
     else if (ZMID) dft3_zmid<DIR>(v);
     else dft3<DIR>(v);
-    if (j > 0) {
+    if (TW) {
 #pragma unroll
       for (int q = 1; q < R; ++q) {
         T2 w = tw[q * j * tmul];
@@ -225,15 +229,22 @@ __device__ __forceinline__ void dif_stage(T2* a, int L, int nb, int ld, const T2
 #pragma unroll
     for (int q = 0; q < R; ++q) x[q * m] = v[q];
   }
+}
+template <int R, int DIR, bool ZMID, typename T2>
+__device__ __forceinline__ void dif_stage(T2* a, int L, int nb, int ld, const T2* __restrict__ tw, int Ls,
+                                          unsigned mag_nbf, unsigned mag_m) {
+  if (mag_m) dif_loop<R, DIR, ZMID, true>(a, L, nb, ld, tw, Ls, mag_nbf, mag_m);   // mag 0: m = 1
+  else dif_loop<R, DIR, ZMID, false>(a, L, nb, ld, tw, Ls, mag_nbf, mag_m);
   __syncthreads();
 }
 
 // DIT stage of radix R on blocks of size Ls: input r of butterfly j is scaled
 // by w_Ls^(DIR r j), then y_q = sum_r x_r w_R^(DIR r q) goes to slot q.  With
-// ZMID the middle output (q = 1) is neither formed nor stored.
-template <int R, int DIR, bool ZMID, typename T2>
-__device__ __forceinline__ void dit_stage(T2* a, int L, int nb, int ld, const T2* __restrict__ tw, int Ls,
-                                          unsigned mag_nbf, unsigned mag_m) {
+// ZMID the middle output (q = 1) is neither formed nor stored.  TW as in the DIF
+// stage.
+template <int R, int DIR, bool ZMID, bool TW, typename T2>
+__device__ __forceinline__ void dit_loop(T2* a, int L, int nb, int ld, const T2* __restrict__ tw, int Ls,
+                                         unsigned mag_nbf, unsigned mag_m) {
   const int m = Ls / R;
   const int nbf = L / R;
   const int tmul = L / Ls;
@@ -241,13 +252,13 @@ __device__ __forceinline__ void dit_stage(T2* a, int L, int nb, int ld, const T2
   for (int t = threadIdx.x; t < total; t += blockDim.x) {
     const int bi = mag_nbf ? (int)__umulhi((unsigned)t, mag_nbf) : t;   // t / nbf (exact while t nbf < 2^32)
     const int u = t - bi * nbf;
-    const int blk = mag_m ? (int)__umulhi((unsigned)u, mag_m) : u;   // u / m (mag 0: m = 1)
+    const int blk = TW ? (int)__umulhi((unsigned)u, mag_m) : u;   // u / m
     const int j = u - blk * m;
     T2* x = a + bi * ld + blk * Ls + j;
     T2 v[R];
 #pragma unroll
     for (int q = 0; q < R; ++q) v[q] = x[q * m];
-    if (j > 0) {
+    if (TW) {
 #pragma unroll
       for (int q = 1; q < R; ++q) {
         T2 w = tw[q * j * tmul];
@@ -263,6 +274,12 @@ __device__ __forceinline__ void dit_stage(T2* a, int L, int nb, int ld, const T2
     for (int q = 0; q < R; ++q)
       if (!(ZMID && q == 1)) x[q * m] = v[q];
   }
+}
+template <int R, int DIR, bool ZMID, typename T2>
+__device__ __forceinline__ void dit_stage(T2* a, int L, int nb, int ld, const T2* __restrict__ tw, int Ls,
+                                          unsigned mag_nbf, unsigned mag_m) {
+  if (mag_m) dit_loop<R, DIR, ZMID, true>(a, L, nb, ld, tw, Ls, mag_nbf, mag_m);   // mag 0: m = 1
+  else dit_loop<R, DIR, ZMID, false>(a, L, nb, ld, tw, Ls, mag_nbf, mag_m);
   __syncthreads();
 }
 
@@ -296,6 +313,185 @@ __device__ void fft_dit(T2* a, int L, int nb, int ld, const T2* __restrict__ tw,
     else if (R == 2) dit_stage<2, DIR, false>(a, L, nb, ld, tw, Ls, mn, mm);
     else if (s == 0 && zmid) dit_stage<3, DIR, true>(a, L, nb, ld, tw, Ls, mn, mm);
     else dit_stage<3, DIR, false>(a, L, nb, ld, tw, Ls, mn, mm);
+  }
+}
+
+// Cooley-Tukey stages for FP64 and FP32: the twiddles scale the INPUTS of each
+// butterfly, so every radix-2 step is a +- w b, and a - w b = 2a - (a + w b) takes
+// the FMA form (six fused operations per radix-2 step instead of a complex multiply
+// and four additions).  A twiddled radix-4 butterfly is two levels of such steps
+// (24 FP64 operations instead of 28), a twiddled radix 3 shares one product between
+// its sum and difference (18 instead of 20).  FP64 throughput is what bounds these
+// transforms on this GPU, so the operation count is the time.
+//
+// The forward transforms (digit-reversed in, natural out) are the decimation-in-time
+// stages above with these butterflies.  The inverse transforms keep natural input
+// and digit-reversed output, with the same digit order as the DIF stages: stage s
+// splits each block of size Ls (the residue of the spectrum modulo z^Ls - c) into R
+// blocks of size m = Ls/R.  Input r of block b is scaled by w_L^(DIR r K m), where K
+// is the digit reversal of b over the radices already applied (K = 0 for the single
+// block of the first stage, which therefore has no twiddles); then the radix-R DFT.
+// Double-float transforms keep the DIF / DIT stages: a pair product is not one fused
+// operation, so the rewrite would save nothing there.
+
+__device__ __forceinline__ double fmaT(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a, b, c); }
+
+// a <- a + w b, b <- a - w b
+template <typename T2> __device__ __forceinline__ void ct2(T2& a, T2& b, T2 w) {
+  typedef typename Scal<T2>::t T;
+  T2 p;
+  p.x = fmaT(w.x, b.x, fmaT(-w.y, b.y, a.x));
+  p.y = fmaT(w.x, b.y, fmaT(w.y, b.x, a.y));
+  b.x = fmaT(T(2), a.x, -p.x);
+  b.y = fmaT(T(2), a.y, -p.y);
+  a = p;
+}
+// y_q = sum_r v_r w^r i^(DIR r q), with w2 = w^2: (v0, v2) and (v1, v3) with w^2, then
+// (e0, o0) with w and (e1, o1) with DIR i w.
+template <int DIR, typename T2> __device__ __forceinline__ void ct4(T2* v, T2 w, T2 w2) {
+  ct2(v[0], v[2], w2);
+  ct2(v[1], v[3], w2);
+  T2 wi;   // DIR i w
+  if (DIR < 0) { wi.x = w.y; wi.y = -w.x; } else { wi.x = -w.y; wi.y = w.x; }
+  ct2(v[0], v[1], w);    // y0, y2
+  ct2(v[2], v[3], wi);   // y1, y3
+  T2 t = v[1]; v[1] = v[2]; v[2] = t;
+}
+// y_q = sum_r v_r w^r w_3^(DIR r q): p = w v1, s = p + w^2 v2, d = p - w^2 v2 = 2p - s.
+// NOMID: the middle output is not formed.
+template <int DIR, bool NOMID, typename T2> __device__ __forceinline__ void ct3(T2* v, T2 w, T2 w2) {
+  typedef typename Scal<T2>::t T;
+  const T h = sqrt3_2<T>();
+  T2 p, sm, d, mm;
+  p.x = fmaT(w.x, v[1].x, -w.y * v[1].y);
+  p.y = fmaT(w.x, v[1].y, w.y * v[1].x);
+  sm.x = fmaT(w2.x, v[2].x, fmaT(-w2.y, v[2].y, p.x));
+  sm.y = fmaT(w2.x, v[2].y, fmaT(w2.y, v[2].x, p.y));
+  d.x = fmaT(T(2), p.x, -sm.x);
+  d.y = fmaT(T(2), p.y, -sm.y);
+  mm.x = fmaT(T(-0.5), sm.x, v[0].x);
+  mm.y = fmaT(T(-0.5), sm.y, v[0].y);
+  v[0].x += sm.x;
+  v[0].y += sm.y;
+  // y1 = mm + DIR i h d, y2 = mm - DIR i h d
+  const T g = DIR < 0 ? h : -h;
+  if (!NOMID) {
+    v[1].x = fmaT(g, d.y, mm.x);
+    v[1].y = fmaT(-g, d.x, mm.y);
+  }
+  v[2].x = fmaT(-g, d.y, mm.x);
+  v[2].y = fmaT(g, d.x, mm.y);
+}
+
+// Digit reversal of block b over the radices of stages 0..s-1; P = R_0 ... R_(s-1).
+__device__ __forceinline__ int block_rev(int b, const FftPlan& pl, int s, int P) {
+  int K = 0;
+  for (int i = s - 1; i >= 0; --i) {
+    const int Ri = pl.radix[i];
+    const int bq = Ri == 3 ? (int)__umulhi((unsigned)b, 0x55555556u) : b >> (Ri >> 1);   // b / Ri (b < 2^31)
+    P = Ri == 3 ? (int)__umulhi((unsigned)P, 0x55555556u) : P >> (Ri >> 1);              // R_0 ... R_(i-1)
+    K += (b - bq * Ri) * P;
+    b = bq;
+  }
+  return K;
+}
+
+// One Cooley-Tukey stage.  NR: inverse (block twiddles, block size Ls shrinking); else
+// forward (twiddle of butterfly j is w_Ls^(DIR j)).  Z = 1: the middle input is zero
+// (first inverse stage of a padded transform); Z = 2: the middle output is dropped
+// (last forward stage before the truncation).  TW = false: every twiddle is 1.
+template <int R, int DIR, int Z, bool TW, bool NR, typename T2>
+__device__ __forceinline__ void ct_loop(T2* a, int L, int nb, int ld, const T2* __restrict__ tw, int Ls,
+                                        unsigned mag_nbf, unsigned mag_m, const FftPlan& pl, int s, int P) {
+  const int m = Ls / R;
+  const int nbf = L / R;
+  const int tmul = L / Ls;
+  const int total = nb * nbf;
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    const int bi = mag_nbf ? (int)__umulhi((unsigned)t, mag_nbf) : t;   // t / nbf (exact while t nbf < 2^32)
+    const int u = t - bi * nbf;
+    const int blk = mag_m ? (int)__umulhi((unsigned)u, mag_m) : u;      // u / m (mag 0: m = 1)
+    const int j = u - blk * m;
+    T2* x = a + bi * ld + blk * Ls + j;
+    T2 v[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) v[q] = (Z == 1 && q == 1) ? zero2<T2>() : x[q * m];
+    if (TW) {
+      const int e = NR ? block_rev(blk, pl, s, P) * m : j * tmul;
+      T2 w = tw[e], w2 = R == 2 ? w : tw[2 * e];
+      if (DIR > 0) { w.y = -w.y; w2.y = -w2.y; }
+      if (R == 4) ct4<DIR>(v, w, w2);
+      else if (R == 2) ct2(v[0], v[1], w);
+      else ct3<DIR, Z == 2>(v, w, w2);
+    } else {
+      if (R == 4) dft4<DIR>(v);
+      else if (R == 2) dft2<DIR>(v);
+      else if (Z == 1) dft3_zmid<DIR>(v);
+      else if (Z == 2) dft3_nomid<DIR>(v);
+      else dft3<DIR>(v);
+    }
+#pragma unroll
+    for (int q = 0; q < R; ++q)
+      if (!(Z == 2 && q == 1)) x[q * m] = v[q];
+  }
+  __syncthreads();
+}
+
+template <typename T2> struct IsPair { static constexpr bool v = false; };
+template <> struct IsPair<dfc> { static constexpr bool v = true; };
+
+// Inverse transform (spectral -> physical) of nb sequences: natural in, digit-reversed out.
+// zmid: the middle third of the input is zero (3/2 padding).
+template <int DIR, typename T2>
+__device__ void fft_inv(T2* a, int L, int nb, int ld, const T2* __restrict__ tw, const FftPlan& pl, bool zmid) {
+  if constexpr (IsPair<T2>::v) {
+    fft_dif<DIR>(a, L, nb, ld, tw, pl, zmid);
+  } else {
+    int Ls = L, P = 1;
+    for (int s = 0; s < pl.np; ++s) {
+      const int R = pl.radix[s];
+      const unsigned mn = pl.mag_nbf[s], mm = pl.mag_mdif[s];
+      if (s == 0) {   // one block, K = 0
+        if (R == 4) ct_loop<4, DIR, 0, false, true>(a, L, nb, ld, tw, Ls, mn, mm, pl, s, P);
+        else if (R == 2) ct_loop<2, DIR, 0, false, true>(a, L, nb, ld, tw, Ls, mn, mm, pl, s, P);
+        else if (zmid) ct_loop<3, DIR, 1, false, true>(a, L, nb, ld, tw, Ls, mn, mm, pl, s, P);
+        else ct_loop<3, DIR, 0, false, true>(a, L, nb, ld, tw, Ls, mn, mm, pl, s, P);
+      } else {
+        if (R == 4) ct_loop<4, DIR, 0, true, true>(a, L, nb, ld, tw, Ls, mn, mm, pl, s, P);
+        else if (R == 2) ct_loop<2, DIR, 0, true, true>(a, L, nb, ld, tw, Ls, mn, mm, pl, s, P);
+        else ct_loop<3, DIR, 0, true, true>(a, L, nb, ld, tw, Ls, mn, mm, pl, s, P);
+      }
+      Ls /= R;
+      P *= R;
+    }
+  }
+}
+
+// Forward transform (physical -> spectral): digit-reversed in (as fft_inv leaves it),
+// natural out.  zmid: the middle third of the output is not needed (3/2 truncation).
+template <int DIR, typename T2>
+__device__ void fft_fwd(T2* a, int L, int nb, int ld, const T2* __restrict__ tw, const FftPlan& pl, bool zmid) {
+  if constexpr (IsPair<T2>::v) {
+    fft_dit<DIR>(a, L, nb, ld, tw, pl, zmid);
+  } else {
+    int Ls = 1;
+    for (int s = pl.np - 1; s >= 0; --s) {
+      const int R = pl.radix[s];
+      Ls *= R;
+      const unsigned mn = pl.mag_nbf[s], mm = pl.mag_mdit[s];
+      if (mm == 0) {   // m = 1: every twiddle is 1
+        if (R == 4) ct_loop<4, DIR, 0, false, false>(a, L, nb, ld, tw, Ls, mn, mm, pl, s, 0);
+        else if (R == 2) ct_loop<2, DIR, 0, false, false>(a, L, nb, ld, tw, Ls, mn, mm, pl, s, 0);
+        else if (s == 0 && zmid) ct_loop<3, DIR, 2, false, false>(a, L, nb, ld, tw, Ls, mn, mm, pl, s, 0);
+        else ct_loop<3, DIR, 0, false, false>(a, L, nb, ld, tw, Ls, mn, mm, pl, s, 0);
+      } else {
+        if (R == 4) ct_loop<4, DIR, 0, true, false>(a, L, nb, ld, tw, Ls, mn, mm, pl, s, 0);
+        else if (R == 2) ct_loop<2, DIR, 0, true, false>(a, L, nb, ld, tw, Ls, mn, mm, pl, s, 0);
+        else if (s == 0 && zmid) ct_loop<3, DIR, 2, true, false>(a, L, nb, ld, tw, Ls, mn, mm, pl, s, 0);
+        else ct_loop<3, DIR, 0, true, false>(a, L, nb, ld, tw, Ls, mn, mm, pl, s, 0);
+      }
+    }
   }
 }
 
@@ -351,7 +547,7 @@ __device__ __forceinline__ void zinv_body(const ZArgs& A, const typename V2<T>::
   else zinv_load<T2, 0>(A, a, in, in32, kx0, hz);
   __syncthreads();
   // the middle third of the padded column is zero: pruned first stage
-  fft_dif<+1>(a, A.L3, A.KB, A.ld, tw, A.pl, true);
+  fft_inv<+1>(a, A.L3, A.KB, A.ld, tw, A.pl, true);
   // physical rows leave in digit-reversed z order (slot = position in the column)
   T2* out = reinterpret_cast<T2*>(A.out[f]) + (size_t)y * A.L3 * A.nxh;
   for (int e = threadIdx.x; e < A.L3 * A.KB; e += blockDim.x) {
@@ -396,7 +592,7 @@ __device__ __forceinline__ void zfwd_body(const ZArgs& A, const typename V2<T>::
   }
   __syncthreads();
   // digit-reversed rows in, natural kz out; the middle third (truncated) is not formed
-  fft_dit<-1>(a, A.L3, A.KB, A.ld, tw, A.pl, true);
+  fft_fwd<-1>(a, A.L3, A.KB, A.ld, tw, A.pl, true);
   double2* out = A.outd[f] + (size_t)y * A.M;
   if (A.pair_out) zfwd_store<T2, 1>(A, a, out, kx0, hz);   // one store loop per output form
   else zfwd_store<T2, 0>(A, a, out, kx0, hz);
@@ -454,7 +650,7 @@ __device__ __forceinline__ void xpass_body(const XArgs& A, const typename V2<T>:
   }
   __syncthreads();
   // kx in [nxh, 2 nxh] is zero padding: pruned first stage; x samples leave digit-reversed
-  fft_dif<+1>(a, L1, NIN, ld, tw, A.pl, true);
+  fft_inv<+1>(a, L1, NIN, ld, tw, A.pl, true);
   T2* r = a;
   T2* o = a;   // products overwrite their own sample slot (all fields share the order)
   for (int x = threadIdx.x; x < L1; x += blockDim.x) {
@@ -488,7 +684,7 @@ __device__ __forceinline__ void xpass_body(const XArgs& A, const typename V2<T>:
   }
   __syncthreads();
   // back to natural kx order; the middle third of the spectrum is discarded, so not formed
-  fft_dit<-1>(a, L1, NOUT, ld, tw, A.pl, true);
+  fft_fwd<-1>(a, L1, NOUT, ld, tw, A.pl, true);
   const T2* s = a;
   const T half = from_d<T>(0.5 * A.scale);
   for (int e = threadIdx.x; e < NOUT * nxh; e += blockDim.x) {
