@@ -74,7 +74,9 @@ def fft_flops(L, pruned=True):
 
     Stage with block Ls and span m = Ls/R: L/R butterflies; each costs its DFT
     (radix 2: 4, radix 4: 16, radix 3: 16 flops) plus (R-1) twiddle complex
-    multiplies (6 flops) unless j = 0 (a 1/m fraction).  With the 3/2 padding
+    multiplies (6 flops) unless j = 0 (a 1/m fraction).  (The inverse transforms
+    run Cooley-Tukey stages whose twiddle-free butterflies are the first block of
+    each stage instead; the count of twiddled butterflies is the same.)  With the 3/2 padding
     the first radix-3 stage of an inverse has a zero middle input (12 flops) and
     the last one of a forward transform skips its middle output (14 flops):
     both cost 13.5 on average over the pair, counted per transform as 12 + 14 / 2.
@@ -94,8 +96,8 @@ def fft_flops(L, pruned=True):
 # DRAM bytes per wall-normal plane of each kernel launch, from ncu on the 384 x 33 x 384
 # profiling case (profiles/*_re550_384x33x384.md: dram__bytes_read.sum + dram__bytes_write.sum
 # divided by 33); valid for Nx = Nz = 384 only and only while the kernels are as captured.
-NCU_BYTES_PER_PLANE = {("k_xpass", "fp64"): (351.300352e6 + 131.277568e6) / 33}
-NCU_PIPE = {("k_xpass", "fp64"): ("fp64", 0.8597)}
+NCU_BYTES_PER_PLANE = {("k_xpass", "fp64"): (350.501888e6 + 133.998080e6) / 33}
+NCU_PIPE = {("k_xpass", "fp64"): ("fp64", 0.8757)}
 
 
 # per mode-point flops of the wall-normal kernels (read off their sweeps)
