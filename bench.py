@@ -299,7 +299,8 @@ def run_ours(args, c, name):
     torch.cuda.set_device(local)
     import paper_1808_06461_b300 as chan
     import synthetic as SY
-    precs = {"fp64": chan.CHAN_PREC_FP64, "mixed": chan.CHAN_PREC_MIXED, "f64x": chan.CHAN_PREC_F64X}
+    precs = {"fp64": chan.CHAN_PREC_FP64, "mixed": chan.CHAN_PREC_MIXED, "f64x": chan.CHAN_PREC_F64X,
+             "mixed_df": chan.CHAN_PREC_MIXED_DF}
     stream = torch.cuda.current_stream()
     nsub = c["sub_per_step"]
     kind, p1, p3 = c["filt"]
@@ -422,7 +423,7 @@ def run_ours(args, c, name):
         def rms(stt):
             return np.sqrt(np.maximum(stt[2:5] - np.array([stt[0] ** 2, 0 * stt[0], stt[1] ** 2]), 0.0))
 
-        for mode in ("mixed", "f64x"):
+        for mode in ("mixed", "f64x", "mixed_df"):
             chm, snap, profm, msm, _ = measure(mode, False)
             chm.close()
             dm, am, fm = roofline(profm, peak64)
@@ -434,7 +435,8 @@ def run_ours(args, c, name):
                              "note": ("FP64-equivalent algorithmic flops over the FP64 ALU peak; "
                                       + ("the kernel runs on the FP32 pipe (pair arithmetic), so the ratio can "
                                          "pass 1" if mode == "f64x" and dm in ("k_xpass", "k_zinv", "k_zfwd")
-                                         else "an FP64 wall-normal kernel"
+                                         else ("a pair-arithmetic wall-normal kernel (FP32 pipe)" if mode != "mixed"
+                                               else "an FP64 wall-normal kernel")
                                          if dm in ("k_helm", "k_pre", "k_poisson", "k_nonlin")
                                          else "FP32 transforms"))},
                 "kernel_shares": {k: round(v[0] / max(1e-9, sum(x[0] for x in profm.values())), 4)
@@ -446,11 +448,13 @@ def run_ours(args, c, name):
                                 "mean_profile_rel": prof_err(sm_[0], st_main[0]),
                                 "rms_profiles_rel": prof_err(rms(sm_), rms(st_main)),
                                 "tau_rel": prof_err(sm_[14:20], st_main[14:20])},
-                "dtype": "f32 transforms + f64 y-solves" if mode == "mixed" else "f32x2 transforms and y-sweeps, f64 state and mean solve"}
+                "dtype": {"mixed": "f32 transforms + f64 y-solves",
+                          "f64x": "f32x2 transforms and y-sweeps, f64 mean solve",
+                          "mixed_df": "f32 transforms + f32x2 y-sweeps, f64 mean solve"}[mode]}
     line = {"metric": "DNS Mpts.substep/s", "value": value, "unit": "Mpts*substep/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp64": "f64", "mixed": "f32+f64", "f64x": "f32x2+f64"}[main_mode],
+            "dtype": {"fp64": "f64", "mixed": "f32+f64", "f64x": "f32x2+f64", "mixed_df": "f32+f32x2+f64"}[main_mode],
             "data": "synthetic",
             "config": {"workload": name, "Nx": c["Nx"], "Ny": c["Ny"], "Nz": c["Nz"], "re_tau": c["re"],
                        "dt": c["dt"], "substeps_per_step": nsub, "filter": {"kind": "sharp" if kind == 0 else "box",
@@ -499,7 +503,7 @@ def run_serving(args, rank):
 
     out = {"requests": args.serve_requests, "rate_per_s": 50.0, "seed": 42, "hbm_budget_gb": 64,
            "max_slots": 16}
-    for prec, tag in ((0, "fp64"), (1, "mixed"), (2, "f64x")):
+    for prec, tag in ((0, "fp64"), (1, "mixed"), (2, "f64x"), (3, "mixed_df")):
         for packed in (False, True):
             reqs = poisson_requests(args.serve_requests, 50.0, 42 + rank, precision=prec)
             _, m = Server(64 << 30, max_slots=16, factory=channel_factory(ic), packed=packed).run(
@@ -518,7 +522,8 @@ def run_precision_study(args, c, name):
     kind, p1, p3 = c["filt"]
     res, times = {}, {}
     s0 = None
-    for tag, prec in (("fp64", chan.CHAN_PREC_FP64), ("mixed", chan.CHAN_PREC_MIXED), ("f64x", chan.CHAN_PREC_F64X)):
+    for tag, prec in (("fp64", chan.CHAN_PREC_FP64), ("mixed", chan.CHAN_PREC_MIXED), ("f64x", chan.CHAN_PREC_F64X),
+                      ("mixed_df", chan.CHAN_PREC_MIXED_DF)):
         ch = chan.Channel(c["re"], c["Lx"], c["Lz"], c["Nx"], c["Ny"], c["Nz"], c["dt"], precision=prec,
                           stream=torch.cuda.current_stream().cuda_stream)
         if s0 is None:
@@ -544,7 +549,7 @@ def run_precision_study(args, c, name):
 
     out = {"workload": name, "substeps": args.precision_study, "filter": c["filt"], "seconds": times,
            "mpts_substep_per_s": {k: c["Nx"] * c["Ny"] * c["Nz"] * args.precision_study / v / 1e6 for k, v in times.items()}}
-    for tag in ("mixed", "f64x"):
+    for tag in ("mixed", "f64x", "mixed_df"):
         st = res[tag]["stats"]
         out[tag + "_vs_fp64"] = {
             "mean_profile_rel": rel_prof(st[0], ref[0]),
@@ -562,7 +567,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp64", "mixed", "f64x"], default="fp64")
+    ap.add_argument("--precision", choices=["fp64", "mixed", "f64x", "mixed_df"], default="fp64")
     ap.add_argument("--no-modes", action="store_true", help="skip the mixed / double-float runs")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-mix run")
     ap.add_argument("--serve-requests", type=int, default=24)

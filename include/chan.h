@@ -55,8 +55,12 @@ extern "C" {
 
 #define CHAN_PREC_FP64  0     /* every step in FP64                                        */
 #define CHAN_PREC_MIXED 1     /* FFTs and products in FP32; y-solves, mean flow, stats FP64 */
-#define CHAN_PREC_F64X  2     /* FFTs and products in double-float (FP32 pairs, ~2^-47);
-                                 y-solves, mean flow, stats FP64                           */
+#define CHAN_PREC_F64X  2     /* FFTs, products and the substep's wall-normal sweeps in
+                                 double-float (FP32 pairs, ~2^-47), Fourier fields stored
+                                 as pairs; mean flow, stats FP64                           */
+#define CHAN_PREC_MIXED_DF 3  /* FFTs and products in FP32; the substep's wall-normal
+                                 sweeps in double-float with Fourier fields stored as
+                                 pairs (as CHAN_PREC_F64X); mean flow, stats FP64           */
 
 #define CHAN_NSTAT 20         /* rows of chan_stats' output, see chan_stats                */
 
@@ -69,7 +73,7 @@ typedef struct chan_opts {
   double dt;         /* time step of a full RK3 step (each substep uses dt)          */
   double eta_w;      /* wall Kolmogorov scale of the mesh (default 1.0)              */
   double grid_re;    /* Re_tau the mesh is clustered for (<= 0: re_tau)              */
-  int precision;     /* CHAN_PREC_FP64, CHAN_PREC_MIXED or CHAN_PREC_F64X            */
+  int precision;     /* CHAN_PREC_FP64, _MIXED, _F64X or _MIXED_DF                    */
   void* stream;      /* cudaStream_t to run on, or NULL for a library-owned stream   */
   const double* mesh;/* explicit wall-normal mesh double[Ny] (increasing from -1 to 1,
                         mirror symmetric), e.g. from chan_optimize_mesh; NULL: the

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(HERE, "libchan.so")
 
 CHAN_OK, CHAN_EINVAL, CHAN_ENOMEM, CHAN_ECUDA, CHAN_ENAN, CHAN_ESTATE = 0, -1, -2, -3, -4, -5
 CHAN_FILTER_SHARP, CHAN_FILTER_BOX = 0, 1
-CHAN_PREC_FP64, CHAN_PREC_MIXED, CHAN_PREC_F64X = 0, 1, 2
+CHAN_PREC_FP64, CHAN_PREC_MIXED, CHAN_PREC_F64X, CHAN_PREC_MIXED_DF = 0, 1, 2, 3
 CHAN_NSTAT = 20
 
 # Exported symbols, exactly the declarations of include/chan.h.

@@ -102,14 +102,14 @@ enum { WF_U1 = 0, WF_U3 = 1, WF_OM1 = 2, WF_OM3 = 3, WF_H1 = 4, WF_H2 = 5, WF_H3
 
 double2* wf(chan_s* h, int k) { return h->wf + (size_t)k * fsize(h); }
 void* mixed(chan_s* h, int k) {
-  const size_t es = h->prec == CHAN_PREC_MIXED ? sizeof(float2) : sizeof(double2);
+  const size_t es = prec_t32(h->prec) ? sizeof(float2) : sizeof(double2);
   return static_cast<char*>(h->mixed) + (size_t)k * h->slab * h->L3 * h->nxh * es;
 }
 
 // Planes per slab of the transform passes (see chan_opts.slab_planes).
 int slab_planes(int Nx, int Ny, int Nz, int prec, int req) {
   if (req > 0) return req < Ny ? req : Ny;
-  const size_t es = prec == CHAN_PREC_MIXED ? sizeof(float2) : sizeof(double2);
+  const size_t es = prec_t32(prec) ? sizeof(float2) : sizeof(double2);
   const size_t plane = 12 * (size_t)(3 * Nz / 2) * (size_t)(Nx / 2) * es;
   size_t smax = ((size_t)16 << 30) / plane;
   if (smax < 1) smax = 1;
@@ -129,7 +129,7 @@ void after_state_upload(chan_s* h) {
   clean_modes(h, h->v);
   clean_modes(h, h->om);
   { Traced t(h, KID_DERIVE); CK(launch_derive(h)); }
-  if (h->prec == CHAN_PREC_F64X)   // the substep keeps its Fourier fields as FP32 pairs
+  if (prec_pairs(h->prec))   // the substep keeps its Fourier fields as FP32 pairs
     for (double2* f : {h->v, h->om, h->chi, h->dv}) CK(launch_to_pairs(h, f, fsize(h)));
   CK(cudaMemsetAsync(h->Nchi_p, 0, fsize(h) * sizeof(double2), h->stream));
   CK(cudaMemsetAsync(h->Nom_p, 0, fsize(h) * sizeof(double2), h->stream));
@@ -150,7 +150,7 @@ int substep_inputs(const chan_s* h, double2* u1, double2* u3, double2* om1, doub
   const size_t o = y0 * h->M, nf = fsize(h);
   in[1] = h->v + o;
   in[4] = h->om + o;
-  if (h->prec != CHAN_PREC_MIXED) {
+  if (!prec_t32(h->prec)) {
     in[0] = u1 + o; in[2] = u3 + o; in[3] = om1 + o; in[5] = om3 + o;
     return 0;
   }
@@ -238,15 +238,15 @@ size_t footprint_ex(int Nx, int Ny, int Nz, int prec, int slab_req, int lean) {
   const size_t nxh = Nx / 2, M = (size_t)Nz * nxh, C = (size_t)(Nz / 2) * nxh, n = (size_t)Ny * M;
   const size_t nslot = lean ? 1 : 3;
   const size_t L1 = 3 * (size_t)Nx / 2, L3 = 3 * (size_t)Nz / 2;
-  const size_t es = prec == CHAN_PREC_MIXED ? sizeof(float2) : sizeof(double2);
+  const size_t es = prec_t32(prec) ? sizeof(float2) : sizeof(double2);
   size_t b = 0;
   b += 8 * n * sizeof(double2) + 4 * Ny * sizeof(double) + 3 * sizeof(double);            // state
   b += 5 * 7 * (size_t)Ny * sizeof(double) + 3 * (size_t)Ny * sizeof(double);              // y tables
   b += (nxh + Nz) * sizeof(double);                                                          // wavenumbers
   b += ((size_t)Ny * 7 * C + nslot * (size_t)Ny * 11 * C + nslot * 4 * C + 3 * ((size_t)Ny + 1)) * sizeof(double);
-  if (prec == CHAN_PREC_F64X)
+  if (prec_pairs(prec))
     b += ((size_t)Ny * 7 * C + nslot * (size_t)Ny * 11 * C + nslot * 4 * C + 30 * (size_t)Ny) * sizeof(dfr);
-  b += (L1 + L3) * (prec == CHAN_PREC_MIXED ? sizeof(float2) : sizeof(double2));             // twiddles
+  b += (L1 + L3) * (prec_t32(prec) ? sizeof(float2) : sizeof(double2));             // twiddles
   const size_t S = slab_planes(Nx, Ny, Nz, prec, slab_req);
   b += (size_t)NWF * n * sizeof(double2);                                                    // work fields
   b += 12 * S * L3 * nxh * es;                                                               // mixed fields
@@ -438,15 +438,16 @@ int chan_init_ex(chan_t* out, const chan_opts* o) {
   if (o->Nx < 2 || o->Nx % 2 || !is_2a3b(o->Nx)) return bad(nullptr, "chan_init: Nx must be even and 2^a 3^b");
   if (o->Nz < 4 || o->Nz % 4 || !is_2a3b(o->Nz)) return bad(nullptr, "chan_init: Nz must be a multiple of 4 and 2^a 3^b");
   if (o->Ny < 9 || o->Ny % 2 == 0) return bad(nullptr, "chan_init: Ny must be odd and >= 9");
-  if (o->precision != CHAN_PREC_FP64 && o->precision != CHAN_PREC_MIXED && o->precision != CHAN_PREC_F64X)
+  if (o->precision != CHAN_PREC_FP64 && o->precision != CHAN_PREC_MIXED && o->precision != CHAN_PREC_F64X &&
+      o->precision != CHAN_PREC_MIXED_DF)
     return bad(nullptr, "chan_init: unknown precision");
   if (o->slab_planes < 0) return bad(nullptr, "chan_init: slab_planes must be >= 0");
   if (o->y_tables < 0 || o->y_tables > 2) return bad(nullptr, "chan_init: y_tables must be 0, 1 or 2");
   const int L1 = 3 * o->Nx / 2, L3 = 3 * o->Nz / 2;
-  const size_t es = o->precision == CHAN_PREC_MIXED ? 8 : 16;
+  const size_t es = prec_t32(o->precision) ? 8 : 16;
   if (2 * 6 * (size_t)(L1 + 1) * es > 227 * 1024 || 2 * (size_t)(L3 + 1) * es > 100 * 1024)
     return bad(nullptr, "chan_init: 3Nx/2 or 3Nz/2 too long for an in-block transform at this precision "
-                        "(FP64 and double-float: Nx <= 768, mixed: Nx <= 1536)");
+                        "(FP64 and double-float: Nx <= 768, the two mixed modes: Nx <= 1536)");
   chan_s* h = new (std::nothrow) chan_s();
   if (!h) return bad(nullptr, "chan_init: out of host memory", CHAN_ENOMEM);
   h->re = o->re_tau; h->Lx = o->Lx; h->Lz = o->Lz; h->dt = o->dt; h->nu = 1.0 / o->re_tau;
@@ -529,7 +530,7 @@ int chan_init_ex(chan_t* out, const chan_opts* o) {
     h->helm = dalloc<double>(h, nslot * Ny * 11 * (size_t)h->C);
     h->infl = dalloc<double>(h, nslot * 4 * (size_t)h->C);
     h->meanh = dalloc<double>(h, 3 * (Ny + 1));
-    if (h->prec == CHAN_PREC_F64X) {
+    if (prec_pairs(h->prec)) {
       h->tab_pairs = dalloc<dfr>(h, 30 * Ny);
       h->pois_df = dalloc<dfr>(h, Ny * 7 * (size_t)h->C);
       h->helm_df = dalloc<dfr>(h, nslot * Ny * 11 * (size_t)h->C);
@@ -641,7 +642,7 @@ static int get_state_impl(chan_t h, void* v, void* om, void* U1, void* U3, cudaM
     const size_t n = fsize(h);
     const double2* sv = h->v;
     const double2* so = h->om;
-    if (h->prec == CHAN_PREC_F64X) {   // pairs back to FP64: into the caller's device arrays, or the u_1, u_3 slots
+    if (prec_pairs(h->prec)) {   // pairs back to FP64: into the caller's device arrays, or the u_1, u_3 slots
       double2* dv_ = k == cudaMemcpyDeviceToDevice ? static_cast<double2*>(v) : wf(h, WF_U1);
       double2* do_ = k == cudaMemcpyDeviceToDevice ? static_cast<double2*>(om) : wf(h, WF_U3);
       if (v) { CK(launch_from_pairs(h, h->v, dv_, n)); sv = dv_; }
@@ -786,7 +787,7 @@ int chan_nonlinear(chan_t h, double* H) {
   try {
     run_pre(h, true);
     run_nonlinear(h);
-    if (h->prec == CHAN_PREC_F64X) CK(launch_from_pairs(h, wf(h, WF_H1), wf(h, WF_H1), 3 * fsize(h)));
+    if (prec_pairs(h->prec)) CK(launch_from_pairs(h, wf(h, WF_H1), wf(h, WF_H1), 3 * fsize(h)));
     CK(cudaMemcpyAsync(H, wf(h, WF_H1), 3 * fsize(h) * sizeof(double2), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
   } catch (Fail f) {
@@ -802,7 +803,7 @@ int chan_rhs_terms(chan_t h, double* N) {
     run_pre(h, true);
     run_nonlinear(h);
     { Traced t(h, KID_NONLIN); CK(launch_nonlin(h, wf(h, WF_H1), wf(h, WF_H2), wf(h, WF_H3), wf(h, WF_NCHI), wf(h, WF_NOM))); }
-    if (h->prec == CHAN_PREC_F64X) CK(launch_from_pairs(h, wf(h, WF_NCHI), wf(h, WF_NCHI), 2 * fsize(h)));
+    if (prec_pairs(h->prec)) CK(launch_from_pairs(h, wf(h, WF_NCHI), wf(h, WF_NCHI), 2 * fsize(h)));
     CK(cudaMemcpyAsync(N, wf(h, WF_NCHI), 2 * fsize(h) * sizeof(double2), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
   } catch (Fail f) {
@@ -1021,7 +1022,7 @@ int chan_autotune(chan_t h) {
   try {
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
-    const size_t es = h->prec == CHAN_PREC_MIXED ? sizeof(float2) : sizeof(double2);
+    const size_t es = prec_t32(h->prec) ? sizeof(float2) : sizeof(double2);
     run_pre(h);
     const double2* in[6] = {wf(h, WF_U1), h->v, wf(h, WF_U3), wf(h, WF_OM1), h->om, wf(h, WF_OM3)};
     void* mx[6] = {mixed(h, 0), mixed(h, 1), mixed(h, 2), mixed(h, 3), mixed(h, 4), mixed(h, 5)};
@@ -1099,7 +1100,7 @@ int chan_autotune(chan_t h) {
 
 int chan_tuned_shape(chan_t h, int* kb_z, int* xthreads, int* ytab_global) {
   if (!h) return bad(nullptr, "chan_tuned_shape: NULL handle");
-  const size_t es = h->prec == CHAN_PREC_MIXED ? sizeof(float2) : sizeof(double2);
+  const size_t es = prec_t32(h->prec) ? sizeof(float2) : sizeof(double2);
   if (kb_z) *kb_z = h->kb_z > 0 ? h->kb_z : pick_kb(h->nxh, h->L3, es);
   if (xthreads) *xthreads = h->xthreads > 0 ? h->xthreads : 256;
   if (ytab_global)

@@ -10,6 +10,11 @@
 #include "chan_host.h"
 #include "df.cuh"
 
+// Precision-mode properties (host side): transforms and products in FP32; Fourier
+// fields stored as double-float pairs, with the substep's wall-normal sweeps in pairs.
+inline bool prec_t32(int p) { return p == CHAN_PREC_MIXED || p == CHAN_PREC_MIXED_DF; }
+inline bool prec_pairs(int p) { return p == CHAN_PREC_F64X || p == CHAN_PREC_MIXED_DF; }
+
 // Fourier fields: double2 arrays [Ny][M], M = Nz * (Nx/2), mode m = jz*nxh + kx.
 // Mixed fields (physical z, Fourier kx): [Ny][L3][nxh] of float2 or double2.
 // Wavenumber classes (shared LU factors): c = |kz| * nxh + kx, |kz| < Nz/2.

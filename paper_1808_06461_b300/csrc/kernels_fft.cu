@@ -88,8 +88,19 @@ template <typename T2> __device__ __forceinline__ void st_fourier(double2* p, si
   p[o] = make_double2(to_d(x.x), to_d(x.y));
 }
 template <> __device__ __forceinline__ void st_fourier<float2>(double2* p, size_t o, float2 x, int pair) {
-  (void)pair;
-  p[o] = make_double2(f2d_int(x.x), f2d_int(x.y));
+  if (pair) reinterpret_cast<float4*>(p)[o] = make_float4(x.x, 0.f, x.y, 0.f);   // (hi, lo = 0) pairs
+  else p[o] = make_double2(f2d_int(x.x), f2d_int(x.y));
+}
+// A pair-stored Fourier value rounded to FP32 (hi + lo), optionally times g.
+__device__ __forceinline__ float2 ld_pair_f32(const double2* p, size_t o, bool useg, double g) {
+  const float4 q = reinterpret_cast<const float4*>(p)[o];
+  float2 v = make_float2(q.x + q.y, q.z + q.w);
+  if (useg) {
+    const float gf = d2f_int(g);
+    v.x *= gf;
+    v.y *= gf;
+  }
+  return v;
 }
 template <> __device__ __forceinline__ void st_fourier<dfc>(double2* p, size_t o, dfc x, int pair) {
   if (pair) reinterpret_cast<float4*>(p)[o] = make_float4(x.x.h, x.x.l, x.y.h, x.y.l);
@@ -504,7 +515,8 @@ struct ZArgs {
   int Ny, Nz, nxh, M, L3, KB, ld;
   int lgKB;       // KB = 2^lgKB columns per CTA
   int pair_out;   // double-float mode: the forward pass writes (hi, lo) pairs
-  int f32_mask;   // inverse pass: bit f set = field f is stored as float2 (mixed mode)
+  int f32_mask;   // inverse pass: bit f set = field f is stored as float2 (mixed modes)
+  int pair_in;    // FP32 transforms of Fourier fields stored as pairs (mixed mode with pair sweeps)
   FftPlan pl;
 };
 
@@ -512,7 +524,8 @@ struct ZArgs {
 // kz zero-padded to 3Nz/2 (the kz Nyquist row is dropped), optional filter
 // transfer G applied on load.
 // Load a column chunk of one Fourier field into the padded transform buffer.  KIND 0: stored
-// as the state is stored; 1: times the filter transfer G; 2: stored as float2 (mixed mode).
+// as the state is stored; 1: times the filter transfer G; 2: stored as float2 (mixed modes);
+// 3, 4: stored as pairs, FP32 transforms (as 0, 1).
 template <typename T2, int KIND>
 __device__ __forceinline__ void zinv_load(const ZArgs& A, T2* a, const double2* in, const float2* in32, int kx0, int hz) {
   for (int e = threadIdx.x; e < A.Nz * A.KB; e += blockDim.x) {
@@ -522,6 +535,8 @@ __device__ __forceinline__ void zinv_load(const ZArgs& A, T2* a, const double2* 
     const int pz = jz < hz ? jz : jz + (A.L3 - A.Nz);
     if constexpr (KIND == 2) {
       if constexpr (std::is_same<T2, float2>::value) a[kl * A.ld + pz] = in32[q];
+    } else if constexpr (KIND >= 3) {
+      if constexpr (std::is_same<T2, float2>::value) a[kl * A.ld + pz] = ld_pair_f32(in, q, KIND == 4, KIND == 4 ? A.G[q] : 0.0);
     } else {
       a[kl * A.ld + pz] = ld_fourier<T2>(in, q, KIND == 1, KIND == 1 ? A.G[q] : 0.0);
     }
@@ -543,7 +558,10 @@ __device__ __forceinline__ void zinv_body(const ZArgs& A, const typename V2<T>::
   const float2* in32 = reinterpret_cast<const float2*>(A.in[f]) + (size_t)y * A.M;
   // one loop per input kind, so that no branch of another kind is issued (predicated) per element
   if (f32) zinv_load<T2, 2>(A, a, in, in32, kx0, hz);   // (float2 inputs are never filtered)
-  else if (A.applyG[f]) zinv_load<T2, 1>(A, a, in, in32, kx0, hz);
+  else if (A.pair_in) {
+    if (A.applyG[f]) zinv_load<T2, 4>(A, a, in, in32, kx0, hz);
+    else zinv_load<T2, 3>(A, a, in, in32, kx0, hz);
+  } else if (A.applyG[f]) zinv_load<T2, 1>(A, a, in, in32, kx0, hz);
   else zinv_load<T2, 0>(A, a, in, in32, kx0, hz);
   __syncthreads();
   // the middle third of the padded column is zero: pruned first stage
@@ -784,21 +802,22 @@ static ZArgs zargs(chan_s* h, size_t es) {
   A.ld = h->L3 + 1;
   A.pl = h->p3;
   A.G = h->G;
+  A.pair_in = h->prec == CHAN_PREC_MIXED_DF;
   return A;
 }
 
-static size_t fft_esize(const chan_s* h) { return h->prec == CHAN_PREC_MIXED ? sizeof(float2) : sizeof(double2); }
+static size_t fft_esize(const chan_s* h) { return prec_t32(h->prec) ? sizeof(float2) : sizeof(double2); }
 
 cudaError_t launch_zinv(chan_s* h, const double2* const* in, const int* apply_G, void* const* out, int nf, int ny,
                         int f32_mask) {
   const size_t es = fft_esize(h);
   ZArgs A = zargs(h, es);
-  A.f32_mask = h->prec == CHAN_PREC_MIXED ? f32_mask : 0;
+  A.f32_mask = prec_t32(h->prec) ? f32_mask : 0;
   for (int f = 0; f < nf; ++f) { A.in[f] = in[f]; A.out[f] = out[f]; A.applyG[f] = apply_G ? apply_G[f] : 0; }
   dim3 grid((h->nxh + A.KB - 1) / A.KB, ny, nf);
   size_t sm = (size_t)A.KB * A.ld * es;
   if (h->prec == CHAN_PREC_FP64) k_zinv<double><<<grid, 256, sm, h->stream>>>(A, (const double2*)h->tw3);
-  else if (h->prec == CHAN_PREC_MIXED) k_zinv<float><<<grid, 256, sm, h->stream>>>(A, (const float2*)h->tw3);
+  else if (prec_t32(h->prec)) k_zinv<float><<<grid, 256, sm, h->stream>>>(A, (const float2*)h->tw3);
   else k_zinv<dfr><<<grid, 256, sm, h->stream>>>(A, (const dfc*)h->tw3);
   return cudaGetLastError();
 }
@@ -806,12 +825,12 @@ cudaError_t launch_zinv(chan_s* h, const double2* const* in, const int* apply_G,
 cudaError_t launch_zfwd(chan_s* h, void* const* in, double2* const* out, int nf, int ny, int pair_out) {
   const size_t es = fft_esize(h);
   ZArgs A = zargs(h, es);
-  A.pair_out = pair_out && h->prec == CHAN_PREC_F64X;
+  A.pair_out = pair_out && prec_pairs(h->prec);
   for (int f = 0; f < nf; ++f) { A.out[f] = in[f]; A.outd[f] = out[f]; }
   dim3 grid((h->nxh + A.KB - 1) / A.KB, ny, nf);
   size_t sm = (size_t)A.KB * A.ld * es;
   if (h->prec == CHAN_PREC_FP64) k_zfwd<double><<<grid, 256, sm, h->stream>>>(A, (const double2*)h->tw3);
-  else if (h->prec == CHAN_PREC_MIXED) k_zfwd<float><<<grid, 256, sm, h->stream>>>(A, (const float2*)h->tw3);
+  else if (prec_t32(h->prec)) k_zfwd<float><<<grid, 256, sm, h->stream>>>(A, (const float2*)h->tw3);
   else k_zfwd<dfr><<<grid, 256, sm, h->stream>>>(A, (const dfc*)h->tw3);
   return cudaGetLastError();
 }
@@ -835,7 +854,7 @@ cudaError_t launch_xpass(chan_s* h, int mode, void* const* in, void* const* out,
     if (mode == 0) k_xpass<double, 0><<<grid, nt, sm, h->stream>>>(A, tw);
     else if (mode == 1) k_xpass<double, 1><<<grid, nt, sm, h->stream>>>(A, tw);
     else k_xpass<double, 2><<<grid, nt, sm, h->stream>>>(A, tw);
-  } else if (h->prec == CHAN_PREC_MIXED) {
+  } else if (prec_t32(h->prec)) {
     const float2* tw = (const float2*)h->tw1;
     if (mode == 0) k_xpass<float, 0><<<grid, nt, sm, h->stream>>>(A, tw);
     else if (mode == 1) k_xpass<float, 1><<<grid, nt, sm, h->stream>>>(A, tw);
@@ -877,7 +896,7 @@ cudaError_t launch_zinv_batch(chan_s* const* hs, int n, const BatchWork* w, cuda
   B.begin[n] = acc;
   const int prec = hs[0]->prec;
   if (prec == CHAN_PREC_FP64) kb_z<double, true><<<acc, 256, sm, st>>>(B);
-  else if (prec == CHAN_PREC_MIXED) kb_z<float, true><<<acc, 256, sm, st>>>(B);
+  else if (prec_t32(prec)) kb_z<float, true><<<acc, 256, sm, st>>>(B);
   else kb_z<dfr, true><<<acc, 256, sm, st>>>(B);
   return cudaGetLastError();
 }
@@ -893,7 +912,7 @@ cudaError_t launch_zfwd_batch(chan_s* const* hs, int n, const BatchWork* w, cuda
     ZArgs A = zargs(h, fft_esize(h));
     double2* outs[3] = {w[r].H1, w[r].H2, w[r].H3};
     for (int f = 0; f < 3; ++f) { A.out[f] = w[r].mixed[f]; A.outd[f] = outs[f]; }
-    A.pair_out = h->prec == CHAN_PREC_F64X;   // H of the substep
+    A.pair_out = prec_pairs(h->prec);   // H of the substep
     B.a[r] = A;
     B.tw[r] = h->tw3;
     B.gx[r] = (h->nxh + A.KB - 1) / A.KB;
@@ -906,7 +925,7 @@ cudaError_t launch_zfwd_batch(chan_s* const* hs, int n, const BatchWork* w, cuda
   B.begin[n] = acc;
   const int prec = hs[0]->prec;
   if (prec == CHAN_PREC_FP64) kb_z<double, false><<<acc, 256, sm, st>>>(B);
-  else if (prec == CHAN_PREC_MIXED) kb_z<float, false><<<acc, 256, sm, st>>>(B);
+  else if (prec_t32(prec)) kb_z<float, false><<<acc, 256, sm, st>>>(B);
   else kb_z<dfr, false><<<acc, 256, sm, st>>>(B);
   return cudaGetLastError();
 }
@@ -938,7 +957,7 @@ cudaError_t launch_xpass_batch(chan_s* const* hs, int n, const BatchWork* w, cud
   B.begin[n] = acc;
   const int prec = hs[0]->prec;
   if (prec == CHAN_PREC_FP64) kb_xpass<double><<<acc, 256, sm, st>>>(B);
-  else if (prec == CHAN_PREC_MIXED) kb_xpass<float><<<acc, 256, sm, st>>>(B);
+  else if (prec_t32(prec)) kb_xpass<float><<<acc, 256, sm, st>>>(B);
   else kb_xpass<dfr><<<acc, 256, sm, st>>>(B);
   return cudaGetLastError();
 }

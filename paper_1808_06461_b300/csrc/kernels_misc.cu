@@ -174,7 +174,7 @@ cudaError_t launch_filter_out(chan_s* h, const double2* const* u, const double2*
   for (int p = 0; p < 6; ++p) { A.puu[p] = puu[p]; A.pbb[p] = pbb[p]; A.tau[p] = tau[p]; }
   A.G = h->G;
   A.n = (size_t)ny * h->M;
-  A.pair = h->prec == CHAN_PREC_F64X;
+  A.pair = prec_pairs(h->prec);
   A.M = h->M;
   k_filter_out<<<(unsigned)((A.n + 255) / 256), 256, 0, h->stream>>>(A);
   return cudaGetLastError();
@@ -195,7 +195,7 @@ cudaError_t launch_gather_retained(chan_s* h, const double2* src, double2* dst, 
 cudaError_t launch_spectra(chan_s* h, const double2* u1, const double2* u3, double* E) {
   const size_t n = (size_t)h->Ny * h->M;
   k_spectra<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(u1, h->v, u3, E, n, h->M, h->nxh,
-                                                                 h->prec == CHAN_PREC_F64X);
+                                                                 prec_pairs(h->prec));
   return cudaGetLastError();
 }
 
@@ -207,7 +207,7 @@ cudaError_t launch_stats(chan_s* h, const double2* u1, const double2* u3, int ze
   A.out = h->stat; A.nu = h->nu;
   A.Ny = h->Ny; A.M = h->M; A.nxh = h->nxh;
   A.y0 = 0; A.nplanes = h->Ny; A.what = 1; A.zero_filtered = zero_filtered;
-  A.pair = h->prec == CHAN_PREC_F64X;
+  A.pair = prec_pairs(h->prec);
   k_stats<<<h->Ny + 1, 256, 0, h->stream>>>(A);
   return cudaGetLastError();
 }

@@ -86,6 +86,9 @@ struct YF64 {
   __device__ static __forceinline__ R neg(R a) { return -a; }
   __device__ static __forceinline__ C ld(const double2* p, size_t o) { return p[o]; }
   __device__ static __forceinline__ void st(double2* p, size_t o, C x) { p[o] = x; }
+  // rounded to FP32 (a transform input of the mixed modes), on the integer pipe
+  __device__ static __forceinline__ float2 f(C x) { return make_float2(d2f_int(x.x), d2f_int(x.y)); }
+  __device__ static __forceinline__ float2 ldf(const double2* p, size_t o) { return f(p[o]); }
   __device__ static __forceinline__ const R* A2(const YTabs& t) { return t.A2; }
   __device__ static __forceinline__ const R* B2(const YTabs& t) { return t.B2; }
   __device__ static __forceinline__ const R* B1(const YTabs& t) { return t.B1; }
@@ -110,6 +113,11 @@ struct YDF {
   }
   __device__ static __forceinline__ void st(double2* p, size_t o, C x) {
     reinterpret_cast<float4*>(p)[o] = make_float4(x.x.h, x.x.l, x.y.h, x.y.l);
+  }
+  __device__ static __forceinline__ float2 f(C x) { return make_float2(x.x.h + x.x.l, x.y.h + x.y.l); }
+  __device__ static __forceinline__ float2 ldf(const double2* p, size_t o) {
+    const float4 q = reinterpret_cast<const float4*>(p)[o];
+    return make_float2(q.x + q.y, q.z + q.w);
   }
   __device__ static __forceinline__ const R* A2(const YTabs& t) { return t.A2p; }
   __device__ static __forceinline__ const R* B2(const YTabs& t) { return t.B2p; }
@@ -189,11 +197,10 @@ __device__ __forceinline__ ModeInfo mode_info(const Geo& g, int m) {
 // a1: u_1, u_3, omega_1, omega_3 from (v, omega_2, dv/dy); two D1 sweeps.
 // dv/dy is part of the state (it is D1 v of the last Poisson solve).
 // ---------------------------------------------------------------------------
-// F32OUT (mixed mode, substep path): the two D1 sweeps stay FP64; u_1, u_3, omega_1,
-// omega_3, which only feed the FP32 transforms, are formed in FP32 from the FP64
-// values and stored as float2: u_1, u_3 in the omega_1 slot ([2][Ny][M] float2),
-// omega_1, omega_3 in the omega_3 slot; the u_1, u_3 slots keep the forward sweep.
-__device__ __forceinline__ float2 tof(double2 x) { return make_float2(d2f_int(x.x), d2f_int(x.y)); }
+// F32OUT (mixed modes, substep path): the two D1 sweeps stay in the sweep precision (FP64
+// or pairs); u_1, u_3, omega_1, omega_3, which only feed the FP32 transforms, are formed in
+// FP32 from those values and stored as float2: u_1, u_3 in the omega_1 slot ([2][Ny][M]
+// float2), omega_1, omega_3 in the omega_3 slot; the u_1, u_3 slots keep the forward sweep.
 
 template <class Y, bool F32OUT = false>
 __device__ __forceinline__ void pre_body(Geo g, YTabs t, const double2* __restrict__ v,
@@ -260,7 +267,7 @@ __device__ __forceinline__ void pre_body(Geo g, YTabs t, const double2* __restri
     const C P = ybwd<Y>(Y::ld(u1o, o), lu[3], lu[4], lu[5], lu[6], px);   // D1 of dv/dy
     const C Q = ybwd<Y>(Y::ld(u3o, o), lu[3], lu[4], lu[5], lu[6], pw);   // D1 omega_2
     if constexpr (F32OUT) {
-      const float2 fP = tof(Y::d(P)), fQ = tof(Y::d(Q));
+      const float2 fP = Y::f(P), fQ = Y::f(Q);
       float2 a1, a3, d1, d3, fv = make_float2(0.f, 0.f);
       if (mean) {
         a1 = make_float2(d2f_int(U1[i]), 0.f);
@@ -268,8 +275,8 @@ __device__ __forceinline__ void pre_body(Geo g, YTabs t, const double2* __restri
         d1 = fP;
         d3 = fQ;
       } else {
-        const float2 fd = tof(dv[o]), fo = tof(om[o]);
-        fv = tof(v[o]);
+        const float2 fd = Y::ldf(dv, o), fo = Y::ldf(om, o);
+        fv = Y::ldf(v, o);
         // u_1 = i (q1 dv - q3 om), u_3 = i (q3 dv + q1 om), likewise d/dy from (P, Q)
         a1 = make_float2(-(q1f * fd.y - q3f * fo.y), q1f * fd.x - q3f * fo.x);
         a3 = make_float2(-(q3f * fd.y + q1f * fo.y), q3f * fd.x + q1f * fo.x);
@@ -316,6 +323,10 @@ __global__ void __launch_bounds__(128) k_pre_df(Geo g, YTabs t, const double2* _
                                                 const double2* __restrict__ om, const double2* __restrict__ dv,
                                                 const double* __restrict__ U1, const double* __restrict__ U3,
                                                 double2* u1o, double2* u3o, double2* om1o, double2* om3o) { pre_body<YDF>(g, t, v, om, dv, U1, U3, u1o, u3o, om1o, om3o, blockIdx.x); }
+__global__ void __launch_bounds__(128) k_pre_df_f32(Geo g, YTabs t, const double2* __restrict__ v,
+                                                    const double2* __restrict__ om, const double2* __restrict__ dv,
+                                                    const double* __restrict__ U1, const double* __restrict__ U3,
+                                                    double2* u1o, double2* u3o, double2* om1o, double2* om3o) { pre_body<YDF, true>(g, t, v, om, dv, U1, U3, u1o, u3o, om1o, om3o, blockIdx.x); }
 
 // ---------------------------------------------------------------------------
 // a5: N_omega2 = i k3 H1 - i k1 H3, N_chi = -D1(i k1 H1 + i k3 H3) - k^2 H2.
@@ -1117,7 +1128,7 @@ static Geo geo(const chan_s* h) {
   Geo g;
   g.Nx = h->Nx; g.Ny = h->Ny; g.Nz = h->Nz; g.nxh = h->nxh; g.M = h->M; g.C = h->C;
   g.L1 = h->L1; g.L3 = h->L3; g.dt = h->dt; g.nu = h->nu; g.k1 = h->k1; g.k3 = h->k3;
-  g.pair = h->prec == CHAN_PREC_F64X;
+  g.pair = prec_pairs(h->prec);
   g.gtab = h->ytab > 0 || (h->ytab < 0 && 23 * (size_t)h->Ny * sizeof(double) > 48 * 1024);
   return g;
 }
@@ -1137,14 +1148,14 @@ static double* helm_slot(const chan_s* h, int s) {
 }
 static const void* helm_slot_y(const chan_s* h, int s) {
   const size_t o = h->lean ? 0 : (size_t)s * h->Ny * 11 * h->C;
-  return h->prec == CHAN_PREC_F64X ? (const void*)(h->helm_df + o) : (const void*)(h->helm + o);
+  return prec_pairs(h->prec) ? (const void*)(h->helm_df + o) : (const void*)(h->helm + o);
 }
 static const void* infl_slot_y(const chan_s* h, int s) {
   const size_t o = h->lean ? 0 : (size_t)s * 4 * h->C;
-  return h->prec == CHAN_PREC_F64X ? (const void*)(h->infl_df + o) : (const void*)(h->infl + o);
+  return prec_pairs(h->prec) ? (const void*)(h->infl_df + o) : (const void*)(h->infl + o);
 }
 static const void* pois_y(const chan_s* h) {
-  return h->prec == CHAN_PREC_F64X ? (const void*)h->pois_df : (const void*)h->pois;
+  return prec_pairs(h->prec) ? (const void*)h->pois_df : (const void*)h->pois;
 }
 static const int kYThreads = 128;
 // Shared memory of a sweep kernel that stages per_y table values per y point (0 when
@@ -1164,7 +1175,7 @@ static cudaError_t smem_attr(const void* fn, size_t bytes) {
   return cudaSuccess;
 }
 
-static bool use_df(const chan_s* h) { return h->prec == CHAN_PREC_F64X; }
+static bool use_df(const chan_s* h) { return prec_pairs(h->prec); }
 
 // Helmholtz factors, homogeneous solutions and influence matrices of substeps
 // s0 .. s0+ns-1 into slots 0 .. ns-1 (and their pair copies in the double-float mode).
@@ -1230,11 +1241,15 @@ cudaError_t launch_derive(chan_s* h) {
 
 cudaError_t launch_pre(chan_s* h, double2* u1, double2* u3, double2* om1, double2* om3, bool f32) {
   size_t sm = ysm(h, 14);
-  f32 = f32 && h->prec == CHAN_PREC_MIXED;
-  const void* fn = use_df(h) ? (const void*)k_pre_df : (f32 ? (const void*)k_pre_f32 : (const void*)k_pre);
+  f32 = f32 && prec_t32(h->prec);
+  const bool df = use_df(h);
+  const void* fn = df ? (f32 ? (const void*)k_pre_df_f32 : (const void*)k_pre_df)
+                      : (f32 ? (const void*)k_pre_f32 : (const void*)k_pre);
   cudaError_t e = smem_attr(fn, sm);
   if (e != cudaSuccess) return e;
-  if (use_df(h))
+  if (df && f32)
+    k_pre_df_f32<<<ygrid(h), kYThreads, sm, h->stream>>>(geo(h), ytabs(h), h->v, h->om, h->dv, h->U1, h->U3, u1, u3, om1, om3);
+  else if (df)
     k_pre_df<<<ygrid(h), kYThreads, sm, h->stream>>>(geo(h), ytabs(h), h->v, h->om, h->dv, h->U1, h->U3, u1, u3, om1, om3);
   else if (f32)
     k_pre_f32<<<ygrid(h), kYThreads, sm, h->stream>>>(geo(h), ytabs(h), h->v, h->om, h->dv, h->U1, h->U3, u1, u3, om1, om3);
@@ -1336,11 +1351,13 @@ cudaError_t launch_pre_batch(chan_s* const* hs, int n, const BatchWork* w, cudaS
   }
   const int blocks = fill_begin(B, hs, n);
   const size_t sm = ysm_batch(hs, n, 14);
-  const bool df = use_df(hs[0]), f32 = hs[0]->prec == CHAN_PREC_MIXED;
-  const void* fn = df ? (const void*)kb_pre<YDF> : (f32 ? (const void*)kb_pre<YF64, true> : (const void*)kb_pre<YF64>);
+  const bool df = use_df(hs[0]), f32 = prec_t32(hs[0]->prec);
+  const void* fn = df ? (f32 ? (const void*)kb_pre<YDF, true> : (const void*)kb_pre<YDF>)
+                      : (f32 ? (const void*)kb_pre<YF64, true> : (const void*)kb_pre<YF64>);
   cudaError_t e = smem_attr(fn, sm);
   if (e != cudaSuccess) return e;
-  if (df) kb_pre<YDF><<<blocks, kYThreads, sm, st>>>(B);
+  if (df && f32) kb_pre<YDF, true><<<blocks, kYThreads, sm, st>>>(B);
+  else if (df) kb_pre<YDF><<<blocks, kYThreads, sm, st>>>(B);
   else if (f32) kb_pre<YF64, true><<<blocks, kYThreads, sm, st>>>(B);
   else kb_pre<YF64><<<blocks, kYThreads, sm, st>>>(B);
   return cudaGetLastError();

@@ -78,6 +78,27 @@ def test_footprint_of_the_large_grids():
     assert small > (6 + 18) * n * 16 + 12 * 257 * 576 * 192 * 16
 
 
+def test_init_rejects_an_unknown_precision():
+    lib = chan.library()
+    o = chan.chan_opts()
+    lib.chan_opts_default(ctypes.byref(o))
+    o.re_tau, o.Lx, o.Lz, o.Nx, o.Ny, o.Nz, o.dt = 180.0, 3.14, 1.57, 32, 49, 32, 1e-3
+    o.precision = 4
+    h = ctypes.c_void_p()
+    assert lib.chan_init_ex(ctypes.byref(h), ctypes.byref(o)) == chan.CHAN_EINVAL
+    assert not h.value
+    assert "precision" in lib.chan_last_error(None).decode()
+
+
+def test_footprint_orders_the_modes():
+    """Pair storage adds the pair copies of the implicit-step tables; FP32 transforms halve
+    the mixed-layout fields.  Same box, same slab choice: FP64 < F64X and MIXED < MIXED_DF."""
+    for args in ((384, 257, 384), (96, 97, 64)):
+        f = [chan.footprint_bytes(*args, p) for p in range(4)]
+        assert f[chan.CHAN_PREC_FP64] < f[chan.CHAN_PREC_F64X]
+        assert f[chan.CHAN_PREC_MIXED] < f[chan.CHAN_PREC_MIXED_DF]
+
+
 def test_init_rejects_an_unknown_table_placement():
     lib = chan.library()
     o = chan.chan_opts()

@@ -13,7 +13,7 @@ pytestmark = pytest.mark.gpu
 CFG = (250.0, 2.0, 1.3, 24, 33, 36, 1e-3)
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
 def test_restart_is_bitwise(prec):
     import paper_1808_06461_b300 as chan
     re, Lx, Lz, Nx, Ny, Nz, dt = CFG

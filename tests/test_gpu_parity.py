@@ -238,11 +238,13 @@ def test_orr_sommerfeld_growth_gpu(chan):
     assert abs(growth - c_ref) < 0.01 * c_ref, growth
 
 
-def test_mixed_precision_error(chan, ten_steps):
-    """FP32 transforms and products, FP64 y-solves: stated error against the FP64 oracle."""
+@pytest.mark.parametrize("prec", [1, 3])
+def test_mixed_precision_error(chan, ten_steps, prec):
+    """FP32 transforms and products with FP64 (mode 1) or double-float (mode 3) wall-normal
+    sweeps: stated error against the FP64 oracle."""
     name = "re180_32x49x32"
     s0, ref = ten_steps[name]
-    ch = make(chan, name, precision=chan.CHAN_PREC_MIXED)
+    ch = make(chan, name, precision=prec)
     ch.set_state(s0["v"], s0["omega2"], s0["U1"], s0["U3"])
     ch.step(10)
     g = ch.get_state()
@@ -253,7 +255,7 @@ def test_mixed_precision_error(chan, ten_steps):
 
 @pytest.mark.parametrize("name", list(CASES))
 def test_double_float_mode_parity(chan, name, ten_steps):
-    """Double-float (FP32-pair) transforms and products, FP64 y-solves: same 1e-10 bar."""
+    """Double-float (FP32-pair) transforms, products and substep sweeps: same 1e-10 bar."""
     st = setup(name)
     s0, ref = ten_steps[name]
     ch = make(chan, name, precision=chan.CHAN_PREC_F64X)
@@ -292,7 +294,7 @@ def test_parity_on_the_optimised_mesh(chan):
         assert rel(g[k], ref[k]) < TOL, (k, rel(g[k], ref[k]))
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
 def test_zero_state_stays_exactly_zero(chan, prec):
     """The empty flow (no velocity, no mean profile) is a fixed point in every mode,
     and the filter outputs and statistics of it are exactly zero."""

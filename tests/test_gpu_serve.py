@@ -33,7 +33,7 @@ def test_graph_replay_is_bitwise_equal_to_single_launches():
 
 def test_footprint_matches_allocation():
     import paper_1808_06461_b300 as chan
-    for prec in (chan.CHAN_PREC_FP64, chan.CHAN_PREC_MIXED, chan.CHAN_PREC_F64X):
+    for prec in (chan.CHAN_PREC_FP64, chan.CHAN_PREC_MIXED, chan.CHAN_PREC_F64X, chan.CHAN_PREC_MIXED_DF):
         ch = chan.Channel(395.0, math.pi, math.pi / 2, 64, 97, 32, 1e-3, precision=prec)
         s0 = SY.perturbed_poiseuille(ch.grid(), 395.0, math.pi, math.pi / 2, 64, 32, seed=1, amp=0.1)
         ch.set_state(s0["v"], s0["omega2"], s0["U1"], s0["U3"])
@@ -42,7 +42,7 @@ def test_footprint_matches_allocation():
         ch.close()
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
 def test_results_alone_and_in_the_mix_are_identical(prec):
     """Each run's final state is bitwise the same served alone (one slot) or in a mix (four slots)."""
     from paper_1808_06461_b300.serve import Request, Server, channel_factory, serving_dt
@@ -84,7 +84,7 @@ def test_packed_batch_step_is_bitwise_equal_to_per_run_steps():
         assert a.substeps() == p.substeps() == 12 and a.time() == p.time()
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
 def test_packed_serving_alone_and_in_the_mix_are_identical(prec):
     from paper_1808_06461_b300.serve import Request, Server, channel_factory, serving_dt
     shapes = [(32, 49, 32, 180.0), (64, 49, 32, 395.0), (32, 97, 64, 550.0), (64, 49, 64, 180.0)]

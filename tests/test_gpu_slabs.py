@@ -43,7 +43,7 @@ def _run(chan, cfg, prec, slab, lean=-1, ytab=2):
     return out
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
 @pytest.mark.parametrize("name", list(CASES))
 def test_slabs_and_lean_tables_are_bitwise_invisible(name, prec):
     import paper_1808_06461_b300 as chan
