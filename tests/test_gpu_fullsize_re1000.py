@@ -1,5 +1,5 @@
 """Parity at the Re_tau = 1000, 768 x 385 x 768 workload (Lx = 2 pi, Lz = pi,
-dt = 1e-4), in FP64 and in the mixed mode the workload is run in.
+dt = 1e-4), in FP64, double-float and the two mixed modes the workload is run in.
 
 The dealiased non-linear term is plane-local, so the oracle computes it on
 sampled x-z planes (padded 1152 x 1152 transforms) from the same state.
@@ -40,12 +40,13 @@ def ref():
 
 
 # FP64: both sides evaluate the same dealiased products in FP64 (rounding order only);
-# mixed: FP32 transforms and products, the state and wall-normal operators in FP64.
+# double-float: pair transforms (~2^-47 per operation); mixed modes: FP32 transforms and
+# products, the state and wall-normal operators in FP64 (mode 1) or pairs (mode 3).
 # hsym: the kx = 0 plane is Hermitian in kz up to the rounding of the z transforms of
 # real rows (unit roundoff 1.1e-16 in FP64, 6e-8 in FP32), entering through dt N (|N| up
 # to 1e3 at the high wavenumbers) over three substeps; the x-pass drops the imaginary part
 # of the kx = 0 column each substep, so the departure does not accumulate.
-@pytest.mark.parametrize("prec,tol,hsym", [(0, 1e-12, 1e-12), (1, 2e-5, 1e-7)])
+@pytest.mark.parametrize("prec,tol,hsym", [(0, 1e-12, 1e-12), (2, 1e-11, 1e-11), (1, 2e-5, 1e-7), (3, 2e-5, 1e-7)])
 def test_re1000_nonlinear_sampled_planes_and_invariants(ref, prec, tol, hsym):
     import torch
     import paper_1808_06461_b300 as chan
