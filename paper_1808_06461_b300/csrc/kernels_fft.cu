@@ -7,8 +7,10 @@
 // physical z-rows at once into real space (two real rows packed into one
 // complex FFT), forms the products there and transforms them back, and a
 // final z-pass truncates to the stored modes.  All transforms are in-CTA,
-// in-place mixed-radix (3, 4, 2) shared-memory FFTs: decimation in frequency
-// for the inverse transforms, decimation in time for the forward ones.
+// in-place mixed-radix (3, 4, 2) shared-memory FFTs with natural-order spectra
+// and digit-reversed physical samples: Cooley-Tukey stages with FMA twiddle
+// steps in FP64 and FP32, decimation in frequency (inverse) and in time
+// (forward) for the double-float pairs.
 #include <cstring>
 #include <type_traits>
 
@@ -188,9 +190,10 @@ template <int DIR, typename T2> __device__ __forceinline__ void dft3_nomid(T2* v
   v[2] = csub(mm, r);
 }
 
-// In-place mixed-radix FFT stages.  The inverse transforms (spectral ->
-// physical) are decimation in frequency (DIF): natural-order input,
-// digit-reversed output.  The forward transforms are decimation in time
+// In-place mixed-radix FFT stages of the double-float transforms (the FP64 and
+// FP32 ones use the Cooley-Tukey stages further down, with the same slots).
+// The inverse transforms (spectral -> physical) are decimation in frequency
+// (DIF): natural-order input, digit-reversed output.  The forward transforms are decimation in time
 // (DIT) with the radices in reverse order: digit-reversed input, natural
 // output.  Physical-space data (the z rows of the mixed buffer, the x
 // samples of the x-pass) therefore stay in digit-reversed order, which the
@@ -208,7 +211,7 @@ template <int DIR, typename T2> __device__ __forceinline__ void dft3_nomid(T2* v
 // with m = 1 (every j is 0).  With m > 1 the butterflies with j = 0 multiply by
 // tw[0] = 1 (exact) rather than branch: a warp holding one of them would run the
 // twiddles for the others anyway, and the compiler predicates a short branch,
-// which still takes FP64 issue slots.
+// which still takes issue slots.
 template <int R, int DIR, bool ZMID, bool TW, typename T2>
 __device__ __forceinline__ void dif_loop(T2* a, int L, int nb, int ld, const T2* __restrict__ tw, int Ls,
                                          unsigned mag_nbf, unsigned mag_m) {
