@@ -140,7 +140,7 @@ int chan_optimize_mesh(const chan_opts* o, int iters, double C, double* y, doubl
 
 /*
  * Autotuner (no paper counterpart): times the z-pass with 1, 2, 4, 8 and 16
- * columns per CTA, the x-pass with 128, 256 and 512 threads per CTA, and the
+ * columns per CTA, the x-pass with 128, 192, 256, 288, 384 and 512 threads per CTA, and the
  * wall-normal sweeps with their mode-independent tables staged in shared
  * memory or read in place from global memory, on the current state; keeps
  * the fastest and caches the choice for every later handle of the same

@@ -1051,10 +1051,14 @@ int chan_autotune(chan_t h) {
     h->kb_z = best_kb;
     // x-pass alone (fresh inputs from an untimed z-pass before each run); the default
     // 256 threads stay unless another shape is more than 2 % faster
-    float t_nt[3] = {1e30f, 1e30f, 1e30f};
-    const int nts[3] = {128, 256, 512};
+    // (192, 288 and 384 divide the butterfly counts of the 576-point stages: no ragged
+    // last round of a stage loop)
+    constexpr int NNT = 6;
+    float t_nt[NNT];
+    for (float& t : t_nt) t = 1e30f;
+    const int nts[NNT] = {256, 128, 192, 288, 384, 512};
     for (int rep = 0; rep < 5; ++rep)
-      for (int k = 0; k < 3; ++k) {
+      for (int k = 0; k < NNT; ++k) {
         h->xthreads = nts[k];
         CK(launch_zinv(h, in, nullptr, mx, 6, ny, 0));
         CK(cudaEventRecord(e0, h->stream));
@@ -1065,9 +1069,9 @@ int chan_autotune(chan_t h) {
         CK(cudaEventElapsedTime(&ms, e0, e1));
         t_nt[k] = ms < t_nt[k] ? ms : t_nt[k];
       }
-    int bk = 1;   // 256 threads
-    for (int k : {0, 2})
-      if (t_nt[k] < 0.98f * t_nt[bk]) bk = k;
+    int bk = 0;   // 256 threads
+    for (int k = 1; k < NNT; ++k)
+      if (t_nt[k] < 0.98f * t_nt[0] && t_nt[k] < t_nt[bk]) bk = k;
     best_nt = nts[bk];
     h->xthreads = best_nt;
     // wall-normal sweeps: y tables staged in shared memory or read in place (work slots only)
