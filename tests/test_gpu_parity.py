@@ -147,6 +147,35 @@ def test_filter_and_stats_parity(chan, kind, p, ten_steps):
     assert np.abs(out[2:8] - out[8:14] - out[14:20]).max() < 1e-12 * scale
 
 
+# Filter from the oracle's state after 10 substeps, in every mode: ubar_i = G u_i is formed
+# from the stored state (FP64 or pairs) in all modes; tau_ij and the statistics rows of
+# <tau_ij> carry the precision of the products.  Mixed modes: FP32 products, unit roundoff
+# 6e-8 relative to u_i u_j, which is 1e2-1e3 times tau_ij in this flow (measured 5e-5 to 7e-5
+# relative L2 on tau, 1e-7 of the <u_i u_j> scale on the statistics rows); bars 1e-3 and 1e-5.
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+@pytest.mark.parametrize("kind,p", [(0, (120.0, 60.0)), (1, (50.0, 50.0))])
+def test_filter_and_stats_every_mode(chan, kind, p, prec, ten_steps):
+    name = "re180_32x49x32"
+    st = setup(name)
+    _, ref = ten_steps[name]
+    ch = make(chan, name, precision=prec)
+    ch.set_state(ref["v"], ref["omega2"], ref["U1"], ref["U3"])
+    ub, tau = ch.filter_stresses(kind, *p)
+    out, utau, ubulk, _ = ch.stats()
+    ub_ref, tau_ref = O.filter_stresses(st, ref, kind, *p)
+    out_ref, utau_ref, ubulk_ref = O.stats(st, ref, ub_ref, tau_ref)
+    scale = np.abs(out_ref[2:8]).max()
+    mixed = prec in (chan.CHAN_PREC_MIXED, chan.CHAN_PREC_MIXED_DF)
+    tol_tau, tol_stat = (1e-3, 1e-5) if mixed else (TOL, TOL)
+    for f in range(3):
+        assert rel(ub[f], ub_ref[f]) < 1e-12, (f, rel(ub[f], ub_ref[f]))
+    for q in range(6):
+        assert rel(tau[q], tau_ref[q]) < tol_tau, (q, rel(tau[q], tau_ref[q]))
+    assert np.abs(out - out_ref).max() < tol_stat * scale
+    assert np.abs(out[2:8] - out[8:14] - out[14:20]).max() < (tol_stat if mixed else 1e-12) * scale
+    assert abs(utau - utau_ref) < TOL * utau_ref and abs(ubulk - ubulk_ref) < TOL * ubulk_ref
+
+
 @pytest.mark.parametrize("kind,p", [(0, (120.0, 60.0)), (1, (50.0, 50.0))])
 def test_filtered_enstrophy_parity(chan, kind, p, ten_steps):
     name = "re180_32x49x32"
