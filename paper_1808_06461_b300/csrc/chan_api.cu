@@ -247,6 +247,7 @@ size_t footprint_ex(int Nx, int Ny, int Nz, int prec, int slab_req, int lean) {
   if (prec_pairs(prec))
     b += ((size_t)Ny * 7 * C + nslot * (size_t)Ny * 11 * C + nslot * 4 * C + 30 * (size_t)Ny) * sizeof(dfr);
   b += (L1 + L3) * (prec_t32(prec) ? sizeof(float2) : sizeof(double2));             // twiddles
+  b += (L1 + L3) * sizeof(int);                                                              // block twiddle exponents
   const size_t S = slab_planes(Nx, Ny, Nz, prec, slab_req);
   b += (size_t)NWF * n * sizeof(double2);                                                    // work fields
   b += 12 * S * L3 * nxh * es;                                                               // mixed fields
@@ -562,6 +563,29 @@ int chan_init_ex(chan_t* out, const chan_opts* o) {
         CK(cudaMemcpy(d, twf.data(), L * sizeof(float2), cudaMemcpyHostToDevice));
       }
       (which ? h->tw3 : h->tw1) = d;
+    }
+    // block twiddle exponents of the inverse transform stages (fewer than L per plan)
+    for (FftPlan* pl : {&h->p1, &h->p3}) {
+      std::vector<int> tab;
+      int Ls = pl->L, P = 1;
+      for (int s = 0; s < pl->np; ++s) {
+        const int R = pl->radix[s], m = Ls / R, nblk = pl->L / Ls;
+        pl->revoff[s] = (int)tab.size();
+        for (int b = 0; b < nblk; ++b) {
+          int K = 0, bb = b, w = P;
+          for (int i = s - 1; i >= 0; --i) {   // least significant digit of b = radix of stage s-1
+            w /= pl->radix[i];
+            K += (bb % pl->radix[i]) * w;
+            bb /= pl->radix[i];
+          }
+          tab.push_back(K * m);
+        }
+        Ls = m;
+        P *= R;
+      }
+      int* d = dalloc<int>(h, pl->L);
+      CK(cudaMemcpy(d, tab.data(), tab.size() * sizeof(int), cudaMemcpyHostToDevice));
+      pl->revK = d;
     }
     // work
     h->nwf = NWF;

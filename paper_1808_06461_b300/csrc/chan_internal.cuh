@@ -51,6 +51,11 @@ struct FftPlan {
   // operand n and divisor d with n d < 2^32; 0 stands for d = 1): L/R, and the span
   // Ls/R of the DIF and DIT stage
   unsigned mag_nbf[16], mag_mdif[16], mag_mdit[16];
+  // inverse (natural in, digit-reversed out) Cooley-Tukey stages: twiddle exponent unit
+  // K m of block b of stage s at revK[revoff[s] + b] (K the digit reversal of b over the
+  // radices of stages 0 .. s-1, m = Ls/R); device table of at most L entries
+  const int* revK;
+  int revoff[16];
 };
 
 enum { KID_PRE = 0, KID_ZINV, KID_XPASS, KID_ZFWD, KID_NONLIN, KID_HELM, KID_POISSON, KID_MEAN,

@@ -345,6 +345,7 @@ __device__ void fft_dit(T2* a, int L, int nb, int ld, const T2* __restrict__ tw,
 // blocks of size m = Ls/R.  Input r of block b is scaled by w_L^(DIR r K m), where K
 // is the digit reversal of b over the radices already applied (K = 0 for the single
 // block of the first stage, which therefore has no twiddles); then the radix-R DFT.
+// K m is read from a per-plan table built at set-up (FftPlan::revK).
 // Double-float transforms keep the DIF / DIT stages: a pair product is not one fused
 // operation, so the rewrite would save nothing there.
 
@@ -398,26 +399,13 @@ template <int DIR, bool NOMID, typename T2> __device__ __forceinline__ void ct3(
   v[2].y = fmaT(g, d.x, mm.y);
 }
 
-// Digit reversal of block b over the radices of stages 0..s-1; P = R_0 ... R_(s-1).
-__device__ __forceinline__ int block_rev(int b, const FftPlan& pl, int s, int P) {
-  int K = 0;
-  for (int i = s - 1; i >= 0; --i) {
-    const int Ri = pl.radix[i];
-    const int bq = Ri == 3 ? (int)__umulhi((unsigned)b, 0x55555556u) : b >> (Ri >> 1);   // b / Ri (b < 2^31)
-    P = Ri == 3 ? (int)__umulhi((unsigned)P, 0x55555556u) : P >> (Ri >> 1);              // R_0 ... R_(i-1)
-    K += (b - bq * Ri) * P;
-    b = bq;
-  }
-  return K;
-}
-
 // One Cooley-Tukey stage.  NR: inverse (block twiddles, block size Ls shrinking); else
 // forward (twiddle of butterfly j is w_Ls^(DIR j)).  Z = 1: the middle input is zero
 // (first inverse stage of a padded transform); Z = 2: the middle output is dropped
 // (last forward stage before the truncation).  TW = false: every twiddle is 1.
 template <int R, int DIR, int Z, bool TW, bool NR, typename T2>
 __device__ __forceinline__ void ct_loop(T2* a, int L, int nb, int ld, const T2* __restrict__ tw, int Ls,
-                                        unsigned mag_nbf, unsigned mag_m, const FftPlan& pl, int s, int P) {
+                                        unsigned mag_nbf, unsigned mag_m, const FftPlan& pl, int s) {
   const int m = Ls / R;
   const int nbf = L / R;
   const int tmul = L / Ls;
@@ -432,7 +420,7 @@ __device__ __forceinline__ void ct_loop(T2* a, int L, int nb, int ld, const T2* 
 #pragma unroll
     for (int q = 0; q < R; ++q) v[q] = (Z == 1 && q == 1) ? zero2<T2>() : x[q * m];
     if (TW) {
-      const int e = NR ? block_rev(blk, pl, s, P) * m : j * tmul;
+      const int e = NR ? pl.revK[pl.revoff[s] + blk] : j * tmul;
       T2 w = tw[e], w2 = R == 2 ? w : tw[2 * e];
       if (DIR > 0) { w.y = -w.y; w2.y = -w2.y; }
       if (R == 4) ct4<DIR>(v, w, w2);
@@ -462,22 +450,21 @@ __device__ void fft_inv(T2* a, int L, int nb, int ld, const T2* __restrict__ tw,
   if constexpr (IsPair<T2>::v) {
     fft_dif<DIR>(a, L, nb, ld, tw, pl, zmid);
   } else {
-    int Ls = L, P = 1;
+    int Ls = L;
     for (int s = 0; s < pl.np; ++s) {
       const int R = pl.radix[s];
       const unsigned mn = pl.mag_nbf[s], mm = pl.mag_mdif[s];
       if (s == 0) {   // one block, K = 0
-        if (R == 4) ct_loop<4, DIR, 0, false, true>(a, L, nb, ld, tw, Ls, mn, mm, pl, s, P);
-        else if (R == 2) ct_loop<2, DIR, 0, false, true>(a, L, nb, ld, tw, Ls, mn, mm, pl, s, P);
-        else if (zmid) ct_loop<3, DIR, 1, false, true>(a, L, nb, ld, tw, Ls, mn, mm, pl, s, P);
-        else ct_loop<3, DIR, 0, false, true>(a, L, nb, ld, tw, Ls, mn, mm, pl, s, P);
+        if (R == 4) ct_loop<4, DIR, 0, false, true>(a, L, nb, ld, tw, Ls, mn, mm, pl, s);
+        else if (R == 2) ct_loop<2, DIR, 0, false, true>(a, L, nb, ld, tw, Ls, mn, mm, pl, s);
+        else if (zmid) ct_loop<3, DIR, 1, false, true>(a, L, nb, ld, tw, Ls, mn, mm, pl, s);
+        else ct_loop<3, DIR, 0, false, true>(a, L, nb, ld, tw, Ls, mn, mm, pl, s);
       } else {
-        if (R == 4) ct_loop<4, DIR, 0, true, true>(a, L, nb, ld, tw, Ls, mn, mm, pl, s, P);
-        else if (R == 2) ct_loop<2, DIR, 0, true, true>(a, L, nb, ld, tw, Ls, mn, mm, pl, s, P);
-        else ct_loop<3, DIR, 0, true, true>(a, L, nb, ld, tw, Ls, mn, mm, pl, s, P);
+        if (R == 4) ct_loop<4, DIR, 0, true, true>(a, L, nb, ld, tw, Ls, mn, mm, pl, s);
+        else if (R == 2) ct_loop<2, DIR, 0, true, true>(a, L, nb, ld, tw, Ls, mn, mm, pl, s);
+        else ct_loop<3, DIR, 0, true, true>(a, L, nb, ld, tw, Ls, mn, mm, pl, s);
       }
       Ls /= R;
-      P *= R;
     }
   }
 }
@@ -495,15 +482,15 @@ __device__ void fft_fwd(T2* a, int L, int nb, int ld, const T2* __restrict__ tw,
       Ls *= R;
       const unsigned mn = pl.mag_nbf[s], mm = pl.mag_mdit[s];
       if (mm == 0) {   // m = 1: every twiddle is 1
-        if (R == 4) ct_loop<4, DIR, 0, false, false>(a, L, nb, ld, tw, Ls, mn, mm, pl, s, 0);
-        else if (R == 2) ct_loop<2, DIR, 0, false, false>(a, L, nb, ld, tw, Ls, mn, mm, pl, s, 0);
-        else if (s == 0 && zmid) ct_loop<3, DIR, 2, false, false>(a, L, nb, ld, tw, Ls, mn, mm, pl, s, 0);
-        else ct_loop<3, DIR, 0, false, false>(a, L, nb, ld, tw, Ls, mn, mm, pl, s, 0);
+        if (R == 4) ct_loop<4, DIR, 0, false, false>(a, L, nb, ld, tw, Ls, mn, mm, pl, s);
+        else if (R == 2) ct_loop<2, DIR, 0, false, false>(a, L, nb, ld, tw, Ls, mn, mm, pl, s);
+        else if (s == 0 && zmid) ct_loop<3, DIR, 2, false, false>(a, L, nb, ld, tw, Ls, mn, mm, pl, s);
+        else ct_loop<3, DIR, 0, false, false>(a, L, nb, ld, tw, Ls, mn, mm, pl, s);
       } else {
-        if (R == 4) ct_loop<4, DIR, 0, true, false>(a, L, nb, ld, tw, Ls, mn, mm, pl, s, 0);
-        else if (R == 2) ct_loop<2, DIR, 0, true, false>(a, L, nb, ld, tw, Ls, mn, mm, pl, s, 0);
-        else if (s == 0 && zmid) ct_loop<3, DIR, 2, true, false>(a, L, nb, ld, tw, Ls, mn, mm, pl, s, 0);
-        else ct_loop<3, DIR, 0, true, false>(a, L, nb, ld, tw, Ls, mn, mm, pl, s, 0);
+        if (R == 4) ct_loop<4, DIR, 0, true, false>(a, L, nb, ld, tw, Ls, mn, mm, pl, s);
+        else if (R == 2) ct_loop<2, DIR, 0, true, false>(a, L, nb, ld, tw, Ls, mn, mm, pl, s);
+        else if (s == 0 && zmid) ct_loop<3, DIR, 2, true, false>(a, L, nb, ld, tw, Ls, mn, mm, pl, s);
+        else ct_loop<3, DIR, 0, true, false>(a, L, nb, ld, tw, Ls, mn, mm, pl, s);
       }
     }
   }
@@ -554,8 +541,10 @@ __device__ __forceinline__ void zinv_body(const ZArgs& A, const typename V2<T>::
   T2* a = reinterpret_cast<T2*>(smraw);
   const int f = bz, y = by, kx0 = bx * A.KB;
   const int hz = A.Nz / 2;
-  for (int e = threadIdx.x; e < A.KB * A.ld; e += blockDim.x) a[e] = zero2<T2>();
-  __syncthreads();
+  // The first stage skips the middle third of each padded column, and the load below
+  // writes every other slot except the dropped kz Nyquist row at 2 L3/3: only that one
+  // is zeroed (no conflict with the loads, so no barrier in between).
+  for (int kl = threadIdx.x; kl < A.KB; kl += blockDim.x) a[kl * A.ld + (A.L3 - hz)] = zero2<T2>();
   const bool f32 = (A.f32_mask >> f) & 1;
   const double2* in = A.in[f] + (size_t)y * A.M;
   const float2* in32 = reinterpret_cast<const float2*>(A.in[f]) + (size_t)y * A.M;
@@ -648,8 +637,9 @@ __device__ __forceinline__ void xpass_body(const XArgs& A, const typename V2<T>:
   const int z0 = 2 * bx, y = by;
   const int L1 = A.L1, nxh = A.nxh, ld = A.ld;
   const size_t rowoff = ((size_t)y * A.L3 + z0) * nxh;   // rows z0, z0 + 1 of plane y
-  for (int e = threadIdx.x; e < NIN * ld; e += blockDim.x) a[e] = zero2<T2>();
-  __syncthreads();
+  // The first stage skips the middle third [nxh, 2 nxh) and the packing below writes every
+  // other slot except the dropped kx Nyquist slot 2 nxh: only that one is zeroed.
+  for (int f = threadIdx.x; f < NIN; f += blockDim.x) a[f * ld + 2 * nxh] = zero2<T2>();
   // pack rows z0 (real part) and z0+1 (imaginary part) with Hermitian extension in kx
   for (int e = threadIdx.x; e < NIN * nxh; e += blockDim.x) {
     const int f = A.mag_nxh ? (int)__umulhi((unsigned)e, A.mag_nxh) : e, k = e - f * nxh;   // e / nxh
