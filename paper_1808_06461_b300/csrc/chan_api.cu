@@ -446,7 +446,7 @@ int chan_init_ex(chan_t* out, const chan_opts* o) {
   if (o->y_tables < 0 || o->y_tables > 2) return bad(nullptr, "chan_init: y_tables must be 0, 1 or 2");
   const int L1 = 3 * o->Nx / 2, L3 = 3 * o->Nz / 2;
   const size_t es = prec_t32(o->precision) ? 8 : 16;
-  if (2 * 6 * (size_t)(L1 + 1) * es > 227 * 1024 || 2 * (size_t)(L3 + 1) * es > 100 * 1024)
+  if (2 * 6 * (size_t)fft_ld(L1, es) * es > 227 * 1024 || 2 * (size_t)fft_ld(L3, es) * es > 100 * 1024)
     return bad(nullptr, "chan_init: 3Nx/2 or 3Nz/2 too long for an in-block transform at this precision "
                         "(FP64 and double-float: Nx <= 768, the two mixed modes: Nx <= 1536)");
   chan_s* h = new (std::nothrow) chan_s();
@@ -1067,7 +1067,7 @@ int chan_autotune(chan_t h) {
     int best_kb = pick_kb(h->nxh, h->L3, es), best_nt = 256;
     float best_t = 1e30f;
     for (int kb = 1; kb <= 16 && kb <= h->nxh; kb *= 2) {
-      if ((size_t)kb * (h->L3 + 1) * es > 110 * 1024) break;
+      if ((size_t)kb * fft_ld(h->L3, es) * es > 110 * 1024) break;
       h->kb_z = kb;
       float t = timed([&] { CK(launch_zinv(h, in, nullptr, mx, 6, ny, 0)); });
       if (t < best_t) { best_t = t; best_kb = kb; }

@@ -199,3 +199,5 @@ cudaError_t launch_zfwd(chan_s* h, void* const* in, double2* const* out, int nf,
 cudaError_t fft_configure(chan_s* h);
 // Default z-pass columns per CTA: as many as fit 56 KB of shared memory, at most 16.
 int pick_kb(int nxh, int L3, size_t es);
+// Row stride (elements) of an in-CTA transform buffer of length L and element size es.
+int fft_ld(int L, size_t es);

@@ -53,6 +53,18 @@ template <typename T2> __device__ __forceinline__ T2 zero2() {
   return r;
 }
 
+// Shared-memory slot of element i of a transform buffer row.  FP32 rows are swizzled
+// within each 16-slot (128-byte) group: slot = i ^ 5 ((i >> 4) & 3).  The unit-span and
+// span-4 stages of a radix-4 transform then hit 16 different bank pairs per half warp
+// (unswizzled: 4-way conflicts, half of the FP32 passes' shared-memory wavefronts), and
+// contiguous runs stay contiguous.  Rows hold whole groups (row stride a multiple of 16
+// slots, plus one).  FP64 and pair transforms, bound by their arithmetic, keep i.
+template <typename T2> struct Swz { static constexpr bool v = false; };
+template <> struct Swz<float2> { static constexpr bool v = true; };
+template <typename T2> __device__ __forceinline__ int sw(int i) {
+  return Swz<T2>::v ? i ^ (((i >> 4) & 3) * 5) : i;
+}
+
 template <typename T2> __device__ __forceinline__ T2 mk(double x, double y) {
   typedef typename Scal<T2>::t T;
   T2 r;
@@ -415,10 +427,11 @@ __device__ __forceinline__ void ct_loop(T2* a, int L, int nb, int ld, const T2* 
     const int u = t - bi * nbf;
     const int blk = mag_m ? (int)__umulhi((unsigned)u, mag_m) : u;      // u / m (mag 0: m = 1)
     const int j = u - blk * m;
-    T2* x = a + bi * ld + blk * Ls + j;
+    T2* row = a + bi * ld;
+    const int ib = blk * Ls + j;
     T2 v[R];
 #pragma unroll
-    for (int q = 0; q < R; ++q) v[q] = (Z == 1 && q == 1) ? zero2<T2>() : x[q * m];
+    for (int q = 0; q < R; ++q) v[q] = (Z == 1 && q == 1) ? zero2<T2>() : row[sw<T2>(ib + q * m)];
     if (TW) {
       const int e = NR ? pl.revK[pl.revoff[s] + blk] : j * tmul;
       T2 w = tw[e], w2 = R == 2 ? w : tw[2 * e];
@@ -435,7 +448,7 @@ __device__ __forceinline__ void ct_loop(T2* a, int L, int nb, int ld, const T2* 
     }
 #pragma unroll
     for (int q = 0; q < R; ++q)
-      if (!(Z == 2 && q == 1)) x[q * m] = v[q];
+      if (!(Z == 2 && q == 1)) row[sw<T2>(ib + q * m)] = v[q];
   }
   __syncthreads();
 }
@@ -524,11 +537,12 @@ __device__ __forceinline__ void zinv_load(const ZArgs& A, T2* a, const double2* 
     const int q = jz * A.nxh + kx;
     const int pz = jz < hz ? jz : jz + (A.L3 - A.Nz);
     if constexpr (KIND == 2) {
-      if constexpr (std::is_same<T2, float2>::value) a[kl * A.ld + pz] = in32[q];
+      if constexpr (std::is_same<T2, float2>::value) a[kl * A.ld + sw<T2>(pz)] = in32[q];
     } else if constexpr (KIND >= 3) {
-      if constexpr (std::is_same<T2, float2>::value) a[kl * A.ld + pz] = ld_pair_f32(in, q, KIND == 4, KIND == 4 ? A.G[q] : 0.0);
+      if constexpr (std::is_same<T2, float2>::value)
+        a[kl * A.ld + sw<T2>(pz)] = ld_pair_f32(in, q, KIND == 4, KIND == 4 ? A.G[q] : 0.0);
     } else {
-      a[kl * A.ld + pz] = ld_fourier<T2>(in, q, KIND == 1, KIND == 1 ? A.G[q] : 0.0);
+      a[kl * A.ld + sw<T2>(pz)] = ld_fourier<T2>(in, q, KIND == 1, KIND == 1 ? A.G[q] : 0.0);
     }
   }
 }
@@ -544,7 +558,7 @@ __device__ __forceinline__ void zinv_body(const ZArgs& A, const typename V2<T>::
   // The first stage skips the middle third of each padded column, and the load below
   // writes every other slot except the dropped kz Nyquist row at 2 L3/3: only that one
   // is zeroed (no conflict with the loads, so no barrier in between).
-  for (int kl = threadIdx.x; kl < A.KB; kl += blockDim.x) a[kl * A.ld + (A.L3 - hz)] = zero2<T2>();
+  for (int kl = threadIdx.x; kl < A.KB; kl += blockDim.x) a[kl * A.ld + sw<T2>(A.L3 - hz)] = zero2<T2>();
   const bool f32 = (A.f32_mask >> f) & 1;
   const double2* in = A.in[f] + (size_t)y * A.M;
   const float2* in32 = reinterpret_cast<const float2*>(A.in[f]) + (size_t)y * A.M;
@@ -562,7 +576,7 @@ __device__ __forceinline__ void zinv_body(const ZArgs& A, const typename V2<T>::
   T2* out = reinterpret_cast<T2*>(A.out[f]) + (size_t)y * A.L3 * A.nxh;
   for (int e = threadIdx.x; e < A.L3 * A.KB; e += blockDim.x) {
     const int z = e >> A.lgKB, kl = e & (A.KB - 1), kx = kx0 + kl;
-    if (kx < A.nxh) out[z * A.nxh + kx] = a[kl * A.ld + z];   // 32-bit index within the plane
+    if (kx < A.nxh) out[z * A.nxh + kx] = a[kl * A.ld + sw<T2>(z)];   // 32-bit index within the plane
   }
 }
 
@@ -580,7 +594,7 @@ __device__ __forceinline__ void zfwd_store(const ZArgs& A, const T2* r, double2*
     if (kx >= A.nxh) continue;
     if (jz != hz) {
       const int pz = jz < hz ? jz : jz + (A.L3 - A.Nz);
-      st_fourier<T2>(out, jz * A.nxh + kx, r[kl * A.ld + pz], PAIR);
+      st_fourier<T2>(out, jz * A.nxh + kx, r[kl * A.ld + sw<T2>(pz)], PAIR);
     } else {
       out[jz * A.nxh + kx] = make_double2(0.0, 0.0);
     }
@@ -598,7 +612,7 @@ __device__ __forceinline__ void zfwd_body(const ZArgs& A, const typename V2<T>::
   const T2* in = reinterpret_cast<const T2*>(A.out[f]) + (size_t)y * A.L3 * A.nxh;
   for (int e = threadIdx.x; e < A.L3 * A.KB; e += blockDim.x) {
     const int z = e >> A.lgKB, kl = e & (A.KB - 1), kx = kx0 + kl;
-    a[kl * A.ld + z] = kx < A.nxh ? in[z * A.nxh + kx] : zero2<T2>();
+    a[kl * A.ld + sw<T2>(z)] = kx < A.nxh ? in[z * A.nxh + kx] : zero2<T2>();
   }
   __syncthreads();
   // digit-reversed rows in, natural kz out; the middle third (truncated) is not formed
@@ -639,7 +653,7 @@ __device__ __forceinline__ void xpass_body(const XArgs& A, const typename V2<T>:
   const size_t rowoff = ((size_t)y * A.L3 + z0) * nxh;   // rows z0, z0 + 1 of plane y
   // The first stage skips the middle third [nxh, 2 nxh) and the packing below writes every
   // other slot except the dropped kx Nyquist slot 2 nxh: only that one is zeroed.
-  for (int f = threadIdx.x; f < NIN; f += blockDim.x) a[f * ld + 2 * nxh] = zero2<T2>();
+  for (int f = threadIdx.x; f < NIN; f += blockDim.x) a[f * ld + sw<T2>(2 * nxh)] = zero2<T2>();
   // pack rows z0 (real part) and z0+1 (imaginary part) with Hermitian extension in kx
   for (int e = threadIdx.x; e < NIN * nxh; e += blockDim.x) {
     const int f = A.mag_nxh ? (int)__umulhi((unsigned)e, A.mag_nxh) : e, k = e - f * nxh;   // e / nxh
@@ -650,13 +664,13 @@ __device__ __forceinline__ void xpass_body(const XArgs& A, const typename V2<T>:
       T2 c0;
       c0.x = P.x;
       c0.y = Q.x;
-      dstf[0] = c0;
+      dstf[sw<T2>(0)] = c0;
     } else {
       T2 c1, c2;
       c1.x = P.x - Q.y; c1.y = P.y + Q.x;      // P_k + i Q_k
       c2.x = P.x + Q.y; c2.y = -P.y + Q.x;     // conj(P_k) + i conj(Q_k) at -k
-      dstf[k] = c1;
-      dstf[L1 - k] = c2;
+      dstf[sw<T2>(k)] = c1;
+      dstf[sw<T2>(L1 - k)] = c2;
     }
   }
   __syncthreads();
@@ -666,22 +680,23 @@ __device__ __forceinline__ void xpass_body(const XArgs& A, const typename V2<T>:
   T2* o = a;   // products overwrite their own sample slot (all fields share the order)
   for (int x = threadIdx.x; x < L1; x += blockDim.x) {
     T2 q[NIN];
+    const int xs = sw<T2>(x);
 #pragma unroll
-    for (int f = 0; f < NIN; ++f) q[f] = r[f * ld + x];
+    for (int f = 0; f < NIN; ++f) q[f] = r[f * ld + xs];
     if (MODE == 0) {
       // H1 = u2 w3 - u3 w2, H2 = u3 w1 - u1 w3, H3 = u1 w2 - u2 w1 (both rows at once)
       T2 h1, h2, h3;
       h1.x = mulu(q[1].x, q[5].x) - mulu(q[2].x, q[4].x); h1.y = mulu(q[1].y, q[5].y) - mulu(q[2].y, q[4].y);
       h2.x = mulu(q[2].x, q[3].x) - mulu(q[0].x, q[5].x); h2.y = mulu(q[2].y, q[3].y) - mulu(q[0].y, q[5].y);
       h3.x = mulu(q[0].x, q[4].x) - mulu(q[1].x, q[3].x); h3.y = mulu(q[0].y, q[4].y) - mulu(q[1].y, q[3].y);
-      o[0 * ld + x] = h1;
-      o[1 * ld + x] = h2;
-      o[2 * ld + x] = h3;
+      o[0 * ld + xs] = h1;
+      o[1 * ld + xs] = h2;
+      o[2 * ld + xs] = h3;
     } else if (MODE == 2) {
       T2 w;
       w.x = q[0].x * q[0].x + q[1].x * q[1].x + q[2].x * q[2].x;
       w.y = q[0].y * q[0].y + q[1].y * q[1].y + q[2].y * q[2].y;
-      o[x] = w;
+      o[xs] = w;
     } else {
       const int pi[6] = {0, 1, 2, 0, 0, 1}, pj[6] = {0, 1, 2, 1, 2, 2};
 #pragma unroll
@@ -689,7 +704,7 @@ __device__ __forceinline__ void xpass_body(const XArgs& A, const typename V2<T>:
         T2 w;
         w.x = q[pi[p]].x * q[pj[p]].x;
         w.y = q[pi[p]].y * q[pj[p]].y;
-        o[p * ld + x] = w;
+        o[p * ld + xs] = w;
       }
     }
   }
@@ -700,8 +715,8 @@ __device__ __forceinline__ void xpass_body(const XArgs& A, const typename V2<T>:
   const T half = from_d<T>(0.5 * A.scale);
   for (int e = threadIdx.x; e < NOUT * nxh; e += blockDim.x) {
     const int gq = A.mag_nxh ? (int)__umulhi((unsigned)e, A.mag_nxh) : e, k = e - gq * nxh;   // e / nxh
-    const T2 c = s[gq * ld + k];
-    const T2 cm = s[gq * ld + (k == 0 ? 0 : L1 - k)];
+    const T2 c = s[gq * ld + sw<T2>(k)];
+    const T2 cm = s[gq * ld + sw<T2>(k == 0 ? 0 : L1 - k)];
     T2 F, G;
     F.x = half * (c.x + cm.x); F.y = half * (c.y - cm.y);      // (C_k + conj C_-k) / 2
     G.x = half * (c.y + cm.y); G.y = -half * (c.x - cm.x);     // (C_k - conj C_-k) / 2i
@@ -761,9 +776,13 @@ template <typename T> size_t esize() { return sizeof(typename V2<T>::t); }
 // Columns per z-pass CTA: as many as fit 56 KB of shared memory (4 CTAs per SM), at most 16.
 }  // namespace
 
+// Row stride (elements) of a transform buffer: one slot more than the row, so rows start in
+// different banks; FP32 rows (swizzled in 16-slot groups) hold whole groups.
+int fft_ld(int L, size_t es) { return (es == sizeof(float2) ? 16 * ((L + 15) / 16) : L) + 1; }
+
 int pick_kb(int nxh, int L3, size_t es) {
   int kb = 1;
-  while (kb * 2 <= nxh && kb * 2 <= 16 && (size_t)(kb * 2) * (L3 + 1) * es <= 56 * 1024) kb *= 2;
+  while (kb * 2 <= nxh && kb * 2 <= 16 && (size_t)(kb * 2) * fft_ld(L3, es) * es <= 56 * 1024) kb *= 2;
   return kb;
 }
 
@@ -792,7 +811,7 @@ static ZArgs zargs(chan_s* h, size_t es) {
   A.KB = h->kb_z > 0 ? h->kb_z : pick_kb(h->nxh, h->L3, es);
   A.lgKB = 0;
   while ((1 << A.lgKB) < A.KB) ++A.lgKB;
-  A.ld = h->L3 + 1;
+  A.ld = fft_ld(h->L3, es);
   A.pl = h->p3;
   A.G = h->G;
   A.pair_in = h->prec == CHAN_PREC_MIXED_DF;
@@ -835,7 +854,7 @@ cudaError_t launch_xpass(chan_s* h, int mode, void* const* in, void* const* out,
   const int nin = mode == 0 ? 6 : 3, nout = mode == 0 ? 3 : (mode == 1 ? 6 : 1);
   for (int f = 0; f < nin; ++f) A.in[f] = in[f];
   for (int f = 0; f < nout; ++f) A.out[f] = out[f];
-  A.nxh = h->nxh; A.L1 = h->L1; A.L3 = h->L3; A.ld = h->L1 + 1;
+  A.nxh = h->nxh; A.L1 = h->L1; A.L3 = h->L3; A.ld = fft_ld(h->L1, fft_esize(h));
   A.mag_nxh = h->nxh == 1 ? 0u : (unsigned)((((unsigned long long)1 << 32) + h->nxh - 1) / h->nxh);
   A.scale = 1.0 / ((double)h->L1 * (double)h->L3);
   A.pl = h->p1;
@@ -935,7 +954,7 @@ cudaError_t launch_xpass_batch(chan_s* const* hs, int n, const BatchWork* w, cud
     memset(&A, 0, sizeof(A));
     for (int f = 0; f < 6; ++f) A.in[f] = w[r].mixed[f];
     for (int f = 0; f < 3; ++f) A.out[f] = w[r].mixed[f];
-    A.nxh = h->nxh; A.L1 = h->L1; A.L3 = h->L3; A.ld = h->L1 + 1;
+    A.nxh = h->nxh; A.L1 = h->L1; A.L3 = h->L3; A.ld = fft_ld(h->L1, fft_esize(h));
   A.mag_nxh = h->nxh == 1 ? 0u : (unsigned)((((unsigned long long)1 << 32) + h->nxh - 1) / h->nxh);
     A.scale = 1.0 / ((double)h->L1 * (double)h->L3);
     A.pl = h->p1;
