@@ -98,6 +98,11 @@ def fft_flops(L, pruned=True):
 # divided by 33); valid for Nx = Nz = 384 only and only while the kernels are as captured.
 NCU_BYTES_PER_PLANE = {("k_xpass", "fp64"): (350.501888e6 + 133.998080e6) / 33}
 NCU_PIPE = {("k_xpass", "fp64"): ("fp64", 0.8757)}
+# The kernels those counters were taken on have changed since (the inverse stages read their
+# block twiddle exponents from a table, the zero fill covers one slot): the DRAM figure is
+# reported beside the roofline as an earlier build's, and the roofline's traffic is null
+# until the counters are taken again.
+NCU_CURRENT = {("k_xpass", "fp64"): False}
 
 
 # per mode-point flops of the wall-normal kernels (read off their sweeps)
@@ -410,8 +415,9 @@ def run_ours(args, c, name):
     peak_main = FP32_PEAK_DERIVED_TFLOPS if main_f32 else peak64
     frac = achieved / peak_main
     key = (dom, "fp64" if dom in ("k_helm", "k_pre", "k_poisson", "k_nonlin", "k_mean") else main_mode)
-    traffic = (NCU_BYTES_PER_PLANE[key] * c["Ny"]
-               if key in NCU_BYTES_PER_PLANE and c["Nx"] == 384 and c["Nz"] == 384 else None)
+    traffic_ncu = (NCU_BYTES_PER_PLANE[key] * c["Ny"]
+                   if key in NCU_BYTES_PER_PLANE and c["Nx"] == 384 and c["Nz"] == 384 else None)
+    traffic = traffic_ncu if NCU_CURRENT.get(key, False) else None
     launches = int(sum(v[1] for v in prof.values()))
     tot_ms = max(1e-9, sum(x[0] for x in prof.values()))
     kernels = {k: {"ms": round(v[0], 3), "launches": v[1], "share": round(v[0] / tot_ms, 4)}
@@ -474,7 +480,9 @@ def run_ours(args, c, name):
             "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak_main,
                          "unit": "TFLOP/s", "frac": frac, "traffic": traffic,
                          "traffic_source": "ncu dram bytes per plane on 384x33x384, scaled to Ny planes",
+                         "traffic_earlier_build": None if traffic is not None else traffic_ncu,
                          "pipe_busy_ncu": NCU_PIPE.get(key),
+                         "ncu_counters_current": bool(NCU_CURRENT.get(key, False)),
                          "peak_source": ("FP32 ALU peak derived from unit counts and clocks: 148 SMs x 128 FMA lanes x 2 flop x 2032 MHz"
                                          if main_f32 else
                                          "FP64 ALU peak derived from unit counts and clocks: 148 SMs x 2 DFMA/clk x 2 flop x 2032 MHz"),
