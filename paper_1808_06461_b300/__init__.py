@@ -133,7 +133,13 @@ def _check(h, rc):
 
 
 class Channel:
-    """One channel box on the current CUDA device (owns its device memory)."""
+    """One channel box on the current CUDA device (owns its device memory).
+
+    precision: CHAN_PREC_FP64; CHAN_PREC_MIXED (FP32 transforms and products, FP64
+    wall-normal solves); CHAN_PREC_F64X (transforms, products and the substep's sweeps in
+    FP32 pairs, about 2^-47); CHAN_PREC_MIXED_DF (FP32 transforms and products, pair sweeps).
+    The mean flow and the statistics are FP64 in every mode.
+    """
 
     def __init__(self, re_tau, Lx, Lz, Nx, Ny, Nz, dt, precision=CHAN_PREC_FP64, eta_w=1.0,
                  grid_re=0.0, stream=None, mesh=None, slab_planes=0, lean_tables=0, y_tables=0):
