@@ -126,7 +126,7 @@ size_t chan_device_bytes(chan_t h);
 size_t chan_footprint_bytes(int Nx, int Ny, int Nz, int precision);
 
 /*
- * Near-wall mesh optimisation of Appendix B (P:L753-770).  Starting from the
+ * Near-wall mesh optimisation of Appendix B.  Starting from the
  * mesh chan_init_ex would build for *o, moves the first 20 interior points at
  * each wall (mirrored) by steepest descent on
  *   L = |g - g_ana| + C |mu - mu_ref|,
