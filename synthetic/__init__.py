@@ -19,8 +19,8 @@ Nyquist mode and is always zero).
 """
 from .ic import (splitmix64, uniform01, bulk_velocity_loglaw, reichardt_profile,
                  perturbed_poiseuille, turbulent_like, single_mode, wavenumbers)
-from .os_mode import orr_sommerfeld_mode
+from .os_mode import orr_sommerfeld_mode, os_squire_mode
 
 __all__ = ["splitmix64", "uniform01", "bulk_velocity_loglaw", "reichardt_profile",
            "perturbed_poiseuille", "turbulent_like", "single_mode", "wavenumbers",
-           "orr_sommerfeld_mode"]
+           "orr_sommerfeld_mode", "os_squire_mode"]

@@ -10,6 +10,7 @@ import numpy as np
 import pytest
 
 import oracle as O
+import pins
 import synthetic as SY
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -430,3 +431,68 @@ def test_filtered_pressure_mean_and_wall_condition(c1, c1_run):
     chib = G * S["chi"]
     mask = (c1.K2 > 0) & c1.keep
     assert np.abs(dP[0][mask] - c1.nu * chib[0][mask]).max() < 1e-10 * np.abs(dP).max()
+
+
+def test_os_squire_generator_obeys_squires_transformation():
+    """The coupled-mode generator's 3-D eigenvalue equals the 2-D one at (k, Re alpha / k)."""
+    for a, b in ((2.0, 1.0), (1.0, 1.0)):
+        k = math.hypot(a, b)
+        c3, _, _ = SY.os_squire_mode(7500, a, b, np.linspace(-1, 1, 5))
+        c2, _ = SY.orr_sommerfeld_mode(7500 * a / k, k, np.linspace(-1, 1, 5))
+        assert abs(c3 - c2) < 1e-7, (a, b, c3, c2)
+
+
+def test_oblique_orr_sommerfeld_squire_mode():
+    """Oblique mode (k_1, k_3) = (2, 1) at Re 7500: |v| and |omega_2| change at alpha c_i.
+
+    Appendix A, Eqs. (hghv), (chi1), (psi) in the linear regime.  Unlike the
+    two-dimensional Orr-Sommerfeld pin, this one has omega_2, u_3 and omega_1
+    non-zero: omega_2 follows the Squire equation only if N_omega2 =
+    i k_3 H_1 - i k_1 H_3 carries the right signs and wavenumbers, and v keeps
+    the Orr-Sommerfeld rate only if the omega_2 parts of H_3 cancel in N_chi.
+    Rates within 0.2 % of alpha c_i = -0.0566 (measured 1e-4) and the
+    omega_2 / v profile within 1e-3 of the eigenmode over t = 2.
+    """
+    rate, rv, rw, prof = pins.oblique_mode_rates()
+    assert abs(rv - rate) < 2e-3 * abs(rate), (rate, rv)
+    assert abs(rw - rate) < 2e-3 * abs(rate), (rate, rw)
+    assert prof < 1e-3, prof
+
+
+def test_energy_identity_of_the_nonlinear_term(c1, c1_run):
+    """sum_k w Re(conj(u_k) . H_k) = 0 at every height for a fully 3-D state.
+
+    <u, P(u x omega)> = <u, u x omega> = 0 (u lies in the retained set, where
+    the 3/2 rule is exact): a dropped, mis-signed or mis-indexed term in any
+    component of H breaks it.
+    """
+    _, S = c1_run
+    assert pins.energy_residual(c1, S) < 1e-14
+
+
+def test_vorticity_is_divergence_free(c1, c1_run):
+    """i k_1 omega_1 + D1 omega_2 + i k_3 omega_3 = 0 to rounding (the divergence of a curl)."""
+    _, S = c1_run
+    assert pins.vorticity_divergence(c1, S) < 1e-13
+
+
+def test_utau_and_bulk_velocity_of_laminar_poiseuille(c1):
+    """Sec. 3.3 outputs on U = 1.5 U_b (1 - y^2): u_tau^2 = 3 nu U_b exactly (the wall
+    rows of D1 are exact on quadratics) and U_b = flux / 2 with the trapezoid rule, whose
+    error on a quadratic is known in closed form: U_b (1 - sum_i h_i^3 / 8)."""
+    ub = 15.98
+    S = dict(v=np.zeros((c1.Ny, c1.Nz, c1.nxh), complex), omega2=np.zeros((c1.Ny, c1.Nz, c1.nxh), complex),
+             U1=1.5 * ub * (1 - c1.y ** 2), U3=np.zeros(c1.Ny))
+    _, utau, bulk = O.stats(c1, S)
+    assert abs(utau ** 2 - 3 * c1.nu * ub) < 1e-12 * 3 * c1.nu * ub   # D1 wall rows: ~1e-13 rounding
+    h = np.diff(c1.y)
+    assert abs(bulk - ub * (1 - np.sum(h ** 3) / 8)) < 1e-14 * ub
+
+
+def test_utau_averages_the_two_walls(c1):
+    """An asymmetric profile U = (1 - y^2)(1 + y/2) has |dU/dy| = 1 at y = -1 and 3 at y = +1:
+    u_tau^2 = nu (1 + 3) / 2."""
+    S = dict(v=np.zeros((c1.Ny, c1.Nz, c1.nxh), complex), omega2=np.zeros((c1.Ny, c1.Nz, c1.nxh), complex),
+             U1=(1 - c1.y ** 2) * (1 + 0.5 * c1.y), U3=np.zeros(c1.Ny))
+    _, utau, _ = O.stats(c1, S)
+    assert abs(utau ** 2 - 2 * c1.nu) < 1e-12 * c1.nu
