@@ -106,7 +106,8 @@ void chan_opts_default(chan_opts* o);
 int chan_init(chan_t* out, double re_tau, double Lx, double Lz, int Nx, int Ny, int Nz, double dt);
 int chan_init_ex(chan_t* out, const chan_opts* o);
 
-/* Release everything the handle owns.  NULL is a no-op. */
+/* Release everything the handle owns (a library interface; the paper has no
+ * counterpart).  NULL is a no-op. */
 void chan_free(chan_t h);
 
 /* Message of the last error on this handle (or of the last failed init when h is NULL). */
@@ -165,8 +166,9 @@ int chan_set_graph(chan_t h, int enable);
 int chan_get_grid(chan_t h, double* y);
 
 /*
- * Set the state from host arrays: v = u_2 and omega_2 in spectral layout,
- * U1, U3 the mean profiles (zero at the walls).  Derives chi = Lap v and
+ * Set the state from host arrays: the variables Appendix A advances, v = u_2
+ * and omega_2 in spectral layout, and the mean profiles U1, U3 of Sec. 2.1
+ * (zero at the walls).  Derives chi = Lap v (Appendix A, Eq. (chi2)) and
  * dv/dy on the device, clears the previous-substep non-linear terms, sets
  * the target mass flux to the flux of U1 and the RK3 substep counter to 0.
  * The (0,0) Fourier coefficients of v and omega_2 are ignored (held at 0).
@@ -175,7 +177,8 @@ int chan_set_state(chan_t h, const double* v, const double* omega2, const double
 /* Same with device pointers (same layouts). */
 int chan_set_state_device(chan_t h, const void* v, const void* omega2, const void* U1, const void* U3);
 
-/* Copy the current state out (host; synchronises). */
+/* Copy the current state (v, omega_2, U1, U3 of Appendix A and Sec. 2.1) out
+ * (host; synchronises).  In the pair-stored modes the pairs are merged to FP64. */
 int chan_get_state(chan_t h, double* v, double* omega2, double* U1, double* U3);
 /* Device-to-device copy of the state into caller buffers (asynchronous). */
 int chan_get_state_device(chan_t h, void* v, void* omega2, void* U1, void* U3);
@@ -309,6 +312,9 @@ int chan_rhs_terms(chan_t h, double* N);
  * reserved all device memory for its own arena.
  *   H: device, 3 fields (H1, H2, H3) in spectral layout, field-major.
  *   N: device, 2 fields (N_chi, N_omega2) written in the same layout.
+ *   Both are plain FP64 complex (interleaved re, im doubles) in every
+ *   precision mode, also for handles whose own fields are stored as FP32
+ *   pairs (CHAN_PREC_F64X, CHAN_PREC_MIXED_DF); the arithmetic is FP64.
  * Runs asynchronously on the handle's stream (chan_sync to wait); the
  * current device must be the handle's.  Its only scratch is a fixed 32 MiB
  * device array inside the library (held on every GPU that loads it until
@@ -342,7 +348,7 @@ int chan_batch_step(chan_batch_t b, int nsub);
 const char* chan_batch_last_error(chan_batch_t b);
 void chan_batch_free(chan_batch_t b);
 
-/* Wait for the handle's stream. */
+/* Wait for the handle's stream (a library interface; the paper has no counterpart). */
 int chan_sync(chan_t h);
 
 /* Simulated time and substeps taken since chan_set_state. */

@@ -267,6 +267,46 @@ def test_orr_sommerfeld_growth_gpu(chan):
     assert abs(growth - c_ref) < 0.01 * c_ref, growth
 
 
+@pytest.mark.parametrize("prec", [0, 2])
+def test_oblique_orr_sommerfeld_squire_mode_gpu(chan, prec):
+    """Oblique mode (k_1, k_3) = (2, 1) at Re 7500 on the device (FP64 and double-float):
+    |v| and |omega_2| change at alpha c_i of linear theory (Squire's transformation of the
+    Orr-Sommerfeld eigenvalue) within 0.2 %, omega_2 / v keeps the coupled eigenmode's
+    profile within 1e-3, and the state matches the oracle's run after 300 substeps
+    (the bar below).  Exercises H_3 and N_omega2 = i k_3 H_1 - i k_1 H_3 (Eq. (hghv)), which the
+    two-dimensional mode leaves at zero.  The mixed modes round the mean flow in FP32,
+    far above this 1e-6 perturbation, so they are not run here."""
+    alpha, beta, re, nsub = 2.0, 1.0, 7500.0, 300
+    st = O.Setup(re, 2 * math.pi / alpha, 2 * math.pi / beta, 4, 97, 4, 0.02, grid_re=180)
+    ch = chan.Channel(re, st.Lx, st.Lz, 4, 97, 4, 0.02, grid_re=180.0, precision=prec)
+    y = ch.grid()
+    c, vp, ep = SY.os_squire_mode(re, alpha, beta, y)
+    s0 = SY.single_mode(y, 4, 4, 1, 1, v_profile=1e-6 * vp, omega_profile=1e-6 * ep, U1=1 - y ** 2)
+    ch.set_state(s0["v"], s0["omega2"], s0["U1"], s0["U3"])
+    ch.step(nsub)
+    g = ch.get_state()
+
+    def amp(F):
+        return math.sqrt(np.sum(st.wq * np.abs(F[:, 1, 1]) ** 2))
+
+    T = ch.time()
+    rate = alpha * c.imag
+    for k, p0 in (("v", s0["v"]), ("omega2", s0["omega2"])):
+        r = math.log(amp(g[k]) / amp(p0)) / T
+        assert abs(r - rate) < 2e-3 * abs(rate), (k, r, rate)
+    j = int(np.argmax(np.abs(vp)))
+    ratio = g["omega2"][:, 1, 1] / g["v"][j, 1, 1]
+    assert np.abs(ratio - ep / vp[j]).max() < 1e-3 * np.abs(ep / vp[j]).max()
+    # parity with the oracle's run: the perturbation is 1e-6 of the O(1) base flow, so each
+    # rounding of a base-flow product is eps * 1e6 relative to v and omega_2 (eps = 2^-53
+    # FP64, ~2^-47 double-float); 1e3 such roundings of margin over 300 substeps
+    ref = O.run(st, O.initial_state(st, s0["v"], s0["omega2"], s0["U1"], s0["U3"]), nsub)
+    bar = (2.0 ** -53 if prec == 0 else 2.0 ** -47) * 1e6 * 1e3
+    for k in ("v", "omega2"):
+        assert rel(g[k], ref[k]) < bar, (k, rel(g[k], ref[k]), bar)
+    assert rel(g["U1"], ref["U1"]) < TOL
+
+
 @pytest.mark.parametrize("prec", [1, 3])
 def test_mixed_precision_error(chan, ten_steps, prec):
     """FP32 transforms and products with FP64 (mode 1) or double-float (mode 3) wall-normal
