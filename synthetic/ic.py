@@ -55,12 +55,32 @@ def _trapz(f, y):
     return float(np.sum(0.5 * (f[1:] + f[:-1]) * np.diff(y)))
 
 
+def _uniform01_vec(seed, kx, kz, field):
+    """uniform01 for an array of kx at one (seed, kz, field): the same integers in uint64."""
+    m = np.uint64(_MASK64)
+    kx = np.asarray(kx, dtype=np.uint64)
+    ctr = (np.uint64((seed & 0xFFFFFFFF) << 32) | ((kx & np.uint64(0xFFF)) << np.uint64(20))
+           | np.uint64((((kz + 2048) & 0xFFF) << 8) | (field & 0xFF)))
+
+    def sm(x):
+        with np.errstate(over="ignore"):
+            x = (x + np.uint64(0x9E3779B97F4A7C15)) & m
+            z = ((x ^ (x >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)) & m
+            z = ((z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)) & m
+        return z ^ (z >> np.uint64(31))
+
+    return (sm(sm(ctr)) >> np.uint64(11)).astype(np.float64) * (1.0 / (1 << 53))
+
+
 def _fill(y, Lx, Lz, Nx, Nz, seed, mode_ok, amp_of_k):
     """Random-phase modes with shapes v ~ (1-y^2)^2 (1 + r y), omega_2 ~ k (1-y^2)(1 + s y).
 
     Returns unit-scaled (v, omega_2) and the volume-mean square of the
     perturbation velocity they imply, computed from analytic y-derivatives of
-    the shapes and trapezoid weights in y.
+    the shapes and trapezoid weights in y.  ``mode_ok(kx, kz)`` and
+    ``amp_of_k(k)`` take an array of kx (one kz at a time) and an array of |k|.
+    The modes of one kz row are generated together; every value is the one a
+    mode-by-mode loop would give.
     """
     y = np.asarray(y, dtype=np.float64)
     Ny = y.size
@@ -69,37 +89,43 @@ def _fill(y, Lx, Lz, Nx, Nz, seed, mode_ok, amp_of_k):
     v = np.zeros((Ny, Nz, nxh), dtype=np.complex128)
     om = np.zeros_like(v)
     ms = np.zeros(Ny)
-    w = 1.0 - y * y
-    for kx in range(nxh):
-        for jz in range(Nz):
-            kz = int(kzi[jz])
-            if nyq[jz] or (kx == 0 and kz == 0) or not mode_ok(kx, kz):
-                continue
-            if kx == 0 and kz < 0:
-                continue  # filled from the conjugate partner below
-            k2 = k1[kx] ** 2 + k3[jz] ** 2
-            k = math.sqrt(k2)
-            a = amp_of_k(k)
-            r = 2.0 * uniform01(seed, kx, kz, 2) - 1.0
-            s = 2.0 * uniform01(seed, kx, kz, 3) - 1.0
-            th = 2.0 * math.pi * uniform01(seed, kx, kz, 0)
-            ph = 2.0 * math.pi * uniform01(seed, kx, kz, 1)
-            f = w * w * (1.0 + r * y)
-            fp = -4.0 * y * w * (1.0 + r * y) + w * w * r
-            g = k * w * (1.0 + s * y)
-            vh = a * f * np.exp(1j * th)
-            dvh = a * fp * np.exp(1j * th)
-            oh = a * g * np.exp(1j * ph)
-            v[:, jz, kx] = vh
-            om[:, jz, kx] = oh
-            u1 = 1j * (k1[kx] * dvh - k3[jz] * oh) / k2
-            u3 = 1j * (k3[jz] * dvh + k1[kx] * oh) / k2
-            wgt = 2.0  # a kx > 0 mode stands for itself and its conjugate; a kx = 0 pair likewise
-            ms += wgt * (np.abs(u1) ** 2 + np.abs(vh) ** 2 + np.abs(u3) ** 2)
-            if kx == 0:
-                jneg = (Nz - kz) % Nz
-                v[:, jneg, 0] = np.conj(vh)
-                om[:, jneg, 0] = np.conj(oh)
+    w = (1.0 - y * y)[:, None]
+    w2 = w * w
+    yc = y[:, None]
+    kxs = np.arange(nxh)
+    for jz in range(Nz):
+        kz = int(kzi[jz])
+        if nyq[jz]:
+            continue
+        sel = np.asarray(mode_ok(kxs, kz), dtype=bool) & ~((kxs == 0) & (kz <= 0))
+        kx = kxs[sel]
+        if kx.size == 0:
+            continue
+        k2 = k1[kx] ** 2 + k3[jz] ** 2
+        k = np.sqrt(k2)
+        a = np.asarray(amp_of_k(k), dtype=np.float64) * np.ones_like(k)
+        r = 2.0 * _uniform01_vec(seed, kx, kz, 2) - 1.0
+        s_ = 2.0 * _uniform01_vec(seed, kx, kz, 3) - 1.0
+        th = 2.0 * math.pi * _uniform01_vec(seed, kx, kz, 0)
+        ph = 2.0 * math.pi * _uniform01_vec(seed, kx, kz, 1)
+        ry = 1.0 + r * yc
+        f = w2 * ry
+        fp = -4.0 * yc * w * ry + w2 * r
+        g = k * w * (1.0 + s_ * yc)
+        vh = f * (a * np.exp(1j * th))
+        oh = g * (a * np.exp(1j * ph))
+        cols = slice(kx[0], kx[-1] + 1) if kx[-1] - kx[0] + 1 == kx.size else kx
+        v[:, jz, cols] = vh
+        om[:, jz, cols] = oh
+        # |u_1|^2 + |u_3|^2 = (|dv/dy|^2 + |omega_2|^2) / k^2 for u_1 = i (k1 dv - k3 om) / k^2,
+        # u_3 = i (k3 dv + k1 om) / k^2 (the cross terms cancel); a kx > 0 mode stands for
+        # itself and its conjugate, a kx = 0 pair likewise
+        a2 = a * a
+        ms += 2.0 * ((f * f + (fp * fp + g * g) / k2) @ a2)
+        if kx[0] == 0:   # kx = 0, kz > 0: its Hermitian partner at -kz
+            jneg = (Nz - kz) % Nz
+            v[:, jneg, 0] = np.conj(vh[:, 0])
+            om[:, jneg, 0] = np.conj(oh[:, 0])
     return v, om, _trapz(ms, y) / 2.0
 
 
@@ -112,7 +138,7 @@ def perturbed_poiseuille(y, re_tau, Lx, Lz, Nx, Nz, seed, amp=0.1, kmax=4):
     """
     y = np.asarray(y, dtype=np.float64)
     ub = bulk_velocity_loglaw(re_tau)
-    v, om, ms = _fill(y, Lx, Lz, Nx, Nz, seed, lambda kx, kz: kx <= kmax and abs(kz) <= kmax,
+    v, om, ms = _fill(y, Lx, Lz, Nx, Nz, seed, lambda kx, kz: (kx <= kmax) & (abs(kz) <= kmax),
                       lambda k: 1.0)
     scale = amp * ub / math.sqrt(ms) if ms > 0 else 0.0
     return dict(v=v * scale, omega2=om * scale, U1=1.5 * ub * (1.0 - y * y),
@@ -127,8 +153,8 @@ def turbulent_like(y, re_tau, Lx, Lz, Nx, Nz, seed, urms=1.0):
     """
     y = np.asarray(y, dtype=np.float64)
     k0 = 2.0 * math.pi / max(Lx, Lz)
-    v, om, ms = _fill(y, Lx, Lz, Nx, Nz, seed, lambda kx, kz: True,
-                      lambda k: (max(k, k0) / k0) ** (-4.0 / 3.0))
+    v, om, ms = _fill(y, Lx, Lz, Nx, Nz, seed, lambda kx, kz: np.ones(np.shape(kx), dtype=bool),
+                      lambda k: (np.maximum(k, k0) / k0) ** (-4.0 / 3.0))
     scale = urms / math.sqrt(ms) if ms > 0 else 0.0
     return dict(v=v * scale, omega2=om * scale, U1=reichardt_profile(y, re_tau),
                 U3=np.zeros_like(y), Ub=None)

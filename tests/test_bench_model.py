@@ -82,3 +82,21 @@ def test_xpass_flops_of_the_bench_workload(bench):
     L1, L3, nxh = 576, 576, 192
     pairs = c["Ny"] * L3 // 2
     assert bench.kernel_flops("k_xpass", c, {}) == pairs * (9 * bench.fft_flops(L1) + L1 * 18 + 3 * nxh * 16)
+
+
+def test_step_bytes_match_the_per_point_budget(bench):
+    """The byte model per collocation point and substep (pt = Nx Ny Nz, a mode-point is two
+    pts): in FP64 the transform passes move a1 56, a2 120 (six inputs: the survey's 112 counts
+    omega_2's load as part of a1), a3 108 and a4 60 bytes per pt, and the FP32 transforms
+    of the mixed modes halve the physical-layout fields."""
+    c = dict(Nx=384, Ny=257, Nz=384)
+    pts = 384 * 257 * 384
+    b = bench.step_bytes(c, "fp64", 1, filtered=False)
+    per = {k: v / pts for k, v in b.items()}
+    assert per["k_pre"] == 56 and per["k_zinv"] == 120 and per["k_xpass"] == 108 and per["k_zfwd"] == 60
+    assert per["k_nonlin"] == 40
+    m = bench.step_bytes(c, "mixed", 1, filtered=False)
+    assert m["k_xpass"] / pts == 54 and m["k_zinv"] / pts == 16 + 16 + 36
+    # the filter pass adds work only when asked, and more of it than one substep's transforms
+    f = bench.step_bytes(c, "fp64", 1)
+    assert f["k_zfwd"] > b["k_zfwd"] and "k_filter_out" in f and "k_filter_out" not in b
