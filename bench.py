@@ -94,15 +94,12 @@ def fft_flops(L, pruned=True):
 
 
 # DRAM bytes per wall-normal plane of each kernel launch, from ncu on the 384 x 33 x 384
-# profiling case (profiles/*_re550_384x33x384.md: dram__bytes_read.sum + dram__bytes_write.sum
-# divided by 33); valid for Nx = Nz = 384 only and only while the kernels are as captured.
-NCU_BYTES_PER_PLANE = {("k_xpass", "fp64"): (350.501888e6 + 133.998080e6) / 33}
-NCU_PIPE = {("k_xpass", "fp64"): ("fp64", 0.8757)}
-# The kernels those counters were taken on have changed since (the inverse stages read their
-# block twiddle exponents from a table, the zero fill covers one slot): the DRAM figure is
-# reported beside the roofline as an earlier build's, and the roofline's traffic is null
-# until the counters are taken again.
-NCU_CURRENT = {("k_xpass", "fp64"): False}
+# profiling case (profiles/k_xpass_fp64_re550_384x33x384.md: dram__bytes_read.sum +
+# dram__bytes_write.sum divided by 33); valid for Nx = Nz = 384 only and only while the
+# kernels are as captured (NCU_CURRENT).
+NCU_BYTES_PER_PLANE = {("k_xpass", "fp64"): (350.522368e6 + 131.073536e6) / 33}
+NCU_PIPE = {("k_xpass", "fp64"): ("fp64", 0.8963)}
+NCU_CURRENT = {("k_xpass", "fp64"): True}
 
 
 # per mode-point flops of the wall-normal kernels (read off their sweeps)
@@ -123,6 +120,70 @@ def kernel_flops(name, c, launches_by_mode):
         pairs = Ny * L3 // 2
         return pairs * (9 * fft_flops(L1) + L1 * 18 + 3 * nxh * 16)
     return 0
+
+
+def step_flops(c, nsub, filtered=True):
+    """Algorithmic flops per bench step by kernel (nsub substeps, then the filter pass when
+    ``filtered``): the per-launch counts of ``kernel_flops`` for the substep launches over all
+    Ny planes, whatever slabs the transform passes run in, plus the filter pass's transforms
+    (six inverse z columns, two x-passes of three inverse and six forward rows with the six
+    products, twelve forward z columns) and its one k_pre."""
+    Nx, Ny, Nz = c["Nx"], c["Ny"], c["Nz"]
+    nxh, L1, L3 = Nx // 2, 3 * Nx // 2, 3 * Nz // 2
+    out = {k: nsub * kernel_flops(k, c, {}) for k in ("k_pre", "k_zinv", "k_xpass", "k_zfwd", "k_nonlin",
+                                                       "k_helm", "k_poisson")}
+    if filtered:
+        pairs = Ny * L3 // 2
+        out["k_pre"] += kernel_flops("k_pre", c, {})
+        out["k_zinv"] += 6 * Ny * nxh * fft_flops(L3)
+        out["k_xpass"] += 2 * pairs * (9 * fft_flops(L1) + L1 * 12 + 6 * nxh * 16)
+        out["k_zfwd"] += 12 * Ny * nxh * fft_flops(L3)
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Algorithmic HBM bytes: every field a kernel reads, once, and every field it
+# writes, once, at the size the precision mode stores it; the wall-normal
+# kernels also read their per-wavenumber-class tables once per class.  Scratch
+# round trips (the forward sweeps parked for the backward sweeps) and re-reads
+# are not counted: they are what measured DRAM traffic above this model shows.
+# Per mode-point (n = Ny Nz Nx/2 of them per field):
+#   F   = 16 B  a Fourier field (complex FP64, or an FP32 (hi, lo) pair per part)
+#   fin = 8 B   the FP32 transform inputs u_1, u_3, omega_1, omega_3 (mixed modes), else 16
+#   X   = 1.5 es  a field in the z-physical layout (3Nz/2 rows; es 8 B FP32, else 16)
+#   tab = 8 B   a table value (FP64, or an FP32 pair)
+# ---------------------------------------------------------------------------
+def step_bytes(c, mode, nsub, filtered=True):
+    """Algorithmic bytes per bench step (nsub substeps, then the filter pass and the
+    statistics when ``filtered``), by kernel name."""
+    Nx, Ny, Nz = c["Nx"], c["Ny"], c["Nz"]
+    nxh = Nx // 2
+    M = Nz * nxh
+    C = (Nz // 2) * nxh
+    n = Ny * M
+    f32 = mode in ("mixed", "mixed_df")
+    F, tab = 16.0, 8.0
+    fin = 8.0 if f32 else 16.0
+    X = 1.5 * (8.0 if f32 else 16.0)
+    sub = {"k_pre": n * (3 * F + 4 * fin),
+           "k_zinv": n * (4 * fin + 2 * F + 6 * X),
+           "k_xpass": n * 9 * X,
+           "k_zfwd": n * (3 * X + 3 * F),
+           "k_nonlin": n * 5 * F,
+           "k_helm": n * 14 * F + 7 * tab * Ny * C,
+           "k_poisson": n * 4 * F + 11 * tab * Ny * C,
+           "k_mean": 10 * 8.0 * Ny}
+    out = {k: v * nsub for k, v in sub.items()}
+    if filtered:
+        fil = {"k_pre": n * 7 * F,
+               "k_zinv": n * (6 * F + 6 * X) + 8.0 * M,
+               "k_xpass": 2 * n * 9 * X,
+               "k_zfwd": n * (12 * X + 12 * F),
+               "k_filter_out": n * (15 * F + 9 * F),
+               "k_stats": n * 12 * F}
+        for k, v in fil.items():
+            out[k] = out.get(k, 0.0) + v
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -206,16 +267,42 @@ def replica_throughput(world, steps, substeps_per_step, points, max_ms):
     return world * steps * substeps_per_step * points / (max_ms * 1e-3) / 1e6
 
 
+def workload_config(name, c, mode, world=1):
+    """The ``config`` of a bench line: the same dict for our arm and the reference arm."""
+    kind, p1, p3 = c["filt"]
+    n = c["Ny"] * c["Nz"] * (c["Nx"] // 2)
+    return {"workload": name, "Nx": c["Nx"], "Ny": c["Ny"], "Nz": c["Nz"], "re_tau": c["re"],
+            "dt": c["dt"], "substeps_per_step": c["sub_per_step"],
+            "filter": {"kind": "sharp" if kind == 0 else "box", "p1": p1, "p3": p3},
+            "precision": mode,
+            "l2": ("inputs larger than L2 (state %.1f GB)" % (6 * n * 16 / 1e9) if 6 * n * 16 > 126e6 else
+                   "inputs within L2 (state %.1f MB): a small parity case, not a bandwidth measurement"
+                   % (6 * n * 16 / 1e6)),
+            "parallelism": "replicas" if world > 1 else "single"}
+
+
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return None
+
+
 # ---------------------------------------------------------------------------
 # CPU oracle on a bounded sample (reference arm and cpu_baseline)
 # ---------------------------------------------------------------------------
-def oracle_sample_substep_seconds(c, n_planes=4, n_modes=512):
-    """Estimated oracle seconds per substep of the full workload, from a sample.
+def oracle_sample_substep_seconds(c, n_planes=4, n_modes=512, with_filter=False):
+    """Estimated oracle seconds per substep (and per filter pass) of the full workload, from a sample.
 
     Timed: the wall-normal derivatives of the a1 step over all modes, the
     a2-a4 transforms and products on ``n_planes`` x-z planes (scaled by
     Ny / n_planes), the a5 terms over all modes, the a6-a7 implicit solves
-    on ``n_modes`` modes (scaled by M / n_modes) and the a8 mean flow.
+    on ``n_modes`` modes (scaled by M / n_modes) and the a8 mean flow; with
+    ``with_filter`` also the filter pass on the same planes.  Returns (seconds per
+    substep, seconds per filter pass, wall seconds the sample took, sample sizes).
     """
     import oracle as O
     import synthetic as SY
@@ -223,7 +310,7 @@ def oracle_sample_substep_seconds(c, n_planes=4, n_modes=512):
     s0 = SY.turbulent_like(st.y, c["re"], c["Lx"], c["Lz"], c["Nx"], c["Nz"], seed=1)
     S = O.initial_state(st, s0["v"], s0["omega2"], s0["U1"], s0["U3"])
     M = st.Nz * st.nxh
-    t0 = time.perf_counter()
+    t_start = t0 = time.perf_counter()
     u1, v, u3, du1, dv, du3 = O.velocities(st, S)
     t_vel = time.perf_counter() - t0
     pl = np.linspace(0, st.Ny - 1, n_planes).astype(int)
@@ -255,7 +342,21 @@ def oracle_sample_substep_seconds(c, n_planes=4, n_modes=512):
     t0 = time.perf_counter()
     O.channel.mean_flow_step(st, S, H[0][:, 0, 0].real, H[2][:, 0, 0].real, 0)
     t_mean = time.perf_counter() - t0
-    return t_vel + t_fft + t_rhs + t_imp + t_mean, dict(planes=n_planes, modes=n_modes)
+    t_sub = t_vel + t_fft + t_rhs + t_imp + t_mean
+    t_filt = 0.0
+    if with_filter:
+        # the filter pass of a step (Sec. 3.1) on the same planes: G u_i, the products
+        # u_i u_j and ubar_i ubar_j, their dealiased projections, tau_ij (scaled by Ny / planes)
+        kind, p1, p3 = c["filt"]
+        t0 = time.perf_counter()
+        G = O.filter_transfer(st, kind, p1, p3)
+        u = [u1[pl], v[pl], u3[pl]]
+        ub = [G * f for f in u]
+        pu = [O.to_physical(st, f) for f in u]
+        pb = [O.to_physical(st, f) for f in ub]
+        [G * O.to_fourier(st, pu[i] * pu[j]) - O.to_fourier(st, pb[i] * pb[j]) for i, j in O.PAIRS]
+        t_filt = (time.perf_counter() - t0) * st.Ny / n_planes + t_vel
+    return t_sub, t_filt, time.perf_counter() - t_start, dict(planes=n_planes, modes=n_modes)
 
 
 def cpu_threads():
@@ -267,30 +368,76 @@ def cpu_threads():
         return os.cpu_count()
 
 
+def oracle_anchor_c1():
+    """The oracle's full small workload, not extrapolated: Re_tau 180, 32 x 49 x 32,
+    10 substeps and the box filter with tau_ij, timed on all host threads and on one."""
+    import oracle as O
+    import synthetic as SY
+    c = CONFIGS["re180_32x49x32"]
+    kind, p1, p3 = c["filt"]
+    st = O.Setup(c["re"], c["Lx"], c["Lz"], c["Nx"], c["Ny"], c["Nz"], c["dt"])
+    s0 = SY.perturbed_poiseuille(st.y, c["re"], c["Lx"], c["Lz"], c["Nx"], c["Nz"], seed=1, amp=0.1)
+    pts = c["Nx"] * c["Ny"] * c["Nz"]
+
+    def once():
+        t0 = time.perf_counter()
+        S = O.run(st, O.initial_state(st, s0["v"], s0["omega2"], s0["U1"], s0["U3"]), c["sub_per_step"])
+        O.filter_stresses(st, S, kind, p1, p3)
+        return time.perf_counter() - t0
+
+    once()   # warm caches (coefficient systems, FFT plans)
+    t_all = min(once() for _ in range(3))
+    try:
+        import threadpoolctl
+        with threadpoolctl.threadpool_limits(1):
+            t_one = min(once() for _ in range(3))
+    except Exception:
+        t_one = None
+    val = lambda t: pts * c["sub_per_step"] / t / 1e6 if t else None
+    return {"workload": "re180_32x49x32", "substeps": c["sub_per_step"], "filter": "box 50 x 50",
+            "seconds_all_threads": t_all, "value_all_threads": val(t_all), "threads": cpu_threads(),
+            "seconds_one_thread": t_one, "value_one_thread": val(t_one), "unit": "Mpts*substep/s",
+            "timed": "whole run (10 substeps + filter pass), best of 3, not extrapolated"}
+
+
 def run_reference(args, c, name):
-    """The oracle, as it stands, on a bounded sample of each step."""
+    """The oracle, as it stands, on a bounded sample of each step.
+
+    Each timed step runs the sample of ``oracle_sample_substep_seconds`` (the
+    transforms and products on 4 planes, the implicit solves on 512 modes, the
+    wall-normal derivatives and mean flow over everything, the filter pass on the
+    4 planes); ``ms_per_step`` is the wall time that sample took, and ``value`` the
+    throughput of the whole workload implied by scaling each part to its full size
+    (``work_per_step_mpts_substep`` = value x the sample's seconds: the share of a
+    step's work the sample stands for)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     pts = c["Nx"] * c["Ny"] * c["Nz"]
-    per_sub = []
+    nsub = c["sub_per_step"]
+    full, wall = [], []
     for k in range(args.warmup + args.steps):
-        t, sample = oracle_sample_substep_seconds(c)
+        t_sub, t_filt, t_wall, sample = oracle_sample_substep_seconds(c, with_filter=True)
         if k >= args.warmup:
-            per_sub.append(t)
-    t_sub = float(np.median(per_sub))
-    value = pts / t_sub / 1e6
-    desc = ("oracle substep estimated from a sample: a2-a4 on %d of %d planes, a6-a7 on %d of %d modes, "
-            "a1/a5 y-derivatives and a8 over everything; per-step time = %d substeps (filter pass not "
-            "included)" % (sample["planes"], c["Ny"], sample["modes"], c["Nz"] * c["Nx"] // 2, c["sub_per_step"]))
+            full.append(nsub * t_sub + t_filt)
+            wall.append(t_wall)
+    t_step = float(np.median(full))
+    t_sample = float(np.median(wall))
+    value = pts * nsub / t_step / 1e6
+    desc = ("a step of the oracle estimated from a sample: a2-a4 and the filter pass on %d of %d planes, "
+            "a6-a7 on %d of %d modes (each scaled to the full size), a1/a5 y-derivatives and a8 over "
+            "everything; a step = %d substeps + the filter pass" %
+            (sample["planes"], c["Ny"], sample["modes"], c["Nz"] * c["Nx"] // 2, nsub))
+    cpu = {"value": value, "unit": "Mpts*substep/s", "cores": cpu_threads(), "kind": "oracle", "sample": desc,
+           "cpu_model": cpu_model(), "nproc": os.cpu_count()}
     line = {"impl": "reference", "metric": "DNS Mpts.substep/s", "value": value, "unit": "Mpts*substep/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": t_sub * c["sub_per_step"] * 1e3, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": t_sample * 1e3, "ms_per_full_step_estimated": t_step * 1e3,
+            "work_per_step_mpts_substep": value * t_sample,
+            "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": name, "Nx": c["Nx"], "Ny": c["Ny"], "Nz": c["Nz"], "re_tau": c["re"],
-                       "substeps_per_step": c["sub_per_step"]},
-            "cpu_baseline": {"value": value, "unit": "Mpts*substep/s", "cores": cpu_threads(), "kind": "oracle",
-                             "sample": desc},
+            "config": workload_config(name, c, "fp64"),
+            "cpu_baseline": cpu,
             "e2e": {"value": value, "unit": "Mpts*substep/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -339,7 +486,8 @@ def run_ours(args, c, name):
             ch.stats()
 
         ch.set_state(s0["v"], s0["omega2"], s0["U1"], s0["U3"])
-        tuned[mode] = ch.autotune()   # launch shapes for this box (results bitwise unchanged)
+        # launch shapes for this box (results bitwise unchanged)
+        tuned[mode] = ch.tuned_shape() if args.no_autotune else ch.autotune()
         for _ in range(args.warmup):
             one_step()
         snap = ch.get_state()
@@ -367,11 +515,32 @@ def run_ours(args, c, name):
         return ch, snap, prof, ms, samples
 
     def roofline(prof, peak64):
+        """The dominant kernel's algorithmic flops per step (all its launches) over its
+        summed CUDA-event time."""
         dom = max(prof, key=lambda k: prof[k][0])
         dms, dn = prof[dom]
-        fl = kernel_flops(dom, c, {})
-        achieved = fl / (dms / dn * 1e-3) / 1e12 if dn else 0.0
+        fl = step_flops(c, nsub).get(dom, 0.0) * args.steps
+        achieved = fl / (dms * 1e-3) / 1e12 if dms else 0.0
         return dom, achieved, achieved / peak64
+
+    hbm_peak = measured_peaks().get("hbm_gbs") or 6400.0
+    hbm_source = "measured" if measured_peaks().get("hbm_gbs") else "fallback"
+
+    def hbm(prof, mode, step_ms, steps):
+        """Algorithmic bytes over time: the dominant kernel's per launch (its bytes per step
+        over its launches per step, against its mean CUDA-event launch time) and the whole
+        step's (every kernel's bytes per step over the step time)."""
+        by = step_bytes(c, mode, nsub)
+        dom = max(prof, key=lambda k: prof[k][0])
+        dms, dn = prof[dom]
+        per_launch = by.get(dom, 0.0) * steps / dn if dn else 0.0
+        gbs = per_launch / (dms / dn * 1e-3) / 1e9 if dn else 0.0
+        step_gbs = sum(by.values()) / (step_ms * 1e-3) / 1e9
+        return {"kernel": dom, "bytes_per_launch": per_launch, "achieved_gbs": gbs, "frac": gbs / hbm_peak,
+                "step_bytes": sum(by.values()), "step_achieved_gbs": step_gbs, "step_frac": step_gbs / hbm_peak,
+                "bytes_per_pt_substep": sum(by.values()) / (pts * nsub),
+                "peak_gbs": hbm_peak, "peak_source": hbm_source + " (MEASURED_PEAKS hbm_gbs, a copy kernel)"
+                if hbm_source == "measured" else "fallback 6400 GB/s"}
 
     main_mode = args.precision
     ch, snap_main, prof, ms, samples = measure(main_mode, True)
@@ -411,6 +580,7 @@ def run_ours(args, c, name):
     ch.close()
 
     dom, achieved, frac = roofline(prof, peak64)
+    hbm_main = hbm(prof, main_mode, ms / args.steps, args.steps)
     main_f32 = main_mode in ("mixed", "mixed_df") and dom in ("k_xpass", "k_zinv", "k_zfwd")
     peak_main = FP32_PEAK_DERIVED_TFLOPS if main_f32 else peak64
     frac = achieved / peak_main
@@ -456,7 +626,10 @@ def run_ours(args, c, name):
                                                else "an FP64 wall-normal kernel")))},
                 "kernel_shares": {k: round(v[0] / max(1e-9, sum(x[0] for x in profm.values())), 4)
                                   for k, v in profm.items() if v[1]},
-                "err_vs_fp64": {"after_substeps": args.warmup * nsub,
+                "hbm": hbm(profm, mode, msm / args.steps, args.steps),
+                "err_vs_gpu_fp64": {"after_substeps": args.warmup * nsub,
+                                "reference": "the FP64 run of this bench (held to the FP64 oracle at 1e-10 "
+                                             "relative L2 by the parity tests)",
                                 "v_rel_l2": float(np.linalg.norm(snap["v"] - snap_main["v"]) / np.linalg.norm(snap_main["v"])),
                                 "omega2_rel_l2": float(np.linalg.norm(snap["omega2"] - snap_main["omega2"]) /
                                                        np.linalg.norm(snap_main["omega2"])),
@@ -471,12 +644,8 @@ def run_ours(args, c, name):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp64": "f64", "mixed": "f32+f64", "f64x": "f32x2+f64", "mixed_df": "f32+f32x2+f64"}[main_mode],
             "data": "synthetic",
-            "config": {"workload": name, "Nx": c["Nx"], "Ny": c["Ny"], "Nz": c["Nz"], "re_tau": c["re"],
-                       "dt": c["dt"], "substeps_per_step": nsub, "filter": {"kind": "sharp" if kind == 0 else "box",
-                                                                           "p1": p1, "p3": p3},
-                       "precision": main_mode, "l2": "inputs larger than L2 (state %.1f GB)" % (6 * n * 16 / 1e9),
-                       "launch_shapes": {m: dict(zip(("kb_z", "xthreads", "ytab_global"), v)) for m, v in tuned.items()},
-                       "parallelism": "replicas" if world > 1 else "single"},
+            "config": workload_config(name, c, main_mode, world),
+            "launch_shapes": {m: dict(zip(("kb_z", "xthreads", "ytab_global"), v)) for m, v in tuned.items()},
             "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak_main,
                          "unit": "TFLOP/s", "frac": frac, "traffic": traffic,
                          "traffic_source": "ncu dram bytes per plane on 384x33x384, scaled to Ny planes",
@@ -487,7 +656,11 @@ def run_ours(args, c, name):
                                          if main_f32 else
                                          "FP64 ALU peak derived from unit counts and clocks: 148 SMs x 2 DFMA/clk x 2 flop x 2032 MHz"),
                          "dgemm_tflops_measured": dgemm64,
-                         "hbm_peak_gbs": peaks.get("hbm_gbs")},
+                         "hbm": hbm_main,
+                         "hbm_note": ("the FP64 step is FP64-ALU bound on this GPU (FP64 issues at 1/59 of "
+                                      "the FP32 rate, 1.2 TFLOP/s against 6.5 TB/s, 0.18 flop/B; the path needs "
+                                      "~3 flop/B), so its HBM fraction stays far below the 60 % a bandwidth-bound "
+                                      "step would reach" if main_mode == "fp64" else None)},
             "kernels": kernels,
             "gpu_launches": launches,
             "e2e": {"value": e2e, "unit": "Mpts*substep/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
@@ -497,17 +670,128 @@ def run_ours(args, c, name):
         line["modes"] = modes
     if not args.no_serve:
         line["serving"] = run_serving(args, rank)
+    if world == 1 and not args.no_configs:
+        del ch
+        line["configs"] = run_configs(args, chan, SY, torch, precs, stream)
     if rank == 0 and not args.no_cpu_baseline:
-        t_sub, sample = oracle_sample_substep_seconds(c)
-        line["cpu_baseline"] = {"value": pts / t_sub / 1e6, "unit": "Mpts*substep/s", "cores": cpu_threads(),
-                                "kind": "oracle",
-                                "sample": "one substep estimated from a2-a4 on %d of %d planes and a6-a7 on %d of %d "
-                                          "modes (scaled), a1/a5/a8 over everything" %
-                                          (sample["planes"], c["Ny"], sample["modes"], c["Nz"] * c["Nx"] // 2)}
+        t_sub, t_filt, _, sample = oracle_sample_substep_seconds(c, with_filter=True)
+        line["cpu_baseline"] = {"value": pts * nsub / (nsub * t_sub + t_filt) / 1e6, "unit": "Mpts*substep/s",
+                                "cores": cpu_threads(), "kind": "oracle", "cpu_model": cpu_model(),
+                                "nproc": os.cpu_count(),
+                                "sample": "one step (%d substeps + the filter pass) estimated from a2-a4 and the "
+                                          "filter on %d of %d planes and a6-a7 on %d of %d modes (scaled), "
+                                          "a1/a5/a8 over everything" %
+                                          (nsub, sample["planes"], c["Ny"], sample["modes"], c["Nz"] * c["Nx"] // 2),
+                                "anchor_c1": oracle_anchor_c1()}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_configs(args, chan, SY, torch, precs, stream):
+    """The two mixed-precision configurations beside the headline workload.
+
+    Re_tau 1000 (768 x 385 x 768, dt 1e-4): FP64, mixed and mixed with pair sweeps,
+    each 500 substeps from the same seeded field and then the sharp filter with
+    tau_ij and the statistics, timed with CUDA events; errors of the mean, rms and
+    tau_ij profiles against the FP64 run (held to the FP64 oracle at 1e-10 by the
+    parity tests), relative to each profile's magnitude and to how far it moved
+    from its initial value.
+    Re_tau 2000 (1536 x 633 x 1152, dt 5e-5, mixed; the padded 2304-point x
+    transform does not fit one CTA in FP64): steps of 20 substeps with the box
+    filter of width 100 wall units and the statistics, 1 warm-up step and 2 timed
+    steps (40 of the configuration's 200 substeps)."""
+    out = {}
+
+    def prof_err(a, b, b0=None):
+        d = float(np.abs(a - b).max())
+        r = {"rel_to_magnitude": d / max(float(np.abs(b).max()), 1e-300)}
+        if b0 is not None:
+            r["rel_to_change"] = d / max(float(np.abs(b - b0).max()), 1e-300)
+        return r
+
+    def rms(stt):
+        return np.sqrt(np.maximum(stt[2:5] - np.array([stt[0] ** 2, 0 * stt[0], stt[1] ** 2]), 0.0))
+
+    def run(cname, modes, nsub, steps, warm):
+        c = CONFIGS[cname]
+        kind, p1, p3 = c["filt"]
+        pts = c["Nx"] * c["Ny"] * c["Nz"]
+        res, s0 = {}, None
+        for mode in modes:
+            torch.cuda.empty_cache()
+            ch = chan.Channel(c["re"], c["Lx"], c["Lz"], c["Nx"], c["Ny"], c["Nz"], c["dt"], precision=precs[mode],
+                              stream=stream.cuda_stream)
+            try:
+                if s0 is None:
+                    s0 = SY.turbulent_like(ch.grid(), c["re"], c["Lx"], c["Lz"], c["Nx"], c["Nz"], seed=1)
+                ch.set_state(s0["v"], s0["omega2"], s0["U1"], s0["U3"])
+                ch.filter_stresses(kind, p1, p3, want=False)
+                st0 = ch.stats()[0]
+                shapes = ch.tuned_shape() if args.no_autotune else ch.autotune()
+                ch.set_state(s0["v"], s0["omega2"], s0["U1"], s0["U3"])
+                for _ in range(warm):
+                    ch.step(nsub)
+                    ch.filter_stresses(kind, p1, p3, want=False)
+                    ch.stats()
+                ch.profile(True)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(steps):
+                    ch.step(nsub)
+                    ch.filter_stresses(kind, p1, p3, want=False)
+                    stt = ch.stats()[0]
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1)
+                prof = ch.profile_read()
+                ch.profile(False)
+            finally:
+                ch.close()
+            tot = max(1e-9, sum(v[0] for v in prof.values()))
+            dom = max(prof, key=lambda k: prof[k][0])
+            by = step_bytes(c, mode, nsub)
+            dms, dn = prof[dom]
+            hb = measured_peaks().get("hbm_gbs") or 6400.0
+            f32k = mode in ("mixed", "mixed_df") and dom in ("k_xpass", "k_zinv", "k_zfwd")
+            alu_peak = FP32_PEAK_DERIVED_TFLOPS if f32k else FP64_PEAK_DERIVED_TFLOPS
+            alu = step_flops(c, nsub).get(dom, 0.0) * steps / (dms * 1e-3) / 1e12 if dms else 0.0
+            res[mode] = {"value": pts * nsub * steps / (ms * 1e-3) / 1e6, "unit": "Mpts*substep/s",
+                         "ms_per_step": ms / steps, "substeps_timed": nsub * steps, "launch_shapes": shapes,
+                         "kernel_shares": {k: round(v[0] / tot, 4) for k, v in prof.items() if v[1]},
+                         "roofline": {"kernel": dom, "bound": "alu", "achieved_tflops": alu,
+                                      "peak_tflops": alu_peak, "frac": alu / alu_peak,
+                                      "hbm_kernel_gbs": by.get(dom, 0.0) * steps / dn / (dms / dn * 1e-3) / 1e9,
+                                      "hbm_kernel_frac": by.get(dom, 0.0) * steps / (dms * 1e-3) / 1e9 / hb,
+                                      "hbm_step_gbs": sum(by.values()) * steps / (ms * 1e-3) / 1e9,
+                                      "hbm_step_frac": sum(by.values()) * steps / (ms * 1e-3) / 1e9 / hb,
+                                      "hbm_peak_gbs": hb},
+                         "_stats": stt, "_stats0": st0}
+        if "fp64" in res:
+            ref, ref0 = res["fp64"]["_stats"], res["fp64"]["_stats0"]
+            for mode in modes:
+                if mode == "fp64":
+                    continue
+                stt = res[mode]["_stats"]
+                res[mode]["err_vs_gpu_fp64"] = {
+                    "after_substeps": nsub * (warm + steps),
+                    "reference": "the FP64 run of the same configuration (held to the FP64 oracle at 1e-10 "
+                                 "relative L2 by the parity tests)",
+                    "mean_profile": prof_err(stt[0], ref[0], ref0[0]),
+                    "rms_profiles": prof_err(rms(stt), rms(ref), rms(ref0)),
+                    "tau_profiles": prof_err(stt[14:20], ref[14:20], ref0[14:20]),
+                    "uu_profiles": prof_err(stt[2:8], ref[2:8], ref0[2:8])}
+        for mode in modes:
+            res[mode].pop("_stats")
+            res[mode].pop("_stats0")
+        return {"config": workload_config(cname, c, "/".join(modes)), "filter_every_substeps": nsub,
+                "modes": res}
+
+    out["re1000_768x385x768"] = run("re1000_768x385x768", ("fp64", "mixed", "mixed_df"), 500, 1, 0)
+    out["re2000_1536x633x1152"] = run("re2000_1536x633x1152", ("mixed",), 20, 2, 1)
+    return out
 
 
 def run_serving(args, rank):
@@ -595,6 +879,9 @@ def main():
     ap.add_argument("--config", choices=sorted(CONFIGS), default=DEFAULT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the Re 1000 and Re 2000 mixed-precision configuration runs")
+    ap.add_argument("--no-autotune", action="store_true", help="default launch shapes (profiling runs)")
     args = ap.parse_args()
     c = CONFIGS[args.config]
     if args.precision_study:
