@@ -89,7 +89,7 @@ typedef struct chan_opts {
                         do not depend on it                                              */
   int y_tables;      /* where the wall-normal sweeps read their mode-independent tables:
                         1 in place from global memory, 2 staged in shared memory, 0 staged
-                        unless that needs more than 48 KB per CTA (chan_autotune may
+                        unless that needs more than 16 KB per CTA (chan_autotune may
                         change it).  Results do not depend on it                        */
 } chan_opts;
 
@@ -141,7 +141,7 @@ int chan_optimize_mesh(const chan_opts* o, int iters, double C, double* y, doubl
 
 /*
  * Autotuner (no paper counterpart): times the z-pass with 1, 2, 4, 8 and 16
- * columns per CTA, the x-pass with 128, 192, 256, 288, 384 and 512 threads per CTA, and the
+ * columns per CTA, the x-pass with 96, 128, 160, 192, 256, 288, 384 and 512 threads per CTA, and the
  * wall-normal sweeps with their mode-independent tables staged in shared
  * memory or read in place from global memory, on the current state; keeps
  * the fastest and caches the choice for every later handle of the same
@@ -149,7 +149,7 @@ int chan_optimize_mesh(const chan_opts* o, int iters, double C, double* y, doubl
  * relocate identical arithmetic, so results are bitwise unchanged.  Needs a
  * state; overwrites only scratch; synchronises.  chan_tuned_shape reports
  * the shapes in use (ytab_global: 1 when the sweeps read their tables in
- * place; by default they do when staging would need more than 48 KB per CTA).
+ * place; by default they do when staging would need more than 16 KB per CTA).
  */
 int chan_autotune(chan_t h);
 int chan_tuned_shape(chan_t h, int* kb_z, int* xthreads, int* ytab_global);

@@ -36,10 +36,13 @@ int bad(chan_s* h, const std::string& msg, int code = CHAN_EINVAL) {
   return code;
 }
 
+// Device memory of a handle comes from the device's stream-ordered pool on the handle's
+// stream (cudaMallocAsync / cudaFreeAsync): releasing a run does not synchronise the
+// device, so a serving loop that retires runs keeps the other runs' work in flight.
 template <typename T>
 T* dalloc(chan_s* h, size_t n) {
   void* p = nullptr;
-  cudaError_t e = cudaMalloc(&p, n * sizeof(T));
+  cudaError_t e = cudaMallocAsync(&p, n * sizeof(T), h->stream);
   if (e != cudaSuccess) {
     cudaGetLastError();   // a failed allocation must not surface later as a launch error
     h->err = std::string("cudaMalloc of ") + std::to_string(n * sizeof(T)) + " bytes: " + cudaGetErrorString(e);
@@ -247,6 +250,10 @@ size_t footprint_ex(int Nx, int Ny, int Nz, int prec, int slab_req, int lean) {
   if (prec_pairs(prec))
     b += ((size_t)Ny * 7 * C + nslot * (size_t)Ny * 11 * C + nslot * 4 * C + 30 * (size_t)Ny) * sizeof(dfr);
   b += (L1 + L3) * (prec_t32(prec) ? sizeof(float2) : sizeof(double2));             // twiddles
+  {                                                                                          // two-pass twiddles (x)
+    int r1, r2;
+    if (prec_t32(prec) && fft_split((int)L1, &r1, &r2)) b += (size_t)r1 * (r2 + 1) * sizeof(float2);
+  }
   b += (L1 + L3) * sizeof(int);                                                              // block twiddle exponents
   const size_t S = slab_planes(Nx, Ny, Nz, prec, slab_req);
   b += (size_t)NWF * n * sizeof(double2);                                                    // work fields
@@ -446,7 +453,7 @@ int chan_init_ex(chan_t* out, const chan_opts* o) {
   if (o->y_tables < 0 || o->y_tables > 2) return bad(nullptr, "chan_init: y_tables must be 0, 1 or 2");
   const int L1 = 3 * o->Nx / 2, L3 = 3 * o->Nz / 2;
   const size_t es = prec_t32(o->precision) ? 8 : 16;
-  if (2 * 6 * (size_t)fft_ld(L1, es) * es > 227 * 1024 || 2 * (size_t)fft_ld(L3, es) * es > 100 * 1024)
+  if (2 * 6 * (size_t)fft_ld_x(L1, es) * es > 227 * 1024 || 2 * (size_t)fft_ld(L3, es) * es > 100 * 1024)
     return bad(nullptr, "chan_init: 3Nx/2 or 3Nz/2 too long for an in-block transform at this precision "
                         "(FP64 and double-float: Nx <= 768, the two mixed modes: Nx <= 1536)");
   chan_s* h = new (std::nothrow) chan_s();
@@ -498,6 +505,12 @@ int chan_init_ex(chan_t* out, const chan_opts* o) {
         Ls *= pl->radix[s];
         pl->mag_mdit[s] = mag(Ls / pl->radix[s]);
       }
+      pl->r1 = pl->r2 = 0;
+      pl->mag_r1 = 0;
+      pl->tw2p = nullptr;
+      // FP32 x transforms run as two register passes; the z transforms keep the stage form (with
+      // KB columns per CTA the register passes left too few warps to hide the column loads)
+      if (prec_t32(h->prec) && pl == &h->p1 && fft_split(pl->L, &pl->r1, &pl->r2)) pl->mag_r1 = mag(pl->r1);
     }
     const size_t n = fsize(h), Ny = h->Ny;
     // state
@@ -561,6 +574,19 @@ int chan_init_ex(chan_t* out, const chan_opts* o) {
         for (size_t k = 0; k < twf.size(); ++k) twf[k] = (float)tw[k];
         d = dalloc<float2>(h, L);
         CK(cudaMemcpy(d, twf.data(), L * sizeof(float2), cudaMemcpyHostToDevice));
+        FftPlan* pl = which ? &h->p3 : &h->p1;
+        if (pl->r1) {   // two-pass twiddles w_L^(-n2 k1), rows of r2 + 1
+          const int r1 = pl->r1, r2 = pl->r2;
+          std::vector<float> t2(2 * (size_t)r1 * (r2 + 1), 0.f);
+          for (int k1 = 0; k1 < r1; ++k1)
+            for (int n2 = 0; n2 < r2; ++n2) {
+              t2[2 * ((size_t)k1 * (r2 + 1) + n2)] = twf[2 * (size_t)n2 * k1];
+              t2[2 * ((size_t)k1 * (r2 + 1) + n2) + 1] = twf[2 * (size_t)n2 * k1 + 1];
+            }
+          float2* d2 = dalloc<float2>(h, (size_t)r1 * (r2 + 1));
+          CK(cudaMemcpy(d2, t2.data(), t2.size() * sizeof(float), cudaMemcpyHostToDevice));
+          pl->tw2p = d2;
+        }
       }
       (which ? h->tw3 : h->tw1) = d;
     }
@@ -619,7 +645,10 @@ void chan_free(chan_t h) {
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   for (ProfRec& r : h->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (void* p : h->allocs)
-    if (p) cudaFree(p);
+    if (p) cudaFreeAsync(p, h->stream);
+  // wait for this stream only: the frees complete and the pool hands the memory back
+  // (its release threshold is 0), so a following large allocation finds it
+  if (h->stream) cudaStreamSynchronize(h->stream);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
 }
@@ -903,7 +932,7 @@ int chan_database_record(chan_t h, double p1, double p3, double* rec, int* m1, i
     const size_t blk = (size_t)h->Ny * M3 * M1;
     if (h->dbrec_n < 10 * blk) {
       if (h->dbrec) {
-        cudaFree(h->dbrec);
+        cudaFreeAsync(h->dbrec, h->stream);
         for (auto& p : h->allocs)
           if (p == h->dbrec) p = nullptr;
         h->dev_bytes -= h->dbrec_n * sizeof(double2);
@@ -1077,12 +1106,15 @@ int chan_autotune(chan_t h) {
     // 256 threads stay unless another shape is more than 2 % faster
     // (192, 288 and 384 divide the butterfly counts of the 576-point stages: no ragged
     // last round of a stage loop)
-    constexpr int NNT = 6;
+    constexpr int NNT = 8;
     float t_nt[NNT];
     for (float& t : t_nt) t = 1e30f;
-    const int nts[NNT] = {256, 128, 192, 288, 384, 512};
+    // (96 and 160 suit the FP32 two-pass transforms: 6 x 24 register transforms per pass)
+    const int nts[NNT] = {256, 128, 192, 288, 384, 512, 96, 160};
+    const int ntmax = fft_plan_category(h->p1) == 3 ? 256 : 512;   // the largest register transforms
     for (int rep = 0; rep < 5; ++rep)
       for (int k = 0; k < NNT; ++k) {
+        if (nts[k] > ntmax) continue;
         h->xthreads = nts[k];
         CK(launch_zinv(h, in, nullptr, mx, 6, ny, 0));
         CK(cudaEventRecord(e0, h->stream));
@@ -1132,7 +1164,7 @@ int chan_tuned_shape(chan_t h, int* kb_z, int* xthreads, int* ytab_global) {
   if (kb_z) *kb_z = h->kb_z > 0 ? h->kb_z : pick_kb(h->nxh, h->L3, es);
   if (xthreads) *xthreads = h->xthreads > 0 ? h->xthreads : 256;
   if (ytab_global)
-    *ytab_global = h->ytab > 0 || (h->ytab < 0 && 23 * (size_t)h->Ny * sizeof(double) > 48 * 1024) ? 1 : 0;
+    *ytab_global = ytab_in_place(h->ytab, h->Ny) ? 1 : 0;
   return CHAN_OK;
 }
 

@@ -14,6 +14,10 @@
 // fields stored as double-float pairs, with the substep's wall-normal sweeps in pairs.
 inline bool prec_t32(int p) { return p == CHAN_PREC_MIXED || p == CHAN_PREC_MIXED_DF; }
 inline bool prec_pairs(int p) { return p == CHAN_PREC_F64X || p == CHAN_PREC_MIXED_DF; }
+// Where the wall-normal sweeps read their mode-independent tables (ytab as in chan_s): in
+// place from global memory when asked, or by default when staging them (23 values per y
+// point in the Poisson kernel) would pass 16 KB beside the sweeps' prefetch rings.
+inline bool ytab_in_place(int ytab, int Ny) { return ytab > 0 || (ytab < 0 && 23 * (size_t)Ny * sizeof(double) > 16 * 1024); }
 
 // Fourier fields: double2 arrays [Ny][M], M = Nz * (Nx/2), mode m = jz*nxh + kx.
 // Mixed fields (physical z, Fourier kx): [Ny][L3][nxh] of float2 or double2.
@@ -56,6 +60,13 @@ struct FftPlan {
   // radices of stages 0 .. s-1, m = Ls/R); device table of at most L entries
   const int* revK;
   int revoff[16];
+  // FP32 two-pass transforms (see fft_split): L = r1 r2, 0 when the stages above serve
+  // this length; mag_r1 = ceil(2^32 / r1)
+  int r1, r2;
+  unsigned mag_r1;
+  // their twiddles w_L^(-n2 k1) at [k1 (r2 + 1) + n2] (rows padded by one), staged into
+  // shared memory by each CTA
+  const float2* tw2p;
 };
 
 enum { KID_PRE = 0, KID_ZINV, KID_XPASS, KID_ZFWD, KID_NONLIN, KID_HELM, KID_POISSON, KID_MEAN,
@@ -122,7 +133,7 @@ struct chan_s {
   int kb_z;                // columns per z-pass CTA
   int xthreads;            // threads per x-pass CTA
   int ytab;                // y sweeps: 1 read tables from global memory, 0 stage them in shared memory,
-                           // -1 (default) stage them unless that needs more than 48 KB per CTA
+                           // -1 (default) stage them unless that needs more than 16 KB per CTA
   // CUDA graph of one full RK3 step (three substeps), captured on first use
   bool use_graph;
   cudaGraphExec_t gexec;
@@ -201,3 +212,10 @@ cudaError_t fft_configure(chan_s* h);
 int pick_kb(int nxh, int L3, size_t es);
 // Row stride (elements) of an in-CTA transform buffer of length L and element size es.
 int fft_ld(int L, size_t es);
+// The same for the x-pass rows (the FP32 two-pass layout when L has a split).
+int fft_ld_x(int L, size_t es);
+// The two factors of an FP32 two-pass transform of length L (both register-resident
+// transform sizes, r1 even); false when L has no such split (the stage transforms serve it).
+bool fft_split(int L, int* r1, int* r2);
+// Register-transform category of a plan (0: stage transforms; 3: at most 256 x-pass threads).
+int fft_plan_category(const FftPlan& pl);

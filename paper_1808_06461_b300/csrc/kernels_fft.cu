@@ -456,10 +456,232 @@ __device__ __forceinline__ void ct_loop(T2* a, int L, int nb, int ld, const T2* 
 template <typename T2> struct IsPair { static constexpr bool v = false; };
 template <> struct IsPair<dfc> { static constexpr bool v = true; };
 
+// ---------------------------------------------------------------------------
+// FP32 two-pass transforms.  For L = R1 R2 with both factors small (2^a 3^b <= 48), a
+// transform is two sets of register-resident DFTs with one exchange through shared
+// memory (Cooley-Tukey in "four-step" order, w_N = exp(2 pi i / N)):
+//   inverse  x[R2 n1 + n2] = sum_k1 w_R1^(n1 k1) [ w_L^(n2 k1) sum_k2 X[k1 + R1 k2] w_R2^(n2 k2) ]
+//   forward  X[k1 + R1 k2] = sum_n2 w_R2^(-n2 k2) [ w_L^(-n2 k1) sum_n1 x[R2 n1 + n2] w_R1^(-n1 k1) ]
+// Every index inside a register DFT is a compile-time constant, and so is every twiddle
+// (template arguments), so a DFT is straight-line arithmetic on registers; the stage
+// transforms instead spend most of their instructions on shared-memory traffic and index
+// arithmetic.  Slot s = c + R1 r of a row lives at element r (R1 + 1) + c (rows of R1
+// padded by one, R1 even): the column sweeps (stride R1) and the row sweeps (unit
+// stride) of a warp both fall in distinct banks.  In place: the inverse takes spectrum
+// entry k from slot k and leaves sample x[R2 n1 + n2] in slot n1 + R1 n2; the forward
+// reads that order and returns the spectrum to natural slots.  Each sweep reads and
+// writes only its own slots, so one barrier separates the two.
+// ---------------------------------------------------------------------------
+constexpr double kPiD = 3.14159265358979323846264338327950288;
+// sin and cos of 2 pi e / n (integers; e may be negative) by their Taylor series on the
+// angle reduced to [-pi, pi]: evaluated by the compiler for the twiddles below.
+__host__ __device__ constexpr double red_angle(int e, int n) {
+  int r = ((e % n) + n) % n;
+  if (2 * r > n) r -= n;
+  return 2.0 * kPiD * r / n;
+}
+__host__ __device__ constexpr double taylor_sin(double x) {
+  double t = x, sum = x;
+  for (int i = 1; i < 30; ++i) { t *= -x * x / ((2.0 * i) * (2.0 * i + 1.0)); sum += t; }
+  return sum;
+}
+__host__ __device__ constexpr double taylor_cos(double x) {
+  double t = 1.0, sum = 1.0;
+  for (int i = 1; i < 30; ++i) { t *= -x * x / ((2.0 * i - 1.0) * (2.0 * i)); sum += t; }
+  return sum;
+}
+
+// In-place DFT of N registers, natural order in and out: y_k = sum_n v_n w_N^(DIR n k).
+// Decimation in time by P = 4 (else 3, else 2): P interleaved DFTs of N / P, then
+// N / P radix-P butterflies with twiddles w_N^(DIR p K).
+template <int N, int DIR> struct RDft;
+template <int DIR> struct RDft<1, DIR> { __device__ static __forceinline__ void run(float2*) {} };
+template <int DIR> struct RDft<2, DIR> { __device__ static __forceinline__ void run(float2* v) { dft2<DIR>(v); } };
+template <int DIR> struct RDft<3, DIR> { __device__ static __forceinline__ void run(float2* v) { dft3<DIR>(v); } };
+template <int DIR> struct RDft<4, DIR> { __device__ static __forceinline__ void run(float2* v) { dft4<DIR>(v); } };
+template <int N, int DIR> struct RDft {
+  static constexpr int P = N % 4 == 0 ? 4 : (N % 3 == 0 ? 3 : 2);
+  static constexpr int Q = N / P;
+  static_assert(P * Q == N && Q > 1, "N must be 2^a 3^b");
+  template <int p, int K>
+  __device__ static __forceinline__ void twiddle(float2 (&t)[P], float2 (&s)[P][Q]) {
+    if constexpr (p < P) {
+      constexpr int q4 = (((4 * DIR * p * K) / N) % 4 + 4) % 4;   // the twiddle is i^q4 when exact
+      if constexpr (K == 0 || p == 0) {
+        t[p] = s[p][K];
+      } else if constexpr ((4 * p * K) % N == 0) {
+        const float2 x = s[p][K];
+        t[p] = q4 == 0 ? x : (q4 == 1 ? make_float2(-x.y, x.x) : (q4 == 2 ? make_float2(-x.x, -x.y) : make_float2(x.y, -x.x)));
+      } else {
+        constexpr float c = (float)taylor_cos(red_angle(DIR * p * K, N));
+        constexpr float sn = (float)taylor_sin(red_angle(DIR * p * K, N));
+        const float2 x = s[p][K];
+        t[p] = make_float2(fmaf(c, x.x, -sn * x.y), fmaf(c, x.y, sn * x.x));
+      }
+      twiddle<p + 1, K>(t, s);
+    }
+  }
+  template <int K>
+  __device__ static __forceinline__ void combine(float2* v, float2 (&s)[P][Q]) {
+    if constexpr (K < Q) {
+      float2 t[P];
+      twiddle<0, K>(t, s);
+      if constexpr (P == 4) dft4<DIR>(t);
+      else if constexpr (P == 3) dft3<DIR>(t);
+      else dft2<DIR>(t);
+#pragma unroll
+      for (int j = 0; j < P; ++j) v[K + Q * j] = t[j];
+      combine<K + 1>(v, s);
+    }
+  }
+  __device__ static __forceinline__ void run(float2* v) {
+    float2 s[P][Q];
+#pragma unroll
+    for (int p = 0; p < P; ++p)
+#pragma unroll
+      for (int q = 0; q < Q; ++q) s[p][q] = v[P * q + p];
+#pragma unroll
+    for (int p = 0; p < P; ++p) RDft<Q, DIR>::run(s[p]);
+    combine<0>(v, s);
+  }
+};
+
+// Inverse of nb rows at a + b ld: spectrum entries with index in [zlo, zhi] are zero (the
+// 3/2 padding) and not read.  ts: the CTA's shared copy of the plan's twiddles, w_L^(-n2 k1)
+// at [k1 (R2 + 1) + n2] (the padding keeps both sweeps' reads in distinct banks).
+template <int R1, int R2>
+__device__ __forceinline__ void fft2p_inv(float2* a, int nb, int ld, const float2* ts, int zlo, int zhi) {
+  constexpr int RS = R1 + 1;
+  for (int it = threadIdx.x; it < nb * R1; it += blockDim.x) {
+    const int b = it / R1, k1 = it - b * R1;
+    float2* col = a + b * ld + k1;
+    float2 v[R2];
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) {
+      const int k = k1 + R1 * k2;
+      v[k2] = (k >= zlo && k <= zhi) ? make_float2(0.f, 0.f) : col[k2 * RS];
+    }
+    RDft<R2, +1>::run(v);
+#pragma unroll
+    for (int n2 = 1; n2 < R2; ++n2) {   // times w_L^(n2 k1), the conjugate of the table's entry
+      const float2 w = ts[k1 * (R2 + 1) + n2];
+      v[n2] = make_float2(fmaf(w.x, v[n2].x, w.y * v[n2].y), fmaf(w.x, v[n2].y, -w.y * v[n2].x));
+    }
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) col[n2 * RS] = v[n2];
+  }
+  __syncthreads();
+  for (int it = threadIdx.x; it < nb * R2; it += blockDim.x) {
+    const int b = it / R2, n2 = it - b * R2;
+    float2* row = a + b * ld + n2 * RS;
+    float2 v[R1];
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) v[k1] = row[k1];
+    RDft<R1, +1>::run(v);
+#pragma unroll
+    for (int n1 = 0; n1 < R1; ++n1) row[n1] = v[n1];
+  }
+  __syncthreads();
+}
+
+// Forward of nb rows in the inverse's output order; spectrum entries with index in
+// [zlo, zhi] are not stored (the 3/2 truncation).
+template <int R1, int R2>
+__device__ __forceinline__ void fft2p_fwd(float2* a, int nb, int ld, const float2* ts, int zlo, int zhi) {
+  constexpr int RS = R1 + 1;
+  for (int it = threadIdx.x; it < nb * R2; it += blockDim.x) {
+    const int b = it / R2, n2 = it - b * R2;
+    float2* row = a + b * ld + n2 * RS;
+    float2 v[R1];
+#pragma unroll
+    for (int n1 = 0; n1 < R1; ++n1) v[n1] = row[n1];
+    RDft<R1, -1>::run(v);
+#pragma unroll
+    for (int k1 = 1; k1 < R1; ++k1) {   // times w_L^(-n2 k1)
+      const float2 w = ts[k1 * (R2 + 1) + n2];
+      v[k1] = make_float2(fmaf(w.x, v[k1].x, -w.y * v[k1].y), fmaf(w.x, v[k1].y, w.y * v[k1].x));
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) row[k1] = v[k1];
+  }
+  __syncthreads();
+  for (int it = threadIdx.x; it < nb * R1; it += blockDim.x) {
+    const int b = it / R1, k1 = it - b * R1;
+    float2* col = a + b * ld + k1;
+    float2 v[R2];
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) v[n2] = col[n2 * RS];
+    RDft<R2, -1>::run(v);
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) {
+      const int k = k1 + R1 * k2;
+      if (!(k >= zlo && k <= zhi)) col[k2 * RS] = v[k2];
+    }
+  }
+  __syncthreads();
+}
+
+// The splits the FP32 path runs as two passes (R1 even; the host's fft_split lists the
+// same pairs).  Returns false for other lengths.
+#define CHAN_FFT2P_SPLITS(X) \
+  X(4, 3) X(6, 3) X(6, 4) X(6, 6) X(8, 6) X(6, 9) X(8, 9) X(8, 12) X(12, 12) X(16, 12) X(16, 18) X(16, 24) \
+  X(24, 24) X(32, 24) X(32, 36) X(32, 48) X(48, 36) X(48, 48)
+
+// Register-size category of a split: 1 (factors <= 16), 2 (<= 24), 3 (<= 48).  A kernel
+// instance of category c holds the splits of categories 1 .. c, so its register allocation
+// follows the largest register transform it may run.
+__host__ __device__ constexpr int fft2p_cat(int a, int b) {
+  return (a > b ? a : b) <= 16 ? 1 : ((a > b ? a : b) <= 24 ? 2 : 3);
+}
+
+template <int DIR, int CAT>
+__device__ __forceinline__ bool fft2p(float2* a, int nb, int ld, const float2* ts, const FftPlan& pl, bool zmid) {
+  const int L = pl.L, zlo = zmid ? L / 3 : 1, zhi = zmid ? 2 * L / 3 : 0;
+#define CHAN_FFT2P_CASE(A, B)                                              \
+  if constexpr (fft2p_cat(A, B) <= CAT) {                                  \
+    if (pl.r1 == A && pl.r2 == B) {                                        \
+      if (DIR > 0) fft2p_inv<A, B>(a, nb, ld, ts, zlo, zhi);               \
+      else fft2p_fwd<A, B>(a, nb, ld, ts, zlo, zhi);                       \
+      return true;                                                         \
+    }                                                                      \
+  }
+  CHAN_FFT2P_SPLITS(CHAN_FFT2P_CASE)
+#undef CHAN_FFT2P_CASE
+  return false;
+}
+
+// A CTA's shared copy of the two-pass twiddles, placed at `end` (after its rows); null when
+// the stage transforms run.  Read only after the CTA's next barrier.
+template <typename T2>
+__device__ __forceinline__ const float2* stage_tw2p(T2* end, const FftPlan& pl) {
+  if constexpr (std::is_same<T2, float2>::value) {
+    if (pl.r1) {
+      const int n = pl.r1 * (pl.r2 + 1);
+      for (int i = threadIdx.x; i < n; i += blockDim.x) end[i] = pl.tw2p[i];
+      return end;
+    }
+  }
+  return nullptr;
+}
+
+// Slot of element i of a transform row: the two-pass padded layout, the FP32 swizzle of
+// the stage transforms, or i.
+template <typename T2>
+__device__ __forceinline__ int slot(int i, const FftPlan& pl) {
+  if constexpr (std::is_same<T2, float2>::value) {
+    if (pl.r1) return i + (int)__umulhi((unsigned)i, pl.mag_r1);
+  }
+  return sw<T2>(i);
+}
+
 // Inverse transform (spectral -> physical) of nb sequences: natural in, digit-reversed out.
 // zmid: the middle third of the input is zero (3/2 padding).
-template <int DIR, typename T2>
-__device__ void fft_inv(T2* a, int L, int nb, int ld, const T2* __restrict__ tw, const FftPlan& pl, bool zmid) {
+template <int DIR, int CAT, typename T2>
+__device__ void fft_inv(T2* a, int L, int nb, int ld, const T2* __restrict__ tw, const FftPlan& pl, bool zmid,
+                        const float2* ts) {
+  if constexpr (std::is_same<T2, float2>::value && CAT > 0) {
+    if (pl.r1 && fft2p<DIR, CAT>(a, nb, ld, ts, pl, zmid)) return;
+  }
   if constexpr (IsPair<T2>::v) {
     fft_dif<DIR>(a, L, nb, ld, tw, pl, zmid);
   } else {
@@ -484,8 +706,12 @@ __device__ void fft_inv(T2* a, int L, int nb, int ld, const T2* __restrict__ tw,
 
 // Forward transform (physical -> spectral): digit-reversed in (as fft_inv leaves it),
 // natural out.  zmid: the middle third of the output is not needed (3/2 truncation).
-template <int DIR, typename T2>
-__device__ void fft_fwd(T2* a, int L, int nb, int ld, const T2* __restrict__ tw, const FftPlan& pl, bool zmid) {
+template <int DIR, int CAT, typename T2>
+__device__ void fft_fwd(T2* a, int L, int nb, int ld, const T2* __restrict__ tw, const FftPlan& pl, bool zmid,
+                        const float2* ts) {
+  if constexpr (std::is_same<T2, float2>::value && CAT > 0) {
+    if (pl.r1 && fft2p<DIR, CAT>(a, nb, ld, ts, pl, zmid)) return;
+  }
   if constexpr (IsPair<T2>::v) {
     fft_dit<DIR>(a, L, nb, ld, tw, pl, zmid);
   } else {
@@ -537,17 +763,17 @@ __device__ __forceinline__ void zinv_load(const ZArgs& A, T2* a, const double2* 
     const int q = jz * A.nxh + kx;
     const int pz = jz < hz ? jz : jz + (A.L3 - A.Nz);
     if constexpr (KIND == 2) {
-      if constexpr (std::is_same<T2, float2>::value) a[kl * A.ld + sw<T2>(pz)] = in32[q];
+      if constexpr (std::is_same<T2, float2>::value) a[kl * A.ld + slot<T2>(pz, A.pl)] = in32[q];
     } else if constexpr (KIND >= 3) {
       if constexpr (std::is_same<T2, float2>::value)
-        a[kl * A.ld + sw<T2>(pz)] = ld_pair_f32(in, q, KIND == 4, KIND == 4 ? A.G[q] : 0.0);
+        a[kl * A.ld + slot<T2>(pz, A.pl)] = ld_pair_f32(in, q, KIND == 4, KIND == 4 ? A.G[q] : 0.0);
     } else {
-      a[kl * A.ld + sw<T2>(pz)] = ld_fourier<T2>(in, q, KIND == 1, KIND == 1 ? A.G[q] : 0.0);
+      a[kl * A.ld + slot<T2>(pz, A.pl)] = ld_fourier<T2>(in, q, KIND == 1, KIND == 1 ? A.G[q] : 0.0);
     }
   }
 }
 
-template <typename T>
+template <typename T, int CAT>
 __device__ __forceinline__ void zinv_body(const ZArgs& A, const typename V2<T>::t* __restrict__ tw, int bx, int by,
                                           int bz) {
   typedef typename V2<T>::t T2;
@@ -558,7 +784,7 @@ __device__ __forceinline__ void zinv_body(const ZArgs& A, const typename V2<T>::
   // The first stage skips the middle third of each padded column, and the load below
   // writes every other slot except the dropped kz Nyquist row at 2 L3/3: only that one
   // is zeroed (no conflict with the loads, so no barrier in between).
-  for (int kl = threadIdx.x; kl < A.KB; kl += blockDim.x) a[kl * A.ld + sw<T2>(A.L3 - hz)] = zero2<T2>();
+  for (int kl = threadIdx.x; kl < A.KB; kl += blockDim.x) a[kl * A.ld + slot<T2>(A.L3 - hz, A.pl)] = zero2<T2>();
   const bool f32 = (A.f32_mask >> f) & 1;
   const double2* in = A.in[f] + (size_t)y * A.M;
   const float2* in32 = reinterpret_cast<const float2*>(A.in[f]) + (size_t)y * A.M;
@@ -569,20 +795,21 @@ __device__ __forceinline__ void zinv_body(const ZArgs& A, const typename V2<T>::
     else zinv_load<T2, 3>(A, a, in, in32, kx0, hz);
   } else if (A.applyG[f]) zinv_load<T2, 1>(A, a, in, in32, kx0, hz);
   else zinv_load<T2, 0>(A, a, in, in32, kx0, hz);
+  const float2* ts = stage_tw2p<T2>(a + A.KB * A.ld, A.pl);
   __syncthreads();
   // the middle third of the padded column is zero: pruned first stage
-  fft_inv<+1>(a, A.L3, A.KB, A.ld, tw, A.pl, true);
+  fft_inv<+1, CAT>(a, A.L3, A.KB, A.ld, tw, A.pl, true, ts);
   // physical rows leave in digit-reversed z order (slot = position in the column)
   T2* out = reinterpret_cast<T2*>(A.out[f]) + (size_t)y * A.L3 * A.nxh;
   for (int e = threadIdx.x; e < A.L3 * A.KB; e += blockDim.x) {
     const int z = e >> A.lgKB, kl = e & (A.KB - 1), kx = kx0 + kl;
-    if (kx < A.nxh) out[z * A.nxh + kx] = a[kl * A.ld + sw<T2>(z)];   // 32-bit index within the plane
+    if (kx < A.nxh) out[z * A.nxh + kx] = a[kl * A.ld + slot<T2>(z, A.pl)];   // 32-bit index within the plane
   }
 }
 
-template <typename T>
+template <typename T, int CAT>
 __global__ void __launch_bounds__(256) k_zinv(ZArgs A, const typename V2<T>::t* __restrict__ tw) {
-  zinv_body<T>(A, tw, blockIdx.x, blockIdx.y, blockIdx.z);
+  zinv_body<T, CAT>(A, tw, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 
@@ -594,14 +821,14 @@ __device__ __forceinline__ void zfwd_store(const ZArgs& A, const T2* r, double2*
     if (kx >= A.nxh) continue;
     if (jz != hz) {
       const int pz = jz < hz ? jz : jz + (A.L3 - A.Nz);
-      st_fourier<T2>(out, jz * A.nxh + kx, r[kl * A.ld + sw<T2>(pz)], PAIR);
+      st_fourier<T2>(out, jz * A.nxh + kx, r[kl * A.ld + slot<T2>(pz, A.pl)], PAIR);
     } else {
       out[jz * A.nxh + kx] = make_double2(0.0, 0.0);
     }
   }
 }
 
-template <typename T>
+template <typename T, int CAT>
 __device__ __forceinline__ void zfwd_body(const ZArgs& A, const typename V2<T>::t* __restrict__ tw, int bx, int by,
                                           int bz) {
   typedef typename V2<T>::t T2;
@@ -612,19 +839,20 @@ __device__ __forceinline__ void zfwd_body(const ZArgs& A, const typename V2<T>::
   const T2* in = reinterpret_cast<const T2*>(A.out[f]) + (size_t)y * A.L3 * A.nxh;
   for (int e = threadIdx.x; e < A.L3 * A.KB; e += blockDim.x) {
     const int z = e >> A.lgKB, kl = e & (A.KB - 1), kx = kx0 + kl;
-    a[kl * A.ld + sw<T2>(z)] = kx < A.nxh ? in[z * A.nxh + kx] : zero2<T2>();
+    a[kl * A.ld + slot<T2>(z, A.pl)] = kx < A.nxh ? in[z * A.nxh + kx] : zero2<T2>();
   }
+  const float2* ts = stage_tw2p<T2>(a + A.KB * A.ld, A.pl);
   __syncthreads();
   // digit-reversed rows in, natural kz out; the middle third (truncated) is not formed
-  fft_fwd<-1>(a, A.L3, A.KB, A.ld, tw, A.pl, true);
+  fft_fwd<-1, CAT>(a, A.L3, A.KB, A.ld, tw, A.pl, true, ts);
   double2* out = A.outd[f] + (size_t)y * A.M;
   if (A.pair_out) zfwd_store<T2, 1>(A, a, out, kx0, hz);   // one store loop per output form
   else zfwd_store<T2, 0>(A, a, out, kx0, hz);
 }
 
-template <typename T>
+template <typename T, int CAT>
 __global__ void __launch_bounds__(256) k_zfwd(ZArgs A, const typename V2<T>::t* __restrict__ tw) {
-  zfwd_body<T>(A, tw, blockIdx.x, blockIdx.y, blockIdx.z);
+  zfwd_body<T, CAT>(A, tw, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 
@@ -641,7 +869,7 @@ struct XArgs {
 // (u1, u2, u3, w1, w2, w3) -> H = u x omega (3 outputs).  MODE 1: inputs
 // (u1, u2, u3) -> the six products u_i u_j (11, 22, 33, 12, 13, 23).
 // MODE 2: inputs (w1, w2, w3) -> w_i w_i (1 output).
-template <typename T, int MODE>
+template <typename T, int MODE, int CAT>
 __device__ __forceinline__ void xpass_body(const XArgs& A, const typename V2<T>::t* __restrict__ tw, int bx, int by) {
   typedef typename V2<T>::t T2;
   constexpr int NIN = MODE == 0 ? 6 : 3;
@@ -653,7 +881,7 @@ __device__ __forceinline__ void xpass_body(const XArgs& A, const typename V2<T>:
   const size_t rowoff = ((size_t)y * A.L3 + z0) * nxh;   // rows z0, z0 + 1 of plane y
   // The first stage skips the middle third [nxh, 2 nxh) and the packing below writes every
   // other slot except the dropped kx Nyquist slot 2 nxh: only that one is zeroed.
-  for (int f = threadIdx.x; f < NIN; f += blockDim.x) a[f * ld + sw<T2>(2 * nxh)] = zero2<T2>();
+  for (int f = threadIdx.x; f < NIN; f += blockDim.x) a[f * ld + slot<T2>(2 * nxh, A.pl)] = zero2<T2>();
   // pack rows z0 (real part) and z0+1 (imaginary part) with Hermitian extension in kx
   for (int e = threadIdx.x; e < NIN * nxh; e += blockDim.x) {
     const int f = A.mag_nxh ? (int)__umulhi((unsigned)e, A.mag_nxh) : e, k = e - f * nxh;   // e / nxh
@@ -664,23 +892,24 @@ __device__ __forceinline__ void xpass_body(const XArgs& A, const typename V2<T>:
       T2 c0;
       c0.x = P.x;
       c0.y = Q.x;
-      dstf[sw<T2>(0)] = c0;
+      dstf[slot<T2>(0, A.pl)] = c0;
     } else {
       T2 c1, c2;
       c1.x = P.x - Q.y; c1.y = P.y + Q.x;      // P_k + i Q_k
       c2.x = P.x + Q.y; c2.y = -P.y + Q.x;     // conj(P_k) + i conj(Q_k) at -k
-      dstf[sw<T2>(k)] = c1;
-      dstf[sw<T2>(L1 - k)] = c2;
+      dstf[slot<T2>(k, A.pl)] = c1;
+      dstf[slot<T2>(L1 - k, A.pl)] = c2;
     }
   }
+  const float2* ts = stage_tw2p<T2>(a + 6 * ld, A.pl);
   __syncthreads();
   // kx in [nxh, 2 nxh] is zero padding: pruned first stage; x samples leave digit-reversed
-  fft_inv<+1>(a, L1, NIN, ld, tw, A.pl, true);
+  fft_inv<+1, CAT>(a, L1, NIN, ld, tw, A.pl, true, ts);
   T2* r = a;
   T2* o = a;   // products overwrite their own sample slot (all fields share the order)
   for (int x = threadIdx.x; x < L1; x += blockDim.x) {
     T2 q[NIN];
-    const int xs = sw<T2>(x);
+    const int xs = slot<T2>(x, A.pl);
 #pragma unroll
     for (int f = 0; f < NIN; ++f) q[f] = r[f * ld + xs];
     if (MODE == 0) {
@@ -710,13 +939,13 @@ __device__ __forceinline__ void xpass_body(const XArgs& A, const typename V2<T>:
   }
   __syncthreads();
   // back to natural kx order; the middle third of the spectrum is discarded, so not formed
-  fft_fwd<-1>(a, L1, NOUT, ld, tw, A.pl, true);
+  fft_fwd<-1, CAT>(a, L1, NOUT, ld, tw, A.pl, true, ts);
   const T2* s = a;
   const T half = from_d<T>(0.5 * A.scale);
   for (int e = threadIdx.x; e < NOUT * nxh; e += blockDim.x) {
     const int gq = A.mag_nxh ? (int)__umulhi((unsigned)e, A.mag_nxh) : e, k = e - gq * nxh;   // e / nxh
-    const T2 c = s[gq * ld + sw<T2>(k)];
-    const T2 cm = s[gq * ld + sw<T2>(k == 0 ? 0 : L1 - k)];
+    const T2 c = s[gq * ld + slot<T2>(k, A.pl)];
+    const T2 cm = s[gq * ld + slot<T2>(k == 0 ? 0 : L1 - k, A.pl)];
     T2 F, G;
     F.x = half * (c.x + cm.x); F.y = half * (c.y - cm.y);      // (C_k + conj C_-k) / 2
     G.x = half * (c.y + cm.y); G.y = -half * (c.x - cm.x);     // (C_k - conj C_-k) / 2i
@@ -726,9 +955,10 @@ __device__ __forceinline__ void xpass_body(const XArgs& A, const typename V2<T>:
   }
 }
 
-template <typename T, int MODE>
-__global__ void __launch_bounds__(512) k_xpass(XArgs A, const typename V2<T>::t* __restrict__ tw) {
-  xpass_body<T, MODE>(A, tw, blockIdx.x, blockIdx.y);
+// (category-3 register transforms need more registers than 512 threads leave)
+template <typename T, int MODE, int CAT>
+__global__ void __launch_bounds__(CAT == 3 ? 256 : 512) k_xpass(XArgs A, const typename V2<T>::t* __restrict__ tw) {
+  xpass_body<T, MODE, CAT>(A, tw, blockIdx.x, blockIdx.y);
 }
 
 
@@ -753,22 +983,22 @@ __device__ __forceinline__ int run_of(const int* begin, int n, int b) {
   while (r + 1 < n && b >= begin[r + 1]) ++r;
   return r;
 }
-template <typename T, bool INV>
+template <typename T, bool INV, int CAT>
 __global__ void __launch_bounds__(256) kb_z(ZBatch B) {
   typedef typename V2<T>::t T2;
   const int r = run_of(B.begin, B.n, blockIdx.x);
   const int l = blockIdx.x - B.begin[r];
   const int bx = l % B.gx[r], t = l / B.gx[r];
   const int by = t % B.gy[r], bz = t / B.gy[r];
-  if (INV) zinv_body<T>(B.a[r], (const T2*)B.tw[r], bx, by, bz);
-  else zfwd_body<T>(B.a[r], (const T2*)B.tw[r], bx, by, bz);
+  if (INV) zinv_body<T, CAT>(B.a[r], (const T2*)B.tw[r], bx, by, bz);
+  else zfwd_body<T, CAT>(B.a[r], (const T2*)B.tw[r], bx, by, bz);
 }
-template <typename T>
+template <typename T, int CAT>
 __global__ void __launch_bounds__(256) kb_xpass(XBatch B) {
   typedef typename V2<T>::t T2;
   const int r = run_of(B.begin, B.n, blockIdx.x);
   const int l = blockIdx.x - B.begin[r];
-  xpass_body<T, 0>(B.a[r], (const T2*)B.tw[r], l % B.gx[r], l / B.gx[r]);
+  xpass_body<T, 0, CAT>(B.a[r], (const T2*)B.tw[r], l % B.gx[r], l / B.gx[r]);
 }
 
 template <typename T> size_t esize() { return sizeof(typename V2<T>::t); }
@@ -780,6 +1010,31 @@ template <typename T> size_t esize() { return sizeof(typename V2<T>::t); }
 // different banks; FP32 rows (swizzled in 16-slot groups) hold whole groups.
 int fft_ld(int L, size_t es) { return (es == sizeof(float2) ? 16 * ((L + 15) / 16) : L) + 1; }
 
+// x-pass rows: with FP32 two-pass transforms, r2 (r1 + 1) elements, the stride congruent to r1
+// mod 16 so that a warp's column sweep that runs into the next row keeps to distinct banks.
+int fft_ld_x(int L, size_t es) {
+  int r1, r2;
+  if (es == sizeof(float2) && fft_split(L, &r1, &r2)) {
+    int ld = r2 * (r1 + 1);
+    while ((ld - r1) % 16) ++ld;
+    return ld;
+  }
+  return fft_ld(L, es);
+}
+
+bool fft_split(int L, int* r1, int* r2) {
+#define CHAN_FFT2P_HOST(A, B) \
+  if (L == (A) * (B)) {       \
+    *r1 = A;                  \
+    *r2 = B;                  \
+    return true;              \
+  }
+  CHAN_FFT2P_SPLITS(CHAN_FFT2P_HOST)
+#undef CHAN_FFT2P_HOST
+  *r1 = *r2 = 0;
+  return false;
+}
+
 int pick_kb(int nxh, int L3, size_t es) {
   int kb = 1;
   while (kb * 2 <= nxh && kb * 2 <= 16 && (size_t)(kb * 2) * fft_ld(L3, es) * es <= 56 * 1024) kb *= 2;
@@ -789,20 +1044,66 @@ int pick_kb(int nxh, int L3, size_t es) {
 // Allow the transform kernels the full 227 KB of shared memory (per process; the handle
 // is not needed).
 cudaError_t fft_configure(chan_s*) {
-  const void* fns[] = {(const void*)k_zinv<double>,     (const void*)k_zinv<float>,      (const void*)k_zinv<dfr>,
-                       (const void*)k_zfwd<double>,     (const void*)k_zfwd<float>,      (const void*)k_zfwd<dfr>,
-                       (const void*)k_xpass<double, 0>, (const void*)k_xpass<double, 1>, (const void*)k_xpass<float, 0>,
-                       (const void*)k_xpass<float, 1>,  (const void*)k_xpass<dfr, 0>,    (const void*)k_xpass<dfr, 1>,
-                       (const void*)k_xpass<double, 2>, (const void*)k_xpass<float, 2>,  (const void*)k_xpass<dfr, 2>,
-                       (const void*)kb_z<double, true>, (const void*)kb_z<float, true>,  (const void*)kb_z<dfr, true>,
-                       (const void*)kb_z<double, false>, (const void*)kb_z<float, false>, (const void*)kb_z<dfr, false>,
-                       (const void*)kb_xpass<double>,   (const void*)kb_xpass<float>,    (const void*)kb_xpass<dfr>};
+  const void* fns[] = {(const void*)k_zinv<double, 0>,
+                       (const void*)k_zfwd<double, 0>,
+                       (const void*)k_xpass<double, 0, 0>,
+                       (const void*)k_xpass<double, 1, 0>,
+                       (const void*)k_xpass<double, 2, 0>,
+                       (const void*)kb_z<double, true, 0>,
+                       (const void*)kb_z<double, false, 0>,
+                       (const void*)kb_xpass<double, 0>,
+                       (const void*)k_zinv<dfr, 0>,
+                       (const void*)k_zfwd<dfr, 0>,
+                       (const void*)k_xpass<dfr, 0, 0>,
+                       (const void*)k_xpass<dfr, 1, 0>,
+                       (const void*)k_xpass<dfr, 2, 0>,
+                       (const void*)kb_z<dfr, true, 0>,
+                       (const void*)kb_z<dfr, false, 0>,
+                       (const void*)kb_xpass<dfr, 0>,
+                       (const void*)k_zinv<float, 0>,
+                       (const void*)k_zfwd<float, 0>,
+                       (const void*)k_xpass<float, 0, 0>,
+                       (const void*)k_xpass<float, 1, 0>,
+                       (const void*)k_xpass<float, 2, 0>,
+                       (const void*)kb_z<float, true, 0>,
+                       (const void*)kb_z<float, false, 0>,
+                       (const void*)kb_xpass<float, 0>,
+                       (const void*)k_zinv<float, 1>,
+                       (const void*)k_zfwd<float, 1>,
+                       (const void*)k_xpass<float, 0, 1>,
+                       (const void*)k_xpass<float, 1, 1>,
+                       (const void*)k_xpass<float, 2, 1>,
+                       (const void*)kb_z<float, true, 1>,
+                       (const void*)kb_z<float, false, 1>,
+                       (const void*)kb_xpass<float, 1>,
+                       (const void*)k_zinv<float, 2>,
+                       (const void*)k_zfwd<float, 2>,
+                       (const void*)k_xpass<float, 0, 2>,
+                       (const void*)k_xpass<float, 1, 2>,
+                       (const void*)k_xpass<float, 2, 2>,
+                       (const void*)kb_z<float, true, 2>,
+                       (const void*)kb_z<float, false, 2>,
+                       (const void*)kb_xpass<float, 2>,
+                       (const void*)k_zinv<float, 3>,
+                       (const void*)k_zfwd<float, 3>,
+                       (const void*)k_xpass<float, 0, 3>,
+                       (const void*)k_xpass<float, 1, 3>,
+                       (const void*)k_xpass<float, 2, 3>,
+                       (const void*)kb_z<float, true, 3>,
+                       (const void*)kb_z<float, false, 3>,
+                       (const void*)kb_xpass<float, 3>};
   for (const void* f : fns) {
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
+
+// Register-transform category of a plan's FP32 two-pass split (0: the stage transforms).
+static int plan_cat(const FftPlan& pl) { return pl.r1 ? fft2p_cat(pl.r1, pl.r2) : 0; }
+// Shared bytes of a CTA's copy of the two-pass twiddles.
+static size_t tw2p_bytes(const FftPlan& pl) { return pl.r1 ? (size_t)pl.r1 * (pl.r2 + 1) * sizeof(float2) : 0; }
+int fft_plan_category(const FftPlan& pl) { return plan_cat(pl); }
 
 static ZArgs zargs(chan_s* h, size_t es) {
   ZArgs A;
@@ -827,10 +1128,17 @@ cudaError_t launch_zinv(chan_s* h, const double2* const* in, const int* apply_G,
   A.f32_mask = prec_t32(h->prec) ? f32_mask : 0;
   for (int f = 0; f < nf; ++f) { A.in[f] = in[f]; A.out[f] = out[f]; A.applyG[f] = apply_G ? apply_G[f] : 0; }
   dim3 grid((h->nxh + A.KB - 1) / A.KB, ny, nf);
-  size_t sm = (size_t)A.KB * A.ld * es;
-  if (h->prec == CHAN_PREC_FP64) k_zinv<double><<<grid, 256, sm, h->stream>>>(A, (const double2*)h->tw3);
-  else if (prec_t32(h->prec)) k_zinv<float><<<grid, 256, sm, h->stream>>>(A, (const float2*)h->tw3);
-  else k_zinv<dfr><<<grid, 256, sm, h->stream>>>(A, (const dfc*)h->tw3);
+  size_t sm = (size_t)A.KB * A.ld * es + tw2p_bytes(h->p3);
+  if (h->prec == CHAN_PREC_FP64) k_zinv<double, 0><<<grid, 256, sm, h->stream>>>(A, (const double2*)h->tw3);
+  else if (prec_t32(h->prec)) {
+    const float2* tw = (const float2*)h->tw3;
+    switch (plan_cat(h->p3)) {
+      case 0: k_zinv<float, 0><<<grid, 256, sm, h->stream>>>(A, tw); break;
+      case 1: k_zinv<float, 1><<<grid, 256, sm, h->stream>>>(A, tw); break;
+      case 2: k_zinv<float, 2><<<grid, 256, sm, h->stream>>>(A, tw); break;
+      default: k_zinv<float, 3><<<grid, 256, sm, h->stream>>>(A, tw); break;
+    }
+  } else k_zinv<dfr, 0><<<grid, 256, sm, h->stream>>>(A, (const dfc*)h->tw3);
   return cudaGetLastError();
 }
 
@@ -840,10 +1148,17 @@ cudaError_t launch_zfwd(chan_s* h, void* const* in, double2* const* out, int nf,
   A.pair_out = pair_out && prec_pairs(h->prec);
   for (int f = 0; f < nf; ++f) { A.out[f] = in[f]; A.outd[f] = out[f]; }
   dim3 grid((h->nxh + A.KB - 1) / A.KB, ny, nf);
-  size_t sm = (size_t)A.KB * A.ld * es;
-  if (h->prec == CHAN_PREC_FP64) k_zfwd<double><<<grid, 256, sm, h->stream>>>(A, (const double2*)h->tw3);
-  else if (prec_t32(h->prec)) k_zfwd<float><<<grid, 256, sm, h->stream>>>(A, (const float2*)h->tw3);
-  else k_zfwd<dfr><<<grid, 256, sm, h->stream>>>(A, (const dfc*)h->tw3);
+  size_t sm = (size_t)A.KB * A.ld * es + tw2p_bytes(h->p3);
+  if (h->prec == CHAN_PREC_FP64) k_zfwd<double, 0><<<grid, 256, sm, h->stream>>>(A, (const double2*)h->tw3);
+  else if (prec_t32(h->prec)) {
+    const float2* tw = (const float2*)h->tw3;
+    switch (plan_cat(h->p3)) {
+      case 0: k_zfwd<float, 0><<<grid, 256, sm, h->stream>>>(A, tw); break;
+      case 1: k_zfwd<float, 1><<<grid, 256, sm, h->stream>>>(A, tw); break;
+      case 2: k_zfwd<float, 2><<<grid, 256, sm, h->stream>>>(A, tw); break;
+      default: k_zfwd<float, 3><<<grid, 256, sm, h->stream>>>(A, tw); break;
+    }
+  } else k_zfwd<dfr, 0><<<grid, 256, sm, h->stream>>>(A, (const dfc*)h->tw3);
   return cudaGetLastError();
 }
 
@@ -854,28 +1169,38 @@ cudaError_t launch_xpass(chan_s* h, int mode, void* const* in, void* const* out,
   const int nin = mode == 0 ? 6 : 3, nout = mode == 0 ? 3 : (mode == 1 ? 6 : 1);
   for (int f = 0; f < nin; ++f) A.in[f] = in[f];
   for (int f = 0; f < nout; ++f) A.out[f] = out[f];
-  A.nxh = h->nxh; A.L1 = h->L1; A.L3 = h->L3; A.ld = fft_ld(h->L1, fft_esize(h));
+  A.nxh = h->nxh; A.L1 = h->L1; A.L3 = h->L3; A.ld = fft_ld_x(h->L1, fft_esize(h));
   A.mag_nxh = h->nxh == 1 ? 0u : (unsigned)((((unsigned long long)1 << 32) + h->nxh - 1) / h->nxh);
   A.scale = 1.0 / ((double)h->L1 * (double)h->L3);
   A.pl = h->p1;
   dim3 grid(h->L3 / 2, ny);
-  size_t sm = 6 * (size_t)A.ld * es;
+  size_t sm = 6 * (size_t)A.ld * es + tw2p_bytes(h->p1);
   const int nt = h->xthreads > 0 ? h->xthreads : 256;
   if (h->prec == CHAN_PREC_FP64) {
     const double2* tw = (const double2*)h->tw1;
-    if (mode == 0) k_xpass<double, 0><<<grid, nt, sm, h->stream>>>(A, tw);
-    else if (mode == 1) k_xpass<double, 1><<<grid, nt, sm, h->stream>>>(A, tw);
-    else k_xpass<double, 2><<<grid, nt, sm, h->stream>>>(A, tw);
+    if (mode == 0) k_xpass<double, 0, 0><<<grid, nt, sm, h->stream>>>(A, tw);
+    else if (mode == 1) k_xpass<double, 1, 0><<<grid, nt, sm, h->stream>>>(A, tw);
+    else k_xpass<double, 2, 0><<<grid, nt, sm, h->stream>>>(A, tw);
   } else if (prec_t32(h->prec)) {
     const float2* tw = (const float2*)h->tw1;
-    if (mode == 0) k_xpass<float, 0><<<grid, nt, sm, h->stream>>>(A, tw);
-    else if (mode == 1) k_xpass<float, 1><<<grid, nt, sm, h->stream>>>(A, tw);
-    else k_xpass<float, 2><<<grid, nt, sm, h->stream>>>(A, tw);
+    const int c = plan_cat(h->p1);
+    const int ntc = c == 3 && nt > 256 ? 256 : nt;   // category-3 instances take at most 256 threads
+#define CHAN_XPASS_CAT(C)                                                       \
+  if (mode == 0) k_xpass<float, 0, C><<<grid, ntc, sm, h->stream>>>(A, tw);     \
+  else if (mode == 1) k_xpass<float, 1, C><<<grid, ntc, sm, h->stream>>>(A, tw); \
+  else k_xpass<float, 2, C><<<grid, ntc, sm, h->stream>>>(A, tw);
+    switch (c) {
+      case 0: CHAN_XPASS_CAT(0) break;
+      case 1: CHAN_XPASS_CAT(1) break;
+      case 2: CHAN_XPASS_CAT(2) break;
+      default: CHAN_XPASS_CAT(3) break;
+    }
+#undef CHAN_XPASS_CAT
   } else {
     const dfc* tw = (const dfc*)h->tw1;
-    if (mode == 0) k_xpass<dfr, 0><<<grid, nt, sm, h->stream>>>(A, tw);
-    else if (mode == 1) k_xpass<dfr, 1><<<grid, nt, sm, h->stream>>>(A, tw);
-    else k_xpass<dfr, 2><<<grid, nt, sm, h->stream>>>(A, tw);
+    if (mode == 0) k_xpass<dfr, 0, 0><<<grid, nt, sm, h->stream>>>(A, tw);
+    else if (mode == 1) k_xpass<dfr, 1, 0><<<grid, nt, sm, h->stream>>>(A, tw);
+    else k_xpass<dfr, 2, 0><<<grid, nt, sm, h->stream>>>(A, tw);
   }
   return cudaGetLastError();
 }
@@ -902,14 +1227,22 @@ cudaError_t launch_zinv_batch(chan_s* const* hs, int n, const BatchWork* w, cuda
     B.gy[r] = h->Ny;
     B.begin[r] = acc;
     acc += B.gx[r] * B.gy[r] * 6;
-    const size_t smr = (size_t)A.KB * A.ld * fft_esize(h);
+    const size_t smr = (size_t)A.KB * A.ld * fft_esize(h) + tw2p_bytes(h->p3);
     sm = smr > sm ? smr : sm;
   }
   B.begin[n] = acc;
   const int prec = hs[0]->prec;
-  if (prec == CHAN_PREC_FP64) kb_z<double, true><<<acc, 256, sm, st>>>(B);
-  else if (prec_t32(prec)) kb_z<float, true><<<acc, 256, sm, st>>>(B);
-  else kb_z<dfr, true><<<acc, 256, sm, st>>>(B);
+  int c = 0;   // the largest register-transform category of the runs
+  for (int r = 0; r < n; ++r) c = plan_cat(hs[r]->p3) > c ? plan_cat(hs[r]->p3) : c;
+  if (prec == CHAN_PREC_FP64) kb_z<double, true, 0><<<acc, 256, sm, st>>>(B);
+  else if (prec_t32(prec)) {
+    switch (c) {
+      case 0: kb_z<float, true, 0><<<acc, 256, sm, st>>>(B); break;
+      case 1: kb_z<float, true, 1><<<acc, 256, sm, st>>>(B); break;
+      case 2: kb_z<float, true, 2><<<acc, 256, sm, st>>>(B); break;
+      default: kb_z<float, true, 3><<<acc, 256, sm, st>>>(B); break;
+    }
+  } else kb_z<dfr, true, 0><<<acc, 256, sm, st>>>(B);
   return cudaGetLastError();
 }
 
@@ -931,14 +1264,22 @@ cudaError_t launch_zfwd_batch(chan_s* const* hs, int n, const BatchWork* w, cuda
     B.gy[r] = h->Ny;
     B.begin[r] = acc;
     acc += B.gx[r] * B.gy[r] * 3;
-    const size_t smr = (size_t)A.KB * A.ld * fft_esize(h);
+    const size_t smr = (size_t)A.KB * A.ld * fft_esize(h) + tw2p_bytes(h->p3);
     sm = smr > sm ? smr : sm;
   }
   B.begin[n] = acc;
   const int prec = hs[0]->prec;
-  if (prec == CHAN_PREC_FP64) kb_z<double, false><<<acc, 256, sm, st>>>(B);
-  else if (prec_t32(prec)) kb_z<float, false><<<acc, 256, sm, st>>>(B);
-  else kb_z<dfr, false><<<acc, 256, sm, st>>>(B);
+  int c = 0;
+  for (int r = 0; r < n; ++r) c = plan_cat(hs[r]->p3) > c ? plan_cat(hs[r]->p3) : c;
+  if (prec == CHAN_PREC_FP64) kb_z<double, false, 0><<<acc, 256, sm, st>>>(B);
+  else if (prec_t32(prec)) {
+    switch (c) {
+      case 0: kb_z<float, false, 0><<<acc, 256, sm, st>>>(B); break;
+      case 1: kb_z<float, false, 1><<<acc, 256, sm, st>>>(B); break;
+      case 2: kb_z<float, false, 2><<<acc, 256, sm, st>>>(B); break;
+      default: kb_z<float, false, 3><<<acc, 256, sm, st>>>(B); break;
+    }
+  } else kb_z<dfr, false, 0><<<acc, 256, sm, st>>>(B);
   return cudaGetLastError();
 }
 
@@ -954,7 +1295,7 @@ cudaError_t launch_xpass_batch(chan_s* const* hs, int n, const BatchWork* w, cud
     memset(&A, 0, sizeof(A));
     for (int f = 0; f < 6; ++f) A.in[f] = w[r].mixed[f];
     for (int f = 0; f < 3; ++f) A.out[f] = w[r].mixed[f];
-    A.nxh = h->nxh; A.L1 = h->L1; A.L3 = h->L3; A.ld = fft_ld(h->L1, fft_esize(h));
+    A.nxh = h->nxh; A.L1 = h->L1; A.L3 = h->L3; A.ld = fft_ld_x(h->L1, fft_esize(h));
   A.mag_nxh = h->nxh == 1 ? 0u : (unsigned)((((unsigned long long)1 << 32) + h->nxh - 1) / h->nxh);
     A.scale = 1.0 / ((double)h->L1 * (double)h->L3);
     A.pl = h->p1;
@@ -963,13 +1304,21 @@ cudaError_t launch_xpass_batch(chan_s* const* hs, int n, const BatchWork* w, cud
     B.gx[r] = h->L3 / 2;   // packed launches use 256 threads whatever a run's tuned shape
     B.begin[r] = acc;
     acc += B.gx[r] * h->Ny;
-    const size_t smr = 6 * (size_t)A.ld * fft_esize(h);
+    const size_t smr = 6 * (size_t)A.ld * fft_esize(h) + tw2p_bytes(h->p1);
     sm = smr > sm ? smr : sm;
   }
   B.begin[n] = acc;
   const int prec = hs[0]->prec;
-  if (prec == CHAN_PREC_FP64) kb_xpass<double><<<acc, 256, sm, st>>>(B);
-  else if (prec_t32(prec)) kb_xpass<float><<<acc, 256, sm, st>>>(B);
-  else kb_xpass<dfr><<<acc, 256, sm, st>>>(B);
+  int c = 0;
+  for (int r = 0; r < n; ++r) c = plan_cat(hs[r]->p1) > c ? plan_cat(hs[r]->p1) : c;
+  if (prec == CHAN_PREC_FP64) kb_xpass<double, 0><<<acc, 256, sm, st>>>(B);
+  else if (prec_t32(prec)) {
+    switch (c) {
+      case 0: kb_xpass<float, 0><<<acc, 256, sm, st>>>(B); break;
+      case 1: kb_xpass<float, 1><<<acc, 256, sm, st>>>(B); break;
+      case 2: kb_xpass<float, 2><<<acc, 256, sm, st>>>(B); break;
+      default: kb_xpass<float, 3><<<acc, 256, sm, st>>>(B); break;
+    }
+  } else kb_xpass<dfr, 0><<<acc, 256, sm, st>>>(B);
   return cudaGetLastError();
 }

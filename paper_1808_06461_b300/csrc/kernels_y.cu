@@ -7,6 +7,8 @@
 // N_chi, N_omega2 of Eq. (hghv); the semi-implicit RK3 steps (chi1), (psi);
 // the Poisson problem (chi2) with the influence-matrix wall correction; the
 // mean profiles with a constant mass flux (Sec. 2.1).
+#include <cstdint>
+
 #include "chan_internal.cuh"
 #include "df.cuh"
 
@@ -67,6 +69,69 @@ __device__ __forceinline__ void load_tab(double* dst, const double* src, int n) 
   for (int k = threadIdx.x; k < n; k += blockDim.x) dst[k] = src[k];
 }
 
+// ---------------------------------------------------------------------------
+// Row prefetch ring.  Each sweep reads the rows of its pencil once, in order, and its
+// serial recurrence would otherwise wait on every row's loads.  cp.async copies the
+// values of the row kRing - 1 rows ahead into this thread's own shared-memory slots while
+// the current row is computed.  A slot is written and read by one thread only, so the
+// thread's own cp.async.wait_group is all the synchronisation there is (no barrier, no
+// spin).  Layout per CTA: [kRing][K16][blockDim] slots of 16 bytes, then
+// [kRing][K8][blockDim] slots of 8 bytes; a warp's 32 slots are contiguous.
+// ---------------------------------------------------------------------------
+constexpr int kRing = 4;   // rows in flight per sweep (a power of two)
+
+__device__ __forceinline__ void cp16(void* s, const void* g) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((unsigned)__cvta_generic_to_shared(s)), "l"(g)
+               : "memory");
+}
+__device__ __forceinline__ void cp8(void* s, const void* g) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"((unsigned)__cvta_generic_to_shared(s)), "l"(g)
+               : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+template <int K16, int K8>
+struct Ring {
+  unsigned char* b;
+  __device__ __forceinline__ explicit Ring(void* base) : b(static_cast<unsigned char*>(base)) {}
+  __device__ __forceinline__ unsigned char* f(int st, int k) const {
+    return b + ((size_t)(st * K16 + k) * blockDim.x + threadIdx.x) * 16;
+  }
+  __device__ __forceinline__ unsigned char* t(int st, int k) const {
+    return b + (size_t)kRing * K16 * blockDim.x * 16 + ((size_t)(st * K8 + k) * blockDim.x + threadIdx.x) * 8;
+  }
+  static constexpr size_t per_thread = (size_t)kRing * (K16 * 16 + K8 * 8);
+};
+
+// Runs fn(t) for t = 0 .. n-1 with issue(t) called kRing - 1 rows ahead: on return from
+// the wait, the copies of row t are in this thread's slots of stage t & (kRing - 1).
+template <class Issue, class Body>
+__device__ __forceinline__ void pipelined(int n, Issue issue, Body body) {
+#pragma unroll 1
+  for (int q = 0; q < kRing - 1; ++q) {
+    if (q < n) issue(q, q & (kRing - 1));
+    cp_commit();
+  }
+#pragma unroll 1
+  for (int t = 0; t < n; ++t) {
+    const int tn = t + kRing - 1;
+    if (tn < n) issue(tn, tn & (kRing - 1));
+    cp_commit();
+    cp_wait<kRing - 1>();
+    body(t, t & (kRing - 1));
+  }
+  cp_wait<0>();
+}
+
+// Shared-memory ring base after the staged tables (16-byte aligned).
+__device__ __forceinline__ void* ring_base(void* p) {
+  return reinterpret_cast<void*>((reinterpret_cast<uintptr_t>(p) + 15) & ~(uintptr_t)15);
+}
+
 
 // Arithmetic and storage of the four substep y-kernels, chosen per precision
 // mode: FP64, or double-float (FP32 pairs, about 2^-47) in the double-float mode,
@@ -77,18 +142,19 @@ struct YF64 {
   typedef double2 C;
   __device__ static __forceinline__ R r(double x) { return x; }
   __device__ static __forceinline__ C c(double2 x) { return x; }
-  __device__ static __forceinline__ double2 d(C x) { return x; }
   __device__ static __forceinline__ C zero() { return make_double2(0.0, 0.0); }
   __device__ static __forceinline__ C axpy(R a, C x, C y) { return make_double2(fma(a, x.x, y.x), fma(a, x.y, y.y)); }
   __device__ static __forceinline__ C scl(R a, C x) { return make_double2(a * x.x, a * x.y); }
   __device__ static __forceinline__ C sub(C a, C b) { return make_double2(a.x - b.x, a.y - b.y); }
   __device__ static __forceinline__ C itimes(C a) { return make_double2(-a.y, a.x); }
   __device__ static __forceinline__ R neg(R a) { return -a; }
-  __device__ static __forceinline__ C ld(const double2* p, size_t o) { return p[o]; }
   __device__ static __forceinline__ void st(double2* p, size_t o, C x) { p[o] = x; }
+  // a value copied into a shared-memory ring slot
+  __device__ static __forceinline__ C lds(const unsigned char* q) { return *reinterpret_cast<const double2*>(q); }
+  __device__ static __forceinline__ R ldr(const unsigned char* q) { return *reinterpret_cast<const double*>(q); }
+  __device__ static __forceinline__ float2 ldsf(const unsigned char* q) { return f(lds(q)); }
   // rounded to FP32 (a transform input of the mixed modes), on the integer pipe
   __device__ static __forceinline__ float2 f(C x) { return make_float2(d2f_int(x.x), d2f_int(x.y)); }
-  __device__ static __forceinline__ float2 ldf(const double2* p, size_t o) { return f(p[o]); }
   __device__ static __forceinline__ const R* A2(const YTabs& t) { return t.A2; }
   __device__ static __forceinline__ const R* B2(const YTabs& t) { return t.B2; }
   __device__ static __forceinline__ const R* B1(const YTabs& t) { return t.B1; }
@@ -107,18 +173,19 @@ struct YDF {
   __device__ static __forceinline__ C sub(C a, C b) { return dfc{a.x - b.x, a.y - b.y}; }
   __device__ static __forceinline__ C itimes(C a) { return dfc{-a.y, a.x}; }
   __device__ static __forceinline__ R neg(R a) { return -a; }
-  __device__ static __forceinline__ C ld(const double2* p, size_t o) {
-    const float4 q = reinterpret_cast<const float4*>(p)[o];
-    return dfc{dfr{q.x, q.y}, dfr{q.z, q.w}};
-  }
   __device__ static __forceinline__ void st(double2* p, size_t o, C x) {
     reinterpret_cast<float4*>(p)[o] = make_float4(x.x.h, x.x.l, x.y.h, x.y.l);
   }
-  __device__ static __forceinline__ float2 f(C x) { return make_float2(x.x.h + x.x.l, x.y.h + x.y.l); }
-  __device__ static __forceinline__ float2 ldf(const double2* p, size_t o) {
-    const float4 q = reinterpret_cast<const float4*>(p)[o];
+  __device__ static __forceinline__ C lds(const unsigned char* p) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    return dfc{dfr{q.x, q.y}, dfr{q.z, q.w}};
+  }
+  __device__ static __forceinline__ R ldr(const unsigned char* p) { return *reinterpret_cast<const dfr*>(p); }
+  __device__ static __forceinline__ float2 ldsf(const unsigned char* p) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
     return make_float2(q.x + q.y, q.z + q.w);
   }
+  __device__ static __forceinline__ float2 f(C x) { return make_float2(x.x.h + x.x.l, x.y.h + x.y.l); }
   __device__ static __forceinline__ const R* A2(const YTabs& t) { return t.A2p; }
   __device__ static __forceinline__ const R* B2(const YTabs& t) { return t.B2p; }
   __device__ static __forceinline__ const R* B1(const YTabs& t) { return t.B1p; }
@@ -202,26 +269,149 @@ __device__ __forceinline__ ModeInfo mode_info(const Geo& g, int m) {
 // FP32 from those values and stored as float2: u_1, u_3 in the omega_1 slot ([2][Ny][M]
 // float2), omega_1, omega_3 in the omega_3 slot; the u_1, u_3 slots keep the forward sweep.
 
+// One mode's two D1 sweeps and outputs; MEAN: the (0,0) mode, whose inputs are the mean
+// profiles (a separate instantiation, so no per-row branch on it is issued elsewhere).
+template <class Y, bool F32OUT, bool MEAN>
+__device__ __forceinline__ void pre_sweep(const Geo& g, const typename Y::R* sB1, const typename Y::R* sLU,
+                                          const ModeInfo& mi, int m, const double2* __restrict__ v,
+                                          const double2* __restrict__ om, const double2* __restrict__ dv,
+                                          const double* __restrict__ U1, const double* __restrict__ U3,
+                                          double2* u1o, double2* u3o, double2* om1o, double2* om3o, void* ring) {
+  typedef typename Y::R R;
+  typedef typename Y::C C;
+  const int Ny = g.Ny;
+  const size_t M = g.M;
+  const size_t nf = (size_t)Ny * M;
+  float2* fu = reinterpret_cast<float2*>(om1o);   // F32OUT: u_1 [0, nf), u_3 [nf, 2 nf)
+  float2* fw = reinterpret_cast<float2*>(om3o);   //         omega_1, omega_3
+  Ring<5, 0> rg(ring);
+  C wx[7], ww[7], hx[3], hw[3];
+#pragma unroll
+  for (int d = 0; d < 7; ++d) { wx[d] = Y::zero(); ww[d] = Y::zero(); }
+#pragma unroll
+  for (int d = 0; d < 3; ++d) { hx[d] = Y::zero(); hw[d] = Y::zero(); }
+  // forward sweep of D1 = A1^-1 B1 on x = dv/dy (U1 for the mean) and w = omega_2 (U3),
+  // parked in the u_1, u_3 outputs
+  pipelined(
+      Ny + 3,
+      [&](int t, int st) {
+        if (!MEAN && t < Ny) {
+          const size_t o = (size_t)t * M + m;
+          cp16(rg.f(st, 0), dv + o);
+          cp16(rg.f(st, 1), om + o);
+        }
+      },
+      [&](int t, int st) {
+        C nx = Y::zero(), nw = Y::zero();
+        if (t < Ny) {
+          if (MEAN) { nx = Y::c(make_double2(U1[t], 0.0)); nw = Y::c(make_double2(U3[t], 0.0)); }
+          else { nx = Y::lds(rg.f(st, 0)); nw = Y::lds(rg.f(st, 1)); }
+        }
+        ypush<Y>(wx, nx);
+        ypush<Y>(ww, nw);
+        const int i = t - 3;
+        if (i < 0) return;
+        const R* b = sB1 + 7 * i;
+        const R* l = sLU + 7 * i;
+        Y::st(u1o, (size_t)i * M + m, yfwd<Y>(yband7<Y>(b, wx), l[0], l[1], l[2], hx));
+        Y::st(u3o, (size_t)i * M + m, yfwd<Y>(yband7<Y>(b, ww), l[0], l[1], l[2], hw));
+      });
+  C px[3] = {Y::zero(), Y::zero(), Y::zero()}, pw[3] = {Y::zero(), Y::zero(), Y::zero()};
+  const R q1 = Y::r(MEAN ? 0.0 : mi.k1 / mi.k2), q3 = Y::r(MEAN ? 0.0 : mi.k3 / mi.k2);
+  const R k1 = Y::r(mi.k1), k3 = Y::r(mi.k3);
+  const float q1f = MEAN ? 0.f : (float)(mi.k1 / mi.k2), q3f = MEAN ? 0.f : (float)(mi.k3 / mi.k2);
+  const float k1f = (float)mi.k1, k3f = (float)mi.k3;
+  pipelined(
+      Ny,
+      [&](int q, int st) {
+        const size_t o = (size_t)(Ny - 1 - q) * M + m;
+        cp16(rg.f(st, 0), u1o + o);
+        cp16(rg.f(st, 1), u3o + o);
+        if (!MEAN) {
+          cp16(rg.f(st, 2), dv + o);
+          cp16(rg.f(st, 3), om + o);
+          cp16(rg.f(st, 4), v + o);
+        }
+      },
+      [&](int q, int st) {
+        const int i = Ny - 1 - q;
+        const size_t o = (size_t)i * M + m;
+        const R* lu = sLU + 7 * i;
+        const C P = ybwd<Y>(Y::lds(rg.f(st, 0)), lu[3], lu[4], lu[5], lu[6], px);   // D1 of dv/dy
+        const C Q = ybwd<Y>(Y::lds(rg.f(st, 1)), lu[3], lu[4], lu[5], lu[6], pw);   // D1 omega_2
+        if constexpr (F32OUT) {
+          const float2 fP = Y::f(P), fQ = Y::f(Q);
+          float2 a1, a3, d1, d3, fv = make_float2(0.f, 0.f);
+          if (MEAN) {
+            a1 = make_float2(d2f_int(U1[i]), 0.f);
+            a3 = make_float2(d2f_int(U3[i]), 0.f);
+            d1 = fP;
+            d3 = fQ;
+          } else {
+            const float2 fd = Y::ldsf(rg.f(st, 2)), fo = Y::ldsf(rg.f(st, 3));
+            fv = Y::ldsf(rg.f(st, 4));
+            // u_1 = i (q1 dv - q3 om), u_3 = i (q3 dv + q1 om), likewise d/dy from (P, Q)
+            a1 = make_float2(-(q1f * fd.y - q3f * fo.y), q1f * fd.x - q3f * fo.x);
+            a3 = make_float2(-(q3f * fd.y + q1f * fo.y), q3f * fd.x + q1f * fo.x);
+            d1 = make_float2(-(q1f * fP.y - q3f * fQ.y), q1f * fP.x - q3f * fQ.x);
+            d3 = make_float2(-(q3f * fP.y + q1f * fQ.y), q3f * fP.x + q1f * fQ.x);
+          }
+          fu[o] = a1;
+          fu[nf + o] = a3;
+          fw[o] = make_float2(d3.x + k3f * fv.y, d3.y - k3f * fv.x);        // du3/dy - i k3 v
+          fw[nf + o] = make_float2(-k1f * fv.y - d1.x, k1f * fv.x - d1.y);  // i k1 v - du1/dy
+          return;
+        }
+        C u1, u3, du1, du3, vi = Y::zero();
+        if (MEAN) {
+          u1 = Y::c(make_double2(U1[i], 0.0));
+          u3 = Y::c(make_double2(U3[i], 0.0));
+          du1 = P;
+          du3 = Q;
+        } else {
+          const C dvi = Y::lds(rg.f(st, 2)), omi = Y::lds(rg.f(st, 3));
+          vi = Y::lds(rg.f(st, 4));
+          u1 = Y::itimes(Y::axpy(Y::neg(q3), omi, Y::scl(q1, dvi)));
+          u3 = Y::itimes(Y::axpy(q1, omi, Y::scl(q3, dvi)));
+          du1 = Y::itimes(Y::axpy(Y::neg(q3), Q, Y::scl(q1, P)));
+          du3 = Y::itimes(Y::axpy(q1, Q, Y::scl(q3, P)));
+        }
+        // omega_1 = du3/dy - i k3 v, omega_3 = i k1 v - du1/dy
+        Y::st(u1o, o, u1);
+        Y::st(u3o, o, u3);
+        Y::st(om1o, o, Y::sub(du3, Y::itimes(Y::scl(k3, vi))));
+        Y::st(om3o, o, Y::sub(Y::itimes(Y::scl(k1, vi)), du1));
+      });
+}
+
 template <class Y, bool F32OUT = false>
 __device__ __forceinline__ void pre_body(Geo g, YTabs t, const double2* __restrict__ v,
                                          const double2* __restrict__ om, const double2* __restrict__ dv,
                                          const double* __restrict__ U1, const double* __restrict__ U3,
                                          double2* u1o, double2* u3o, double2* om1o, double2* om3o, int bid) {
   typedef typename Y::R R;
-  typedef typename Y::C C;
   extern __shared__ double sm[];
   const int Ny = g.Ny;
   R* sp = reinterpret_cast<R*>(sm);
   const R* sB1 = ystage<Y>(sp, Y::B1(t), 7 * Ny, !g.gtab);
   const R* sLU = ystage<Y>(sp, Y::LU1(t), 7 * Ny, !g.gtab);
   if (!g.gtab) __syncthreads();
+  void* ring = ring_base(sp);
+  // The (0,0) mode runs its own instantiation of the sweeps in a block of its own (the one
+  // after the mode blocks), so no warp holds both code paths.
+  const int nblk = (g.M + blockDim.x - 1) / blockDim.x;
+  if (bid == nblk) {
+    if (threadIdx.x == 0)
+      pre_sweep<Y, F32OUT, true>(g, sB1, sLU, mode_info(g, 0), 0, v, om, dv, U1, U3, u1o, u3o, om1o, om3o, ring);
+    return;
+  }
   const int m = bid * blockDim.x + threadIdx.x;
-  if (m >= g.M) return;
+  if (m >= g.M || m == 0) return;
   const size_t M = g.M;
   ModeInfo mi = mode_info(g, m);
   const size_t nf = (size_t)Ny * M;
-  float2* fu = reinterpret_cast<float2*>(om1o);   // F32OUT: u_1 [0, nf), u_3 [nf, 2 nf)
-  float2* fw = reinterpret_cast<float2*>(om3o);   //         omega_1, omega_3
+  float2* fu = reinterpret_cast<float2*>(om1o);
+  float2* fw = reinterpret_cast<float2*>(om3o);
   if (mi.nyq) {
     for (int i = 0; i < Ny; ++i) {
       size_t o = (size_t)i * M + m;
@@ -234,81 +424,7 @@ __device__ __forceinline__ void pre_body(Geo g, YTabs t, const double2* __restri
     }
     return;
   }
-  const bool mean = (m == 0);   // forward-sweep values parked in the u_1, u_3 outputs
-  C wx[7], ww[7], hx[3], hw[3];
-#pragma unroll
-  for (int d = 0; d < 7; ++d) { wx[d] = Y::zero(); ww[d] = Y::zero(); }
-#pragma unroll
-  for (int d = 0; d < 3; ++d) { hx[d] = Y::zero(); hw[d] = Y::zero(); }
-  // forward sweep of D1 = A1^-1 B1 on x = dv/dy (U1 for the mean) and w = omega_2 (U3)
-  for (int j = 0; j < Ny + 3; ++j) {
-    C nx = Y::zero(), nw = Y::zero();
-    if (j < Ny) {
-      if (mean) { nx = Y::c(make_double2(U1[j], 0.0)); nw = Y::c(make_double2(U3[j], 0.0)); }
-      else { nx = Y::ld(dv, (size_t)j * M + m); nw = Y::ld(om, (size_t)j * M + m); }
-    }
-    ypush<Y>(wx, nx);
-    ypush<Y>(ww, nw);
-    const int i = j - 3;
-    if (i < 0) continue;
-    const R* b = sB1 + 7 * i;
-    const R* l = sLU + 7 * i;
-    Y::st(u1o, (size_t)i * M + m, yfwd<Y>(yband7<Y>(b, wx), l[0], l[1], l[2], hx));
-    Y::st(u3o, (size_t)i * M + m, yfwd<Y>(yband7<Y>(b, ww), l[0], l[1], l[2], hw));
-  }
-  C px[3] = {Y::zero(), Y::zero(), Y::zero()}, pw[3] = {Y::zero(), Y::zero(), Y::zero()};
-  const R q1 = Y::r(mean ? 0.0 : mi.k1 / mi.k2), q3 = Y::r(mean ? 0.0 : mi.k3 / mi.k2);
-  const R k1 = Y::r(mi.k1), k3 = Y::r(mi.k3);
-  const float q1f = mean ? 0.f : (float)(mi.k1 / mi.k2), q3f = mean ? 0.f : (float)(mi.k3 / mi.k2);
-  const float k1f = (float)mi.k1, k3f = (float)mi.k3;
-  for (int i = Ny - 1; i >= 0; --i) {
-    const size_t o = (size_t)i * M + m;
-    const R* lu = sLU + 7 * i;
-    const C P = ybwd<Y>(Y::ld(u1o, o), lu[3], lu[4], lu[5], lu[6], px);   // D1 of dv/dy
-    const C Q = ybwd<Y>(Y::ld(u3o, o), lu[3], lu[4], lu[5], lu[6], pw);   // D1 omega_2
-    if constexpr (F32OUT) {
-      const float2 fP = Y::f(P), fQ = Y::f(Q);
-      float2 a1, a3, d1, d3, fv = make_float2(0.f, 0.f);
-      if (mean) {
-        a1 = make_float2(d2f_int(U1[i]), 0.f);
-        a3 = make_float2(d2f_int(U3[i]), 0.f);
-        d1 = fP;
-        d3 = fQ;
-      } else {
-        const float2 fd = Y::ldf(dv, o), fo = Y::ldf(om, o);
-        fv = Y::ldf(v, o);
-        // u_1 = i (q1 dv - q3 om), u_3 = i (q3 dv + q1 om), likewise d/dy from (P, Q)
-        a1 = make_float2(-(q1f * fd.y - q3f * fo.y), q1f * fd.x - q3f * fo.x);
-        a3 = make_float2(-(q3f * fd.y + q1f * fo.y), q3f * fd.x + q1f * fo.x);
-        d1 = make_float2(-(q1f * fP.y - q3f * fQ.y), q1f * fP.x - q3f * fQ.x);
-        d3 = make_float2(-(q3f * fP.y + q1f * fQ.y), q3f * fP.x + q1f * fQ.x);
-      }
-      fu[o] = a1;
-      fu[nf + o] = a3;
-      fw[o] = make_float2(d3.x + k3f * fv.y, d3.y - k3f * fv.x);        // du3/dy - i k3 v
-      fw[nf + o] = make_float2(-k1f * fv.y - d1.x, k1f * fv.x - d1.y);  // i k1 v - du1/dy
-      continue;
-    }
-    C u1, u3, du1, du3, vi = Y::zero();
-    if (mean) {
-      u1 = Y::c(make_double2(U1[i], 0.0));
-      u3 = Y::c(make_double2(U3[i], 0.0));
-      du1 = P;
-      du3 = Q;
-    } else {
-      const C dvi = Y::ld(dv, o), omi = Y::ld(om, o);
-      vi = Y::ld(v, o);
-      u1 = Y::itimes(Y::axpy(Y::neg(q3), omi, Y::scl(q1, dvi)));
-      u3 = Y::itimes(Y::axpy(q1, omi, Y::scl(q3, dvi)));
-      du1 = Y::itimes(Y::axpy(Y::neg(q3), Q, Y::scl(q1, P)));
-      du3 = Y::itimes(Y::axpy(q1, Q, Y::scl(q3, P)));
-    }
-    // omega_1 = du3/dy - i k3 v, omega_3 = i k1 v - du1/dy
-    Y::st(u1o, o, u1);
-    Y::st(u3o, o, u3);
-    Y::st(om1o, o, Y::sub(du3, Y::itimes(Y::scl(k3, vi))));
-    Y::st(om3o, o, Y::sub(Y::itimes(Y::scl(k1, vi)), du1));
-  }
+  pre_sweep<Y, F32OUT, false>(g, sB1, sLU, mi, m, v, om, dv, U1, U3, u1o, u3o, om1o, om3o, ring);
 }
 
 __global__ void __launch_bounds__(128) k_pre(Geo g, YTabs t, const double2* __restrict__ v,
@@ -343,6 +459,7 @@ __device__ __forceinline__ void nonlin_body(Geo g, YTabs t, const double2* __res
   const R* sB1 = ystage<Y>(sp, Y::B1(t), 7 * Ny, !g.gtab);
   const R* sLU = ystage<Y>(sp, Y::LU1(t), 7 * Ny, !g.gtab);
   if (!g.gtab) __syncthreads();
+  void* ring = ring_base(sp);
   const int m = bid * blockDim.x + threadIdx.x;
   if (m >= g.M) return;
   const size_t M = g.M;
@@ -353,32 +470,49 @@ __device__ __forceinline__ void nonlin_body(Geo g, YTabs t, const double2* __res
   }
   double2* scr = scr_;
   const R k1 = Y::r(mi.k1), k3 = Y::r(mi.k3), mk2 = Y::r(-mi.k2);
+  Ring<4, 0> rg(ring);
   C w[7], hz[3];
 #pragma unroll
   for (int d = 0; d < 7; ++d) w[d] = Y::zero();
 #pragma unroll
   for (int d = 0; d < 3; ++d) hz[d] = Y::zero();
-  for (int j = 0; j < Ny + 3; ++j) {
-    C f = Y::zero();
-    if (j < Ny) {
-      const size_t o = (size_t)j * M + m;
-      f = Y::itimes(Y::axpy(k3, Y::ld(H3, o), Y::scl(k1, Y::ld(H1, o))));   // i k1 H1 + i k3 H3
-    }
-    ypush<Y>(w, f);
-    const int i = j - 3;
-    if (i < 0) continue;
-    const R* l = sLU + 7 * i;
-    Y::st(scr, (size_t)i * M + m, yfwd<Y>(yband7<Y>(sB1 + 7 * i, w), l[0], l[1], l[2], hz));
-  }
+  pipelined(
+      Ny + 3,
+      [&](int t, int st) {
+        if (t < Ny) {
+          const size_t o = (size_t)t * M + m;
+          cp16(rg.f(st, 0), H1 + o);
+          cp16(rg.f(st, 1), H3 + o);
+        }
+      },
+      [&](int t, int st) {
+        C f = Y::zero();
+        if (t < Ny) f = Y::itimes(Y::axpy(k3, Y::lds(rg.f(st, 1)), Y::scl(k1, Y::lds(rg.f(st, 0)))));   // i k1 H1 + i k3 H3
+        ypush<Y>(w, f);
+        const int i = t - 3;
+        if (i < 0) return;
+        const R* l = sLU + 7 * i;
+        Y::st(scr, (size_t)i * M + m, yfwd<Y>(yband7<Y>(sB1 + 7 * i, w), l[0], l[1], l[2], hz));
+      });
   C nx[3] = {Y::zero(), Y::zero(), Y::zero()};
-  for (int i = Ny - 1; i >= 0; --i) {
-    const size_t o = (size_t)i * M + m;
-    const R* lu = sLU + 7 * i;
-    const C d = ybwd<Y>(Y::ld(scr, o), lu[3], lu[4], lu[5], lu[6], nx);
-    const C h2 = Y::ld(H2, o), h1 = Y::ld(H1, o), h3 = Y::ld(H3, o);
-    Y::st(Nchi, o, Y::axpy(mk2, h2, Y::sub(Y::zero(), d)));                 // -D1 f - k^2 H2
-    Y::st(Nom, o, Y::itimes(Y::axpy(Y::neg(k1), h3, Y::scl(k3, h1))));      // i k3 H1 - i k1 H3
-  }
+  pipelined(
+      Ny,
+      [&](int q, int st) {
+        const size_t o = (size_t)(Ny - 1 - q) * M + m;
+        cp16(rg.f(st, 0), scr + o);
+        cp16(rg.f(st, 1), H2 + o);
+        cp16(rg.f(st, 2), H1 + o);
+        cp16(rg.f(st, 3), H3 + o);
+      },
+      [&](int q, int st) {
+        const int i = Ny - 1 - q;
+        const size_t o = (size_t)i * M + m;
+        const R* lu = sLU + 7 * i;
+        const C d = ybwd<Y>(Y::lds(rg.f(st, 0)), lu[3], lu[4], lu[5], lu[6], nx);
+        const C h2 = Y::lds(rg.f(st, 1)), h1 = Y::lds(rg.f(st, 2)), h3 = Y::lds(rg.f(st, 3));
+        Y::st(Nchi, o, Y::axpy(mk2, h2, Y::sub(Y::zero(), d)));                 // -D1 f - k^2 H2
+        Y::st(Nom, o, Y::itimes(Y::axpy(Y::neg(k1), h3, Y::scl(k3, h1))));      // i k3 H1 - i k1 H3
+      });
 }
 
 __global__ void __launch_bounds__(128) k_nonlin(Geo g, YTabs t, const double2* __restrict__ H1,
@@ -406,43 +540,74 @@ __device__ __forceinline__ void helm_one(int Ny, size_t M, size_t NC, int m, con
                                          const typename Y::R* sB, const typename Y::R* __restrict__ H, double2* X,
                                          const double2* __restrict__ N, double2* Np, double2* Rf, double2* scr,
                                          typename Y::R c1, typename Y::R cg, typename Y::R cz,
-                                         typename Y::R ca, typename Y::R qp) {
+                                         typename Y::R ca, typename Y::R qp, void* ring) {
   typedef typename Y::R R;
   typedef typename Y::C C;
+  Ring<4, 4> rg(ring);
   C wa[7], wx[7], hz[3];
 #pragma unroll
   for (int d = 0; d < 7; ++d) { wa[d] = Y::zero(); wx[d] = Y::zero(); }
 #pragma unroll
   for (int d = 0; d < 3; ++d) hz[d] = Y::zero();
-  for (int j = 0; j < Ny + 3; ++j) {
-    C a = Y::zero(), x = Y::zero();
-    if (j < Ny) {
-      const size_t o = (size_t)j * M + m;
-      const C n = Y::ld(N, o);
-      x = Y::ld(X, o);
-      a = Y::axpy(cz, Y::ld(Np, o), Y::axpy(cg, n, Y::scl(c1, x)));
-      Y::st(Np, o, n);
-    }
-    ypush<Y>(wa, a);
-    ypush<Y>(wx, x);
-    const int i = j - 3;
-    if (i < 0) continue;
-    C r = Y::zero();
-    if (i > 0 && i < Ny - 1) {
-      const size_t oi = (size_t)i * M + m;
-      if constexpr (PREV) r = Y::axpy(qp, Y::ld(Rf, oi), yband7<Y>(sA + 7 * i, wa));
-      else r = Y::axpy(ca, yband7<Y>(sB + 7 * i, wx), yband7<Y>(sA + 7 * i, wa));
-      Y::st(Rf, oi, r);
-    }
-    const R* Hi = H + (size_t)i * 11 * NC;
-    Y::st(scr, (size_t)i * M + m, yfwd<Y>(r, Hi[0], Hi[NC], Hi[2 * NC], hz));
-  }
+  // forward: row t of N, X, Nprev and, three rows behind, the kept right-hand side and the
+  // L factors of row t - 3
+  pipelined(
+      Ny + 3,
+      [&](int t, int st) {
+        if (t < Ny) {
+          const size_t o = (size_t)t * M + m;
+          cp16(rg.f(st, 0), N + o);
+          cp16(rg.f(st, 1), X + o);
+          cp16(rg.f(st, 2), Np + o);
+        }
+        const int i = t - 3;
+        if (i >= 0) {
+          if (PREV && i > 0 && i < Ny - 1) cp16(rg.f(st, 3), Rf + (size_t)i * M + m);
+          const R* Hi = H + (size_t)i * 11 * NC;
+          cp8(rg.t(st, 0), Hi);
+          cp8(rg.t(st, 1), Hi + NC);
+          cp8(rg.t(st, 2), Hi + 2 * NC);
+        }
+      },
+      [&](int t, int st) {
+        C a = Y::zero(), x = Y::zero();
+        if (t < Ny) {
+          const C n = Y::lds(rg.f(st, 0));
+          x = Y::lds(rg.f(st, 1));
+          a = Y::axpy(cz, Y::lds(rg.f(st, 2)), Y::axpy(cg, n, Y::scl(c1, x)));
+          Y::st(Np, (size_t)t * M + m, n);
+        }
+        ypush<Y>(wa, a);
+        ypush<Y>(wx, x);
+        const int i = t - 3;
+        if (i < 0) return;
+        C r = Y::zero();
+        if (i > 0 && i < Ny - 1) {
+          if constexpr (PREV) r = Y::axpy(qp, Y::lds(rg.f(st, 3)), yband7<Y>(sA + 7 * i, wa));
+          else r = Y::axpy(ca, yband7<Y>(sB + 7 * i, wx), yband7<Y>(sA + 7 * i, wa));
+          Y::st(Rf, (size_t)i * M + m, r);
+        }
+        Y::st(scr, (size_t)i * M + m,
+              yfwd<Y>(r, Y::ldr(rg.t(st, 0)), Y::ldr(rg.t(st, 1)), Y::ldr(rg.t(st, 2)), hz));
+      });
   C nx[3] = {Y::zero(), Y::zero(), Y::zero()};
-  for (int i = Ny - 1; i >= 0; --i) {
-    const size_t o = (size_t)i * M + m;
-    const R* Hi = H + (size_t)i * 11 * NC;
-    Y::st(X, o, ybwd<Y>(Y::ld(scr, o), Hi[3 * NC], Hi[4 * NC], Hi[5 * NC], Hi[6 * NC], nx));
-  }
+  pipelined(
+      Ny,
+      [&](int q, int st) {
+        const int i = Ny - 1 - q;
+        cp16(rg.f(st, 0), scr + (size_t)i * M + m);
+        const R* Hi = H + (size_t)i * 11 * NC;
+        cp8(rg.t(st, 0), Hi + 3 * NC);
+        cp8(rg.t(st, 1), Hi + 4 * NC);
+        cp8(rg.t(st, 2), Hi + 5 * NC);
+        cp8(rg.t(st, 3), Hi + 6 * NC);
+      },
+      [&](int q, int st) {
+        const int i = Ny - 1 - q;
+        Y::st(X, (size_t)i * M + m,
+              ybwd<Y>(Y::lds(rg.f(st, 0)), Y::ldr(rg.t(st, 0)), Y::ldr(rg.t(st, 1)), Y::ldr(rg.t(st, 2)),
+                      Y::ldr(rg.t(st, 3)), nx));
+      });
 }
 
 // FS: 0 omega_2 only, 1 chi only, 2 both (one after the other).  Each field's arithmetic
@@ -460,6 +625,7 @@ __device__ __forceinline__ void helm_body(Geo g, YTabs t, const typename Y::R* _
   const R* sA = ystage<Y>(sp, Y::A2(t), 7 * Ny, !g.gtab);
   const R* sB = ystage<Y>(sp, Y::B2(t), 7 * Ny, !g.gtab);
   if (!g.gtab) __syncthreads();
+  void* ring = ring_base(sp);
   const int m = bid * blockDim.x + threadIdx.x;
   if (m >= g.M) return;
   const size_t M = g.M;
@@ -483,11 +649,11 @@ __device__ __forceinline__ void helm_body(Geo g, YTabs t, const typename Y::R* _
   // separate instantiations: the B product of the first substep is not issued under a predicate
   double2* scr2 = scr_ + (size_t)Ny * M;
   if (prev) {
-    if (FS != 1) helm_one<Y, true>(Ny, M, NC, m, sA, sB, H, om, Nom, Nom_p, Rom, scr_, c1, cg, cz, ca, qp);
-    if (FS != 0) helm_one<Y, true>(Ny, M, NC, m, sA, sB, H, chi, Nchi, Nchi_p, Rchi, scr2, c1, cg, cz, ca, qp);
+    if (FS != 1) helm_one<Y, true>(Ny, M, NC, m, sA, sB, H, om, Nom, Nom_p, Rom, scr_, c1, cg, cz, ca, qp, ring);
+    if (FS != 0) helm_one<Y, true>(Ny, M, NC, m, sA, sB, H, chi, Nchi, Nchi_p, Rchi, scr2, c1, cg, cz, ca, qp, ring);
   } else {
-    if (FS != 1) helm_one<Y, false>(Ny, M, NC, m, sA, sB, H, om, Nom, Nom_p, Rom, scr_, c1, cg, cz, ca, qp);
-    if (FS != 0) helm_one<Y, false>(Ny, M, NC, m, sA, sB, H, chi, Nchi, Nchi_p, Rchi, scr2, c1, cg, cz, ca, qp);
+    if (FS != 1) helm_one<Y, false>(Ny, M, NC, m, sA, sB, H, om, Nom, Nom_p, Rom, scr_, c1, cg, cz, ca, qp, ring);
+    if (FS != 0) helm_one<Y, false>(Ny, M, NC, m, sA, sB, H, chi, Nchi, Nchi_p, Rchi, scr2, c1, cg, cz, ca, qp, ring);
   }
 }
 
@@ -524,6 +690,7 @@ __device__ __forceinline__ void poisson_body(Geo g, YTabs t, const typename Y::R
   const R* sd0 = ystage<Y>(sp, Y::D0(t), Ny, !g.gtab);
   const R* sdN = ystage<Y>(sp, Y::DN(t), Ny, !g.gtab);
   if (!g.gtab) __syncthreads();
+  void* ring = ring_base(sp);
   const int m = bid * blockDim.x + threadIdx.x;
   if (m >= g.M) return;
   const size_t M = g.M;
@@ -536,29 +703,54 @@ __device__ __forceinline__ void poisson_body(Geo g, YTabs t, const typename Y::R
   const R* P = pois + mi.c;
   const R* H = helm + mi.c;   // the substep's slot
   double2* scr = scr_;
+  Ring<2, 4> rg(ring);
   C w[7], hz[3];
 #pragma unroll
   for (int d = 0; d < 7; ++d) w[d] = Y::zero();
 #pragma unroll
   for (int d = 0; d < 3; ++d) hz[d] = Y::zero();
-  for (int j = 0; j < Ny + 3; ++j) {
-    ypush<Y>(w, j < Ny ? Y::ld(chi, (size_t)j * M + m) : Y::zero());
-    const int i = j - 3;
-    if (i < 0) continue;
-    C r = (i > 0 && i < Ny - 1) ? yband7<Y>(sA + 7 * i, w) : Y::zero();
-    const R* Pi = P + (size_t)i * 7 * NC;
-    Y::st(scr, (size_t)i * M + m, yfwd<Y>(r, Pi[0], Pi[NC], Pi[2 * NC], hz));
-  }
+  // particular solution: forward sweep of (B - k^2 A) v_p = A chi_p (interior rows)
+  pipelined(
+      Ny + 3,
+      [&](int t, int st) {
+        if (t < Ny) cp16(rg.f(st, 0), chi + (size_t)t * M + m);
+        const int i = t - 3;
+        if (i >= 0) {
+          const R* Pi = P + (size_t)i * 7 * NC;
+          cp8(rg.t(st, 0), Pi);
+          cp8(rg.t(st, 1), Pi + NC);
+          cp8(rg.t(st, 2), Pi + 2 * NC);
+        }
+      },
+      [&](int t, int st) {
+        ypush<Y>(w, t < Ny ? Y::lds(rg.f(st, 0)) : Y::zero());
+        const int i = t - 3;
+        if (i < 0) return;
+        C r = (i > 0 && i < Ny - 1) ? yband7<Y>(sA + 7 * i, w) : Y::zero();
+        Y::st(scr, (size_t)i * M + m,
+              yfwd<Y>(r, Y::ldr(rg.t(st, 0)), Y::ldr(rg.t(st, 1)), Y::ldr(rg.t(st, 2)), hz));
+      });
   C nx[3] = {Y::zero(), Y::zero(), Y::zero()};
   C s0 = Y::zero(), sN = Y::zero();
-  for (int i = Ny - 1; i >= 0; --i) {
-    const size_t o = (size_t)i * M + m;
-    const R* Pi = P + (size_t)i * 7 * NC;
-    const C vp = ybwd<Y>(Y::ld(scr, o), Pi[3 * NC], Pi[4 * NC], Pi[5 * NC], Pi[6 * NC], nx);
-    Y::st(scr, o, vp);   // v_p parked in the scratch until the wall correction is known
-    s0 = Y::axpy(sd0[i], vp, s0);
-    sN = Y::axpy(sdN[i], vp, sN);
-  }
+  pipelined(
+      Ny,
+      [&](int q, int st) {
+        const int i = Ny - 1 - q;
+        cp16(rg.f(st, 0), scr + (size_t)i * M + m);
+        const R* Pi = P + (size_t)i * 7 * NC;
+        cp8(rg.t(st, 0), Pi + 3 * NC);
+        cp8(rg.t(st, 1), Pi + 4 * NC);
+        cp8(rg.t(st, 2), Pi + 5 * NC);
+        cp8(rg.t(st, 3), Pi + 6 * NC);
+      },
+      [&](int q, int st) {
+        const int i = Ny - 1 - q;
+        const C vp = ybwd<Y>(Y::lds(rg.f(st, 0)), Y::ldr(rg.t(st, 0)), Y::ldr(rg.t(st, 1)), Y::ldr(rg.t(st, 2)),
+                             Y::ldr(rg.t(st, 3)), nx);
+        Y::st(scr, (size_t)i * M + m, vp);   // v_p parked in the scratch until the wall correction is known
+        s0 = Y::axpy(sd0[i], vp, s0);
+        sN = Y::axpy(sdN[i], vp, sN);
+      });
   const R* Gi = infl + mi.c;
   const R g11 = Gi[0], g12 = Gi[NC], g21 = Gi[2 * NC], g22 = Gi[3 * NC];  // inverse influence matrix
   const C cA = Y::sub(Y::zero(), Y::axpy(g12, sN, Y::scl(g11, s0)));
@@ -568,28 +760,46 @@ __device__ __forceinline__ void poisson_body(Geo g, YTabs t, const typename Y::R
   for (int d = 0; d < 7; ++d) w[d] = Y::zero();
 #pragma unroll
   for (int d = 0; d < 3; ++d) hz[d] = Y::zero();
-  for (int j = 0; j < Ny + 3; ++j) {
-    C vj = Y::zero();
-    if (j < Ny) {
-      const size_t o = (size_t)j * M + m;
-      const R* Hj = H + (size_t)j * 11 * NC;
-      const R xa = Hj[7 * NC], xb = Hj[8 * NC], va = Hj[9 * NC], vb = Hj[10 * NC];
-      vj = Y::axpy(vb, cB, Y::axpy(va, cA, Y::ld(scr, o)));
-      Y::st(v, o, vj);
-      Y::st(chi, o, Y::axpy(xb, cB, Y::axpy(xa, cA, Y::ld(chi, o))));
-    }
-    ypush<Y>(w, vj);
-    const int i = j - 3;
-    if (i < 0) continue;
-    const R* l = sLU + 7 * i;
-    Y::st(scr2, (size_t)i * M + m, yfwd<Y>(yband7<Y>(sB1 + 7 * i, w), l[0], l[1], l[2], hz));
-  }
+  // v = v_p + c_a v_a + c_b v_b, chi likewise; forward sweep of dv/dy = D1 v
+  pipelined(
+      Ny + 3,
+      [&](int t, int st) {
+        if (t < Ny) {
+          const size_t o = (size_t)t * M + m;
+          cp16(rg.f(st, 0), scr + o);
+          cp16(rg.f(st, 1), chi + o);
+          const R* Hj = H + (size_t)t * 11 * NC;
+          cp8(rg.t(st, 0), Hj + 7 * NC);
+          cp8(rg.t(st, 1), Hj + 8 * NC);
+          cp8(rg.t(st, 2), Hj + 9 * NC);
+          cp8(rg.t(st, 3), Hj + 10 * NC);
+        }
+      },
+      [&](int t, int st) {
+        C vj = Y::zero();
+        if (t < Ny) {
+          const size_t o = (size_t)t * M + m;
+          const R xa = Y::ldr(rg.t(st, 0)), xb = Y::ldr(rg.t(st, 1)), va = Y::ldr(rg.t(st, 2)),
+                  vb = Y::ldr(rg.t(st, 3));
+          vj = Y::axpy(vb, cB, Y::axpy(va, cA, Y::lds(rg.f(st, 0))));
+          Y::st(v, o, vj);
+          Y::st(chi, o, Y::axpy(xb, cB, Y::axpy(xa, cA, Y::lds(rg.f(st, 1)))));
+        }
+        ypush<Y>(w, vj);
+        const int i = t - 3;
+        if (i < 0) return;
+        const R* l = sLU + 7 * i;
+        Y::st(scr2, (size_t)i * M + m, yfwd<Y>(yband7<Y>(sB1 + 7 * i, w), l[0], l[1], l[2], hz));
+      });
   for (int d = 0; d < 3; ++d) nx[d] = Y::zero();
-  for (int i = Ny - 1; i >= 0; --i) {
-    const size_t o = (size_t)i * M + m;
-    const R* lu = sLU + 7 * i;
-    Y::st(dv, o, ybwd<Y>(Y::ld(scr2, o), lu[3], lu[4], lu[5], lu[6], nx));
-  }
+  pipelined(
+      Ny,
+      [&](int q, int st) { cp16(rg.f(st, 0), scr2 + (size_t)(Ny - 1 - q) * M + m); },
+      [&](int q, int st) {
+        const int i = Ny - 1 - q;
+        const R* lu = sLU + 7 * i;
+        Y::st(dv, (size_t)i * M + m, ybwd<Y>(Y::lds(rg.f(st, 0)), lu[3], lu[4], lu[5], lu[6], nx));
+      });
 }
 
 template <class Y>
@@ -1129,7 +1339,7 @@ static Geo geo(const chan_s* h) {
   g.Nx = h->Nx; g.Ny = h->Ny; g.Nz = h->Nz; g.nxh = h->nxh; g.M = h->M; g.C = h->C;
   g.L1 = h->L1; g.L3 = h->L3; g.dt = h->dt; g.nu = h->nu; g.k1 = h->k1; g.k3 = h->k3;
   g.pair = prec_pairs(h->prec);
-  g.gtab = h->ytab > 0 || (h->ytab < 0 && 23 * (size_t)h->Ny * sizeof(double) > 48 * 1024);
+  g.gtab = ytab_in_place(h->ytab, h->Ny);
   return g;
 }
 static YTabs ytabs(const chan_s* h) {
@@ -1160,14 +1370,19 @@ static const void* pois_y(const chan_s* h) {
 static const int kYThreads = 128;
 // Shared memory of a sweep kernel that stages per_y table values per y point (0 when
 // the tables are read in place).
-static size_t ysm(const chan_s* h, int per_y) {
-  return geo(h).gtab ? 0 : sizeof(double) * per_y * (size_t)h->Ny;
+// Shared memory of a sweep kernel: the staged tables (per_y values per y point, none when
+// the tables are read in place) and the kernel's row prefetch ring.
+static size_t ysm(const chan_s* h, int per_y, size_t ring) {
+  return (geo(h).gtab ? 0 : sizeof(double) * per_y * (size_t)h->Ny) + 16 + ring * kYThreads;
 }
-static size_t ysm_batch(chan_s* const* hs, int n, int per_y) {
+static size_t ysm_batch(chan_s* const* hs, int n, int per_y, size_t ring) {
   size_t m = 0;
-  for (int r = 0; r < n; ++r) m = ysm(hs[r], per_y) > m ? ysm(hs[r], per_y) : m;
+  for (int r = 0; r < n; ++r) m = ysm(hs[r], per_y, ring) > m ? ysm(hs[r], per_y, ring) : m;
   return m;
 }
+// Prefetch ring bytes per thread of each sweep kernel.
+static const size_t kRingPre = Ring<5, 0>::per_thread, kRingNonlin = Ring<4, 0>::per_thread,
+                    kRingHelm = Ring<4, 4>::per_thread, kRingPois = Ring<2, 4>::per_thread;
 static dim3 ygrid(const chan_s* h) { return dim3((h->M + kYThreads - 1) / kYThreads); }
 
 static cudaError_t smem_attr(const void* fn, size_t bytes) {
@@ -1240,7 +1455,7 @@ cudaError_t launch_derive(chan_s* h) {
 }
 
 cudaError_t launch_pre(chan_s* h, double2* u1, double2* u3, double2* om1, double2* om3, bool f32) {
-  size_t sm = ysm(h, 14);
+  size_t sm = ysm(h, 14, kRingPre);
   f32 = f32 && prec_t32(h->prec);
   const bool df = use_df(h);
   const void* fn = df ? (f32 ? (const void*)k_pre_df_f32 : (const void*)k_pre_df)
@@ -1248,19 +1463,19 @@ cudaError_t launch_pre(chan_s* h, double2* u1, double2* u3, double2* om1, double
   cudaError_t e = smem_attr(fn, sm);
   if (e != cudaSuccess) return e;
   if (df && f32)
-    k_pre_df_f32<<<ygrid(h), kYThreads, sm, h->stream>>>(geo(h), ytabs(h), h->v, h->om, h->dv, h->U1, h->U3, u1, u3, om1, om3);
+    k_pre_df_f32<<<ygrid(h).x + 1, kYThreads, sm, h->stream>>>(geo(h), ytabs(h), h->v, h->om, h->dv, h->U1, h->U3, u1, u3, om1, om3);
   else if (df)
-    k_pre_df<<<ygrid(h), kYThreads, sm, h->stream>>>(geo(h), ytabs(h), h->v, h->om, h->dv, h->U1, h->U3, u1, u3, om1, om3);
+    k_pre_df<<<ygrid(h).x + 1, kYThreads, sm, h->stream>>>(geo(h), ytabs(h), h->v, h->om, h->dv, h->U1, h->U3, u1, u3, om1, om3);
   else if (f32)
-    k_pre_f32<<<ygrid(h), kYThreads, sm, h->stream>>>(geo(h), ytabs(h), h->v, h->om, h->dv, h->U1, h->U3, u1, u3, om1, om3);
+    k_pre_f32<<<ygrid(h).x + 1, kYThreads, sm, h->stream>>>(geo(h), ytabs(h), h->v, h->om, h->dv, h->U1, h->U3, u1, u3, om1, om3);
   else
-    k_pre<<<ygrid(h), kYThreads, sm, h->stream>>>(geo(h), ytabs(h), h->v, h->om, h->dv, h->U1, h->U3, u1, u3, om1, om3);
+    k_pre<<<ygrid(h).x + 1, kYThreads, sm, h->stream>>>(geo(h), ytabs(h), h->v, h->om, h->dv, h->U1, h->U3, u1, u3, om1, om3);
   return cudaGetLastError();
 }
 
 cudaError_t launch_nonlin(chan_s* h, const double2* H1, const double2* H2, const double2* H3, double2* Nchi,
                           double2* Nom) {
-  size_t sm = ysm(h, 14);
+  size_t sm = ysm(h, 14, kRingNonlin);
   const void* fn = use_df(h) ? (const void*)k_nonlin_df : (const void*)k_nonlin;
   cudaError_t e = smem_attr(fn, sm);
   if (e != cudaSuccess) return e;
@@ -1273,7 +1488,7 @@ cudaError_t launch_nonlin(chan_s* h, const double2* H1, const double2* H2, const
 
 cudaError_t launch_nonlin_scratch(chan_s* h, const double2* H1, const double2* H2, const double2* H3, double2* Nchi,
                                  double2* Nom, double2* scr) {
-  size_t sm = ysm(h, 14);
+  size_t sm = ysm(h, 14, kRingNonlin);
   cudaError_t e = smem_attr((const void*)k_nonlin, sm);
   if (e != cudaSuccess) return e;
   k_nonlin<<<ygrid(h), kYThreads, sm, h->stream>>>(geo(h), ytabs(h), H1, H2, H3, Nchi, Nom, scr);
@@ -1281,7 +1496,7 @@ cudaError_t launch_nonlin_scratch(chan_s* h, const double2* H1, const double2* H
 }
 
 cudaError_t launch_helm(chan_s* h, const double2* Nchi, const double2* Nom, int s) {
-  size_t sm = ysm(h, 14);
+  size_t sm = ysm(h, 14, kRingHelm);
   const void* fn = use_df(h) ? (const void*)k_helm<YDF> : (const void*)k_helm<YF64>;
   cudaError_t e = smem_attr(fn, sm);
   if (e != cudaSuccess) return e;
@@ -1297,7 +1512,7 @@ cudaError_t launch_helm(chan_s* h, const double2* Nchi, const double2* Nom, int 
 }
 
 cudaError_t launch_poisson(chan_s* h, int s) {
-  size_t sm = ysm(h, 23);
+  size_t sm = ysm(h, 23, kRingPois);
   const void* fn = use_df(h) ? (const void*)k_poisson<YDF> : (const void*)k_poisson<YF64>;
   cudaError_t e = smem_attr(fn, sm);
   if (e != cudaSuccess) return e;
@@ -1327,12 +1542,12 @@ cudaError_t launch_mean(chan_s* h, const double2* H1, const double2* H3, int s) 
 // `stream`; w[r] holds run r's work-field pointers (see batch_step in chan_api).
 // ---------------------------------------------------------------------------
 template <class P>
-static int fill_begin(YBatch<P>& B, chan_s* const* hs, int n) {
+static int fill_begin(YBatch<P>& B, chan_s* const* hs, int n, int extra = 0) {
   B.n = n;
   int acc = 0;
   for (int r = 0; r < n; ++r) {
     B.begin[r] = acc;
-    acc += (hs[r]->M + kYThreads - 1) / kYThreads;
+    acc += (hs[r]->M + kYThreads - 1) / kYThreads + extra;
   }
   B.begin[n] = acc;
   return acc;
@@ -1349,8 +1564,8 @@ cudaError_t launch_pre_batch(chan_s* const* hs, int n, const BatchWork* w, cudaS
     chan_s* h = hs[r];
     B.p[r] = PreP{geo(h), ytabs(h), h->v, h->om, h->dv, h->U1, h->U3, w[r].u1, w[r].u3, w[r].om1, w[r].om3};
   }
-  const int blocks = fill_begin(B, hs, n);
-  const size_t sm = ysm_batch(hs, n, 14);
+  const int blocks = fill_begin(B, hs, n, 1);   // + the mean-mode block of each run
+  const size_t sm = ysm_batch(hs, n, 14, kRingPre);
   const bool df = use_df(hs[0]), f32 = prec_t32(hs[0]->prec);
   const void* fn = df ? (f32 ? (const void*)kb_pre<YDF, true> : (const void*)kb_pre<YDF>)
                       : (f32 ? (const void*)kb_pre<YF64, true> : (const void*)kb_pre<YF64>);
@@ -1370,7 +1585,7 @@ cudaError_t launch_nonlin_batch(chan_s* const* hs, int n, const BatchWork* w, cu
     B.p[r] = NonlinP{geo(h), ytabs(h), w[r].H1, w[r].H2, w[r].H3, w[r].Nchi, w[r].Nom, h->scr};
   }
   const int blocks = fill_begin(B, hs, n);
-  const size_t sm = ysm_batch(hs, n, 14);
+  const size_t sm = ysm_batch(hs, n, 14, kRingNonlin);
   const bool df = use_df(hs[0]);
   cudaError_t e = smem_attr(df ? (const void*)kb_nonlin<YDF> : (const void*)kb_nonlin<YF64>, sm);
   if (e != cudaSuccess) return e;
@@ -1387,7 +1602,7 @@ cudaError_t launch_helm_batch(chan_s* const* hs, int n, const BatchWork* w, cuda
                    h->Rom, h->Rchi, h->scal, h->scr, (int)(h->nsub % 3)};
   }
   const int blocks = fill_begin(B, hs, n);
-  const size_t sm = ysm_batch(hs, n, 14);
+  const size_t sm = ysm_batch(hs, n, 14, kRingHelm);
   const bool df = use_df(hs[0]);
   cudaError_t e = smem_attr(df ? (const void*)kb_helm<YDF> : (const void*)kb_helm<YF64>, sm);
   if (e != cudaSuccess) return e;
@@ -1405,7 +1620,7 @@ cudaError_t launch_poisson_batch(chan_s* const* hs, int n, const BatchWork* w, c
     B.p[r] = PoisP{geo(h), ytabs(h), helm_slot_y(h, s), pois_y(h), infl_slot_y(h, s), h->v, h->chi, h->dv, h->scr, (int)(h->nsub % 3)};
   }
   const int blocks = fill_begin(B, hs, n);
-  const size_t sm = ysm_batch(hs, n, 23);
+  const size_t sm = ysm_batch(hs, n, 23, kRingPois);
   const bool df = use_df(hs[0]);
   cudaError_t e = smem_attr(df ? (const void*)kb_poisson<YDF> : (const void*)kb_poisson<YF64>, sm);
   if (e != cudaSuccess) return e;

@@ -20,8 +20,14 @@ Per-step latency is the device time between CUDA events recorded around each
 RK3 step (contention included; in packed mode the packed step's time counts
 once for every run in it); request latency is arrival to completion on the
 host clock.
+
+A newly admitted run is built (tables, state upload, launch-shape tuning) on
+a set-up thread while the loop keeps issuing the other runs' steps; the run
+holds its slot and its memory from admission on and starts stepping once its
+set-up is done.  A retired run's packed batches are dropped with it.
 """
 import collections
+import concurrent.futures
 import math
 import time
 
@@ -100,7 +106,7 @@ class Server:
 
     def __init__(self, hbm_budget, max_slots=16, chunk=3, max_inflight=2, factory=None, footprint=None,
                  make_stream=None, make_event=None, clock=time.perf_counter, idle_sleep=2e-4, packed=False,
-                 make_batch=None):
+                 make_batch=None, setup_threads=1):
         self.hbm_budget, self.max_slots, self.chunk, self.max_inflight = int(hbm_budget), max_slots, chunk, max_inflight
         if factory is None:
             raise ValueError("a channel factory is required (see channel_factory)")
@@ -111,34 +117,60 @@ class Server:
         self.clock, self.idle_sleep = clock, idle_sleep
         self.packed = packed
         self.make_batch = make_batch or (lambda chans, stream: ChannelBatch(chans, stream=stream.cuda_stream))
+        self.setup_threads = int(setup_threads)   # 0: build admitted runs on the loop's own thread
 
     def run(self, requests, keep_results=True):
         for r in requests:
             if self.footprint(r) > self.hbm_budget:
                 raise ValueError("request %d needs %d bytes, more than the whole budget" % (r.rid, self.footprint(r)))
+        dev = _current_device()
+        pool = (concurrent.futures.ThreadPoolExecutor(max_workers=self.setup_threads, initializer=_set_device,
+                                                      initargs=(dev,))
+                if self.setup_threads > 0 else None)
+        try:
+            return self._run(requests, keep_results, pool)
+        finally:
+            if pool is not None:
+                pool.shutdown(wait=True)
+
+    def _run(self, requests, keep_results, pool):
         pending = collections.deque(sorted(requests, key=lambda r: r.t_arrival))
         waiting = collections.deque()
-        active = []
+        active, starting = [], []
         used = 0
         results, done = {}, {}
         step_ms, max_conc, conc_samples = [], 0, []
-        bstream, binflight, batches = None, collections.deque(), {}
+        bstream, binflight, batches, nbuilt = None, collections.deque(), {}, 0
         t0 = self.clock()
-        while pending or waiting or active:
+        while pending or waiting or active or starting:
             now = self.clock() - t0
             while pending and pending[0].t_arrival <= now:
                 waiting.append(pending.popleft())
             progressed = False
-            # admission: first come, first served, while a slot and the memory allow
-            while waiting and len(active) < self.max_slots and used + self.footprint(waiting[0]) <= self.hbm_budget:
+            # admission: first come, first served, while a slot and the memory allow; the run
+            # is built on the set-up thread and holds its slot and memory meanwhile
+            while (waiting and len(active) + len(starting) < self.max_slots
+                   and used + self.footprint(waiting[0]) <= self.hbm_budget):
                 r = waiting.popleft()
                 stream = self.make_stream()
                 fp = self.footprint(r)
-                ch = self.factory(r, stream)
                 used += fp
-                active.append(_Slot(r, ch, stream, fp, self.clock() - t0))
+                t_admit = self.clock() - t0
+                if pool is None:
+                    active.append(_Slot(r, self.factory(r, stream), stream, fp, t_admit))
+                else:
+                    starting.append((r, stream, fp, t_admit, pool.submit(self.factory, r, stream)))
                 progressed = True
-            max_conc = max(max_conc, len(active))
+            if starting:
+                still_starting = []
+                for r, stream, fp, t_admit, fut in starting:
+                    if fut.done():
+                        active.append(_Slot(r, fut.result(), stream, fp, t_admit))
+                        progressed = True
+                    else:
+                        still_starting.append((r, stream, fp, t_admit, fut))
+                starting = still_starting
+            max_conc = max(max_conc, len(active) + len(starting))
             # packed issue: one RK3 step of every full-step run of a precision in one launch per kernel
             if self.packed:
                 if bstream is None:
@@ -153,6 +185,7 @@ class Server:
                     key = tuple(sl.req.rid for sl in sls)
                     if key not in batches:
                         batches[key] = self.make_batch([sl.ch for sl in sls], bstream)
+                        nbuilt += 1
                     e0, e1 = self.make_event(), self.make_event()
                     e0.record(bstream)
                     batches[key].step(self.chunk)
@@ -193,6 +226,9 @@ class Server:
                 if sl.remaining == 0 and not sl.inflight and not sl.packed_pending:
                     if keep_results:
                         results[sl.req.rid] = sl.ch.get_state()
+                    # the packed batches this run was part of are of no further use
+                    for key in [k for k in batches if sl.req.rid in k]:
+                        batches.pop(key).close()
                     sl.ch.close()
                     used -= sl.fp
                     done[sl.req.rid] = dict(t_admit=sl.t_admit, t_done=self.clock() - t0,
@@ -209,11 +245,29 @@ class Server:
             b.close()
         work = sum(r.points * r.nsub for r in requests)
         lat = [d["latency"] for d in done.values()]
-        metrics = dict(requests=len(requests), wall_s=wall, packed=self.packed, batches_built=len(batches), mpts_substep_per_s=work / wall / 1e6,
+        metrics = dict(requests=len(requests), wall_s=wall, packed=self.packed, batches_built=nbuilt,
+                       mpts_substep_per_s=work / wall / 1e6,
                        step_ms_p50=_pct(step_ms, 50), step_ms_p99=_pct(step_ms, 99), steps_timed=len(step_ms),
                        request_s_p50=_pct(lat, 50), request_s_p99=_pct(lat, 99), max_concurrency=max_conc,
-                       mean_concurrency=float(np.mean(conc_samples)) if conc_samples else 0.0)
+                       mean_concurrency=float(np.mean(conc_samples)) if conc_samples else 0.0,
+                       setup_threads=self.setup_threads)
         return results, metrics
+
+
+def _current_device():
+    """The CUDA device of the calling thread (None without a GPU): set-up threads build
+    their runs on the loop's device, not on the runtime's default for a new thread."""
+    try:
+        import torch
+        return torch.cuda.current_device() if torch.cuda.is_available() else None
+    except Exception:
+        return None
+
+
+def _set_device(dev):
+    if dev is not None:
+        import torch
+        torch.cuda.set_device(dev)
 
 
 def _torch_stream():

@@ -136,3 +136,51 @@ def test_packed_mode_completes_every_run_exactly():
     for r in reqs:
         assert res[r.rid]["steps"] == r.nsub      # packed steps plus the per-run tail add up
     assert m["packed"] and m["batches_built"] >= 1
+
+
+def test_a_slow_set_up_does_not_stall_the_other_runs():
+    """Admission builds the run on the set-up thread: while a slow factory call is under
+    way, the loop keeps issuing steps of the runs already active."""
+    import threading
+    import time as _time
+    clock = Clock()
+    gate = threading.Event()
+    issued_while_building = []
+
+    class Tracked(FakeChannel):
+        def step(self, k):
+            if gate.is_set():
+                issued_while_building.append(self.r.rid)
+            super().step(k)
+
+    def factory(r, stream):
+        if r.rid == 1:           # the second run takes a while to build
+            gate.set()
+            _time.sleep(0.05)
+            gate.clear()
+        return Tracked(r, stream, clock)
+
+    reqs = [Request(i, 0.0, 180.0, 3.1, 1.5, 32, 49, 32, 1e-3, 3000, i) for i in range(2)]
+    srv = Server(10 ** 9, max_slots=2, factory=factory, footprint=lambda r: 1,
+                 make_stream=lambda: FakeStream(clock), make_event=lambda: FakeEvent(clock), clock=clock,
+                 idle_sleep=0.0)
+    res, m = srv.run(reqs)
+    assert 0 in issued_while_building
+    assert res[0]["steps"] == res[1]["steps"] == 3000 and m["setup_threads"] == 1
+
+
+def test_retired_runs_drop_their_packed_batches():
+    clock, log = Clock(), []
+    closed = []
+
+    class ClosingBatch(FakeBatch):
+        def close(self):
+            closed.append(tuple(ch.r.rid for ch in self.chans))
+
+    reqs = poisson_requests(12, rate=50.0, seed=5, length=(10, 60))
+    srv = _server(10 ** 9, 4, clock, log)
+    srv.packed = True
+    srv.make_batch = lambda chans, stream: ClosingBatch(chans, stream)
+    res, m = srv.run(reqs)
+    assert len(closed) == m["batches_built"]            # every batch is closed exactly once
+    assert all(res[r.rid]["steps"] == r.nsub for r in reqs)
