@@ -368,16 +368,14 @@ def cpu_threads():
         return os.cpu_count()
 
 
-def oracle_anchor_c1():
-    """The oracle's full small workload, not extrapolated: Re_tau 180, 32 x 49 x 32,
-    10 substeps and the box filter with tau_ij, timed on all host threads and on one."""
+def _anchor_seconds():
+    """Best of three whole runs of the oracle on the small workload (after one warm-up)."""
     import oracle as O
     import synthetic as SY
     c = CONFIGS["re180_32x49x32"]
     kind, p1, p3 = c["filt"]
     st = O.Setup(c["re"], c["Lx"], c["Lz"], c["Nx"], c["Ny"], c["Nz"], c["dt"])
     s0 = SY.perturbed_poiseuille(st.y, c["re"], c["Lx"], c["Lz"], c["Nx"], c["Nz"], seed=1, amp=0.1)
-    pts = c["Nx"] * c["Ny"] * c["Nz"]
 
     def once():
         t0 = time.perf_counter()
@@ -386,11 +384,21 @@ def oracle_anchor_c1():
         return time.perf_counter() - t0
 
     once()   # warm caches (coefficient systems, FFT plans)
-    t_all = min(once() for _ in range(3))
+    return min(once() for _ in range(3))
+
+
+def oracle_anchor_c1():
+    """The oracle's full small workload, not extrapolated: Re_tau 180, 32 x 49 x 32,
+    10 substeps and the box filter with tau_ij, timed on all host threads and, in a child
+    process whose thread pools are limited to one thread, on one."""
+    c = CONFIGS["re180_32x49x32"]
+    pts = c["Nx"] * c["Ny"] * c["Nz"]
+    t_all = _anchor_seconds()
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     try:
-        import threadpoolctl
-        with threadpoolctl.threadpool_limits(1):
-            t_one = min(once() for _ in range(3))
+        r = subprocess.run([sys.executable, "-c", "import bench; print(bench._anchor_seconds())"], cwd=ROOT,
+                           env=env, capture_output=True, text=True, timeout=600)
+        t_one = float(r.stdout.strip().splitlines()[-1]) if r.returncode == 0 else None
     except Exception:
         t_one = None
     val = lambda t: pts * c["sub_per_step"] / t / 1e6 if t else None
@@ -873,7 +881,7 @@ def main():
     ap.add_argument("--precision", choices=["fp64", "mixed", "f64x", "mixed_df"], default="fp64")
     ap.add_argument("--no-modes", action="store_true", help="skip the mixed / double-float runs")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-mix run")
-    ap.add_argument("--serve-requests", type=int, default=24)
+    ap.add_argument("--serve-requests", type=int, default=96)
     ap.add_argument("--precision-study", type=int, default=0,
                     help="run FP64 / mixed / double-float for this many substeps and report profile errors")
     ap.add_argument("--config", choices=sorted(CONFIGS), default=DEFAULT)
