@@ -80,8 +80,10 @@ typedef struct chan_opts {
                         Kolmogorov-scaled formula                                      */
   int slab_planes;   /* planes per slab of the plane-local transform passes (0: all Ny
                         planes unless the twelve mixed-layout transform fields would
-                        pass 16 GiB, then the fewest equal slabs below that).  Results
-                        do not depend on it; only the transform buffers scale with it */
+                        pass 8 GiB, then the fewest equal slabs below that).  Results
+                        do not depend on it; only the transform buffers scale with it.
+                        The filter pass runs in slabs of at most these planes whose six
+                        products and nine outputs stay within 4 GiB                    */
   int lean_tables;   /* 1: keep the implicit-step LU factors and homogeneous solutions of
                         one RK3 substep only and recompute them at each substep (a third
                         of the table memory, more FP64 work); -1: keep all three; 0: lean
@@ -91,6 +93,12 @@ typedef struct chan_opts {
                         1 in place from global memory, 2 staged in shared memory, 0 staged
                         unless that needs more than 16 KB per CTA (chan_autotune may
                         change it).  Results do not depend on it                        */
+  int keep_rhs;      /* 1: keep the interior right-hand sides of the last Helmholtz solves
+                        (two Fourier fields), from which the next substep's right-hand
+                        side follows without the B product (Appendix A); -1: form B X
+                        in every substep instead; 0: keep them unless the box would then
+                        need more than 150 GB.  The two forms agree to rounding, not
+                        bitwise                                                         */
 } chan_opts;
 
 /* Fill *o with defaults: eta_w = 1, grid_re = 0, FP64, library stream. */

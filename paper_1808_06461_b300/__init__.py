@@ -43,7 +43,7 @@ class chan_opts(ctypes.Structure):
                 ("dt", ctypes.c_double), ("eta_w", ctypes.c_double), ("grid_re", ctypes.c_double),
                 ("precision", ctypes.c_int), ("stream", ctypes.c_void_p),
                 ("mesh", ctypes.POINTER(ctypes.c_double)), ("slab_planes", ctypes.c_int),
-                ("lean_tables", ctypes.c_int), ("y_tables", ctypes.c_int)]
+                ("lean_tables", ctypes.c_int), ("y_tables", ctypes.c_int), ("keep_rhs", ctypes.c_int)]
 
 
 class ChanError(RuntimeError):
@@ -142,7 +142,7 @@ class Channel:
     """
 
     def __init__(self, re_tau, Lx, Lz, Nx, Ny, Nz, dt, precision=CHAN_PREC_FP64, eta_w=1.0,
-                 grid_re=0.0, stream=None, mesh=None, slab_planes=0, lean_tables=0, y_tables=0):
+                 grid_re=0.0, stream=None, mesh=None, slab_planes=0, lean_tables=0, y_tables=0, keep_rhs=0):
         o = chan_opts()
         _lib.chan_opts_default(ctypes.byref(o))
         o.re_tau, o.Lx, o.Lz, o.Nx, o.Ny, o.Nz, o.dt = re_tau, Lx, Lz, Nx, Ny, Nz, dt
@@ -150,6 +150,7 @@ class Channel:
         o.slab_planes = int(slab_planes)
         o.lean_tables = int(lean_tables)
         o.y_tables = int(y_tables)
+        o.keep_rhs = int(keep_rhs)
         o.stream = stream
         if mesh is not None:
             self._mesh = np.ascontiguousarray(mesh, dtype=np.float64)

@@ -114,11 +114,20 @@ int slab_planes(int Nx, int Ny, int Nz, int prec, int req) {
   if (req > 0) return req < Ny ? req : Ny;
   const size_t es = prec_t32(prec) ? sizeof(float2) : sizeof(double2);
   const size_t plane = 12 * (size_t)(3 * Nz / 2) * (size_t)(Nx / 2) * es;
-  size_t smax = ((size_t)16 << 30) / plane;
+  size_t smax = ((size_t)8 << 30) / plane;
   if (smax < 1) smax = 1;
   if ((size_t)Ny <= smax) return Ny;
   const size_t nslab = (Ny + smax - 1) / smax;
   return (int)((Ny + nslab - 1) / nslab);
+}
+
+// Planes per slab of the filter pass: its six products and nine outputs ([15][slab][M]
+// complex doubles) within 4 GiB, and no more planes than a transform slab.
+int filter_slab(int Nx, int Nz, int slab) {
+  const size_t per_plane = 15 * (size_t)Nz * (size_t)(Nx / 2) * sizeof(double2);
+  size_t s = ((size_t)4 << 30) / per_plane;
+  if (s < 1) s = 1;
+  return (size_t)slab < s ? slab : (int)s;
 }
 
 void clean_modes(chan_s* h, double2* f) {
@@ -237,13 +246,13 @@ void set_filter(chan_s* h, int kind, double p1, double p3) {
 
 // Device bytes chan_init_ex requests for a box (the filter transfer function,
 // allocated on the first filter call, included).  Mirrors the allocations below.
-size_t footprint_ex(int Nx, int Ny, int Nz, int prec, int slab_req, int lean) {
+size_t footprint_ex(int Nx, int Ny, int Nz, int prec, int slab_req, int lean, int keep) {
   const size_t nxh = Nx / 2, M = (size_t)Nz * nxh, C = (size_t)(Nz / 2) * nxh, n = (size_t)Ny * M;
   const size_t nslot = lean ? 1 : 3;
   const size_t L1 = 3 * (size_t)Nx / 2, L3 = 3 * (size_t)Nz / 2;
   const size_t es = prec_t32(prec) ? sizeof(float2) : sizeof(double2);
   size_t b = 0;
-  b += 8 * n * sizeof(double2) + 4 * Ny * sizeof(double) + 3 * sizeof(double);            // state
+  b += (keep ? 8 : 6) * n * sizeof(double2) + 4 * Ny * sizeof(double) + 3 * sizeof(double);   // state
   b += 5 * 7 * (size_t)Ny * sizeof(double) + 3 * (size_t)Ny * sizeof(double);              // y tables
   b += (nxh + Nz) * sizeof(double);                                                          // wavenumbers
   b += ((size_t)Ny * 7 * C + nslot * (size_t)Ny * 11 * C + nslot * 4 * C + 3 * ((size_t)Ny + 1)) * sizeof(double);
@@ -258,7 +267,7 @@ size_t footprint_ex(int Nx, int Ny, int Nz, int prec, int slab_req, int lean) {
   const size_t S = slab_planes(Nx, Ny, Nz, prec, slab_req);
   b += (size_t)NWF * n * sizeof(double2);                                                    // work fields
   b += 12 * S * L3 * nxh * es;                                                               // mixed fields
-  b += (6 + 9) * S * M * sizeof(double2);                                                    // filter products, outputs
+  b += (6 + 9) * (size_t)filter_slab(Nx, Nz, (int)S) * M * sizeof(double2);                 // filter products, outputs
   b += (CHAN_NSTAT * (size_t)Ny + 2) * sizeof(double);                                       // statistics
   b += M * sizeof(double);                                                                   // filter G
   return b;
@@ -267,11 +276,19 @@ size_t footprint_ex(int Nx, int Ny, int Nz, int prec, int slab_req, int lean) {
 // Lean tables when asked, or automatically when the box would pass 200 GB with all three.
 int lean_tables(int Nx, int Ny, int Nz, int prec, int slab_req, int req) {
   if (req != 0) return req > 0;
-  return footprint_ex(Nx, Ny, Nz, prec, slab_req, 0) > (size_t)200e9;
+  return footprint_ex(Nx, Ny, Nz, prec, slab_req, 0, 1) > (size_t)200e9;
 }
 
-size_t footprint(int Nx, int Ny, int Nz, int prec) {   // automatic slab and table choice
-  return footprint_ex(Nx, Ny, Nz, prec, 0, lean_tables(Nx, Ny, Nz, prec, 0, 0));
+// Kept Helmholtz right-hand sides unless asked not to, or automatically when the box would
+// pass 150 GB with them.
+int keep_rhs(int Nx, int Ny, int Nz, int prec, int slab_req, int lean, int req) {
+  if (req != 0) return req > 0;
+  return footprint_ex(Nx, Ny, Nz, prec, slab_req, lean, 1) <= (size_t)150e9;
+}
+
+size_t footprint(int Nx, int Ny, int Nz, int prec) {   // automatic slab, table and right-hand-side choice
+  const int lean = lean_tables(Nx, Ny, Nz, prec, 0, 0);
+  return footprint_ex(Nx, Ny, Nz, prec, 0, lean, keep_rhs(Nx, Ny, Nz, prec, 0, lean, 0));
 }
 
 // Capture one RK3 step (substeps 0, 1, 2) into a graph; the handle's
@@ -364,7 +381,7 @@ void batch_substep(chan_batch_s* b) {
 }  // namespace
 
 // The filter outputs of one slab: ubar_i (k = 0..2) and tau_ij (k = 3..8), [slab][M] each.
-static double2* filt(chan_s* h, int k) { return h->fout + (size_t)k * h->slab * h->M; }
+static double2* filt(chan_s* h, int k) { return h->fout + (size_t)k * h->fslab * h->M; }
 
 // The filter pass (Sec. 3.1), slab by slab: P(u_i u_j) to work slots 2..7 (kept for the
 // filtered pressure and the database record), P(ubar_i ubar_j) to the slab buffer, then
@@ -378,25 +395,27 @@ static void filter_pass(chan_s* h, int kind, double p1, double p3, double* host_
   const int applyG[6] = {0, 0, 0, 1, 1, 1};
   void* mx[12];
   for (int k = 0; k < 12; ++k) mx[k] = mixed(h, k);
-  const size_t n = fsize(h), sn = (size_t)h->slab * h->M;
-  for (int y0 = 0; y0 < h->Ny; y0 += h->slab) {
-    const int ny = h->Ny - y0 < h->slab ? h->Ny - y0 : h->slab;
+  const size_t n = fsize(h), sn = (size_t)h->fslab * h->M;
+  for (int y0 = 0; y0 < h->Ny; y0 += h->fslab) {
+    const int ny = h->Ny - y0 < h->fslab ? h->Ny - y0 : h->fslab;
     const size_t o = (size_t)y0 * h->M;
     const double2* u[3] = {wf(h, WF_U1) + o, h->v + o, wf(h, WF_U3) + o};
     const double2* in[6] = {u[0], u[1], u[2], u[0], u[1], u[2]};
-    { Traced t(h, KID_ZINV); CK(launch_zinv(h, in, applyG, mx, 6, ny, 0)); }
-    { Traced t(h, KID_XPASS); CK(launch_xpass(h, 1, mx + 3, mx + 6, ny)); }   // ubar_i ubar_j -> slots 6..11
-    { Traced t(h, KID_XPASS); CK(launch_xpass(h, 1, mx, mx, ny)); }           // u_i u_j       -> slots 0..5
+    // the products are formed from the fluctuations (the (0,0) modes taken as zero); the
+    // epilogue adds the mean parts back where they do not cancel
+    { Traced t(h, KID_ZINV); CK(launch_zinv(h, in, applyG, mx, 6, ny, 0, 1)); }
+    { Traced t(h, KID_XPASS); CK(launch_xpass(h, 1, mx + 3, mx + 6, ny)); }   // ubar'_i ubar'_j -> slots 6..11
+    { Traced t(h, KID_XPASS); CK(launch_xpass(h, 1, mx, mx, ny)); }           // u'_i u'_j       -> slots 0..5
     double2* fo[12];
     for (int k = 0; k < 6; ++k) { fo[k] = wf(h, 2 + k) + o; fo[6 + k] = h->pbb + k * sn; }
     { Traced t(h, KID_ZFWD); CK(launch_zfwd(h, mx, fo, 12, ny, 0)); }
-    const double2* puu[6] = {fo[0], fo[1], fo[2], fo[3], fo[4], fo[5]};
+    double2* puu[6] = {fo[0], fo[1], fo[2], fo[3], fo[4], fo[5]};
     const double2* pbb[6] = {fo[6], fo[7], fo[8], fo[9], fo[10], fo[11]};
     double2* ub[3];
     double2* ta[6];
     for (int k = 0; k < 3; ++k) ub[k] = filt(h, k);
     for (int k = 0; k < 6; ++k) ta[k] = filt(h, 3 + k);
-    { Traced t(h, KID_FILTER_OUT); CK(launch_filter_out(h, u, puu, pbb, ub, ta, ny)); }
+    { Traced t(h, KID_FILTER_OUT); CK(launch_filter_out(h, u, puu, pbb, ub, ta, y0, ny)); }
     const double2* cub[3] = {ub[0], ub[1], ub[2]};
     const double2* cta[6] = {ta[0], ta[1], ta[2], ta[3], ta[4], ta[5]};
     { Traced t(h, KID_STATS); CK(launch_stats_filtered(h, cub, cta, y0, ny)); }
@@ -516,7 +535,6 @@ int chan_init_ex(chan_t* out, const chan_opts* o) {
     // state
     h->v = dalloc<double2>(h, n); h->om = dalloc<double2>(h, n); h->chi = dalloc<double2>(h, n);
     h->dv = dalloc<double2>(h, n); h->Nchi_p = dalloc<double2>(h, n); h->Nom_p = dalloc<double2>(h, n);
-    h->Rom = dalloc<double2>(h, n); h->Rchi = dalloc<double2>(h, n);
     h->U1 = dalloc<double>(h, Ny); h->U3 = dalloc<double>(h, Ny);
     h->H1m_p = dalloc<double>(h, Ny); h->H3m_p = dalloc<double>(h, Ny);
     h->scal = dalloc<double>(h, 3);
@@ -540,6 +558,12 @@ int chan_init_ex(chan_t* out, const chan_opts* o) {
     h->ytab = o->y_tables == 1 ? 1 : (o->y_tables == 2 ? 0 : -1);
     h->lean = lean_tables(h->Nx, h->Ny, h->Nz, h->prec, o->slab_planes, o->lean_tables);
     const size_t nslot = h->lean ? 1 : 3;
+    // kept Helmholtz right-hand sides (without them the Helmholtz steps form B X in every substep)
+    h->Rom = h->Rchi = nullptr;
+    if (keep_rhs(h->Nx, h->Ny, h->Nz, h->prec, o->slab_planes, h->lean, o->keep_rhs)) {
+      h->Rom = dalloc<double2>(h, n);
+      h->Rchi = dalloc<double2>(h, n);
+    }
     h->pois = dalloc<double>(h, Ny * 7 * (size_t)h->C);
     h->helm = dalloc<double>(h, nslot * Ny * 11 * (size_t)h->C);
     h->infl = dalloc<double>(h, nslot * 4 * (size_t)h->C);
@@ -619,8 +643,9 @@ int chan_init_ex(chan_t* out, const chan_opts* o) {
     h->nmix = 12;
     h->slab = slab_planes(h->Nx, h->Ny, h->Nz, h->prec, o->slab_planes);
     h->mixed = dalloc<unsigned char>(h, (size_t)h->nmix * h->slab * L3 * h->nxh * es);
-    h->pbb = dalloc<double2>(h, 6 * (size_t)h->slab * h->M);
-    h->fout = dalloc<double2>(h, 9 * (size_t)h->slab * h->M);
+    h->fslab = filter_slab(h->Nx, h->Nz, h->slab);
+    h->pbb = dalloc<double2>(h, 6 * (size_t)h->fslab * h->M);
+    h->fout = dalloc<double2>(h, 9 * (size_t)h->fslab * h->M);
     h->scr = wf(h, WF_U1);   // [2][Ny][M]: the u_1, u_3 slots
     h->stat = dalloc<double>(h, CHAN_NSTAT * Ny + 2);
     CK(fft_configure(h));
@@ -733,6 +758,7 @@ struct CkptHeader {
   double re, Lx, Lz, dt, eta_w, grid_re;
   long long nsub;
   double t;
+  int keep_rhs;   // the Helmholtz right-hand sides follow (not for a lean box)
 };
 
 static int ckpt_arrays(chan_s* h, void** p, size_t* bytes) {
@@ -740,8 +766,10 @@ static int ckpt_arrays(chan_s* h, void** p, size_t* bytes) {
   void* ptr[] = {h->v, h->om, h->chi, h->dv, h->Nchi_p, h->Nom_p, h->Rom, h->Rchi,
                  h->U1, h->U3, h->H1m_p, h->H3m_p, h->scal};
   const size_t sz[] = {n, n, n, n, n, n, n, n, ny, ny, ny, ny, 3 * sizeof(double)};
-  for (int k = 0; k < 13; ++k) { p[k] = ptr[k]; bytes[k] = sz[k]; }
-  return 13;
+  int na = 0;
+  for (int k = 0; k < 13; ++k)
+    if (ptr[k]) { p[na] = ptr[k]; bytes[na] = sz[k]; ++na; }   // a handle may keep no right-hand sides
+  return na;
 }
 
 size_t chan_checkpoint_bytes(chan_t h) {
@@ -758,10 +786,10 @@ int chan_checkpoint_save(chan_t h, void* buf) {
   if (!h->have_state) return bad(h, "chan_checkpoint_save: no state set", CHAN_ESTATE);
   CkptHeader hd;
   std::memset(&hd, 0, sizeof(hd));
-  std::memcpy(hd.magic, "CHANCKP1", 8);
+  std::memcpy(hd.magic, "CHANCKP2", 8);
   hd.Nx = h->Nx; hd.Ny = h->Ny; hd.Nz = h->Nz; hd.prec = h->prec;
   hd.re = h->re; hd.Lx = h->Lx; hd.Lz = h->Lz; hd.dt = h->dt; hd.eta_w = h->eta_w; hd.grid_re = h->grid_re;
-  hd.nsub = h->nsub; hd.t = h->t;
+  hd.nsub = h->nsub; hd.t = h->t; hd.keep_rhs = h->Rom != nullptr;
   char* out = static_cast<char*>(buf);
   std::memcpy(out, &hd, sizeof(hd));
   size_t off = sizeof(hd);
@@ -784,10 +812,13 @@ int chan_checkpoint_load(chan_t h, const void* buf) {
   if (!h || !buf) return bad(h, "chan_checkpoint_load: NULL argument");
   CkptHeader hd;
   std::memcpy(&hd, buf, sizeof(hd));
-  if (std::memcmp(hd.magic, "CHANCKP1", 8) != 0) return bad(h, "chan_checkpoint_load: not a checkpoint");
+  if (std::memcmp(hd.magic, "CHANCKP2", 8) != 0) return bad(h, "chan_checkpoint_load: not a checkpoint");
   if (hd.Nx != h->Nx || hd.Ny != h->Ny || hd.Nz != h->Nz || hd.prec != h->prec || hd.re != h->re ||
       hd.Lx != h->Lx || hd.Lz != h->Lz || hd.dt != h->dt || hd.eta_w != h->eta_w || hd.grid_re != h->grid_re)
     return bad(h, "chan_checkpoint_load: written by a handle of another box, grid, time step or precision");
+  if (hd.keep_rhs != (h->Rom != nullptr))
+    return bad(h, "chan_checkpoint_load: written by a handle that keeps its Helmholtz right-hand sides differently "
+                  "(lean_tables)");
   const char* in = static_cast<const char*>(buf);
   size_t off = sizeof(hd);
   try {

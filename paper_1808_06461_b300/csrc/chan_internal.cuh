@@ -89,7 +89,8 @@ struct chan_s {
   std::vector<double> y, wq;
   // state (device)
   double2 *v, *om, *chi, *dv, *Nchi_p, *Nom_p;
-  double2 *Rom, *Rchi;     // interior right-hand sides of the last Helmholtz solves (valid when scal[2] != 0)
+  double2 *Rom, *Rchi;     // interior right-hand sides of the last Helmholtz solves (valid when scal[2] != 0;
+                           // NULL for a lean box, whose Helmholtz steps always form B X)
   double *U1, *U3, *H1m_p, *H3m_p;
   double* scal;            // [0] f of last substep, [1] Q0, [2] Rom / Rchi valid
   // tables (device)
@@ -109,7 +110,8 @@ struct chan_s {
   int nwf;
   void* mixed;             // mixed fields of one slab [NMIX][slab][L3][nxh]
   int nmix;
-  int slab;                // planes per transform slab (Ny unless the mixed fields would pass 16 GiB)
+  int slab;                // planes per transform slab (Ny unless the mixed fields would pass 8 GiB)
+  int fslab;               // planes per slab of the filter pass (its products and outputs within 4 GiB)
   double2* pbb;            // filter pass: products of the filtered velocities of one slab [6][slab][M]
   double2* fout;           // filter pass: ubar_i, tau_ij of one slab [9][slab][M]
   double2* scr;            // wall-normal sweep scratch [2][Ny][M] (aliases the u_1, u_3 work slots)
@@ -167,8 +169,10 @@ cudaError_t launch_helm(chan_s* h, const double2* Nchi, const double2* Nom, int 
 cudaError_t launch_poisson(chan_s* h, int s);
 cudaError_t launch_mean(chan_s* h, const double2* H1, const double2* H3, int s);
 // Filter epilogue over ny planes (pointers at the slab's first plane).
-cudaError_t launch_filter_out(chan_s* h, const double2* const* u, const double2* const* puu,
-                              const double2* const* pbb, double2* const* ubar, double2* const* tau, int ny);
+// puu holds P(u'_i u'_j) of the fluctuations on entry and P(u_i u_j) on return; the planes
+// start at y0.
+cudaError_t launch_filter_out(chan_s* h, const double2* const* u, double2* const* puu,
+                              const double2* const* pbb, double2* const* ubar, double2* const* tau, int y0, int ny);
 cudaError_t launch_apply_G(chan_s* h, const double2* in, double2* out);
 // Double-float storage: n complex values to (hi, lo) pairs in place; pairs back to FP64
 // (src == dst allowed).
@@ -196,8 +200,9 @@ cudaError_t launch_zfwd_batch(chan_s* const* hs, int n, const BatchWork* w, cuda
 // FFT passes.  in/out are arrays of nf device pointers.
 // Transform passes over ny planes; the pointers address the first plane of the slab.
 // f32_mask (mixed mode only): bit f set = input f is stored as float2 [Ny][M].
+// skip00: every field's (0,0) mode (its plane mean) is transformed as zero.
 cudaError_t launch_zinv(chan_s* h, const double2* const* in, const int* apply_G, void* const* out, int nf, int ny,
-                        int f32_mask);
+                        int f32_mask, int skip00 = 0);
 // The six substep transform inputs (u1, v, u3, w1, w2, w3) from plane y0 on, given the
 // work slots of the pre kernel's outputs, and their float2 mask: in the mixed mode the
 // substep's pre kernel leaves u1, u3 as float2 [2][Ny][M] in the w1 slot and w1, w3 in

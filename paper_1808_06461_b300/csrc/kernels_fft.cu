@@ -746,6 +746,7 @@ struct ZArgs {
   int pair_out;   // double-float mode: the forward pass writes (hi, lo) pairs
   int f32_mask;   // inverse pass: bit f set = field f is stored as float2 (mixed modes)
   int pair_in;    // FP32 transforms of Fourier fields stored as pairs (mixed mode with pair sweeps)
+  int skip00;     // inverse pass: the (0,0) mode (the plane mean) is taken as zero
   FftPlan pl;
 };
 
@@ -795,6 +796,8 @@ __device__ __forceinline__ void zinv_body(const ZArgs& A, const typename V2<T>::
     else zinv_load<T2, 3>(A, a, in, in32, kx0, hz);
   } else if (A.applyG[f]) zinv_load<T2, 1>(A, a, in, in32, kx0, hz);
   else zinv_load<T2, 0>(A, a, in, in32, kx0, hz);
+  // the (0,0) mode is element 0 of the first column chunk, loaded by thread 0 above
+  if (A.skip00 && bx == 0 && threadIdx.x == 0) a[slot<T2>(0, A.pl)] = zero2<T2>();
   const float2* ts = stage_tw2p<T2>(a + A.KB * A.ld, A.pl);
   __syncthreads();
   // the middle third of the padded column is zero: pruned first stage
@@ -1122,10 +1125,11 @@ static ZArgs zargs(chan_s* h, size_t es) {
 static size_t fft_esize(const chan_s* h) { return prec_t32(h->prec) ? sizeof(float2) : sizeof(double2); }
 
 cudaError_t launch_zinv(chan_s* h, const double2* const* in, const int* apply_G, void* const* out, int nf, int ny,
-                        int f32_mask) {
+                        int f32_mask, int skip00) {
   const size_t es = fft_esize(h);
   ZArgs A = zargs(h, es);
   A.f32_mask = prec_t32(h->prec) ? f32_mask : 0;
+  A.skip00 = skip00;
   for (int f = 0; f < nf; ++f) { A.in[f] = in[f]; A.out[f] = out[f]; A.applyG[f] = apply_G ? apply_G[f] : 0; }
   dim3 grid((h->nxh + A.KB - 1) / A.KB, ny, nf);
   size_t sm = (size_t)A.KB * A.ld * es + tw2p_bytes(h->p3);

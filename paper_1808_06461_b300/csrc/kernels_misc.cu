@@ -9,29 +9,51 @@ namespace {
 
 struct FiltArgs {
   const double2* u[3];
-  const double2* puu[6];
-  const double2* pbb[6];
+  double2* puu[6];        // in: P(u'_i u'_j); out: P(u_i u_j)
+  const double2* pbb[6];  // P(ubar'_i ubar'_j)
   double2* ubar[3];
   double2* tau[6];
   const double* G;
+  const double *U1, *U3;  // mean profiles, indexed by plane
   size_t n;        // planes * M
   int M;
+  int y0;          // first plane
   int pair;        // u_i stored as FP32 pairs (double-float mode)
 };
 
+// The products of the filter pass are formed from the fluctuations u'_i = u_i - U_i(y) (the
+// transforms take the (0,0) mode as zero).  The filter acts in x and z only and G(0) = 1, so
+// filt(U_i u'_j) = U_i ubar'_j and, u'_j being band-limited, P(U_i u'_j) = U_i u'_j; hence
+//   tau_ij = G P(u'_i u'_j) - P(ubar'_i ubar'_j)   (the same tau_ij, without the large mean
+//   parts that cancel in G P(u_i u_j) - P(ubar_i ubar_j)), and
+//   P(u_i u_j) = P(u'_i u'_j) + U_i u'_j + U_j u'_i, plus U_i U_j in the (0,0) mode.
 __global__ void k_filter_out(FiltArgs A) {
   const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= A.n) return;
-  const double g = A.G[e % A.M];
+  const int m = (int)(e % A.M);
+  const int y = A.y0 + (int)(e / A.M);
+  const double g = A.G[m];
+  double2 x[3];
 #pragma unroll
   for (int f = 0; f < 3; ++f) {
-    double2 x = load_c(A.u[f], e, A.pair);
-    A.ubar[f][e] = make_double2(g * x.x, g * x.y);
+    x[f] = load_c(A.u[f], e, A.pair);
+    A.ubar[f][e] = make_double2(g * x[f].x, g * x[f].y);
   }
+  const double U[3] = {A.U1[y], 0.0, A.U3[y]};
+  const int pi[6] = {0, 1, 2, 0, 0, 1}, pj[6] = {0, 1, 2, 1, 2, 2};
 #pragma unroll
   for (int p = 0; p < 6; ++p) {
-    double2 a = A.puu[p][e], b = A.pbb[p][e];
+    double2 a = A.puu[p][e];
+    const double2 b = A.pbb[p][e];
     A.tau[p][e] = make_double2(fma(g, a.x, -b.x), fma(g, a.y, -b.y));
+    const int i = pi[p], j = pj[p];
+    if (m == 0) {
+      a.x += U[i] * U[j];
+    } else {
+      a.x += fma(U[i], x[j].x, U[j] * x[i].x);
+      a.y += fma(U[i], x[j].y, U[j] * x[i].y);
+    }
+    A.puu[p][e] = a;
   }
 }
 
@@ -167,9 +189,12 @@ cudaError_t launch_from_pairs(chan_s* h, const double2* src, double2* dst, size_
   return cudaGetLastError();
 }
 
-cudaError_t launch_filter_out(chan_s* h, const double2* const* u, const double2* const* puu, const double2* const* pbb,
-                              double2* const* ubar, double2* const* tau, int ny) {
+cudaError_t launch_filter_out(chan_s* h, const double2* const* u, double2* const* puu, const double2* const* pbb,
+                              double2* const* ubar, double2* const* tau, int y0, int ny) {
   FiltArgs A;
+  A.U1 = h->U1;
+  A.U3 = h->U3;
+  A.y0 = y0;
   for (int f = 0; f < 3; ++f) { A.u[f] = u[f]; A.ubar[f] = ubar[f]; }
   for (int p = 0; p < 6; ++p) { A.puu[p] = puu[p]; A.pbb[p] = pbb[p]; A.tau[p] = tau[p]; }
   A.G = h->G;

@@ -585,7 +585,7 @@ __device__ __forceinline__ void helm_one(int Ny, size_t M, size_t NC, int m, con
         if (i > 0 && i < Ny - 1) {
           if constexpr (PREV) r = Y::axpy(qp, Y::lds(rg.f(st, 3)), yband7<Y>(sA + 7 * i, wa));
           else r = Y::axpy(ca, yband7<Y>(sB + 7 * i, wx), yband7<Y>(sA + 7 * i, wa));
-          Y::st(Rf, (size_t)i * M + m, r);
+          if (Rf) Y::st(Rf, (size_t)i * M + m, r);   // kept unless the handle keeps none (lean boxes)
         }
         Y::st(scr, (size_t)i * M + m,
               yfwd<Y>(r, Y::ldr(rg.t(st, 0)), Y::ldr(rg.t(st, 1)), Y::ldr(rg.t(st, 2)), hz));
@@ -641,7 +641,8 @@ __device__ __forceinline__ void helm_body(Geo g, YTabs t, const typename Y::R* _
   }
   const double gm = c_rk3[s][0], zt = c_rk3[s][1], al = c_rk3[s][2];
   const double dt = g.dt, nu = g.nu;
-  const bool prev = scal[2] != 0.0;   // the previous substep's right-hand sides are valid
+  // the previous substep's right-hand sides are valid (a lean box keeps none: Rom = NULL)
+  const bool prev = Rom != nullptr && scal[2] != 0.0;
   const double bp = c_rk3[(s + 2) % 3][3];
   const R c1 = Y::r(prev ? 1.0 + al / bp : 1.0 - al * dt * nu * mi.k2), cg = Y::r(dt * gm), cz = Y::r(dt * zt);
   const R ca = Y::r(al * dt * nu), qp = Y::r(-al / bp);

@@ -41,7 +41,7 @@ def test_allocation_beyond_the_device_is_an_error_not_a_fault():
     import paper_1808_06461_b300 as chan
     lib = chan.library()
     need = chan.footprint_bytes(768, 4097, 768, chan.CHAN_PREC_FP64)
-    assert need > 400e9                  # more than the 288 GB (275,040 MiB) of HBM
+    assert need > 300e9                  # more than the 288 GB (275,040 MiB) of HBM
     h = ctypes.c_void_p()
     rc = lib.chan_init(ctypes.byref(h), 180.0, math.pi, math.pi / 2, 768, 4097, 768, 1e-3)
     assert rc == chan.CHAN_ENOMEM and not h.value

@@ -166,7 +166,9 @@ def test_filter_and_stats_every_mode(chan, kind, p, prec, ten_steps):
     out_ref, utau_ref, ubulk_ref = O.stats(st, ref, ub_ref, tau_ref)
     scale = np.abs(out_ref[2:8]).max()
     mixed = prec in (chan.CHAN_PREC_MIXED, chan.CHAN_PREC_MIXED_DF)
-    tol_tau, tol_stat = (1e-3, 1e-5) if mixed else (TOL, TOL)
+    # mixed modes: the products are FP32; formed from the fluctuations, tau_ij carries the FP32
+    # rounding of u'_i u'_j (not of the mean parts, which cancel), about 1e-6 relative
+    tol_tau, tol_stat = (1e-4, 1e-6) if mixed else (TOL, TOL)
     for f in range(3):
         assert rel(ub[f], ub_ref[f]) < 1e-12, (f, rel(ub[f], ub_ref[f]))
     for q in range(6):
