@@ -14,7 +14,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libchan.so")
 CU = ["chan_api.cu", "kernels_y.cu", "kernels_fft.cu", "kernels_misc.cu", "noalloc.cu"]
 CPP = ["setup_host.cpp"]
-HEADERS = ["chan_internal.cuh", "chan_host.h", "df.cuh"]
+HEADERS = ["chan_internal.cuh", "chan_host.h", "df.cuh", "y_bodies.cuh", "fft_bodies.cuh"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
               "-Xcompiler", "-fPIC"]
 
