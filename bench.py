@@ -814,13 +814,13 @@ def run_serving(args, rank):
 
     out = {"requests": args.serve_requests, "rate_per_s": 50.0, "seed": 42, "hbm_budget_gb": 64,
            "max_slots": 16}
+    how = {"streams": False, "persistent": "persistent", "packed": True}
     for prec, tag in ((0, "fp64"), (1, "mixed"), (2, "f64x"), (3, "mixed_df")):
-        for packed in (False, True):
+        for mode in args.serve_modes.split(","):
             reqs = poisson_requests(args.serve_requests, 50.0, 42 + rank, precision=prec)
-            _, m = Server(64 << 30, max_slots=16, factory=channel_factory(ic), packed=packed).run(
+            _, m = Server(64 << 30, max_slots=16, factory=channel_factory(ic), packed=how[mode]).run(
                 reqs, keep_results=False)
-            out[tag + ("_packed" if packed else "_streams")] = {
-                k: (round(v, 4) if isinstance(v, float) else v) for k, v in m.items()}
+            out[tag + "_" + mode] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in m.items()}
     return out
 
 
@@ -882,6 +882,9 @@ def main():
     ap.add_argument("--no-modes", action="store_true", help="skip the mixed / double-float runs")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-mix run")
     ap.add_argument("--serve-requests", type=int, default=96)
+    ap.add_argument("--serve-modes", default="streams,persistent",
+                    help="comma-separated serving issue modes: streams (per-run streams), persistent "
+                         "(one work-list launch per RK3 step of all runs), packed (one launch per kernel)")
     ap.add_argument("--precision-study", type=int, default=0,
                     help="run FP64 / mixed / double-float for this many substeps and report profile errors")
     ap.add_argument("--config", choices=sorted(CONFIGS), default=DEFAULT)

@@ -49,6 +49,7 @@ extern "C" {
 #define CHAN_ECUDA    -3   /* a CUDA runtime call or kernel launch failed                */
 #define CHAN_ENAN     -4   /* the state holds a non-finite value (checked on read-back)  */
 #define CHAN_ESTATE   -5   /* call out of order (e.g. chan_step before chan_set_state)   */
+#define CHAN_ETIMEOUT -6   /* a bounded device-side wait ran out (persistent batches)   */
 
 #define CHAN_FILTER_SHARP 0   /* Eq. (fou_fil): G = 1 if |k1| < pi/l1c and |k3| < pi/l3c   */
 #define CHAN_FILTER_BOX   1   /* top-hat of widths (D1, D3): G = sinc(k1 D1/2) sinc(k3 D3/2) */
@@ -355,6 +356,37 @@ int chan_batch_create(chan_batch_t* out, chan_t* runs, int n, void* stream);
 int chan_batch_step(chan_batch_t b, int nsub);
 const char* chan_batch_last_error(chan_batch_t b);
 void chan_batch_free(chan_batch_t b);
+
+/*
+ * A batch created with CHAN_BATCH_PERSISTENT (at most 16 runs; no paper
+ * counterpart) steps with persistent launches instead of one launch per
+ * kernel: one launch advances each run by up to 48 substeps.  A run's work is
+ * its sequence of stages (substep, phase: pre, z inverse, x, z forward,
+ * non-linear terms, Helmholtz, Poisson, mean flow), each stage the blocks of
+ * that phase's kernel; the launch's CTAs take blocks of any run whose previous
+ * stage is complete, so the phases of different runs run at once and every run
+ * goes on to its next substep without waiting for the others.  A CTA that finds
+ * no ready block polls again, a bounded number of times (chan_batch_set_wait);
+ * when the polls run out the launch is void (its remaining blocks are skipped)
+ * and chan_batch_status then returns CHAN_ETIMEOUT.  Each run's result is
+ * bitwise the one chan_step gives.  The plan (stage table and an argument table
+ * in device memory) is built at creation from the runs' current buffers and
+ * launch shapes.  chan_batch_step(b, nsub) advances every run by nsub;
+ * chan_batch_step_each(b, nsub) advances run r by nsub[r] >= 0 (runs may differ).
+ */
+#define CHAN_BATCH_PERSISTENT 1
+int chan_batch_create_ex(chan_batch_t* out, chan_t* runs, int n, void* stream, int flags);
+int chan_batch_step_each(chan_batch_t b, const int* nsub);
+/* Wait for the batch stream; CHAN_ETIMEOUT if a persistent launch ran out of polls since
+ * the last call (the runs' states are then void and must be set again), else CHAN_OK. */
+int chan_batch_status(chan_batch_t b);
+/* Persistent batches: empty polls (>= 1, about 0.13 us each) after which a CTA gives up
+ * (default 2^23, about a second); hold_run, hold_stage >= 0 make that run's stage
+ * (substep of the launch * 8 + phase, phases in the order above) need one completion more
+ * than it can get, so that the polls run out (a test of the timeout path); -1, -1: none. */
+int chan_batch_set_wait(chan_batch_t b, long long polls, int hold_run, int hold_stage);
+/* CTAs of a persistent launch (resident CTAs per SM x SMs); 0 for other batches. */
+int chan_batch_persistent_grid(chan_batch_t b);
 
 /* Wait for the handle's stream (a library interface; the paper has no counterpart). */
 int chan_sync(chan_t h);

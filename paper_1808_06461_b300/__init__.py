@@ -18,7 +18,8 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libchan.so")
 
-CHAN_OK, CHAN_EINVAL, CHAN_ENOMEM, CHAN_ECUDA, CHAN_ENAN, CHAN_ESTATE = 0, -1, -2, -3, -4, -5
+CHAN_OK, CHAN_EINVAL, CHAN_ENOMEM, CHAN_ECUDA, CHAN_ENAN, CHAN_ESTATE, CHAN_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
+CHAN_BATCH_PERSISTENT = 1
 CHAN_FILTER_SHARP, CHAN_FILTER_BOX = 0, 1
 CHAN_PREC_FP64, CHAN_PREC_MIXED, CHAN_PREC_F64X, CHAN_PREC_MIXED_DF = 0, 1, 2, 3
 CHAN_NSTAT = 20
@@ -33,7 +34,8 @@ SYMBOLS = ("chan_opts_default", "chan_init", "chan_init_ex", "chan_free", "chan_
            "chan_filtered_enstrophy", "chan_batch_create", "chan_batch_step", "chan_batch_last_error",
            "chan_batch_free", "chan_autotune", "chan_tuned_shape", "chan_database_record",
            "chan_spectra", "chan_optimize_mesh", "chan_filtered_pressure", "chan_checkpoint_bytes",
-           "chan_checkpoint_save", "chan_checkpoint_load")
+           "chan_checkpoint_save", "chan_checkpoint_load", "chan_batch_create_ex", "chan_batch_status",
+           "chan_batch_set_wait", "chan_batch_persistent_grid", "chan_batch_step_each")
 CHAN_NKERNELS = 16
 
 
@@ -85,6 +87,11 @@ def load_library(path=LIB_PATH):
         "chan_set_graph": (I, [P, I]),
         "chan_filtered_enstrophy": (I, [P, I, D, D, P]),
         "chan_batch_create": (I, [ctypes.POINTER(P), ctypes.POINTER(P), I, P]),
+        "chan_batch_create_ex": (I, [ctypes.POINTER(P), ctypes.POINTER(P), I, P, I]),
+        "chan_batch_status": (I, [P]),
+        "chan_batch_step_each": (I, [P, P]),
+        "chan_batch_set_wait": (I, [P, ctypes.c_longlong, I, I]),
+        "chan_batch_persistent_grid": (I, [P]),
         "chan_batch_step": (I, [P, I]),
         "chan_batch_last_error": (ctypes.c_char_p, [P]),
         "chan_batch_free": (None, [P]),
@@ -323,21 +330,47 @@ class Channel:
 
 
 class ChannelBatch:
-    """Packed stepping of several Channels of one precision (one launch per kernel for all)."""
+    """Packed stepping of several Channels of one precision: one launch per kernel for all,
+    or (persistent=True, at most 16 runs) persistent work-list launches of up to 48
+    substeps of every run."""
 
-    def __init__(self, channels, stream=None):
+    def __init__(self, channels, stream=None, persistent=False):
         self.channels = list(channels)
         arr = (ctypes.c_void_p * len(self.channels))(*[c.h.value for c in self.channels])
         b = ctypes.c_void_p()
-        rc = _lib.chan_batch_create(ctypes.byref(b), arr, len(self.channels), stream)
+        flags = CHAN_BATCH_PERSISTENT if persistent else 0
+        rc = _lib.chan_batch_create_ex(ctypes.byref(b), arr, len(self.channels), stream, flags)
         if rc != CHAN_OK:
             raise ChanError(rc, _lib.chan_batch_last_error(None).decode())
         self.b = b
+        self.persistent = bool(persistent)
 
     def step(self, nsub):
         rc = _lib.chan_batch_step(self.b, int(nsub))
         if rc != CHAN_OK:
             raise ChanError(rc, _lib.chan_batch_last_error(self.b).decode())
+
+    def step_each(self, nsub):
+        """Persistent batches: run r advances by nsub[r] substeps (counts may differ)."""
+        arr = (ctypes.c_int * len(self.channels))(*[int(k) for k in nsub])
+        rc = _lib.chan_batch_step_each(self.b, arr)
+        if rc != CHAN_OK:
+            raise ChanError(rc, _lib.chan_batch_last_error(self.b).decode())
+
+    def status(self):
+        """Wait for the batch; raises ChanError(CHAN_ETIMEOUT) if a persistent wait ran out."""
+        rc = _lib.chan_batch_status(self.b)
+        if rc != CHAN_OK:
+            raise ChanError(rc, _lib.chan_batch_last_error(self.b).decode())
+
+    def set_wait(self, polls, hold_run=-1, hold_stage=-1):
+        """Wait limit of the persistent launches; (hold_run, hold_stage) for timeout tests."""
+        rc = _lib.chan_batch_set_wait(self.b, int(polls), int(hold_run), int(hold_stage))
+        if rc != CHAN_OK:
+            raise ChanError(rc, _lib.chan_batch_last_error(self.b).decode())
+
+    def persistent_grid(self):
+        return int(_lib.chan_batch_persistent_grid(self.b))
 
     def close(self):
         if getattr(self, "b", None):

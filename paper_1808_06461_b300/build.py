@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libchan.so")
-CU = ["chan_api.cu", "kernels_y.cu", "kernels_fft.cu", "kernels_misc.cu", "noalloc.cu"]
+CU = ["chan_api.cu", "kernels_y.cu", "kernels_fft.cu", "kernels_misc.cu", "kernels_persist.cu", "noalloc.cu"]
 CPP = ["setup_host.cpp"]
 HEADERS = ["chan_internal.cuh", "chan_host.h", "df.cuh", "y_bodies.cuh", "fft_bodies.cuh"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
@@ -36,25 +36,37 @@ def _stale(obj, srcs):
 def build(verbose=False, force=False):
     os.makedirs(BUILD, exist_ok=True)
     hdrs = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(HERE, "..", "include", "chan.h")]
-    objs = []
-    for f in CPP:
+    objs, jobs = [], []
+    for f in CPP + CU:
         src = os.path.join(CSRC, f)
         obj = os.path.join(BUILD, f + ".o")
         if force or _stale(obj, [src] + hdrs):
-            cmd = ["g++", "-O2", "-fPIC", "-std=c++17", "-c", src, "-o", obj]
-            _run(cmd, verbose)
+            if f in CPP:
+                jobs.append(["g++", "-O2", "-fPIC", "-std=c++17", "-c", src, "-o", obj])
+            else:
+                jobs.append([_nvcc()] + NVCC_FLAGS + ["-c", src, "-o", obj])
         objs.append(obj)
-    for f in CU:
-        src = os.path.join(CSRC, f)
-        obj = os.path.join(BUILD, f + ".o")
-        if force or _stale(obj, [src] + hdrs):
-            cmd = [_nvcc()] + NVCC_FLAGS + ["-c", src, "-o", obj]
-            _run(cmd, verbose)
-        objs.append(obj)
+    _run_all(jobs, verbose)   # the units compile concurrently
     if force or _stale(LIB, objs):
         cmd = [_nvcc(), "-shared", "-o", LIB] + objs + ["-lquadmath", "-lcudart"]
         _run(cmd, verbose)
     return LIB
+
+
+def _run_all(cmds, verbose):
+    procs = []
+    for cmd in cmds:
+        if verbose:
+            print(" ".join(cmd), flush=True)
+        procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)))
+    failed = None
+    for cmd, p in procs:
+        out, _ = p.communicate()
+        if p.returncode != 0 and failed is None:
+            sys.stderr.write(out)
+            failed = cmd
+    if failed:
+        raise RuntimeError("build step failed: " + " ".join(failed))
 
 
 def _run(cmd, verbose):

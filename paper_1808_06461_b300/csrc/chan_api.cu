@@ -339,6 +339,7 @@ struct chan_batch_s {
   bool own_stream;
   std::vector<cudaEvent_t> ev;   // one per run (join) + one (fork)
   cudaGraphExec_t gexec;
+  PersistPlan* plan;             // persistent work-list launches (CHAN_BATCH_PERSISTENT), else NULL
   std::string err;
 };
 
@@ -1228,7 +1229,14 @@ size_t chan_footprint_bytes(int Nx, int Ny, int Nz, int precision) {
 const char* chan_kernel_name(int k) { return (k >= 0 && k < KID_COUNT) ? kKernelNames[k] : nullptr; }
 
 int chan_batch_create(chan_batch_t* out, chan_t* runs, int n, void* stream) {
+  return chan_batch_create_ex(out, runs, n, stream, 0);
+}
+
+int chan_batch_create_ex(chan_batch_t* out, chan_t* runs, int n, void* stream, int flags) {
   if (!out) return bad(nullptr, "chan_batch_create: out is NULL");
+  if (flags & ~CHAN_BATCH_PERSISTENT) return bad(nullptr, "chan_batch_create: unknown flags");
+  if ((flags & CHAN_BATCH_PERSISTENT) && n > CHAN_MAXBATCH)
+    return bad(nullptr, "chan_batch_create: a persistent batch holds at most 16 runs");
   *out = nullptr;
   if (!runs || n < 1) return bad(nullptr, "chan_batch_create: no runs");
   for (int r = 0; r < n; ++r) {
@@ -1246,6 +1254,7 @@ int chan_batch_create(chan_batch_t* out, chan_t* runs, int n, void* stream) {
   if (!b) return bad(nullptr, "chan_batch_create: out of host memory", CHAN_ENOMEM);
   b->runs.assign(runs, runs + n);
   b->gexec = nullptr;
+  b->plan = nullptr;
   if (stream) { b->stream = (cudaStream_t)stream; b->own_stream = false; }
   else if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
     delete b;
@@ -1259,9 +1268,45 @@ int chan_batch_create(chan_batch_t* out, chan_t* runs, int n, void* stream) {
       chan_batch_free(b);
       return bad(nullptr, "chan_batch_create: cudaEventCreate failed", CHAN_ECUDA);
     }
+  if (flags & CHAN_BATCH_PERSISTENT) {
+    std::vector<BatchWork> w(n);
+    for (int r = 0; r < n; ++r) w[r] = batch_work(runs[r]);
+    const cudaError_t e = persist_create(runs, n, w.data(), b->stream, &b->plan);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      chan_batch_free(b);
+      return bad(nullptr, std::string("chan_batch_create: persistent plan: ") + cudaGetErrorString(e), CHAN_ECUDA);
+    }
+  }
   *out = b;
   return CHAN_OK;
 }
+
+namespace {
+// nsub[r] substeps of each run r in persistent launches of up to persist_max_substeps() each.
+void persist_steps(chan_batch_s* b, const int* nsub) {
+  const int n = (int)b->runs.size(), kmax = persist_max_substeps();
+  std::vector<int> left(nsub, nsub + n), now(n);
+  for (;;) {
+    bool any = false;
+    for (int r = 0; r < n; ++r) {
+      now[r] = left[r] < kmax ? left[r] : kmax;
+      any = any || now[r] > 0;
+    }
+    if (!any) break;
+    BK(persist_launch(b->plan, b->runs.data(), now.data(), b->stream));
+    for (int r = 0; r < n; ++r) {
+      chan_s* h = b->runs[r];
+      for (int q = 0; q < now[r]; ++q) {
+        h->t += chan_rk3_weight((int)(h->nsub % 3)) * h->dt;
+        h->nsub += 1;
+        h->have_filter = false;
+      }
+      left[r] -= now[r];
+    }
+  }
+}
+}  // namespace
 
 int chan_batch_step(chan_batch_t b, int nsub) {
   if (!b) return bad(nullptr, "chan_batch_step: NULL batch");
@@ -1271,6 +1316,13 @@ int chan_batch_step(chan_batch_t b, int nsub) {
     for (int r = 0; r < n; ++r) {   // join: the batch stream waits for each run's stream
       BK(cudaEventRecord(b->ev[r], b->runs[r]->stream));
       BK(cudaStreamWaitEvent(b->stream, b->ev[r], 0));
+    }
+    if (b->plan) {
+      std::vector<int> each(n, nsub);
+      persist_steps(b, each.data());
+      BK(cudaEventRecord(b->ev[n], b->stream));   // fork: each run's stream waits for the batch
+      for (int r = 0; r < n; ++r) BK(cudaStreamWaitEvent(b->runs[r]->stream, b->ev[n], 0));
+      return CHAN_OK;
     }
     int k = 0;
     auto aligned = [&]() {
@@ -1316,12 +1368,67 @@ int chan_batch_step(chan_batch_t b, int nsub) {
   return CHAN_OK;
 }
 
+int chan_batch_step_each(chan_batch_t b, const int* nsub) {
+  if (!b) return bad(nullptr, "chan_batch_step_each: NULL batch");
+  if (!b->plan) { b->err = "chan_batch_step_each: not a persistent batch"; return CHAN_EINVAL; }
+  const int n = (int)b->runs.size();
+  if (!nsub) { b->err = "chan_batch_step_each: NULL counts"; return CHAN_EINVAL; }
+  for (int r = 0; r < n; ++r)
+    if (nsub[r] < 0) { b->err = "chan_batch_step_each: a count < 0"; return CHAN_EINVAL; }
+  try {
+    for (int r = 0; r < n; ++r) {   // join: the batch stream waits for each run's stream
+      BK(cudaEventRecord(b->ev[r], b->runs[r]->stream));
+      BK(cudaStreamWaitEvent(b->stream, b->ev[r], 0));
+    }
+    persist_steps(b, nsub);
+    BK(cudaEventRecord(b->ev[n], b->stream));   // fork: each run's stream waits for the batch
+    for (int r = 0; r < n; ++r) BK(cudaStreamWaitEvent(b->runs[r]->stream, b->ev[n], 0));
+  } catch (Fail f) {
+    return f.code;
+  }
+  return CHAN_OK;
+}
+
+int chan_batch_status(chan_batch_t b) {
+  if (!b) return bad(nullptr, "chan_batch_status: NULL batch");
+  if (!b->plan) {
+    const cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) { b->err = std::string("chan_batch_status: ") + cudaGetErrorString(e); return CHAN_ECUDA; }
+    return CHAN_OK;
+  }
+  int timed_out = 0;
+  const cudaError_t e = persist_status(b->plan, b->stream, &timed_out);
+  if (e != cudaSuccess) { b->err = std::string("chan_batch_status: ") + cudaGetErrorString(e); return CHAN_ECUDA; }
+  if (timed_out) {
+    b->err = "chan_batch_status: a wait of a persistent launch ran out; the runs' states are void";
+    return CHAN_ETIMEOUT;
+  }
+  return CHAN_OK;
+}
+
+int chan_batch_set_wait(chan_batch_t b, long long polls, int hold_run, int hold_stage) {
+  if (!b) return bad(nullptr, "chan_batch_set_wait: NULL batch");
+  if (!b->plan) { b->err = "chan_batch_set_wait: not a persistent batch"; return CHAN_EINVAL; }
+  if (polls < 1 || hold_run >= (int)b->runs.size() || hold_stage >= 8 * persist_max_substeps()) {
+    b->err = "chan_batch_set_wait: polls < 1, or no such run or stage";
+    return CHAN_EINVAL;
+  }
+  persist_set_wait(b->plan, polls, hold_run, hold_stage);
+  return CHAN_OK;
+}
+
+int chan_batch_persistent_grid(chan_batch_t b) { return b && b->plan ? persist_grid(b->plan) : 0; }
+
 const char* chan_batch_last_error(chan_batch_t b) { return b ? b->err.c_str() : g_init_err.c_str(); }
 
 void chan_batch_free(chan_batch_t b) {
   if (!b) return;
   if (b->stream) cudaStreamSynchronize(b->stream);
   if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  if (b->plan) {
+    persist_free(b->plan, b->stream);
+    cudaStreamSynchronize(b->stream);
+  }
   for (cudaEvent_t e : b->ev)
     if (e) cudaEventDestroy(e);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);

@@ -187,6 +187,19 @@ cudaError_t launch_stats(chan_s* h, const double2* u1, const double2* u3, int ze
 // <ubar_i ubar_j> and <tau_ij> rows of planes y0 .. y0+ny-1 from the slab's filter outputs.
 cudaError_t launch_stats_filtered(chan_s* h, const double2* const* ubar, const double2* const* tau, int y0, int ny);
 
+// Persistent work-list launches of a batch (kernels_persist.cu): the stage table and device
+// argument table of n <= CHAN_MAXBATCH runs; one launch of nsub[r] (0 .. persist_max_substeps())
+// substeps of each run r; whether a bounded wait of a launch gave up since the last status
+// call; the wait limit and a (run, stage) that is made to need one completion more (tests).
+struct PersistPlan;
+cudaError_t persist_create(chan_s* const* hs, int n, const BatchWork* w, cudaStream_t st, PersistPlan** out);
+cudaError_t persist_launch(PersistPlan* P, chan_s* const* hs, const int* nsub, cudaStream_t st);
+int persist_max_substeps();
+cudaError_t persist_status(PersistPlan* P, cudaStream_t st, int* timed_out);
+void persist_set_wait(PersistPlan* P, long long spins, int hold_run, int hold_stage);
+int persist_grid(const PersistPlan* P);
+void persist_free(PersistPlan* P, cudaStream_t st);
+
 // Packed launches over n <= CHAN_MAXBATCH runs of one precision, on `st`.
 cudaError_t launch_pre_batch(chan_s* const* hs, int n, const BatchWork* w, cudaStream_t st);
 cudaError_t launch_nonlin_batch(chan_s* const* hs, int n, const BatchWork* w, cudaStream_t st);

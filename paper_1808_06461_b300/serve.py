@@ -14,7 +14,14 @@ sizes only), so a result is bitwise the same alone and in the mix.
 With ``packed=True`` the admitted runs of one precision advance together:
 one RK3 step of all of them is one launch per kernel (``chan_batch_step``,
 graph-replayed), on a single batch stream; a run's last partial step runs on
-its own stream.
+its own stream.  With ``packed="persistent"`` every admitted run of a precision (up to
+16 per batch) advances in persistent launches (``chan_batch_step_each``) of up to
+``persist_chunk`` substeps of each run (fewer for larger runs, in proportion to their
+points, so that the runs of a launch end together): the launch's CTAs take the blocks of any run whose
+previous stage is done, so the phases of different runs overlap and each run goes on to
+its next substep without a batch-wide boundary; a run's last partial step is part of a
+launch too.  There a run's step latency is its launch's device time per RK3 step the
+launch advanced it by.
 
 Per-step latency is the device time between CUDA events recorded around each
 RK3 step (contention included; in packed mode the packed step's time counts
@@ -106,7 +113,7 @@ class Server:
 
     def __init__(self, hbm_budget, max_slots=16, chunk=3, max_inflight=2, factory=None, footprint=None,
                  make_stream=None, make_event=None, clock=time.perf_counter, idle_sleep=2e-4, packed=False,
-                 make_batch=None, setup_threads=1):
+                 make_batch=None, setup_threads=1, persist_chunk=48):
         self.hbm_budget, self.max_slots, self.chunk, self.max_inflight = int(hbm_budget), max_slots, chunk, max_inflight
         if factory is None:
             raise ValueError("a channel factory is required (see channel_factory)")
@@ -116,8 +123,24 @@ class Server:
         self.make_event = make_event or _torch_event
         self.clock, self.idle_sleep = clock, idle_sleep
         self.packed = packed
-        self.make_batch = make_batch or (lambda chans, stream: ChannelBatch(chans, stream=stream.cuda_stream))
+        persistent = packed == "persistent"
+        self.batch_runs = 16 if persistent else None   # runs per batch (a persistent launch holds 16)
+        self.make_batch = make_batch or (lambda chans, stream: ChannelBatch(chans, stream=stream.cuda_stream,
+                                                                            persistent=persistent))
         self.setup_threads = int(setup_threads)   # 0: build admitted runs on the loop's own thread
+        self.persist_chunk = int(persist_chunk)    # substeps of the smallest run per persistent launch
+
+    def _persist_counts(self, part):
+        """Substeps of each run of a persistent launch: persist_chunk for the smallest run of
+        the batch, fewer (whole RK3 steps, at least one) for larger runs in proportion to their
+        points, so that the runs of a launch end at about the same time and no large run's
+        tail holds the launch while the device idles."""
+        pmin = min(sl.req.points for sl in part)
+        out = []
+        for sl in part:
+            k = self.chunk * max(1, int(round(self.persist_chunk * pmin / sl.req.points / self.chunk)))
+            out.append(min(sl.remaining, k))
+        return out
 
     def run(self, requests, keep_results=True):
         for r in requests:
@@ -171,15 +194,55 @@ class Server:
                         still_starting.append((r, stream, fp, t_admit, fut))
                 starting = still_starting
             max_conc = max(max_conc, len(active) + len(starting))
+            # persistent issue: every run with work left advances by up to persist_chunk substeps
+            # in one launch per batch of a precision
+            if self.packed == "persistent":
+                if bstream is None:
+                    bstream = self.make_stream()
+                groups = collections.defaultdict(list)
+                for sl in active:
+                    if sl.remaining > 0:
+                        groups[sl.req.precision].append(sl)
+                for prec, sls in groups.items():
+                    for i in range(0, len(sls), self.batch_runs):
+                        part = sls[i:i + self.batch_runs]
+                        if len(binflight) >= self.max_inflight:
+                            break
+                        key = tuple(sl.req.rid for sl in part)
+                        if key not in batches:
+                            batches[key] = self.make_batch([sl.ch for sl in part], bstream)
+                            nbuilt += 1
+                        ks = self._persist_counts(part)
+                        e0, e1 = self.make_event(), self.make_event()
+                        e0.record(bstream)
+                        batches[key].step_each(ks)
+                        e1.record(bstream)
+                        binflight.append((e0, e1, list(zip(part, ks))))
+                        for sl, k in zip(part, ks):
+                            sl.remaining -= k
+                            sl.packed_pending += 1
+                        progressed = True
+                while binflight and binflight[0][1].query():
+                    e0, e1, ran = binflight.popleft()
+                    t = e0.elapsed_time(e1)
+                    for sl, k in ran:
+                        sl.packed_pending -= 1
+                        if k >= self.chunk:
+                            step_ms.append(t * self.chunk / k)
+                    progressed = True
             # packed issue: one RK3 step of every full-step run of a precision in one launch per kernel
-            if self.packed:
+            elif self.packed:
                 if bstream is None:
                     bstream = self.make_stream()
                 groups = collections.defaultdict(list)
                 for sl in active:
                     if sl.remaining >= self.chunk:
                         groups[sl.req.precision].append(sl)
+                parts = []
                 for prec, sls in groups.items():
+                    n = self.batch_runs or len(sls)
+                    parts += [sls[i:i + n] for i in range(0, len(sls), n)]
+                for sls in parts:
                     if len(binflight) >= self.max_inflight:
                         break
                     key = tuple(sl.req.rid for sl in sls)
@@ -204,7 +267,7 @@ class Server:
                     progressed = True
             # issue: one RK3 step per run, up to max_inflight steps queued per stream
             for sl in active:
-                if self.packed and (sl.remaining >= self.chunk or sl.packed_pending):
+                if self.packed == "persistent" or (self.packed and (sl.remaining >= self.chunk or sl.packed_pending)):
                     continue
                 while sl.remaining > 0 and len(sl.inflight) < self.max_inflight:
                     k = min(self.chunk, sl.remaining)

@@ -184,3 +184,36 @@ def test_retired_runs_drop_their_packed_batches():
     res, m = srv.run(reqs)
     assert len(closed) == m["batches_built"]            # every batch is closed exactly once
     assert all(res[r.rid]["steps"] == r.nsub for r in reqs)
+
+
+class FakeEachBatch(FakeBatch):
+    """A persistent batch: run r advances by its own count; at most 16 runs."""
+
+    def __init__(self, chans, stream):
+        assert len(chans) <= 16
+        super().__init__(chans, stream)
+
+    def step_each(self, ks):
+        assert len(ks) == len(self.chans) and all(k >= 0 for k in ks)
+        for ch, k in zip(self.chans, ks):
+            ch.steps += k
+        self.stream.busy_until = max(self.stream.busy_until, self.stream.clock.t) + 1e-3 * max(ks)
+
+
+def test_persistent_mode_completes_every_run_exactly_and_never_steps_a_run_alone():
+    clock, log = Clock(), []
+    reqs = poisson_requests(40, rate=50.0, seed=5, length=(10, 100))
+    srv = _server(10 ** 9, 20, clock, log)
+    srv.packed, srv.batch_runs, srv.persist_chunk = "persistent", 16, 12
+    srv.make_batch = lambda chans, stream: FakeEachBatch(chans, stream)
+    inner = srv.factory
+
+    def no_solo_steps(r, stream):
+        ch = inner(r, stream)
+        ch.step = None     # a run of a persistent server is only ever stepped by its batch
+        return ch
+    srv.factory = no_solo_steps
+    res, m = srv.run(reqs)
+    for r in reqs:
+        assert res[r.rid]["steps"] == r.nsub      # whole and partial chunks add up in the launches
+    assert m["packed"] == "persistent" and m["batches_built"] >= 2 and m["max_concurrency"] >= 2
