@@ -872,6 +872,30 @@ def run_precision_study(args, c, name):
     print(json.dumps(out), flush=True)
 
 
+def run_batch_probe(args):
+    """Profiling case of the persistent batch launch: four serving-size runs, one launch of
+    12 substeps of each (``--batch-probe``); prints one JSON line with the wall time."""
+    import torch
+    import synthetic as SY
+    import paper_1808_06461_b300 as chan
+    prec = {"fp64": 0, "mixed": 1, "f64x": 2, "mixed_df": 3}[args.precision]
+    runs = []
+    for (nx, ny, nz, re) in ((32, 49, 32, 180.0), (64, 97, 64, 395.0), (128, 129, 128, 550.0), (64, 49, 128, 395.0)):
+        ch = chan.Channel(re, math.pi, math.pi / 2, nx, ny, nz, 2e-4, precision=prec)
+        s0 = SY.perturbed_poiseuille(ch.grid(), re, math.pi, math.pi / 2, nx, nz, seed=nx + ny, amp=0.1)
+        ch.set_state(s0["v"], s0["omega2"], s0["U1"], s0["U3"])
+        runs.append(ch)
+    b = chan.ChannelBatch(runs, persistent=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b.step(12)
+    b.status()
+    t = time.perf_counter() - t0
+    pts = sum(ch.Nx * ch.Ny * ch.Nz for ch in runs)
+    b.close()
+    print(json.dumps({"probe": "persistent batch", "runs": 4, "substeps": 12, "points": pts, "seconds": t}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -893,9 +917,13 @@ def main():
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the Re 1000 and Re 2000 mixed-precision configuration runs")
     ap.add_argument("--no-autotune", action="store_true", help="default launch shapes (profiling runs)")
+    ap.add_argument("--batch-probe", action="store_true",
+                    help="profiling case of the persistent batch launch (four serving-size runs, 12 substeps)")
     args = ap.parse_args()
     c = CONFIGS[args.config]
-    if args.precision_study:
+    if args.batch_probe:
+        run_batch_probe(args)
+    elif args.precision_study:
         run_precision_study(args, c, args.config)
     elif args.impl == "reference":
         run_reference(args, c, args.config)
