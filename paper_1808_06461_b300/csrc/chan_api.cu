@@ -81,7 +81,8 @@ const char* const kKernelNames[KID_COUNT] = {"k_pre",     "k_zinv",       "k_xpa
 struct Traced {
   chan_s* h;
   ProfRec* r;
-  Traced(chan_s* hh, int k) : h(hh), r(nullptr) {
+  cudaStream_t st;
+  Traced(chan_s* hh, int k, cudaStream_t s = nullptr) : h(hh), r(nullptr), st(s ? s : hh->stream) {
     h->launches[k] += 1;
     if (!h->prof) return;
     if (h->nrec == h->recs.size()) {
@@ -91,10 +92,10 @@ struct Traced {
     }
     r = &h->recs[h->nrec++];
     r->k = k;
-    cudaEventRecord(r->a, h->stream);
+    cudaEventRecord(r->a, st);
   }
   ~Traced() {
-    if (r) cudaEventRecord(r->b, h->stream);
+    if (r) cudaEventRecord(r->b, st);
   }
 };
 
@@ -206,10 +207,17 @@ void run_substep(chan_s* h) {
   if (h->lean) { Traced t(h, KID_TABLES); CK(launch_setup_substep(h, s)); }
   run_pre(h, true);
   run_nonlinear(h);
+  // The mean-flow solve (one CTA) needs only the (0,0) modes of H and the mean profiles,
+  // which the wall-normal sweeps neither read nor write: it runs on the side stream beside
+  // them, and the next substep waits for it.
+  CK(cudaEventRecord(h->ev_fork, h->stream));
+  CK(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+  { Traced t(h, KID_MEAN, h->side); CK(launch_mean(h, wf(h, WF_H1), wf(h, WF_H3), s, h->side)); }
+  CK(cudaEventRecord(h->ev_join, h->side));
   { Traced t(h, KID_NONLIN); CK(launch_nonlin(h, wf(h, WF_H1), wf(h, WF_H2), wf(h, WF_H3), wf(h, WF_NCHI), wf(h, WF_NOM))); }
   { Traced t(h, KID_HELM); CK(launch_helm(h, wf(h, WF_NCHI), wf(h, WF_NOM), s)); }
   { Traced t(h, KID_POISSON); CK(launch_poisson(h, s)); }
-  { Traced t(h, KID_MEAN); CK(launch_mean(h, wf(h, WF_H1), wf(h, WF_H3), s)); }
+  CK(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
   h->t += chan_rk3_weight(s) * h->dt;
   h->nsub += 1;
 }
@@ -499,6 +507,9 @@ int chan_init_ex(chan_t* out, const chan_opts* o) {
     CK(cudaGetDevice(&h->device));
     if (o->stream) { h->stream = (cudaStream_t)o->stream; h->own_stream = false; }
     else { CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking)); h->own_stream = true; }
+    CK(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
     if (o->mesh) {
       const double* m = o->mesh;
       bool ok = m[0] == -1.0 && m[h->Ny - 1] == 1.0;
@@ -676,6 +687,9 @@ void chan_free(chan_t h) {
   // (its release threshold is 0), so a following large allocation finds it
   if (h->stream) cudaStreamSynchronize(h->stream);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  if (h->side) cudaStreamDestroy(h->side);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
   delete h;
 }
 

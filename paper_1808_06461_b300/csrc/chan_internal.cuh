@@ -84,6 +84,8 @@ struct chan_s {
   int Nx, Ny, Nz, nxh, M, C, L1, L3, prec;
   cudaStream_t stream;
   bool own_stream;
+  cudaStream_t side;       // the mean-flow solve of a substep, beside the wall-normal sweeps
+  cudaEvent_t ev_fork, ev_join;
   int device;
   // host copies
   std::vector<double> y, wq;
@@ -167,7 +169,8 @@ cudaError_t launch_nonlin_scratch(chan_s* h, const double2* H1, const double2* H
                                   double2* Nchi, double2* Nom, double2* scr);
 cudaError_t launch_helm(chan_s* h, const double2* Nchi, const double2* Nom, int s);
 cudaError_t launch_poisson(chan_s* h, int s);
-cudaError_t launch_mean(chan_s* h, const double2* H1, const double2* H3, int s);
+// st: the stream to launch on (NULL: the handle's stream)
+cudaError_t launch_mean(chan_s* h, const double2* H1, const double2* H3, int s, cudaStream_t st = nullptr);
 // Filter epilogue over ny planes (pointers at the slab's first plane).
 // puu holds P(u'_i u'_j) of the fluctuations on entry and P(u_i u_j) on return; the planes
 // start at y0.

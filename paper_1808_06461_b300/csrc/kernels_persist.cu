@@ -109,7 +109,7 @@ __device__ __forceinline__ void p_item(const PRun& R, int p, int s, int b) {
     case PH_POIS: {
       const PoisP& a = R.po[s];
       poisson_body<Y>(a.g, a.t, static_cast<const YR*>(a.helm), static_cast<const YR*>(a.pois),
-                      static_cast<const YR*>(a.infl), a.v, a.chi, a.dv, a.scr, a.s, b);
+                      static_cast<const YR*>(a.infl), a.v, a.chi, a.dv, a.scr, a.scal, a.s, b);
       break;
     }
     default: {
@@ -243,7 +243,7 @@ cudaError_t persist_create(chan_s* const* hs, int n, const BatchWork* w, cudaStr
     for (int s = 0; s < 3; ++s) {
       A.he[s] = HelmP{g, t, helm_slot_y(h, s), h->om, h->chi, w[r].Nchi, w[r].Nom, h->Nchi_p, h->Nom_p,
                       h->Rom, h->Rchi, h->scal, h->scr, s};
-      A.po[s] = PoisP{g, t, helm_slot_y(h, s), pois_y(h), infl_slot_y(h, s), h->v, h->chi, h->dv, h->scr, s};
+      A.po[s] = PoisP{g, t, helm_slot_y(h, s), pois_y(h), infl_slot_y(h, s), h->v, h->chi, h->dv, h->scr, h->scal, s};
       A.me[s] = MeanP{g, t, helm_slot(h, s), h->meanh, w[r].H1, w[r].H3, h->U1, h->U3, h->H1m_p, h->H3m_p,
                       h->scal, s};
     }

@@ -58,7 +58,9 @@ template <class Y>
 __global__ void __launch_bounds__(128) k_poisson(Geo g, YTabs t, const typename Y::R* __restrict__ helm,
                                                  const typename Y::R* __restrict__ pois,
                                                  const typename Y::R* __restrict__ infl, double2* v, double2* chi,
-                                                 double2* dv, double2* scr, int s) { poisson_body<Y>(g, t, helm, pois, infl, v, chi, dv, scr, s, blockIdx.x); }
+                                                 double2* dv, double2* scr, double* scal, int s) {
+  poisson_body<Y>(g, t, helm, pois, infl, v, chi, dv, scr, scal, s, blockIdx.x);
+}
 
 
 
@@ -482,7 +484,7 @@ __global__ void __launch_bounds__(128) kb_poisson(YBatch<PoisP> B) {
   const int r = batch_run(B.begin, B.n, blockIdx.x);
   const PoisP& p = B.p[r];
   poisson_body<Y>(p.g, p.t, static_cast<const R*>(p.helm), static_cast<const R*>(p.pois),
-                  static_cast<const R*>(p.infl), p.v, p.chi, p.dv, p.scr, p.s, blockIdx.x - B.begin[r]);
+                  static_cast<const R*>(p.infl), p.v, p.chi, p.dv, p.scr, p.scal, p.s, blockIdx.x - B.begin[r]);
 }
 __global__ void __launch_bounds__(256) kb_mean(YBatch<MeanP> B) {
   const MeanP& p = B.p[blockIdx.x];
@@ -634,19 +636,19 @@ cudaError_t launch_poisson(chan_s* h, int s) {
   if (use_df(h))
     k_poisson<YDF><<<ygrid(h), kYThreads, sm, h->stream>>>(geo(h), ytabs(h), (const dfr*)helm_slot_y(h, s),
                                                            (const dfr*)pois_y(h), (const dfr*)infl_slot_y(h, s),
-                                                           h->v, h->chi, h->dv, h->scr, s);
+                                                           h->v, h->chi, h->dv, h->scr, h->scal, s);
   else
     k_poisson<YF64><<<ygrid(h), kYThreads, sm, h->stream>>>(geo(h), ytabs(h), (const double*)helm_slot_y(h, s),
                                                             (const double*)pois_y(h), (const double*)infl_slot_y(h, s),
-                                                            h->v, h->chi, h->dv, h->scr, s);
+                                                            h->v, h->chi, h->dv, h->scr, h->scal, s);
   return cudaGetLastError();
 }
 
-cudaError_t launch_mean(chan_s* h, const double2* H1, const double2* H3, int s) {
+cudaError_t launch_mean(chan_s* h, const double2* H1, const double2* H3, int s, cudaStream_t st) {
   size_t sm = sizeof(double) * (9 * h->Ny + 256);
   cudaError_t e = smem_attr((const void*)k_mean, sm);
   if (e != cudaSuccess) return e;
-  k_mean<<<1, 256, sm, h->stream>>>(geo(h), ytabs(h), helm_slot(h, s), h->meanh, H1, H3, h->U1, h->U3, h->H1m_p,
+  k_mean<<<1, 256, sm, st ? st : h->stream>>>(geo(h), ytabs(h), helm_slot(h, s), h->meanh, H1, H3, h->U1, h->U3, h->H1m_p,
                                     h->H3m_p, h->scal, s);
   return cudaGetLastError();
 }
@@ -732,7 +734,8 @@ cudaError_t launch_poisson_batch(chan_s* const* hs, int n, const BatchWork* w, c
   for (int r = 0; r < n; ++r) {
     chan_s* h = hs[r];
     const int s = (int)(h->nsub % 3);
-    B.p[r] = PoisP{geo(h), ytabs(h), helm_slot_y(h, s), pois_y(h), infl_slot_y(h, s), h->v, h->chi, h->dv, h->scr, (int)(h->nsub % 3)};
+    B.p[r] = PoisP{geo(h), ytabs(h), helm_slot_y(h, s), pois_y(h), infl_slot_y(h, s), h->v, h->chi, h->dv, h->scr,
+                   h->scal, (int)(h->nsub % 3)};
   }
   const int blocks = fill_begin(B, hs, n);
   const size_t sm = ysm_batch(hs, n, 23, kRingPois);

@@ -683,7 +683,10 @@ template <class Y>
 __device__ __forceinline__ void poisson_body(Geo g, YTabs t, const typename Y::R* CHAN_RO helm,
                                              const typename Y::R* CHAN_RO pois,
                                              const typename Y::R* CHAN_RO infl, double2* v, double2* chi,
-                                             double2* dv, double2* scr_, int s, int bid) {
+                                             double2* dv, double2* scr_, double* scal, int s, int bid) {
+  // the Helmholtz right-hand sides of this substep are in place for the next one (the
+  // Helmholtz kernel of this substep, which reads the flag, is complete)
+  if (bid == 0 && threadIdx.x == 0) scal[2] = 1.0;
   typedef typename Y::R R;
   typedef typename Y::C C;
   extern __shared__ double sm[];
@@ -883,17 +886,14 @@ __device__ __forceinline__ void mean_body(Geo g, YTabs t, const double* CHAN_RO 
     U1[i] = r1[i] + c * uh[i];
     U3[i] = r3[i];
   }
-  if (threadIdx.x == 0) {
-    scal[0] = c / ((al + be) * dt);
-    scal[2] = 1.0;   // the Helmholtz right-hand sides of this substep are in place
-  }
+  if (threadIdx.x == 0) scal[0] = c / ((al + be) * dt);
 }
 
 // Arguments of each body for one run (the packed and persistent launches).
 struct PreP { Geo g; YTabs t; const double2 *v, *om, *dv; const double *U1, *U3; double2 *u1o, *u3o, *om1o, *om3o; };
 struct NonlinP { Geo g; YTabs t; const double2 *H1, *H2, *H3; double2 *Nchi, *Nom, *scr; };
 struct HelmP { Geo g; YTabs t; const void* helm; double2 *om, *chi; const double2 *Nchi, *Nom; double2 *Nchi_p, *Nom_p, *Rom, *Rchi; const double* scal; double2* scr; int s; };
-struct PoisP { Geo g; YTabs t; const void *helm, *pois, *infl; double2 *v, *chi, *dv, *scr; int s; };
+struct PoisP { Geo g; YTabs t; const void *helm, *pois, *infl; double2 *v, *chi, *dv, *scr; double* scal; int s; };
 struct MeanP { Geo g; YTabs t; const double *helm, *meanh; const double2 *H1, *H3; double *U1, *U3, *H1p, *H3p, *scal; int s; };
 
 // ---------------------------------------------------------------------------

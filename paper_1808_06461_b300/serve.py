@@ -28,6 +28,10 @@ RK3 step (contention included; in packed mode the packed step's time counts
 once for every run in it); request latency is arrival to completion on the
 host clock.
 
+Every admitted run issues on its own stream: a process that serves many runs should set
+CUDA_DEVICE_MAX_CONNECTIONS (e.g. 32) before it creates its CUDA context, since with the
+default 8 hardware work queues the streams alias and their work serialises (bench.py does).
+
 A newly admitted run is built (tables, state upload, launch-shape tuning) on
 a set-up thread while the loop keeps issuing the other runs' steps; the run
 holds its slot and its memory from admission on and starts stepping once its
