@@ -211,13 +211,13 @@ struct PersistPlan {
   std::vector<PRun> host;   // the uploaded table, kept until the plan dies (the copy is asynchronous)
   PRun* runs;          // device [n]
   unsigned* ctr;       // device [kCtrWords + 1]; the last word is the sticky error
-  PSched S;            // schedule without the per-launch fields (nsub, s0)
+  PSched S;            // schedule without the per-launch fields (nq, s0)
   const void* fn;
   size_t smem;
   int grid;
 };
 
-// Builds the item list and the device argument table of a batch (hs[0..n), n <= CHAN_MAXBATCH,
+// Builds the stage table and the device argument table of a batch (hs[0..n), n <= CHAN_MAXBATCH,
 // one precision, no slabs, no per-substep tables; w[r] = run r's work fields).
 cudaError_t persist_create(chan_s* const* hs, int n, const BatchWork* w, cudaStream_t st, PersistPlan** out) {
   *out = nullptr;
