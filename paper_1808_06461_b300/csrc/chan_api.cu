@@ -1152,11 +1152,11 @@ int chan_autotune(chan_t h) {
     // 256 threads stay unless another shape is more than 2 % faster
     // (192, 288 and 384 divide the butterfly counts of the 576-point stages: no ragged
     // last round of a stage loop)
-    constexpr int NNT = 8;
+    constexpr int NNT = 9;
     float t_nt[NNT];
     for (float& t : t_nt) t = 1e30f;
-    // (96 and 160 suit the FP32 two-pass transforms: 6 x 24 register transforms per pass)
-    const int nts[NNT] = {256, 128, 192, 288, 384, 512, 96, 160};
+    // (96, 144 and 160 suit the FP32 two-pass transforms: 6 x 24 register transforms per pass)
+    const int nts[NNT] = {256, 128, 192, 288, 384, 512, 96, 160, 144};
     const int ntmax = fft_plan_category(h->p1) == 3 ? 256 : 512;   // the largest register transforms
     for (int rep = 0; rep < 5; ++rep)
       for (int k = 0; k < NNT; ++k) {

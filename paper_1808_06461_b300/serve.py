@@ -16,8 +16,7 @@ one RK3 step of all of them is one launch per kernel (``chan_batch_step``,
 graph-replayed), on a single batch stream; a run's last partial step runs on
 its own stream.  With ``packed="persistent"`` every admitted run of a precision (up to
 16 per batch) advances in persistent launches (``chan_batch_step_each``) of up to
-``persist_chunk`` substeps of each run (fewer for larger runs, in proportion to their
-points, so that the runs of a launch end together): the launch's CTAs take the blocks of any run whose
+``persist_chunk`` substeps of each run: the launch's CTAs take the blocks of any run whose
 previous stage is done, so the phases of different runs overlap and each run goes on to
 its next substep without a batch-wide boundary; a run's last partial step is part of a
 launch too.  There a run's step latency is its launch's device time per RK3 step the
@@ -117,7 +116,7 @@ class Server:
 
     def __init__(self, hbm_budget, max_slots=16, chunk=3, max_inflight=2, factory=None, footprint=None,
                  make_stream=None, make_event=None, clock=time.perf_counter, idle_sleep=2e-4, packed=False,
-                 make_batch=None, setup_threads=1, persist_chunk=48):
+                 make_batch=None, setup_threads=1, persist_chunk=24):
         self.hbm_budget, self.max_slots, self.chunk, self.max_inflight = int(hbm_budget), max_slots, chunk, max_inflight
         if factory is None:
             raise ValueError("a channel factory is required (see channel_factory)")
@@ -132,19 +131,14 @@ class Server:
         self.make_batch = make_batch or (lambda chans, stream: ChannelBatch(chans, stream=stream.cuda_stream,
                                                                             persistent=persistent))
         self.setup_threads = int(setup_threads)   # 0: build admitted runs on the loop's own thread
-        self.persist_chunk = int(persist_chunk)    # substeps of the smallest run per persistent launch
+        self.persist_chunk = int(persist_chunk)    # substeps of a run per persistent launch
 
     def _persist_counts(self, part):
-        """Substeps of each run of a persistent launch: persist_chunk for the smallest run of
-        the batch, fewer (whole RK3 steps, at least one) for larger runs in proportion to their
-        points, so that the runs of a launch end at about the same time and no large run's
-        tail holds the launch while the device idles."""
-        pmin = min(sl.req.points for sl in part)
-        out = []
-        for sl in part:
-            k = self.chunk * max(1, int(round(self.persist_chunk * pmin / sl.req.points / self.chunk)))
-            out.append(min(sl.remaining, k))
-        return out
+        """Substeps of each run of a persistent launch: persist_chunk (whole RK3 steps), or what
+        the run has left.  (Counts in proportion to the runs' sizes served less: a small run's
+        substep is not proportionally shorter, its sweeps being serial over its wall-normal
+        points.)"""
+        return [min(sl.remaining, self.persist_chunk) for sl in part]
 
     def run(self, requests, keep_results=True):
         for r in requests:

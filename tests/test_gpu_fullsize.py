@@ -124,3 +124,27 @@ def test_fullsize_invariants_after_substeps(big):
     for jz in (1, 2, 50, st.Nz // 2 - 1):
         assert np.abs(F[:, jz, 0] - np.conj(F[:, st.Nz - jz, 0])).max() < 1e-12 * np.abs(F).max()
     assert np.abs(F[:, st.Nz // 2, :]).max() == 0
+
+
+@pytest.mark.parametrize("kind,p", [(0, (120.0, 60.0)), (1, (50.0, 50.0))])
+def test_fullsize_filter_sampled_planes(big, kind, p):
+    """ubar_i and tau_ij (Sec. 3.1) of the full workload on sampled planes.  The filter pass
+    runs in slabs of 242 planes here (six products and nine outputs within 4 GiB): planes 241
+    and 242 lie on either side of the slab boundary.  The filter is plane-local, so the oracle
+    computes tau on those planes alone, from the full fields' products."""
+    st, s0, S, ch = big
+    g = ch.get_state()
+    Sg = O.initial_state(st, g["v"], g["omega2"], g["U1"], g["U3"])
+    ub, tau = ch.filter_stresses(kind, *p)
+    planes = np.array([0, 1, 120, 241, 242, 243, 256])
+    G = O.filter_transfer(st, kind, *p)
+    u1, v, u3, _, _, _ = O.velocities(st, Sg)
+    u = [u1[planes], v[planes], u3[planes]]
+    ubr = [G * f for f in u]
+    pu = [O.to_physical(st, f) for f in u]
+    pb = [O.to_physical(st, f) for f in ubr]
+    for f in range(3):
+        assert rel(ub[f][planes], ubr[f]) < TOL, (f, rel(ub[f][planes], ubr[f]))
+    for q, (i, j) in enumerate(O.PAIRS):
+        ref = G * O.to_fourier(st, pu[i] * pu[j]) - O.to_fourier(st, pb[i] * pb[j])
+        assert rel(tau[q][planes], ref) < TOL, (q, rel(tau[q][planes], ref))

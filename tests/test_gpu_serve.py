@@ -107,7 +107,7 @@ def test_autotuned_shapes_leave_results_unchanged():
         ch.set_state(s0["v"], s0["omega2"], s0["U1"], s0["U3"])
         if tune:
             kb, nt, yt = ch.autotune()
-            assert kb in (1, 2, 4, 8, 16) and nt in (96, 128, 160, 192, 256, 288, 384, 512) and yt in (0, 1)
+            assert kb in (1, 2, 4, 8, 16) and nt in (96, 128, 144, 160, 192, 256, 288, 384, 512) and yt in (0, 1)
         ch.step(6)
         out.append(ch.get_state())
         ch.close()
