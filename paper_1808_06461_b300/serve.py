@@ -285,11 +285,16 @@ class Server:
                         step_ms.append(e0.elapsed_time(e1))
                     progressed = True
                 if sl.remaining == 0 and not sl.inflight and not sl.packed_pending:
+                    # the packed batches this run was part of are of no further use; a persistent
+                    # one first reports whether any of its launches ran out of polls (the run's
+                    # state would then be void: ChanError)
+                    for key in [k for k in batches if sl.req.rid in k]:
+                        b = batches.pop(key)
+                        if self.packed == "persistent" and hasattr(b, "status"):
+                            b.status()
+                        b.close()
                     if keep_results:
                         results[sl.req.rid] = sl.ch.get_state()
-                    # the packed batches this run was part of are of no further use
-                    for key in [k for k in batches if sl.req.rid in k]:
-                        batches.pop(key).close()
                     sl.ch.close()
                     used -= sl.fp
                     done[sl.req.rid] = dict(t_admit=sl.t_admit, t_done=self.clock() - t0,
