@@ -39,6 +39,12 @@ template <typename T, int MODE, int CAT>
 __global__ void __launch_bounds__(CAT == 3 ? 256 : 512) k_xpass(XArgs A, const typename V2<T>::t* __restrict__ tw) {
   xpass_body<T, MODE, CAT>(A, tw, blockIdx.x, blockIdx.y);
 }
+// The same for CTAs of at most 128 threads, with registers held to what six CTAs per SM allow
+// (the FP32 register transforms otherwise take 86, five CTAs)
+template <typename T, int MODE, int CAT>
+__global__ void __launch_bounds__(128, 6) k_xpass128(XArgs A, const typename V2<T>::t* __restrict__ tw) {
+  xpass_body<T, MODE, CAT>(A, tw, blockIdx.x, blockIdx.y);
+}
 
 
 
@@ -142,6 +148,10 @@ cudaError_t fft_configure(chan_s*) {
                        (const void*)k_zinv<float, 0>,
                        (const void*)k_zfwd<float, 0>,
                        (const void*)k_xpass<float, 0, 0>,
+                       (const void*)k_xpass128<float, 0, 0>,
+                       (const void*)k_xpass128<float, 0, 1>,
+                       (const void*)k_xpass128<float, 0, 2>,
+                       (const void*)k_xpass128<float, 0, 3>,
                        (const void*)k_xpass<float, 1, 0>,
                        (const void*)k_xpass<float, 2, 0>,
                        (const void*)kb_z<float, true, 0>,
@@ -246,7 +256,8 @@ cudaError_t launch_xpass(chan_s* h, int mode, void* const* in, void* const* out,
     const int c = plan_cat(h->p1);
     const int ntc = c == 3 && nt > 256 ? 256 : nt;   // category-3 instances take at most 256 threads
 #define CHAN_XPASS_CAT(C)                                                       \
-  if (mode == 0) k_xpass<float, 0, C><<<grid, ntc, sm, h->stream>>>(A, tw);     \
+  if (mode == 0 && ntc <= 128) k_xpass128<float, 0, C><<<grid, ntc, sm, h->stream>>>(A, tw); \
+  else if (mode == 0) k_xpass<float, 0, C><<<grid, ntc, sm, h->stream>>>(A, tw); \
   else if (mode == 1) k_xpass<float, 1, C><<<grid, ntc, sm, h->stream>>>(A, tw); \
   else k_xpass<float, 2, C><<<grid, ntc, sm, h->stream>>>(A, tw);
     switch (c) {
