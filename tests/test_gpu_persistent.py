@@ -116,3 +116,34 @@ def test_runs_of_one_launch_advance_by_their_own_counts(prec):
         for k in ("v", "omega2", "U1", "U3"):
             assert np.array_equal(ga[k], gp[k]), (prec, ks, k)
         assert p.substeps() == sum(ks) and a.time() == p.time()
+
+
+def test_persistent_batches_refuse_what_they_cannot_hold():
+    import ctypes
+    import paper_1808_06461_b300 as chan
+    lib = chan.library()
+    runs = [_make(chan, 32, 17, 32, 180.0, 0) for _ in range(17)]
+    arr = (ctypes.c_void_p * 17)(*[c.h.value for c in runs])
+    b = ctypes.c_void_p()
+    # more than 16 runs in one persistent launch
+    assert lib.chan_batch_create_ex(ctypes.byref(b), arr, 17, None, chan.CHAN_BATCH_PERSISTENT) == chan.CHAN_EINVAL
+    assert not b.value
+    # an unknown flag
+    assert lib.chan_batch_create_ex(ctypes.byref(b), arr, 2, None, 2) == chan.CHAN_EINVAL
+    # per-run counts and wait limits are checked
+    pb = chan.ChannelBatch(runs[:2], persistent=True)
+    with pytest.raises(chan.ChanError):
+        pb.step_each([3, -1])
+    with pytest.raises(chan.ChanError):
+        pb.set_wait(0)
+    pb.close()
+    # the per-kernel batch has no persistent controls
+    kb = chan.ChannelBatch(runs[:2])
+    with pytest.raises(chan.ChanError):
+        kb.step_each([3, 3])
+    with pytest.raises(chan.ChanError):
+        kb.set_wait(100)
+    kb.status()
+    kb.close()
+    for c in runs:
+        c.close()
