@@ -45,8 +45,8 @@ CONFIGS = {
     "re1000_768x385x768": dict(re=1000.0, Lx=2 * math.pi, Lz=math.pi, Nx=768, Ny=385, Nz=768, dt=1e-4,
                                sub_per_step=50, filt=(0, 120.0, 60.0)),
     # relaxed-resolution Re 2000 box, mixed precision only (3Nx/2 = 2304 exceeds the FP64
-    # in-CTA transform); box filter of width 100 wall units every 20 substeps; about 236 GB
-    # on the device (slabbed transforms, per-substep implicit tables)
+    # in-CTA transform); box filter of width 100 wall units every 20 substeps; about 147 GB
+    # on the device (slabbed transforms, per-substep implicit tables in the work fields)
     "re2000_1536x633x1152": dict(re=2000.0, Lx=2 * math.pi, Lz=math.pi, Nx=1536, Ny=633, Nz=1152, dt=5e-5,
                                  sub_per_step=20, filt=(1, 100.0, 100.0)),
 }

@@ -87,9 +87,14 @@ typedef struct chan_opts {
                         products and nine outputs stay within 4 GiB                    */
   int lean_tables;   /* 1: keep the implicit-step LU factors and homogeneous solutions of
                         one RK3 substep only and recompute them at each substep (a third
-                        of the table memory, more FP64 work); -1: keep all three; 0: lean
-                        only when the box would otherwise need more than 200 GB.  Results
-                        do not depend on it                                              */
+                        of the table memory, more FP64 work); 2: as 1, and those tables
+                        and the Poisson factors occupy no memory of their own: each
+                        substep computes them into work fields that are dead from the
+                        non-linear terms to the Poisson step (the filtered pressure then
+                        allocates its own Poisson factors on its first call); in the
+                        pair-stored precisions 2 acts as 1; -1: keep all three; 0: 1 when
+                        the box would otherwise need more than 200 GB, and 2 when it would
+                        still need more than 150 GB.  Results do not depend on it        */
   int y_tables;      /* where the wall-normal sweeps read their mode-independent tables:
                         1 in place from global memory, 2 staged in shared memory, 0 staged
                         unless that needs more than 16 KB per CTA (chan_autotune may

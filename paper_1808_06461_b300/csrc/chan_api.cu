@@ -204,17 +204,23 @@ void run_nonlinear(chan_s* h) {
 
 void run_substep(chan_s* h) {
   const int s = (int)(h->nsub % 3);
-  if (h->lean) { Traced t(h, KID_TABLES); CK(launch_setup_substep(h, s)); }
+  if (h->lean == 1) { Traced t(h, KID_TABLES); CK(launch_setup_substep(h, s)); }
   run_pre(h, true);
   run_nonlinear(h);
   // The mean-flow solve (one CTA) needs only the (0,0) modes of H and the mean profiles,
   // which the wall-normal sweeps neither read nor write: it runs on the side stream beside
-  // them, and the next substep waits for it.
+  // them, and the next substep waits for it.  With the tables in the work slots it reads
+  // copies of the (0,0) modes, since the table set-up below overwrites H.
+  if (h->lean == 2) { Traced t(h, KID_TABLES); CK(launch_copy_mean_modes(h, wf(h, WF_H1), wf(h, WF_H3))); }
   CK(cudaEventRecord(h->ev_fork, h->stream));
   CK(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
   { Traced t(h, KID_MEAN, h->side); CK(launch_mean(h, wf(h, WF_H1), wf(h, WF_H3), s, h->side)); }
   CK(cudaEventRecord(h->ev_join, h->side));
   { Traced t(h, KID_NONLIN); CK(launch_nonlin(h, wf(h, WF_H1), wf(h, WF_H2), wf(h, WF_H3), wf(h, WF_NCHI), wf(h, WF_NOM))); }
+  if (h->lean == 2) {   // omega_1 .. H_3 are dead until the next substep: the tables go there
+    { Traced t(h, KID_TABLES); CK(launch_setup_pois(h, h->pois)); }
+    { Traced t(h, KID_TABLES); CK(launch_setup_substep(h, s)); }
+  }
   { Traced t(h, KID_HELM); CK(launch_helm(h, wf(h, WF_NCHI), wf(h, WF_NOM), s)); }
   { Traced t(h, KID_POISSON); CK(launch_poisson(h, s)); }
   CK(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
@@ -257,13 +263,15 @@ void set_filter(chan_s* h, int kind, double p1, double p3) {
 size_t footprint_ex(int Nx, int Ny, int Nz, int prec, int slab_req, int lean, int keep) {
   const size_t nxh = Nx / 2, M = (size_t)Nz * nxh, C = (size_t)(Nz / 2) * nxh, n = (size_t)Ny * M;
   const size_t nslot = lean ? 1 : 3;
+  const size_t ntab = lean == 2 ? 0 : (size_t)Ny * 7 * C + nslot * (size_t)Ny * 11 * C;   // lean 2: in the work slots
   const size_t L1 = 3 * (size_t)Nx / 2, L3 = 3 * (size_t)Nz / 2;
   const size_t es = prec_t32(prec) ? sizeof(float2) : sizeof(double2);
   size_t b = 0;
   b += (keep ? 8 : 6) * n * sizeof(double2) + 4 * Ny * sizeof(double) + 3 * sizeof(double);   // state
   b += 5 * 7 * (size_t)Ny * sizeof(double) + 3 * (size_t)Ny * sizeof(double);              // y tables
   b += (nxh + Nz) * sizeof(double);                                                          // wavenumbers
-  b += ((size_t)Ny * 7 * C + nslot * (size_t)Ny * 11 * C + nslot * 4 * C + 3 * ((size_t)Ny + 1)) * sizeof(double);
+  b += (ntab + nslot * 4 * C + 3 * ((size_t)Ny + 1)) * sizeof(double);
+  if (lean == 2) b += 3 * 11 * (size_t)Ny * sizeof(double) + 2 * (size_t)Ny * sizeof(double2);   // mean_tab, h00
   if (prec_pairs(prec))
     b += ((size_t)Ny * 7 * C + nslot * (size_t)Ny * 11 * C + nslot * 4 * C + 30 * (size_t)Ny) * sizeof(dfr);
   b += (L1 + L3) * (prec_t32(prec) ? sizeof(float2) : sizeof(double2));             // twiddles
@@ -281,10 +289,16 @@ size_t footprint_ex(int Nx, int Ny, int Nz, int prec, int slab_req, int lean, in
   return b;
 }
 
-// Lean tables when asked, or automatically when the box would pass 200 GB with all three.
+// Table placement (see chan_s::lean): as asked, or automatically: one substep's tables when
+// the box would pass 200 GB with all three, and those in the work slots when it would still
+// pass 150 GB without the kept right-hand sides.  The pair modes keep pair copies of the
+// tables beside the FP64 ones, which the work slots cannot hold: level 2 is level 1 there.
 int lean_tables(int Nx, int Ny, int Nz, int prec, int slab_req, int req) {
-  if (req != 0) return req > 0;
-  return footprint_ex(Nx, Ny, Nz, prec, slab_req, 0, 1) > (size_t)200e9;
+  if (req < 0) return 0;
+  if (req > 0) return req == 2 && !prec_pairs(prec) ? 2 : 1;
+  if (footprint_ex(Nx, Ny, Nz, prec, slab_req, 0, 1) <= (size_t)200e9) return 0;
+  if (prec_pairs(prec) || footprint_ex(Nx, Ny, Nz, prec, slab_req, 1, 0) <= (size_t)150e9) return 1;
+  return 2;
 }
 
 // Kept Helmholtz right-hand sides unless asked not to, or automatically when the box would
@@ -576,8 +590,13 @@ int chan_init_ex(chan_t* out, const chan_opts* o) {
       h->Rom = dalloc<double2>(h, n);
       h->Rchi = dalloc<double2>(h, n);
     }
-    h->pois = dalloc<double>(h, Ny * 7 * (size_t)h->C);
-    h->helm = dalloc<double>(h, nslot * Ny * 11 * (size_t)h->C);
+    if (h->lean != 2) {   // lean 2: pois and helm point into the work slots (below)
+      h->pois = dalloc<double>(h, Ny * 7 * (size_t)h->C);
+      h->helm = dalloc<double>(h, nslot * Ny * 11 * (size_t)h->C);
+    } else {
+      h->mean_tab = dalloc<double>(h, 3 * 11 * (size_t)Ny);
+      h->h00 = dalloc<double2>(h, 2 * (size_t)Ny);
+    }
     h->infl = dalloc<double>(h, nslot * 4 * (size_t)h->C);
     h->meanh = dalloc<double>(h, 3 * (Ny + 1));
     if (prec_pairs(h->prec)) {
@@ -659,6 +678,14 @@ int chan_init_ex(chan_t* out, const chan_opts* o) {
     h->pbb = dalloc<double2>(h, 6 * (size_t)h->fslab * h->M);
     h->fout = dalloc<double2>(h, 9 * (size_t)h->fslab * h->M);
     h->scr = wf(h, WF_U1);   // [2][Ny][M]: the u_1, u_3 slots
+    if (h->lean == 2) {
+      // Poisson factors, then one substep's Helmholtz tables (256-byte aligned), in the slots
+      // omega_1 .. H_3 (2..6): 18 Ny C doubles = 9 Ny M of the 10 Ny M those five slots hold
+      const size_t np = ((Ny * 7 * (size_t)h->C + 31) / 32) * 32;
+      h->pois = reinterpret_cast<double*>(wf(h, WF_OM1));
+      h->helm = h->pois + np;
+      if (np + Ny * 11 * (size_t)h->C > 5 * 2 * n) { h->err = "chan_init: tables do not fit the work slots"; throw Fail{CHAN_EINVAL}; }
+    }
     h->stat = dalloc<double>(h, CHAN_NSTAT * Ny + 2);
     CK(fft_configure(h));
     CK(launch_setup_tables(h));
@@ -1013,6 +1040,10 @@ int chan_filtered_pressure(chan_t h, int kind, double p1, double p3, double* pr)
   if (rc != CHAN_OK) return rc;
   try {
     if (!h->prs) {
+      if (h->lean == 2) {   // the substep's Poisson factors live in the slots that now hold P
+        h->pois_prs = dalloc<double>(h, (size_t)h->Ny * 7 * h->C);
+        CK(launch_setup_pois(h, h->pois_prs));
+      }
       h->prs = dalloc<double>(h, (size_t)h->Ny * 2 * h->C);
       h->prsinv = dalloc<double>(h, 4 * (size_t)h->C);
       CK(launch_setup_pressure(h));

@@ -102,8 +102,14 @@ struct chan_s {
   double* helm;            // [3][Ny][11][C], or [1][Ny][11][C] refilled per substep (lean)
   double* pois;            // [Ny][7][C]
   double* infl;            // [3][4][C] (lean: [1][4][C])
-  int lean;                // per-substep Helmholtz tables (one slot, refilled each substep)
+  int lean;                // 0: Helmholtz tables of all three substeps; 1: one slot, refilled each substep;
+                           // 2: one slot and the Poisson factors, both in the work slots 2..6 (dead from the
+                           // non-linear terms to the Poisson step) and both recomputed in every substep
   int lean_slot;           // the substep whose tables the slot holds
+  double* mean_tab;        // lean 2: the (0,0) class of each substep's Helmholtz tables [3][Ny][11], read by
+                           // the mean-flow solve, which runs beside the table set-up
+  double2* h00;            // lean 2: the (0,0) modes of H_1, H_3 of the current substep [2][Ny]
+  double* pois_prs;        // lean 2: Poisson factors of the filtered pressure (allocated on its first call)
   dfr *helm_df, *pois_df, *infl_df;   // pair copies for the double-float y-kernels (that mode only)
   double* meanh;           // [3][Ny+1]: U_h of each substep and its flux
   void *tw1, *tw3;         // twiddles of L1, L3 in the FFT precision
@@ -159,6 +165,10 @@ struct BatchWork {
 cudaError_t launch_setup_tables(chan_s* h);
 // Lean tables: refill the single Helmholtz slot for substep s (no-op otherwise).
 cudaError_t launch_setup_substep(chan_s* h, int s);
+// Poisson factors [Ny][7][C] into dst (lean 2: h->pois each substep, or the filtered pressure's own).
+cudaError_t launch_setup_pois(chan_s* h, double* dst);
+// Lean 2: the (0,0) modes of H1, H3 into h->h00, for the mean-flow solve.
+cudaError_t launch_copy_mean_modes(chan_s* h, const double2* H1, const double2* H3);
 cudaError_t launch_derive(chan_s* h);
 // f32: the mixed mode's substep variant (float2 transform inputs, see substep_inputs).
 cudaError_t launch_pre(chan_s* h, double2* u1, double2* u3, double2* om1, double2* om3, bool f32 = false);

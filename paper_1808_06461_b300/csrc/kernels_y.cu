@@ -69,6 +69,21 @@ __global__ void __launch_bounds__(256) k_mean(Geo g, YTabs t, const double* __re
                                               const double2* __restrict__ H3, double* U1, double* U3, double* H1p,
                                               double* H3p, double* scal, int s) { mean_body(g, t, helm, meanh, H1, H3, U1, U3, H1p, H3p, scal, s, blockIdx.x); }
 
+// Tables in the work slots: the mean-flow solve runs beside the kernels that overwrite
+// those slots, so it reads compact copies of what it needs from them.
+// dst[i] = src[i * stride], i < n (the (0,0) class of a Helmholtz table slot).
+__global__ void k_gather_class0(const double* __restrict__ src, size_t stride, int n, double* dst) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dst[i] = src[(size_t)i * stride];
+}
+// dst[y] = H1[y M], dst[Ny + y] = H3[y M]: the (0,0) modes of H_1, H_3 on every plane.
+__global__ void k_copy_mean_modes(const double2* __restrict__ H1, const double2* __restrict__ H3, size_t M, int Ny,
+                                  double2* dst) {
+  for (int i = threadIdx.x; i < Ny; i += blockDim.x) {
+    dst[i] = H1[(size_t)i * M];
+    dst[Ny + i] = H3[(size_t)i * M];
+  }
+}
+
 
 // U_h(s) = (A - b_s dt nu B)^-1 A 1 with zero wall values, and its trapezoid flux, from the
 // substep's Helmholtz factors (helm at its slot) into out[Ny + 1].
@@ -548,9 +563,22 @@ cudaError_t launch_setup_tables(chan_s* h) {
     for (int s = 0; s < 3; ++s) {
       if ((e = setup_helm_slots(h, s, 1)) != cudaSuccess) return e;
       k_setup_mean<<<1, 32, 0, h->stream>>>(g, t, h->helm, h->meanh + (size_t)s * (h->Ny + 1));
+      if (h->lean == 2)
+        k_gather_class0<<<(11 * h->Ny + 255) / 256, 256, 0, h->stream>>>(h->helm, (size_t)h->C, 11 * h->Ny,
+                                                                           h->mean_tab + (size_t)s * 11 * h->Ny);
     }
     h->lean_slot = 2;
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_setup_pois(chan_s* h, double* dst) {
+  k_setup_pois<<<(h->C + 127) / 128, 128, 0, h->stream>>>(geo(h), ytabs(h), dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy_mean_modes(chan_s* h, const double2* H1, const double2* H3) {
+  k_copy_mean_modes<<<1, 256, 0, h->stream>>>(H1, H3, (size_t)h->M, h->Ny, h->h00);
   return cudaGetLastError();
 }
 
@@ -648,7 +676,16 @@ cudaError_t launch_mean(chan_s* h, const double2* H1, const double2* H3, int s, 
   size_t sm = sizeof(double) * (9 * h->Ny + 256);
   cudaError_t e = smem_attr((const void*)k_mean, sm);
   if (e != cudaSuccess) return e;
-  k_mean<<<1, 256, sm, st ? st : h->stream>>>(geo(h), ytabs(h), helm_slot(h, s), h->meanh, H1, H3, h->U1, h->U3, h->H1m_p,
+  Geo g = geo(h);
+  const double* helm = helm_slot(h, s);
+  if (h->lean == 2) {   // the compact copies: one class, one mode per plane
+    g.M = 1;
+    g.C = 1;
+    helm = h->mean_tab + (size_t)s * 11 * h->Ny;
+    H1 = h->h00;
+    H3 = h->h00 + h->Ny;
+  }
+  k_mean<<<1, 256, sm, st ? st : h->stream>>>(g, ytabs(h), helm, h->meanh, H1, H3, h->U1, h->U3, h->H1m_p,
                                     h->H3m_p, h->scal, s);
   return cudaGetLastError();
 }
@@ -767,13 +804,14 @@ cudaError_t launch_pressure(chan_s* h, const double2* const* P, double2* out) {
   size_t sm = sizeof(double) * 28 * h->Ny;
   cudaError_t e = smem_attr((const void*)k_pressure, sm);
   if (e != cudaSuccess) return e;
-  k_pressure<<<ygrid(h), kYThreads, sm, h->stream>>>(geo(h), ytabs(h), h->pois, h->prs, h->prsinv, P[0], P[1], P[2],
+  k_pressure<<<ygrid(h), kYThreads, sm, h->stream>>>(geo(h), ytabs(h), h->pois_prs ? h->pois_prs : h->pois, h->prs, h->prsinv, P[0], P[1], P[2],
                                                      P[3], P[4], P[5], h->G, h->chi, out, h->scr);
   return cudaGetLastError();
 }
 
 cudaError_t launch_setup_pressure(chan_s* h) {
-  k_setup_pressure<<<(h->C + 127) / 128, 128, 0, h->stream>>>(geo(h), ytabs(h), h->pois, h->prs, h->prsinv);
+  k_setup_pressure<<<(h->C + 127) / 128, 128, 0, h->stream>>>(geo(h), ytabs(h), h->pois_prs ? h->pois_prs : h->pois,
+                                                               h->prs, h->prsinv);
   return cudaGetLastError();
 }
 

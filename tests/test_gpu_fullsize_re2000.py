@@ -1,7 +1,9 @@
 """The Re_tau = 2000 relaxed-resolution workload (Lx = 2 pi, Lz = pi, 1536 x 633 x
-1152, dt = 5e-5) in mixed precision, the mode it is run in: about 187 GB on the
-device, with the transforms in slabs, the implicit-step tables recomputed each
-substep and no kept Helmholtz right-hand sides.
+1152, dt = 5e-5) in mixed precision, the mode it is run in: about 147 GB on the
+device, with the transforms in slabs, no kept Helmholtz right-hand sides, and the
+implicit-step tables and Poisson factors recomputed each substep into work fields
+that are dead from the non-linear terms to the Poisson step (all chosen
+automatically for a box of this size).
 
 The oracle computes the dealiased non-linear term on sampled x-z planes
 (padded 2304 x 1728 transforms); the velocities it needs come from the
@@ -83,7 +85,7 @@ def test_re2000_mixed_nonlinear_sampled_planes_and_invariants(ref):
     st, s0, Href = ref
     ch = chan.Channel(*CFG, precision=chan.CHAN_PREC_MIXED, stream=torch.cuda.current_stream().cuda_stream)
     try:
-        assert ch.device_bytes() < 190e9
+        assert ch.device_bytes() < 150e9
         ch.set_state(s0["v"], s0["omega2"], s0["U1"], s0["U3"])
         H = ch.nonlinear()
         for f in range(3):
