@@ -745,6 +745,16 @@ struct ZArgs {
   FftPlan pl;
 };
 
+// FP32 column elements copied global -> shared without a register round trip (cp.async,
+// 8 bytes each, zero-filled when !valid): all of a thread's copies of a column chunk are in
+// flight at once.  The thread waits for its own copies (zc_wait) before the block barrier.
+__device__ __forceinline__ void zc8(void* s, const void* g, bool valid = true) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"((unsigned)__cvta_generic_to_shared(s)), "l"(g),
+               "r"(valid ? 8 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void zc_wait() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // Inverse z-pass: Fourier [Ny][Nz][nxh] (double) -> mixed [Ny][L3][nxh] (T),
 // kz zero-padded to 3Nz/2 (the kz Nyquist row is dropped), optional filter
 // transfer G applied on load.
@@ -759,7 +769,7 @@ __device__ __forceinline__ void zinv_load(const ZArgs& A, T2* a, const double2* 
     const int q = jz * A.nxh + kx;
     const int pz = jz < hz ? jz : jz + (A.L3 - A.Nz);
     if constexpr (KIND == 2) {
-      if constexpr (std::is_same<T2, float2>::value) a[kl * A.ld + slot<T2>(pz, A.pl)] = in32[q];
+      if constexpr (std::is_same<T2, float2>::value) zc8(&a[kl * A.ld + slot<T2>(pz, A.pl)], &in32[q]);
     } else if constexpr (KIND >= 3) {
       if constexpr (std::is_same<T2, float2>::value)
         a[kl * A.ld + slot<T2>(pz, A.pl)] = ld_pair_f32(in, q, KIND == 4, KIND == 4 ? A.G[q] : 0.0);
@@ -791,6 +801,7 @@ __device__ __forceinline__ void zinv_body(const ZArgs& A, const typename V2<T>::
     else zinv_load<T2, 3>(A, a, in, in32, kx0, hz);
   } else if (A.applyG[f]) zinv_load<T2, 1>(A, a, in, in32, kx0, hz);
   else zinv_load<T2, 0>(A, a, in, in32, kx0, hz);
+  if constexpr (std::is_same<T2, float2>::value) zc_wait();
   // the (0,0) mode is element 0 of the first column chunk, loaded by thread 0 above
   if (A.skip00 && bx == 0 && threadIdx.x == 0) a[slot<T2>(0, A.pl)] = zero2<T2>();
   const float2* ts = stage_tw2p<T2>(a + A.KB * A.ld, A.pl);
@@ -831,8 +842,12 @@ __device__ __forceinline__ void zfwd_body(const ZArgs& A, const typename V2<T>::
   const T2* in = reinterpret_cast<const T2*>(A.out[f]) + (size_t)y * A.L3 * A.nxh;
   for (int e = threadIdx.x; e < A.L3 * A.KB; e += blockDim.x) {
     const int z = e >> A.lgKB, kl = e & (A.KB - 1), kx = kx0 + kl;
-    a[kl * A.ld + slot<T2>(z, A.pl)] = kx < A.nxh ? in[z * A.nxh + kx] : zero2<T2>();
+    if constexpr (std::is_same<T2, float2>::value)
+      zc8(&a[kl * A.ld + slot<T2>(z, A.pl)], &in[z * A.nxh + (kx < A.nxh ? kx : 0)], kx < A.nxh);
+    else
+      a[kl * A.ld + slot<T2>(z, A.pl)] = kx < A.nxh ? in[z * A.nxh + kx] : zero2<T2>();
   }
+  if constexpr (std::is_same<T2, float2>::value) zc_wait();
   const float2* ts = stage_tw2p<T2>(a + A.KB * A.ld, A.pl);
   __syncthreads();
   // digit-reversed rows in, natural kz out; the middle third (truncated) is not formed
