@@ -763,6 +763,32 @@ __device__ __forceinline__ void zc_wait() { asm volatile("cp.async.wait_all;\n" 
 // 3, 4: stored as pairs, FP32 transforms (as 0, 1).
 template <typename T2, int KIND>
 __device__ __forceinline__ void zinv_load(const ZArgs& A, T2* a, const double2* in, const float2* in32, int kx0, int hz) {
+  if constexpr (std::is_same<T2, float2>::value && KIND != 2) {
+    // FP32 transforms of FP64 or pair-stored fields: the rounding to FP32 needs the value in
+    // registers, so ZB elements' loads are issued before any is converted and stored
+    constexpr int ZB = 4;
+    for (int e0 = threadIdx.x; e0 < A.Nz * A.KB; e0 += ZB * blockDim.x) {
+      float2 v[ZB];
+      int dst[ZB];
+#pragma unroll
+      for (int b = 0; b < ZB; ++b) {
+        const int e = e0 + b * blockDim.x;
+        dst[b] = -1;
+        if (e >= A.Nz * A.KB) continue;
+        const int jz = e >> A.lgKB, kl = e & (A.KB - 1), kx = kx0 + kl;
+        if (kx >= A.nxh || jz == hz) continue;
+        const int q = jz * A.nxh + kx;
+        const int pz = jz < hz ? jz : jz + (A.L3 - A.Nz);
+        if constexpr (KIND >= 3) v[b] = ld_pair_f32(in, q, KIND == 4, KIND == 4 ? A.G[q] : 0.0);
+        else v[b] = ld_fourier<T2>(in, q, KIND == 1, KIND == 1 ? A.G[q] : 0.0);
+        dst[b] = kl * A.ld + slot<T2>(pz, A.pl);
+      }
+#pragma unroll
+      for (int b = 0; b < ZB; ++b)
+        if (dst[b] >= 0) a[dst[b]] = v[b];
+    }
+    return;
+  }
   for (int e = threadIdx.x; e < A.Nz * A.KB; e += blockDim.x) {
     const int jz = e >> A.lgKB, kl = e & (A.KB - 1), kx = kx0 + kl;
     if (kx >= A.nxh || jz == hz) continue;
@@ -884,10 +910,7 @@ __device__ __forceinline__ void xpass_body(const XArgs& A, const typename V2<T>:
   // other slot except the dropped kx Nyquist slot 2 nxh: only that one is zeroed.
   for (int f = threadIdx.x; f < NIN; f += blockDim.x) a[f * ld + slot<T2>(2 * nxh, A.pl)] = zero2<T2>();
   // pack rows z0 (real part) and z0+1 (imaginary part) with Hermitian extension in kx
-  for (int e = threadIdx.x; e < NIN * nxh; e += blockDim.x) {
-    const int f = A.mag_nxh ? (int)__umulhi((unsigned)e, A.mag_nxh) : e, k = e - f * nxh;   // e / nxh
-    const T2* row = reinterpret_cast<const T2*>(A.in[f]) + rowoff;
-    T2 P = row[k], Q = row[nxh + k];
+  auto pack = [&](int f, int k, T2 P, T2 Q) {
     T2* dstf = a + f * ld;
     if (k == 0) {
       T2 c0;
@@ -900,6 +923,38 @@ __device__ __forceinline__ void xpass_body(const XArgs& A, const typename V2<T>:
       c2.x = P.x + Q.y; c2.y = -P.y + Q.x;     // conj(P_k) + i conj(Q_k) at -k
       dstf[slot<T2>(k, A.pl)] = c1;
       dstf[slot<T2>(L1 - k, A.pl)] = c2;
+    }
+  };
+  if constexpr (std::is_same<T2, float2>::value) {
+    // FP32 (bound by waiting on these loads): XB elements' loads issued before any is packed
+    constexpr int XB = 4;
+    for (int e0 = threadIdx.x; e0 < NIN * nxh; e0 += XB * blockDim.x) {
+      T2 P[XB], Q[XB];
+      int fk[XB];
+#pragma unroll
+      for (int b = 0; b < XB; ++b) {
+        const int e = e0 + b * blockDim.x;
+        fk[b] = -1;
+        if (e < NIN * nxh) {
+          const int f = A.mag_nxh ? (int)__umulhi((unsigned)e, A.mag_nxh) : e, k = e - f * nxh;   // e / nxh
+          const T2* row = reinterpret_cast<const T2*>(A.in[f]) + rowoff;
+          P[b] = row[k];
+          Q[b] = row[nxh + k];
+          fk[b] = f * nxh + k;
+        }
+      }
+#pragma unroll
+      for (int b = 0; b < XB; ++b)
+        if (fk[b] >= 0) {
+          const int f = A.mag_nxh ? (int)__umulhi((unsigned)fk[b], A.mag_nxh) : fk[b];
+          pack(f, fk[b] - f * nxh, P[b], Q[b]);
+        }
+    }
+  } else {
+    for (int e = threadIdx.x; e < NIN * nxh; e += blockDim.x) {
+      const int f = A.mag_nxh ? (int)__umulhi((unsigned)e, A.mag_nxh) : e, k = e - f * nxh;   // e / nxh
+      const T2* row = reinterpret_cast<const T2*>(A.in[f]) + rowoff;
+      pack(f, k, row[k], row[nxh + k]);
     }
   }
   const float2* ts = stage_tw2p<T2>(a + 6 * ld, A.pl);
