@@ -302,7 +302,7 @@ int chan_nonlinear(chan_t h, double* H);
  * since the last reset (launches are counted even when timing is off).
  * chan_kernel_name(k) names kernel k (NULL when out of range).
  */
-#define CHAN_NKERNELS 16
+#define CHAN_NKERNELS 18
 int chan_profile(chan_t h, int enable);
 int chan_profile_read(chan_t h, double* ms, long long* launches);
 const char* chan_kernel_name(int k);

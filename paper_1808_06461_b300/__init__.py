@@ -36,7 +36,7 @@ SYMBOLS = ("chan_opts_default", "chan_init", "chan_init_ex", "chan_free", "chan_
            "chan_spectra", "chan_optimize_mesh", "chan_filtered_pressure", "chan_checkpoint_bytes",
            "chan_checkpoint_save", "chan_checkpoint_load", "chan_batch_create_ex", "chan_batch_status",
            "chan_batch_set_wait", "chan_batch_persistent_grid", "chan_batch_step_each")
-CHAN_NKERNELS = 16
+CHAN_NKERNELS = 18
 
 
 class chan_opts(ctypes.Structure):

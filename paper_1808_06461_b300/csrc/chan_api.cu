@@ -75,7 +75,8 @@ size_t fsize(const chan_s* h) { return (size_t)h->Ny * h->M; }
 const char* const kKernelNames[KID_COUNT] = {"k_pre",     "k_zinv",       "k_xpass", "k_zfwd",
                                              "k_nonlin",  "k_helm",       "k_poisson", "k_mean",
                                              "k_filter_out", "k_stats",   "k_derive", "k_apply_G",
-                                             "k_gather_retained", "k_spectra", "k_pressure", "k_setup_helm"};
+                                             "k_gather_retained", "k_spectra", "k_pressure", "k_setup_helm",
+                                             "k_setup_pois", "k_copy_mean_modes"};
 
 // Launch bracket: counts the launch and, when tracing, records an event pair.
 struct Traced {
@@ -211,14 +212,14 @@ void run_substep(chan_s* h) {
   // which the wall-normal sweeps neither read nor write: it runs on the side stream beside
   // them, and the next substep waits for it.  With the tables in the work slots it reads
   // copies of the (0,0) modes, since the table set-up below overwrites H.
-  if (h->lean == 2) { Traced t(h, KID_TABLES); CK(launch_copy_mean_modes(h, wf(h, WF_H1), wf(h, WF_H3))); }
+  if (h->lean == 2) { Traced t(h, KID_COPY_MEAN); CK(launch_copy_mean_modes(h, wf(h, WF_H1), wf(h, WF_H3))); }
   CK(cudaEventRecord(h->ev_fork, h->stream));
   CK(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
   { Traced t(h, KID_MEAN, h->side); CK(launch_mean(h, wf(h, WF_H1), wf(h, WF_H3), s, h->side)); }
   CK(cudaEventRecord(h->ev_join, h->side));
   { Traced t(h, KID_NONLIN); CK(launch_nonlin(h, wf(h, WF_H1), wf(h, WF_H2), wf(h, WF_H3), wf(h, WF_NCHI), wf(h, WF_NOM))); }
   if (h->lean == 2) {   // omega_1 .. H_3 are dead until the next substep: the tables go there
-    { Traced t(h, KID_TABLES); CK(launch_setup_pois(h, h->pois)); }
+    { Traced t(h, KID_SETUP_POIS); CK(launch_setup_pois(h, h->pois)); }
     { Traced t(h, KID_TABLES); CK(launch_setup_substep(h, s)); }
   }
   { Traced t(h, KID_HELM); CK(launch_helm(h, wf(h, WF_NCHI), wf(h, WF_NOM), s)); }

@@ -71,7 +71,8 @@ struct FftPlan {
 
 enum { KID_PRE = 0, KID_ZINV, KID_XPASS, KID_ZFWD, KID_NONLIN, KID_HELM, KID_POISSON, KID_MEAN,
        KID_FILTER_OUT, KID_STATS, KID_DERIVE, KID_APPLY_G, KID_GATHER, KID_SPECTRA, KID_PRESSURE, KID_TABLES,
-       KID_COUNT };
+       KID_SETUP_POIS, KID_COPY_MEAN, KID_COUNT };
+static_assert(KID_COUNT == CHAN_NKERNELS, "every traced kernel id has a name in the ABI's count");
 
 struct ProfRec {
   int k;
