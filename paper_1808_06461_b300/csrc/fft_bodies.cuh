@@ -410,42 +410,103 @@ template <int DIR, bool NOMID, typename T2> __device__ __forceinline__ void ct3(
 // forward (twiddle of butterfly j is w_Ls^(DIR j)).  Z = 1: the middle input is zero
 // (first inverse stage of a padded transform); Z = 2: the middle output is dropped
 // (last forward stage before the truncation).  TW = false: every twiddle is 1.
-template <int R, int DIR, int Z, bool TW, bool NR, typename T2>
+// G (divides nb): a thread takes butterfly u of G rows (cg, cg + nb/G, ...), so its
+// indices, swizzled slots and twiddles are formed once for the G of them; each butterfly's
+// arithmetic is the same whatever G.
+template <int R, int DIR, int Z, bool TW, bool NR, int G, typename T2>
 __device__ __forceinline__ void ct_loop(T2* a, int L, int nb, int ld, const T2* CHAN_RO tw, int Ls,
                                         unsigned mag_nbf, unsigned mag_m, const FftPlan& pl, int s) {
   const int m = Ls / R;
   const int nbf = L / R;
   const int tmul = L / Ls;
-  const int total = nb * nbf;
+  const int ng = G == 1 ? nb : nb / G;
+  const int total = ng * nbf;
   for (int t = threadIdx.x; t < total; t += blockDim.x) {
-    const int bi = mag_nbf ? (int)__umulhi((unsigned)t, mag_nbf) : t;   // t / nbf (exact while t nbf < 2^32)
-    const int u = t - bi * nbf;
+    const int cg = mag_nbf ? (int)__umulhi((unsigned)t, mag_nbf) : t;   // t / nbf (exact while t nbf < 2^32)
+    const int u = t - cg * nbf;
     const int blk = mag_m ? (int)__umulhi((unsigned)u, mag_m) : u;      // u / m (mag 0: m = 1)
     const int j = u - blk * m;
-    T2* row = a + bi * ld;
     const int ib = blk * Ls + j;
-    T2 v[R];
+    int o[R];
 #pragma unroll
-    for (int q = 0; q < R; ++q) v[q] = (Z == 1 && q == 1) ? zero2<T2>() : row[sw<T2>(ib + q * m)];
+    for (int q = 0; q < R; ++q) o[q] = sw<T2>(ib + q * m);
+    T2 w, w2;
     if (TW) {
       const int e = NR ? pl.revK[pl.revoff[s] + blk] : j * tmul;
-      T2 w = tw[e], w2 = R == 2 ? w : tw[2 * e];
+      w = tw[e];
+      w2 = R == 2 ? w : tw[2 * e];
       if (DIR > 0) { w.y = -w.y; w2.y = -w2.y; }
-      if (R == 4) ct4<DIR>(v, w, w2);
-      else if (R == 2) ct2(v[0], v[1], w);
-      else ct3<DIR, Z == 2>(v, w, w2);
-    } else {
-      if (R == 4) dft4<DIR>(v);
-      else if (R == 2) dft2<DIR>(v);
-      else if (Z == 1) dft3_zmid<DIR>(v);
-      else if (Z == 2) dft3_nomid<DIR>(v);
-      else dft3<DIR>(v);
     }
 #pragma unroll
-    for (int q = 0; q < R; ++q)
-      if (!(Z == 2 && q == 1)) row[sw<T2>(ib + q * m)] = v[q];
+    for (int g = 0; g < G; ++g) {
+      T2* row = a + (cg + g * ng) * ld;
+      T2 v[R];
+#pragma unroll
+      for (int q = 0; q < R; ++q) v[q] = (Z == 1 && q == 1) ? zero2<T2>() : row[o[q]];
+      if (TW) {
+        if (R == 4) ct4<DIR>(v, w, w2);
+        else if (R == 2) ct2(v[0], v[1], w);
+        else ct3<DIR, Z == 2>(v, w, w2);
+      } else {
+        if (R == 4) dft4<DIR>(v);
+        else if (R == 2) dft2<DIR>(v);
+        else if (Z == 1) dft3_zmid<DIR>(v);
+        else if (Z == 2) dft3_nomid<DIR>(v);
+        else dft3<DIR>(v);
+      }
+#pragma unroll
+      for (int q = 0; q < R; ++q)
+        if (!(Z == 2 && q == 1)) row[o[q]] = v[q];
+    }
   }
   __syncthreads();
+}
+
+// The Cooley-Tukey stages of a whole transform, G rows per butterfly item (see ct_loop).
+// Inverse: natural in, digit-reversed out, block size shrinking; the first stage has one
+// block (no twiddles) and, when zmid, a zero middle input.
+template <int DIR, int G, typename T2>
+__device__ __forceinline__ void ct_inv_stages(T2* a, int L, int nb, int ld, const T2* CHAN_RO tw, const FftPlan& pl,
+                                              bool zmid) {
+  int Ls = L;
+  for (int s = 0; s < pl.np; ++s) {
+    const int R = pl.radix[s];
+    const unsigned mn = pl.mag_nbf[s], mm = pl.mag_mdif[s];
+    if (s == 0) {   // one block, K = 0
+      if (R == 4) ct_loop<4, DIR, 0, false, true, G>(a, L, nb, ld, tw, Ls, mn, mm, pl, s);
+      else if (R == 2) ct_loop<2, DIR, 0, false, true, G>(a, L, nb, ld, tw, Ls, mn, mm, pl, s);
+      else if (zmid) ct_loop<3, DIR, 1, false, true, G>(a, L, nb, ld, tw, Ls, mn, mm, pl, s);
+      else ct_loop<3, DIR, 0, false, true, G>(a, L, nb, ld, tw, Ls, mn, mm, pl, s);
+    } else {
+      if (R == 4) ct_loop<4, DIR, 0, true, true, G>(a, L, nb, ld, tw, Ls, mn, mm, pl, s);
+      else if (R == 2) ct_loop<2, DIR, 0, true, true, G>(a, L, nb, ld, tw, Ls, mn, mm, pl, s);
+      else ct_loop<3, DIR, 0, true, true, G>(a, L, nb, ld, tw, Ls, mn, mm, pl, s);
+    }
+    Ls /= R;
+  }
+}
+// Forward: digit-reversed in, natural out, the radices in reverse; when zmid the last
+// stage does not form its middle output.
+template <int DIR, int G, typename T2>
+__device__ __forceinline__ void ct_fwd_stages(T2* a, int L, int nb, int ld, const T2* CHAN_RO tw, const FftPlan& pl,
+                                              bool zmid) {
+  int Ls = 1;
+  for (int s = pl.np - 1; s >= 0; --s) {
+    const int R = pl.radix[s];
+    Ls *= R;
+    const unsigned mn = pl.mag_nbf[s], mm = pl.mag_mdit[s];
+    if (mm == 0) {   // m = 1: every twiddle is 1
+      if (R == 4) ct_loop<4, DIR, 0, false, false, G>(a, L, nb, ld, tw, Ls, mn, mm, pl, s);
+      else if (R == 2) ct_loop<2, DIR, 0, false, false, G>(a, L, nb, ld, tw, Ls, mn, mm, pl, s);
+      else if (s == 0 && zmid) ct_loop<3, DIR, 2, false, false, G>(a, L, nb, ld, tw, Ls, mn, mm, pl, s);
+      else ct_loop<3, DIR, 0, false, false, G>(a, L, nb, ld, tw, Ls, mn, mm, pl, s);
+    } else {
+      if (R == 4) ct_loop<4, DIR, 0, true, false, G>(a, L, nb, ld, tw, Ls, mn, mm, pl, s);
+      else if (R == 2) ct_loop<2, DIR, 0, true, false, G>(a, L, nb, ld, tw, Ls, mn, mm, pl, s);
+      else if (s == 0 && zmid) ct_loop<3, DIR, 2, true, false, G>(a, L, nb, ld, tw, Ls, mn, mm, pl, s);
+      else ct_loop<3, DIR, 0, true, false, G>(a, L, nb, ld, tw, Ls, mn, mm, pl, s);
+    }
+  }
 }
 
 template <typename T2> struct IsPair { static constexpr bool v = false; };
@@ -680,22 +741,12 @@ __device__ void fft_inv(T2* a, int L, int nb, int ld, const T2* CHAN_RO tw, cons
   if constexpr (IsPair<T2>::v) {
     fft_dif<DIR>(a, L, nb, ld, tw, pl, zmid);
   } else {
-    int Ls = L;
-    for (int s = 0; s < pl.np; ++s) {
-      const int R = pl.radix[s];
-      const unsigned mn = pl.mag_nbf[s], mm = pl.mag_mdif[s];
-      if (s == 0) {   // one block, K = 0
-        if (R == 4) ct_loop<4, DIR, 0, false, true>(a, L, nb, ld, tw, Ls, mn, mm, pl, s);
-        else if (R == 2) ct_loop<2, DIR, 0, false, true>(a, L, nb, ld, tw, Ls, mn, mm, pl, s);
-        else if (zmid) ct_loop<3, DIR, 1, false, true>(a, L, nb, ld, tw, Ls, mn, mm, pl, s);
-        else ct_loop<3, DIR, 0, false, true>(a, L, nb, ld, tw, Ls, mn, mm, pl, s);
-      } else {
-        if (R == 4) ct_loop<4, DIR, 0, true, true>(a, L, nb, ld, tw, Ls, mn, mm, pl, s);
-        else if (R == 2) ct_loop<2, DIR, 0, true, true>(a, L, nb, ld, tw, Ls, mn, mm, pl, s);
-        else ct_loop<3, DIR, 0, true, true>(a, L, nb, ld, tw, Ls, mn, mm, pl, s);
-      }
-      Ls /= R;
+    // FP32 rows in even numbers: two rows per butterfly item (ct_loop G); FP64 is bound by
+    // its FP64 arithmetic, not by the index work G shares
+    if constexpr (std::is_same<T2, float2>::value) {
+      if ((nb & 1) == 0) { ct_inv_stages<DIR, 2>(a, L, nb, ld, tw, pl, zmid); return; }
     }
+    ct_inv_stages<DIR, 1>(a, L, nb, ld, tw, pl, zmid);
   }
 }
 
@@ -710,23 +761,10 @@ __device__ void fft_fwd(T2* a, int L, int nb, int ld, const T2* CHAN_RO tw, cons
   if constexpr (IsPair<T2>::v) {
     fft_dit<DIR>(a, L, nb, ld, tw, pl, zmid);
   } else {
-    int Ls = 1;
-    for (int s = pl.np - 1; s >= 0; --s) {
-      const int R = pl.radix[s];
-      Ls *= R;
-      const unsigned mn = pl.mag_nbf[s], mm = pl.mag_mdit[s];
-      if (mm == 0) {   // m = 1: every twiddle is 1
-        if (R == 4) ct_loop<4, DIR, 0, false, false>(a, L, nb, ld, tw, Ls, mn, mm, pl, s);
-        else if (R == 2) ct_loop<2, DIR, 0, false, false>(a, L, nb, ld, tw, Ls, mn, mm, pl, s);
-        else if (s == 0 && zmid) ct_loop<3, DIR, 2, false, false>(a, L, nb, ld, tw, Ls, mn, mm, pl, s);
-        else ct_loop<3, DIR, 0, false, false>(a, L, nb, ld, tw, Ls, mn, mm, pl, s);
-      } else {
-        if (R == 4) ct_loop<4, DIR, 0, true, false>(a, L, nb, ld, tw, Ls, mn, mm, pl, s);
-        else if (R == 2) ct_loop<2, DIR, 0, true, false>(a, L, nb, ld, tw, Ls, mn, mm, pl, s);
-        else if (s == 0 && zmid) ct_loop<3, DIR, 2, true, false>(a, L, nb, ld, tw, Ls, mn, mm, pl, s);
-        else ct_loop<3, DIR, 0, true, false>(a, L, nb, ld, tw, Ls, mn, mm, pl, s);
-      }
+    if constexpr (std::is_same<T2, float2>::value) {
+      if ((nb & 1) == 0) { ct_fwd_stages<DIR, 2>(a, L, nb, ld, tw, pl, zmid); return; }
     }
+    ct_fwd_stages<DIR, 1>(a, L, nb, ld, tw, pl, zmid);
   }
 }
 

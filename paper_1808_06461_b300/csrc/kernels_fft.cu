@@ -20,15 +20,20 @@
 
 namespace {
 
+// The FP32 stage-transform z passes are held to 32 registers (eight CTAs of 256 threads per
+// SM): they issue on most of their cycles, and their column loads want every warp the SM holds.
 template <typename T, int CAT>
-__global__ void __launch_bounds__(256) k_zinv(ZArgs A, const typename V2<T>::t* __restrict__ tw) {
+constexpr int kZMinBlocks = std::is_same<T, float>::value && CAT == 0 ? 6 : 1;
+
+template <typename T, int CAT>
+__global__ void __launch_bounds__(256, kZMinBlocks<T, CAT>) k_zinv(ZArgs A, const typename V2<T>::t* __restrict__ tw) {
   zinv_body<T, CAT>(A, tw, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 
 
 template <typename T, int CAT>
-__global__ void __launch_bounds__(256) k_zfwd(ZArgs A, const typename V2<T>::t* __restrict__ tw) {
+__global__ void __launch_bounds__(256, kZMinBlocks<T, CAT>) k_zfwd(ZArgs A, const typename V2<T>::t* __restrict__ tw) {
   zfwd_body<T, CAT>(A, tw, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
