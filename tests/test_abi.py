@@ -109,3 +109,17 @@ def test_init_rejects_an_unknown_table_placement():
     h = ctypes.c_void_p()
     assert lib.chan_init_ex(ctypes.byref(h), ctypes.byref(o)) == chan.CHAN_EINVAL
     assert "y_tables" in lib.chan_last_error(None).decode()
+
+
+def test_every_traced_kernel_id_has_a_name():
+    """The binding's CHAN_NKERNELS is the header's and the library's: chan_kernel_name names
+    ids 0 .. CHAN_NKERNELS - 1 (distinct names) and no id past them."""
+    lib = chan.library()
+    hdr = open(os.path.join(os.path.dirname(__file__), "..", "include", "chan.h")).read()
+    assert int(re.search(r"#define CHAN_NKERNELS (\d+)", hdr).group(1)) == chan.CHAN_NKERNELS
+    names = [lib.chan_kernel_name(k) for k in range(chan.CHAN_NKERNELS)]
+    assert all(n is not None for n in names)
+    assert len(set(names)) == chan.CHAN_NKERNELS
+    assert lib.chan_kernel_name(chan.CHAN_NKERNELS) is None
+    assert lib.chan_kernel_name(-1) is None
+    assert b"k_setup_pois" in names and b"k_copy_mean_modes" in names
