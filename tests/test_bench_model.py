@@ -86,8 +86,8 @@ def test_xpass_flops_of_the_bench_workload(bench):
 
 def test_step_bytes_match_the_per_point_budget(bench):
     """The byte model per collocation point and substep (pt = Nx Ny Nz, a mode-point is two
-    pts): in FP64 the transform passes move a1 56, a2 120 (six inputs: the survey's 112 counts
-    omega_2's load as part of a1), a3 108 and a4 60 bytes per pt, and the FP32 transforms
+    pts): in FP64 the transform passes move a1 56, a2 120 (six inputs; a budget that counts
+    omega_2's load under a1 gives 112), a3 108 and a4 60 bytes per pt, and the FP32 transforms
     of the mixed modes halve the physical-layout fields."""
     c = dict(Nx=384, Ny=257, Nz=384)
     pts = 384 * 257 * 384
