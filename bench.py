@@ -760,6 +760,7 @@ def run_configs(args, chan, SY, torch, precs, stream):
                 ms = e0.elapsed_time(e1)
                 prof = ch.profile_read()
                 ch.profile(False)
+                dev_bytes = ch.device_bytes()
             finally:
                 ch.close()
             tot = max(1e-9, sum(v[0] for v in prof.values()))
@@ -772,6 +773,7 @@ def run_configs(args, chan, SY, torch, precs, stream):
             alu = step_flops(c, nsub).get(dom, 0.0) * steps / (dms * 1e-3) / 1e12 if dms else 0.0
             res[mode] = {"value": pts * nsub * steps / (ms * 1e-3) / 1e6, "unit": "Mpts*substep/s",
                          "ms_per_step": ms / steps, "substeps_timed": nsub * steps, "launch_shapes": shapes,
+                         "device_bytes": dev_bytes,
                          "kernel_shares": {k: round(v[0] / tot, 4) for k, v in prof.items() if v[1]},
                          "roofline": {"kernel": dom, "bound": "alu", "achieved_tflops": alu,
                                       "peak_tflops": alu_peak, "frac": alu / alu_peak,
