@@ -143,7 +143,8 @@ size_t chan_footprint_bytes(int Nx, int Ny, int Nz, int precision);
 /*
  * Near-wall mesh optimisation of Appendix B.  Starting from the
  * mesh chan_init_ex would build for *o, moves the first 20 interior points at
- * each wall (mirrored) by steepest descent on
+ * each wall (mirrored), every moved cell kept within a factor of two of its
+ * starting size, by steepest descent on
  *   L = |g - g_ana| + C |mu - mu_ref|,
  * g the discrete solution of (B - k* A) g = 0 with g(-1) = 1, g(+1) = 0 at the
  * box's most critical modified wavenumber k* = k1max^2 + k3max^2 + 6/(nu dt),

@@ -32,8 +32,9 @@ int chanh_build_mesh(int ny, double grid_re, double eta_w, const double* mesh, c
 
 // Near-wall mesh optimisation of Appendix B (see setup_host.cpp).  y_in: the
 // starting mesh; kstar: the Helmholtz modified wavenumber to fit; npts: mesh
-// points per wall in the optimisation (the wall point stays); C: displacement
-// penalty; iters: steepest-descent iterations.  Writes the mesh to y_out and
+// points per wall in the optimisation (the wall point stays; each moved cell stays
+// within a factor of two of its starting size); C: displacement penalty; iters:
+// steepest-descent iterations.  Writes the mesh to y_out and
 // the Helmholtz errors before and after.  Returns 0, or < 0 on bad input.
 int chanh_optimize_mesh(int ny, const double* y_in, double kstar, int npts, double C, int iters, double* y_out,
                         double* err_before, double* err_after);

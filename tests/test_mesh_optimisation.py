@@ -32,3 +32,23 @@ def test_optimised_mesh_reduces_the_helmholtz_error():
     I = slice(1, Ny - 1)
     ev = np.linalg.eigvals(np.linalg.solve(A[I, I], B[I, I]))
     assert ev.real.max() < 0 and np.abs(ev.imag).max() <= 1e-8 * np.abs(ev.real).max()
+
+
+def test_the_papers_re2000_box_keeps_its_spacing():
+    """The paper's Re_tau 2000 box (8 pi x 3 pi, 6144 x 4096 modes; Ny = 513 and dt = 5e-5
+    here, which the paper does not fix).  There the error functional is lowest where the
+    first cell collapses onto the wall; the optimised grid keeps every moved cell within a
+    factor of two of its starting size (Appendix B: the points move slightly, the spacing
+    changes little) and still lowers |g - g_ana|, by the oracle's own coefficients."""
+    re, Lx, Lz, Nx, Ny, Nz, dt = 2000.0, 8 * math.pi, 3 * math.pi, 6144, 513, 4096, 5e-5
+    y0, _, _ = chan.optimize_mesh(re, Lx, Lz, Nx, Ny, Nz, dt, iters=0)
+    y, e_before, e_after = chan.optimize_mesh(re, Lx, Lz, Nx, Ny, Nz, dt, iters=60)
+    kstar = ((2 * math.pi / Lx * (Nx // 2 - 1)) ** 2 + (2 * math.pi / Lz * (Nz // 2 - 1)) ** 2
+             + 1.0 / ((1.0 / 6.0) * (1.0 / re) * dt))
+    ob, oa = O.helmholtz_error(y0, kstar), O.helmholtz_error(y, kstar)
+    assert abs(ob - e_before) < 1e-6 * ob and abs(oa - e_after) < 1e-6 * ob
+    assert oa < ob / 1.3
+    assert y[0] == -1.0 and y[-1] == 1.0 and np.array_equal(y, -y[::-1]) and np.all(np.diff(y) > 0)
+    r = np.diff(y[:22]) / np.diff(y0[:22])
+    assert r.min() >= 0.5 - 1e-12 and r.max() <= 2.0 + 1e-12
+    assert np.array_equal(y[21:Ny - 21], y0[21:Ny - 21])
